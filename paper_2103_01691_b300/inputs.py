@@ -1,0 +1,90 @@
+"""Seeded synthetic inputs for the five workloads (shared by tests, the
+oracle checks and the benchmark).
+
+This module holds random draws and their shaping only; none of the
+method's arithmetic lives here.  Quantities the method computes (grid
+nodes, quadrature weights) are passed in by the caller, so each side uses
+its own.  Every tensor follows the paper's layout (section 4.1: i_1
+fastest): a numpy array of shape (n_d, ..., n_1).
+
+Random numbers come from ``numpy.random.default_rng(seed)`` (PCG64),
+drawn in float64 on the host.
+"""
+from __future__ import annotations
+
+import numpy as np
+
+
+def heat_u0(n: int = 32, seed: int = 0) -> np.ndarray:
+    """Real FP64 heat initial datum, i.i.d. uniform on [-1, 1]."""
+    rng = np.random.default_rng(seed)
+    return 2.0 * rng.random((n, n, n)) - 1.0
+
+
+def complex_normal(shape, seed: int) -> np.ndarray:
+    """Complex normal tensor: real and imaginary parts i.i.d. N(0, 1)."""
+    rng = np.random.default_rng(seed)
+    re = rng.standard_normal(shape)
+    im = rng.standard_normal(shape)
+    return re + 1j * im
+
+
+def free_schrodinger_u0(n: int = 256, seed: int = 2) -> np.ndarray:
+    """Random complex normal datum for the free Schroedinger precision sweep."""
+    return complex_normal((n, n, n), seed)
+
+
+def gaussian_at_nodes(x: np.ndarray) -> np.ndarray:
+    """pi^{-3/4} exp(-|x|^2 / 2) on the tensor grid of 1D nodes x (m^3 values)."""
+    g = np.exp(-0.5 * x * x)
+    return (np.pi ** -0.75) * g[:, None, None] * g[None, :, None] * g[None, None, :]
+
+
+def _normalise(psi: np.ndarray, W: np.ndarray) -> np.ndarray:
+    w3 = W[:, None, None] * W[None, :, None] * W[None, None, :]
+    return psi / np.sqrt(np.sum(np.abs(psi) ** 2 * w3))
+
+
+def harmonic_psi0(x: np.ndarray, W: np.ndarray, seed: int = 1, sigma: float = 0.1) -> np.ndarray:
+    """Normalised Gaussian times (1 + sigma (xi_r + i xi_i)), xi i.i.d. N(0,1)
+    at the nodes, renormalised in the discrete weighted norm."""
+    m = x.size
+    rng = np.random.default_rng(seed)
+    xi = rng.standard_normal((m, m, m)) + 1j * rng.standard_normal((m, m, m))
+    return _normalise(gaussian_at_nodes(x) * (1.0 + sigma * xi), W)
+
+
+def gpe_psi0(x: np.ndarray, W: np.ndarray, seed: int = 4, noise: float = 0.05) -> np.ndarray:
+    """Normalised Gaussian ground-state guess with a random phase
+    exp(i noise xi), xi i.i.d. N(0,1), renormalised."""
+    m = x.size
+    rng = np.random.default_rng(seed)
+    xi = rng.standard_normal((m, m, m))
+    return _normalise(gaussian_at_nodes(x) * np.exp(1j * noise * xi), W)
+
+
+def gpe_target(x: np.ndarray, W: np.ndarray) -> np.ndarray:
+    """Noise-free normalised Gaussian, the target state of the adjoint loss."""
+    return _normalise(gaussian_at_nodes(x).astype(np.complex128), W)
+
+
+def batched_dims(count: int = 64, seed: int = 3) -> np.ndarray:
+    """Per-direction sizes of the uneven batch: uniform on {48, 64, ..., 160}."""
+    rng = np.random.default_rng(seed)
+    return 48 + 16 * rng.integers(0, 8, size=(count, 3))
+
+
+def batched_u0(dims: np.ndarray, seed: int = 3) -> list:
+    """One complex normal datum per problem, drawn after the sizes."""
+    rng = np.random.default_rng(seed)
+    rng.integers(0, 8, size=(dims.shape[0], 3))  # the size draw comes first
+    out = []
+    for n1, n2, n3 in dims:
+        shape = (int(n3), int(n2), int(n1))
+        out.append(rng.standard_normal(shape) + 1j * rng.standard_normal(shape))
+    return out
+
+
+def direction(shape, seed: int = 5) -> np.ndarray:
+    """Random complex direction for finite-difference checks."""
+    return complex_normal(shape, seed)

@@ -1,0 +1,309 @@
+"""Pins for the FP64 CPU oracle, against facts fixed independently of it:
+library routines in special cases (scipy expm, numpy hermgauss, scipy
+Hermite polynomials), the Kronecker-sum identity, closed forms, invariants
+and the values the paper prints.  CPU only."""
+import math
+import os
+
+import numpy as np
+import pytest
+import scipy.linalg
+import scipy.special
+
+from paper_2103_01691_b300 import inputs
+
+GOLDEN = os.path.join(os.path.dirname(__file__), "golden")
+
+
+def kron_operator(mats, mu):
+    """I_d x ... x L_mu x ... x I_1 for vectorisation with i_1 fastest
+    (section 2, eq. (tensor-structure))."""
+    d = len(mats)
+    out = np.array([[1.0]])
+    for v in range(d, 0, -1):  # leftmost factor is direction d
+        f = mats[v - 1] if v == mu else np.eye(mats[v - 1].shape[1])
+        out = np.kron(out, f)
+    return out
+
+
+# ---------------------------------------------------------------- operators
+
+def test_fd_dirichlet_special_case(orc):
+    A = orc.fd_dirichlet(3)  # h = 1/4
+    assert np.array_equal(A, 16.0 * np.array([[-2, 1, 0], [1, -2, 1], [0, 1, -2]]))
+
+
+def test_fd_periodic_special_case(orc):
+    A = orc.fd_periodic(4, 4.0)  # h = 1
+    expect = np.array([[-2, 1, 0, 1], [1, -2, 1, 0], [0, 1, -2, 1], [1, 0, 1, -2]], float)
+    assert np.array_equal(A, expect)
+
+
+@pytest.mark.parametrize("n", [4, 7, 16, 33])
+@pytest.mark.parametrize("z", [1e-3, -2e-3, 1e-4j, 0.05j, 1e-3 + 2e-3j])
+def test_expm_closed_form_vs_scipy(orc, n, z):
+    ref = scipy.linalg.expm(z * orc.fd_dirichlet(n))
+    got = orc.expm_dirichlet_fd(n, z)
+    assert np.max(np.abs(got - ref)) <= 1e-13 * max(1.0, np.max(np.abs(ref)))
+
+
+@pytest.mark.parametrize("scale", [0.1, 3.0, 40.0])
+def test_expm_taylor_vs_scipy(orc, scale):
+    rng = np.random.default_rng(11)
+    A = rng.standard_normal((9, 9)) + 1j * rng.standard_normal((9, 9))
+    A *= scale / np.linalg.norm(A, 1)
+    ref = scipy.linalg.expm(A)
+    got = orc.expm_taylor(A, 1.0)
+    assert np.max(np.abs(got - ref)) <= 1e-12 * np.max(np.abs(ref))
+
+
+def test_expm_taylor_matches_closed_form(orc):
+    n = 40
+    A = orc.fd_dirichlet(n)
+    for z in (1e-4j * 10, 2e-3):
+        assert np.max(np.abs(orc.expm_taylor(A, z) - orc.expm_dirichlet_fd(n, z))) < 1e-12
+
+
+# ------------------------------------------------------------ mode products
+
+@pytest.mark.parametrize("dims", [(4, 5), (5, 4), (4, 5, 6), (6, 5, 4), (3, 4, 2, 5)])
+def test_mode_product_is_kronecker_matvec(orc, dims):
+    """vec(U x_mu L) = (I x .. x L x .. x I) vec(U), L rectangular (Def. 2.1)."""
+    rng = np.random.default_rng(3)
+    U = rng.standard_normal(dims[::-1]) + 1j * rng.standard_normal(dims[::-1])
+    for mu in range(1, len(dims) + 1):
+        m = dims[mu - 1] + 2
+        L = rng.standard_normal((m, dims[mu - 1])) + 1j * rng.standard_normal((m, dims[mu - 1]))
+        mats = [np.eye(n) for n in dims]
+        mats[mu - 1] = L
+        ref = kron_operator(mats, mu) @ U.reshape(-1)
+        got = orc.mode_product(U, mu, L)
+        out_dims = list(dims)
+        out_dims[mu - 1] = m
+        assert got.shape == tuple(out_dims[::-1])
+        assert np.max(np.abs(got.reshape(-1) - ref)) < 1e-12
+
+
+@pytest.mark.parametrize("dims", [(4, 5), (4, 5, 6), (8, 7, 6), (5, 5, 5)])
+def test_tucker_equals_expm_of_kronecker_sum(orc, dims):
+    """Section 2: exp(t M) u0 with M = A_d (+) ... (+) A_1 equals the Tucker
+    operator with the 1D exponentials; A_mu arbitrary (non-symmetric)."""
+    rng = np.random.default_rng(7)
+    As = [rng.standard_normal((n, n)) for n in dims]
+    t = 0.3
+    M = sum(kron_operator(As, mu) for mu in range(1, len(dims) + 1))
+    U = rng.standard_normal(dims[::-1]) + 1j * rng.standard_normal(dims[::-1])
+    ref = scipy.linalg.expm(t * M) @ U.reshape(-1)
+    Es = [orc.expm_taylor(A, t) for A in As]
+    got = orc.tucker(U, Es)
+    assert np.linalg.norm(got.reshape(-1) - ref) <= 1e-13 * np.linalg.norm(ref)
+
+
+def test_mode_order_independence(orc):
+    import itertools
+
+    rng = np.random.default_rng(8)
+    dims = (6, 7, 5)
+    Es = [orc.expm_taylor(rng.standard_normal((n, n)), 0.2) for n in dims]
+    U = rng.standard_normal(dims[::-1]) + 1j * rng.standard_normal(dims[::-1])
+    base = orc.tucker(U, Es)
+    for order in itertools.permutations([1, 2, 3]):
+        got = orc.tucker(U, Es, order=order)
+        assert np.linalg.norm(got - base) <= 1e-14 * np.linalg.norm(base) * 10
+
+
+@pytest.mark.parametrize("z", [1e-3, 1e-4j])
+def test_sine_modes_decay_in_closed_form(orc, z):
+    """A product of discrete sine modes is an eigenvector of the Dirichlet FD
+    Kronecker sum: one step multiplies it by exp(z sum lambda_k)."""
+    n = 32
+    h = 1.0 / (n + 1)
+    j = np.arange(1, n + 1)
+    ks = (1, 5, 17)
+    vec = [np.sin(k * j * np.pi / (n + 1)) for k in ks]
+    U = vec[2][:, None, None] * vec[1][None, :, None] * vec[0][None, None, :]
+    lam = sum(-4.0 / h**2 * np.sin(k * np.pi / (2 * (n + 1))) ** 2 for k in ks)
+    E = orc.expm_dirichlet_fd(n, z)
+    got = orc.tucker(U.astype(complex), [E, E, E], nsteps=3)
+    ref = np.exp(3 * z * lam) * U
+    assert np.linalg.norm(got - ref) <= 1e-13 * np.linalg.norm(U)
+
+
+def test_unitary_flow_conserves_norm_and_one_shot(orc):
+    """i Lap flow: E = exp(i tau A) is unitary, so the l2 norm is conserved
+    (section 2, "conserved quantities ... are preserved"); and 10 steps of
+    exp(i tau A) equal one step of exp(10 i tau A)."""
+    n = 24
+    U = inputs.complex_normal((n, n, n), seed=2)
+    E1 = orc.expm_dirichlet_fd(n, 1e-4j)
+    E10 = orc.expm_dirichlet_fd(n, 1e-3j)
+    many = orc.tucker(U, [E1] * 3, nsteps=10)
+    once = orc.tucker(U, [E10] * 3)
+    assert abs(np.linalg.norm(many) / np.linalg.norm(U) - 1) < 1e-13
+    assert np.linalg.norm(many - once) <= 1e-12 * np.linalg.norm(once)
+
+
+def test_tucker3_entries_match_full(orc):
+    rng = np.random.default_rng(9)
+    dims = (7, 6, 5)
+    Es = [rng.standard_normal((n, n)) + 1j * rng.standard_normal((n, n)) for n in dims]
+    U = rng.standard_normal(dims[::-1]) + 1j * rng.standard_normal(dims[::-1])
+    full = orc.tucker(U, Es)
+    idx = np.array([[0, 0, 0], [6, 5, 4], [3, 2, 1], [1, 4, 2]])
+    got = orc.tucker3_entries(U, *Es, idx)
+    ref = full[idx[:, 2], idx[:, 1], idx[:, 0]]
+    assert np.max(np.abs(got - ref)) < 1e-12
+
+
+# ------------------------------------------------- printed heat errors (4.1, 5.1)
+
+def _golden_heat():
+    rows = []
+    with open(os.path.join(GOLDEN, "heat_errors.txt")) as f:
+        for line in f:
+            if line.startswith("#") or not line.strip():
+                continue
+            n, err, use = line.split()
+            if int(use):
+                rows.append((int(n), float(err)))
+    return rows
+
+
+@pytest.mark.parametrize("n,printed", [r for r in _golden_heat() if r[0] <= 100])
+def test_printed_heat_errors_3d(orc, n, printed):
+    """3D periodic heat, FD2, T = 1 (section 4.1, Test 1): the relative error
+    of the mu-mode solution equals the printed value to 3 digits."""
+    L = 2 * np.pi
+    x = np.arange(n) * (L / n)
+    c = np.cos(x)
+    U0 = c[:, None, None] + c[None, :, None] + c[None, None, :]
+    E = orc.expm_taylor(orc.fd_periodic(n, L), 1.0)
+    U = orc.tucker(U0.astype(complex), [E, E, E]).real
+    err = np.linalg.norm(U - np.exp(-1.0) * U0) / np.linalg.norm(np.exp(-1.0) * U0)
+    assert float(f"{err:.2e}") == printed
+
+
+@pytest.mark.parametrize("n,printed", [r for r in _golden_heat() if r[0] > 100])
+def test_printed_heat_errors_large_n(orc, n, printed):
+    """Section 5.1 errors (n = 200..400).  u0 is a sum of 1D cosines, so the
+    3D error equals the error of one direction's 1D problem."""
+    L = 2 * np.pi
+    x = np.arange(n) * (L / n)
+    E = orc.expm_taylor(orc.fd_periodic(n, L), 1.0)
+    u = (E @ np.cos(x)).real
+    err = np.linalg.norm(u - np.exp(-1.0) * np.cos(x)) / np.linalg.norm(np.exp(-1.0) * np.cos(x))
+    assert float(f"{err:.2e}") == printed
+
+
+# ------------------------------------------------------------------ Hermite
+
+@pytest.mark.parametrize("m", [1, 2, 5, 16, 64, 128, 150])
+def test_gauss_hermite_vs_numpy(orc, m):
+    x, w, W = orc.gauss_hermite(m)
+    xr, wr = np.polynomial.hermite.hermgauss(m)
+    assert np.max(np.abs(x - xr)) < 1e-13 * max(1.0, np.max(np.abs(xr)))
+    big = wr > 1e-280
+    assert np.max(np.abs(w[big] - wr[big]) / wr[big]) < 1e-11
+    assert abs(w.sum() - math.sqrt(math.pi)) < 1e-14 * 10
+
+
+def test_hermite_functions_vs_scipy(orc):
+    x = np.linspace(-6, 6, 41)
+    H = orc.hermite_functions(21, x)
+    for k in range(21):
+        norm = math.sqrt(2.0**k * math.factorial(k) * math.sqrt(math.pi))
+        ref = scipy.special.eval_hermite(k, x) * np.exp(-x * x / 2) / norm
+        assert np.max(np.abs(H[k] - ref)) < 1e-13
+
+
+@pytest.mark.parametrize("m", [16, 64, 128, 192, 256])
+def test_discrete_orthonormality(orc, m):
+    """Section 3: with m = k Gauss-Hermite nodes the Hermite functions are
+    orthonormal at the discrete level as well."""
+    x, _, W = orc.gauss_hermite(m)
+    H = orc.hermite_functions(m, x)
+    G = (H * W) @ H.T
+    assert np.max(np.abs(G - np.eye(m))) < 1e-12
+
+
+def test_hermite_round_trip(orc):
+    m = 12
+    x, _, W = orc.gauss_hermite(m)
+    v = inputs.complex_normal((m, m, m), seed=6)
+    c = orc.hermite_forward(v, x, W)
+    back = orc.hermite_backward(c, x, W)
+    assert np.linalg.norm(back - v) <= 1e-12 * np.linalg.norm(v)
+
+
+def test_harmonic_oscillator_exact_phase(orc):
+    """phi_k1 phi_k2 phi_k3 is an eigenfunction with lambda = k1+k2+k3+3/2
+    (section 3); after t it picks up exp(-i lambda t); after t = 2 pi it is
+    -psi0."""
+    m = 16
+    x, _, W = orc.gauss_hermite(m)
+    H = orc.hermite_functions(m, x)
+    k1, k2, k3 = 3, 0, 7
+    psi0 = (H[k3][:, None, None] * H[k2][None, :, None] * H[k1][None, None, :]).astype(complex)
+    lam = k1 + k2 + k3 + 1.5
+    tau, steps = 0.01, 25
+    got = orc.ho_steps(psi0, x, W, tau, steps)
+    assert np.max(np.abs(got - np.exp(-1j * lam * tau * steps) * psi0)) < 1e-12
+    period = orc.ho_steps(psi0, x, W, 2 * np.pi / 8, 8)
+    assert np.max(np.abs(period + psi0)) < 1e-12
+
+
+# ---------------------------------------------------------------------- GPE
+
+def test_gpe_beta_zero_is_linear_flow(orc):
+    m = 10
+    x, _, W = orc.gauss_hermite(m)
+    psi0 = inputs.gpe_psi0(x, W)
+    a = orc.gpe_steps(psi0, x, W, 0.0, 0.01, 5)
+    b = orc.ho_steps(psi0, x, W, 0.01, 5)
+    assert np.linalg.norm(a - b) < 1e-13
+
+
+def test_gpe_norm_and_reversibility(orc):
+    m = 12
+    x, _, W = orc.gauss_hermite(m)
+    w3 = orc.weight3(W)
+    psi0 = inputs.gpe_psi0(x, W)
+    fwd = orc.gpe_steps(psi0, x, W, 100.0, 1e-3, 20)
+    n0 = np.sum(np.abs(psi0) ** 2 * w3)
+    assert abs(np.sum(np.abs(fwd) ** 2 * w3) / n0 - 1) < 1e-12
+    back = orc.gpe_steps(fwd, x, W, 100.0, -1e-3, 20)
+    assert orc.rel_l2(back, psi0, w3) < 1e-11
+
+
+def test_gpe_second_order_in_tau(orc):
+    m = 10
+    x, _, W = orc.gauss_hermite(m)
+    psi0 = inputs.gpe_psi0(x, W)
+    T = 0.08
+    ref = orc.gpe_steps(psi0, x, W, 100.0, T / 64, 64)
+    e1 = np.linalg.norm(orc.gpe_steps(psi0, x, W, 100.0, T / 4, 4) - ref)
+    e2 = np.linalg.norm(orc.gpe_steps(psi0, x, W, 100.0, T / 8, 8) - ref)
+    assert 3.0 < e1 / e2 < 5.0
+
+
+def test_gpe_adjoint_finite_differences(orc):
+    m = 8
+    x, _, W = orc.gauss_hermite(m)
+    w3 = orc.weight3(W)
+    beta, tau, steps = 100.0, 1e-3, 6
+    psi0 = inputs.gpe_psi0(x, W)
+    target = inputs.gpe_target(x, W)
+
+    def J(p):
+        pT = orc.gpe_steps(p, x, W, beta, tau, steps)
+        return float(np.sum(np.abs(pT - target) ** 2 * w3))
+
+    pT = orc.gpe_steps(psi0, x, W, beta, tau, steps)
+    gT = 2.0 * w3 * (pT - target)
+    g0 = orc.gpe_adjoint(psi0, gT, x, W, beta, tau, steps)
+    delta = inputs.direction(psi0.shape)
+    delta /= np.linalg.norm(delta)
+    eps = 1e-6
+    fd = (J(psi0 + eps * delta) - J(psi0 - eps * delta)) / (2 * eps)
+    an = float(np.real(np.vdot(g0, delta)))
+    assert abs(fd - an) <= 1e-7 * max(abs(an), 1e-12) + 1e-12
