@@ -1,0 +1,235 @@
+/*
+ * mumode.h -- C ABI of the B300 mu-mode integrator library (libmumode.so).
+ *
+ * The library applies the mu-mode integrator of Caliari, Cassini, Einkemmer,
+ * Ostermann and Zivcovich (arXiv 2103.01691) on one GPU: the Tucker operator
+ * U x_1 E_1 x_2 E_2 ... x_d E_d with precomputed one-dimensional
+ * exponentials E_mu = exp(tau A_mu) (section 2, eq. (dd-tensor)), Hermite
+ * spectral transforms written as mu-mode products (section 3, eqs.
+ * (real2spec) and (spec2real)), and the Strang splitting step of the cubic
+ * nonlinear Schroedinger / Gross-Pitaevskii equation (section 4.5).
+ *
+ * Conventions shared by every call
+ * --------------------------------
+ * Tensor layout.  A d-way tensor with sizes n[0..d-1] = (n_1, ..., n_d) is
+ *   stored with i_1 fastest: element (i_1, ..., i_d) (0-based) lives at
+ *   i_1 + n_1 (i_2 + n_2 (i_3 + ...)) (section 4.1, after eq. (exactsol)).
+ *   A torch tensor of shape (n_d, ..., n_1), contiguous, has this layout.
+ * Matrices.  Host matrices are row-major FP64.  Complex host matrices are
+ *   interleaved (re, im) pairs: entry (i, j) of an m x n complex matrix is
+ *   at [2 (i n + j)] (re) and [2 (i n + j) + 1] (im).
+ * Complex device data.  MM_C64 is interleaved (re, im) float32 pairs,
+ *   MM_C128 interleaved float64 pairs.
+ * Ownership.  The caller owns every pointer it passes.  *_dev pointers are
+ *   device memory of the context's device, 16-byte aligned, holding the
+ *   full tensor contiguously.  Plans own their device copies of the
+ *   matrices and their workspace.
+ * Streams.  `stream` is a cudaStream_t passed as void*; NULL is the legacy
+ *   default stream.  Calls enqueue work and return without synchronising
+ *   unless stated.
+ * Errors.  Every call returns mm_status.  Arguments are checked before
+ *   any work is enqueued; on failure nothing is launched and
+ *   mm_last_error() (thread-local) describes the problem.  Device-side
+ *   bounded waits never hang: when one gives up the kernel records
+ *   MM_ERR_TIMEOUT in the context's device error word, which
+ *   mm_device_status() reads.  Nothing aborts or traps.
+ */
+#ifndef MUMODE_H
+#define MUMODE_H
+
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef struct mm_ctx mm_ctx;
+typedef struct mm_plan mm_plan;
+
+typedef enum {
+    MM_OK = 0,
+    MM_ERR_INVALID_ARG = 1, /* null pointer, bad index or value */
+    MM_ERR_SHAPE = 2,       /* sizes outside what the chosen path supports */
+    MM_ERR_DTYPE = 3,       /* dtype / precision combination not supported */
+    MM_ERR_ALIGN = 4,       /* device pointer not 16-byte aligned */
+    MM_ERR_OOM = 5,         /* device allocation failed */
+    MM_ERR_CUDA = 6,        /* a CUDA runtime call failed */
+    MM_ERR_TIMEOUT = 7,     /* a device-side bounded wait gave up */
+    MM_ERR_UNSUPPORTED = 8  /* feature not available on this device */
+} mm_status;
+
+typedef enum {
+    MM_R64 = 0,  /* real float64 */
+    MM_C64 = 1,  /* complex float32 (interleaved) */
+    MM_C128 = 2, /* complex float64 (interleaved) */
+    MM_R32 = 3   /* real float32 */
+} mm_dtype;
+
+/* Arithmetic of the mode contractions.
+ * MM_PREC_FP64_SIMT  FP64 FMA on CUDA cores; state MM_R64 or MM_C128.
+ * MM_PREC_FP32_SIMT  FP32 FMA on CUDA cores; state MM_R32 or MM_C64.
+ * MM_PREC_BF16X6     tcgen05 tensor cores, state MM_C64.  Matrix and state
+ *                    are split into three BF16 pieces (x = x0 + x1 + x2,
+ *                    exact for FP32 x), the six products with piece
+ *                    orders a + b <= 2 are summed in FP32 in tensor memory,
+ *                    the leading product in an accumulator of its own.
+ * MM_PREC_BF16X3     as above with two pieces and the three products
+ *                    a + b <= 1.
+ * MM_PREC_BF16       one BF16 piece, one product (reported, not accurate). */
+typedef enum {
+    MM_PREC_FP64_SIMT = 0,
+    MM_PREC_FP32_SIMT = 1,
+    MM_PREC_BF16X6 = 2,
+    MM_PREC_BF16X3 = 3,
+    MM_PREC_BF16 = 4
+} mm_prec;
+
+/* ---------------------------------------------------------------------
+ * Context
+ * ------------------------------------------------------------------- */
+
+/* Create a context on CUDA device `device` (makes it current for the
+ * calling thread).  Allocates a small device error word.  *out receives
+ * the context.  Errors: MM_ERR_INVALID_ARG (out NULL or bad device),
+ * MM_ERR_CUDA, MM_ERR_UNSUPPORTED (device is not sm_103). */
+mm_status mm_ctx_create(int device, mm_ctx **out);
+void mm_ctx_destroy(mm_ctx *ctx);
+
+/* Thread-local description of the last failure (never NULL). */
+const char *mm_last_error(void);
+
+/* Synchronise `stream`, read and clear the context's device error word.
+ * Returns MM_OK, MM_ERR_TIMEOUT (a bounded device wait gave up) or
+ * MM_ERR_CUDA (a kernel or copy failed). */
+mm_status mm_device_status(mm_ctx *ctx, void *stream);
+
+/* Number of kernels this library has launched in the calling process
+ * (all contexts), for launch accounting. */
+int64_t mm_launch_count(void);
+
+/* Kernel timing (tracing aid, not from the paper).  While enabled, every
+ * mode-product kernel launched through `ctx` is bracketed by a pair of CUDA
+ * events on its stream.  mm_kernel_timing_read() waits for the recorded
+ * events, returns the summed kernel time in milliseconds and the number of
+ * timed launches, and starts a new record.  Enabling also clears the
+ * record.  Errors: MM_ERR_INVALID_ARG for NULL arguments, MM_ERR_CUDA. */
+mm_status mm_kernel_timing(mm_ctx *ctx, int enable);
+mm_status mm_kernel_timing_read(mm_ctx *ctx, double *total_ms, int64_t *launches);
+
+/* ---------------------------------------------------------------------
+ * Host set-up in FP64 (section 2: the d small exponentials are computed
+ * once for a constant step; section 4.1: expm by scaling and squaring).
+ * ------------------------------------------------------------------- */
+
+/* Centered second-order FD Laplacian with homogeneous Dirichlet conditions
+ * on (0,1), interior nodes x_j = j/(n+1): A = (n+1)^2 tridiag(1,-2,1),
+ * n x n row-major into A_out (caller-allocated, n*n doubles). */
+mm_status mm_fd_laplacian_dirichlet(int n, double *A_out);
+
+/* E = exp(z A) in FP64 for an n x n matrix A (real part A_re, imaginary
+ * part A_im or NULL) and a complex scalar z = z_re + i z_im, by scaling and
+ * squaring with the degree-13 Pade approximant (Higham 2005).  E_out is an
+ * n x n complex matrix (2*n*n doubles, interleaved), caller-allocated. */
+mm_status mm_expm(int n, const double *A_re, const double *A_im, double z_re, double z_im,
+                  double *E_out);
+
+/* Gauss-Hermite rule with m nodes (section 3, eq. (quadrature); the nodes
+ * make the Hermite functions discretely orthonormal).  x_out: nodes
+ * ascending; W_out: weights for plain integrals, sum_l W_l f(x_l) ~ int f,
+ * i.e. the Gauss weights for exp(-x^2) times exp(x_l^2).  Computed as the
+ * eigenvalues of the Jacobi matrix (Golub-Welsch) by Sturm bisection, then
+ * W_l = 1 / sum_{k<m} phi_k(x_l)^2.  Both arrays hold m doubles. */
+mm_status mm_gauss_hermite(int m, double *x_out, double *W_out);
+
+/* Hermite-function matrices at the m Gauss-Hermite nodes (section 3):
+ * fwd[k][l] = phi_k(x_l) W_l   (values -> coefficients, eq. (real2spec)
+ *                               with the weights folded in),
+ * bwd[l][k] = phi_k(x_l)       (coefficients -> values, eq. (spec2real),
+ *                               Psi = Phi^*).
+ * Either output may be NULL.  m x m doubles each, row-major. */
+mm_status mm_hermite_matrices(int m, double *fwd, double *bwd);
+
+/* ---------------------------------------------------------------------
+ * mu-mode product (Definition 2.1): S = U x_mu L.
+ * d in 1..8, n[0..d-1] the sizes of U, mu in 1..d, L an m x n_mu matrix
+ * (FP64 host, complex interleaved if L_is_complex), S has n_mu replaced by
+ * m.  u_dev and s_dev must not overlap.  dtype / prec:
+ *   MM_PREC_FP64_SIMT with MM_C128 (or MM_R64 if L is real),
+ *   MM_PREC_FP32_SIMT with MM_C64 (or MM_R32 if L is real),
+ *   MM_PREC_BF16* with MM_C64; tensor-core paths need n_mu, m <= 256.
+ * The matrix is uploaded on every call (use a plan for repeated use);
+ * the call allocates and frees its temporaries, so it synchronises the
+ * stream before returning.
+ * ------------------------------------------------------------------- */
+mm_status mumode_product(mm_ctx *ctx, int d, const int64_t *n, int mu, const double *L,
+                         int64_t m, int L_is_complex, mm_dtype dtype, mm_prec prec,
+                         const void *u_dev, void *s_dev, void *stream);
+
+/* ---------------------------------------------------------------------
+ * Tucker-operator plan: U <- U x_{o_1} E_{o_1} ... x_{o_d} E_{o_d}
+ * (section 2, eq. (dd-tensor)), repeated nsteps times (a marching scheme
+ * with constant step).  E_host[mu-1] is the n_mu x n_mu matrix for
+ * direction mu (complex interleaved if E_is_complex).  mode_order lists
+ * the directions (1-based) in application order; NULL means 1..d.  The
+ * factors commute mathematically; the order only changes rounding.
+ * The plan uploads the matrices in the form the precision needs and
+ * allocates its workspace (two state-sized buffers).
+ * ------------------------------------------------------------------- */
+mm_status mumode_plan_create(mm_ctx *ctx, int d, const int64_t *n, const double *const *E_host,
+                             int E_is_complex, mm_dtype dtype, mm_prec prec,
+                             const int *mode_order, mm_plan **out);
+
+/* nsteps applications of the plan's Tucker operator to u_dev, in place. */
+mm_status mumode_step(mm_plan *plan, void *u_dev, int64_t nsteps, void *stream);
+
+/* The same on a HOST tensor (u_host, pinned or pageable): copies it to the
+ * plan's device staging buffer, steps, copies the result back, and
+ * synchronises the stream. */
+mm_status mumode_step_host(mm_plan *plan, void *u_host, int64_t nsteps, void *stream);
+
+void mm_plan_destroy(mm_plan *plan);
+
+/* ---------------------------------------------------------------------
+ * Hermite spectral method (section 3; section 4.3 HKP) for d = 3 with
+ * m = n_mu Gauss-Hermite nodes per direction (square transforms).
+ * ------------------------------------------------------------------- */
+
+/* Plan holding the forward / backward Hermite matrices of every direction
+ * and the harmonic-oscillator propagators.  dtype MM_C64 with a BF16*
+ * precision or MM_PREC_FP32_SIMT, or MM_C128 with MM_PREC_FP64_SIMT. */
+mm_status hermite_plan_create(mm_ctx *ctx, int d, const int64_t *n, mm_dtype dtype, mm_prec prec,
+                              mm_plan **out);
+
+/* Nodes and plain-integral weights of direction mu (1-based). */
+mm_status hermite_nodes(const mm_plan *plan, int mu, double *x_out, double *W_out);
+
+/* values at the nodes -> coefficients: F_hat = F x_1 Phi_1^W ... (eq. (real2spec)). */
+mm_status hermite_forward(mm_plan *plan, const void *values_dev, void *coeffs_dev, void *stream);
+
+/* coefficients -> values at the nodes: F = F_hat x_1 Psi_1 ... (eq. (spec2real)). */
+mm_status hermite_backward(mm_plan *plan, const void *coeffs_dev, void *values_dev, void *stream);
+
+/* nsteps exact steps of i psi_t = -1/2 Lap psi + |x|^2/2 psi (HKP with the
+ * harmonic potential): forward transform, phase exp(-i tau (k1+k2+k3+3/2)),
+ * backward transform.  The three factors of every direction are folded
+ * into one complex matrix Psi_mu D_mu Phi_mu^W (the phase is separable),
+ * so a step is three complex mu-mode products.  In place. */
+mm_status hermite_ho_step(mm_plan *plan, void *psi_dev, double tau, int64_t nsteps, void *stream);
+
+/* nsteps Strang steps of i psi_t = -1/2 Lap psi + |x|^2/2 psi + beta |psi|^2 psi
+ * (section 4.5): half linear step, exact nonlinear phase
+ * psi <- psi exp(-i tau beta |psi|^2), half linear step.  Adjacent linear
+ * halves of consecutive steps are merged into one full step; the nonlinear
+ * phase is applied in the epilogue of the last mode product.  In place. */
+mm_status split_step_gpe(mm_plan *plan, void *psi_dev, double beta, double tau, int64_t nsteps,
+                         void *stream);
+
+/* FP64 sum of |u|^2 (times w_l = W_l1 W_l2 W_l3 for a Hermite plan when
+ * weighted != 0) over the plan's tensor; the result is written to
+ * *out_host after synchronising the stream. */
+mm_status mm_norm2(mm_plan *plan, const void *u_dev, int weighted, double *out_host, void *stream);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* MUMODE_H */

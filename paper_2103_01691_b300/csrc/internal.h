@@ -1,0 +1,77 @@
+// Internal declarations shared by the library's translation units.
+#pragma once
+
+#include <cuda_runtime.h>
+
+#include <complex>
+#include <cstdint>
+
+#include "mumode.h"
+
+namespace mm {
+
+// ---- host set-up (host_setup.cpp) ---------------------------------------
+void fd_laplacian_dirichlet(int n, double *A);
+bool expm(int n, const double *Are, const double *Aim, std::complex<double> z, std::complex<double> *E);
+bool gauss_hermite(int m, double *x, double *W);
+void hermite_matrices(int m, const double *x, const double *W, double *fwd, double *bwd);
+
+// ---- error reporting (mumode_api.cu) --------------------------------------
+mm_status fail(mm_status st, const char *fmt, ...);
+void count_launch(int k = 1);
+
+// ---- CUDA-core kernels (simt_kernels.cu) ----------------------------------
+// Y[r][i][l] = sum_j L[i][j] X[r][j][l]; i < m, j < n, l < left, r < right.
+// `complex_data` selects interleaved complex elements; L has the same
+// element type as the data.  fp64 selects double, otherwise float.
+cudaError_t simt_mode_product(bool fp64, bool complex_data, int64_t left, int64_t n, int64_t right,
+                              int64_t m, const void *L, const void *X, void *Y, cudaStream_t s);
+// psi *= exp(-i tb |psi|^2) for count complex elements.
+cudaError_t simt_nonlinear_phase(bool fp64, int64_t count, double tb, void *psi, cudaStream_t s);
+// out (device double) += sum |u|^2 w, w = w1[i1] w2[i2] w3[i3] if w1 != NULL.
+cudaError_t norm2_accumulate(mm_dtype dt, int64_t n1, int64_t n2, int64_t n3, const void *u,
+                             const double *w1, const double *w2, const double *w3, double *out,
+                             cudaStream_t s);
+
+// ---- tensor-core path (tc_kernels.cu) -------------------------------------
+constexpr int kMaxDims = 8;
+
+// Device layout of the split state: pieces[c][p][...] for c in {re, im},
+// p < npieces, each plane the padded tensor (sizes np[]) in bf16.
+struct TcState {
+    int d = 0;
+    int64_t n[kMaxDims] = {};   // logical sizes
+    int64_t np[kMaxDims] = {};  // padded sizes (multiples of 16)
+    int64_t plane = 0;          // elements per plane = prod np
+};
+
+// Per-direction matrix in the tensor-core form (device, bf16 pieces).
+struct TcMatrix {
+    int64_t n_in = 0, n_out = 0;    // logical sizes (columns, rows)
+    int64_t k_pad = 0;              // padded contraction length
+    int ni = 0, it = 0;             // number of row tiles, rows per tile
+    void *pieces = nullptr;         // [p][tile][3 blocks (-S, C, S)][it][k_pad] bf16
+    int npieces = 0;
+};
+
+int tc_pieces(mm_prec p);
+bool tc_prec(mm_prec p);
+// Build the bf16 pieces of an m x n complex matrix (interleaved FP64, row-major).
+mm_status tc_matrix_create(const double *E, int64_t m, int64_t n, int npieces, TcMatrix *out);
+void tc_matrix_destroy(TcMatrix *M);
+// Split an interleaved complex64 tensor into padded bf16 piece planes.
+cudaError_t tc_split(const TcState &st, int npieces, const void *u_c64, void *pieces, cudaStream_t s);
+// Sum the piece planes back into an interleaved complex64 tensor.
+cudaError_t tc_merge(const TcState &st, int npieces, const void *pieces, void *u_c64, cudaStream_t s);
+
+struct TcEpilogue {
+    int kind = 0;      // 0: store pieces, 1: nonlinear phase then store pieces
+    double tb = 0.0;   // tau * beta for kind 1
+};
+// One mu-mode product on the split state: in (sizes st_in) -> out (sizes
+// st_out, equal except direction mu which becomes M.n_out).
+cudaError_t tc_mode_product(const TcState &st_in, const TcState &st_out, int mu, const TcMatrix &M,
+                            mm_prec prec, const void *in_pieces, void *out_pieces,
+                            const TcEpilogue &epi, int *d_err, cudaStream_t s);
+
+}  // namespace mm

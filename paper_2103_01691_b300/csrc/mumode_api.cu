@@ -1,0 +1,822 @@
+// C ABI of the library (declared in include/mumode.h): argument checking,
+// contexts, plans and the per-step launch sequences.
+#include <cuda_runtime.h>
+
+#include <atomic>
+#include <cmath>
+#include <complex>
+#include <cstdarg>
+#include <cstdio>
+#include <cstring>
+#include <vector>
+
+#include "internal.h"
+
+using cd = std::complex<double>;
+
+struct mm_ctx {
+    int device = 0;
+    int sm_major = 0, sm_minor = 0;
+    int *d_err = nullptr;
+    double *d_scratch = nullptr;  // one double for reductions
+    // optional CUDA-event timing of the mode-product kernels
+    bool timing = false;
+    std::vector<std::pair<cudaEvent_t, cudaEvent_t>> events;
+    size_t events_used = 0;
+};
+
+struct mm_plan {
+    mm_ctx *ctx = nullptr;
+    bool hermite = false;
+    int d = 0;
+    int64_t n[mm::kMaxDims] = {};
+    int64_t count = 0;
+    mm_dtype dtype = MM_C64;
+    mm_prec prec = MM_PREC_BF16X6;
+    int order[mm::kMaxDims] = {};
+    bool tc = false;
+    int npieces = 0;
+    // Tucker matrices (one per direction) in the form of the precision
+    void *Edev[mm::kMaxDims] = {};        // SIMT: element type of the state
+    mm::TcMatrix Etc[mm::kMaxDims] = {};  // tensor cores
+    // workspace
+    mm::TcState st;
+    void *work[2] = {nullptr, nullptr};  // TC: piece buffers; SIMT: work[0] state-sized
+    size_t work_bytes = 0;
+    void *staging = nullptr;  // device copy for host stepping
+    // Hermite data
+    std::vector<double> x[mm::kMaxDims], W[mm::kMaxDims];
+    std::vector<double> fwd[mm::kMaxDims], bwd[mm::kMaxDims];
+    double *Wdev[mm::kMaxDims] = {};
+    void *Fdev[mm::kMaxDims] = {}, *Bdev[mm::kMaxDims] = {};      // SIMT forward/backward
+    mm::TcMatrix Ftc[mm::kMaxDims] = {}, Btc[mm::kMaxDims] = {};  // TC forward/backward
+    // cached harmonic propagators Psi D(s) Phi_W for up to two step sizes
+    double prop_s[2] = {NAN, NAN};
+    void *Pdev[2][mm::kMaxDims] = {};
+    mm::TcMatrix Ptc[2][mm::kMaxDims] = {};
+};
+
+namespace mm {
+
+static thread_local char g_err[512] = "no error";
+static std::atomic<long long> g_launches{0};
+
+mm_status fail(mm_status st, const char *fmt, ...)
+{
+    va_list ap;
+    va_start(ap, fmt);
+    vsnprintf(g_err, sizeof g_err, fmt, ap);
+    va_end(ap);
+    return st;
+}
+
+void count_launch(int k) { g_launches += k; }
+
+}  // namespace mm
+
+using mm::fail;
+
+namespace {
+
+size_t elem_bytes(mm_dtype dt)
+{
+    switch (dt) {
+    case MM_R64: return 8;
+    case MM_C64: return 8;
+    case MM_C128: return 16;
+    case MM_R32: return 4;
+    }
+    return 0;
+}
+bool is_complex(mm_dtype dt) { return dt == MM_C64 || dt == MM_C128; }
+
+mm_status cuda_fail(cudaError_t e, const char *what)
+{
+    return fail(MM_ERR_CUDA, "%s: %s", what, cudaGetErrorString(e));
+}
+
+mm_status check_dims(int d, const int64_t *n)
+{
+    if (d < 1 || d > mm::kMaxDims) return fail(MM_ERR_SHAPE, "d = %d outside 1..%d", d, mm::kMaxDims);
+    if (!n) return fail(MM_ERR_INVALID_ARG, "n is NULL");
+    for (int v = 0; v < d; ++v)
+        if (n[v] < 1 || n[v] > (int64_t(1) << 24)) return fail(MM_ERR_SHAPE, "n[%d] = %lld out of range", v, (long long)n[v]);
+    return MM_OK;
+}
+
+mm_status check_ptr(const void *p, const char *name)
+{
+    if (!p) return fail(MM_ERR_INVALID_ARG, "%s is NULL", name);
+    if (reinterpret_cast<uintptr_t>(p) % 16) return fail(MM_ERR_ALIGN, "%s is not 16-byte aligned", name);
+    return MM_OK;
+}
+
+mm_status check_combo(mm_dtype dt, mm_prec pr, bool matrix_complex)
+{
+    switch (pr) {
+    case MM_PREC_FP64_SIMT:
+        if (dt == MM_C128 || (dt == MM_R64 && !matrix_complex)) return MM_OK;
+        break;
+    case MM_PREC_FP32_SIMT:
+        if (dt == MM_C64 || (dt == MM_R32 && !matrix_complex)) return MM_OK;
+        break;
+    case MM_PREC_BF16X6:
+    case MM_PREC_BF16X3:
+    case MM_PREC_BF16:
+        if (dt == MM_C64) return MM_OK;
+        break;
+    default: return fail(MM_ERR_INVALID_ARG, "unknown precision %d", int(pr));
+    }
+    return fail(MM_ERR_DTYPE, "dtype %d is not supported with precision %d%s", int(dt), int(pr),
+                matrix_complex ? " and a complex matrix" : "");
+}
+
+// Matrix (m x n, host FP64, complex interleaved or real) -> device copy in
+// the element type of dt.  Real data types take the real part only.
+mm_status upload_simt(const double *L, int64_t m, int64_t n, bool Lc, mm_dtype dt, void **out)
+{
+    const size_t cnt = size_t(m * n);
+    std::vector<uint8_t> buf(cnt * elem_bytes(dt));
+    for (size_t q = 0; q < cnt; ++q) {
+        const double re = Lc ? L[2 * q] : L[q], im = Lc ? L[2 * q + 1] : 0.0;
+        switch (dt) {
+        case MM_R64: reinterpret_cast<double *>(buf.data())[q] = re; break;
+        case MM_R32: reinterpret_cast<float *>(buf.data())[q] = float(re); break;
+        case MM_C128:
+            reinterpret_cast<double *>(buf.data())[2 * q] = re;
+            reinterpret_cast<double *>(buf.data())[2 * q + 1] = im;
+            break;
+        case MM_C64:
+            reinterpret_cast<float *>(buf.data())[2 * q] = float(re);
+            reinterpret_cast<float *>(buf.data())[2 * q + 1] = float(im);
+            break;
+        }
+    }
+    cudaError_t e = cudaMalloc(out, buf.size());
+    if (e != cudaSuccess) return fail(MM_ERR_OOM, "cudaMalloc(%zu) failed", buf.size());
+    e = cudaMemcpy(*out, buf.data(), buf.size(), cudaMemcpyHostToDevice);
+    if (e != cudaSuccess) return cuda_fail(e, "matrix upload");
+    return MM_OK;
+}
+
+// complex interleaved copy of a real or complex host matrix
+std::vector<double> as_complex(const double *L, int64_t cnt, bool Lc)
+{
+    std::vector<double> out(size_t(2 * cnt));
+    for (int64_t q = 0; q < cnt; ++q) {
+        out[2 * q] = Lc ? L[2 * q] : L[q];
+        out[2 * q + 1] = Lc ? L[2 * q + 1] : 0.0;
+    }
+    return out;
+}
+
+mm::TcState make_state(int d, const int64_t *n)
+{
+    mm::TcState st;
+    st.d = d;
+    st.plane = 1;
+    for (int v = 0; v < d; ++v) {
+        st.n[v] = n[v];
+        st.np[v] = (n[v] + 15) / 16 * 16;
+        st.plane *= st.np[v];
+    }
+    return st;
+}
+
+void left_right(int d, const int64_t *n, int mu, int64_t *left, int64_t *right)
+{
+    *left = 1;
+    *right = 1;
+    for (int v = 0; v < mu - 1; ++v) *left *= n[v];
+    for (int v = mu; v < d; ++v) *right *= n[v];
+}
+
+// Events bracketing one mode-product launch when timing is on.
+cudaEvent_t timing_event(mm_ctx *c, bool start)
+{
+    if (!c->timing) return nullptr;
+    if (start) {
+        if (c->events_used == c->events.size()) {
+            cudaEvent_t a, b;
+            if (cudaEventCreate(&a) != cudaSuccess) return nullptr;
+            if (cudaEventCreate(&b) != cudaSuccess) {
+                cudaEventDestroy(a);
+                return nullptr;
+            }
+            c->events.push_back({a, b});
+        }
+        return c->events[c->events_used].first;
+    }
+    return c->events[c->events_used++].second;
+}
+
+// One Tucker sweep on the TC piece state: modes in plan order with
+// matrices M[mu-1]; cur is the index of the buffer holding the state.
+mm_status tc_sweep(mm_plan *p, mm::TcMatrix *const *M, int &cur, const mm::TcEpilogue &last_epi, cudaStream_t s)
+{
+    for (int q = 0; q < p->d; ++q) {
+        const int mu = p->order[q];
+        mm::TcEpilogue epi;
+        if (q == p->d - 1) epi = last_epi;
+        cudaEvent_t ev0 = timing_event(p->ctx, true);
+        if (ev0) cudaEventRecord(ev0, s);
+        cudaError_t e = mm::tc_mode_product(p->st, p->st, mu, *M[mu - 1], p->prec, p->work[cur], p->work[1 - cur],
+                                            epi, p->ctx->d_err, s);
+        if (ev0) cudaEventRecord(timing_event(p->ctx, false), s);
+        if (e != cudaSuccess) return cuda_fail(e, "tensor-core mode product launch");
+        cur = 1 - cur;
+    }
+    return MM_OK;
+}
+
+// One Tucker sweep on the SIMT state: u holds the state on entry and exit.
+mm_status simt_sweep(mm_plan *p, void *const *Ed, void *u, cudaStream_t s)
+{
+    const bool fp64 = p->dtype == MM_R64 || p->dtype == MM_C128;
+    const bool cplx = is_complex(p->dtype);
+    void *src = u, *dst = p->work[0];
+    for (int q = 0; q < p->d; ++q) {
+        const int mu = p->order[q];
+        int64_t left, right;
+        left_right(p->d, p->n, mu, &left, &right);
+        cudaEvent_t ev0 = timing_event(p->ctx, true);
+        if (ev0) cudaEventRecord(ev0, s);
+        cudaError_t e = mm::simt_mode_product(fp64, cplx, left, p->n[mu - 1], right, p->n[mu - 1], Ed[mu - 1], src, dst, s);
+        if (ev0) cudaEventRecord(timing_event(p->ctx, false), s);
+        if (e != cudaSuccess) return cuda_fail(e, "SIMT mode product launch");
+        std::swap(src, dst);
+    }
+    if (src != u) {
+        cudaError_t e = cudaMemcpyAsync(u, src, size_t(p->count) * elem_bytes(p->dtype), cudaMemcpyDeviceToDevice, s);
+        if (e != cudaSuccess) return cuda_fail(e, "state copy");
+    }
+    return MM_OK;
+}
+
+mm_status alloc_workspace(mm_plan *p)
+{
+    cudaError_t e;
+    if (p->tc) {
+        p->st = make_state(p->d, p->n);
+        p->work_bytes = size_t(p->st.plane) * 2 * p->npieces * 2;
+        for (int b = 0; b < 2; ++b) {
+            e = cudaMalloc(&p->work[b], p->work_bytes);
+            if (e != cudaSuccess) return fail(MM_ERR_OOM, "workspace cudaMalloc(%zu) failed", p->work_bytes);
+            e = cudaMemset(p->work[b], 0, p->work_bytes);
+            if (e != cudaSuccess) return cuda_fail(e, "workspace memset");
+        }
+    } else {
+        p->work_bytes = size_t(p->count) * elem_bytes(p->dtype);
+        e = cudaMalloc(&p->work[0], p->work_bytes);
+        if (e != cudaSuccess) return fail(MM_ERR_OOM, "workspace cudaMalloc(%zu) failed", p->work_bytes);
+    }
+    return MM_OK;
+}
+
+mm_status upload_matrix(mm_plan *p, const double *E, int64_t m, int64_t n, bool Ec, void **simt, mm::TcMatrix *tcm)
+{
+    if (p->tc) {
+        std::vector<double> c = as_complex(E, m * n, Ec);
+        return mm::tc_matrix_create(c.data(), m, n, p->npieces, tcm);
+    }
+    return upload_simt(E, m, n, Ec, p->dtype, simt);
+}
+
+mm_status plan_common(mm_ctx *ctx, int d, const int64_t *n, mm_dtype dtype, mm_prec prec, const int *order,
+                      bool matrix_complex, mm_plan **out, mm_plan **made)
+{
+    if (!ctx) return fail(MM_ERR_INVALID_ARG, "ctx is NULL");
+    if (!out) return fail(MM_ERR_INVALID_ARG, "out is NULL");
+    mm_status st = check_dims(d, n);
+    if (st) return st;
+    st = check_combo(dtype, prec, matrix_complex);
+    if (st) return st;
+    const bool tc = mm::tc_prec(prec);
+    if (tc) {
+        if (!(ctx->sm_major == 10 && ctx->sm_minor == 3))
+            return fail(MM_ERR_UNSUPPORTED, "tensor-core precisions need an sm_103 device (have sm_%d%d)", ctx->sm_major,
+                        ctx->sm_minor);
+        for (int v = 0; v < d; ++v)
+            if (n[v] > 256) return fail(MM_ERR_SHAPE, "tensor-core path supports n_mu <= 256 (n[%d] = %lld)", v, (long long)n[v]);
+    }
+    bool seen[mm::kMaxDims] = {};
+    auto *p = new mm_plan;
+    p->ctx = ctx;
+    p->d = d;
+    p->count = 1;
+    for (int v = 0; v < d; ++v) {
+        p->n[v] = n[v];
+        p->count *= n[v];
+        p->order[v] = order ? order[v] : v + 1;
+        if (p->order[v] < 1 || p->order[v] > d || seen[p->order[v] - 1]) {
+            delete p;
+            return fail(MM_ERR_INVALID_ARG, "mode_order is not a permutation of 1..%d", d);
+        }
+        seen[p->order[v] - 1] = true;
+    }
+    p->dtype = dtype;
+    p->prec = prec;
+    p->tc = tc;
+    p->npieces = mm::tc_pieces(prec);
+    *made = p;
+    return MM_OK;
+}
+
+// Psi D(s) Phi_W for one direction: D = diag(exp(-i s (k + 1/2))).
+std::vector<double> harmonic_propagator(const mm_plan *p, int v, double s)
+{
+    const int64_t m = p->n[v];
+    std::vector<cd> tmp(size_t(m * m));
+    for (int64_t k = 0; k < m; ++k) {
+        const cd ph = std::exp(cd(0, -s * (double(k) + 0.5)));
+        for (int64_t l = 0; l < m; ++l) tmp[size_t(k * m + l)] = ph * p->fwd[v][size_t(k * m + l)];
+    }
+    std::vector<double> P(size_t(2 * m * m), 0.0);
+    for (int64_t a = 0; a < m; ++a)
+        for (int64_t b = 0; b < m; ++b) {
+            cd acc = 0;
+            for (int64_t k = 0; k < m; ++k) acc += p->bwd[v][size_t(a * m + k)] * tmp[size_t(k * m + b)];
+            P[size_t(2 * (a * m + b))] = acc.real();
+            P[size_t(2 * (a * m + b) + 1)] = acc.imag();
+        }
+    return P;
+}
+
+void free_prop(mm_plan *p, int slot)
+{
+    for (int v = 0; v < p->d; ++v) {
+        if (p->Pdev[slot][v]) cudaFree(p->Pdev[slot][v]);
+        p->Pdev[slot][v] = nullptr;
+        mm::tc_matrix_destroy(&p->Ptc[slot][v]);
+    }
+    p->prop_s[slot] = NAN;
+}
+
+// Make sure the propagators for step s are in a cache slot; returns the slot.
+mm_status ensure_prop(mm_plan *p, double s, int avoid, int *slot)
+{
+    for (int k = 0; k < 2; ++k)
+        if (p->prop_s[k] == s) {
+            *slot = k;
+            return MM_OK;
+        }
+    int k = (avoid == 0) ? 1 : 0;
+    free_prop(p, k);
+    for (int v = 0; v < p->d; ++v) {
+        std::vector<double> P = harmonic_propagator(p, v, s);
+        mm_status st = upload_matrix(p, P.data(), p->n[v], p->n[v], true, &p->Pdev[k][v], &p->Ptc[k][v]);
+        if (st) return st;
+    }
+    p->prop_s[k] = s;
+    *slot = k;
+    return MM_OK;
+}
+
+}  // namespace
+
+extern "C" {
+
+const char *mm_last_error(void) { return mm::g_err; }
+
+int64_t mm_launch_count(void) { return mm::g_launches.load(); }
+
+mm_status mm_ctx_create(int device, mm_ctx **out)
+{
+    if (!out) return fail(MM_ERR_INVALID_ARG, "out is NULL");
+    int count = 0;
+    cudaError_t e = cudaGetDeviceCount(&count);
+    if (e != cudaSuccess) return cuda_fail(e, "cudaGetDeviceCount");
+    if (device < 0 || device >= count) return fail(MM_ERR_INVALID_ARG, "device %d not present (%d devices)", device, count);
+    e = cudaSetDevice(device);
+    if (e != cudaSuccess) return cuda_fail(e, "cudaSetDevice");
+    auto *c = new mm_ctx;
+    c->device = device;
+    cudaDeviceGetAttribute(&c->sm_major, cudaDevAttrComputeCapabilityMajor, device);
+    cudaDeviceGetAttribute(&c->sm_minor, cudaDevAttrComputeCapabilityMinor, device);
+    e = cudaMalloc(&c->d_err, sizeof(int));
+    if (e == cudaSuccess) e = cudaMemset(c->d_err, 0, sizeof(int));
+    if (e == cudaSuccess) e = cudaMalloc(&c->d_scratch, sizeof(double));
+    if (e != cudaSuccess) {
+        delete c;
+        return cuda_fail(e, "context allocation");
+    }
+    *out = c;
+    return MM_OK;
+}
+
+mm_status mm_kernel_timing(mm_ctx *ctx, int enable)
+{
+    if (!ctx) return fail(MM_ERR_INVALID_ARG, "ctx is NULL");
+    ctx->timing = enable != 0;
+    ctx->events_used = 0;
+    return MM_OK;
+}
+
+mm_status mm_kernel_timing_read(mm_ctx *ctx, double *total_ms, int64_t *launches)
+{
+    if (!ctx || !total_ms || !launches) return fail(MM_ERR_INVALID_ARG, "NULL argument");
+    double tot = 0.0;
+    for (size_t k = 0; k < ctx->events_used; ++k) {
+        cudaError_t e = cudaEventSynchronize(ctx->events[k].second);
+        float ms = 0.f;
+        if (e == cudaSuccess) e = cudaEventElapsedTime(&ms, ctx->events[k].first, ctx->events[k].second);
+        if (e != cudaSuccess) return cuda_fail(e, "event timing");
+        tot += ms;
+    }
+    *total_ms = tot;
+    *launches = int64_t(ctx->events_used);
+    ctx->events_used = 0;
+    return MM_OK;
+}
+
+void mm_ctx_destroy(mm_ctx *ctx)
+{
+    if (!ctx) return;
+    for (auto &pr : ctx->events) {
+        cudaEventDestroy(pr.first);
+        cudaEventDestroy(pr.second);
+    }
+    cudaFree(ctx->d_err);
+    cudaFree(ctx->d_scratch);
+    delete ctx;
+}
+
+mm_status mm_device_status(mm_ctx *ctx, void *stream)
+{
+    if (!ctx) return fail(MM_ERR_INVALID_ARG, "ctx is NULL");
+    cudaError_t e = cudaStreamSynchronize((cudaStream_t)stream);
+    if (e != cudaSuccess) return cuda_fail(e, "stream synchronize");
+    int word = 0;
+    e = cudaMemcpy(&word, ctx->d_err, sizeof(int), cudaMemcpyDeviceToHost);
+    if (e != cudaSuccess) return cuda_fail(e, "error word read");
+    if (word != 0) {
+        cudaMemset(ctx->d_err, 0, sizeof(int));
+        return fail(mm_status(word), "a device-side bounded wait gave up (status %d)", word);
+    }
+    return MM_OK;
+}
+
+mm_status mm_fd_laplacian_dirichlet(int n, double *A_out)
+{
+    if (n < 1) return fail(MM_ERR_SHAPE, "n = %d < 1", n);
+    if (!A_out) return fail(MM_ERR_INVALID_ARG, "A_out is NULL");
+    mm::fd_laplacian_dirichlet(n, A_out);
+    return MM_OK;
+}
+
+mm_status mm_expm(int n, const double *A_re, const double *A_im, double z_re, double z_im, double *E_out)
+{
+    if (n < 1) return fail(MM_ERR_SHAPE, "n = %d < 1", n);
+    if (!A_re || !E_out) return fail(MM_ERR_INVALID_ARG, "A_re or E_out is NULL");
+    if (!mm::expm(n, A_re, A_im, cd(z_re, z_im), reinterpret_cast<cd *>(E_out)))
+        return fail(MM_ERR_INVALID_ARG, "expm: singular Pade denominator");
+    return MM_OK;
+}
+
+mm_status mm_gauss_hermite(int m, double *x_out, double *W_out)
+{
+    if (m < 1 || m > 4096) return fail(MM_ERR_SHAPE, "m = %d outside 1..4096", m);
+    if (!x_out || !W_out) return fail(MM_ERR_INVALID_ARG, "x_out or W_out is NULL");
+    mm::gauss_hermite(m, x_out, W_out);
+    return MM_OK;
+}
+
+mm_status mm_hermite_matrices(int m, double *fwd, double *bwd)
+{
+    if (m < 1 || m > 4096) return fail(MM_ERR_SHAPE, "m = %d outside 1..4096", m);
+    std::vector<double> x(m), W(m);
+    mm::gauss_hermite(m, x.data(), W.data());
+    mm::hermite_matrices(m, x.data(), W.data(), fwd, bwd);
+    return MM_OK;
+}
+
+mm_status mumode_product(mm_ctx *ctx, int d, const int64_t *n, int mu, const double *L, int64_t m, int L_is_complex,
+                         mm_dtype dtype, mm_prec prec, const void *u_dev, void *s_dev, void *stream)
+{
+    if (!ctx) return fail(MM_ERR_INVALID_ARG, "ctx is NULL");
+    mm_status st = check_dims(d, n);
+    if (st) return st;
+    if (mu < 1 || mu > d) return fail(MM_ERR_INVALID_ARG, "mu = %d outside 1..%d", mu, d);
+    if (m < 1 || m > (int64_t(1) << 24)) return fail(MM_ERR_SHAPE, "m = %lld out of range", (long long)m);
+    if (!L) return fail(MM_ERR_INVALID_ARG, "L is NULL");
+    if ((st = check_ptr(u_dev, "u_dev")) || (st = check_ptr(s_dev, "s_dev"))) return st;
+    if ((st = check_combo(dtype, prec, L_is_complex != 0))) return st;
+    int64_t nout[mm::kMaxDims];
+    int64_t cnt_in = 1, cnt_out = 1;
+    for (int v = 0; v < d; ++v) {
+        nout[v] = (v == mu - 1) ? m : n[v];
+        cnt_in *= n[v];
+        cnt_out *= nout[v];
+    }
+    const size_t eb = elem_bytes(dtype);
+    const char *u0 = (const char *)u_dev, *s0 = (const char *)s_dev;
+    if (u0 < s0 + cnt_out * eb && s0 < u0 + cnt_in * eb) return fail(MM_ERR_INVALID_ARG, "u_dev and s_dev overlap");
+    cudaStream_t s = (cudaStream_t)stream;
+    const int64_t nmu = n[mu - 1];
+    if (!mm::tc_prec(prec)) {
+        void *Ld = nullptr;
+        if ((st = upload_simt(L, m, nmu, L_is_complex != 0, dtype, &Ld))) return st;
+        int64_t left, right;
+        left_right(d, n, mu, &left, &right);
+        const bool fp64 = dtype == MM_R64 || dtype == MM_C128;
+        cudaError_t e = mm::simt_mode_product(fp64, is_complex(dtype), left, nmu, right, m, Ld, u_dev, s_dev, s);
+        cudaError_t e2 = cudaStreamSynchronize(s);
+        cudaFree(Ld);
+        if (e != cudaSuccess) return cuda_fail(e, "SIMT mode product");
+        if (e2 != cudaSuccess) return cuda_fail(e2, "SIMT mode product (sync)");
+        return MM_OK;
+    }
+    if (!(ctx->sm_major == 10 && ctx->sm_minor == 3))
+        return fail(MM_ERR_UNSUPPORTED, "tensor-core precisions need an sm_103 device");
+    if (nmu > 256 || m > 256) return fail(MM_ERR_SHAPE, "tensor-core path supports n_mu, m <= 256");
+    const int NP = mm::tc_pieces(prec);
+    std::vector<double> Lc = as_complex(L, m * nmu, L_is_complex != 0);
+    mm::TcMatrix M;
+    if ((st = mm::tc_matrix_create(Lc.data(), m, nmu, NP, &M))) return st;
+    mm::TcState si = make_state(d, n), so = make_state(d, nout);
+    void *bi = nullptr, *bo = nullptr;
+    const size_t bytes_i = size_t(si.plane) * 2 * NP * 2, bytes_o = size_t(so.plane) * 2 * NP * 2;
+    cudaError_t e = cudaMalloc(&bi, bytes_i);
+    if (e == cudaSuccess) e = cudaMalloc(&bo, bytes_o);
+    if (e != cudaSuccess) {
+        cudaFree(bi);
+        mm::tc_matrix_destroy(&M);
+        return fail(MM_ERR_OOM, "temporary piece buffers (%zu + %zu bytes)", bytes_i, bytes_o);
+    }
+    e = mm::tc_split(si, NP, u_dev, bi, s);
+    if (e == cudaSuccess) e = mm::tc_mode_product(si, so, mu, M, prec, bi, bo, mm::TcEpilogue{}, ctx->d_err, s);
+    if (e == cudaSuccess) e = mm::tc_merge(so, NP, bo, s_dev, s);
+    cudaError_t e2 = cudaStreamSynchronize(s);
+    cudaFree(bi);
+    cudaFree(bo);
+    mm::tc_matrix_destroy(&M);
+    if (e != cudaSuccess) return cuda_fail(e, "tensor-core mode product");
+    if (e2 != cudaSuccess) return cuda_fail(e2, "tensor-core mode product (sync)");
+    return MM_OK;
+}
+
+mm_status mumode_plan_create(mm_ctx *ctx, int d, const int64_t *n, const double *const *E_host, int E_is_complex,
+                             mm_dtype dtype, mm_prec prec, const int *mode_order, mm_plan **out)
+{
+    mm_plan *p = nullptr;
+    mm_status st = plan_common(ctx, d, n, dtype, prec, mode_order, E_is_complex != 0, out, &p);
+    if (st) return st;
+    if (!E_host) {
+        delete p;
+        return fail(MM_ERR_INVALID_ARG, "E_host is NULL");
+    }
+    for (int v = 0; v < d; ++v) {
+        if (!E_host[v]) {
+            mm_plan_destroy(p);
+            return fail(MM_ERR_INVALID_ARG, "E_host[%d] is NULL", v);
+        }
+        st = upload_matrix(p, E_host[v], n[v], n[v], E_is_complex != 0, &p->Edev[v], &p->Etc[v]);
+        if (st) {
+            mm_plan_destroy(p);
+            return st;
+        }
+    }
+    if ((st = alloc_workspace(p))) {
+        mm_plan_destroy(p);
+        return st;
+    }
+    *out = p;
+    return MM_OK;
+}
+
+mm_status mumode_step(mm_plan *p, void *u_dev, int64_t nsteps, void *stream)
+{
+    if (!p) return fail(MM_ERR_INVALID_ARG, "plan is NULL");
+    mm_status st = check_ptr(u_dev, "u_dev");
+    if (st) return st;
+    if (nsteps < 0) return fail(MM_ERR_INVALID_ARG, "nsteps < 0");
+    if (nsteps == 0) return MM_OK;
+    cudaStream_t s = (cudaStream_t)stream;
+    if (p->hermite) return fail(MM_ERR_INVALID_ARG, "mumode_step needs a Tucker plan (use hermite_ho_step)");
+    if (!p->tc) {
+        for (int64_t k = 0; k < nsteps; ++k)
+            if ((st = simt_sweep(p, p->Edev, u_dev, s))) return st;
+        return MM_OK;
+    }
+    cudaError_t e = mm::tc_split(p->st, p->npieces, u_dev, p->work[0], s);
+    if (e != cudaSuccess) return cuda_fail(e, "split");
+    int cur = 0;
+    mm::TcMatrix *M[mm::kMaxDims];
+    for (int v = 0; v < p->d; ++v) M[v] = &p->Etc[v];
+    for (int64_t k = 0; k < nsteps; ++k)
+        if ((st = tc_sweep(p, M, cur, mm::TcEpilogue{}, s))) return st;
+    e = mm::tc_merge(p->st, p->npieces, p->work[cur], u_dev, s);
+    if (e != cudaSuccess) return cuda_fail(e, "merge");
+    return MM_OK;
+}
+
+mm_status mumode_step_host(mm_plan *p, void *u_host, int64_t nsteps, void *stream)
+{
+    if (!p) return fail(MM_ERR_INVALID_ARG, "plan is NULL");
+    if (!u_host) return fail(MM_ERR_INVALID_ARG, "u_host is NULL");
+    const size_t bytes = size_t(p->count) * elem_bytes(p->dtype);
+    cudaStream_t s = (cudaStream_t)stream;
+    if (!p->staging) {
+        cudaError_t e = cudaMalloc(&p->staging, bytes);
+        if (e != cudaSuccess) return fail(MM_ERR_OOM, "staging cudaMalloc(%zu) failed", bytes);
+    }
+    cudaError_t e = cudaMemcpyAsync(p->staging, u_host, bytes, cudaMemcpyHostToDevice, s);
+    if (e != cudaSuccess) return cuda_fail(e, "host-to-device copy");
+    mm_status st = mumode_step(p, p->staging, nsteps, stream);
+    if (st) return st;
+    e = cudaMemcpyAsync(u_host, p->staging, bytes, cudaMemcpyDeviceToHost, s);
+    if (e != cudaSuccess) return cuda_fail(e, "device-to-host copy");
+    e = cudaStreamSynchronize(s);
+    if (e != cudaSuccess) return cuda_fail(e, "synchronize");
+    return MM_OK;
+}
+
+void mm_plan_destroy(mm_plan *p)
+{
+    if (!p) return;
+    for (int v = 0; v < mm::kMaxDims; ++v) {
+        if (p->Edev[v]) cudaFree(p->Edev[v]);
+        mm::tc_matrix_destroy(&p->Etc[v]);
+        if (p->Wdev[v]) cudaFree(p->Wdev[v]);
+        if (p->Fdev[v]) cudaFree(p->Fdev[v]);
+        if (p->Bdev[v]) cudaFree(p->Bdev[v]);
+        mm::tc_matrix_destroy(&p->Ftc[v]);
+        mm::tc_matrix_destroy(&p->Btc[v]);
+    }
+    free_prop(p, 0);
+    free_prop(p, 1);
+    if (p->work[0]) cudaFree(p->work[0]);
+    if (p->work[1]) cudaFree(p->work[1]);
+    if (p->staging) cudaFree(p->staging);
+    delete p;
+}
+
+mm_status hermite_plan_create(mm_ctx *ctx, int d, const int64_t *n, mm_dtype dtype, mm_prec prec, mm_plan **out)
+{
+    mm_plan *p = nullptr;
+    mm_status st = plan_common(ctx, d, n, dtype, prec, nullptr, true, out, &p);
+    if (st) return st;
+    if (!is_complex(dtype)) {
+        delete p;
+        return fail(MM_ERR_DTYPE, "Hermite plans need complex data");
+    }
+    p->hermite = true;
+    for (int v = 0; v < d; ++v) {
+        const int m = int(n[v]);
+        p->x[v].resize(m);
+        p->W[v].resize(m);
+        p->fwd[v].resize(size_t(m) * m);
+        p->bwd[v].resize(size_t(m) * m);
+        mm::gauss_hermite(m, p->x[v].data(), p->W[v].data());
+        mm::hermite_matrices(m, p->x[v].data(), p->W[v].data(), p->fwd[v].data(), p->bwd[v].data());
+        if (cudaMalloc(&p->Wdev[v], sizeof(double) * m) != cudaSuccess ||
+            cudaMemcpy(p->Wdev[v], p->W[v].data(), sizeof(double) * m, cudaMemcpyHostToDevice) != cudaSuccess) {
+            mm_plan_destroy(p);
+            return fail(MM_ERR_OOM, "weights upload");
+        }
+        if ((st = upload_matrix(p, p->fwd[v].data(), m, m, false, &p->Fdev[v], &p->Ftc[v])) ||
+            (st = upload_matrix(p, p->bwd[v].data(), m, m, false, &p->Bdev[v], &p->Btc[v]))) {
+            mm_plan_destroy(p);
+            return st;
+        }
+    }
+    if ((st = alloc_workspace(p))) {
+        mm_plan_destroy(p);
+        return st;
+    }
+    *out = p;
+    return MM_OK;
+}
+
+mm_status hermite_nodes(const mm_plan *p, int mu, double *x_out, double *W_out)
+{
+    if (!p || !p->hermite) return fail(MM_ERR_INVALID_ARG, "not a Hermite plan");
+    if (mu < 1 || mu > p->d) return fail(MM_ERR_INVALID_ARG, "mu = %d outside 1..%d", mu, p->d);
+    if (x_out) std::memcpy(x_out, p->x[mu - 1].data(), sizeof(double) * p->n[mu - 1]);
+    if (W_out) std::memcpy(W_out, p->W[mu - 1].data(), sizeof(double) * p->n[mu - 1]);
+    return MM_OK;
+}
+
+static mm_status hermite_apply(mm_plan *p, bool forward, const void *in, void *out, void *stream)
+{
+    if (!p || !p->hermite) return fail(MM_ERR_INVALID_ARG, "not a Hermite plan");
+    mm_status st;
+    if ((st = check_ptr(in, "input")) || (st = check_ptr(out, "output"))) return st;
+    cudaStream_t s = (cudaStream_t)stream;
+    if (!p->tc) {
+        cudaError_t e = cudaMemcpyAsync(out, in, size_t(p->count) * elem_bytes(p->dtype), cudaMemcpyDeviceToDevice, s);
+        if (e != cudaSuccess) return cuda_fail(e, "copy");
+        return simt_sweep(p, forward ? p->Fdev : p->Bdev, out, s);
+    }
+    cudaError_t e = mm::tc_split(p->st, p->npieces, in, p->work[0], s);
+    if (e != cudaSuccess) return cuda_fail(e, "split");
+    int cur = 0;
+    mm::TcMatrix *M[mm::kMaxDims];
+    for (int v = 0; v < p->d; ++v) M[v] = forward ? &p->Ftc[v] : &p->Btc[v];
+    if ((st = tc_sweep(p, M, cur, mm::TcEpilogue{}, s))) return st;
+    e = mm::tc_merge(p->st, p->npieces, p->work[cur], out, s);
+    if (e != cudaSuccess) return cuda_fail(e, "merge");
+    return MM_OK;
+}
+
+mm_status hermite_forward(mm_plan *p, const void *values_dev, void *coeffs_dev, void *stream)
+{
+    return hermite_apply(p, true, values_dev, coeffs_dev, stream);
+}
+
+mm_status hermite_backward(mm_plan *p, const void *coeffs_dev, void *values_dev, void *stream)
+{
+    return hermite_apply(p, false, coeffs_dev, values_dev, stream);
+}
+
+mm_status hermite_ho_step(mm_plan *p, void *psi, double tau, int64_t nsteps, void *stream)
+{
+    if (!p || !p->hermite) return fail(MM_ERR_INVALID_ARG, "not a Hermite plan");
+    mm_status st = check_ptr(psi, "psi_dev");
+    if (st) return st;
+    if (nsteps < 0 || !std::isfinite(tau)) return fail(MM_ERR_INVALID_ARG, "bad nsteps or tau");
+    if (nsteps == 0) return MM_OK;
+    int slot;
+    if ((st = ensure_prop(p, tau, -1, &slot))) return st;
+    cudaStream_t s = (cudaStream_t)stream;
+    if (!p->tc) {
+        for (int64_t k = 0; k < nsteps; ++k)
+            if ((st = simt_sweep(p, p->Pdev[slot], psi, s))) return st;
+        return MM_OK;
+    }
+    cudaError_t e = mm::tc_split(p->st, p->npieces, psi, p->work[0], s);
+    if (e != cudaSuccess) return cuda_fail(e, "split");
+    int cur = 0;
+    mm::TcMatrix *M[mm::kMaxDims];
+    for (int v = 0; v < p->d; ++v) M[v] = &p->Ptc[slot][v];
+    for (int64_t k = 0; k < nsteps; ++k)
+        if ((st = tc_sweep(p, M, cur, mm::TcEpilogue{}, s))) return st;
+    e = mm::tc_merge(p->st, p->npieces, p->work[cur], psi, s);
+    if (e != cudaSuccess) return cuda_fail(e, "merge");
+    return MM_OK;
+}
+
+mm_status split_step_gpe(mm_plan *p, void *psi, double beta, double tau, int64_t nsteps, void *stream)
+{
+    if (!p || !p->hermite) return fail(MM_ERR_INVALID_ARG, "not a Hermite plan");
+    mm_status st = check_ptr(psi, "psi_dev");
+    if (st) return st;
+    if (nsteps < 0 || !std::isfinite(tau) || !std::isfinite(beta)) return fail(MM_ERR_INVALID_ARG, "bad arguments");
+    if (nsteps == 0) return MM_OK;
+    int half, full;
+    if ((st = ensure_prop(p, 0.5 * tau, -1, &half))) return st;
+    if (nsteps > 1) {
+        if ((st = ensure_prop(p, tau, half, &full))) return st;
+    } else {
+        full = half;
+    }
+    cudaStream_t s = (cudaStream_t)stream;
+    const double tb = tau * beta;
+    if (!p->tc) {
+        const bool fp64 = p->dtype == MM_C128;
+        for (int64_t k = 0; k < nsteps; ++k) {
+            if ((st = simt_sweep(p, p->Pdev[k == 0 ? half : full], psi, s))) return st;
+            cudaError_t e = mm::simt_nonlinear_phase(fp64, p->count, tb, psi, s);
+            if (e != cudaSuccess) return cuda_fail(e, "nonlinear phase");
+        }
+        return simt_sweep(p, p->Pdev[half], psi, s);
+    }
+    cudaError_t e = mm::tc_split(p->st, p->npieces, psi, p->work[0], s);
+    if (e != cudaSuccess) return cuda_fail(e, "split");
+    int cur = 0;
+    mm::TcMatrix *Mh[mm::kMaxDims], *Mf[mm::kMaxDims];
+    for (int v = 0; v < p->d; ++v) {
+        Mh[v] = &p->Ptc[half][v];
+        Mf[v] = &p->Ptc[full][v];
+    }
+    mm::TcEpilogue nl;
+    nl.kind = 1;
+    nl.tb = tb;
+    for (int64_t k = 0; k < nsteps; ++k)
+        if ((st = tc_sweep(p, k == 0 ? Mh : Mf, cur, nl, s))) return st;
+    if ((st = tc_sweep(p, Mh, cur, mm::TcEpilogue{}, s))) return st;
+    e = mm::tc_merge(p->st, p->npieces, p->work[cur], psi, s);
+    if (e != cudaSuccess) return cuda_fail(e, "merge");
+    return MM_OK;
+}
+
+mm_status mm_norm2(mm_plan *p, const void *u_dev, int weighted, double *out_host, void *stream)
+{
+    if (!p) return fail(MM_ERR_INVALID_ARG, "plan is NULL");
+    if (!out_host) return fail(MM_ERR_INVALID_ARG, "out_host is NULL");
+    mm_status st = check_ptr(u_dev, "u_dev");
+    if (st) return st;
+    if (weighted && (!p->hermite || p->d != 3)) return fail(MM_ERR_INVALID_ARG, "weighted norm needs a 3D Hermite plan");
+    cudaStream_t s = (cudaStream_t)stream;
+    cudaError_t e = cudaMemsetAsync(p->ctx->d_scratch, 0, sizeof(double), s);
+    int64_t n1 = p->n[0], n2 = p->d > 1 ? p->n[1] : 1, n3 = p->count / (n1 * n2);
+    if (e == cudaSuccess)
+        e = mm::norm2_accumulate(p->dtype, n1, n2, n3, u_dev, weighted ? p->Wdev[0] : nullptr,
+                                 weighted ? p->Wdev[1] : nullptr, weighted ? p->Wdev[2] : nullptr, p->ctx->d_scratch, s);
+    if (e == cudaSuccess) e = cudaMemcpyAsync(out_host, p->ctx->d_scratch, sizeof(double), cudaMemcpyDeviceToHost, s);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(s);
+    if (e != cudaSuccess) return cuda_fail(e, "norm");
+    return MM_OK;
+}
+
+}  // extern "C"

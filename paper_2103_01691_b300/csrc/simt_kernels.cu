@@ -1,0 +1,210 @@
+// CUDA-core (SIMT) mu-mode product in FP64 or FP32: the "plain FP64 GPU
+// form" against which the split-precision tensor-core form is compared, and
+// the path for the real FP64 heat problem.
+//
+// Definition 2.1: with left = n_1..n_{mu-1} and right = n_{mu+1}..n_d the
+// input is X[r][j][l] and the output Y[r][i][l] = sum_j L[i][j] X[r][j][l].
+// Every direction is one strided GEMM on the tensor in place, with no
+// permutation between directions (section 5: the direct approach the paper
+// prefers over permute + GEMM): rows of the GEMM are the output index i,
+// columns the flattened (r, l) pairs.
+#include <cuda_runtime.h>
+
+#include <cstdint>
+
+#include "internal.h"
+
+namespace mm {
+namespace {
+
+template <typename R, bool C>
+struct Elem;
+template <typename R>
+struct Elem<R, false> {
+    R v;
+    __device__ static Elem zero() { return {R(0)}; }
+    __device__ void fma(const Elem &a, const Elem &b) { v += a.v * b.v; }
+};
+template <typename R>
+struct Elem<R, true> {
+    R re, im;
+    __device__ static Elem zero() { return {R(0), R(0)}; }
+    __device__ void fma(const Elem &a, const Elem &b)
+    {
+        re += a.re * b.re - a.im * b.im;
+        im += a.re * b.im + a.im * b.re;
+    }
+};
+
+constexpr int BM = 64, BN = 64, BK = 16, NT = 256;
+
+// One CTA computes a BM x BN tile of Y for rows i0.. and columns c0..;
+// thread (tx, ty) owns rows ty + 16 a and columns tx + 16 b, a, b < 4.
+template <typename R, bool C>
+__global__ void __launch_bounds__(NT) simt_mode_kernel(int64_t left, int64_t n, int64_t right, int64_t m,
+                                                       const Elem<R, C> *__restrict__ L,
+                                                       const Elem<R, C> *__restrict__ X,
+                                                       Elem<R, C> *__restrict__ Y)
+{
+    using E = Elem<R, C>;
+    __shared__ E sL[BK][BM + 1];
+    __shared__ E sX[BK][BN + 1];
+    const int t = threadIdx.x, tx = t % 16, ty = t / 16;
+    const int64_t i0 = int64_t(blockIdx.y) * BM;
+    const int64_t c0 = int64_t(blockIdx.x) * BN;
+    const int64_t ncols = left * right;
+    const bool fiber_contig = (left == 1);
+    E acc[4][4];
+#pragma unroll
+    for (int a = 0; a < 4; ++a)
+#pragma unroll
+        for (int b = 0; b < 4; ++b) acc[a][b] = E::zero();
+
+    for (int64_t k0 = 0; k0 < n; k0 += BK) {
+#pragma unroll
+        for (int q = 0; q < (BK * BM) / NT; ++q) {
+            const int e = t + NT * q;
+            const int kk = e % BK, ii = e / BK;  // consecutive threads walk j (row-major L)
+            const int64_t i = i0 + ii, j = k0 + kk;
+            sL[kk][ii] = (i < m && j < n) ? L[i * n + j] : E::zero();
+        }
+#pragma unroll
+        for (int q = 0; q < (BK * BN) / NT; ++q) {
+            const int e = t + NT * q;
+            int kk, cc;
+            if (fiber_contig) { kk = e % BK; cc = e / BK; }  // j contiguous in memory
+            else { cc = e % BN; kk = e / BN; }               // l contiguous in memory
+            const int64_t c = c0 + cc, j = k0 + kk;
+            E v = E::zero();
+            if (c < ncols && j < n) {
+                const int64_t r = c / left, l = c - r * left;
+                v = X[(r * n + j) * left + l];
+            }
+            sX[kk][cc] = v;
+        }
+        __syncthreads();
+#pragma unroll
+        for (int kk = 0; kk < BK; ++kk) {
+            E a[4], b[4];
+#pragma unroll
+            for (int q = 0; q < 4; ++q) {
+                a[q] = sL[kk][ty + 16 * q];
+                b[q] = sX[kk][tx + 16 * q];
+            }
+#pragma unroll
+            for (int p = 0; p < 4; ++p)
+#pragma unroll
+                for (int q = 0; q < 4; ++q) acc[p][q].fma(a[p], b[q]);
+        }
+        __syncthreads();
+    }
+#pragma unroll
+    for (int p = 0; p < 4; ++p) {
+        const int64_t i = i0 + ty + 16 * p;
+        if (i >= m) continue;
+#pragma unroll
+        for (int q = 0; q < 4; ++q) {
+            const int64_t c = c0 + tx + 16 * q;
+            if (c >= ncols) continue;
+            const int64_t r = c / left, l = c - r * left;
+            Y[(r * m + i) * left + l] = acc[p][q];
+        }
+    }
+}
+
+template <typename R>
+__global__ void nonlinear_phase_kernel(int64_t count, double tb, Elem<R, true> *psi)
+{
+    for (int64_t q = blockIdx.x * int64_t(blockDim.x) + threadIdx.x; q < count;
+         q += int64_t(gridDim.x) * blockDim.x) {
+        Elem<R, true> v = psi[q];
+        const double th = tb * (double(v.re) * v.re + double(v.im) * v.im);
+        double s, c;
+        sincos(th, &s, &c);
+        // v * exp(-i th)
+        psi[q] = {R(v.re * c + v.im * s), R(v.im * c - v.re * s)};
+    }
+}
+
+template <typename T>
+__device__ double abs2(const T &v);
+template <>
+__device__ double abs2<double>(const double &v) { return v * v; }
+template <>
+__device__ double abs2<float>(const float &v) { return double(v) * v; }
+template <>
+__device__ double abs2<double2>(const double2 &v) { return v.x * v.x + v.y * v.y; }
+template <>
+__device__ double abs2<float2>(const float2 &v) { return double(v.x) * v.x + double(v.y) * v.y; }
+
+template <typename T>
+__global__ void norm2_kernel(int64_t n1, int64_t n2, int64_t n3, const T *u, const double *w1,
+                             const double *w2, const double *w3, double *out)
+{
+    const int64_t N = n1 * n2 * n3;
+    double s = 0.0;
+    for (int64_t q = blockIdx.x * int64_t(blockDim.x) + threadIdx.x; q < N; q += int64_t(gridDim.x) * blockDim.x) {
+        double w = 1.0;
+        if (w1) {
+            const int64_t i1 = q % n1, i2 = (q / n1) % n2, i3 = q / (n1 * n2);
+            w = w1[i1] * w2[i2] * w3[i3];
+        }
+        s += abs2(u[q]) * w;
+    }
+    __shared__ double red[32];
+    for (int o = 16; o > 0; o >>= 1) s += __shfl_down_sync(0xffffffffu, s, o);
+    if ((threadIdx.x & 31) == 0) red[threadIdx.x >> 5] = s;
+    __syncthreads();
+    if (threadIdx.x < 32) {
+        s = (threadIdx.x < blockDim.x / 32) ? red[threadIdx.x] : 0.0;
+        for (int o = 16; o > 0; o >>= 1) s += __shfl_down_sync(0xffffffffu, s, o);
+        if (threadIdx.x == 0) atomicAdd(out, s);
+    }
+}
+
+}  // namespace
+
+cudaError_t simt_mode_product(bool fp64, bool cplx, int64_t left, int64_t n, int64_t right, int64_t m,
+                              const void *L, const void *X, void *Y, cudaStream_t s)
+{
+    const int64_t ncols = left * right;
+    dim3 grid(unsigned((ncols + BN - 1) / BN), unsigned((m + BM - 1) / BM));
+    if (grid.y > 65535u) return cudaErrorInvalidConfiguration;
+#define MM_LAUNCH(R, C)                                                                                  \
+    simt_mode_kernel<R, C><<<grid, NT, 0, s>>>(left, n, right, m, (const Elem<R, C> *)L,                 \
+                                               (const Elem<R, C> *)X, (Elem<R, C> *)Y)
+    if (fp64 && cplx) MM_LAUNCH(double, true);
+    else if (fp64) MM_LAUNCH(double, false);
+    else if (cplx) MM_LAUNCH(float, true);
+    else MM_LAUNCH(float, false);
+#undef MM_LAUNCH
+    count_launch();
+    return cudaGetLastError();
+}
+
+cudaError_t simt_nonlinear_phase(bool fp64, int64_t count, double tb, void *psi, cudaStream_t s)
+{
+    const int blocks = int((count + 255) / 256 < 148 * 16 ? (count + 255) / 256 : 148 * 16);
+    if (fp64) nonlinear_phase_kernel<double><<<blocks, 256, 0, s>>>(count, tb, (Elem<double, true> *)psi);
+    else nonlinear_phase_kernel<float><<<blocks, 256, 0, s>>>(count, tb, (Elem<float, true> *)psi);
+    count_launch();
+    return cudaGetLastError();
+}
+
+cudaError_t norm2_accumulate(mm_dtype dt, int64_t n1, int64_t n2, int64_t n3, const void *u,
+                             const double *w1, const double *w2, const double *w3, double *out,
+                             cudaStream_t s)
+{
+    const int64_t N = n1 * n2 * n3;
+    const int blocks = int((N + 255) / 256 < 148 * 8 ? (N + 255) / 256 : 148 * 8);
+    switch (dt) {
+    case MM_R64: norm2_kernel<double><<<blocks, 256, 0, s>>>(n1, n2, n3, (const double *)u, w1, w2, w3, out); break;
+    case MM_R32: norm2_kernel<float><<<blocks, 256, 0, s>>>(n1, n2, n3, (const float *)u, w1, w2, w3, out); break;
+    case MM_C128: norm2_kernel<double2><<<blocks, 256, 0, s>>>(n1, n2, n3, (const double2 *)u, w1, w2, w3, out); break;
+    default: norm2_kernel<float2><<<blocks, 256, 0, s>>>(n1, n2, n3, (const float2 *)u, w1, w2, w3, out); break;
+    }
+    count_launch();
+    return cudaGetLastError();
+}
+
+}  // namespace mm

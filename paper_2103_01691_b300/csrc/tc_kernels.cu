@@ -1,0 +1,548 @@
+// Split-precision mu-mode product on the tcgen05 tensor cores (sm_103a).
+//
+// What is computed (Definition 2.1 with a complex n_out x n_in matrix
+// E = C + iS):  Y[r][i][l] = sum_j E[i][j] X[r][j][l]  on complex data.
+//
+// State format between mode products.  The complex FP32 state is held as
+// BF16 "pieces": x = x0 + x1 + x2 with x0 = bf16(x), x1 = bf16(x - x0),
+// x2 = bf16(x - x0 - x1), which is exact for every normal FP32 x.  The real
+// and imaginary parts live in separate planes, so the buffer is
+// pieces[c][p][padded tensor] (c = re/im, p = piece).  Every direction is
+// padded to a multiple of 16 with zeros, which keeps all TMA boxes aligned;
+// the zero padding is invariant under the products (zero matrix rows and
+// columns).  The last epilogue writes the pieces of its FP32 result, so a
+// chain of mode products never leaves this format until the final merge.
+//
+// GEMM form.  For every direction the GEMM rows are 128 "points" (the
+// non-contracted indices), the contraction runs over (plane c, j), the
+// columns over (output part c', row i) of one tile of IT matrix rows:
+//   D[pt][c'=re, i] = sum_j Xre[pt][j] C[i][j] + Xim[pt][j] (-S[i][j])
+//   D[pt][c'=im, i] = sum_j Xre[pt][j] S[i][j] + Xim[pt][j]   C[i][j]
+// The matrix tile is stored as the row blocks [-S; C; S] (3 IT rows), so
+// the real-plane products read the window [C; S] and the imaginary-plane
+// products the window [-S; C]: one MMA with N = 2 IT per plane and piece
+// pair.  For direction 1 (left == 1) the points are fibers and X is
+// K-major in memory; for the other directions the points run along the
+// contiguous index l and X is MN-major; both are loaded by TMA as they lie
+// in HBM, with no permutation between directions (section 5).
+//
+// Precision.  The products e_a x_b with a + b <= P-1 (P pieces) are
+// accumulated in FP32 in tensor memory; the leading product e0 x0 has an
+// accumulator of its own so that the smaller corrections are not rounded
+// against the large running sum; the epilogue adds the two in FP32.
+//
+// Roles (256 threads): warp 0 lane 0 issues TMA loads into a 3-stage ring,
+// warp 1 allocates tensor memory and its lane 0 issues tcgen05.mma, and
+// after the main loop all eight warps drain tensor memory (warp w reads
+// lanes 32 (w % 4) .. + 31, half of the column chunks each).
+#include <cuda.h>
+#include <cuda_bf16.h>
+#include <cuda_runtime.h>
+
+#include <cmath>
+#include <cstdint>
+#include <cstring>
+#include <vector>
+
+#include "internal.h"
+#include "tc_ptx.cuh"
+
+namespace mm {
+
+int tc_pieces(mm_prec p)
+{
+    switch (p) {
+    case MM_PREC_BF16X6: return 3;
+    case MM_PREC_BF16X3: return 2;
+    case MM_PREC_BF16: return 1;
+    default: return 0;
+    }
+}
+bool tc_prec(mm_prec p) { return tc_pieces(p) > 0; }
+
+static inline int64_t round16(int64_t v) { return (v + 15) / 16 * 16; }
+
+// ---- host: BF16 pieces of the matrix ----------------------------------------------
+
+// Round a double to the nearest BF16 value (ties to even), returned as a double.
+static double bf16_round(double v)
+{
+    if (v == 0.0 || !std::isfinite(v)) return 0.0;
+    int e = std::ilogb(v);
+    if (e < -126) return 0.0;  // below the BF16 normal range: flush
+    double scaled = std::ldexp(v, 7 - e);  // |scaled| in [128, 256)
+    double r = std::nearbyint(scaled);     // default rounding mode: nearest, ties to even
+    return std::ldexp(r, e - 7);
+}
+static uint16_t bf16_bits(double exact_bf16_value)
+{
+    float f = float(exact_bf16_value);
+    uint32_t u;
+    std::memcpy(&u, &f, 4);
+    return uint16_t(u >> 16);
+}
+
+mm_status tc_matrix_create(const double *E, int64_t m, int64_t n, int npieces, TcMatrix *out)
+{
+    TcMatrix M;
+    M.n_in = n;
+    M.n_out = m;
+    M.k_pad = round16(n);
+    const int64_t m_pad = round16(m);
+    M.ni = int((m_pad + 127) / 128);
+    M.it = int(round16((m_pad + M.ni - 1) / M.ni));
+    M.npieces = npieces;
+    const int64_t rows = int64_t(npieces) * M.ni * 3 * M.it;
+    std::vector<uint16_t> h(size_t(rows * M.k_pad), 0);
+    for (int64_t i = 0; i < m; ++i)
+        for (int64_t j = 0; j < n; ++j) {
+            double rest[2] = {E[2 * (i * n + j)], E[2 * (i * n + j) + 1]};  // C, S
+            const int64_t tile = i / M.it, il = i % M.it;
+            for (int p = 0; p < npieces; ++p) {
+                double piece[2];
+                for (int q = 0; q < 2; ++q) {
+                    piece[q] = bf16_round(rest[q]);
+                    rest[q] -= piece[q];
+                }
+                // blocks: 0 = -S, 1 = C, 2 = S
+                const double vals[3] = {-piece[1], piece[0], piece[1]};
+                for (int w = 0; w < 3; ++w) {
+                    const int64_t row = ((int64_t(p) * M.ni + tile) * 3 + w) * M.it + il;
+                    h[size_t(row * M.k_pad + j)] = bf16_bits(vals[w]);
+                }
+            }
+        }
+    if (cudaMalloc(&M.pieces, h.size() * 2) != cudaSuccess)
+        return fail(MM_ERR_OOM, "cudaMalloc of %zu bytes for matrix pieces failed", h.size() * 2);
+    if (cudaMemcpy(M.pieces, h.data(), h.size() * 2, cudaMemcpyHostToDevice) != cudaSuccess) {
+        cudaFree(M.pieces);
+        return fail(MM_ERR_CUDA, "upload of matrix pieces failed");
+    }
+    *out = M;
+    return MM_OK;
+}
+
+void tc_matrix_destroy(TcMatrix *M)
+{
+    if (M && M->pieces) cudaFree(M->pieces);
+    if (M) M->pieces = nullptr;
+}
+
+// ---- device: splitting, merging -----------------------------------------------------
+
+struct Dims {
+    int d;
+    int64_t n[kMaxDims];
+    int64_t np[kMaxDims];
+};
+
+__device__ __forceinline__ void split_value(float v, int np, __nv_bfloat16 *out, int64_t stride)
+{
+    float r = v;
+    for (int p = 0; p < np; ++p) {
+        const __nv_bfloat16 b = __float2bfloat16_rn(r);
+        out[p * stride] = b;
+        r -= __bfloat162float(b);
+    }
+}
+
+// Padded-index loop: reads the logical complex64 tensor, writes all pieces.
+__global__ void split_kernel(Dims dm, int64_t plane, int npieces, const float2 *__restrict__ u,
+                             __nv_bfloat16 *__restrict__ pieces)
+{
+    for (int64_t q = blockIdx.x * int64_t(blockDim.x) + threadIdx.x; q < plane; q += int64_t(gridDim.x) * blockDim.x) {
+        int64_t rem = q, lin = 0, mul = 1;
+        bool inside = true;
+        for (int v = 0; v < dm.d; ++v) {
+            const int64_t c = rem % dm.np[v];
+            rem /= dm.np[v];
+            inside &= c < dm.n[v];
+            lin += c * mul;
+            mul *= dm.n[v];
+        }
+        const float2 x = inside ? u[lin] : make_float2(0.f, 0.f);
+        split_value(x.x, npieces, pieces + q, plane);
+        split_value(x.y, npieces, pieces + int64_t(npieces) * plane + q, plane);
+    }
+}
+
+// Logical-index loop: sums the pieces back (exact for three pieces).
+__global__ void merge_kernel(Dims dm, int64_t plane, int npieces, const __nv_bfloat16 *__restrict__ pieces,
+                             float2 *__restrict__ u, int64_t count)
+{
+    for (int64_t q = blockIdx.x * int64_t(blockDim.x) + threadIdx.x; q < count; q += int64_t(gridDim.x) * blockDim.x) {
+        int64_t rem = q, pad = 0, mul = 1;
+        for (int v = 0; v < dm.d; ++v) {
+            const int64_t c = rem % dm.n[v];
+            rem /= dm.n[v];
+            pad += c * mul;
+            mul *= dm.np[v];
+        }
+        float re = 0.f, im = 0.f;
+        for (int p = npieces - 1; p >= 0; --p) {
+            re += __bfloat162float(pieces[p * plane + pad]);
+            im += __bfloat162float(pieces[(npieces + p) * plane + pad]);
+        }
+        u[q] = make_float2(re, im);
+    }
+}
+
+static Dims make_dims(const TcState &st)
+{
+    Dims dm;
+    dm.d = st.d;
+    for (int v = 0; v < kMaxDims; ++v) {
+        dm.n[v] = v < st.d ? st.n[v] : 1;
+        dm.np[v] = v < st.d ? st.np[v] : 1;
+    }
+    return dm;
+}
+
+static int grid_for(int64_t count)
+{
+    int64_t b = (count + 255) / 256;
+    return int(b < 148 * 32 ? (b > 0 ? b : 1) : 148 * 32);
+}
+
+cudaError_t tc_split(const TcState &st, int npieces, const void *u_c64, void *pieces, cudaStream_t s)
+{
+    split_kernel<<<grid_for(st.plane), 256, 0, s>>>(make_dims(st), st.plane, npieces, (const float2 *)u_c64,
+                                                    (__nv_bfloat16 *)pieces);
+    count_launch();
+    return cudaGetLastError();
+}
+
+cudaError_t tc_merge(const TcState &st, int npieces, const void *pieces, void *u_c64, cudaStream_t s)
+{
+    int64_t count = 1;
+    for (int v = 0; v < st.d; ++v) count *= st.n[v];
+    merge_kernel<<<grid_for(count), 256, 0, s>>>(make_dims(st), st.plane, npieces, (const __nv_bfloat16 *)pieces,
+                                                 (float2 *)u_c64, count);
+    count_launch();
+    return cudaGetLastError();
+}
+
+// ---- device: the tensor-core mode product ---------------------------------------------
+
+constexpr int kStages = 3;
+constexpr int kBK = 16;             // contraction elements per stage (one MMA K)
+constexpr int kTileM = 128;         // points per CTA
+constexpr int kDataTileBytes = kTileM * kBK * 2;  // 4 KB per (plane, piece)
+
+struct TcArgs {
+    int64_t left, right;    // padded sizes of the fast / slow index groups
+    int64_t kp;             // padded contraction length
+    int64_t mp;             // padded output length
+    int64_t aps;            // 64-point atoms per slab (MN-major)
+    int64_t plane_out;      // elements per output plane
+    int it, ni, kblocks;
+    int stage_bytes, tx_bytes, e_offset;
+    float tb;               // tau * beta for the nonlinear epilogue
+    __nv_bfloat16 *out;
+    int *err;
+};
+
+// Piece pairs (a, b) of e_a x_b with a + b <= NP - 1, leading pair first.
+__host__ __device__ constexpr int num_terms(int NP) { return NP == 3 ? 6 : (NP == 2 ? 3 : 1); }
+__host__ __device__ constexpr int term_a(int t) { return t == 2 ? 1 : (t == 4 ? 1 : (t == 5 ? 2 : 0)); }
+__host__ __device__ constexpr int term_b(int t) { return t == 1 ? 1 : (t == 3 ? 2 : (t == 4 ? 1 : 0)); }
+
+template <int NP, bool KMAJOR, int EPI>
+__global__ void __launch_bounds__(256, 1)
+    tc_mode_kernel(const __grid_constant__ CUtensorMap mapX, const __grid_constant__ CUtensorMap mapE, TcArgs a)
+{
+    extern __shared__ __align__(1024) uint8_t smem_raw[];
+    uint8_t *smem = reinterpret_cast<uint8_t *>((reinterpret_cast<uintptr_t>(smem_raw) + 1023) & ~uintptr_t(1023));
+    uint64_t *full = reinterpret_cast<uint64_t *>(smem + kStages * a.stage_bytes);
+    uint64_t *empty = full + kStages;
+    uint64_t *accf = empty + kStages;
+    uint32_t *tmem_slot = reinterpret_cast<uint32_t *>(accf + 1);
+
+    const int warp = threadIdx.x / 32, lane = threadIdx.x % 32;
+    const int tile = blockIdx.x / a.ni, h = blockIdx.x % a.ni;
+    const int acc_cols = 2 * a.it;
+    const uint32_t ncols = NP > 1 ? (acc_cols * 2 <= 32 ? 32 : (acc_cols * 2 <= 64 ? 64 : (acc_cols * 2 <= 128 ? 128 : (acc_cols * 2 <= 256 ? 256 : 512))))
+                                  : (acc_cols <= 32 ? 32 : (acc_cols <= 64 ? 64 : (acc_cols <= 128 ? 128 : 256)));
+
+    if (threadIdx.x == 0) {
+        for (int s = 0; s < kStages; ++s) {
+            mbar_init(&full[s], 1);
+            mbar_init(&empty[s], 1);
+        }
+        mbar_init(accf, 1);
+        mbar_fence_init();
+        tma_prefetch_desc(&mapX);
+        tma_prefetch_desc(&mapE);
+    }
+    if (warp == 1) {
+        tmem_alloc(tmem_slot, ncols);
+        tmem_relinquish();
+    }
+    tc_fence_before();
+    __syncthreads();
+    tc_fence_after();
+    const uint32_t tmem = *tmem_slot;
+    bool ok = true;
+
+    if (warp == 0 && lane == 0) {
+        // ---------------- TMA producer ----------------
+        for (int kb = 0; kb < a.kblocks && ok; ++kb) {
+            const int s = kb % kStages;
+            const uint32_t ph = uint32_t(kb / kStages) & 1u;
+            ok = mbar_wait(&empty[s], ph ^ 1u, a.err, MM_ERR_TIMEOUT);
+            if (!ok) break;
+            uint8_t *st = smem + s * a.stage_bytes;
+            mbar_arrive_expect_tx(&full[s], uint32_t(a.tx_bytes));
+            for (int c = 0; c < 2; ++c)
+                for (int p = 0; p < NP; ++p) {
+                    uint8_t *dst = st + (c * NP + p) * kDataTileBytes;
+                    if (KMAJOR) {
+                        tma_load_3d(&mapX, &full[s], dst, kb * kBK, tile * kTileM, c * NP + p);
+                    } else {
+                        for (int q = 0; q < 2; ++q) {
+                            const int64_t atom = 2 * int64_t(tile) + q;
+                            int64_t r = atom / a.aps;
+                            const int64_t l0 = (atom % a.aps) * 64;
+                            if (r > a.right) r = a.right;  // past the end: zero fill
+                            tma_load_4d(&mapX, &full[s], dst + q * 2048, int(l0), kb * kBK, int(r), c * NP + p);
+                        }
+                    }
+                }
+            uint8_t *est = st + a.e_offset;
+            for (int p = 0; p < NP; ++p)
+                for (int w = 0; w < 3; ++w)
+                    tma_load_2d(&mapE, &full[s], est + (p * 3 + w) * a.it * 32, kb * kBK,
+                                ((p * a.ni + h) * 3 + w) * a.it);
+        }
+    } else if (warp == 1 && lane == 0) {
+        // ---------------- MMA issuer ----------------
+        const uint32_t idesc = idesc_bf16_f32(kTileM, 2 * a.it, !KMAJOR, false);
+        bool started[2] = {false, false};
+        for (int kb = 0; kb < a.kblocks && ok; ++kb) {
+            const int s = kb % kStages;
+            const uint32_t ph = uint32_t(kb / kStages) & 1u;
+            ok = mbar_wait(&full[s], ph, a.err, MM_ERR_TIMEOUT);
+            if (!ok) break;
+            tc_fence_after();
+            const uint32_t st = smem_u32(smem + s * a.stage_bytes);
+            const uint32_t est = st + a.e_offset;
+            for (int c = 0; c < 2; ++c) {
+#pragma unroll
+                for (int t = 0; t < num_terms(NP); ++t) {
+                    const int pa = term_a(t), pb = term_b(t);
+                    const uint32_t xaddr = st + (c * NP + pb) * kDataTileBytes;
+                    const uint64_t adesc =
+                        KMAJOR ? smem_desc(xaddr, 16, 256, kSwz32) : smem_desc(xaddr, 2048, 1024, kSwz128);
+                    // real plane: window [C; S] (block 1); imaginary plane: [-S; C] (block 0)
+                    const uint32_t eaddr = est + (pa * 3 + (c == 0 ? 1 : 0)) * a.it * 32;
+                    const uint64_t bdesc = smem_desc(eaddr, 16, 256, kSwz32);
+                    const int acc = (NP > 1 && (pa != 0 || pb != 0)) ? 1 : 0;
+                    umma_f16(tmem + uint32_t(acc * acc_cols), adesc, bdesc, idesc, started[acc] ? 1u : 0u);
+                    started[acc] = true;
+                }
+            }
+            umma_commit(&empty[s]);
+        }
+        umma_commit(accf);
+    }
+    __syncwarp();
+
+    // ---------------- epilogue: all warps ----------------
+    bool acc_ready = mbar_wait(accf, 0, a.err, MM_ERR_TIMEOUT);
+    tc_fence_after();
+    const int quarter = warp % 4, half = warp / 4;
+    const int row = quarter * 32 + lane;
+    // point of this thread
+    bool valid;
+    int64_t r, l = 0;
+    if (KMAJOR) {
+        r = int64_t(tile) * kTileM + row;
+        valid = r < a.right;
+    } else {
+        const int64_t atom = 2 * int64_t(tile) + row / 64;
+        r = atom / a.aps;
+        l = (atom % a.aps) * 64 + row % 64;
+        valid = r < a.right && l < a.left;
+    }
+    const uint32_t tbase = tmem + (uint32_t(quarter * 32) << 16);
+    const int nchunks = a.it / 16;
+    for (int ch = half; ch < nchunks; ch += 2) {
+        float re0[16], im0[16], re1[16], im1[16];
+        tmem_ld16(tbase + uint32_t(ch * 16), re0);
+        tmem_ld16(tbase + uint32_t(a.it + ch * 16), im0);
+        if (NP > 1) {
+            tmem_ld16(tbase + uint32_t(acc_cols + ch * 16), re1);
+            tmem_ld16(tbase + uint32_t(acc_cols + a.it + ch * 16), im1);
+        }
+        tmem_ld_wait();
+        if (!acc_ready || !valid) continue;
+        const int64_t i0 = int64_t(h) * a.it + ch * 16;
+        if (i0 >= a.mp) continue;
+        __nv_bfloat16 pr[3][16], pi[3][16];
+#pragma unroll
+        for (int k = 0; k < 16; ++k) {
+            float xr = re0[k], xi = im0[k];
+            if (NP > 1) {
+                xr += re1[k];
+                xi += im1[k];
+            }
+            if (EPI == 1) {
+                const float th = a.tb * (xr * xr + xi * xi);
+                float sn, cs;
+                sincosf(th, &sn, &cs);
+                const float yr = xr * cs + xi * sn, yi = xi * cs - xr * sn;
+                xr = yr;
+                xi = yi;
+            }
+            float rr = xr, ri = xi;
+#pragma unroll
+            for (int p = 0; p < NP; ++p) {
+                pr[p][k] = __float2bfloat16_rn(rr);
+                pi[p][k] = __float2bfloat16_rn(ri);
+                rr -= __bfloat162float(pr[p][k]);
+                ri -= __bfloat162float(pi[p][k]);
+            }
+        }
+        if (KMAJOR) {
+            const int64_t base = r * a.mp + i0;
+#pragma unroll
+            for (int p = 0; p < NP; ++p) {
+                uint4 *dr = reinterpret_cast<uint4 *>(a.out + int64_t(p) * a.plane_out + base);
+                uint4 *di = reinterpret_cast<uint4 *>(a.out + int64_t(NP + p) * a.plane_out + base);
+                dr[0] = *reinterpret_cast<const uint4 *>(&pr[p][0]);
+                dr[1] = *reinterpret_cast<const uint4 *>(&pr[p][8]);
+                di[0] = *reinterpret_cast<const uint4 *>(&pi[p][0]);
+                di[1] = *reinterpret_cast<const uint4 *>(&pi[p][8]);
+            }
+        } else {
+#pragma unroll
+            for (int k = 0; k < 16; ++k) {
+                const int64_t off = (r * a.mp + i0 + k) * a.left + l;
+#pragma unroll
+                for (int p = 0; p < NP; ++p) {
+                    a.out[int64_t(p) * a.plane_out + off] = pr[p][k];
+                    a.out[int64_t(NP + p) * a.plane_out + off] = pi[p][k];
+                }
+            }
+        }
+    }
+    tc_fence_before();
+    __syncthreads();
+    if (warp == 1) {
+        tc_fence_after();
+        tmem_dealloc(tmem, ncols);
+    }
+}
+
+// ---- host: tensor maps and launch -------------------------------------------------------
+
+using EncodeTiledFn = CUresult (*)(CUtensorMap *, CUtensorMapDataType, cuuint32_t, void *, const cuuint64_t *,
+                                   const cuuint64_t *, const cuuint32_t *, const cuuint32_t *, CUtensorMapInterleave,
+                                   CUtensorMapSwizzle, CUtensorMapL2promotion, CUtensorMapFloatOOBfill);
+
+static EncodeTiledFn encode_fn()
+{
+    static EncodeTiledFn fn = nullptr;
+    if (!fn) {
+        void *p = nullptr;
+        cudaDriverEntryPointQueryResult q;
+        if (cudaGetDriverEntryPointByVersion("cuTensorMapEncodeTiled", &p, 12000, cudaEnableDefault, &q) ==
+                cudaSuccess &&
+            q == cudaDriverEntryPointSuccess)
+            fn = reinterpret_cast<EncodeTiledFn>(p);
+    }
+    return fn;
+}
+
+static bool encode(CUtensorMap *map, void *base, int rank, const cuuint64_t *dims, const cuuint64_t *strides_bytes,
+                   const cuuint32_t *box, CUtensorMapSwizzle swz)
+{
+    EncodeTiledFn fn = encode_fn();
+    if (!fn) return false;
+    cuuint32_t estr[5] = {1, 1, 1, 1, 1};
+    return fn(map, CU_TENSOR_MAP_DATA_TYPE_BFLOAT16, cuuint32_t(rank), base, dims, strides_bytes, box, estr,
+              CU_TENSOR_MAP_INTERLEAVE_NONE, swz, CU_TENSOR_MAP_L2_PROMOTION_L2_256B,
+              CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE) == CUDA_SUCCESS;
+}
+
+template <int NP, bool KM, int EPI>
+static cudaError_t launch_tc(const CUtensorMap &mx, const CUtensorMap &me, const TcArgs &a, int grid, int smem,
+                             cudaStream_t s)
+{
+    auto kern = tc_mode_kernel<NP, KM, EPI>;
+    cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
+    if (e != cudaSuccess) return e;
+    kern<<<grid, 256, smem, s>>>(mx, me, a);
+    count_launch();
+    return cudaGetLastError();
+}
+
+template <int NP>
+static cudaError_t dispatch_np(bool km, int epi, const CUtensorMap &mx, const CUtensorMap &me, const TcArgs &a,
+                               int grid, int smem, cudaStream_t s)
+{
+    if (km) return epi ? launch_tc<NP, true, 1>(mx, me, a, grid, smem, s) : launch_tc<NP, true, 0>(mx, me, a, grid, smem, s);
+    return epi ? launch_tc<NP, false, 1>(mx, me, a, grid, smem, s) : launch_tc<NP, false, 0>(mx, me, a, grid, smem, s);
+}
+
+cudaError_t tc_mode_product(const TcState &si, const TcState &so, int mu, const TcMatrix &M, mm_prec prec,
+                            const void *in_pieces, void *out_pieces, const TcEpilogue &epi, int *d_err,
+                            cudaStream_t s)
+{
+    const int NP = tc_pieces(prec);
+    if (NP == 0 || NP != M.npieces) return cudaErrorInvalidValue;
+    TcArgs a{};
+    a.left = 1;
+    a.right = 1;
+    for (int v = 0; v < mu - 1; ++v) a.left *= si.np[v];
+    for (int v = mu; v < si.d; ++v) a.right *= si.np[v];
+    a.kp = si.np[mu - 1];
+    a.mp = so.np[mu - 1];
+    if (a.kp != M.k_pad) return cudaErrorInvalidValue;
+    a.aps = (a.left + 63) / 64;
+    a.plane_out = so.plane;
+    a.it = M.it;
+    a.ni = M.ni;
+    a.kblocks = int(a.kp / kBK);
+    a.e_offset = 2 * NP * kDataTileBytes;
+    a.tx_bytes = a.e_offset + NP * 3 * M.it * 32;
+    a.stage_bytes = (a.tx_bytes + 1023) / 1024 * 1024;
+    a.tb = float(epi.tb);
+    a.out = (__nv_bfloat16 *)out_pieces;
+    a.err = d_err;
+    const bool km = a.left == 1;
+
+    CUtensorMap mx, me;
+    void *xin = const_cast<void *>(in_pieces);
+    if (km) {
+        cuuint64_t dims[3] = {cuuint64_t(a.kp), cuuint64_t(a.right), cuuint64_t(2 * NP)};
+        cuuint64_t str[2] = {cuuint64_t(a.kp * 2), cuuint64_t(si.plane * 2)};
+        cuuint32_t box[3] = {kBK, kTileM, 1};
+        if (!encode(&mx, xin, 3, dims, str, box, CU_TENSOR_MAP_SWIZZLE_32B)) return cudaErrorInvalidValue;
+    } else {
+        cuuint64_t dims[4] = {cuuint64_t(a.left), cuuint64_t(a.kp), cuuint64_t(a.right), cuuint64_t(2 * NP)};
+        cuuint64_t str[3] = {cuuint64_t(a.left * 2), cuuint64_t(a.left * a.kp * 2), cuuint64_t(si.plane * 2)};
+        cuuint32_t box[4] = {64, kBK, 1, 1};
+        if (!encode(&mx, xin, 4, dims, str, box, CU_TENSOR_MAP_SWIZZLE_128B)) return cudaErrorInvalidValue;
+    }
+    {
+        const int64_t rows = int64_t(NP) * M.ni * 3 * M.it;
+        cuuint64_t dims[2] = {cuuint64_t(M.k_pad), cuuint64_t(rows)};
+        cuuint64_t str[1] = {cuuint64_t(M.k_pad * 2)};
+        cuuint32_t box[2] = {kBK, cuuint32_t(M.it)};
+        if (!encode(&me, M.pieces, 2, dims, str, box, CU_TENSOR_MAP_SWIZZLE_32B)) return cudaErrorInvalidValue;
+    }
+    int64_t tiles;
+    if (km) tiles = (a.right + kTileM - 1) / kTileM;
+    else tiles = (a.right * a.aps + 1) / 2;
+    const int64_t grid = tiles * a.ni;
+    if (grid > 0x7fffffff) return cudaErrorInvalidConfiguration;
+    const int smem = kStages * a.stage_bytes + 1024 + 256;
+    switch (NP) {
+    case 3: return dispatch_np<3>(km, epi.kind, mx, me, a, int(grid), smem, s);
+    case 2: return dispatch_np<2>(km, epi.kind, mx, me, a, int(grid), smem, s);
+    default: return dispatch_np<1>(km, epi.kind, mx, me, a, int(grid), smem, s);
+    }
+}
+
+}  // namespace mm

@@ -1,0 +1,336 @@
+"""Thin Python binding of libmumode.so (include/mumode.h): argument
+marshalling only.  Every step of the hot path runs in the library's CUDA
+kernels; torch supplies device memory and the current stream.  There is no
+fallback: if the library is missing or a call fails, an exception is
+raised.
+
+Tensors follow the paper's layout (i_1 fastest): a tensor with sizes
+(n_1, ..., n_d) is a contiguous torch tensor of shape (n_d, ..., n_1).
+Matrices are numpy arrays (FP64, real or complex) indexed [row, column].
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+
+import numpy as np
+
+_HERE = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(_HERE, "libmumode.so")
+
+MM_R64, MM_C64, MM_C128, MM_R32 = 0, 1, 2, 3
+PREC = {"fp64": 0, "fp32": 1, "bf16x6": 2, "bf16x3": 3, "bf16": 4}
+STATUS = {0: "MM_OK", 1: "MM_ERR_INVALID_ARG", 2: "MM_ERR_SHAPE", 3: "MM_ERR_DTYPE", 4: "MM_ERR_ALIGN",
+          5: "MM_ERR_OOM", 6: "MM_ERR_CUDA", 7: "MM_ERR_TIMEOUT", 8: "MM_ERR_UNSUPPORTED"}
+
+# Every symbol include/mumode.h declares, with its ctypes signature.
+_vp, _i, _i64, _d = ctypes.c_void_p, ctypes.c_int, ctypes.c_int64, ctypes.c_double
+_dp = ctypes.POINTER(ctypes.c_double)
+_i64p = ctypes.POINTER(ctypes.c_int64)
+SIGNATURES = {
+    "mm_ctx_create": (_i, [_i, ctypes.POINTER(_vp)]),
+    "mm_ctx_destroy": (None, [_vp]),
+    "mm_last_error": (ctypes.c_char_p, []),
+    "mm_device_status": (_i, [_vp, _vp]),
+    "mm_launch_count": (_i64, []),
+    "mm_kernel_timing": (_i, [_vp, _i]),
+    "mm_kernel_timing_read": (_i, [_vp, _dp, ctypes.POINTER(_i64)]),
+    "mm_fd_laplacian_dirichlet": (_i, [_i, _dp]),
+    "mm_expm": (_i, [_i, _dp, _dp, _d, _d, _dp]),
+    "mm_gauss_hermite": (_i, [_i, _dp, _dp]),
+    "mm_hermite_matrices": (_i, [_i, _dp, _dp]),
+    "mumode_product": (_i, [_vp, _i, _i64p, _i, _dp, _i64, _i, _i, _i, _vp, _vp, _vp]),
+    "mumode_plan_create": (_i, [_vp, _i, _i64p, ctypes.POINTER(_dp), _i, _i, _i, ctypes.POINTER(_i),
+                                ctypes.POINTER(_vp)]),
+    "mumode_step": (_i, [_vp, _vp, _i64, _vp]),
+    "mumode_step_host": (_i, [_vp, _vp, _i64, _vp]),
+    "mm_plan_destroy": (None, [_vp]),
+    "hermite_plan_create": (_i, [_vp, _i, _i64p, _i, _i, ctypes.POINTER(_vp)]),
+    "hermite_nodes": (_i, [_vp, _i, _dp, _dp]),
+    "hermite_forward": (_i, [_vp, _vp, _vp, _vp]),
+    "hermite_backward": (_i, [_vp, _vp, _vp, _vp]),
+    "hermite_ho_step": (_i, [_vp, _vp, _d, _i64, _vp]),
+    "split_step_gpe": (_i, [_vp, _vp, _d, _d, _i64, _vp]),
+    "mm_norm2": (_i, [_vp, _vp, _i, _dp, _vp]),
+}
+
+_lib = None
+
+
+class MumodeError(RuntimeError):
+    def __init__(self, status: int, msg: str):
+        super().__init__(f"{STATUS.get(status, status)}: {msg}")
+        self.status = status
+
+
+def lib():
+    """Load libmumode.so (built by ``python -m paper_2103_01691_b300.build``)."""
+    global _lib
+    if _lib is None:
+        if not os.path.exists(LIB_PATH):
+            raise ImportError(f"{LIB_PATH} is missing: build it with python -m paper_2103_01691_b300.build")
+        L = ctypes.CDLL(LIB_PATH)
+        for name, (res, args) in SIGNATURES.items():
+            f = getattr(L, name)
+            f.restype = res
+            f.argtypes = args
+        _lib = L
+    return _lib
+
+
+def _check(status: int):
+    if status != 0:
+        raise MumodeError(status, lib().mm_last_error().decode())
+
+
+def _dptr(a: np.ndarray):
+    return a.ctypes.data_as(_dp)
+
+
+def _complex_interleaved(M) -> tuple[np.ndarray, int]:
+    M = np.asarray(M)
+    if np.iscomplexobj(M):
+        return np.ascontiguousarray(M, dtype=np.complex128).view(np.float64), 1
+    return np.ascontiguousarray(M, dtype=np.float64), 0
+
+
+def _stream(stream=None):
+    import torch
+
+    if stream is None:
+        stream = torch.cuda.current_stream()
+    return ctypes.c_void_p(stream.cuda_stream)
+
+
+def _dtype_code(t) -> int:
+    import torch
+
+    codes = {torch.complex64: MM_C64, torch.complex128: MM_C128, torch.float64: MM_R64, torch.float32: MM_R32}
+    if t.dtype not in codes:
+        raise TypeError(f"unsupported dtype {t.dtype}")
+    return codes[t.dtype]
+
+
+def _dims(shape) -> np.ndarray:
+    return np.array(list(shape)[::-1], dtype=np.int64)
+
+
+def _need_cuda(t):
+    if not t.is_cuda or not t.is_contiguous():
+        raise ValueError("expected a contiguous CUDA tensor")
+
+
+# --------------------------------------------------------------------- context
+
+class Context:
+    def __init__(self, device: int = 0):
+        h = ctypes.c_void_p()
+        _check(lib().mm_ctx_create(device, ctypes.byref(h)))
+        self.handle = h
+        self.device = device
+
+    def status(self, stream=None):
+        _check(lib().mm_device_status(self.handle, _stream(stream)))
+
+    def kernel_timing(self, enable: bool = True):
+        _check(lib().mm_kernel_timing(self.handle, int(enable)))
+
+    def kernel_timing_read(self):
+        """(total milliseconds, launches) of the mode-product kernels timed since enabling."""
+        ms, n = ctypes.c_double(), ctypes.c_int64()
+        _check(lib().mm_kernel_timing_read(self.handle, ctypes.byref(ms), ctypes.byref(n)))
+        return ms.value, n.value
+
+    def close(self):
+        if self.handle:
+            lib().mm_ctx_destroy(self.handle)
+            self.handle = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+
+def launch_count() -> int:
+    return int(lib().mm_launch_count())
+
+
+# ------------------------------------------------------------ host set-up (FP64)
+
+def fd_laplacian_dirichlet(n: int) -> np.ndarray:
+    A = np.empty((n, n))
+    _check(lib().mm_fd_laplacian_dirichlet(n, _dptr(A)))
+    return A
+
+
+def expm(A, z: complex = 1.0) -> np.ndarray:
+    A = np.asarray(A)
+    n = A.shape[0]
+    Are = np.ascontiguousarray(A.real, dtype=np.float64)
+    Aim = np.ascontiguousarray(A.imag, dtype=np.float64) if np.iscomplexobj(A) else None
+    E = np.empty((n, n), dtype=np.complex128)
+    z = complex(z)
+    _check(lib().mm_expm(n, _dptr(Are), _dptr(Aim) if Aim is not None else None, z.real, z.imag,
+                         E.view(np.float64).ctypes.data_as(_dp)))
+    return E
+
+
+def gauss_hermite(m: int):
+    x, W = np.empty(m), np.empty(m)
+    _check(lib().mm_gauss_hermite(m, _dptr(x), _dptr(W)))
+    return x, W
+
+
+def hermite_matrices(m: int):
+    F, B = np.empty((m, m)), np.empty((m, m))
+    _check(lib().mm_hermite_matrices(m, _dptr(F), _dptr(B)))
+    return F, B
+
+
+# ------------------------------------------------------------- mu-mode product
+
+def mumode_product(ctx: Context, u, mu: int, L, prec: str = "bf16x6", out=None, stream=None):
+    """S = U x_mu L (Definition 2.1) on a CUDA tensor u."""
+    import torch
+
+    _need_cuda(u)
+    Lf, Lc = _complex_interleaved(L)
+    m = int(np.asarray(L).shape[0])
+    dims = _dims(u.shape)
+    d = len(dims)
+    out_shape = list(u.shape)
+    out_shape[d - mu] = m
+    if out is None:
+        out = torch.empty(out_shape, dtype=u.dtype, device=u.device)
+    _check(lib().mumode_product(ctx.handle, d, dims.ctypes.data_as(_i64p), mu, _dptr(Lf), m, Lc,
+                                _dtype_code(u), PREC[prec], ctypes.c_void_p(u.data_ptr()),
+                                ctypes.c_void_p(out.data_ptr()), _stream(stream)))
+    return out
+
+
+class TuckerPlan:
+    """U <- U x_1 E_1 ... x_d E_d repeated (eq. (dd-tensor))."""
+
+    def __init__(self, ctx: Context, dims, Es, prec: str = "bf16x6", dtype=None, order=None):
+        import torch
+
+        self.ctx = ctx
+        self.dims = np.array(dims, dtype=np.int64)
+        d = len(self.dims)
+        cplx = any(np.iscomplexobj(E) for E in Es)
+        self._mats = [(np.ascontiguousarray(E, dtype=np.complex128).view(np.float64) if cplx
+                       else np.ascontiguousarray(E, dtype=np.float64)) for E in Es]
+        ptrs = (_dp * d)(*[_dptr(M) for M in self._mats])
+        if dtype is None:
+            dtype = torch.complex128 if prec == "fp64" else torch.complex64
+        self.dtype = dtype
+        code = {torch.complex64: MM_C64, torch.complex128: MM_C128, torch.float64: MM_R64, torch.float32: MM_R32}[dtype]
+        optr = (_i * d)(*order) if order is not None else None
+        h = ctypes.c_void_p()
+        _check(lib().mumode_plan_create(ctx.handle, d, self.dims.ctypes.data_as(_i64p), ptrs, int(cplx), code,
+                                        PREC[prec], optr, ctypes.byref(h)))
+        self.handle = h
+
+    def step(self, u, nsteps: int = 1, stream=None):
+        _need_cuda(u)
+        _check(lib().mumode_step(self.handle, ctypes.c_void_p(u.data_ptr()), int(nsteps), _stream(stream)))
+        return u
+
+    def norm2(self, u, stream=None) -> float:
+        _need_cuda(u)
+        out = ctypes.c_double()
+        _check(lib().mm_norm2(self.handle, ctypes.c_void_p(u.data_ptr()), 0, ctypes.byref(out), _stream(stream)))
+        return out.value
+
+    def step_host(self, u_host, nsteps: int = 1, stream=None):
+        """u_host: a CPU torch tensor (pinned for speed), stepped in place."""
+        if u_host.is_cuda or not u_host.is_contiguous():
+            raise ValueError("expected a contiguous CPU tensor")
+        _check(lib().mumode_step_host(self.handle, ctypes.c_void_p(u_host.data_ptr()), int(nsteps),
+                                      _stream(stream)))
+        return u_host
+
+    def close(self):
+        if self.handle:
+            lib().mm_plan_destroy(self.handle)
+            self.handle = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+
+class HermitePlan:
+    """Hermite spectral transforms and the HKP / GPE steps (sections 3, 4.3, 4.5)."""
+
+    def __init__(self, ctx: Context, dims, prec: str = "bf16x6", dtype=None):
+        import torch
+
+        self.ctx = ctx
+        self.dims = np.array(dims, dtype=np.int64)
+        if dtype is None:
+            dtype = torch.complex128 if prec == "fp64" else torch.complex64
+        self.dtype = dtype
+        code = MM_C128 if dtype == torch.complex128 else MM_C64
+        h = ctypes.c_void_p()
+        _check(lib().hermite_plan_create(ctx.handle, len(self.dims), self.dims.ctypes.data_as(_i64p), code,
+                                         PREC[prec], ctypes.byref(h)))
+        self.handle = h
+
+    def nodes(self, mu: int):
+        m = int(self.dims[mu - 1])
+        x, W = np.empty(m), np.empty(m)
+        _check(lib().hermite_nodes(self.handle, mu, _dptr(x), _dptr(W)))
+        return x, W
+
+    def forward(self, vals, out=None, stream=None):
+        import torch
+
+        _need_cuda(vals)
+        out = torch.empty_like(vals) if out is None else out
+        _check(lib().hermite_forward(self.handle, ctypes.c_void_p(vals.data_ptr()), ctypes.c_void_p(out.data_ptr()),
+                                     _stream(stream)))
+        return out
+
+    def backward(self, coef, out=None, stream=None):
+        import torch
+
+        _need_cuda(coef)
+        out = torch.empty_like(coef) if out is None else out
+        _check(lib().hermite_backward(self.handle, ctypes.c_void_p(coef.data_ptr()), ctypes.c_void_p(out.data_ptr()),
+                                      _stream(stream)))
+        return out
+
+    def ho_step(self, psi, tau: float, nsteps: int = 1, stream=None):
+        _need_cuda(psi)
+        _check(lib().hermite_ho_step(self.handle, ctypes.c_void_p(psi.data_ptr()), float(tau), int(nsteps),
+                                     _stream(stream)))
+        return psi
+
+    def gpe_step(self, psi, beta: float, tau: float, nsteps: int = 1, stream=None):
+        _need_cuda(psi)
+        _check(lib().split_step_gpe(self.handle, ctypes.c_void_p(psi.data_ptr()), float(beta), float(tau),
+                                    int(nsteps), _stream(stream)))
+        return psi
+
+    def norm2(self, u, weighted: bool = True, stream=None) -> float:
+        _need_cuda(u)
+        out = ctypes.c_double()
+        _check(lib().mm_norm2(self.handle, ctypes.c_void_p(u.data_ptr()), int(weighted), ctypes.byref(out),
+                              _stream(stream)))
+        return out.value
+
+    def close(self):
+        if self.handle:
+            lib().mm_plan_destroy(self.handle)
+            self.handle = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass

@@ -1,0 +1,238 @@
+"""Parity of the CUDA path (through the C ABI) with the FP64 CPU oracle.
+
+Tolerances (relative L2 over all compared points):
+  FP64 SIMT                      1e-12
+  FP32 SIMT                      2e-5 per run of a few steps
+  BF16x6 (3 pieces, 6 products)  3e-7 per mode product, 1e-6 after the
+                                 50-step n=256 run (the target accuracy)
+  BF16x3                         2e-4 per run
+  BF16 (1 piece)                 3e-2 per run (reported only)
+"""
+import numpy as np
+import pytest
+
+from paper_2103_01691_b300 import inputs
+
+pytestmark = pytest.mark.gpu
+
+TOL_STEP = {"fp64": 1e-12, "fp32": 2e-5, "bf16x6": 1e-6, "bf16x3": 2e-4, "bf16": 3e-2}
+
+
+@pytest.fixture(scope="module")
+def env():
+    import torch
+
+    from paper_2103_01691_b300 import build as mmbuild
+
+    mmbuild.build()
+    from paper_2103_01691_b300 import mumode
+
+    ctx = mumode.Context(0)
+    yield mumode, ctx, torch
+    ctx.status()
+
+
+def rel(a, b):
+    a = np.asarray(a, dtype=np.complex128)
+    b = np.asarray(b, dtype=np.complex128)
+    return float(np.linalg.norm(a - b) / np.linalg.norm(b))
+
+
+def fd_schrodinger_E(mm, n, tau):
+    return mm.expm(mm.fd_laplacian_dirichlet(n), 1j * tau)
+
+
+def to_gpu(torch, a, dtype):
+    return torch.from_numpy(np.ascontiguousarray(a)).to(dtype).cuda()
+
+
+# ------------------------------------------------------------------ FP64 paths
+
+def test_heat_fp64_n32(env, orc):
+    """Real FP64 heat equation, n = 32, tau = 1e-3, 10 steps."""
+    mm, ctx, torch = env
+    n, tau = 32, 1e-3
+    u0 = inputs.heat_u0(n, seed=0)
+    E = mm.expm(mm.fd_laplacian_dirichlet(n), tau).real
+    plan = mm.TuckerPlan(ctx, [n] * 3, [E] * 3, prec="fp64", dtype=torch.float64)
+    u = to_gpu(torch, u0, torch.float64)
+    plan.step(u, 10)
+    Eo = orc.expm_dirichlet_fd(n, tau)
+    ref = orc.tucker(u0.astype(complex), [Eo] * 3, nsteps=10).real
+    assert rel(u.cpu().numpy(), ref) <= 1e-12
+
+
+@pytest.mark.parametrize("dims,order", [((20, 24, 17), None), ((20, 24, 17), (3, 1, 2)), ((7, 5), None),
+                                        ((9,), None), ((5, 6, 4, 3), (2, 4, 1, 3))])
+def test_complex_fp64_ragged(env, orc, dims, order):
+    mm, ctx, torch = env
+    tau = 1e-4
+    Es = [fd_schrodinger_E(mm, n, tau) for n in dims]
+    u0 = inputs.complex_normal(dims[::-1], seed=2)
+    plan = mm.TuckerPlan(ctx, dims, Es, prec="fp64", order=order)
+    u = to_gpu(torch, u0, torch.complex128)
+    plan.step(u, 3)
+    Eo = [orc.expm_dirichlet_fd(n, 1j * tau) for n in dims]
+    ref = orc.tucker(u0, Eo, order=order, nsteps=3)
+    assert rel(u.cpu().numpy(), ref) <= 1e-12
+
+
+def test_fp32_simt(env, orc):
+    mm, ctx, torch = env
+    dims, tau = (33, 16, 20), 1e-4
+    Es = [fd_schrodinger_E(mm, n, tau) for n in dims]
+    u0 = inputs.complex_normal(dims[::-1], seed=2)
+    plan = mm.TuckerPlan(ctx, dims, Es, prec="fp32")
+    u = to_gpu(torch, u0, torch.complex64)
+    plan.step(u, 3)
+    ref = orc.tucker(u0.astype(np.complex64).astype(complex), [orc.expm_dirichlet_fd(n, 1j * tau) for n in dims], nsteps=3)
+    assert rel(u.cpu().numpy(), ref) <= TOL_STEP["fp32"]
+
+
+# ------------------------------------------------------------ tensor-core paths
+
+TC_DIMS = [(16, 16, 16), (32, 48, 16), (17, 33, 20), (64, 64, 64), (100, 37, 48), (128, 128, 64), (256, 16, 16),
+           (16, 256, 16), (16, 16, 256), (160, 48, 80), (9,), (40, 24)]
+
+
+@pytest.mark.parametrize("dims", TC_DIMS)
+@pytest.mark.parametrize("prec", ["bf16x6", "bf16x3", "bf16"])
+def test_tc_tucker_steps(env, orc, dims, prec):
+    mm, ctx, torch = env
+    tau, steps = 1e-4, 2
+    Es = [fd_schrodinger_E(mm, n, tau) for n in dims]
+    u0 = inputs.complex_normal(dims[::-1], seed=2).astype(np.complex64)
+    plan = mm.TuckerPlan(ctx, dims, Es, prec=prec)
+    u = to_gpu(torch, u0, torch.complex64)
+    plan.step(u, steps)
+    ref = orc.tucker(u0.astype(complex), [orc.expm_dirichlet_fd(n, 1j * tau) for n in dims], nsteps=steps)
+    err = rel(u.cpu().numpy(), ref)
+    print(f"{prec} dims={dims} steps={steps} rel_err={err:.3e}")
+    tol = {"bf16x6": 3e-7 * steps * len(dims), "bf16x3": TOL_STEP["bf16x3"], "bf16": TOL_STEP["bf16"]}[prec]
+    assert err <= tol
+
+
+@pytest.mark.parametrize("prec", ["bf16x6", "fp64", "fp32"])
+@pytest.mark.parametrize("dims", [(40, 24, 18), (17, 64, 9)])
+def test_mumode_product_rectangular(env, orc, prec, dims):
+    """Definition 2.1 with a rectangular complex (and a real) L."""
+    mm, ctx, torch = env
+    rng = np.random.default_rng(12)
+    u0 = inputs.complex_normal(dims[::-1], seed=3)
+    dt = torch.complex128 if prec == "fp64" else torch.complex64
+    tol = {"fp64": 1e-13, "fp32": 1e-5, "bf16x6": 3e-7}[prec]
+    for mu in range(1, 4):
+        for m in (dims[mu - 1] + 8, max(1, dims[mu - 1] - 5)):
+            for cplx in (True, False):
+                L = rng.standard_normal((m, dims[mu - 1]))
+                if cplx:
+                    L = L + 1j * rng.standard_normal(L.shape)
+                uin = u0 if prec == "fp64" else u0.astype(np.complex64)
+                s = mm.mumode_product(ctx, to_gpu(torch, uin, dt), mu, L, prec=prec)
+                ref = orc.mode_product(uin.astype(complex), mu, L.astype(complex))
+                err = rel(s.cpu().numpy(), ref)
+                assert err <= tol, (mu, m, cplx, err)
+
+
+def test_mode_order_independence_tc(env, orc):
+    mm, ctx, torch = env
+    dims, tau = (48, 32, 64), 1e-4
+    Es = [fd_schrodinger_E(mm, n, tau) for n in dims]
+    u0 = inputs.complex_normal(dims[::-1], seed=2).astype(np.complex64)
+    ref = orc.tucker(u0.astype(complex), [orc.expm_dirichlet_fd(n, 1j * tau) for n in dims], nsteps=2)
+    for order in [(1, 2, 3), (3, 2, 1), (2, 3, 1)]:
+        plan = mm.TuckerPlan(ctx, dims, Es, prec="bf16x6", order=order)
+        u = to_gpu(torch, u0, torch.complex64)
+        plan.step(u, 2)
+        assert rel(u.cpu().numpy(), ref) <= 3e-7 * 6
+
+
+# ------------------------------------------------------------------ Hermite / GPE
+
+@pytest.mark.parametrize("prec", ["bf16x6", "fp64"])
+def test_hermite_transforms(env, orc, prec):
+    mm, ctx, torch = env
+    m = 32
+    plan = mm.HermitePlan(ctx, [m] * 3, prec=prec)
+    x, W = plan.nodes(1)
+    xo, _, Wo = orc.gauss_hermite(m)
+    v = inputs.complex_normal((m, m, m), seed=6)
+    dt = torch.complex128 if prec == "fp64" else torch.complex64
+    vin = v if prec == "fp64" else v.astype(np.complex64)
+    c = plan.forward(to_gpu(torch, vin, dt))
+    ref_c = orc.hermite_forward(vin.astype(complex), xo, Wo)
+    tol = 1e-12 if prec == "fp64" else 1e-6
+    assert rel(c.cpu().numpy(), ref_c) <= tol
+    back = plan.backward(c)
+    ref_b = orc.hermite_backward(c.cpu().numpy().astype(complex), xo, Wo)
+    assert rel(back.cpu().numpy(), ref_b) <= tol
+
+
+@pytest.mark.parametrize("prec", ["bf16x6", "fp64"])
+def test_harmonic_oscillator_steps(env, orc, prec):
+    mm, ctx, torch = env
+    m, tau, steps = 24, 0.01, 20
+    plan = mm.HermitePlan(ctx, [m] * 3, prec=prec)
+    xo, _, Wo = orc.gauss_hermite(m)
+    psi0 = inputs.harmonic_psi0(xo, Wo, seed=1)
+    dt = torch.complex128 if prec == "fp64" else torch.complex64
+    pin = psi0 if prec == "fp64" else psi0.astype(np.complex64)
+    psi = to_gpu(torch, pin, dt)
+    plan.ho_step(psi, tau, steps)
+    ref = orc.ho_steps(pin.astype(complex), xo, Wo, tau, steps)
+    w3 = orc.weight3(Wo)
+    tol = 1e-12 if prec == "fp64" else 2e-6
+    assert orc.rel_l2(psi.cpu().numpy(), ref, w3) <= tol
+
+
+@pytest.mark.parametrize("prec", ["bf16x6", "fp64"])
+def test_gpe_strang_steps(env, orc, prec):
+    mm, ctx, torch = env
+    m, beta, tau, steps = 16, 100.0, 1e-3, 20
+    plan = mm.HermitePlan(ctx, [m] * 3, prec=prec)
+    xo, _, Wo = orc.gauss_hermite(m)
+    psi0 = inputs.gpe_psi0(xo, Wo, seed=4)
+    dt = torch.complex128 if prec == "fp64" else torch.complex64
+    pin = psi0 if prec == "fp64" else psi0.astype(np.complex64)
+    psi = to_gpu(torch, pin, dt)
+    plan.gpe_step(psi, beta, tau, steps)
+    ref = orc.gpe_steps(pin.astype(complex), xo, Wo, beta, tau, steps)
+    w3 = orc.weight3(Wo)
+    tol = 1e-11 if prec == "fp64" else 5e-6
+    assert orc.rel_l2(psi.cpu().numpy(), ref, w3) <= tol
+    n0 = plan.norm2(to_gpu(torch, pin, dt))
+    n1 = plan.norm2(psi)
+    assert abs(n1 / n0 - 1) <= (1e-12 if prec == "fp64" else 2e-6)
+
+
+# ------------------------------------------------- full size, sampled (n = 256)
+
+def test_free_schrodinger_n256_50_steps_sampled(env, orc):
+    """The precision-sweep workload at full size: n = 256, tau = 1e-4, 50
+    steps of BF16x6.  The oracle evaluates sampled entries of the exact
+    50-step result U0 x_mu E(50 tau) (E(tau)^50 = E(50 tau))."""
+    mm, ctx, torch = env
+    n, tau, steps = 256, 1e-4, 50
+    E = fd_schrodinger_E(mm, n, tau)
+    plan = mm.TuckerPlan(ctx, [n] * 3, [E] * 3, prec="bf16x6")
+    u0 = inputs.free_schrodinger_u0(n, seed=2).astype(np.complex64)
+    u = to_gpu(torch, u0, torch.complex64)
+    nrm0 = plan.norm2(u)
+    plan.step(u, steps)
+    nrm1 = plan.norm2(u)
+    got = u.cpu().numpy()
+    rng = np.random.default_rng(21)
+    idx = rng.integers(0, n, size=(48, 3))
+    idx[0] = (0, 0, 0)
+    idx[1] = (n - 1, n - 1, n - 1)
+    E50 = orc.expm_dirichlet_fd(n, 1j * tau * steps)
+    ref = orc.tucker3_entries(u0.astype(complex), E50, E50, E50, idx)
+    err = rel(got[idx[:, 2], idx[:, 1], idx[:, 0]], ref)
+    print(f"n=256 50 steps bf16x6 sampled rel_err={err:.3e} norm drift={abs(nrm1 / nrm0 - 1):.3e}")
+    assert err <= 1e-6
+    assert abs(nrm1 / nrm0 - 1) <= 1e-6
+
+
+def test_device_status_clean(env):
+    mm, ctx, torch = env
+    ctx.status()
