@@ -55,7 +55,9 @@ typedef enum {
     MM_ERR_OOM = 5,         /* device allocation failed */
     MM_ERR_CUDA = 6,        /* a CUDA runtime call failed */
     MM_ERR_TIMEOUT = 7,     /* a device-side bounded wait gave up */
-    MM_ERR_UNSUPPORTED = 8  /* feature not available on this device */
+    MM_ERR_UNSUPPORTED = 8, /* feature not available on this device */
+    MM_ERR_RANGE = 9        /* MM_PREC_F16X6: the state grew more than 16x within
+                               one sweep, beyond its fixed-point range */
 } mm_status;
 
 typedef enum {
@@ -75,13 +77,24 @@ typedef enum {
  *                    the leading product in an accumulator of its own.
  * MM_PREC_BF16X3     as above with two pieces and the three products
  *                    a + b <= 1.
- * MM_PREC_BF16       one BF16 piece, one product (reported, not accurate). */
+ * MM_PREC_BF16       one BF16 piece, one product (reported, not accurate).
+ * MM_PREC_F16X6      tcgen05 tensor cores, state MM_C64, the accurate split
+ *                    mode.  The tensor cores truncate when they add to an
+ *                    FP32 accumulator, which biases long runs of the BF16
+ *                    modes.  Here the leading pieces are integers on
+ *                    power-of-two grids (a scale per matrix row, and one
+ *                    per state tensor that follows the state's maximum from
+ *                    sweep to sweep), so the leading product is summed
+ *                    exactly; two FP16 pieces carry the remainders and the
+ *                    five correction products go to a second accumulator.
+ *                    Relative L2 error <= 1e-6 after 50 steps at n = 256. */
 typedef enum {
     MM_PREC_FP64_SIMT = 0,
     MM_PREC_FP32_SIMT = 1,
     MM_PREC_BF16X6 = 2,
     MM_PREC_BF16X3 = 3,
-    MM_PREC_BF16 = 4
+    MM_PREC_BF16 = 4,
+    MM_PREC_F16X6 = 5
 } mm_prec;
 
 /* ---------------------------------------------------------------------

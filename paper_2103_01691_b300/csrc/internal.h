@@ -45,24 +45,42 @@ struct TcState {
     int64_t plane = 0;          // elements per plane = prod np
 };
 
-// Per-direction matrix in the tensor-core form (device, bf16 pieces).
+// Per-direction matrix in the tensor-core form (device pieces).
 struct TcMatrix {
     int64_t n_in = 0, n_out = 0;    // logical sizes (columns, rows)
     int64_t k_pad = 0;              // padded contraction length
     int ni = 0, it = 0;             // number of row tiles, rows per tile
-    void *pieces = nullptr;         // [p][tile][3 blocks (-S, C, S)][it][k_pad] bf16
+    void *pieces = nullptr;         // [p][tile][3 blocks (-S, C, S)][it][k_pad], bf16 or fp16
     int npieces = 0;
+    bool fixed = false;             // MM_PREC_F16X6 pieces
+    float *rho = nullptr;           // fixed: power-of-two scale of each row (ni * it floats)
+    double row_norm = 0.0;          // max_i sum_j |E_ij|, bounds the growth of one product
+};
+
+// Device words that carry the state scale of MM_PREC_F16X6 through a sweep.
+struct TcScales {
+    const float *s_in = nullptr;          // scale of the input pieces
+    float *s_out = nullptr;               // written: scale chosen for the output pieces
+    const unsigned *max_prev = nullptr;   // max |output| of the previous sweep (float bits) or a bound
+    unsigned *max_cur = nullptr;          // atomicMax of |output| (float bits), zero before the launch
 };
 
 int tc_pieces(mm_prec p);
 bool tc_prec(mm_prec p);
-// Build the bf16 pieces of an m x n complex matrix (interleaved FP64, row-major).
-mm_status tc_matrix_create(const double *E, int64_t m, int64_t n, int npieces, TcMatrix *out);
+bool tc_fixed(mm_prec p);
+// Build the pieces of an m x n complex matrix (interleaved FP64, row-major).
+mm_status tc_matrix_create(const double *E, int64_t m, int64_t n, int npieces, bool fixed, TcMatrix *out);
 void tc_matrix_destroy(TcMatrix *M);
-// Split an interleaved complex64 tensor into padded bf16 piece planes.
-cudaError_t tc_split(const TcState &st, int npieces, const void *u_c64, void *pieces, cudaStream_t s);
-// Sum the piece planes back into an interleaved complex64 tensor.
-cudaError_t tc_merge(const TcState &st, int npieces, const void *pieces, void *u_c64, cudaStream_t s);
+// Split an interleaved complex64 tensor into padded piece planes.  For the
+// fixed-point mode the scale comes from the tensor's maximum: `work` (one
+// unsigned, device) receives it, `scale_out` the chosen scale, and
+// bound_words[q] = max * bounds[q] (float bits) for the first sweep.
+cudaError_t tc_split(const TcState &st, int npieces, bool fixed, const void *u_c64, void *pieces, unsigned *work,
+                     float *scale_out, unsigned *bound_words, const double *bounds, int nbounds, cudaStream_t s);
+// Sum the piece planes back into an interleaved complex64 tensor
+// (fixed-point mode: times *scale).
+cudaError_t tc_merge(const TcState &st, int npieces, bool fixed, const void *pieces, const float *scale, void *u_c64,
+                     cudaStream_t s);
 
 struct TcEpilogue {
     int kind = 0;      // 0: store pieces, 1: nonlinear phase then store pieces
@@ -72,6 +90,6 @@ struct TcEpilogue {
 // st_out, equal except direction mu which becomes M.n_out).
 cudaError_t tc_mode_product(const TcState &st_in, const TcState &st_out, int mu, const TcMatrix &M,
                             mm_prec prec, const void *in_pieces, void *out_pieces,
-                            const TcEpilogue &epi, int *d_err, cudaStream_t s);
+                            const TcEpilogue &epi, const TcScales &sc, int *d_err, cudaStream_t s);
 
 }  // namespace mm

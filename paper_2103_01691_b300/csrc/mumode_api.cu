@@ -35,7 +35,13 @@ struct mm_plan {
     mm_prec prec = MM_PREC_BF16X6;
     int order[mm::kMaxDims] = {};
     bool tc = false;
+    bool fixed = false;  // MM_PREC_F16X6
     int npieces = 0;
+    // fixed-point state scale words (device): scale[d], max[2][d], one work word
+    float *d_scale = nullptr;
+    unsigned *d_max = nullptr;
+    unsigned *d_work = nullptr;
+    int64_t sweep = 0;
     // Tucker matrices (one per direction) in the form of the precision
     void *Edev[mm::kMaxDims] = {};        // SIMT: element type of the state
     mm::TcMatrix Etc[mm::kMaxDims] = {};  // tensor cores
@@ -123,6 +129,7 @@ mm_status check_combo(mm_dtype dt, mm_prec pr, bool matrix_complex)
     case MM_PREC_BF16X6:
     case MM_PREC_BF16X3:
     case MM_PREC_BF16:
+    case MM_PREC_F16X6:
         if (dt == MM_C64) return MM_OK;
         break;
     default: return fail(MM_ERR_INVALID_ARG, "unknown precision %d", int(pr));
@@ -218,14 +225,51 @@ mm_status tc_sweep(mm_plan *p, mm::TcMatrix *const *M, int &cur, const mm::TcEpi
         const int mu = p->order[q];
         mm::TcEpilogue epi;
         if (q == p->d - 1) epi = last_epi;
+        mm::TcScales sc;
+        if (p->fixed) {
+            const int t = int(p->sweep & 1);
+            unsigned *cur_word = p->d_max + t * p->d + q;
+            cudaError_t e = cudaMemsetAsync(cur_word, 0, sizeof(unsigned), s);
+            if (e != cudaSuccess) return cuda_fail(e, "scale word reset");
+            sc.s_in = p->d_scale + q;
+            sc.s_out = p->d_scale + (q + 1) % p->d;
+            sc.max_prev = p->d_max + (1 - t) * p->d + q;
+            sc.max_cur = cur_word;
+        }
         cudaEvent_t ev0 = timing_event(p->ctx, true);
         if (ev0) cudaEventRecord(ev0, s);
         cudaError_t e = mm::tc_mode_product(p->st, p->st, mu, *M[mu - 1], p->prec, p->work[cur], p->work[1 - cur],
-                                            epi, p->ctx->d_err, s);
+                                            epi, sc, p->ctx->d_err, s);
         if (ev0) cudaEventRecord(timing_event(p->ctx, false), s);
         if (e != cudaSuccess) return cuda_fail(e, "tensor-core mode product launch");
         cur = 1 - cur;
     }
+    ++p->sweep;
+    return MM_OK;
+}
+
+// Split the user's complex64 tensor into the plan's piece buffer 0.  The
+// fixed-point mode also sets the state scale and, for the first sweep, the
+// bounds max|u| * prod_{r<=q} ||E_{o_r}||_inf on each position's output.
+mm_status tc_begin(mm_plan *p, mm::TcMatrix *const *M, const void *u, cudaStream_t s)
+{
+    double bounds[mm::kMaxDims];
+    double acc = 1.0;
+    for (int q = 0; q < p->d; ++q) {
+        acc *= M[p->order[q] - 1]->row_norm;
+        bounds[q] = acc;
+    }
+    p->sweep = 0;
+    cudaError_t e = mm::tc_split(p->st, p->npieces, p->fixed, u, p->work[0], p->d_work, p->d_scale,
+                                 p->d_max ? p->d_max + p->d : nullptr, bounds, p->d, s);
+    if (e != cudaSuccess) return cuda_fail(e, "split");
+    return MM_OK;
+}
+
+mm_status tc_end(mm_plan *p, int cur, void *u, cudaStream_t s)
+{
+    cudaError_t e = mm::tc_merge(p->st, p->npieces, p->fixed, p->work[cur], p->d_scale, u, s);
+    if (e != cudaSuccess) return cuda_fail(e, "merge");
     return MM_OK;
 }
 
@@ -265,6 +309,13 @@ mm_status alloc_workspace(mm_plan *p)
             e = cudaMemset(p->work[b], 0, p->work_bytes);
             if (e != cudaSuccess) return cuda_fail(e, "workspace memset");
         }
+        if (p->fixed) {
+            e = cudaMalloc(&p->d_scale, sizeof(float) * p->d);
+            if (e == cudaSuccess) e = cudaMalloc(&p->d_max, sizeof(unsigned) * 2 * p->d);
+            if (e == cudaSuccess) e = cudaMalloc(&p->d_work, sizeof(unsigned));
+            if (e == cudaSuccess) e = cudaMemset(p->d_max, 0, sizeof(unsigned) * 2 * p->d);
+            if (e != cudaSuccess) return fail(MM_ERR_OOM, "scale words");
+        }
     } else {
         p->work_bytes = size_t(p->count) * elem_bytes(p->dtype);
         e = cudaMalloc(&p->work[0], p->work_bytes);
@@ -277,7 +328,7 @@ mm_status upload_matrix(mm_plan *p, const double *E, int64_t m, int64_t n, bool 
 {
     if (p->tc) {
         std::vector<double> c = as_complex(E, m * n, Ec);
-        return mm::tc_matrix_create(c.data(), m, n, p->npieces, tcm);
+        return mm::tc_matrix_create(c.data(), m, n, p->npieces, p->fixed, tcm);
     }
     return upload_simt(E, m, n, Ec, p->dtype, simt);
 }
@@ -317,6 +368,7 @@ mm_status plan_common(mm_ctx *ctx, int d, const int64_t *n, mm_dtype dtype, mm_p
     p->dtype = dtype;
     p->prec = prec;
     p->tc = tc;
+    p->fixed = mm::tc_fixed(prec);
     p->npieces = mm::tc_pieces(prec);
     *made = p;
     return MM_OK;
@@ -530,25 +582,41 @@ mm_status mumode_product(mm_ctx *ctx, int d, const int64_t *n, int mu, const dou
         return fail(MM_ERR_UNSUPPORTED, "tensor-core precisions need an sm_103 device");
     if (nmu > 256 || m > 256) return fail(MM_ERR_SHAPE, "tensor-core path supports n_mu, m <= 256");
     const int NP = mm::tc_pieces(prec);
+    const bool fixed = mm::tc_fixed(prec);
     std::vector<double> Lc = as_complex(L, m * nmu, L_is_complex != 0);
     mm::TcMatrix M;
-    if ((st = mm::tc_matrix_create(Lc.data(), m, nmu, NP, &M))) return st;
+    if ((st = mm::tc_matrix_create(Lc.data(), m, nmu, NP, fixed, &M))) return st;
     mm::TcState si = make_state(d, n), so = make_state(d, nout);
-    void *bi = nullptr, *bo = nullptr;
+    void *bi = nullptr, *bo = nullptr, *words = nullptr;
     const size_t bytes_i = size_t(si.plane) * 2 * NP * 2, bytes_o = size_t(so.plane) * 2 * NP * 2;
     cudaError_t e = cudaMalloc(&bi, bytes_i);
     if (e == cudaSuccess) e = cudaMalloc(&bo, bytes_o);
+    if (e == cudaSuccess) e = cudaMalloc(&words, 64);
     if (e != cudaSuccess) {
         cudaFree(bi);
+        cudaFree(bo);
         mm::tc_matrix_destroy(&M);
         return fail(MM_ERR_OOM, "temporary piece buffers (%zu + %zu bytes)", bytes_i, bytes_o);
     }
-    e = mm::tc_split(si, NP, u_dev, bi, s);
-    if (e == cudaSuccess) e = mm::tc_mode_product(si, so, mu, M, prec, bi, bo, mm::TcEpilogue{}, ctx->d_err, s);
-    if (e == cudaSuccess) e = mm::tc_merge(so, NP, bo, s_dev, s);
+    // words: [0] scale in, [1] scale out (floats), [2] bound, [3] max, [4] work (unsigned)
+    float *scales = reinterpret_cast<float *>(words);
+    unsigned *uw = reinterpret_cast<unsigned *>(words);
+    mm::TcScales sc;
+    if (fixed) {
+        sc.s_in = scales;
+        sc.s_out = scales + 1;
+        sc.max_prev = uw + 2;
+        sc.max_cur = uw + 3;
+    }
+    const double bound = M.row_norm;
+    e = cudaMemsetAsync(words, 0, 64, s);
+    if (e == cudaSuccess) e = mm::tc_split(si, NP, fixed, u_dev, bi, uw + 4, scales, uw + 2, &bound, 1, s);
+    if (e == cudaSuccess) e = mm::tc_mode_product(si, so, mu, M, prec, bi, bo, mm::TcEpilogue{}, sc, ctx->d_err, s);
+    if (e == cudaSuccess) e = mm::tc_merge(so, NP, fixed, bo, scales + 1, s_dev, s);
     cudaError_t e2 = cudaStreamSynchronize(s);
     cudaFree(bi);
     cudaFree(bo);
+    cudaFree(words);
     mm::tc_matrix_destroy(&M);
     if (e != cudaSuccess) return cuda_fail(e, "tensor-core mode product");
     if (e2 != cudaSuccess) return cuda_fail(e2, "tensor-core mode product (sync)");
@@ -598,16 +666,13 @@ mm_status mumode_step(mm_plan *p, void *u_dev, int64_t nsteps, void *stream)
             if ((st = simt_sweep(p, p->Edev, u_dev, s))) return st;
         return MM_OK;
     }
-    cudaError_t e = mm::tc_split(p->st, p->npieces, u_dev, p->work[0], s);
-    if (e != cudaSuccess) return cuda_fail(e, "split");
     int cur = 0;
     mm::TcMatrix *M[mm::kMaxDims];
     for (int v = 0; v < p->d; ++v) M[v] = &p->Etc[v];
+    if ((st = tc_begin(p, M, u_dev, s))) return st;
     for (int64_t k = 0; k < nsteps; ++k)
         if ((st = tc_sweep(p, M, cur, mm::TcEpilogue{}, s))) return st;
-    e = mm::tc_merge(p->st, p->npieces, p->work[cur], u_dev, s);
-    if (e != cudaSuccess) return cuda_fail(e, "merge");
-    return MM_OK;
+    return tc_end(p, cur, u_dev, s);
 }
 
 mm_status mumode_step_host(mm_plan *p, void *u_host, int64_t nsteps, void *stream)
@@ -648,6 +713,9 @@ void mm_plan_destroy(mm_plan *p)
     if (p->work[0]) cudaFree(p->work[0]);
     if (p->work[1]) cudaFree(p->work[1]);
     if (p->staging) cudaFree(p->staging);
+    if (p->d_scale) cudaFree(p->d_scale);
+    if (p->d_max) cudaFree(p->d_max);
+    if (p->d_work) cudaFree(p->d_work);
     delete p;
 }
 
@@ -708,15 +776,12 @@ static mm_status hermite_apply(mm_plan *p, bool forward, const void *in, void *o
         if (e != cudaSuccess) return cuda_fail(e, "copy");
         return simt_sweep(p, forward ? p->Fdev : p->Bdev, out, s);
     }
-    cudaError_t e = mm::tc_split(p->st, p->npieces, in, p->work[0], s);
-    if (e != cudaSuccess) return cuda_fail(e, "split");
     int cur = 0;
     mm::TcMatrix *M[mm::kMaxDims];
     for (int v = 0; v < p->d; ++v) M[v] = forward ? &p->Ftc[v] : &p->Btc[v];
+    if ((st = tc_begin(p, M, in, s))) return st;
     if ((st = tc_sweep(p, M, cur, mm::TcEpilogue{}, s))) return st;
-    e = mm::tc_merge(p->st, p->npieces, p->work[cur], out, s);
-    if (e != cudaSuccess) return cuda_fail(e, "merge");
-    return MM_OK;
+    return tc_end(p, cur, out, s);
 }
 
 mm_status hermite_forward(mm_plan *p, const void *values_dev, void *coeffs_dev, void *stream)
@@ -744,16 +809,13 @@ mm_status hermite_ho_step(mm_plan *p, void *psi, double tau, int64_t nsteps, voi
             if ((st = simt_sweep(p, p->Pdev[slot], psi, s))) return st;
         return MM_OK;
     }
-    cudaError_t e = mm::tc_split(p->st, p->npieces, psi, p->work[0], s);
-    if (e != cudaSuccess) return cuda_fail(e, "split");
     int cur = 0;
     mm::TcMatrix *M[mm::kMaxDims];
     for (int v = 0; v < p->d; ++v) M[v] = &p->Ptc[slot][v];
+    if ((st = tc_begin(p, M, psi, s))) return st;
     for (int64_t k = 0; k < nsteps; ++k)
         if ((st = tc_sweep(p, M, cur, mm::TcEpilogue{}, s))) return st;
-    e = mm::tc_merge(p->st, p->npieces, p->work[cur], psi, s);
-    if (e != cudaSuccess) return cuda_fail(e, "merge");
-    return MM_OK;
+    return tc_end(p, cur, psi, s);
 }
 
 mm_status split_step_gpe(mm_plan *p, void *psi, double beta, double tau, int64_t nsteps, void *stream)
@@ -781,23 +843,20 @@ mm_status split_step_gpe(mm_plan *p, void *psi, double beta, double tau, int64_t
         }
         return simt_sweep(p, p->Pdev[half], psi, s);
     }
-    cudaError_t e = mm::tc_split(p->st, p->npieces, psi, p->work[0], s);
-    if (e != cudaSuccess) return cuda_fail(e, "split");
     int cur = 0;
     mm::TcMatrix *Mh[mm::kMaxDims], *Mf[mm::kMaxDims];
     for (int v = 0; v < p->d; ++v) {
         Mh[v] = &p->Ptc[half][v];
         Mf[v] = &p->Ptc[full][v];
     }
+    if ((st = tc_begin(p, Mh, psi, s))) return st;
     mm::TcEpilogue nl;
     nl.kind = 1;
     nl.tb = tb;
     for (int64_t k = 0; k < nsteps; ++k)
         if ((st = tc_sweep(p, k == 0 ? Mh : Mf, cur, nl, s))) return st;
     if ((st = tc_sweep(p, Mh, cur, mm::TcEpilogue{}, s))) return st;
-    e = mm::tc_merge(p->st, p->npieces, p->work[cur], psi, s);
-    if (e != cudaSuccess) return cuda_fail(e, "merge");
-    return MM_OK;
+    return tc_end(p, cur, psi, s);
 }
 
 mm_status mm_norm2(mm_plan *p, const void *u_dev, int weighted, double *out_host, void *stream)

@@ -30,6 +30,22 @@
 // accumulated in FP32 in tensor memory; the leading product e0 x0 has an
 // accumulator of its own so that the smaller corrections are not rounded
 // against the large running sum; the epilogue adds the two in FP32.
+// The tensor cores truncate (round toward zero) when they add to an FP32
+// accumulator, so with floating BF16 pieces the leading sum carries a bias
+// of about half an ulp per addition, which grows linearly over many steps.
+// The fixed-point variant (MM_PREC_F16X6, template flag FX) removes it:
+//   E_ij = rho_i (e0 + eR),  rho_i a power of two per row chosen so that
+//          sum_j (|C_ij| + |S_ij|) / rho_i <= 4096, e0 = rint(E_ij / rho_i),
+//   x    = s (x0 + xR),      s a power of two per state tensor chosen so
+//          that max |x| / s <= 1024, x0 = rint(x / s),
+// and the remainders eR, xR (|.| <= 1/2) are each carried by two FP16
+// pieces.  The integer products e0 x0 then sum to integers below 2^24
+// (4096 * 2048 * 2 planes), which the FP32 accumulator holds exactly, so
+// truncation never acts on the leading sum; only the five correction
+// products (about 2^-7 of the result) see it.  The state scale follows the
+// state: each epilogue takes its output scale from the maximum that the
+// same direction produced one sweep earlier (or from a bound in the first
+// sweep) and accumulates the new maximum with atomicMax.
 //
 // Roles (256 threads): warp 0 lane 0 issues TMA loads into a 3-stage ring,
 // warp 1 allocates tensor memory and its lane 0 issues tcgen05.mma, and
@@ -37,8 +53,10 @@
 // lanes 32 (w % 4) .. + 31, half of the column chunks each).
 #include <cuda.h>
 #include <cuda_bf16.h>
+#include <cuda_fp16.h>
 #include <cuda_runtime.h>
 
+#include <algorithm>
 #include <cmath>
 #include <cstdint>
 #include <cstring>
@@ -55,10 +73,12 @@ int tc_pieces(mm_prec p)
     case MM_PREC_BF16X6: return 3;
     case MM_PREC_BF16X3: return 2;
     case MM_PREC_BF16: return 1;
+    case MM_PREC_F16X6: return 3;
     default: return 0;
     }
 }
 bool tc_prec(mm_prec p) { return tc_pieces(p) > 0; }
+bool tc_fixed(mm_prec p) { return p == MM_PREC_F16X6; }
 
 static inline int64_t round16(int64_t v) { return (v + 15) / 16 * 16; }
 
@@ -82,7 +102,26 @@ static uint16_t bf16_bits(double exact_bf16_value)
     return uint16_t(u >> 16);
 }
 
-mm_status tc_matrix_create(const double *E, int64_t m, int64_t n, int npieces, TcMatrix *out)
+// Round a double to the nearest FP16 value (ties to even, subnormals kept).
+static double f16_round(double v)
+{
+    if (v == 0.0 || !std::isfinite(v)) return 0.0;
+    const int e = std::ilogb(v);
+    if (e < -14) return std::nearbyint(std::ldexp(v, 24)) * std::ldexp(1.0, -24);  // subnormal grid 2^-24
+    return std::ldexp(std::nearbyint(std::ldexp(v, 10 - e)), e - 10);
+}
+static uint16_t f16_bits(double exact)
+{
+    if (exact == 0.0) return 0;
+    const uint16_t sign = exact < 0 ? 0x8000u : 0u;
+    const double a = std::fabs(exact);
+    if (a < std::ldexp(1.0, -14)) return uint16_t(sign | uint16_t(std::ldexp(a, 24)));
+    const int e = std::ilogb(a);
+    const uint16_t mant = uint16_t(std::ldexp(a, -e) * 1024.0 - 1024.0);
+    return uint16_t(sign | uint16_t((e + 15) << 10) | mant);
+}
+
+mm_status tc_matrix_create(const double *E, int64_t m, int64_t n, int npieces, bool fixed, TcMatrix *out)
 {
     TcMatrix M;
     M.n_in = n;
@@ -92,31 +131,58 @@ mm_status tc_matrix_create(const double *E, int64_t m, int64_t n, int npieces, T
     M.ni = int((m_pad + 127) / 128);
     M.it = int(round16((m_pad + M.ni - 1) / M.ni));
     M.npieces = npieces;
+    M.fixed = fixed;
     const int64_t rows = int64_t(npieces) * M.ni * 3 * M.it;
     std::vector<uint16_t> h(size_t(rows * M.k_pad), 0);
-    for (int64_t i = 0; i < m; ++i)
+    std::vector<float> rho(size_t(M.ni) * M.it, 1.0f);
+    for (int64_t i = 0; i < m; ++i) {
+        double sum_abs = 0.0, sum_mod = 0.0;
+        for (int64_t j = 0; j < n; ++j) {
+            const double c = E[2 * (i * n + j)], sv = E[2 * (i * n + j) + 1];
+            sum_abs += std::fabs(c) + std::fabs(sv);
+            sum_mod += std::hypot(c, sv);
+        }
+        M.row_norm = std::max(M.row_norm, sum_mod);
+        double r = 1.0;
+        if (fixed && sum_abs > 0.0) r = std::ldexp(1.0, int(std::ceil(std::log2(sum_abs / 4096.0))));
+        rho[size_t(i)] = float(r);
+        const int64_t tile = i / M.it, il = i % M.it;
         for (int64_t j = 0; j < n; ++j) {
             double rest[2] = {E[2 * (i * n + j)], E[2 * (i * n + j) + 1]};  // C, S
-            const int64_t tile = i / M.it, il = i % M.it;
+            if (fixed) {
+                rest[0] /= r;
+                rest[1] /= r;
+            }
             for (int p = 0; p < npieces; ++p) {
                 double piece[2];
                 for (int q = 0; q < 2; ++q) {
-                    piece[q] = bf16_round(rest[q]);
+                    if (!fixed) piece[q] = bf16_round(rest[q]);
+                    else if (p == 0) piece[q] = f16_round(std::nearbyint(rest[q]));  // integer, exact below 2048
+                    else piece[q] = f16_round(rest[q]);
                     rest[q] -= piece[q];
                 }
                 // blocks: 0 = -S, 1 = C, 2 = S
                 const double vals[3] = {-piece[1], piece[0], piece[1]};
                 for (int w = 0; w < 3; ++w) {
                     const int64_t row = ((int64_t(p) * M.ni + tile) * 3 + w) * M.it + il;
-                    h[size_t(row * M.k_pad + j)] = bf16_bits(vals[w]);
+                    h[size_t(row * M.k_pad + j)] = fixed ? f16_bits(vals[w]) : bf16_bits(vals[w]);
                 }
             }
         }
+    }
     if (cudaMalloc(&M.pieces, h.size() * 2) != cudaSuccess)
         return fail(MM_ERR_OOM, "cudaMalloc of %zu bytes for matrix pieces failed", h.size() * 2);
     if (cudaMemcpy(M.pieces, h.data(), h.size() * 2, cudaMemcpyHostToDevice) != cudaSuccess) {
         cudaFree(M.pieces);
         return fail(MM_ERR_CUDA, "upload of matrix pieces failed");
+    }
+    if (fixed) {
+        if (cudaMalloc(&M.rho, rho.size() * sizeof(float)) != cudaSuccess ||
+            cudaMemcpy(M.rho, rho.data(), rho.size() * sizeof(float), cudaMemcpyHostToDevice) != cudaSuccess) {
+            cudaFree(M.pieces);
+            if (M.rho) cudaFree(M.rho);
+            return fail(MM_ERR_OOM, "row scales upload failed");
+        }
     }
     *out = M;
     return MM_OK;
@@ -124,8 +190,11 @@ mm_status tc_matrix_create(const double *E, int64_t m, int64_t n, int npieces, T
 
 void tc_matrix_destroy(TcMatrix *M)
 {
-    if (M && M->pieces) cudaFree(M->pieces);
-    if (M) M->pieces = nullptr;
+    if (!M) return;
+    if (M->pieces) cudaFree(M->pieces);
+    if (M->rho) cudaFree(M->rho);
+    M->pieces = nullptr;
+    M->rho = nullptr;
 }
 
 // ---- device: splitting, merging -----------------------------------------------------
@@ -136,20 +205,75 @@ struct Dims {
     int64_t np[kMaxDims];
 };
 
-__device__ __forceinline__ void split_value(float v, int np, __nv_bfloat16 *out, int64_t stride)
+struct Bounds {
+    double b[kMaxDims];
+};
+
+// Floating BF16 pieces: out[p * stride] = bf16 of what remains after p pieces.
+__device__ __forceinline__ void split_bf16(float v, int np, uint16_t *out, int64_t stride)
 {
     float r = v;
     for (int p = 0; p < np; ++p) {
         const __nv_bfloat16 b = __float2bfloat16_rn(r);
-        out[p * stride] = b;
+        out[p * stride] = __bfloat16_as_ushort(b);
         r -= __bfloat162float(b);
     }
 }
 
-// Padded-index loop: reads the logical complex64 tensor, writes all pieces.
-__global__ void split_kernel(Dims dm, int64_t plane, int npieces, const float2 *__restrict__ u,
-                             __nv_bfloat16 *__restrict__ pieces)
+// Fixed-point FP16 pieces of x on the grid s = 2^es: x / s = h0 + h1 + h2
+// with h0 an integer (exact in FP16 below 2048) and h1, h2 the remainder.
+// Every subtraction is exact (Sterbenz), so the pieces represent x / s to
+// about 2^-22 of the grid unit.
+__device__ __forceinline__ void split_fx(float x, int es, uint16_t &b0, uint16_t &b1, uint16_t &b2)
 {
+    const float xs = ldexpf(x, -es);
+    const __half h0 = __float2half_rn(rintf(xs));
+    const float r = xs - __half2float(h0);
+    const __half h1 = __float2half_rn(r);
+    const __half h2 = __float2half_rn(r - __half2float(h1));
+    b0 = __half_as_ushort(h0);
+    b1 = __half_as_ushort(h1);
+    b2 = __half_as_ushort(h2);
+}
+
+// Grid exponent for a tensor whose largest magnitude is m: s = 2^es with m / s < 1024.
+__device__ __forceinline__ int grid_exponent(float m)
+{
+    if (!(m > 0.0f) || !(m < 3.0e38f)) return 0;
+    int e;
+    frexpf(m, &e);  // m = f 2^e, f in [0.5, 1)
+    return e - 10;
+}
+
+__global__ void max_abs_kernel(int64_t count, const float2 *__restrict__ u, unsigned *out)
+{
+    float m = 0.0f;
+    for (int64_t q = blockIdx.x * int64_t(blockDim.x) + threadIdx.x; q < count; q += int64_t(gridDim.x) * blockDim.x) {
+        const float2 v = u[q];
+        m = fmaxf(m, fmaxf(fabsf(v.x), fabsf(v.y)));
+    }
+    unsigned b = __reduce_max_sync(0xffffffffu, __float_as_uint(m));
+    if ((threadIdx.x & 31) == 0 && b) atomicMax(out, b);
+}
+
+// Padded-index loop: reads the logical complex64 tensor, writes all pieces.
+template <bool FX>
+__global__ void split_kernel(Dims dm, int64_t plane, int npieces, const float2 *__restrict__ u,
+                             uint16_t *__restrict__ pieces, const unsigned *maxw, float *scale_out,
+                             unsigned *bound_words, Bounds bounds, int nb)
+{
+    int es = 0;
+    if (FX) {
+        const float m = __uint_as_float(*maxw);
+        es = grid_exponent(m);
+        if (blockIdx.x == 0 && threadIdx.x == 0) {
+            *scale_out = ldexpf(1.0f, es);
+            for (int q = 0; q < nb; ++q) {
+                const double v = double(m) * bounds.b[q];
+                bound_words[q] = __float_as_uint(float(v < 3.0e38 ? v : 3.0e38));
+            }
+        }
+    }
     for (int64_t q = blockIdx.x * int64_t(blockDim.x) + threadIdx.x; q < plane; q += int64_t(gridDim.x) * blockDim.x) {
         int64_t rem = q, lin = 0, mul = 1;
         bool inside = true;
@@ -161,15 +285,25 @@ __global__ void split_kernel(Dims dm, int64_t plane, int npieces, const float2 *
             mul *= dm.n[v];
         }
         const float2 x = inside ? u[lin] : make_float2(0.f, 0.f);
-        split_value(x.x, npieces, pieces + q, plane);
-        split_value(x.y, npieces, pieces + int64_t(npieces) * plane + q, plane);
+        if (FX) {
+            uint16_t b[6];
+            split_fx(x.x, es, b[0], b[1], b[2]);
+            split_fx(x.y, es, b[3], b[4], b[5]);
+#pragma unroll
+            for (int k = 0; k < 6; ++k) pieces[k * plane + q] = b[k];
+        } else {
+            split_bf16(x.x, npieces, pieces + q, plane);
+            split_bf16(x.y, npieces, pieces + int64_t(npieces) * plane + q, plane);
+        }
     }
 }
 
-// Logical-index loop: sums the pieces back (exact for three pieces).
-__global__ void merge_kernel(Dims dm, int64_t plane, int npieces, const __nv_bfloat16 *__restrict__ pieces,
-                             float2 *__restrict__ u, int64_t count)
+// Logical-index loop: sums the pieces back (exact for three BF16 pieces).
+template <bool FX>
+__global__ void merge_kernel(Dims dm, int64_t plane, int npieces, const uint16_t *__restrict__ pieces,
+                             const float *scale, float2 *__restrict__ u, int64_t count)
 {
+    const float s = FX ? *scale : 1.0f;
     for (int64_t q = blockIdx.x * int64_t(blockDim.x) + threadIdx.x; q < count; q += int64_t(gridDim.x) * blockDim.x) {
         int64_t rem = q, pad = 0, mul = 1;
         for (int v = 0; v < dm.d; ++v) {
@@ -180,10 +314,16 @@ __global__ void merge_kernel(Dims dm, int64_t plane, int npieces, const __nv_bfl
         }
         float re = 0.f, im = 0.f;
         for (int p = npieces - 1; p >= 0; --p) {
-            re += __bfloat162float(pieces[p * plane + pad]);
-            im += __bfloat162float(pieces[(npieces + p) * plane + pad]);
+            const uint16_t br = pieces[p * plane + pad], bi = pieces[(npieces + p) * plane + pad];
+            if (FX) {
+                re += __half2float(__ushort_as_half(br));
+                im += __half2float(__ushort_as_half(bi));
+            } else {
+                re += __bfloat162float(__ushort_as_bfloat16(br));
+                im += __bfloat162float(__ushort_as_bfloat16(bi));
+            }
         }
-        u[q] = make_float2(re, im);
+        u[q] = make_float2(re * s, im * s);
     }
 }
 
@@ -204,20 +344,41 @@ static int grid_for(int64_t count)
     return int(b < 148 * 32 ? (b > 0 ? b : 1) : 148 * 32);
 }
 
-cudaError_t tc_split(const TcState &st, int npieces, const void *u_c64, void *pieces, cudaStream_t s)
+cudaError_t tc_split(const TcState &st, int npieces, bool fixed, const void *u_c64, void *pieces, unsigned *work,
+                     float *scale_out, unsigned *bound_words, const double *bounds, int nbounds, cudaStream_t s)
 {
-    split_kernel<<<grid_for(st.plane), 256, 0, s>>>(make_dims(st), st.plane, npieces, (const float2 *)u_c64,
-                                                    (__nv_bfloat16 *)pieces);
+    Bounds bd{};
+    for (int q = 0; q < nbounds && q < kMaxDims; ++q) bd.b[q] = bounds[q];
+    if (fixed) {
+        int64_t count = 1;
+        for (int v = 0; v < st.d; ++v) count *= st.n[v];
+        cudaError_t e = cudaMemsetAsync(work, 0, sizeof(unsigned), s);
+        if (e != cudaSuccess) return e;
+        max_abs_kernel<<<grid_for(count), 256, 0, s>>>(count, (const float2 *)u_c64, work);
+        count_launch();
+        split_kernel<true><<<grid_for(st.plane), 256, 0, s>>>(make_dims(st), st.plane, npieces, (const float2 *)u_c64,
+                                                            (uint16_t *)pieces, work, scale_out, bound_words, bd,
+                                                            nbounds);
+    } else {
+        split_kernel<false><<<grid_for(st.plane), 256, 0, s>>>(make_dims(st), st.plane, npieces,
+                                                             (const float2 *)u_c64, (uint16_t *)pieces, nullptr,
+                                                             nullptr, nullptr, bd, 0);
+    }
     count_launch();
     return cudaGetLastError();
 }
 
-cudaError_t tc_merge(const TcState &st, int npieces, const void *pieces, void *u_c64, cudaStream_t s)
+cudaError_t tc_merge(const TcState &st, int npieces, bool fixed, const void *pieces, const float *scale, void *u_c64,
+                     cudaStream_t s)
 {
     int64_t count = 1;
     for (int v = 0; v < st.d; ++v) count *= st.n[v];
-    merge_kernel<<<grid_for(count), 256, 0, s>>>(make_dims(st), st.plane, npieces, (const __nv_bfloat16 *)pieces,
-                                                 (float2 *)u_c64, count);
+    if (fixed)
+        merge_kernel<true><<<grid_for(count), 256, 0, s>>>(make_dims(st), st.plane, npieces, (const uint16_t *)pieces,
+                                                         scale, (float2 *)u_c64, count);
+    else
+        merge_kernel<false><<<grid_for(count), 256, 0, s>>>(make_dims(st), st.plane, npieces, (const uint16_t *)pieces,
+                                                          nullptr, (float2 *)u_c64, count);
     count_launch();
     return cudaGetLastError();
 }
@@ -238,8 +399,11 @@ struct TcArgs {
     int it, ni, kblocks;
     int stage_bytes, tx_bytes, e_offset;
     float tb;               // tau * beta for the nonlinear epilogue
-    __nv_bfloat16 *out;
+    uint16_t *out;
     int *err;
+    // fixed-point mode
+    const float *rho;
+    TcScales sc;
 };
 
 // Piece pairs (a, b) of e_a x_b with a + b <= NP - 1, leading pair first.
@@ -247,7 +411,7 @@ __host__ __device__ constexpr int num_terms(int NP) { return NP == 3 ? 6 : (NP =
 __host__ __device__ constexpr int term_a(int t) { return t == 2 ? 1 : (t == 4 ? 1 : (t == 5 ? 2 : 0)); }
 __host__ __device__ constexpr int term_b(int t) { return t == 1 ? 1 : (t == 3 ? 2 : (t == 4 ? 1 : 0)); }
 
-template <int NP, bool KMAJOR, int EPI>
+template <int NP, bool KMAJOR, int EPI, bool FX>
 __global__ void __launch_bounds__(256, 1)
     tc_mode_kernel(const __grid_constant__ CUtensorMap mapX, const __grid_constant__ CUtensorMap mapE, TcArgs a)
 {
@@ -261,8 +425,8 @@ __global__ void __launch_bounds__(256, 1)
     const int warp = threadIdx.x / 32, lane = threadIdx.x % 32;
     const int tile = blockIdx.x / a.ni, h = blockIdx.x % a.ni;
     const int acc_cols = 2 * a.it;
-    const uint32_t ncols = NP > 1 ? (acc_cols * 2 <= 32 ? 32 : (acc_cols * 2 <= 64 ? 64 : (acc_cols * 2 <= 128 ? 128 : (acc_cols * 2 <= 256 ? 256 : 512))))
-                                  : (acc_cols <= 32 ? 32 : (acc_cols <= 64 ? 64 : (acc_cols <= 128 ? 128 : 256)));
+    const int need = NP > 1 ? 2 * acc_cols : acc_cols;
+    const uint32_t ncols = need <= 32 ? 32 : (need <= 64 ? 64 : (need <= 128 ? 128 : (need <= 256 ? 256 : 512)));
 
     if (threadIdx.x == 0) {
         for (int s = 0; s < kStages; ++s) {
@@ -316,7 +480,8 @@ __global__ void __launch_bounds__(256, 1)
         }
     } else if (warp == 1 && lane == 0) {
         // ---------------- MMA issuer ----------------
-        const uint32_t idesc = idesc_bf16_f32(kTileM, 2 * a.it, !KMAJOR, false);
+        const uint32_t idesc = FX ? idesc_f16_f32(kTileM, 2 * a.it, !KMAJOR, false)
+                                  : idesc_bf16_f32(kTileM, 2 * a.it, !KMAJOR, false);
         bool started[2] = {false, false};
         for (int kb = 0; kb < a.kblocks && ok; ++kb) {
             const int s = kb % kStages;
@@ -348,6 +513,15 @@ __global__ void __launch_bounds__(256, 1)
     __syncwarp();
 
     // ---------------- epilogue: all warps ----------------
+    float s_in = 1.0f;
+    int es_out = 0;
+    if (FX) {
+        s_in = *a.sc.s_in;
+        es_out = grid_exponent(__uint_as_float(*a.sc.max_prev));
+        if (blockIdx.x == 0 && threadIdx.x == 0) *a.sc.s_out = ldexpf(1.0f, es_out);
+    }
+    float local_max = 0.0f;
+    bool range_ok = true;
     bool acc_ready = mbar_wait(accf, 0, a.err, MM_ERR_TIMEOUT);
     tc_fence_after();
     const int quarter = warp % 4, half = warp / 4;
@@ -378,13 +552,18 @@ __global__ void __launch_bounds__(256, 1)
         if (!acc_ready || !valid) continue;
         const int64_t i0 = int64_t(h) * a.it + ch * 16;
         if (i0 >= a.mp) continue;
-        __nv_bfloat16 pr[3][16], pi[3][16];
+        uint16_t pr[3][16], pi[3][16];
 #pragma unroll
         for (int k = 0; k < 16; ++k) {
             float xr = re0[k], xi = im0[k];
             if (NP > 1) {
                 xr += re1[k];
                 xi += im1[k];
+            }
+            if (FX) {
+                const float g = __ldg(a.rho + i0 + k) * s_in;  // power of two: exact
+                xr *= g;
+                xi *= g;
             }
             if (EPI == 1) {
                 const float th = a.tb * (xr * xr + xi * xi);
@@ -394,13 +573,21 @@ __global__ void __launch_bounds__(256, 1)
                 xr = yr;
                 xi = yi;
             }
-            float rr = xr, ri = xi;
+            if (FX) {
+                local_max = fmaxf(local_max, fmaxf(fabsf(xr), fabsf(xi)));
+                range_ok &= fabsf(ldexpf(xr, -es_out)) < 16384.f && fabsf(ldexpf(xi, -es_out)) < 16384.f;
+                split_fx(xr, es_out, pr[0][k], pr[1][k], pr[2][k]);
+                split_fx(xi, es_out, pi[0][k], pi[1][k], pi[2][k]);
+            } else {
+                float rr = xr, ri = xi;
 #pragma unroll
-            for (int p = 0; p < NP; ++p) {
-                pr[p][k] = __float2bfloat16_rn(rr);
-                pi[p][k] = __float2bfloat16_rn(ri);
-                rr -= __bfloat162float(pr[p][k]);
-                ri -= __bfloat162float(pi[p][k]);
+                for (int p = 0; p < NP; ++p) {
+                    const __nv_bfloat16 br = __float2bfloat16_rn(rr), bi = __float2bfloat16_rn(ri);
+                    pr[p][k] = __bfloat16_as_ushort(br);
+                    pi[p][k] = __bfloat16_as_ushort(bi);
+                    rr -= __bfloat162float(br);
+                    ri -= __bfloat162float(bi);
+                }
             }
         }
         if (KMAJOR) {
@@ -425,6 +612,11 @@ __global__ void __launch_bounds__(256, 1)
                 }
             }
         }
+    }
+    if (FX) {
+        const unsigned m = __reduce_max_sync(0xffffffffu, __float_as_uint(local_max));
+        if (lane == 0 && m) atomicMax(a.sc.max_cur, m);
+        if (!range_ok && a.err) atomicCAS(a.err, 0, MM_ERR_RANGE);
     }
     tc_fence_before();
     __syncthreads();
@@ -460,16 +652,17 @@ static bool encode(CUtensorMap *map, void *base, int rank, const cuuint64_t *dim
     EncodeTiledFn fn = encode_fn();
     if (!fn) return false;
     cuuint32_t estr[5] = {1, 1, 1, 1, 1};
+    // 16-bit elements (BF16 or FP16 pieces: TMA copies them bit for bit; zero fill is +0 in both)
     return fn(map, CU_TENSOR_MAP_DATA_TYPE_BFLOAT16, cuuint32_t(rank), base, dims, strides_bytes, box, estr,
               CU_TENSOR_MAP_INTERLEAVE_NONE, swz, CU_TENSOR_MAP_L2_PROMOTION_L2_256B,
               CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE) == CUDA_SUCCESS;
 }
 
-template <int NP, bool KM, int EPI>
+template <int NP, bool KM, int EPI, bool FX>
 static cudaError_t launch_tc(const CUtensorMap &mx, const CUtensorMap &me, const TcArgs &a, int grid, int smem,
                              cudaStream_t s)
 {
-    auto kern = tc_mode_kernel<NP, KM, EPI>;
+    auto kern = tc_mode_kernel<NP, KM, EPI, FX>;
     cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
     if (e != cudaSuccess) return e;
     kern<<<grid, 256, smem, s>>>(mx, me, a);
@@ -477,20 +670,25 @@ static cudaError_t launch_tc(const CUtensorMap &mx, const CUtensorMap &me, const
     return cudaGetLastError();
 }
 
-template <int NP>
+template <int NP, bool FX>
 static cudaError_t dispatch_np(bool km, int epi, const CUtensorMap &mx, const CUtensorMap &me, const TcArgs &a,
                                int grid, int smem, cudaStream_t s)
 {
-    if (km) return epi ? launch_tc<NP, true, 1>(mx, me, a, grid, smem, s) : launch_tc<NP, true, 0>(mx, me, a, grid, smem, s);
-    return epi ? launch_tc<NP, false, 1>(mx, me, a, grid, smem, s) : launch_tc<NP, false, 0>(mx, me, a, grid, smem, s);
+    if (km)
+        return epi ? launch_tc<NP, true, 1, FX>(mx, me, a, grid, smem, s)
+                   : launch_tc<NP, true, 0, FX>(mx, me, a, grid, smem, s);
+    return epi ? launch_tc<NP, false, 1, FX>(mx, me, a, grid, smem, s)
+               : launch_tc<NP, false, 0, FX>(mx, me, a, grid, smem, s);
 }
 
 cudaError_t tc_mode_product(const TcState &si, const TcState &so, int mu, const TcMatrix &M, mm_prec prec,
-                            const void *in_pieces, void *out_pieces, const TcEpilogue &epi, int *d_err,
-                            cudaStream_t s)
+                            const void *in_pieces, void *out_pieces, const TcEpilogue &epi, const TcScales &sc,
+                            int *d_err, cudaStream_t s)
 {
     const int NP = tc_pieces(prec);
-    if (NP == 0 || NP != M.npieces) return cudaErrorInvalidValue;
+    const bool fx = tc_fixed(prec);
+    if (NP == 0 || NP != M.npieces || fx != M.fixed) return cudaErrorInvalidValue;
+    if (fx && (!sc.s_in || !sc.s_out || !sc.max_prev || !sc.max_cur || !M.rho)) return cudaErrorInvalidValue;
     TcArgs a{};
     a.left = 1;
     a.right = 1;
@@ -508,8 +706,10 @@ cudaError_t tc_mode_product(const TcState &si, const TcState &so, int mu, const 
     a.tx_bytes = a.e_offset + NP * 3 * M.it * 32;
     a.stage_bytes = (a.tx_bytes + 1023) / 1024 * 1024;
     a.tb = float(epi.tb);
-    a.out = (__nv_bfloat16 *)out_pieces;
+    a.out = (uint16_t *)out_pieces;
     a.err = d_err;
+    a.rho = M.rho;
+    a.sc = sc;
     const bool km = a.left == 1;
 
     CUtensorMap mx, me;
@@ -538,10 +738,11 @@ cudaError_t tc_mode_product(const TcState &si, const TcState &so, int mu, const 
     const int64_t grid = tiles * a.ni;
     if (grid > 0x7fffffff) return cudaErrorInvalidConfiguration;
     const int smem = kStages * a.stage_bytes + 1024 + 256;
+    if (fx) return dispatch_np<3, true>(km, epi.kind, mx, me, a, int(grid), smem, s);
     switch (NP) {
-    case 3: return dispatch_np<3>(km, epi.kind, mx, me, a, int(grid), smem, s);
-    case 2: return dispatch_np<2>(km, epi.kind, mx, me, a, int(grid), smem, s);
-    default: return dispatch_np<1>(km, epi.kind, mx, me, a, int(grid), smem, s);
+    case 3: return dispatch_np<3, false>(km, epi.kind, mx, me, a, int(grid), smem, s);
+    case 2: return dispatch_np<2, false>(km, epi.kind, mx, me, a, int(grid), smem, s);
+    default: return dispatch_np<1, false>(km, epi.kind, mx, me, a, int(grid), smem, s);
     }
 }
 

@@ -19,9 +19,9 @@ _HERE = os.path.dirname(os.path.abspath(__file__))
 LIB_PATH = os.path.join(_HERE, "libmumode.so")
 
 MM_R64, MM_C64, MM_C128, MM_R32 = 0, 1, 2, 3
-PREC = {"fp64": 0, "fp32": 1, "bf16x6": 2, "bf16x3": 3, "bf16": 4}
+PREC = {"fp64": 0, "fp32": 1, "bf16x6": 2, "bf16x3": 3, "bf16": 4, "f16x6": 5}
 STATUS = {0: "MM_OK", 1: "MM_ERR_INVALID_ARG", 2: "MM_ERR_SHAPE", 3: "MM_ERR_DTYPE", 4: "MM_ERR_ALIGN",
-          5: "MM_ERR_OOM", 6: "MM_ERR_CUDA", 7: "MM_ERR_TIMEOUT", 8: "MM_ERR_UNSUPPORTED"}
+          5: "MM_ERR_OOM", 6: "MM_ERR_CUDA", 7: "MM_ERR_TIMEOUT", 8: "MM_ERR_UNSUPPORTED", 9: "MM_ERR_RANGE"}
 
 # Every symbol include/mumode.h declares, with its ctypes signature.
 _vp, _i, _i64, _d = ctypes.c_void_p, ctypes.c_int, ctypes.c_int64, ctypes.c_double
@@ -191,7 +191,7 @@ def hermite_matrices(m: int):
 
 # ------------------------------------------------------------- mu-mode product
 
-def mumode_product(ctx: Context, u, mu: int, L, prec: str = "bf16x6", out=None, stream=None):
+def mumode_product(ctx: Context, u, mu: int, L, prec: str = "f16x6", out=None, stream=None):
     """S = U x_mu L (Definition 2.1) on a CUDA tensor u."""
     import torch
 
@@ -213,7 +213,7 @@ def mumode_product(ctx: Context, u, mu: int, L, prec: str = "bf16x6", out=None, 
 class TuckerPlan:
     """U <- U x_1 E_1 ... x_d E_d repeated (eq. (dd-tensor))."""
 
-    def __init__(self, ctx: Context, dims, Es, prec: str = "bf16x6", dtype=None, order=None):
+    def __init__(self, ctx: Context, dims, Es, prec: str = "f16x6", dtype=None, order=None):
         import torch
 
         self.ctx = ctx
@@ -267,7 +267,7 @@ class TuckerPlan:
 class HermitePlan:
     """Hermite spectral transforms and the HKP / GPE steps (sections 3, 4.3, 4.5)."""
 
-    def __init__(self, ctx: Context, dims, prec: str = "bf16x6", dtype=None):
+    def __init__(self, ctx: Context, dims, prec: str = "f16x6", dtype=None):
         import torch
 
         self.ctx = ctx

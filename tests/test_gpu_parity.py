@@ -3,8 +3,10 @@
 Tolerances (relative L2 over all compared points):
   FP64 SIMT                      1e-12
   FP32 SIMT                      2e-5 per run of a few steps
-  BF16x6 (3 pieces, 6 products)  3e-7 per mode product, 1e-6 after the
-                                 50-step n=256 run (the target accuracy)
+  F16x6 (fixed-point leading     1.5e-7 per mode product, 1e-6 after the
+  piece, 6 products)             50-step n=256 run (the target accuracy)
+  BF16x6 (floating pieces)       3e-7 per mode product; its truncation bias
+                                 grows linearly, so it fails the 50-step bound
   BF16x3                         2e-4 per run
   BF16 (1 piece)                 3e-2 per run (reported only)
 """
@@ -15,7 +17,8 @@ from paper_2103_01691_b300 import inputs
 
 pytestmark = pytest.mark.gpu
 
-TOL_STEP = {"fp64": 1e-12, "fp32": 2e-5, "bf16x6": 1e-6, "bf16x3": 2e-4, "bf16": 3e-2}
+TOL_STEP = {"fp64": 1e-12, "fp32": 2e-5, "f16x6": 1e-6, "bf16x6": 1e-6, "bf16x3": 2e-4, "bf16": 3e-2}
+TOL_MODE = {"f16x6": 1.5e-7, "bf16x6": 3e-7}
 
 
 @pytest.fixture(scope="module")
@@ -96,7 +99,7 @@ TC_DIMS = [(16, 16, 16), (32, 48, 16), (17, 33, 20), (64, 64, 64), (100, 37, 48)
 
 
 @pytest.mark.parametrize("dims", TC_DIMS)
-@pytest.mark.parametrize("prec", ["bf16x6", "bf16x3", "bf16"])
+@pytest.mark.parametrize("prec", ["f16x6", "bf16x6", "bf16x3", "bf16"])
 def test_tc_tucker_steps(env, orc, dims, prec):
     mm, ctx, torch = env
     tau, steps = 1e-4, 2
@@ -108,11 +111,12 @@ def test_tc_tucker_steps(env, orc, dims, prec):
     ref = orc.tucker(u0.astype(complex), [orc.expm_dirichlet_fd(n, 1j * tau) for n in dims], nsteps=steps)
     err = rel(u.cpu().numpy(), ref)
     print(f"{prec} dims={dims} steps={steps} rel_err={err:.3e}")
-    tol = {"bf16x6": 3e-7 * steps * len(dims), "bf16x3": TOL_STEP["bf16x3"], "bf16": TOL_STEP["bf16"]}[prec]
+    tol = {"f16x6": TOL_MODE["f16x6"] * steps * len(dims), "bf16x6": TOL_MODE["bf16x6"] * steps * len(dims),
+           "bf16x3": TOL_STEP["bf16x3"], "bf16": TOL_STEP["bf16"]}[prec]
     assert err <= tol
 
 
-@pytest.mark.parametrize("prec", ["bf16x6", "fp64", "fp32"])
+@pytest.mark.parametrize("prec", ["f16x6", "bf16x6", "fp64", "fp32"])
 @pytest.mark.parametrize("dims", [(40, 24, 18), (17, 64, 9)])
 def test_mumode_product_rectangular(env, orc, prec, dims):
     """Definition 2.1 with a rectangular complex (and a real) L."""
@@ -120,7 +124,7 @@ def test_mumode_product_rectangular(env, orc, prec, dims):
     rng = np.random.default_rng(12)
     u0 = inputs.complex_normal(dims[::-1], seed=3)
     dt = torch.complex128 if prec == "fp64" else torch.complex64
-    tol = {"fp64": 1e-13, "fp32": 1e-5, "bf16x6": 3e-7}[prec]
+    tol = {"fp64": 1e-13, "fp32": 1e-5, "bf16x6": 3e-7, "f16x6": 1.5e-7}[prec]
     for mu in range(1, 4):
         for m in (dims[mu - 1] + 8, max(1, dims[mu - 1] - 5)):
             for cplx in (True, False):
@@ -141,15 +145,15 @@ def test_mode_order_independence_tc(env, orc):
     u0 = inputs.complex_normal(dims[::-1], seed=2).astype(np.complex64)
     ref = orc.tucker(u0.astype(complex), [orc.expm_dirichlet_fd(n, 1j * tau) for n in dims], nsteps=2)
     for order in [(1, 2, 3), (3, 2, 1), (2, 3, 1)]:
-        plan = mm.TuckerPlan(ctx, dims, Es, prec="bf16x6", order=order)
+        plan = mm.TuckerPlan(ctx, dims, Es, prec="f16x6", order=order)
         u = to_gpu(torch, u0, torch.complex64)
         plan.step(u, 2)
-        assert rel(u.cpu().numpy(), ref) <= 3e-7 * 6
+        assert rel(u.cpu().numpy(), ref) <= TOL_MODE["f16x6"] * 6
 
 
 # ------------------------------------------------------------------ Hermite / GPE
 
-@pytest.mark.parametrize("prec", ["bf16x6", "fp64"])
+@pytest.mark.parametrize("prec", ["f16x6", "bf16x6", "fp64"])
 def test_hermite_transforms(env, orc, prec):
     mm, ctx, torch = env
     m = 32
@@ -161,14 +165,14 @@ def test_hermite_transforms(env, orc, prec):
     vin = v if prec == "fp64" else v.astype(np.complex64)
     c = plan.forward(to_gpu(torch, vin, dt))
     ref_c = orc.hermite_forward(vin.astype(complex), xo, Wo)
-    tol = 1e-12 if prec == "fp64" else 1e-6
+    tol = {"fp64": 1e-12, "f16x6": 5e-7, "bf16x6": 1e-6}[prec]
     assert rel(c.cpu().numpy(), ref_c) <= tol
     back = plan.backward(c)
     ref_b = orc.hermite_backward(c.cpu().numpy().astype(complex), xo, Wo)
     assert rel(back.cpu().numpy(), ref_b) <= tol
 
 
-@pytest.mark.parametrize("prec", ["bf16x6", "fp64"])
+@pytest.mark.parametrize("prec", ["f16x6", "fp64"])
 def test_harmonic_oscillator_steps(env, orc, prec):
     mm, ctx, torch = env
     m, tau, steps = 24, 0.01, 20
@@ -181,11 +185,13 @@ def test_harmonic_oscillator_steps(env, orc, prec):
     plan.ho_step(psi, tau, steps)
     ref = orc.ho_steps(pin.astype(complex), xo, Wo, tau, steps)
     w3 = orc.weight3(Wo)
-    tol = 1e-12 if prec == "fp64" else 2e-6
-    assert orc.rel_l2(psi.cpu().numpy(), ref, w3) <= tol
+    tol = 1e-12 if prec == "fp64" else 1e-6
+    err = orc.rel_l2(psi.cpu().numpy(), ref, w3)
+    print(f"HO {prec} m={m} steps={steps} rel_err={err:.3e}")
+    assert err <= tol
 
 
-@pytest.mark.parametrize("prec", ["bf16x6", "fp64"])
+@pytest.mark.parametrize("prec", ["f16x6", "fp64"])
 def test_gpe_strang_steps(env, orc, prec):
     mm, ctx, torch = env
     m, beta, tau, steps = 16, 100.0, 1e-3, 20
@@ -198,23 +204,25 @@ def test_gpe_strang_steps(env, orc, prec):
     plan.gpe_step(psi, beta, tau, steps)
     ref = orc.gpe_steps(pin.astype(complex), xo, Wo, beta, tau, steps)
     w3 = orc.weight3(Wo)
-    tol = 1e-11 if prec == "fp64" else 5e-6
-    assert orc.rel_l2(psi.cpu().numpy(), ref, w3) <= tol
+    tol = 1e-11 if prec == "fp64" else 1e-6
+    err = orc.rel_l2(psi.cpu().numpy(), ref, w3)
+    print(f"GPE {prec} m={m} steps={steps} rel_err={err:.3e}")
+    assert err <= tol
     n0 = plan.norm2(to_gpu(torch, pin, dt))
     n1 = plan.norm2(psi)
-    assert abs(n1 / n0 - 1) <= (1e-12 if prec == "fp64" else 2e-6)
+    assert abs(n1 / n0 - 1) <= (1e-12 if prec == "fp64" else 1e-6)
 
 
 # ------------------------------------------------- full size, sampled (n = 256)
 
 def test_free_schrodinger_n256_50_steps_sampled(env, orc):
     """The precision-sweep workload at full size: n = 256, tau = 1e-4, 50
-    steps of BF16x6.  The oracle evaluates sampled entries of the exact
+    steps of F16x6.  The oracle evaluates sampled entries of the exact
     50-step result U0 x_mu E(50 tau) (E(tau)^50 = E(50 tau))."""
     mm, ctx, torch = env
     n, tau, steps = 256, 1e-4, 50
     E = fd_schrodinger_E(mm, n, tau)
-    plan = mm.TuckerPlan(ctx, [n] * 3, [E] * 3, prec="bf16x6")
+    plan = mm.TuckerPlan(ctx, [n] * 3, [E] * 3, prec="f16x6")
     u0 = inputs.free_schrodinger_u0(n, seed=2).astype(np.complex64)
     u = to_gpu(torch, u0, torch.complex64)
     nrm0 = plan.norm2(u)
@@ -228,9 +236,26 @@ def test_free_schrodinger_n256_50_steps_sampled(env, orc):
     E50 = orc.expm_dirichlet_fd(n, 1j * tau * steps)
     ref = orc.tucker3_entries(u0.astype(complex), E50, E50, E50, idx)
     err = rel(got[idx[:, 2], idx[:, 1], idx[:, 0]], ref)
-    print(f"n=256 50 steps bf16x6 sampled rel_err={err:.3e} norm drift={abs(nrm1 / nrm0 - 1):.3e}")
+    print(f"n=256 50 steps f16x6 sampled rel_err={err:.3e} norm drift={abs(nrm1 / nrm0 - 1):.3e}")
     assert err <= 1e-6
     assert abs(nrm1 / nrm0 - 1) <= 1e-6
+
+
+def test_fixed_point_wide_dynamic_range(env, orc):
+    """F16x6 keeps a relative L2 accuracy when magnitudes span 1e-6 .. 1:
+    the fixed-point leading piece is relative to the maximum, the FP16
+    remainders carry the small values."""
+    mm, ctx, torch = env
+    dims, tau = (32, 40, 24), 1e-4
+    Es = [fd_schrodinger_E(mm, n, tau) for n in dims]
+    u0 = inputs.complex_normal(dims[::-1], seed=8)
+    scale = np.exp(np.linspace(np.log(1e-6), 0.0, dims[2]))[:, None, None]
+    u0 = (u0 * scale).astype(np.complex64)
+    plan = mm.TuckerPlan(ctx, dims, Es, prec="f16x6")
+    u = to_gpu(torch, u0, torch.complex64)
+    plan.step(u, 3)
+    ref = orc.tucker(u0.astype(complex), [orc.expm_dirichlet_fd(n, 1j * tau) for n in dims], nsteps=3)
+    assert rel(u.cpu().numpy(), ref) <= TOL_MODE["f16x6"] * 9
 
 
 def test_device_status_clean(env):
