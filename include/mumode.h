@@ -178,6 +178,36 @@ mm_status mumode_product(mm_ctx *ctx, int d, const int64_t *n, int mu, const dou
                          int64_t m, int L_is_complex, mm_dtype dtype, mm_prec prec,
                          const void *u_dev, void *s_dev, void *stream);
 
+/* The paper has no counterpart to this call: it is a service for callers
+ * that cannot allocate device memory.  Examples are code running under a
+ * framework whose caching allocator already owns the GPU's memory (a
+ * cudaMalloc there either fails or fragments the pool), latency-critical
+ * loops that cannot afford cudaMalloc's implicit device synchronisation,
+ * and plugins whose host forbids device allocation.
+ *
+ * mumode_product_noalloc computes what mumode_product computes with
+ * MM_PREC_F16X6 on MM_C64 data, on the current CUDA device, without calling
+ * cudaMalloc, cudaFree or any allocating routine.  The caller passes the
+ * input u_dev and the output s_dev as in mumode_product.  All temporaries
+ * (the split input and output states, the matrix pieces, the scale and
+ * status words) live in one static device array of 64 MiB that every GPU
+ * loading this library reserves until the process exits.  A product fits
+ * when about 12 bytes per padded input point plus 12 per padded output
+ * point plus ~1.2 MB for the matrix stay within 64 MiB (for example
+ * 128^3 points); larger products are rejected with MM_ERR_SHAPE before
+ * anything is enqueued.  n_mu and m must be at most 256.
+ *
+ * Every call uses the same array, and the array keeps the previous call's
+ * contents; the call clears the words that must start at zero itself.
+ * Calls whose work overlaps on the GPU (other threads, other streams) race
+ * on the array: serialise them.  The first call on each device looks up
+ * the array's device address (cudaGetSymbolAddress) with that device
+ * current; make that first call before any stream capture.  The call
+ * synchronises `stream` before returning and reports device-side checks
+ * (MM_ERR_TIMEOUT, MM_ERR_RANGE) in its status. */
+mm_status mumode_product_noalloc(int d, const int64_t *n, int mu, const double *L, int64_t m,
+                                 int L_is_complex, const void *u_dev, void *s_dev, void *stream);
+
 /* ---------------------------------------------------------------------
  * Tucker-operator plan: U <- U x_{o_1} E_{o_1} ... x_{o_d} E_{o_d}
  * (section 2, eq. (dd-tensor)), repeated nsteps times (a marching scheme

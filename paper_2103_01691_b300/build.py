@@ -10,7 +10,7 @@ HERE = os.path.dirname(os.path.abspath(__file__))
 ROOT = os.path.dirname(HERE)
 CSRC = os.path.join(HERE, "csrc")
 LIB = os.path.join(HERE, "libmumode.so")
-SOURCES = ["mumode_api.cu", "simt_kernels.cu", "tc_kernels.cu", "host_setup.cpp"]
+SOURCES = ["mumode_api.cu", "simt_kernels.cu", "tc_kernels.cu", "noalloc.cu", "host_setup.cpp"]
 HEADERS = ["internal.h", "tc_ptx.cuh"]
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 

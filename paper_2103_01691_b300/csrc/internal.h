@@ -5,6 +5,7 @@
 
 #include <complex>
 #include <cstdint>
+#include <vector>
 
 #include "mumode.h"
 
@@ -71,6 +72,10 @@ bool tc_fixed(mm_prec p);
 // Build the pieces of an m x n complex matrix (interleaved FP64, row-major).
 mm_status tc_matrix_create(const double *E, int64_t m, int64_t n, int npieces, bool fixed, TcMatrix *out);
 void tc_matrix_destroy(TcMatrix *M);
+// Host half of tc_matrix_create: geometry (pieces/rho left null) and the
+// host images of the pieces and row scales.
+mm_status tc_matrix_host(const double *E, int64_t m, int64_t n, int npieces, bool fixed, TcMatrix *geom,
+                         std::vector<uint16_t> &pieces, std::vector<float> &rho);
 // Split an interleaved complex64 tensor into padded piece planes.  For the
 // fixed-point mode the scale comes from the tensor's maximum: `work` (one
 // unsigned, device) receives it, `scale_out` the chosen scale, and

@@ -121,7 +121,8 @@ static uint16_t f16_bits(double exact)
     return uint16_t(sign | uint16_t((e + 15) << 10) | mant);
 }
 
-mm_status tc_matrix_create(const double *E, int64_t m, int64_t n, int npieces, bool fixed, TcMatrix *out)
+mm_status tc_matrix_host(const double *E, int64_t m, int64_t n, int npieces, bool fixed, TcMatrix *geom,
+                         std::vector<uint16_t> &h, std::vector<float> &rho)
 {
     TcMatrix M;
     M.n_in = n;
@@ -133,8 +134,8 @@ mm_status tc_matrix_create(const double *E, int64_t m, int64_t n, int npieces, b
     M.npieces = npieces;
     M.fixed = fixed;
     const int64_t rows = int64_t(npieces) * M.ni * 3 * M.it;
-    std::vector<uint16_t> h(size_t(rows * M.k_pad), 0);
-    std::vector<float> rho(size_t(M.ni) * M.it, 1.0f);
+    h.assign(size_t(rows * M.k_pad), 0);
+    rho.assign(size_t(M.ni) * M.it, 1.0f);
     for (int64_t i = 0; i < m; ++i) {
         double sum_abs = 0.0, sum_mod = 0.0;
         for (int64_t j = 0; j < n; ++j) {
@@ -170,6 +171,17 @@ mm_status tc_matrix_create(const double *E, int64_t m, int64_t n, int npieces, b
             }
         }
     }
+    *geom = M;
+    return MM_OK;
+}
+
+mm_status tc_matrix_create(const double *E, int64_t m, int64_t n, int npieces, bool fixed, TcMatrix *out)
+{
+    TcMatrix M;
+    std::vector<uint16_t> h;
+    std::vector<float> rho;
+    mm_status st = tc_matrix_host(E, m, n, npieces, fixed, &M, h, rho);
+    if (st) return st;
     if (cudaMalloc(&M.pieces, h.size() * 2) != cudaSuccess)
         return fail(MM_ERR_OOM, "cudaMalloc of %zu bytes for matrix pieces failed", h.size() * 2);
     if (cudaMemcpy(M.pieces, h.data(), h.size() * 2, cudaMemcpyHostToDevice) != cudaSuccess) {

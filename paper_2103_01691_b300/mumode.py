@@ -40,6 +40,7 @@ SIGNATURES = {
     "mm_gauss_hermite": (_i, [_i, _dp, _dp]),
     "mm_hermite_matrices": (_i, [_i, _dp, _dp]),
     "mumode_product": (_i, [_vp, _i, _i64p, _i, _dp, _i64, _i, _i, _i, _vp, _vp, _vp]),
+    "mumode_product_noalloc": (_i, [_i, _i64p, _i, _dp, _i64, _i, _vp, _vp, _vp]),
     "mumode_plan_create": (_i, [_vp, _i, _i64p, ctypes.POINTER(_dp), _i, _i, _i, ctypes.POINTER(_i),
                                 ctypes.POINTER(_vp)]),
     "mumode_step": (_i, [_vp, _vp, _i64, _vp]),
@@ -207,6 +208,29 @@ def mumode_product(ctx: Context, u, mu: int, L, prec: str = "f16x6", out=None, s
     _check(lib().mumode_product(ctx.handle, d, dims.ctypes.data_as(_i64p), mu, _dptr(Lf), m, Lc,
                                 _dtype_code(u), PREC[prec], ctypes.c_void_p(u.data_ptr()),
                                 ctypes.c_void_p(out.data_ptr()), _stream(stream)))
+    return out
+
+
+def mumode_product_noalloc(u, mu: int, L, out=None, stream=None):
+    """S = U x_mu L with MM_PREC_F16X6, using only the library's static
+    device scratch (no device allocation inside the call; `out` may be
+    passed preallocated).  See mumode_product_noalloc in include/mumode.h."""
+    import torch
+
+    _need_cuda(u)
+    if u.dtype != torch.complex64:
+        raise TypeError("mumode_product_noalloc takes complex64 data")
+    Lf, Lc = _complex_interleaved(L)
+    m = int(np.asarray(L).shape[0])
+    dims = _dims(u.shape)
+    d = len(dims)
+    out_shape = list(u.shape)
+    out_shape[d - mu] = m
+    if out is None:
+        out = torch.empty(out_shape, dtype=u.dtype, device=u.device)
+    _check(lib().mumode_product_noalloc(d, dims.ctypes.data_as(_i64p), mu, _dptr(Lf), m, Lc,
+                                        ctypes.c_void_p(u.data_ptr()), ctypes.c_void_p(out.data_ptr()),
+                                        _stream(stream)))
     return out
 
 
