@@ -248,6 +248,18 @@ __device__ __forceinline__ void split_fx(float x, int es, uint16_t &b0, uint16_t
     b2 = __half_as_ushort(h2);
 }
 
+// The same split for a value already divided by the grid spacing.
+__device__ __forceinline__ void split_fx_scaled(float xs, uint16_t &b0, uint16_t &b1, uint16_t &b2)
+{
+    const __half h0 = __float2half_rn(rintf(xs));
+    const float r = xs - __half2float(h0);
+    const __half h1 = __float2half_rn(r);
+    const __half h2 = __float2half_rn(r - __half2float(h1));
+    b0 = __half_as_ushort(h0);
+    b1 = __half_as_ushort(h1);
+    b2 = __half_as_ushort(h2);
+}
+
 // Grid exponent for a tensor whose largest magnitude is m: s = 2^es with m / s < 1024.
 __device__ __forceinline__ int grid_exponent(float m)
 {
@@ -408,6 +420,7 @@ struct TcArgs {
     int64_t mp;             // padded output length
     int64_t aps;            // 64-point atoms per slab (MN-major)
     int64_t plane_out;      // elements per output plane
+    int64_t items;          // work items = point tiles x row tiles
     int it, ni, kblocks;
     int stage_bytes, tx_bytes, e_offset;
     float tb;               // tau * beta for the nonlinear epilogue
@@ -423,8 +436,18 @@ __host__ __device__ constexpr int num_terms(int NP) { return NP == 3 ? 6 : (NP =
 __host__ __device__ constexpr int term_a(int t) { return t == 2 ? 1 : (t == 4 ? 1 : (t == 5 ? 2 : 0)); }
 __host__ __device__ constexpr int term_b(int t) { return t == 1 ? 1 : (t == 3 ? 2 : (t == 4 ? 1 : 0)); }
 
+constexpr int kEpiWarps = 16;      // four per TMEM lane quarter
+constexpr int kThreads = 32 * (2 + kEpiWarps);  // warp 0 TMA, warp 1 TMEM + MMA, then the epilogue warps
+constexpr int kChunksPerWarp = 2;  // 16-row chunks each epilogue warp drains (IT <= 128)
+
+// Persistent kernel: CTA b processes work items b, b + gridDim.x, ...;
+// item T is (point tile T / ni, row tile T % ni), so neighbouring CTAs share
+// the data tile through L2.  The TMA warp runs ahead across item
+// boundaries; the epilogue warps copy the two accumulators into registers,
+// release tensor memory to the MMA warp at once, and then scale, split and
+// store while the next item's MMAs run.
 template <int NP, bool KMAJOR, int EPI, bool FX>
-__global__ void __launch_bounds__(256, 1)
+__global__ void __launch_bounds__(kThreads, 1)
     tc_mode_kernel(const __grid_constant__ CUtensorMap mapX, const __grid_constant__ CUtensorMap mapE, TcArgs a)
 {
     extern __shared__ __align__(1024) uint8_t smem_raw[];
@@ -432,10 +455,11 @@ __global__ void __launch_bounds__(256, 1)
     uint64_t *full = reinterpret_cast<uint64_t *>(smem + kStages * a.stage_bytes);
     uint64_t *empty = full + kStages;
     uint64_t *accf = empty + kStages;
-    uint32_t *tmem_slot = reinterpret_cast<uint32_t *>(accf + 1);
+    uint64_t *tmem_empty = accf + 1;
+    uint32_t *tmem_slot = reinterpret_cast<uint32_t *>(tmem_empty + 1);
+    volatile int *abort_flag = reinterpret_cast<volatile int *>(tmem_slot + 1);
 
     const int warp = threadIdx.x / 32, lane = threadIdx.x % 32;
-    const int tile = blockIdx.x / a.ni, h = blockIdx.x % a.ni;
     const int acc_cols = 2 * a.it;
     const int need = NP > 1 ? 2 * acc_cols : acc_cols;
     const uint32_t ncols = need <= 32 ? 32 : (need <= 64 ? 64 : (need <= 128 ? 128 : (need <= 256 ? 256 : 512)));
@@ -446,6 +470,8 @@ __global__ void __launch_bounds__(256, 1)
             mbar_init(&empty[s], 1);
         }
         mbar_init(accf, 1);
+        mbar_init(tmem_empty, kEpiWarps);
+        *abort_flag = 0;
         mbar_fence_init();
         tma_prefetch_desc(&mapX);
         tma_prefetch_desc(&mapE);
@@ -458,177 +484,244 @@ __global__ void __launch_bounds__(256, 1)
     __syncthreads();
     tc_fence_after();
     const uint32_t tmem = *tmem_slot;
-    bool ok = true;
 
-    if (warp == 0 && lane == 0) {
-        // ---------------- TMA producer ----------------
-        for (int kb = 0; kb < a.kblocks && ok; ++kb) {
-            const int s = kb % kStages;
-            const uint32_t ph = uint32_t(kb / kStages) & 1u;
-            ok = mbar_wait(&empty[s], ph ^ 1u, a.err, MM_ERR_TIMEOUT);
-            if (!ok) break;
-            uint8_t *st = smem + s * a.stage_bytes;
-            mbar_arrive_expect_tx(&full[s], uint32_t(a.tx_bytes));
-            for (int c = 0; c < 2; ++c)
-                for (int p = 0; p < NP; ++p) {
-                    uint8_t *dst = st + (c * NP + p) * kDataTileBytes;
-                    if (KMAJOR) {
-                        tma_load_3d(&mapX, &full[s], dst, kb * kBK, tile * kTileM, c * NP + p);
+    if (warp == 0) {
+        if (lane == 0) {
+            // ---------------- TMA producer ----------------
+            uint32_t gk = 0;  // k-blocks issued by this CTA over all items
+            for (int64_t T = blockIdx.x; T < a.items && !*abort_flag; T += gridDim.x) {
+                const int64_t tile = T / a.ni;
+                const int h = int(T % a.ni);
+                // TMA coordinates of this item's two 64-point atoms (MN-major), fixed over k
+                int ac_l[2] = {0, 0}, ac_r[2] = {0, 0};
+                if (!KMAJOR) {
+                    for (int q = 0; q < 2; ++q) {
+                        const int64_t atom = 2 * tile + q;
+                        int64_t r = atom / a.aps;
+                        if (r > a.right) r = a.right;  // past the end: zero fill
+                        ac_r[q] = int(r);
+                        ac_l[q] = int((atom % a.aps) * 64);
+                    }
+                }
+                const int e_row0 = (h * 3) * a.it;
+                const int e_pstride = a.ni * 3 * a.it;
+                const int k_row = int(tile * kTileM);
+                for (int kb = 0; kb < a.kblocks; ++kb, ++gk) {
+                    const int s = int(gk % kStages);
+                    const uint32_t ph = (gk / kStages) & 1u;
+                    if (!mbar_wait(&empty[s], ph ^ 1u, a.err, MM_ERR_TIMEOUT)) {
+                        *abort_flag = 1;
+                        break;
+                    }
+                    uint8_t *st = smem + s * a.stage_bytes;
+                    mbar_arrive_expect_tx(&full[s], uint32_t(a.tx_bytes));
+                    for (int c = 0; c < 2; ++c)
+                        for (int p = 0; p < NP; ++p) {
+                            uint8_t *dst = st + (c * NP + p) * kDataTileBytes;
+                            if (KMAJOR) {
+                                tma_load_3d(&mapX, &full[s], dst, kb * kBK, k_row, c * NP + p);
+                            } else {
+                                tma_load_4d(&mapX, &full[s], dst, ac_l[0], kb * kBK, ac_r[0], c * NP + p);
+                                tma_load_4d(&mapX, &full[s], dst + 2048, ac_l[1], kb * kBK, ac_r[1], c * NP + p);
+                            }
+                        }
+                    uint8_t *est = st + a.e_offset;
+                    for (int p = 0; p < NP; ++p)
+                        for (int w = 0; w < 3; ++w)
+                            tma_load_2d(&mapE, &full[s], est + (p * 3 + w) * a.it * 32, kb * kBK,
+                                        p * e_pstride + e_row0 + w * a.it);
+                }
+            }
+        }
+    } else if (warp == 1) {
+        if (lane == 0) {
+            // ---------------- MMA issuer ----------------
+            const uint32_t idesc = FX ? idesc_f16_f32(kTileM, 2 * a.it, !KMAJOR, false)
+                                      : idesc_bf16_f32(kTileM, 2 * a.it, !KMAJOR, false);
+            uint32_t gk = 0, lt = 0;
+            for (int64_t T = blockIdx.x; T < a.items && !*abort_flag; T += gridDim.x, ++lt) {
+                if (lt > 0 && !mbar_wait(tmem_empty, (lt - 1) & 1u, a.err, MM_ERR_TIMEOUT)) {
+                    *abort_flag = 1;
+                    break;
+                }
+                tc_fence_after();
+                bool started[2] = {false, false};
+                for (int kb = 0; kb < a.kblocks; ++kb, ++gk) {
+                    const int s = int(gk % kStages);
+                    const uint32_t ph = (gk / kStages) & 1u;
+                    if (!mbar_wait(&full[s], ph, a.err, MM_ERR_TIMEOUT)) {
+                        *abort_flag = 1;
+                        break;
+                    }
+                    tc_fence_after();
+                    const uint32_t st = smem_u32(smem + s * a.stage_bytes);
+                    const uint32_t est = st + a.e_offset;
+                    for (int c = 0; c < 2; ++c) {
+#pragma unroll
+                        for (int t = 0; t < num_terms(NP); ++t) {
+                            const int pa = term_a(t), pb = term_b(t);
+                            const uint32_t xaddr = st + (c * NP + pb) * kDataTileBytes;
+                            const uint64_t adesc =
+                                KMAJOR ? smem_desc(xaddr, 16, 256, kSwz32) : smem_desc(xaddr, 2048, 1024, kSwz128);
+                            // real plane: window [C; S] (block 1); imaginary plane: [-S; C] (block 0)
+                            const uint32_t eaddr = est + (pa * 3 + (c == 0 ? 1 : 0)) * a.it * 32;
+                            const uint64_t bdesc = smem_desc(eaddr, 16, 256, kSwz32);
+                            const int acc = (NP > 1 && (pa != 0 || pb != 0)) ? 1 : 0;
+                            umma_f16(tmem + uint32_t(acc * acc_cols), adesc, bdesc, idesc, started[acc] ? 1u : 0u);
+                            started[acc] = true;
+                        }
+                    }
+                    umma_commit(&empty[s]);
+                }
+                umma_commit(accf);
+            }
+        }
+    } else {
+        // ---------------- epilogue warps ----------------
+        const int ew = warp - 2;          // 0 .. kEpiWarps - 1
+        const int quarter = warp % 4;     // TMEM lanes 32 quarter .. + 31
+        const int grp = ew / 4;           // chunks of 16 rows: grp, grp + 4, ...
+        const int row = quarter * 32 + lane;
+        const uint32_t tbase = tmem + (uint32_t(quarter * 32) << 16);
+        const int nchunks = a.it / 16;
+        float s_in = 1.0f, inv_out = 1.0f, lim = 0.0f;
+        int es_out = 0;
+        if (FX) {
+            s_in = *a.sc.s_in;
+            es_out = grid_exponent(__uint_as_float(*a.sc.max_prev));
+            inv_out = ldexpf(1.0f, -es_out);
+            lim = ldexpf(16384.0f, es_out);
+            if (blockIdx.x == 0 && ew == 0 && lane == 0) *a.sc.s_out = ldexpf(1.0f, es_out);
+        }
+        float local_max = 0.0f;
+        bool range_ok = true;
+        uint32_t lt = 0;
+        for (int64_t T = blockIdx.x; T < a.items; T += gridDim.x, ++lt) {
+            const int64_t tile = T / a.ni;
+            const int h = int(T % a.ni);
+            const bool acc_ready = !*abort_flag && mbar_wait(accf, lt & 1u, a.err, MM_ERR_TIMEOUT);
+            if (!acc_ready) *abort_flag = 1;
+            tc_fence_after();
+            // drain: up to kChunksPerWarp chunks of 16 rows, real and imaginary, both accumulators summed
+            float v[kChunksPerWarp][32];
+#pragma unroll
+            for (int q = 0; q < kChunksPerWarp; ++q) {
+                const int ch = grp + 4 * q;
+                if (ch < nchunks) {
+                    float t0[16], t1[16];
+                    tmem_ld16(tbase + uint32_t(ch * 16), t0);
+                    if (NP > 1) tmem_ld16(tbase + uint32_t(acc_cols + ch * 16), t1);
+                    tmem_ld_wait();
+#pragma unroll
+                    for (int k = 0; k < 16; ++k) v[q][k] = NP > 1 ? t0[k] + t1[k] : t0[k];
+                    tmem_ld16(tbase + uint32_t(a.it + ch * 16), t0);
+                    if (NP > 1) tmem_ld16(tbase + uint32_t(acc_cols + a.it + ch * 16), t1);
+                    tmem_ld_wait();
+#pragma unroll
+                    for (int k = 0; k < 16; ++k) v[q][16 + k] = NP > 1 ? t0[k] + t1[k] : t0[k];
+                }
+            }
+            tc_fence_before();
+            __syncwarp();
+            if (lane == 0) mbarrier_arrive(tmem_empty);
+            if (!acc_ready) break;
+            // this thread's point
+            bool valid;
+            int64_t r, l = 0;
+            if (KMAJOR) {
+                r = tile * kTileM + row;
+                valid = r < a.right;
+            } else {
+                const int64_t atom = 2 * tile + row / 64;
+                r = atom / a.aps;
+                l = (atom % a.aps) * 64 + row % 64;
+                valid = r < a.right && l < a.left;
+            }
+#pragma unroll
+            for (int q = 0; q < kChunksPerWarp; ++q) {
+                const int ch = grp + 4 * q;
+                if (ch >= nchunks || !valid) continue;
+                const int64_t i0 = int64_t(h) * a.it + ch * 16;
+                if (i0 >= a.mp) continue;
+                // value k of this chunk -> its 2 NP pieces (re pieces, im pieces)
+                auto pieces_of = [&](int k, uint16_t *br, uint16_t *bi) {
+                    float xr = v[q][k], xi = v[q][16 + k];
+                    if (FX) {
+                        const float g = __ldg(a.rho + i0 + k) * s_in;  // power of two: exact
+                        xr *= g;
+                        xi *= g;
+                    }
+                    if (EPI == 1) {
+                        const float th = a.tb * (xr * xr + xi * xi);
+                        float sn, cs;
+                        sincosf(th, &sn, &cs);
+                        const float yr = xr * cs + xi * sn, yi = xi * cs - xr * sn;
+                        xr = yr;
+                        xi = yi;
+                    }
+                    if (FX) {
+                        const float ar = fabsf(xr), ai = fabsf(xi);
+                        local_max = fmaxf(local_max, fmaxf(ar, ai));
+                        range_ok &= ar < lim && ai < lim;
+                        split_fx_scaled(xr * inv_out, br[0], br[1], br[2]);
+                        split_fx_scaled(xi * inv_out, bi[0], bi[1], bi[2]);
                     } else {
-                        for (int q = 0; q < 2; ++q) {
-                            const int64_t atom = 2 * int64_t(tile) + q;
-                            int64_t r = atom / a.aps;
-                            const int64_t l0 = (atom % a.aps) * 64;
-                            if (r > a.right) r = a.right;  // past the end: zero fill
-                            tma_load_4d(&mapX, &full[s], dst + q * 2048, int(l0), kb * kBK, int(r), c * NP + p);
+                        float rr = xr, ri = xi;
+#pragma unroll
+                        for (int p = 0; p < NP; ++p) {
+                            const __nv_bfloat16 hr = __float2bfloat16_rn(rr), hi = __float2bfloat16_rn(ri);
+                            br[p] = __bfloat16_as_ushort(hr);
+                            bi[p] = __bfloat16_as_ushort(hi);
+                            rr -= __bfloat162float(hr);
+                            ri -= __bfloat162float(hi);
+                        }
+                    }
+                };
+                if (KMAJOR) {
+                    // 8 consecutive outputs of one row -> one 16-byte store per (plane, piece)
+                    const int64_t base = r * a.mp + i0;
+#pragma unroll
+                    for (int g8 = 0; g8 < 2; ++g8) {
+                        uint32_t wr[3][4], wi[3][4];
+#pragma unroll
+                        for (int k2 = 0; k2 < 4; ++k2) {
+                            uint16_t r0[3], i0p[3], r1[3], i1p[3];
+                            pieces_of(g8 * 8 + 2 * k2, r0, i0p);
+                            pieces_of(g8 * 8 + 2 * k2 + 1, r1, i1p);
+#pragma unroll
+                            for (int p = 0; p < NP; ++p) {
+                                wr[p][k2] = uint32_t(r0[p]) | (uint32_t(r1[p]) << 16);
+                                wi[p][k2] = uint32_t(i0p[p]) | (uint32_t(i1p[p]) << 16);
+                            }
+                        }
+#pragma unroll
+                        for (int p = 0; p < NP; ++p) {
+                            *reinterpret_cast<uint4 *>(a.out + int64_t(p) * a.plane_out + base + g8 * 8) =
+                                make_uint4(wr[p][0], wr[p][1], wr[p][2], wr[p][3]);
+                            *reinterpret_cast<uint4 *>(a.out + int64_t(NP + p) * a.plane_out + base + g8 * 8) =
+                                make_uint4(wi[p][0], wi[p][1], wi[p][2], wi[p][3]);
+                        }
+                    }
+                } else {
+#pragma unroll
+                    for (int k = 0; k < 16; ++k) {
+                        uint16_t br[3], bi[3];
+                        pieces_of(k, br, bi);
+                        const int64_t off = (r * a.mp + i0 + k) * a.left + l;
+#pragma unroll
+                        for (int p = 0; p < NP; ++p) {
+                            a.out[int64_t(p) * a.plane_out + off] = br[p];
+                            a.out[int64_t(NP + p) * a.plane_out + off] = bi[p];
                         }
                     }
                 }
-            uint8_t *est = st + a.e_offset;
-            for (int p = 0; p < NP; ++p)
-                for (int w = 0; w < 3; ++w)
-                    tma_load_2d(&mapE, &full[s], est + (p * 3 + w) * a.it * 32, kb * kBK,
-                                ((p * a.ni + h) * 3 + w) * a.it);
-        }
-    } else if (warp == 1 && lane == 0) {
-        // ---------------- MMA issuer ----------------
-        const uint32_t idesc = FX ? idesc_f16_f32(kTileM, 2 * a.it, !KMAJOR, false)
-                                  : idesc_bf16_f32(kTileM, 2 * a.it, !KMAJOR, false);
-        bool started[2] = {false, false};
-        for (int kb = 0; kb < a.kblocks && ok; ++kb) {
-            const int s = kb % kStages;
-            const uint32_t ph = uint32_t(kb / kStages) & 1u;
-            ok = mbar_wait(&full[s], ph, a.err, MM_ERR_TIMEOUT);
-            if (!ok) break;
-            tc_fence_after();
-            const uint32_t st = smem_u32(smem + s * a.stage_bytes);
-            const uint32_t est = st + a.e_offset;
-            for (int c = 0; c < 2; ++c) {
-#pragma unroll
-                for (int t = 0; t < num_terms(NP); ++t) {
-                    const int pa = term_a(t), pb = term_b(t);
-                    const uint32_t xaddr = st + (c * NP + pb) * kDataTileBytes;
-                    const uint64_t adesc =
-                        KMAJOR ? smem_desc(xaddr, 16, 256, kSwz32) : smem_desc(xaddr, 2048, 1024, kSwz128);
-                    // real plane: window [C; S] (block 1); imaginary plane: [-S; C] (block 0)
-                    const uint32_t eaddr = est + (pa * 3 + (c == 0 ? 1 : 0)) * a.it * 32;
-                    const uint64_t bdesc = smem_desc(eaddr, 16, 256, kSwz32);
-                    const int acc = (NP > 1 && (pa != 0 || pb != 0)) ? 1 : 0;
-                    umma_f16(tmem + uint32_t(acc * acc_cols), adesc, bdesc, idesc, started[acc] ? 1u : 0u);
-                    started[acc] = true;
-                }
-            }
-            umma_commit(&empty[s]);
-        }
-        umma_commit(accf);
-    }
-    __syncwarp();
-
-    // ---------------- epilogue: all warps ----------------
-    float s_in = 1.0f;
-    int es_out = 0;
-    if (FX) {
-        s_in = *a.sc.s_in;
-        es_out = grid_exponent(__uint_as_float(*a.sc.max_prev));
-        if (blockIdx.x == 0 && threadIdx.x == 0) *a.sc.s_out = ldexpf(1.0f, es_out);
-    }
-    float local_max = 0.0f;
-    bool range_ok = true;
-    bool acc_ready = mbar_wait(accf, 0, a.err, MM_ERR_TIMEOUT);
-    tc_fence_after();
-    const int quarter = warp % 4, half = warp / 4;
-    const int row = quarter * 32 + lane;
-    // point of this thread
-    bool valid;
-    int64_t r, l = 0;
-    if (KMAJOR) {
-        r = int64_t(tile) * kTileM + row;
-        valid = r < a.right;
-    } else {
-        const int64_t atom = 2 * int64_t(tile) + row / 64;
-        r = atom / a.aps;
-        l = (atom % a.aps) * 64 + row % 64;
-        valid = r < a.right && l < a.left;
-    }
-    const uint32_t tbase = tmem + (uint32_t(quarter * 32) << 16);
-    const int nchunks = a.it / 16;
-    for (int ch = half; ch < nchunks; ch += 2) {
-        float re0[16], im0[16], re1[16], im1[16];
-        tmem_ld16(tbase + uint32_t(ch * 16), re0);
-        tmem_ld16(tbase + uint32_t(a.it + ch * 16), im0);
-        if (NP > 1) {
-            tmem_ld16(tbase + uint32_t(acc_cols + ch * 16), re1);
-            tmem_ld16(tbase + uint32_t(acc_cols + a.it + ch * 16), im1);
-        }
-        tmem_ld_wait();
-        if (!acc_ready || !valid) continue;
-        const int64_t i0 = int64_t(h) * a.it + ch * 16;
-        if (i0 >= a.mp) continue;
-        uint16_t pr[3][16], pi[3][16];
-#pragma unroll
-        for (int k = 0; k < 16; ++k) {
-            float xr = re0[k], xi = im0[k];
-            if (NP > 1) {
-                xr += re1[k];
-                xi += im1[k];
-            }
-            if (FX) {
-                const float g = __ldg(a.rho + i0 + k) * s_in;  // power of two: exact
-                xr *= g;
-                xi *= g;
-            }
-            if (EPI == 1) {
-                const float th = a.tb * (xr * xr + xi * xi);
-                float sn, cs;
-                sincosf(th, &sn, &cs);
-                const float yr = xr * cs + xi * sn, yi = xi * cs - xr * sn;
-                xr = yr;
-                xi = yi;
-            }
-            if (FX) {
-                local_max = fmaxf(local_max, fmaxf(fabsf(xr), fabsf(xi)));
-                range_ok &= fabsf(ldexpf(xr, -es_out)) < 16384.f && fabsf(ldexpf(xi, -es_out)) < 16384.f;
-                split_fx(xr, es_out, pr[0][k], pr[1][k], pr[2][k]);
-                split_fx(xi, es_out, pi[0][k], pi[1][k], pi[2][k]);
-            } else {
-                float rr = xr, ri = xi;
-#pragma unroll
-                for (int p = 0; p < NP; ++p) {
-                    const __nv_bfloat16 br = __float2bfloat16_rn(rr), bi = __float2bfloat16_rn(ri);
-                    pr[p][k] = __bfloat16_as_ushort(br);
-                    pi[p][k] = __bfloat16_as_ushort(bi);
-                    rr -= __bfloat162float(br);
-                    ri -= __bfloat162float(bi);
-                }
             }
         }
-        if (KMAJOR) {
-            const int64_t base = r * a.mp + i0;
-#pragma unroll
-            for (int p = 0; p < NP; ++p) {
-                uint4 *dr = reinterpret_cast<uint4 *>(a.out + int64_t(p) * a.plane_out + base);
-                uint4 *di = reinterpret_cast<uint4 *>(a.out + int64_t(NP + p) * a.plane_out + base);
-                dr[0] = *reinterpret_cast<const uint4 *>(&pr[p][0]);
-                dr[1] = *reinterpret_cast<const uint4 *>(&pr[p][8]);
-                di[0] = *reinterpret_cast<const uint4 *>(&pi[p][0]);
-                di[1] = *reinterpret_cast<const uint4 *>(&pi[p][8]);
-            }
-        } else {
-#pragma unroll
-            for (int k = 0; k < 16; ++k) {
-                const int64_t off = (r * a.mp + i0 + k) * a.left + l;
-#pragma unroll
-                for (int p = 0; p < NP; ++p) {
-                    a.out[int64_t(p) * a.plane_out + off] = pr[p][k];
-                    a.out[int64_t(NP + p) * a.plane_out + off] = pi[p][k];
-                }
-            }
+        if (FX) {
+            const unsigned m = __reduce_max_sync(0xffffffffu, __float_as_uint(local_max));
+            if (lane == 0 && m) atomicMax(a.sc.max_cur, m);
+            if (!range_ok && a.err) atomicCAS(a.err, 0, MM_ERR_RANGE);
         }
-    }
-    if (FX) {
-        const unsigned m = __reduce_max_sync(0xffffffffu, __float_as_uint(local_max));
-        if (lane == 0 && m) atomicMax(a.sc.max_cur, m);
-        if (!range_ok && a.err) atomicCAS(a.err, 0, MM_ERR_RANGE);
     }
     tc_fence_before();
     __syncthreads();
@@ -643,6 +736,18 @@ __global__ void __launch_bounds__(256, 1)
 using EncodeTiledFn = CUresult (*)(CUtensorMap *, CUtensorMapDataType, cuuint32_t, void *, const cuuint64_t *,
                                    const cuuint64_t *, const cuuint32_t *, const cuuint32_t *, CUtensorMapInterleave,
                                    CUtensorMapSwizzle, CUtensorMapL2promotion, CUtensorMapFloatOOBfill);
+
+static int num_sms()
+{
+    static int sms = 0;
+    if (!sms) {
+        int dev = 0;
+        cudaGetDevice(&dev);
+        cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+        if (sms <= 0) sms = 148;
+    }
+    return sms;
+}
 
 static EncodeTiledFn encode_fn()
 {
@@ -677,7 +782,7 @@ static cudaError_t launch_tc(const CUtensorMap &mx, const CUtensorMap &me, const
     auto kern = tc_mode_kernel<NP, KM, EPI, FX>;
     cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
     if (e != cudaSuccess) return e;
-    kern<<<grid, 256, smem, s>>>(mx, me, a);
+    kern<<<grid, kThreads, smem, s>>>(mx, me, a);
     count_launch();
     return cudaGetLastError();
 }
@@ -747,8 +852,8 @@ cudaError_t tc_mode_product(const TcState &si, const TcState &so, int mu, const 
     int64_t tiles;
     if (km) tiles = (a.right + kTileM - 1) / kTileM;
     else tiles = (a.right * a.aps + 1) / 2;
-    const int64_t grid = tiles * a.ni;
-    if (grid > 0x7fffffff) return cudaErrorInvalidConfiguration;
+    a.items = tiles * a.ni;
+    const int64_t grid = a.items < num_sms() ? a.items : num_sms();
     const int smem = kStages * a.stage_bytes + 1024 + 256;
     if (fx) return dispatch_np<3, true>(km, epi.kind, mx, me, a, int(grid), smem, s);
     switch (NP) {
