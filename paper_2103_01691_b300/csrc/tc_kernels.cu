@@ -643,8 +643,9 @@ __global__ void __launch_bounds__(kThreads, 1)
                 if (ch >= nchunks || !valid) continue;
                 const int64_t i0 = int64_t(h) * a.it + ch * 16;
                 if (i0 >= a.mp) continue;
-                // value k of this chunk -> its 2 NP pieces (re pieces, im pieces)
-                auto pieces_of = [&](int k, uint16_t *br, uint16_t *bi) {
+                // scale (fixed point), nonlinear phase, range and maximum, in place
+#pragma unroll
+                for (int k = 0; k < 16; ++k) {
                     float xr = v[q][k], xi = v[q][16 + k];
                     if (FX) {
                         const float g = __ldg(a.rho + i0 + k) * s_in;  // power of two: exact
@@ -663,50 +664,48 @@ __global__ void __launch_bounds__(kThreads, 1)
                         const float ar = fabsf(xr), ai = fabsf(xi);
                         local_max = fmaxf(local_max, fmaxf(ar, ai));
                         range_ok &= ar < lim && ai < lim;
-                        split_fx_scaled(xr * inv_out, br[0], br[1], br[2]);
-                        split_fx_scaled(xi * inv_out, bi[0], bi[1], bi[2]);
+                        xr *= inv_out;
+                        xi *= inv_out;
+                    }
+                    v[q][k] = xr;
+                    v[q][16 + k] = xi;
+                }
+                // pieces of one value: fixed point (already divided by the grid) or floating BF16
+                auto pieces_of = [&](float x, uint16_t *b) {
+                    if (FX) {
+                        split_fx_scaled(x, b[0], b[1], b[2]);
                     } else {
-                        float rr = xr, ri = xi;
 #pragma unroll
                         for (int p = 0; p < NP; ++p) {
-                            const __nv_bfloat16 hr = __float2bfloat16_rn(rr), hi = __float2bfloat16_rn(ri);
-                            br[p] = __bfloat16_as_ushort(hr);
-                            bi[p] = __bfloat16_as_ushort(hi);
-                            rr -= __bfloat162float(hr);
-                            ri -= __bfloat162float(hi);
+                            const __nv_bfloat16 h16 = __float2bfloat16_rn(x);
+                            b[p] = __bfloat16_as_ushort(h16);
+                            x -= __bfloat162float(h16);
                         }
                     }
                 };
                 if (KMAJOR) {
-                    // 8 consecutive outputs of one row -> one 16-byte store per (plane, piece)
+                    // 16 consecutive outputs of one row: one 32-byte store per (plane, piece)
                     const int64_t base = r * a.mp + i0;
 #pragma unroll
-                    for (int g8 = 0; g8 < 2; ++g8) {
-                        uint32_t wr[3][4], wi[3][4];
+                    for (int c = 0; c < 2; ++c) {
+                        uint32_t w[3][8];
 #pragma unroll
-                        for (int k2 = 0; k2 < 4; ++k2) {
-                            uint16_t r0[3], i0p[3], r1[3], i1p[3];
-                            pieces_of(g8 * 8 + 2 * k2, r0, i0p);
-                            pieces_of(g8 * 8 + 2 * k2 + 1, r1, i1p);
+                        for (int k2 = 0; k2 < 8; ++k2) {
+                            uint16_t b0[3], b1[3];
+                            pieces_of(v[q][16 * c + 2 * k2], b0);
+                            pieces_of(v[q][16 * c + 2 * k2 + 1], b1);
 #pragma unroll
-                            for (int p = 0; p < NP; ++p) {
-                                wr[p][k2] = uint32_t(r0[p]) | (uint32_t(r1[p]) << 16);
-                                wi[p][k2] = uint32_t(i0p[p]) | (uint32_t(i1p[p]) << 16);
-                            }
+                            for (int p = 0; p < NP; ++p) w[p][k2] = uint32_t(b0[p]) | (uint32_t(b1[p]) << 16);
                         }
 #pragma unroll
-                        for (int p = 0; p < NP; ++p) {
-                            *reinterpret_cast<uint4 *>(a.out + int64_t(p) * a.plane_out + base + g8 * 8) =
-                                make_uint4(wr[p][0], wr[p][1], wr[p][2], wr[p][3]);
-                            *reinterpret_cast<uint4 *>(a.out + int64_t(NP + p) * a.plane_out + base + g8 * 8) =
-                                make_uint4(wi[p][0], wi[p][1], wi[p][2], wi[p][3]);
-                        }
+                        for (int p = 0; p < NP; ++p) st_global_v8(a.out + int64_t(c * NP + p) * a.plane_out + base, w[p]);
                     }
                 } else {
 #pragma unroll
                     for (int k = 0; k < 16; ++k) {
                         uint16_t br[3], bi[3];
-                        pieces_of(k, br, bi);
+                        pieces_of(v[q][k], br);
+                        pieces_of(v[q][16 + k], bi);
                         const int64_t off = (r * a.mp + i0 + k) * a.left + l;
 #pragma unroll
                         for (int p = 0; p < NP; ++p) {

@@ -155,6 +155,14 @@ __device__ __forceinline__ void tmem_ld_wait()
     asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
 }
 
+// One 32-byte global store (8 x 32 bit); the address must be 32-byte aligned.
+__device__ __forceinline__ void st_global_v8(void *ptr, const uint32_t (&w)[8])
+{
+    asm volatile("st.global.v8.b32 [%0], {%1, %2, %3, %4, %5, %6, %7, %8};" ::"l"(ptr), "r"(w[0]), "r"(w[1]),
+                 "r"(w[2]), "r"(w[3]), "r"(w[4]), "r"(w[5]), "r"(w[6]), "r"(w[7])
+                 : "memory");
+}
+
 // Shared-memory matrix descriptor (tcgen05 form): start address, leading
 // and stride byte offsets (16-byte units), fixed version field 1 at bit 46,
 // swizzle mode in bits 61..63 (0 none, 2 128B, 4 64B, 6 32B).
