@@ -420,7 +420,8 @@ struct TcArgs {
     int64_t mp;             // padded output length
     int64_t aps;            // 64-point atoms per slab (MN-major)
     int64_t plane_out;      // elements per output plane
-    int64_t items;          // work items = point tiles x row tiles
+    int64_t pairs;          // work items of a CTA pair: (pair of point tiles, row tile)
+    int64_t tiles;          // point tiles
     int it, ni, kblocks;
     int stage_bytes, tx_bytes, e_offset;
     float tb;               // tau * beta for the nonlinear epilogue
@@ -440,12 +441,15 @@ constexpr int kEpiWarps = 16;      // four per TMEM lane quarter
 constexpr int kThreads = 32 * (2 + kEpiWarps);  // warp 0 TMA, warp 1 TMEM + MMA, then the epilogue warps
 constexpr int kChunksPerWarp = 2;  // 16-row chunks each epilogue warp drains (IT <= 128)
 
-// Persistent kernel: CTA b processes work items b, b + gridDim.x, ...;
-// item T is (point tile T / ni, row tile T % ni), so neighbouring CTAs share
-// the data tile through L2.  The TMA warp runs ahead across item
-// boundaries; the epilogue warps copy the two accumulators into registers,
-// release tensor memory to the MMA warp at once, and then scale, split and
-// store while the next item's MMAs run.
+// Persistent kernel in clusters of two CTAs.  Cluster c processes work
+// items P = c, c + #clusters, ...; item P is the row tile h = P % ni of the
+// point tiles 2 (P / ni) + rank, rank = 0, 1, so the two CTAs of a cluster
+// need the same matrix tiles at the same time: each loads half of every
+// matrix tile and multicasts it to both, and each MMA warp releases a
+// stage in both CTAs (the stage is free once both have consumed it).  The
+// TMA warp runs ahead across item boundaries; the epilogue warps copy the
+// two accumulators into registers, release tensor memory to the MMA warp
+// at once, and then scale, split and store while the next item's MMAs run.
 template <int NP, bool KMAJOR, int EPI, bool FX>
 __global__ void __launch_bounds__(kThreads, 1)
     tc_mode_kernel(const __grid_constant__ CUtensorMap mapX, const __grid_constant__ CUtensorMap mapE, TcArgs a)
@@ -467,7 +471,7 @@ __global__ void __launch_bounds__(kThreads, 1)
     if (threadIdx.x == 0) {
         for (int s = 0; s < kStages; ++s) {
             mbar_init(&full[s], 1);
-            mbar_init(&empty[s], 1);
+            mbar_init(&empty[s], 2);  // released by the MMA warps of both CTAs
         }
         mbar_init(accf, 1);
         mbar_init(tmem_empty, kEpiWarps);
@@ -482,16 +486,20 @@ __global__ void __launch_bounds__(kThreads, 1)
     }
     tc_fence_before();
     __syncthreads();
+    cluster_sync();  // the peer's barriers are initialised before any multicast reaches them
     tc_fence_after();
     const uint32_t tmem = *tmem_slot;
+    const int rank = int(blockIdx.x & 1);
+    const int64_t cid = blockIdx.x / 2, nclusters = gridDim.x / 2;
+    const int half_rows = a.it / 2;
 
     if (warp == 0) {
         if (lane == 0) {
             // ---------------- TMA producer ----------------
             uint32_t gk = 0;  // k-blocks issued by this CTA over all items
-            for (int64_t T = blockIdx.x; T < a.items && !*abort_flag; T += gridDim.x) {
-                const int64_t tile = T / a.ni;
-                const int h = int(T % a.ni);
+            for (int64_t P = cid; P < a.pairs && !*abort_flag; P += nclusters) {
+                const int64_t tile = (P / a.ni) * 2 + rank;
+                const int h = int(P % a.ni);
                 // TMA coordinates of this item's two 64-point atoms (MN-major), fixed over k
                 int ac_l[2] = {0, 0}, ac_r[2] = {0, 0};
                 if (!KMAJOR) {
@@ -525,11 +533,12 @@ __global__ void __launch_bounds__(kThreads, 1)
                                 tma_load_4d(&mapX, &full[s], dst + 2048, ac_l[1], kb * kBK, ac_r[1], c * NP + p);
                             }
                         }
-                    uint8_t *est = st + a.e_offset;
+                    // this CTA's half of every matrix block, to both CTAs
+                    uint8_t *est = st + a.e_offset + rank * half_rows * 32;
                     for (int p = 0; p < NP; ++p)
                         for (int w = 0; w < 3; ++w)
-                            tma_load_2d(&mapE, &full[s], est + (p * 3 + w) * a.it * 32, kb * kBK,
-                                        p * e_pstride + e_row0 + w * a.it);
+                            tma_load_2d_mc(&mapE, &full[s], est + (p * 3 + w) * a.it * 32, kb * kBK,
+                                           p * e_pstride + e_row0 + w * a.it + rank * half_rows, 0x3);
                 }
             }
         }
@@ -539,7 +548,7 @@ __global__ void __launch_bounds__(kThreads, 1)
             const uint32_t idesc = FX ? idesc_f16_f32(kTileM, 2 * a.it, !KMAJOR, false)
                                       : idesc_bf16_f32(kTileM, 2 * a.it, !KMAJOR, false);
             uint32_t gk = 0, lt = 0;
-            for (int64_t T = blockIdx.x; T < a.items && !*abort_flag; T += gridDim.x, ++lt) {
+            for (int64_t P = cid; P < a.pairs && !*abort_flag; P += nclusters, ++lt) {
                 if (lt > 0 && !mbar_wait(tmem_empty, (lt - 1) & 1u, a.err, MM_ERR_TIMEOUT)) {
                     *abort_flag = 1;
                     break;
@@ -571,7 +580,7 @@ __global__ void __launch_bounds__(kThreads, 1)
                             started[acc] = true;
                         }
                     }
-                    umma_commit(&empty[s]);
+                    umma_commit_mc(&empty[s], 0x3);
                 }
                 umma_commit(accf);
             }
@@ -596,9 +605,9 @@ __global__ void __launch_bounds__(kThreads, 1)
         float local_max = 0.0f;
         bool range_ok = true;
         uint32_t lt = 0;
-        for (int64_t T = blockIdx.x; T < a.items; T += gridDim.x, ++lt) {
-            const int64_t tile = T / a.ni;
-            const int h = int(T % a.ni);
+        for (int64_t P = cid; P < a.pairs; P += nclusters, ++lt) {
+            const int64_t tile = (P / a.ni) * 2 + rank;
+            const int h = int(P % a.ni);
             const bool acc_ready = !*abort_flag && mbar_wait(accf, lt & 1u, a.err, MM_ERR_TIMEOUT);
             if (!acc_ready) *abort_flag = 1;
             tc_fence_after();
@@ -724,6 +733,7 @@ __global__ void __launch_bounds__(kThreads, 1)
     }
     tc_fence_before();
     __syncthreads();
+    cluster_sync();  // no CTA leaves while its peer may still write into its shared memory
     if (warp == 1) {
         tc_fence_after();
         tmem_dealloc(tmem, ncols);
@@ -781,8 +791,25 @@ static cudaError_t launch_tc(const CUtensorMap &mx, const CUtensorMap &me, const
     auto kern = tc_mode_kernel<NP, KM, EPI, FX>;
     cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
     if (e != cudaSuccess) return e;
-    kern<<<grid, kThreads, smem, s>>>(mx, me, a);
+    cudaLaunchConfig_t cfg = {};
+    cfg.gridDim = dim3(unsigned(grid));
+    cfg.blockDim = dim3(kThreads);
+    cfg.dynamicSmemBytes = size_t(smem);
+    cfg.stream = s;
+    cudaLaunchAttribute attr[1];
+    attr[0].id = cudaLaunchAttributeClusterDimension;
+    attr[0].val.clusterDim.x = 2;
+    attr[0].val.clusterDim.y = 1;
+    attr[0].val.clusterDim.z = 1;
+    cfg.attrs = attr;
+    cfg.numAttrs = 1;
+    // persistent grid: no more clusters than can be resident at once
+    int active = 0;
+    if (cudaOccupancyMaxActiveClusters(&active, kern, &cfg) == cudaSuccess && active > 0 && 2 * active < grid)
+        cfg.gridDim = dim3(unsigned(2 * active));
+    e = cudaLaunchKernelEx(&cfg, kern, mx, me, a);
     count_launch();
+    if (e != cudaSuccess) return e;
     return cudaGetLastError();
 }
 
@@ -845,14 +872,15 @@ cudaError_t tc_mode_product(const TcState &si, const TcState &so, int mu, const 
         const int64_t rows = int64_t(NP) * M.ni * 3 * M.it;
         cuuint64_t dims[2] = {cuuint64_t(M.k_pad), cuuint64_t(rows)};
         cuuint64_t str[1] = {cuuint64_t(M.k_pad * 2)};
-        cuuint32_t box[2] = {kBK, cuuint32_t(M.it)};
+        cuuint32_t box[2] = {kBK, cuuint32_t(M.it / 2)};  // each CTA of a pair loads half the rows
         if (!encode(&me, M.pieces, 2, dims, str, box, CU_TENSOR_MAP_SWIZZLE_32B)) return cudaErrorInvalidValue;
     }
     int64_t tiles;
     if (km) tiles = (a.right + kTileM - 1) / kTileM;
     else tiles = (a.right * a.aps + 1) / 2;
-    a.items = tiles * a.ni;
-    const int64_t grid = a.items < num_sms() ? a.items : num_sms();
+    a.tiles = tiles;
+    a.pairs = (tiles + 1) / 2 * a.ni;
+    int64_t grid = 2 * (a.pairs < num_sms() / 2 ? a.pairs : num_sms() / 2);
     const int smem = kStages * a.stage_bytes + 1024 + 256;
     if (fx) return dispatch_np<3, true>(km, epi.kind, mx, me, a, int(grid), smem, s);
     switch (NP) {
