@@ -162,11 +162,12 @@ mm_status tc_matrix_host(const double *E, int64_t m, int64_t n, int npieces, boo
                     else piece[q] = f16_round(rest[q]);
                     rest[q] -= piece[q];
                 }
-                // blocks: 0 = -S, 1 = C, 2 = S
+                // blocks: 0 = -S, 1 = C, 2 = S; stored tile by tile (see TcMatrix)
                 const double vals[3] = {-piece[1], piece[0], piece[1]};
+                const int64_t kb = j / 16, jj = j % 16, kbs = M.k_pad / 16;
                 for (int w = 0; w < 3; ++w) {
-                    const int64_t row = ((int64_t(p) * M.ni + tile) * 3 + w) * M.it + il;
-                    h[size_t(row * M.k_pad + j)] = fixed ? f16_bits(vals[w]) : bf16_bits(vals[w]);
+                    const int64_t row = (((int64_t(p) * M.ni + tile) * kbs + kb) * 3 + w) * M.it + il;
+                    h[size_t(row * 16 + jj)] = fixed ? f16_bits(vals[w]) : bf16_bits(vals[w]);
                 }
             }
         }
@@ -511,8 +512,9 @@ __global__ void __launch_bounds__(kThreads, 1)
                         ac_l[q] = int((atom % a.aps) * 64);
                     }
                 }
-                const int e_row0 = (h * 3) * a.it;
-                const int e_pstride = a.ni * 3 * a.it;
+                // matrix tiles are stored contiguously per (piece, row tile, k-block): 3 it rows of 16
+                const int e_row0 = h * a.kblocks * 3 * a.it;
+                const int e_pstride = a.ni * a.kblocks * 3 * a.it;
                 const int k_row = int(tile * kTileM);
                 for (int kb = 0; kb < a.kblocks; ++kb, ++gk) {
                     const int s = int(gk % kStages);
@@ -537,8 +539,8 @@ __global__ void __launch_bounds__(kThreads, 1)
                     uint8_t *est = st + a.e_offset + rank * half_rows * 32;
                     for (int p = 0; p < NP; ++p)
                         for (int w = 0; w < 3; ++w)
-                            tma_load_2d_mc(&mapE, &full[s], est + (p * 3 + w) * a.it * 32, kb * kBK,
-                                           p * e_pstride + e_row0 + w * a.it + rank * half_rows, 0x3);
+                            tma_load_2d_mc(&mapE, &full[s], est + (p * 3 + w) * a.it * 32, 0,
+                                           p * e_pstride + e_row0 + (kb * 3 + w) * a.it + rank * half_rows, 0x3);
                 }
             }
         }
@@ -869,9 +871,9 @@ cudaError_t tc_mode_product(const TcState &si, const TcState &so, int mu, const 
         if (!encode(&mx, xin, 4, dims, str, box, CU_TENSOR_MAP_SWIZZLE_128B)) return cudaErrorInvalidValue;
     }
     {
-        const int64_t rows = int64_t(NP) * M.ni * 3 * M.it;
-        cuuint64_t dims[2] = {cuuint64_t(M.k_pad), cuuint64_t(rows)};
-        cuuint64_t str[1] = {cuuint64_t(M.k_pad * 2)};
+        const int64_t rows = int64_t(NP) * M.ni * (M.k_pad / 16) * 3 * M.it;
+        cuuint64_t dims[2] = {16, cuuint64_t(rows)};
+        cuuint64_t str[1] = {32};
         cuuint32_t box[2] = {kBK, cuuint32_t(M.it / 2)};  // each CTA of a pair loads half the rows
         if (!encode(&me, M.pieces, 2, dims, str, box, CU_TENSOR_MAP_SWIZZLE_32B)) return cudaErrorInvalidValue;
     }
