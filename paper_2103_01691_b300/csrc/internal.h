@@ -51,7 +51,7 @@ struct TcMatrix {
     int64_t n_in = 0, n_out = 0;    // logical sizes (columns, rows)
     int64_t k_pad = 0;              // padded contraction length
     int ni = 0, it = 0;             // number of row tiles, rows per tile
-    void *pieces = nullptr;         // [p][tile][k_pad/16][3 blocks (-S, C, S)][it][16], bf16 or fp16
+    void *pieces = nullptr;         // [p][tile][k_pad/16][2 blocks (C, S)][it][16], bf16 or fp16
     int npieces = 0;
     bool fixed = false;             // MM_PREC_F16X6 pieces
     float *rho = nullptr;           // fixed: power-of-two scale of each row (ni * it floats)

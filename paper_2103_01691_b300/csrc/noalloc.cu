@@ -87,7 +87,7 @@ extern "C" mm_status mumode_product_noalloc(int d, const int64_t *n, int mu, con
     const int64_t k_pad = (nmu + 15) / 16 * 16, m_pad = (m + 15) / 16 * 16;
     const int64_t ni = (m_pad + 127) / 128, it = ((m_pad + ni - 1) / ni + 15) / 16 * 16;
     const size_t words = 256;
-    const size_t mat_bytes = align256(size_t(NP * ni * 3 * it * k_pad) * 2);
+    const size_t mat_bytes = align256(size_t(NP * ni * 2 * it * k_pad) * 2);  // C and S blocks
     const size_t rho_bytes = align256(size_t(ni * it) * sizeof(float));
     const size_t in_bytes = align256(size_t(si.plane) * 2 * NP * 2);
     const size_t out_bytes = align256(size_t(so.plane) * 2 * NP * 2);

@@ -18,10 +18,10 @@
 // columns over (output part c', row i) of one tile of IT matrix rows:
 //   D[pt][c'=re, i] = sum_j Xre[pt][j] C[i][j] + Xim[pt][j] (-S[i][j])
 //   D[pt][c'=im, i] = sum_j Xre[pt][j] S[i][j] + Xim[pt][j]   C[i][j]
-// The matrix tile is stored as the row blocks [-S; C; S] (3 IT rows), so
-// the real-plane products read the window [C; S] and the imaginary-plane
-// products the window [-S; C]: one MMA with N = 2 IT per plane and piece
-// pair.  For direction 1 (left == 1) the points are fibers and X is
+// The matrix tile is stored as the row blocks [C; S] (2 IT rows): the
+// real-plane product is one MMA with N = 2 IT over [C; S]; the imaginary
+// plane takes two MMAs with N = IT, -Xim S (the MMA's negate-A bit) into
+// the real columns and Xim C into the imaginary ones.  For direction 1 (left == 1) the points are fibers and X is
 // K-major in memory; for the other directions the points run along the
 // contiguous index l and X is MN-major; both are loaded by TMA as they lie
 // in HBM, with no permutation between directions (section 5).
@@ -82,6 +82,9 @@ bool tc_fixed(mm_prec p) { return p == MM_PREC_F16X6; }
 
 static inline int64_t round16(int64_t v) { return (v + 15) / 16 * 16; }
 
+// Matrix blocks per piece and row tile: C = Re E and S = Im E.
+constexpr int kBlocks = 2;
+
 // ---- host: BF16 pieces of the matrix ----------------------------------------------
 
 // Round a double to the nearest BF16 value (ties to even), returned as a double.
@@ -133,7 +136,7 @@ mm_status tc_matrix_host(const double *E, int64_t m, int64_t n, int npieces, boo
     M.it = int(round16((m_pad + M.ni - 1) / M.ni));
     M.npieces = npieces;
     M.fixed = fixed;
-    const int64_t rows = int64_t(npieces) * M.ni * 3 * M.it;
+    const int64_t rows = int64_t(npieces) * M.ni * kBlocks * M.it;
     h.assign(size_t(rows * M.k_pad), 0);
     rho.assign(size_t(M.ni) * M.it, 1.0f);
     for (int64_t i = 0; i < m; ++i) {
@@ -162,11 +165,11 @@ mm_status tc_matrix_host(const double *E, int64_t m, int64_t n, int npieces, boo
                     else piece[q] = f16_round(rest[q]);
                     rest[q] -= piece[q];
                 }
-                // blocks: 0 = -S, 1 = C, 2 = S; stored tile by tile (see TcMatrix)
-                const double vals[3] = {-piece[1], piece[0], piece[1]};
+                // blocks: 0 = C, 1 = S; stored tile by tile (see TcMatrix)
+                const double vals[kBlocks] = {piece[0], piece[1]};
                 const int64_t kb = j / 16, jj = j % 16, kbs = M.k_pad / 16;
-                for (int w = 0; w < 3; ++w) {
-                    const int64_t row = (((int64_t(p) * M.ni + tile) * kbs + kb) * 3 + w) * M.it + il;
+                for (int w = 0; w < kBlocks; ++w) {
+                    const int64_t row = (((int64_t(p) * M.ni + tile) * kbs + kb) * kBlocks + w) * M.it + il;
                     h[size_t(row * 16 + jj)] = fixed ? f16_bits(vals[w]) : bf16_bits(vals[w]);
                 }
             }
@@ -410,7 +413,7 @@ cudaError_t tc_merge(const TcState &st, int npieces, bool fixed, const void *pie
 
 // ---- device: the tensor-core mode product ---------------------------------------------
 
-constexpr int kStages = 3;
+constexpr int kStages = 4;
 constexpr int kBK = 16;             // contraction elements per stage (one MMA K)
 constexpr int kTileM = 128;         // points per CTA
 constexpr int kDataTileBytes = kTileM * kBK * 2;  // 4 KB per (plane, piece)
@@ -513,8 +516,8 @@ __global__ void __launch_bounds__(kThreads, 1)
                     }
                 }
                 // matrix tiles are stored contiguously per (piece, row tile, k-block): 3 it rows of 16
-                const int e_row0 = h * a.kblocks * 3 * a.it;
-                const int e_pstride = a.ni * a.kblocks * 3 * a.it;
+                const int e_row0 = h * a.kblocks * kBlocks * a.it;
+                const int e_pstride = a.ni * a.kblocks * kBlocks * a.it;
                 const int k_row = int(tile * kTileM);
                 for (int kb = 0; kb < a.kblocks; ++kb, ++gk) {
                     const int s = int(gk % kStages);
@@ -538,17 +541,21 @@ __global__ void __launch_bounds__(kThreads, 1)
                     // this CTA's half of every matrix block, to both CTAs
                     uint8_t *est = st + a.e_offset + rank * half_rows * 32;
                     for (int p = 0; p < NP; ++p)
-                        for (int w = 0; w < 3; ++w)
-                            tma_load_2d_mc(&mapE, &full[s], est + (p * 3 + w) * a.it * 32, 0,
-                                           p * e_pstride + e_row0 + (kb * 3 + w) * a.it + rank * half_rows, 0x3);
+                        for (int w = 0; w < kBlocks; ++w)
+                            tma_load_2d_mc(&mapE, &full[s], est + (p * kBlocks + w) * a.it * 32, 0,
+                                           p * e_pstride + e_row0 + (kb * kBlocks + w) * a.it + rank * half_rows,
+                                           0x3);
                 }
             }
         }
     } else if (warp == 1) {
         if (lane == 0) {
             // ---------------- MMA issuer ----------------
-            const uint32_t idesc = FX ? idesc_f16_f32(kTileM, 2 * a.it, !KMAJOR, false)
-                                      : idesc_bf16_f32(kTileM, 2 * a.it, !KMAJOR, false);
+            const uint32_t idesc_full = FX ? idesc_f16_f32(kTileM, 2 * a.it, !KMAJOR, false)
+                                           : idesc_bf16_f32(kTileM, 2 * a.it, !KMAJOR, false);
+            const uint32_t idesc_half = FX ? idesc_f16_f32(kTileM, a.it, !KMAJOR, false)
+                                           : idesc_bf16_f32(kTileM, a.it, !KMAJOR, false);
+            const uint32_t idesc_half_neg = idesc_half | (1u << 13);  // negate A
             uint32_t gk = 0, lt = 0;
             for (int64_t P = cid; P < a.pairs && !*abort_flag; P += nclusters, ++lt) {
                 if (lt > 0 && !mbar_wait(tmem_empty, (lt - 1) & 1u, a.err, MM_ERR_TIMEOUT)) {
@@ -567,20 +574,23 @@ __global__ void __launch_bounds__(kThreads, 1)
                     tc_fence_after();
                     const uint32_t st = smem_u32(smem + s * a.stage_bytes);
                     const uint32_t est = st + a.e_offset;
-                    for (int c = 0; c < 2; ++c) {
+                    // real plane: one MMA over the window [C; S] writes (re, im) columns;
+                    // imaginary plane: -Xi S into the re columns (negated A), Xi C into the im columns
 #pragma unroll
-                        for (int t = 0; t < num_terms(NP); ++t) {
-                            const int pa = term_a(t), pb = term_b(t);
-                            const uint32_t xaddr = st + (c * NP + pb) * kDataTileBytes;
-                            const uint64_t adesc =
-                                KMAJOR ? smem_desc(xaddr, 16, 256, kSwz32) : smem_desc(xaddr, 2048, 1024, kSwz128);
-                            // real plane: window [C; S] (block 1); imaginary plane: [-S; C] (block 0)
-                            const uint32_t eaddr = est + (pa * 3 + (c == 0 ? 1 : 0)) * a.it * 32;
-                            const uint64_t bdesc = smem_desc(eaddr, 16, 256, kSwz32);
-                            const int acc = (NP > 1 && (pa != 0 || pb != 0)) ? 1 : 0;
-                            umma_f16(tmem + uint32_t(acc * acc_cols), adesc, bdesc, idesc, started[acc] ? 1u : 0u);
-                            started[acc] = true;
-                        }
+                    for (int t = 0; t < num_terms(NP); ++t) {
+                        const int pa = term_a(t), pb = term_b(t);
+                        const int acc = (NP > 1 && (pa != 0 || pb != 0)) ? 1 : 0;
+                        const uint32_t dcol = tmem + uint32_t(acc * acc_cols);
+                        const uint32_t eC = est + (pa * kBlocks + 0) * a.it * 32;
+                        const uint32_t eS = est + (pa * kBlocks + 1) * a.it * 32;
+                        const uint32_t xre = st + (0 * NP + pb) * kDataTileBytes;
+                        const uint32_t xim = st + (1 * NP + pb) * kDataTileBytes;
+                        const uint64_t are = KMAJOR ? smem_desc(xre, 16, 256, kSwz32) : smem_desc(xre, 2048, 1024, kSwz128);
+                        const uint64_t aim = KMAJOR ? smem_desc(xim, 16, 256, kSwz32) : smem_desc(xim, 2048, 1024, kSwz128);
+                        umma_f16(dcol, are, smem_desc(eC, 16, 256, kSwz32), idesc_full, started[acc] ? 1u : 0u);
+                        started[acc] = true;
+                        umma_f16(dcol, aim, smem_desc(eS, 16, 256, kSwz32), idesc_half_neg, 1u);
+                        umma_f16(dcol + uint32_t(a.it), aim, smem_desc(eC, 16, 256, kSwz32), idesc_half, 1u);
                     }
                     umma_commit_mc(&empty[s], 0x3);
                 }
@@ -848,7 +858,7 @@ cudaError_t tc_mode_product(const TcState &si, const TcState &so, int mu, const 
     a.ni = M.ni;
     a.kblocks = int(a.kp / kBK);
     a.e_offset = 2 * NP * kDataTileBytes;
-    a.tx_bytes = a.e_offset + NP * 3 * M.it * 32;
+    a.tx_bytes = a.e_offset + NP * kBlocks * M.it * 32;
     a.stage_bytes = (a.tx_bytes + 1023) / 1024 * 1024;
     a.tb = float(epi.tb);
     a.out = (uint16_t *)out_pieces;
@@ -871,7 +881,7 @@ cudaError_t tc_mode_product(const TcState &si, const TcState &so, int mu, const 
         if (!encode(&mx, xin, 4, dims, str, box, CU_TENSOR_MAP_SWIZZLE_128B)) return cudaErrorInvalidValue;
     }
     {
-        const int64_t rows = int64_t(NP) * M.ni * (M.k_pad / 16) * 3 * M.it;
+        const int64_t rows = int64_t(NP) * M.ni * (M.k_pad / 16) * kBlocks * M.it;
         cuuint64_t dims[2] = {16, cuuint64_t(rows)};
         cuuint64_t str[1] = {32};
         cuuint32_t box[2] = {kBK, cuuint32_t(M.it / 2)};  // each CTA of a pair loads half the rows
