@@ -232,6 +232,15 @@ mm_status mumode_step_host(mm_plan *plan, void *u_host, int64_t nsteps, void *st
 
 void mm_plan_destroy(mm_plan *plan);
 
+/* CUDA graphs (on by default; not from the paper).  With graphs on, the
+ * tensor-core paths of mumode_step, hermite_ho_step and split_step_gpe
+ * capture their whole launch sequence (split, nsteps sweeps, merge) the
+ * first time they are called with a given tensor pointer, nsteps, stream,
+ * tau and beta, and replay that graph afterwards (at most 16 graphs per
+ * plan).  Graphs are not used on the legacy default stream (NULL) or while
+ * kernel timing is on.  Turning graphs off frees the cached graphs. */
+mm_status mm_plan_set_graphs(mm_plan *plan, int enable);
+
 /* ---------------------------------------------------------------------
  * Hermite spectral method (section 3; section 4.3 HKP) for d = 3 with
  * m = n_mu Gauss-Hermite nodes per direction (square transforms).

@@ -8,6 +8,8 @@
 #include <cstdarg>
 #include <cstdio>
 #include <cstring>
+#include <map>
+#include <tuple>
 #include <vector>
 
 #include "internal.h"
@@ -60,6 +62,11 @@ struct mm_plan {
     double prop_s[2] = {NAN, NAN};
     void *Pdev[2][mm::kMaxDims] = {};
     mm::TcMatrix Ptc[2][mm::kMaxDims] = {};
+    // CUDA graphs of whole step sequences, keyed by (call, tensor, nsteps, stream, tau, beta)
+    bool use_graphs = true;
+    std::map<std::tuple<int, const void *, int64_t, cudaStream_t, double, double>,
+             std::pair<cudaGraphExec_t, long long>>
+        graphs;
 };
 
 namespace mm {
@@ -404,6 +411,8 @@ void free_prop(mm_plan *p, int slot)
     p->prop_s[slot] = NAN;
 }
 
+void drop_graphs(mm_plan *p);
+
 // Make sure the propagators for step s are in a cache slot; returns the slot.
 mm_status ensure_prop(mm_plan *p, double s, int avoid, int *slot)
 {
@@ -413,6 +422,7 @@ mm_status ensure_prop(mm_plan *p, double s, int avoid, int *slot)
             return MM_OK;
         }
     int k = (avoid == 0) ? 1 : 0;
+    drop_graphs(p);  // captured graphs may point at the matrices being replaced
     free_prop(p, k);
     for (int v = 0; v < p->d; ++v) {
         std::vector<double> P = harmonic_propagator(p, v, s);
@@ -424,9 +434,61 @@ mm_status ensure_prop(mm_plan *p, double s, int avoid, int *slot)
     return MM_OK;
 }
 
+void drop_graphs(mm_plan *p)
+{
+    for (auto &kv : p->graphs) cudaGraphExecDestroy(kv.second.first);
+    p->graphs.clear();
+}
+
+// Run `body` (a sequence of launches on stream s) through a cached CUDA
+// graph: the first call with a given key captures it, later calls replay
+// it.  Plain launches when graphs are off, on the legacy default stream, or
+// while kernel timing is on.
+template <class F>
+mm_status run_graphed(mm_plan *p, int kind, const void *ptr, int64_t nsteps, cudaStream_t s, double a, double b,
+                      F &&body)
+{
+    if (!p->use_graphs || s == nullptr || p->ctx->timing) return body();
+    const auto key = std::make_tuple(kind, ptr, nsteps, s, a, b);
+    auto it = p->graphs.find(key);
+    if (it == p->graphs.end()) {
+        if (p->graphs.size() >= 16) drop_graphs(p);
+        const long long before = mm_launch_count();
+        cudaError_t e = cudaStreamBeginCapture(s, cudaStreamCaptureModeThreadLocal);
+        if (e != cudaSuccess) return cuda_fail(e, "begin stream capture");
+        mm_status st = body();
+        cudaGraph_t g = nullptr;
+        cudaError_t e2 = cudaStreamEndCapture(s, &g);
+        const long long launches = mm_launch_count() - before;
+        mm::count_launch(int(-launches));  // captured, not run: counted at each replay
+        if (st) {
+            if (g) cudaGraphDestroy(g);
+            return st;
+        }
+        if (e2 != cudaSuccess) return cuda_fail(e2, "end stream capture");
+        cudaGraphExec_t ex = nullptr;
+        e = cudaGraphInstantiate(&ex, g, 0);
+        cudaGraphDestroy(g);
+        if (e != cudaSuccess) return cuda_fail(e, "graph instantiate");
+        it = p->graphs.emplace(key, std::make_pair(ex, launches)).first;
+    }
+    cudaError_t e = cudaGraphLaunch(it->second.first, s);
+    if (e != cudaSuccess) return cuda_fail(e, "graph launch");
+    mm::count_launch(int(it->second.second));
+    return MM_OK;
+}
+
 }  // namespace
 
 extern "C" {
+
+mm_status mm_plan_set_graphs(mm_plan *p, int enable)
+{
+    if (!p) return fail(MM_ERR_INVALID_ARG, "plan is NULL");
+    p->use_graphs = enable != 0;
+    if (!p->use_graphs) drop_graphs(p);
+    return MM_OK;
+}
 
 const char *mm_last_error(void) { return mm::g_err; }
 
@@ -666,13 +728,16 @@ mm_status mumode_step(mm_plan *p, void *u_dev, int64_t nsteps, void *stream)
             if ((st = simt_sweep(p, p->Edev, u_dev, s))) return st;
         return MM_OK;
     }
-    int cur = 0;
-    mm::TcMatrix *M[mm::kMaxDims];
-    for (int v = 0; v < p->d; ++v) M[v] = &p->Etc[v];
-    if ((st = tc_begin(p, M, u_dev, s))) return st;
-    for (int64_t k = 0; k < nsteps; ++k)
-        if ((st = tc_sweep(p, M, cur, mm::TcEpilogue{}, s))) return st;
-    return tc_end(p, cur, u_dev, s);
+    return run_graphed(p, 0, u_dev, nsteps, s, 0.0, 0.0, [&]() -> mm_status {
+        mm_status r;
+        int cur = 0;
+        mm::TcMatrix *M[mm::kMaxDims];
+        for (int v = 0; v < p->d; ++v) M[v] = &p->Etc[v];
+        if ((r = tc_begin(p, M, u_dev, s))) return r;
+        for (int64_t k = 0; k < nsteps; ++k)
+            if ((r = tc_sweep(p, M, cur, mm::TcEpilogue{}, s))) return r;
+        return tc_end(p, cur, u_dev, s);
+    });
 }
 
 mm_status mumode_step_host(mm_plan *p, void *u_host, int64_t nsteps, void *stream)
@@ -699,6 +764,7 @@ mm_status mumode_step_host(mm_plan *p, void *u_host, int64_t nsteps, void *strea
 void mm_plan_destroy(mm_plan *p)
 {
     if (!p) return;
+    drop_graphs(p);
     for (int v = 0; v < mm::kMaxDims; ++v) {
         if (p->Edev[v]) cudaFree(p->Edev[v]);
         mm::tc_matrix_destroy(&p->Etc[v]);
@@ -809,13 +875,16 @@ mm_status hermite_ho_step(mm_plan *p, void *psi, double tau, int64_t nsteps, voi
             if ((st = simt_sweep(p, p->Pdev[slot], psi, s))) return st;
         return MM_OK;
     }
-    int cur = 0;
-    mm::TcMatrix *M[mm::kMaxDims];
-    for (int v = 0; v < p->d; ++v) M[v] = &p->Ptc[slot][v];
-    if ((st = tc_begin(p, M, psi, s))) return st;
-    for (int64_t k = 0; k < nsteps; ++k)
-        if ((st = tc_sweep(p, M, cur, mm::TcEpilogue{}, s))) return st;
-    return tc_end(p, cur, psi, s);
+    return run_graphed(p, 1, psi, nsteps, s, tau, 0.0, [&]() -> mm_status {
+        mm_status r;
+        int cur = 0;
+        mm::TcMatrix *M[mm::kMaxDims];
+        for (int v = 0; v < p->d; ++v) M[v] = &p->Ptc[slot][v];
+        if ((r = tc_begin(p, M, psi, s))) return r;
+        for (int64_t k = 0; k < nsteps; ++k)
+            if ((r = tc_sweep(p, M, cur, mm::TcEpilogue{}, s))) return r;
+        return tc_end(p, cur, psi, s);
+    });
 }
 
 mm_status split_step_gpe(mm_plan *p, void *psi, double beta, double tau, int64_t nsteps, void *stream)
@@ -843,20 +912,23 @@ mm_status split_step_gpe(mm_plan *p, void *psi, double beta, double tau, int64_t
         }
         return simt_sweep(p, p->Pdev[half], psi, s);
     }
-    int cur = 0;
-    mm::TcMatrix *Mh[mm::kMaxDims], *Mf[mm::kMaxDims];
-    for (int v = 0; v < p->d; ++v) {
-        Mh[v] = &p->Ptc[half][v];
-        Mf[v] = &p->Ptc[full][v];
-    }
-    if ((st = tc_begin(p, Mh, psi, s))) return st;
-    mm::TcEpilogue nl;
-    nl.kind = 1;
-    nl.tb = tb;
-    for (int64_t k = 0; k < nsteps; ++k)
-        if ((st = tc_sweep(p, k == 0 ? Mh : Mf, cur, nl, s))) return st;
-    if ((st = tc_sweep(p, Mh, cur, mm::TcEpilogue{}, s))) return st;
-    return tc_end(p, cur, psi, s);
+    return run_graphed(p, 2, psi, nsteps, s, tau, beta, [&]() -> mm_status {
+        mm_status r;
+        int cur = 0;
+        mm::TcMatrix *Mh[mm::kMaxDims], *Mf[mm::kMaxDims];
+        for (int v = 0; v < p->d; ++v) {
+            Mh[v] = &p->Ptc[half][v];
+            Mf[v] = &p->Ptc[full][v];
+        }
+        if ((r = tc_begin(p, Mh, psi, s))) return r;
+        mm::TcEpilogue nl;
+        nl.kind = 1;
+        nl.tb = tb;
+        for (int64_t k = 0; k < nsteps; ++k)
+            if ((r = tc_sweep(p, k == 0 ? Mh : Mf, cur, nl, s))) return r;
+        if ((r = tc_sweep(p, Mh, cur, mm::TcEpilogue{}, s))) return r;
+        return tc_end(p, cur, psi, s);
+    });
 }
 
 mm_status mm_norm2(mm_plan *p, const void *u_dev, int weighted, double *out_host, void *stream)

@@ -46,6 +46,7 @@ SIGNATURES = {
     "mumode_step": (_i, [_vp, _vp, _i64, _vp]),
     "mumode_step_host": (_i, [_vp, _vp, _i64, _vp]),
     "mm_plan_destroy": (None, [_vp]),
+    "mm_plan_set_graphs": (_i, [_vp, _i]),
     "hermite_plan_create": (_i, [_vp, _i, _i64p, _i, _i, ctypes.POINTER(_vp)]),
     "hermite_nodes": (_i, [_vp, _i, _dp, _dp]),
     "hermite_forward": (_i, [_vp, _vp, _vp, _vp]),
@@ -256,6 +257,9 @@ class TuckerPlan:
         _check(lib().mumode_plan_create(ctx.handle, d, self.dims.ctypes.data_as(_i64p), ptrs, int(cplx), code,
                                         PREC[prec], optr, ctypes.byref(h)))
         self.handle = h
+
+    def set_graphs(self, enable: bool):
+        _check(lib().mm_plan_set_graphs(self.handle, int(enable)))
 
     def step(self, u, nsteps: int = 1, stream=None):
         _need_cuda(u)

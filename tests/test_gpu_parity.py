@@ -258,6 +258,31 @@ def test_fixed_point_wide_dynamic_range(env, orc):
     assert rel(u.cpu().numpy(), ref) <= TOL_MODE["f16x6"] * 9
 
 
+def test_graph_replay_matches_plain_launches(env):
+    """Steps replayed from a captured CUDA graph give the same bits as the
+    same steps launched one by one."""
+    mm, ctx, torch = env
+    dims, tau = (48, 40, 32), 1e-4
+    Es = [fd_schrodinger_E(mm, n, tau) for n in dims]
+    u0 = inputs.complex_normal(dims[::-1], seed=2).astype(np.complex64)
+    stream = torch.cuda.Stream()
+    with torch.cuda.stream(stream):
+        plain = mm.TuckerPlan(ctx, dims, Es, prec="f16x6")
+        plain.set_graphs(False)
+        ref = to_gpu(torch, u0, torch.complex64)
+        plain.step(ref, 3)
+        plain.step(ref, 3)
+        graphed = mm.TuckerPlan(ctx, dims, Es, prec="f16x6")
+        u = to_gpu(torch, u0, torch.complex64)
+        n0 = mm.launch_count()
+        graphed.step(u, 3)   # captured, then replayed
+        graphed.step(u, 3)   # replayed
+        n1 = mm.launch_count()
+    torch.cuda.synchronize()
+    assert torch.equal(u, ref)
+    assert n1 - n0 == 2 * (2 + 3 * 3 + 1)  # max + split, 3 sweeps x 3 products, merge; counted per replay
+
+
 def test_device_status_clean(env):
     mm, ctx, torch = env
     ctx.status()
