@@ -276,6 +276,23 @@ mm_status hermite_ho_step(mm_plan *plan, void *psi_dev, double tau, int64_t nste
 mm_status split_step_gpe(mm_plan *plan, void *psi_dev, double beta, double tau, int64_t nsteps,
                          void *stream);
 
+/* Gradient of a real loss J(psi_T), psi_T = nsteps Strang steps of psi0
+ * (split_step_gpe with the same beta, tau), with respect to psi0 (reverse
+ * mode; not in the paper).  Gradients are g = dJ/dRe psi + i dJ/dIm psi, so
+ * that dJ = Re <g, delta> (the convention of torch autograd for complex
+ * tensors).  gT_dev holds the gradient at psi_T, g0_dev receives the one at
+ * psi0 (g0 may alias gT, not psi0).  The linear flows enter through their
+ * conjugate transposes (mu-mode products with Psi D(s) Phi_W transposed
+ * and conjugated); the nonlinear stage psi' = psi e^{-i theta},
+ * theta = tau beta |psi|^2, through g = e^{i theta} g' + 2 tau beta
+ * Im(conj(g') psi') psi.  Forward states are kept every ckpt_every steps
+ * and recomputed within a segment (memory: ceil(nsteps / ckpt_every) +
+ * ckpt_every + 1 states, allocated and freed by the call, which
+ * synchronises the stream). */
+mm_status split_step_gpe_adjoint(mm_plan *plan, const void *psi0_dev, const void *gT_dev, void *g0_dev,
+                                 double beta, double tau, int64_t nsteps, int64_t ckpt_every,
+                                 void *stream);
+
 /* FP64 sum of |u|^2 (times w_l = W_l1 W_l2 W_l3 for a Hermite plan when
  * weighted != 0) over the plan's tensor; the result is written to
  * *out_host after synchronising the stream. */

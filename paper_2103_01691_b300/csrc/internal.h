@@ -29,6 +29,8 @@ cudaError_t simt_mode_product(bool fp64, bool complex_data, int64_t left, int64_
                               int64_t m, const void *L, const void *X, void *Y, cudaStream_t s);
 // psi *= exp(-i tb |psi|^2) for count complex elements.
 cudaError_t simt_nonlinear_phase(bool fp64, int64_t count, double tb, void *psi, cudaStream_t s);
+// g <- adjoint of the nonlinear phase at psi (psi: state before the phase).
+cudaError_t simt_nonlinear_adjoint(bool fp64, int64_t count, double tb, const void *psi, void *g, cudaStream_t s);
 // out (device double) += sum |u|^2 w, w = w1[i1] w2[i2] w3[i3] if w1 != NULL.
 cudaError_t norm2_accumulate(mm_dtype dt, int64_t n1, int64_t n2, int64_t n3, const void *u,
                              const double *w1, const double *w2, const double *w3, double *out,

@@ -951,3 +951,157 @@ mm_status mm_norm2(mm_plan *p, const void *u_dev, int weighted, double *out_host
 }
 
 }  // extern "C"
+
+// ---- adjoint of the GPE Strang step ---------------------------------------------------
+
+namespace {
+
+// conjugate transpose of an m x m complex matrix (interleaved)
+std::vector<double> conj_transpose(const std::vector<double> &P, int64_t m)
+{
+    std::vector<double> H(P.size());
+    for (int64_t a = 0; a < m; ++a)
+        for (int64_t b = 0; b < m; ++b) {
+            H[size_t(2 * (a * m + b))] = P[size_t(2 * (b * m + a))];
+            H[size_t(2 * (a * m + b) + 1)] = -P[size_t(2 * (b * m + a) + 1)];
+        }
+    return H;
+}
+
+struct MatSet {  // one matrix per direction, in the plan's precision
+    void *simt[mm::kMaxDims] = {};
+    mm::TcMatrix tc[mm::kMaxDims] = {};
+    void release()
+    {
+        for (int v = 0; v < mm::kMaxDims; ++v) {
+            if (simt[v]) cudaFree(simt[v]);
+            simt[v] = nullptr;
+            mm::tc_matrix_destroy(&tc[v]);
+        }
+    }
+};
+
+mm_status make_set(mm_plan *p, double s, bool adjoint, MatSet *out)
+{
+    for (int v = 0; v < p->d; ++v) {
+        std::vector<double> P = harmonic_propagator(p, v, s);
+        if (adjoint) P = conj_transpose(P, p->n[v]);
+        mm_status st = upload_matrix(p, P.data(), p->n[v], p->n[v], true, &out->simt[v], &out->tc[v]);
+        if (st) return st;
+    }
+    return MM_OK;
+}
+
+// out = L in (one linear flow: a sweep of the set's matrices); in may equal out.
+mm_status apply_set(mm_plan *p, MatSet &S, const void *in, void *out, cudaStream_t s)
+{
+    if (!p->tc) {
+        if (in != out) {
+            cudaError_t e = cudaMemcpyAsync(out, in, size_t(p->count) * elem_bytes(p->dtype), cudaMemcpyDeviceToDevice, s);
+            if (e != cudaSuccess) return cuda_fail(e, "copy");
+        }
+        return simt_sweep(p, S.simt, out, s);
+    }
+    mm::TcMatrix *M[mm::kMaxDims];
+    for (int v = 0; v < p->d; ++v) M[v] = &S.tc[v];
+    int cur = 0;
+    mm_status st = tc_begin(p, M, in, s);
+    if (st) return st;
+    if ((st = tc_sweep(p, M, cur, mm::TcEpilogue{}, s))) return st;
+    return tc_end(p, cur, out, s);
+}
+
+}  // namespace
+
+extern "C" mm_status split_step_gpe_adjoint(mm_plan *p, const void *psi0, const void *gT, void *g0, double beta,
+                                            double tau, int64_t nsteps, int64_t ckpt_every, void *stream)
+{
+    if (!p || !p->hermite) return fail(MM_ERR_INVALID_ARG, "not a Hermite plan");
+    mm_status st;
+    if ((st = check_ptr(psi0, "psi0_dev")) || (st = check_ptr(gT, "gT_dev")) || (st = check_ptr(g0, "g0_dev")))
+        return st;
+    if (nsteps < 0 || ckpt_every < 1 || !std::isfinite(tau) || !std::isfinite(beta))
+        return fail(MM_ERR_INVALID_ARG, "bad nsteps, ckpt_every, tau or beta");
+    cudaStream_t s = (cudaStream_t)stream;
+    const size_t bytes = size_t(p->count) * elem_bytes(p->dtype);
+    const bool fp64 = p->dtype == MM_C128;
+    const double tb = tau * beta, h = 0.5 * tau;
+    if (nsteps == 0) {
+        cudaError_t e = cudaMemcpyAsync(g0, gT, bytes, cudaMemcpyDeviceToDevice, s);
+        return e == cudaSuccess ? MM_OK : cuda_fail(e, "copy");
+    }
+    const int64_t nseg = (nsteps + ckpt_every - 1) / ckpt_every;
+    const int64_t seglen = std::min(ckpt_every, nsteps);
+    MatSet Fh, Ff, Ah, Af;  // forward half / full, adjoint half / full
+    void *ckpt = nullptr, *mid = nullptr, *tmp = nullptr;
+    auto cleanup = [&]() {
+        Fh.release();
+        Ff.release();
+        Ah.release();
+        Af.release();
+        if (ckpt) cudaFree(ckpt);
+        if (mid) cudaFree(mid);
+        if (tmp) cudaFree(tmp);
+    };
+    if ((st = make_set(p, h, false, &Fh)) || (st = make_set(p, tau, false, &Ff)) || (st = make_set(p, h, true, &Ah)) ||
+        (st = make_set(p, tau, true, &Af))) {
+        cleanup();
+        return st;
+    }
+    if (cudaMalloc(&ckpt, bytes * size_t(nseg)) != cudaSuccess || cudaMalloc(&mid, bytes * size_t(seglen)) != cudaSuccess ||
+        cudaMalloc(&tmp, bytes) != cudaSuccess) {
+        cleanup();
+        return fail(MM_ERR_OOM, "checkpoint storage (%lld states)", (long long)(nseg + seglen + 1));
+    }
+    auto ck = [&](int64_t k) { return static_cast<char *>(ckpt) + bytes * size_t(k); };
+    auto md = [&](int64_t k) { return static_cast<char *>(mid) + bytes * size_t(k); };
+    auto nl = [&](void *x) -> mm_status {
+        cudaError_t e = mm::simt_nonlinear_phase(fp64, p->count, tb, x, s);
+        return e == cudaSuccess ? MM_OK : cuda_fail(e, "nonlinear phase");
+    };
+    // forward sweep: checkpoints psi_{k c}; one step is L_h, N, L_h
+    cudaError_t e = cudaMemcpyAsync(tmp, psi0, bytes, cudaMemcpyDeviceToDevice, s);
+    if (e != cudaSuccess) {
+        cleanup();
+        return cuda_fail(e, "copy");
+    }
+    for (int64_t k = 0; k < nseg; ++k) {
+        e = cudaMemcpyAsync(ck(k), tmp, bytes, cudaMemcpyDeviceToDevice, s);
+        if (e != cudaSuccess) {
+            cleanup();
+            return cuda_fail(e, "checkpoint copy");
+        }
+        if (k == nseg - 1) break;
+        for (int64_t q = 0; q < ckpt_every; ++q)
+            if ((st = apply_set(p, Fh, tmp, tmp, s)) || (st = nl(tmp)) || (st = apply_set(p, Fh, tmp, tmp, s))) {
+                cleanup();
+                return st;
+            }
+    }
+    // reverse sweep, segment by segment: recompute the states before each
+    // nonlinear stage, then g <- L_h^H (N^adj (L_h^H g)) per step, with the
+    // adjacent L_h^H of consecutive steps merged into L_tau^H.
+    e = cudaMemcpyAsync(g0, gT, bytes, cudaMemcpyDeviceToDevice, s);
+    if (e == cudaSuccess) st = apply_set(p, Ah, g0, g0, s);
+    else st = cuda_fail(e, "copy");
+    for (int64_t k = nseg - 1; k >= 0 && !st; --k) {
+        const int64_t first = k * ckpt_every, last = std::min(nsteps, first + ckpt_every);
+        st = apply_set(p, Fh, ck(k), md(0), s);  // state before the nonlinear stage of step `first`
+        for (int64_t q = first + 1; q < last && !st; ++q) {
+            e = cudaMemcpyAsync(md(q - first), md(q - first - 1), bytes, cudaMemcpyDeviceToDevice, s);
+            if (e != cudaSuccess) st = cuda_fail(e, "copy");
+            if (!st) st = nl(md(q - first));
+            if (!st) st = apply_set(p, Ff, md(q - first), md(q - first), s);
+        }
+        for (int64_t q = last - 1; q >= first && !st; --q) {
+            e = mm::simt_nonlinear_adjoint(fp64, p->count, tb, md(q - first), g0, s);
+            if (e != cudaSuccess) st = cuda_fail(e, "nonlinear adjoint");
+            if (!st) st = apply_set(p, q > 0 ? Af : Ah, g0, g0, s);
+        }
+    }
+    cudaError_t e2 = cudaStreamSynchronize(s);  // the temporaries are freed below
+    cleanup();
+    if (st) return st;
+    if (e2 != cudaSuccess) return cuda_fail(e2, "adjoint (sync)");
+    return MM_OK;
+}

@@ -126,6 +126,28 @@ __global__ void nonlinear_phase_kernel(int64_t count, double tb, Elem<R, true> *
     }
 }
 
+// Adjoint of psi' = psi exp(-i theta), theta = tb |psi|^2, for a real loss
+// with gradients g = dJ/dRe + i dJ/dIm:  g = e^{i theta} g' + 2 tb Im(conj(g') psi') psi.
+template <typename R>
+__global__ void nonlinear_adjoint_kernel(int64_t count, double tb, const Elem<R, true> *psi, Elem<R, true> *g)
+{
+    for (int64_t q = blockIdx.x * int64_t(blockDim.x) + threadIdx.x; q < count;
+         q += int64_t(gridDim.x) * blockDim.x) {
+        const Elem<R, true> p = psi[q], gp = g[q];
+        const double th = tb * (double(p.re) * p.re + double(p.im) * p.im);
+        double sn, cs;
+        sincos(th, &sn, &cs);
+        // psi' = p (cs - i sn)
+        const double pr = p.re * cs + p.im * sn, pi = p.im * cs - p.re * sn;
+        // Im(conj(g') psi') = g'.re psi'.im - g'.im psi'.re
+        const double im = double(gp.re) * pi - double(gp.im) * pr;
+        // e^{i th} g' = (cs + i sn) g'
+        const double gr = gp.re * cs - gp.im * sn + 2.0 * tb * im * p.re;
+        const double gi = gp.re * sn + gp.im * cs + 2.0 * tb * im * p.im;
+        g[q] = {R(gr), R(gi)};
+    }
+}
+
 template <typename T>
 __device__ double abs2(const T &v);
 template <>
@@ -187,6 +209,19 @@ cudaError_t simt_nonlinear_phase(bool fp64, int64_t count, double tb, void *psi,
     const int blocks = int((count + 255) / 256 < 148 * 16 ? (count + 255) / 256 : 148 * 16);
     if (fp64) nonlinear_phase_kernel<double><<<blocks, 256, 0, s>>>(count, tb, (Elem<double, true> *)psi);
     else nonlinear_phase_kernel<float><<<blocks, 256, 0, s>>>(count, tb, (Elem<float, true> *)psi);
+    count_launch();
+    return cudaGetLastError();
+}
+
+cudaError_t simt_nonlinear_adjoint(bool fp64, int64_t count, double tb, const void *psi, void *g, cudaStream_t s)
+{
+    const int blocks = int((count + 255) / 256 < 148 * 16 ? (count + 255) / 256 : 148 * 16);
+    if (fp64)
+        nonlinear_adjoint_kernel<double><<<blocks, 256, 0, s>>>(count, tb, (const Elem<double, true> *)psi,
+                                                                 (Elem<double, true> *)g);
+    else
+        nonlinear_adjoint_kernel<float><<<blocks, 256, 0, s>>>(count, tb, (const Elem<float, true> *)psi,
+                                                                (Elem<float, true> *)g);
     count_launch();
     return cudaGetLastError();
 }

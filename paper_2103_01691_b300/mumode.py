@@ -53,6 +53,7 @@ SIGNATURES = {
     "hermite_backward": (_i, [_vp, _vp, _vp, _vp]),
     "hermite_ho_step": (_i, [_vp, _vp, _d, _i64, _vp]),
     "split_step_gpe": (_i, [_vp, _vp, _d, _d, _i64, _vp]),
+    "split_step_gpe_adjoint": (_i, [_vp, _vp, _vp, _vp, _d, _d, _i64, _i64, _vp]),
     "mm_norm2": (_i, [_vp, _vp, _i, _dp, _vp]),
 }
 
@@ -345,6 +346,20 @@ class HermitePlan:
                                     int(nsteps), _stream(stream)))
         return psi
 
+    def gpe_adjoint(self, psi0, gT, beta: float, tau: float, nsteps: int, ckpt_every: int = 50, out=None,
+                    stream=None):
+        """Gradient at psi0 of a real loss whose gradient at psi_T is gT."""
+        import torch
+
+        _need_cuda(psi0)
+        _need_cuda(gT)
+        out = torch.empty_like(psi0) if out is None else out
+        _check(lib().split_step_gpe_adjoint(self.handle, ctypes.c_void_p(psi0.data_ptr()),
+                                            ctypes.c_void_p(gT.data_ptr()), ctypes.c_void_p(out.data_ptr()),
+                                            float(beta), float(tau), int(nsteps), int(ckpt_every),
+                                            _stream(stream)))
+        return out
+
     def norm2(self, u, weighted: bool = True, stream=None) -> float:
         _need_cuda(u)
         out = ctypes.c_double()
@@ -362,3 +377,24 @@ class HermitePlan:
             self.close()
         except Exception:
             pass
+
+
+def gpe_evolve(plan: HermitePlan, psi0, beta: float, tau: float, nsteps: int, ckpt_every: int = 50):
+    """psi_T = nsteps Strang steps of psi0, differentiable with respect to psi0
+    (torch.autograd); the backward pass runs split_step_gpe_adjoint."""
+    import torch
+
+    class _GPE(torch.autograd.Function):
+        @staticmethod
+        def forward(ctx, psi):
+            out = psi.detach().clone()
+            plan.gpe_step(out, beta, tau, nsteps)
+            ctx.save_for_backward(psi.detach())
+            return out
+
+        @staticmethod
+        def backward(ctx, g):
+            (psi,) = ctx.saved_tensors
+            return plan.gpe_adjoint(psi, g.contiguous(), beta, tau, nsteps, ckpt_every)
+
+    return _GPE.apply(psi0)

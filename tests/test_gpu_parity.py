@@ -286,3 +286,46 @@ def test_graph_replay_matches_plain_launches(env):
 def test_device_status_clean(env):
     mm, ctx, torch = env
     ctx.status()
+
+
+# ---------------------------------------------------------------- GPE adjoint
+
+@pytest.mark.parametrize("prec,ckpt", [("fp64", 4), ("fp64", 100), ("f16x6", 4)])
+def test_gpe_adjoint_matches_oracle(env, orc, prec, ckpt):
+    """split_step_gpe_adjoint (checkpointed reverse sweep) against the
+    oracle's adjoint, itself pinned by finite differences."""
+    mm, ctx, torch = env
+    m, beta, tau, steps = 12, 100.0, 1e-3, 10
+    plan = mm.HermitePlan(ctx, [m] * 3, prec=prec)
+    xo, _, Wo = orc.gauss_hermite(m)
+    w3 = orc.weight3(Wo)
+    psi0 = inputs.gpe_psi0(xo, Wo, seed=4)
+    target = inputs.gpe_target(xo, Wo)
+    dt = torch.complex128 if prec == "fp64" else torch.complex64
+    p0 = psi0 if prec == "fp64" else psi0.astype(np.complex64)
+    pT = orc.gpe_steps(p0.astype(complex), xo, Wo, beta, tau, steps)
+    gT = 2.0 * w3 * (pT - target)
+    ref = orc.gpe_adjoint(p0.astype(complex), gT, xo, Wo, beta, tau, steps)
+    g0 = plan.gpe_adjoint(to_gpu(torch, p0, dt), to_gpu(torch, gT, dt), beta, tau, steps, ckpt_every=ckpt)
+    err = rel(g0.cpu().numpy(), ref)
+    print(f"adjoint {prec} ckpt={ckpt} rel_err={err:.3e}")
+    assert err <= (1e-10 if prec == "fp64" else 2e-5)
+
+
+def test_gpe_autograd_gradient(env, orc):
+    """torch.autograd through gpe_evolve gives the oracle's gradient of
+    J = sum |psi_T - target|^2 W."""
+    mm, ctx, torch = env
+    m, beta, tau, steps = 10, 100.0, 1e-3, 6
+    plan = mm.HermitePlan(ctx, [m] * 3, prec="fp64")
+    xo, _, Wo = orc.gauss_hermite(m)
+    w3 = torch.from_numpy(orc.weight3(Wo)).cuda()
+    psi0 = inputs.gpe_psi0(xo, Wo, seed=4)
+    target = torch.from_numpy(inputs.gpe_target(xo, Wo)).cuda()
+    p = torch.from_numpy(psi0).cuda().requires_grad_(True)
+    pT = mm.gpe_evolve(plan, p, beta, tau, steps, ckpt_every=4)
+    J = (torch.abs(pT - target) ** 2 * w3).sum()
+    J.backward()
+    pTo = orc.gpe_steps(psi0, xo, Wo, beta, tau, steps)
+    ref = orc.gpe_adjoint(psi0, 2.0 * orc.weight3(Wo) * (pTo - inputs.gpe_target(xo, Wo)), xo, Wo, beta, tau, steps)
+    assert rel(p.grad.cpu().numpy(), ref) <= 1e-10
