@@ -242,6 +242,23 @@ void mm_plan_destroy(mm_plan *plan);
 mm_status mm_plan_set_graphs(mm_plan *plan, int enable);
 
 /* ---------------------------------------------------------------------
+ * Batches of independent problems (not in the paper): many Tucker plans of
+ * different sizes stepped together, every direction of every problem in
+ * one persistent launch (the work items of all problems are dealt to the
+ * same clusters of CTAs).  The plans must be tensor-core plans with the same
+ * precision, d and mode order; each keeps its own matrices and workspace,
+ * so a plan must not be stepped on its own while a batch step that holds
+ * it is in flight.  The batch keeps device copies of the per-problem launch
+ * records and refers to the plans, which must outlive it.
+ * ------------------------------------------------------------------- */
+typedef struct mm_batch mm_batch;
+mm_status mumode_batch_create(mm_ctx *ctx, mm_plan *const *plans, int nprob, mm_batch **out);
+/* nsteps steps of every problem: u_dev[k] is problem k's tensor (in place).
+ * Results equal those of mumode_step on each plan. */
+mm_status mumode_batch_step(mm_batch *batch, void *const *u_dev, int64_t nsteps, void *stream);
+void mm_batch_destroy(mm_batch *batch);
+
+/* ---------------------------------------------------------------------
  * Hermite spectral method (section 3; section 4.3 HKP) for d = 3 with
  * m = n_mu Gauss-Hermite nodes per direction (square transforms).
  * ------------------------------------------------------------------- */

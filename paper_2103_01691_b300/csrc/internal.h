@@ -1,6 +1,7 @@
 // Internal declarations shared by the library's translation units.
 #pragma once
 
+#include <cuda.h>
 #include <cuda_runtime.h>
 
 #include <complex>
@@ -89,6 +90,25 @@ cudaError_t tc_split(const TcState &st, int npieces, bool fixed, const void *u_c
 cudaError_t tc_merge(const TcState &st, int npieces, bool fixed, const void *pieces, const float *scale, void *u_c64,
                      cudaStream_t s);
 
+// One problem of a tensor-core launch: its two tensor maps (64-byte
+// aligned, as TMA requires of a tensor map in memory) and its sizes,
+// buffers and scales.  Built by tc_problem_build.
+struct alignas(64) TcProblem {
+    CUtensorMap mapX;       // split input state
+    CUtensorMap mapE;       // matrix pieces
+    int64_t left, right;    // padded sizes of the fast / slow index groups
+    int64_t mp;             // padded output length
+    int64_t aps;            // 64-point atoms per slab (MN-major)
+    int64_t plane_out;      // elements per output plane
+    int64_t pairs_begin;    // first work item of this problem in a batched launch
+    int64_t pairs;          // work items: (pair of point tiles, row tile)
+    int it, ni, kblocks, tx_bytes;
+    uint16_t *out;
+    const float *rho;       // fixed-point row scales
+    TcScales sc;
+    unsigned *zero_word;    // batched launches: a max word to clear at kernel start
+};
+
 struct TcEpilogue {
     int kind = 0;      // 0: store pieces, 1: nonlinear phase then store pieces
     double tb = 0.0;   // tau * beta for kind 1
@@ -98,5 +118,13 @@ struct TcEpilogue {
 cudaError_t tc_mode_product(const TcState &st_in, const TcState &st_out, int mu, const TcMatrix &M,
                             mm_prec prec, const void *in_pieces, void *out_pieces,
                             const TcEpilogue &epi, const TcScales &sc, int *d_err, cudaStream_t s);
+// The record of one such product, for a batched launch (kmajor: direction 1).
+cudaError_t tc_problem_build(const TcState &st_in, const TcState &st_out, int mu, const TcMatrix &M, mm_prec prec,
+                             const void *in_pieces, void *out_pieces, const TcScales &sc, TcProblem *pr, bool *kmajor);
+// One launch over many problems (same direction kind and precision); the
+// records are in device memory (dev_probs) with a host copy (host_probs),
+// pairs_begin set to the running sum of pairs.
+cudaError_t tc_mode_product_batched(const TcProblem *host_probs, const TcProblem *dev_probs, int nprob, bool kmajor,
+                                    mm_prec prec, const TcEpilogue &epi, int *d_err, cudaStream_t s);
 
 }  // namespace mm

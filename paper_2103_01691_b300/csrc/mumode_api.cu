@@ -1105,3 +1105,136 @@ extern "C" mm_status split_step_gpe_adjoint(mm_plan *p, const void *psi0, const 
     if (e2 != cudaSuccess) return cuda_fail(e2, "adjoint (sync)");
     return MM_OK;
 }
+
+// ---- batches of independent problems ---------------------------------------------------
+
+struct mm_batch {
+    mm_ctx *ctx = nullptr;
+    std::vector<mm_plan *> plans;
+    int d = 0;
+    mm_prec prec = MM_PREC_F16X6;
+    bool fixed = false;
+    // problem records for sweep position q and sweep parity t: host copy and device array
+    std::vector<mm::TcProblem> host[mm::kMaxDims][2];
+    mm::TcProblem *dev[mm::kMaxDims][2] = {};
+    bool kmajor[mm::kMaxDims] = {};
+};
+
+extern "C" mm_status mumode_batch_create(mm_ctx *ctx, mm_plan *const *plans, int nprob, mm_batch **out)
+{
+    if (!ctx || !plans || !out) return fail(MM_ERR_INVALID_ARG, "NULL argument");
+    if (nprob < 1) return fail(MM_ERR_INVALID_ARG, "nprob = %d < 1", nprob);
+    mm_plan *p0 = plans[0];
+    if (!p0) return fail(MM_ERR_INVALID_ARG, "plans[0] is NULL");
+    for (int k = 0; k < nprob; ++k) {
+        mm_plan *p = plans[k];
+        if (!p || p->hermite || !p->tc) return fail(MM_ERR_INVALID_ARG, "plan %d is not a tensor-core Tucker plan", k);
+        if (p->ctx != ctx) return fail(MM_ERR_INVALID_ARG, "plan %d belongs to another context", k);
+        if (p->prec != p0->prec || p->d != p0->d) return fail(MM_ERR_INVALID_ARG, "plan %d differs in precision or d", k);
+        for (int v = 0; v < p->d; ++v)
+            if (p->order[v] != p0->order[v]) return fail(MM_ERR_INVALID_ARG, "plan %d has another mode order", k);
+        for (int j = 0; j < k; ++j)
+            if (plans[j] == p) return fail(MM_ERR_INVALID_ARG, "plan %d appears twice", k);
+    }
+    auto *b = new mm_batch;
+    b->ctx = ctx;
+    b->plans.assign(plans, plans + nprob);
+    b->d = p0->d;
+    b->prec = p0->prec;
+    b->fixed = p0->fixed;
+    const int d = b->d;
+    for (int q = 0; q < d; ++q)
+        for (int t = 0; t < 2; ++t) {
+            auto &vec = b->host[q][t];
+            vec.resize(size_t(nprob));
+            int64_t begin = 0;
+            const int cur = (t * d + q) % 2;  // buffer holding the input of this launch
+            for (int k = 0; k < nprob; ++k) {
+                mm_plan *p = plans[k];
+                const int mu = p->order[q];
+                mm::TcScales sc;
+                unsigned *zero = nullptr;
+                if (p->fixed) {
+                    sc.s_in = p->d_scale + q;
+                    sc.s_out = p->d_scale + (q + 1) % d;
+                    sc.max_prev = p->d_max + (1 - t) * d + q;
+                    sc.max_cur = p->d_max + t * d + q;
+                    // the max word of this position's output is cleared by the launch one position later
+                    zero = (q >= 1) ? p->d_max + (1 - t) * d + (q - 1) : p->d_max + t * d + (d - 1);
+                }
+                bool km = false;
+                cudaError_t e = mm::tc_problem_build(p->st, p->st, mu, p->Etc[mu - 1], p->prec, p->work[cur],
+                                                     p->work[1 - cur], sc, &vec[size_t(k)], &km);
+                if (e != cudaSuccess) {
+                    mm_batch_destroy(b);
+                    return cuda_fail(e, "problem record");
+                }
+                vec[size_t(k)].pairs_begin = begin;
+                vec[size_t(k)].zero_word = zero;
+                begin += vec[size_t(k)].pairs;
+                if (k == 0) b->kmajor[q] = km;
+                else if (km != b->kmajor[q]) {
+                    mm_batch_destroy(b);
+                    return fail(MM_ERR_SHAPE, "plans disagree on the layout of direction %d", mu);
+                }
+            }
+            const size_t bytes = sizeof(mm::TcProblem) * size_t(nprob);
+            if (cudaMalloc(&b->dev[q][t], bytes) != cudaSuccess) {
+                mm_batch_destroy(b);
+                return fail(MM_ERR_OOM, "problem records");
+            }
+            cudaError_t e = cudaMemcpy(b->dev[q][t], vec.data(), bytes, cudaMemcpyHostToDevice);
+            if (e != cudaSuccess) {
+                mm_batch_destroy(b);
+                return cuda_fail(e, "problem records upload");
+            }
+        }
+    *out = b;
+    return MM_OK;
+}
+
+extern "C" mm_status mumode_batch_step(mm_batch *b, void *const *u_dev, int64_t nsteps, void *stream)
+{
+    if (!b || !u_dev) return fail(MM_ERR_INVALID_ARG, "NULL argument");
+    if (nsteps < 0) return fail(MM_ERR_INVALID_ARG, "nsteps < 0");
+    mm_status st;
+    for (size_t k = 0; k < b->plans.size(); ++k)
+        if ((st = check_ptr(u_dev[k], "u_dev[k]"))) return st;
+    if (nsteps == 0) return MM_OK;
+    cudaStream_t s = (cudaStream_t)stream;
+    const int d = b->d;
+    // split every problem (sets its state scale and first-sweep bounds)
+    for (size_t k = 0; k < b->plans.size(); ++k) {
+        mm_plan *p = b->plans[k];
+        if (p->fixed) {
+            cudaError_t e = cudaMemsetAsync(p->d_max, 0, sizeof(unsigned) * d, s);  // max words of sweep 0
+            if (e != cudaSuccess) return cuda_fail(e, "max words");
+        }
+        mm::TcMatrix *M[mm::kMaxDims];
+        for (int v = 0; v < d; ++v) M[v] = &p->Etc[v];
+        if ((st = tc_begin(p, M, u_dev[k], s))) return st;
+    }
+    for (int64_t t = 0; t < nsteps; ++t)
+        for (int q = 0; q < d; ++q) {
+            const int par = int(t & 1);
+            cudaEvent_t ev0 = timing_event(b->ctx, true);
+            if (ev0) cudaEventRecord(ev0, s);
+            cudaError_t e = mm::tc_mode_product_batched(b->host[q][par].data(), b->dev[q][par], int(b->plans.size()),
+                                                        b->kmajor[q], b->prec, mm::TcEpilogue{}, b->ctx->d_err, s);
+            if (ev0) cudaEventRecord(timing_event(b->ctx, false), s);
+            if (e != cudaSuccess) return cuda_fail(e, "batched mode product");
+        }
+    const int cur = int((nsteps * d) % 2);
+    for (size_t k = 0; k < b->plans.size(); ++k)
+        if ((st = tc_end(b->plans[k], cur, u_dev[k], s))) return st;
+    return MM_OK;
+}
+
+extern "C" void mm_batch_destroy(mm_batch *b)
+{
+    if (!b) return;
+    for (int q = 0; q < mm::kMaxDims; ++q)
+        for (int t = 0; t < 2; ++t)
+            if (b->dev[q][t]) cudaFree(b->dev[q][t]);
+    delete b;
+}

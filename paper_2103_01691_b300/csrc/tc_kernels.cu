@@ -752,6 +752,368 @@ __global__ void __launch_bounds__(kThreads, 1)
     }
 }
 
+struct TcBatchArgs {
+    int64_t total_pairs;    // work items over all problems
+    int nprob;
+    int it_max;             // widest row tile of the launch (tensor-memory allocation)
+    int stage_bytes, e_offset;
+    float tb;               // tau * beta for the nonlinear epilogue
+    int *err;
+};
+
+// Problem of work item P: the last problem whose first item is <= P.
+template <bool BATCH>
+__device__ __forceinline__ const TcProblem &problem_of(int64_t P, const TcProblem &one, const TcProblem *many,
+                                                      int nprob)
+{
+    if (!BATCH) return one;
+    int lo = 0, hi = nprob - 1;
+    while (lo < hi) {
+        const int mid = (lo + hi + 1) / 2;
+        if (many[mid].pairs_begin <= P) lo = mid;
+        else hi = mid - 1;
+    }
+    return many[lo];
+}
+
+// The kernel above generalised to a list of problems (BATCH): the same
+// persistent cluster-pair structure, with every per-problem quantity read
+// from the item's problem record.  Cluster c processes work
+// items P = c, c + #clusters, ...; item P of a problem is the row tile
+// h = P % ni of the point tiles 2 (P / ni) + rank, rank = 0, 1, so the two
+// CTAs of a cluster need the same matrix tiles at the same time: each loads
+// half of every matrix tile and multicasts it to both, and each MMA warp
+// releases a stage in both CTAs (the stage is free once both have consumed
+// it).  The TMA warp runs ahead across item boundaries; the epilogue warps
+// copy the two accumulators into registers, release tensor memory to the
+// MMA warp at once, and then scale, split and store while the next item's
+// MMAs run.  A batched launch (BATCH) covers the same direction of many
+// independent problems of different sizes; their records are in global
+// memory and each item looks its problem up.
+template <int NP, bool KMAJOR, int EPI, bool FX, bool BATCH>
+__global__ void __launch_bounds__(kThreads, 1)
+    tc_mode_kernel_batched(const __grid_constant__ TcProblem one, const TcProblem *__restrict__ many, TcBatchArgs a)
+{
+    extern __shared__ __align__(1024) uint8_t smem_raw[];
+    uint8_t *smem = reinterpret_cast<uint8_t *>((reinterpret_cast<uintptr_t>(smem_raw) + 1023) & ~uintptr_t(1023));
+    uint64_t *full = reinterpret_cast<uint64_t *>(smem + kStages * a.stage_bytes);
+    uint64_t *empty = full + kStages;
+    uint64_t *accf = empty + kStages;
+    uint64_t *tmem_empty = accf + 1;
+    uint32_t *tmem_slot = reinterpret_cast<uint32_t *>(tmem_empty + 1);
+    volatile int *abort_flag = reinterpret_cast<volatile int *>(tmem_slot + 1);
+
+    const int warp = threadIdx.x / 32, lane = threadIdx.x % 32;
+    const int acc_cols_max = 2 * a.it_max;
+    const int need = NP > 1 ? 2 * acc_cols_max : acc_cols_max;
+    const uint32_t ncols = need <= 32 ? 32 : (need <= 64 ? 64 : (need <= 128 ? 128 : (need <= 256 ? 256 : 512)));
+
+    if (threadIdx.x == 0) {
+        for (int s = 0; s < kStages; ++s) {
+            mbar_init(&full[s], 1);
+            mbar_init(&empty[s], 2);  // released by the MMA warps of both CTAs
+        }
+        mbar_init(accf, 1);
+        mbar_init(tmem_empty, kEpiWarps);
+        *abort_flag = 0;
+        mbar_fence_init();
+        if (!BATCH) {
+            tma_prefetch_desc(&one.mapX);
+            tma_prefetch_desc(&one.mapE);
+        } else if (blockIdx.x == 0) {
+            for (int q = 0; q < a.nprob; ++q)
+                if (many[q].zero_word) *many[q].zero_word = 0u;
+        }
+    }
+    if (warp == 1) {
+        tmem_alloc(tmem_slot, ncols);
+        tmem_relinquish();
+    }
+    tc_fence_before();
+    __syncthreads();
+    cluster_sync();  // the peer's barriers are initialised before any multicast reaches them
+    tc_fence_after();
+    const uint32_t tmem = *tmem_slot;
+    const int rank = int(blockIdx.x & 1);
+    const int64_t cid = blockIdx.x / 2, nclusters = gridDim.x / 2;
+
+    if (warp == 0) {
+        if (lane == 0) {
+            // ---------------- TMA producer ----------------
+            uint32_t gk = 0;  // k-blocks issued by this CTA over all items
+            for (int64_t P = cid; P < a.total_pairs && !*abort_flag; P += nclusters) {
+                const TcProblem &pr = problem_of<BATCH>(P, one, many, a.nprob);
+                const CUtensorMap *mx = &pr.mapX, *me = &pr.mapE;
+                const int64_t right = pr.right, aps = pr.aps;
+                const int ni = pr.ni, kblocks = pr.kblocks;
+                const uint32_t tx = uint32_t(pr.tx_bytes);
+                const int64_t pl = P - pr.pairs_begin;
+                const int64_t tile = (pl / ni) * 2 + rank;
+                const int h = int(pl % ni);
+                const int it = pr.it, half_rows = it / 2;
+                // TMA coordinates of this item's two 64-point atoms (MN-major), fixed over k
+                int ac_l[2] = {0, 0}, ac_r[2] = {0, 0};
+                if (!KMAJOR) {
+                    for (int q = 0; q < 2; ++q) {
+                        const int64_t atom = 2 * tile + q;
+                        int64_t r = atom / aps;
+                        if (r > right) r = right;  // past the end: zero fill
+                        ac_r[q] = int(r);
+                        ac_l[q] = int((atom % aps) * 64);
+                    }
+                }
+                // matrix tiles are stored contiguously per (piece, row tile, k-block): C, S blocks of it rows
+                const int e_row0 = h * kblocks * kBlocks * it;
+                const int e_pstride = ni * kblocks * kBlocks * it;
+                const int k_row = int(tile * kTileM);
+                for (int kb = 0; kb < kblocks; ++kb, ++gk) {
+                    const int s = int(gk % kStages);
+                    const uint32_t ph = (gk / kStages) & 1u;
+                    if (!mbar_wait(&empty[s], ph ^ 1u, a.err, MM_ERR_TIMEOUT)) {
+                        *abort_flag = 1;
+                        break;
+                    }
+                    uint8_t *st = smem + s * a.stage_bytes;
+                    mbar_arrive_expect_tx(&full[s], tx);
+                    for (int c = 0; c < 2; ++c)
+                        for (int p = 0; p < NP; ++p) {
+                            uint8_t *dst = st + (c * NP + p) * kDataTileBytes;
+                            if (KMAJOR) {
+                                tma_load_3d(mx, &full[s], dst, kb * kBK, k_row, c * NP + p);
+                            } else {
+                                tma_load_4d(mx, &full[s], dst, ac_l[0], kb * kBK, ac_r[0], c * NP + p);
+                                tma_load_4d(mx, &full[s], dst + 2048, ac_l[1], kb * kBK, ac_r[1], c * NP + p);
+                            }
+                        }
+                    // this CTA's half of every matrix block, to both CTAs
+                    uint8_t *est = st + a.e_offset + rank * half_rows * 32;
+                    for (int p = 0; p < NP; ++p)
+                        for (int w = 0; w < kBlocks; ++w)
+                            tma_load_2d_mc(me, &full[s], est + (p * kBlocks + w) * it * 32, 0,
+                                           p * e_pstride + e_row0 + (kb * kBlocks + w) * it + rank * half_rows,
+                                           0x3);
+                }
+            }
+        }
+    } else if (warp == 1) {
+        if (lane == 0) {
+            // ---------------- MMA issuer ----------------
+            uint32_t gk = 0, lt = 0;
+            for (int64_t P = cid; P < a.total_pairs && !*abort_flag; P += nclusters, ++lt) {
+                const TcProblem &pr = problem_of<BATCH>(P, one, many, a.nprob);
+                const int it = pr.it, acc_cols = 2 * it, kblocks = pr.kblocks;
+                const uint32_t idesc_full = FX ? idesc_f16_f32(kTileM, 2 * it, !KMAJOR, false)
+                                               : idesc_bf16_f32(kTileM, 2 * it, !KMAJOR, false);
+                const uint32_t idesc_half = FX ? idesc_f16_f32(kTileM, it, !KMAJOR, false)
+                                               : idesc_bf16_f32(kTileM, it, !KMAJOR, false);
+                const uint32_t idesc_half_neg = idesc_half | (1u << 13);  // negate A
+                if (lt > 0 && !mbar_wait(tmem_empty, (lt - 1) & 1u, a.err, MM_ERR_TIMEOUT)) {
+                    *abort_flag = 1;
+                    break;
+                }
+                tc_fence_after();
+                bool started[2] = {false, false};
+                for (int kb = 0; kb < kblocks; ++kb, ++gk) {
+                    const int s = int(gk % kStages);
+                    const uint32_t ph = (gk / kStages) & 1u;
+                    if (!mbar_wait(&full[s], ph, a.err, MM_ERR_TIMEOUT)) {
+                        *abort_flag = 1;
+                        break;
+                    }
+                    tc_fence_after();
+                    const uint32_t st = smem_u32(smem + s * a.stage_bytes);
+                    const uint32_t est = st + a.e_offset;
+                    // real plane: one MMA over the window [C; S] writes (re, im) columns;
+                    // imaginary plane: -Xi S into the re columns (negated A), Xi C into the im columns
+#pragma unroll
+                    for (int t = 0; t < num_terms(NP); ++t) {
+                        const int pa = term_a(t), pb = term_b(t);
+                        const int acc = (NP > 1 && (pa != 0 || pb != 0)) ? 1 : 0;
+                        const uint32_t dcol = tmem + uint32_t(acc * acc_cols);
+                        const uint32_t eC = est + (pa * kBlocks + 0) * it * 32;
+                        const uint32_t eS = est + (pa * kBlocks + 1) * it * 32;
+                        const uint32_t xre = st + (0 * NP + pb) * kDataTileBytes;
+                        const uint32_t xim = st + (1 * NP + pb) * kDataTileBytes;
+                        const uint64_t are = KMAJOR ? smem_desc(xre, 16, 256, kSwz32) : smem_desc(xre, 2048, 1024, kSwz128);
+                        const uint64_t aim = KMAJOR ? smem_desc(xim, 16, 256, kSwz32) : smem_desc(xim, 2048, 1024, kSwz128);
+                        umma_f16(dcol, are, smem_desc(eC, 16, 256, kSwz32), idesc_full, started[acc] ? 1u : 0u);
+                        started[acc] = true;
+                        umma_f16(dcol, aim, smem_desc(eS, 16, 256, kSwz32), idesc_half_neg, 1u);
+                        umma_f16(dcol + uint32_t(it), aim, smem_desc(eC, 16, 256, kSwz32), idesc_half, 1u);
+                    }
+                    umma_commit_mc(&empty[s], 0x3);
+                }
+                umma_commit(accf);
+            }
+        }
+    } else {
+        // ---------------- epilogue warps ----------------
+        const int ew = warp - 2;          // 0 .. kEpiWarps - 1
+        const int quarter = warp % 4;     // TMEM lanes 32 quarter .. + 31
+        const int grp = ew / 4;           // chunks of 16 rows: grp, grp + 4, ...
+        const int row = quarter * 32 + lane;
+        const uint32_t tbase = tmem + (uint32_t(quarter * 32) << 16);
+        bool range_ok = true;
+        uint32_t lt = 0;
+        // running maximum of |output|, flushed (one atomicMax per warp) when the problem changes
+        float local_max = 0.0f;
+        unsigned *max_word = nullptr;
+        auto flush_max = [&]() {
+            const unsigned m = __reduce_max_sync(0xffffffffu, __float_as_uint(local_max));
+            if (lane == 0 && m && max_word) atomicMax(max_word, m);
+            local_max = 0.0f;
+        };
+        for (int64_t P = cid; P < a.total_pairs; P += nclusters, ++lt) {
+            const TcProblem &pr = problem_of<BATCH>(P, one, many, a.nprob);
+            const int64_t right = pr.right, aps = pr.aps, mp = pr.mp, left = pr.left, plane_out = pr.plane_out;
+            uint16_t *const out = pr.out;
+            const float *const rho = pr.rho;
+            const int ni = pr.ni;
+            if (FX && pr.sc.max_cur != max_word) {
+                flush_max();
+                max_word = pr.sc.max_cur;
+            }
+            const int64_t pl = P - pr.pairs_begin;
+            const int64_t tile = (pl / ni) * 2 + rank;
+            const int h = int(pl % ni);
+            const int it = pr.it, acc_cols = 2 * it, nchunks = it / 16;
+            float s_in = 1.0f, inv_out = 1.0f, lim = 0.0f;
+            if (FX) {
+                s_in = *pr.sc.s_in;
+                const int es_out = grid_exponent(__uint_as_float(*pr.sc.max_prev));
+                inv_out = ldexpf(1.0f, -es_out);
+                lim = ldexpf(16384.0f, es_out);
+                if (ew == 0 && lane == 0) *pr.sc.s_out = ldexpf(1.0f, es_out);  // same value from every CTA
+            }
+            const bool acc_ready = !*abort_flag && mbar_wait(accf, lt & 1u, a.err, MM_ERR_TIMEOUT);
+            if (!acc_ready) *abort_flag = 1;
+            tc_fence_after();
+            // drain: up to kChunksPerWarp chunks of 16 rows, real and imaginary, both accumulators summed
+            float v[kChunksPerWarp][32];
+#pragma unroll
+            for (int q = 0; q < kChunksPerWarp; ++q) {
+                const int ch = grp + 4 * q;
+                if (ch < nchunks) {
+                    float t0[16], t1[16];
+                    tmem_ld16(tbase + uint32_t(ch * 16), t0);
+                    if (NP > 1) tmem_ld16(tbase + uint32_t(acc_cols + ch * 16), t1);
+                    tmem_ld_wait();
+#pragma unroll
+                    for (int k = 0; k < 16; ++k) v[q][k] = NP > 1 ? t0[k] + t1[k] : t0[k];
+                    tmem_ld16(tbase + uint32_t(it + ch * 16), t0);
+                    if (NP > 1) tmem_ld16(tbase + uint32_t(acc_cols + it + ch * 16), t1);
+                    tmem_ld_wait();
+#pragma unroll
+                    for (int k = 0; k < 16; ++k) v[q][16 + k] = NP > 1 ? t0[k] + t1[k] : t0[k];
+                }
+            }
+            tc_fence_before();
+            __syncwarp();
+            if (lane == 0) mbarrier_arrive(tmem_empty);
+            if (!acc_ready) break;
+            // this thread's point
+            bool valid;
+            int64_t r, l = 0;
+            if (KMAJOR) {
+                r = tile * kTileM + row;
+                valid = r < right;
+            } else {
+                const int64_t atom = 2 * tile + row / 64;
+                r = atom / aps;
+                l = (atom % aps) * 64 + row % 64;
+                valid = r < right && l < left;
+            }
+#pragma unroll
+            for (int q = 0; q < kChunksPerWarp; ++q) {
+                const int ch = grp + 4 * q;
+                if (ch >= nchunks || !valid) continue;
+                const int64_t i0 = int64_t(h) * it + ch * 16;
+                if (i0 >= mp) continue;
+                // scale (fixed point), nonlinear phase, range and maximum, in place
+#pragma unroll
+                for (int k = 0; k < 16; ++k) {
+                    float xr = v[q][k], xi = v[q][16 + k];
+                    if (FX) {
+                        const float g = __ldg(rho + i0 + k) * s_in;  // power of two: exact
+                        xr *= g;
+                        xi *= g;
+                    }
+                    if (EPI == 1) {
+                        const float th = a.tb * (xr * xr + xi * xi);
+                        float sn, cs;
+                        sincosf(th, &sn, &cs);
+                        const float yr = xr * cs + xi * sn, yi = xi * cs - xr * sn;
+                        xr = yr;
+                        xi = yi;
+                    }
+                    if (FX) {
+                        const float ar = fabsf(xr), ai = fabsf(xi);
+                        local_max = fmaxf(local_max, fmaxf(ar, ai));
+                        range_ok &= ar < lim && ai < lim;
+                        xr *= inv_out;
+                        xi *= inv_out;
+                    }
+                    v[q][k] = xr;
+                    v[q][16 + k] = xi;
+                }
+                // pieces of one value: fixed point (already divided by the grid) or floating BF16
+                auto pieces_of = [&](float x, uint16_t *b) {
+                    if (FX) {
+                        split_fx_scaled(x, b[0], b[1], b[2]);
+                    } else {
+#pragma unroll
+                        for (int p = 0; p < NP; ++p) {
+                            const __nv_bfloat16 h16 = __float2bfloat16_rn(x);
+                            b[p] = __bfloat16_as_ushort(h16);
+                            x -= __bfloat162float(h16);
+                        }
+                    }
+                };
+                if (KMAJOR) {
+                    // 16 consecutive outputs of one row: one 32-byte store per (plane, piece)
+                    const int64_t base = r * mp + i0;
+#pragma unroll
+                    for (int c = 0; c < 2; ++c) {
+                        uint32_t w[3][8];
+#pragma unroll
+                        for (int k2 = 0; k2 < 8; ++k2) {
+                            uint16_t b0[3], b1[3];
+                            pieces_of(v[q][16 * c + 2 * k2], b0);
+                            pieces_of(v[q][16 * c + 2 * k2 + 1], b1);
+#pragma unroll
+                            for (int p = 0; p < NP; ++p) w[p][k2] = uint32_t(b0[p]) | (uint32_t(b1[p]) << 16);
+                        }
+#pragma unroll
+                        for (int p = 0; p < NP; ++p) st_global_v8(out + int64_t(c * NP + p) * plane_out + base, w[p]);
+                    }
+                } else {
+#pragma unroll
+                    for (int k = 0; k < 16; ++k) {
+                        uint16_t br[3], bi[3];
+                        pieces_of(v[q][k], br);
+                        pieces_of(v[q][16 + k], bi);
+                        const int64_t off = (r * mp + i0 + k) * left + l;
+#pragma unroll
+                        for (int p = 0; p < NP; ++p) {
+                            out[int64_t(p) * plane_out + off] = br[p];
+                            out[int64_t(NP + p) * plane_out + off] = bi[p];
+                        }
+                    }
+                }
+            }
+        }
+        if (FX) flush_max();
+        if (FX && !range_ok && a.err) atomicCAS(a.err, 0, MM_ERR_RANGE);
+    }
+    tc_fence_before();
+    __syncthreads();
+    cluster_sync();  // no CTA leaves while its peer may still write into its shared memory
+    if (warp == 1) {
+        tc_fence_after();
+        tmem_dealloc(tmem, ncols);
+    }
+}
+
 // ---- host: tensor maps and launch -------------------------------------------------------
 
 using EncodeTiledFn = CUresult (*)(CUtensorMap *, CUtensorMapDataType, cuuint32_t, void *, const cuuint64_t *,
@@ -900,6 +1262,132 @@ cudaError_t tc_mode_product(const TcState &si, const TcState &so, int mu, const 
     case 2: return dispatch_np<2, false>(km, epi.kind, mx, me, a, int(grid), smem, s);
     default: return dispatch_np<1, false>(km, epi.kind, mx, me, a, int(grid), smem, s);
     }
+}
+
+template <int NP, bool KM, int EPI, bool FX, bool BATCH>
+static cudaError_t launch_tcb(const TcProblem &one, const TcProblem *many, const TcBatchArgs &a, int smem, cudaStream_t s)
+{
+    auto kern = tc_mode_kernel_batched<NP, KM, EPI, FX, BATCH>;
+    cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
+    if (e != cudaSuccess) return e;
+    const int64_t grid = 2 * (a.total_pairs < num_sms() / 2 ? a.total_pairs : num_sms() / 2);
+    cudaLaunchConfig_t cfg = {};
+    cfg.gridDim = dim3(unsigned(grid));
+    cfg.blockDim = dim3(kThreads);
+    cfg.dynamicSmemBytes = size_t(smem);
+    cfg.stream = s;
+    cudaLaunchAttribute attr[1];
+    attr[0].id = cudaLaunchAttributeClusterDimension;
+    attr[0].val.clusterDim.x = 2;
+    attr[0].val.clusterDim.y = 1;
+    attr[0].val.clusterDim.z = 1;
+    cfg.attrs = attr;
+    cfg.numAttrs = 1;
+    // persistent grid: no more clusters than can be resident at once
+    int active = 0;
+    if (cudaOccupancyMaxActiveClusters(&active, kern, &cfg) == cudaSuccess && active > 0 && 2 * active < grid)
+        cfg.gridDim = dim3(unsigned(2 * active));
+    e = cudaLaunchKernelEx(&cfg, kern, one, many, a);
+    count_launch();
+    if (e != cudaSuccess) return e;
+    return cudaGetLastError();
+}
+
+template <int NP, bool FX, bool BATCH>
+static cudaError_t dispatch_npb(bool km, int epi, const TcProblem &one, const TcProblem *many, const TcBatchArgs &a,
+                                int smem, cudaStream_t s)
+{
+    if (km)
+        return epi ? launch_tcb<NP, true, 1, FX, BATCH>(one, many, a, smem, s)
+                   : launch_tcb<NP, true, 0, FX, BATCH>(one, many, a, smem, s);
+    return epi ? launch_tcb<NP, false, 1, FX, BATCH>(one, many, a, smem, s)
+               : launch_tcb<NP, false, 0, FX, BATCH>(one, many, a, smem, s);
+}
+
+cudaError_t tc_problem_build(const TcState &si, const TcState &so, int mu, const TcMatrix &M, mm_prec prec,
+                             const void *in_pieces, void *out_pieces, const TcScales &sc, TcProblem *pr, bool *kmajor)
+{
+    const int NP = tc_pieces(prec);
+    const bool fx = tc_fixed(prec);
+    if (NP == 0 || NP != M.npieces || fx != M.fixed) return cudaErrorInvalidValue;
+    if (fx && (!sc.s_in || !sc.s_out || !sc.max_prev || !sc.max_cur || !M.rho)) return cudaErrorInvalidValue;
+    TcProblem q;
+    std::memset(&q, 0, sizeof q);
+    q.left = 1;
+    q.right = 1;
+    for (int v = 0; v < mu - 1; ++v) q.left *= si.np[v];
+    for (int v = mu; v < si.d; ++v) q.right *= si.np[v];
+    const int64_t kp = si.np[mu - 1];
+    q.mp = so.np[mu - 1];
+    if (kp != M.k_pad) return cudaErrorInvalidValue;
+    q.aps = (q.left + 63) / 64;
+    q.plane_out = so.plane;
+    q.it = M.it;
+    q.ni = M.ni;
+    q.kblocks = int(kp / kBK);
+    q.tx_bytes = 2 * NP * kDataTileBytes + NP * kBlocks * M.it * 32;
+    q.out = (uint16_t *)out_pieces;
+    q.rho = M.rho;
+    q.sc = sc;
+    const bool km = q.left == 1;
+    void *xin = const_cast<void *>(in_pieces);
+    if (km) {
+        cuuint64_t dims[3] = {cuuint64_t(kp), cuuint64_t(q.right), cuuint64_t(2 * NP)};
+        cuuint64_t str[2] = {cuuint64_t(kp * 2), cuuint64_t(si.plane * 2)};
+        cuuint32_t box[3] = {kBK, kTileM, 1};
+        if (!encode(&q.mapX, xin, 3, dims, str, box, CU_TENSOR_MAP_SWIZZLE_32B)) return cudaErrorInvalidValue;
+    } else {
+        cuuint64_t dims[4] = {cuuint64_t(q.left), cuuint64_t(kp), cuuint64_t(q.right), cuuint64_t(2 * NP)};
+        cuuint64_t str[3] = {cuuint64_t(q.left * 2), cuuint64_t(q.left * kp * 2), cuuint64_t(si.plane * 2)};
+        cuuint32_t box[4] = {64, kBK, 1, 1};
+        if (!encode(&q.mapX, xin, 4, dims, str, box, CU_TENSOR_MAP_SWIZZLE_128B)) return cudaErrorInvalidValue;
+    }
+    {
+        const int64_t rows = int64_t(NP) * M.ni * (M.k_pad / 16) * kBlocks * M.it;
+        cuuint64_t dims[2] = {16, cuuint64_t(rows)};
+        cuuint64_t str[1] = {32};
+        cuuint32_t box[2] = {kBK, cuuint32_t(M.it / 2)};  // each CTA of a pair loads half the rows
+        if (!encode(&q.mapE, M.pieces, 2, dims, str, box, CU_TENSOR_MAP_SWIZZLE_32B)) return cudaErrorInvalidValue;
+    }
+    const int64_t tiles = km ? (q.right + kTileM - 1) / kTileM : (q.right * q.aps + 1) / 2;
+    q.pairs = (tiles + 1) / 2 * q.ni;
+    *pr = q;
+    *kmajor = km;
+    return cudaSuccess;
+}
+
+static cudaError_t launch_batched(int NP, bool fx, bool km, int epi, const TcProblem &one, const TcProblem *many,
+                                  const TcBatchArgs &a, int smem, cudaStream_t s)
+{
+    if (fx) return dispatch_npb<3, true, true>(km, epi, one, many, a, smem, s);
+    switch (NP) {
+    case 3: return dispatch_npb<3, false, true>(km, epi, one, many, a, smem, s);
+    case 2: return dispatch_npb<2, false, true>(km, epi, one, many, a, smem, s);
+    default: return dispatch_npb<1, false, true>(km, epi, one, many, a, smem, s);
+    }
+}
+
+static int stage_bytes_for(int tx_bytes) { return (tx_bytes + 1023) / 1024 * 1024; }
+
+cudaError_t tc_mode_product_batched(const TcProblem *host_probs, const TcProblem *dev_probs, int nprob, bool kmajor,
+                                    mm_prec prec, const TcEpilogue &epi, int *d_err, cudaStream_t s)
+{
+    if (nprob < 1) return cudaSuccess;
+    const int NP = tc_pieces(prec);
+    TcBatchArgs a{};
+    int max_tx = 0;
+    for (int q = 0; q < nprob; ++q) {
+        a.total_pairs = std::max(a.total_pairs, host_probs[q].pairs_begin + host_probs[q].pairs);
+        a.it_max = std::max(a.it_max, host_probs[q].it);
+        max_tx = std::max(max_tx, host_probs[q].tx_bytes);
+    }
+    a.nprob = nprob;
+    a.e_offset = 2 * NP * kDataTileBytes;
+    a.stage_bytes = stage_bytes_for(max_tx);
+    a.tb = float(epi.tb);
+    a.err = d_err;
+    const int smem = kStages * a.stage_bytes + 1024 + 256;
+    return launch_batched(NP, tc_fixed(prec), kmajor, epi.kind, host_probs[0], dev_probs, a, smem, s);
 }
 
 }  // namespace mm

@@ -47,6 +47,9 @@ SIGNATURES = {
     "mumode_step_host": (_i, [_vp, _vp, _i64, _vp]),
     "mm_plan_destroy": (None, [_vp]),
     "mm_plan_set_graphs": (_i, [_vp, _i]),
+    "mumode_batch_create": (_i, [_vp, ctypes.POINTER(_vp), _i, ctypes.POINTER(_vp)]),
+    "mumode_batch_step": (_i, [_vp, ctypes.POINTER(_vp), _i64, _vp]),
+    "mm_batch_destroy": (None, [_vp]),
     "hermite_plan_create": (_i, [_vp, _i, _i64p, _i, _i, ctypes.POINTER(_vp)]),
     "hermite_nodes": (_i, [_vp, _i, _dp, _dp]),
     "hermite_forward": (_i, [_vp, _vp, _vp, _vp]),
@@ -284,6 +287,36 @@ class TuckerPlan:
     def close(self):
         if self.handle:
             lib().mm_plan_destroy(self.handle)
+            self.handle = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+
+class Batch:
+    """Independent Tucker plans stepped together, one launch per direction."""
+
+    def __init__(self, ctx: Context, plans):
+        self.ctx = ctx
+        self.plans = list(plans)  # keeps the plans alive
+        arr = (_vp * len(self.plans))(*[p.handle.value for p in self.plans])
+        h = ctypes.c_void_p()
+        _check(lib().mumode_batch_create(ctx.handle, arr, len(self.plans), ctypes.byref(h)))
+        self.handle = h
+
+    def step(self, us, nsteps: int = 1, stream=None):
+        for u in us:
+            _need_cuda(u)
+        arr = (_vp * len(us))(*[u.data_ptr() for u in us])
+        _check(lib().mumode_batch_step(self.handle, arr, int(nsteps), _stream(stream)))
+        return us
+
+    def close(self):
+        if self.handle:
+            lib().mm_batch_destroy(self.handle)
             self.handle = None
 
     def __del__(self):

@@ -329,3 +329,34 @@ def test_gpe_autograd_gradient(env, orc):
     pTo = orc.gpe_steps(psi0, xo, Wo, beta, tau, steps)
     ref = orc.gpe_adjoint(psi0, 2.0 * orc.weight3(Wo) * (pTo - inputs.gpe_target(xo, Wo)), xo, Wo, beta, tau, steps)
     assert rel(p.grad.cpu().numpy(), ref) <= 1e-10
+
+
+# ------------------------------------------------------- batched uneven problems
+
+def test_batched_uneven_problems(env, orc):
+    """Independent problems of uneven sizes (48..160 per direction) stepped
+    in one launch per direction: identical to stepping each plan alone, and
+    within tolerance of the oracle."""
+    mm, ctx, torch = env
+    dims = inputs.batched_dims(count=64, seed=3)[:6]
+    us0 = inputs.batched_u0(inputs.batched_dims(count=64, seed=3), seed=3)[:6]
+    tau, steps = 1e-4, 3
+    plans, us, alone = [], [], []
+    for (n1, n2, n3), u0 in zip(dims, us0):
+        nd = (int(n1), int(n2), int(n3))
+        Es = [fd_schrodinger_E(mm, n, tau) for n in nd]
+        plans.append(mm.TuckerPlan(ctx, nd, Es, prec="f16x6"))
+        us.append(to_gpu(torch, u0.astype(np.complex64), torch.complex64))
+        alone.append(to_gpu(torch, u0.astype(np.complex64), torch.complex64))
+    batch = mm.Batch(ctx, plans)
+    batch.step(us, steps)
+    for p, u in zip(plans, alone):
+        p.step(u, steps)
+    torch.cuda.synchronize()
+    for k in range(len(plans)):
+        assert torch.equal(us[k], alone[k]), k
+    for k in (0, len(plans) - 1):
+        nd = tuple(int(v) for v in dims[k])
+        ref = orc.tucker(us0[k].astype(np.complex64).astype(complex),
+                         [orc.expm_dirichlet_fd(n, 1j * tau) for n in nd], nsteps=steps)
+        assert rel(us[k].cpu().numpy(), ref) <= TOL_MODE["f16x6"] * 3 * steps
