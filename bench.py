@@ -173,8 +173,14 @@ def main():
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-fp64", action="store_true")
+    ap.add_argument("--workload", default="free256",
+                    choices=["free256", "heat32", "ho128", "batched64", "gpe192"],
+                    help="free256 (default) is the headline line; the others time the remaining workloads")
     args = ap.parse_args()
     rank, world, local = dist_env()
+    if args.workload != "free256":
+        other_workload(args)
+        return
 
     if args.impl == "reference":
         run_reference(args, rank, world)
@@ -336,6 +342,102 @@ def main():
         print(json.dumps(line), flush=True)
     if dist:
         dist.destroy_process_group()
+
+
+def _time(fn, stream):
+    import torch
+
+    e0 = torch.cuda.Event(enable_timing=True)
+    e1 = torch.cuda.Event(enable_timing=True)
+    torch.cuda.synchronize()
+    e0.record(stream)
+    fn()
+    e1.record(stream)
+    torch.cuda.synchronize()
+    return e0.elapsed_time(e1)
+
+
+def other_workload(args):
+    """Steps/s of the other workloads (one JSON line each, 1 GPU)."""
+    import torch
+
+    from paper_2103_01691_b300 import build as mmbuild
+    from paper_2103_01691_b300 import inputs
+
+    mmbuild.build()
+    from paper_2103_01691_b300 import mumode as mm
+
+    ctx = mm.Context(0)
+    stream = torch.cuda.Stream()
+    torch.cuda.set_stream(stream)
+    line = {"workload": args.workload, "unit": "steps/s", "higher_is_better": True, "data": "synthetic"}
+    if args.workload == "heat32":
+        n, tau, K = 32, 1e-3, 10
+        E = mm.expm(mm.fd_laplacian_dirichlet(n), tau).real
+        plan = mm.TuckerPlan(ctx, [n] * 3, [E] * 3, prec="fp64", dtype=torch.float64)
+        u = torch.from_numpy(inputs.heat_u0(n, seed=0)).cuda()
+        plan.step(u, K)
+        ms = _time(lambda: plan.step(u, K), stream)
+        line.update(value=K / (ms / 1e3), steps=K, precision="fp64", config="heat FD2 n=32^3 real, tau=1e-3")
+    elif args.workload == "ho128":
+        n, tau, K = 128, 0.01, 100
+        for prec in ("f16x6", "fp64"):
+            plan = mm.HermitePlan(ctx, [n] * 3, prec=prec)
+            x, W = plan.nodes(1)
+            dt = torch.complex128 if prec == "fp64" else torch.complex64
+            psi = torch.from_numpy(inputs.harmonic_psi0(x, W, seed=1)).to(dt).cuda()
+            k = K if prec != "fp64" else 2
+            plan.ho_step(psi, tau, k)
+            ms = _time(lambda: plan.ho_step(psi, tau, k), stream)
+            line[prec] = {"steps_per_s": k / (ms / 1e3), "steps": k}
+        line.update(value=line["f16x6"]["steps_per_s"], precision="f16x6",
+                    config="harmonic oscillator, Hermite n=128^3 complex64, tau=0.01 (folded propagators)")
+    elif args.workload == "gpe192":
+        n, beta, tau, K = 192, 100.0, 1e-3, 500
+        plan = mm.HermitePlan(ctx, [n] * 3, prec="f16x6")
+        x, W = plan.nodes(1)
+        psi0 = torch.from_numpy(inputs.gpe_psi0(x, W, seed=4).astype(np.complex64)).cuda()
+        psi = psi0.clone()
+        plan.gpe_step(psi, beta, tau, K)
+        ms = _time(lambda: plan.gpe_step(psi, beta, tau, K), stream)
+        gT = torch.randn_like(psi0)
+        ms_adj = _time(lambda: plan.gpe_adjoint(psi0, gT, beta, tau, 100, ckpt_every=50), stream)
+        line.update(value=K / (ms / 1e3), steps=K, precision="f16x6",
+                    adjoint_ms_per_step=ms_adj / 100,
+                    config="GPE Strang, Hermite n=192^3 complex64, beta=100, tau=1e-3; adjoint 100 steps, ckpt 50")
+    else:  # batched64
+        dims = inputs.batched_dims(64, seed=3)
+        u0s = inputs.batched_u0(dims, seed=3)
+        tau, K = 1e-4, 200
+        plans, us = [], []
+        for (n1, n2, n3), u0 in zip(dims, u0s):
+            nd = (int(n1), int(n2), int(n3))
+            Es = [mm.expm(mm.fd_laplacian_dirichlet(v), 1j * tau) for v in nd]
+            plans.append(mm.TuckerPlan(ctx, nd, Es, prec="f16x6"))
+            us.append(torch.from_numpy(u0.astype(np.complex64)).cuda())
+        batch = mm.Batch(ctx, plans)
+        batch.step(us, 5)
+        ms_b = _time(lambda: batch.step(us, K), stream)
+
+        def each():
+            for p, u in zip(plans, us):
+                p.step(u, K)
+
+        each()
+        ms_e = _time(each, stream)
+        # plain FP64 per-instance launches, one step each
+        p64 = []
+        for (n1, n2, n3), u0 in zip(dims, u0s):
+            nd = (int(n1), int(n2), int(n3))
+            Es = [mm.expm(mm.fd_laplacian_dirichlet(v), 1j * tau) for v in nd]
+            p64.append((mm.TuckerPlan(ctx, nd, Es, prec="fp64"), torch.from_numpy(u0).cuda()))
+        ms_64 = _time(lambda: [p.step(u, 1) for p, u in p64], stream)
+        flop = sum(8.0 * float(np.prod(d)) * float(np.sum(d)) for d in dims)
+        line.update(value=K / (ms_b / 1e3), steps=K, precision="f16x6", problems=64,
+                    per_plan_graphs_steps_per_s=K / (ms_e / 1e3), fp64_per_instance_steps_per_s=1e3 / ms_64,
+                    tflops_algorithmic=flop * K / (ms_b / 1e3) / 1e12,
+                    config="64 FD Schroedinger problems, sizes 48..160 per direction (seed 3), tau=1e-4")
+    print(json.dumps(line), flush=True)
 
 
 if __name__ == "__main__":
