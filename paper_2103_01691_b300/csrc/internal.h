@@ -59,6 +59,7 @@ struct TcMatrix {
     bool fixed = false;             // MM_PREC_F16X6 pieces
     float *rho = nullptr;           // fixed: power-of-two scale of each row (ni * it floats)
     double row_norm = 0.0;          // max_i sum_j |E_ij|, bounds the growth of one product
+    int kb_lo[2] = {0, 0}, kb_hi[2] = {0, 0};  // per row tile: k-blocks with a nonzero piece
 };
 
 // Device words that carry the state scale of MM_PREC_F16X6 through a sweep.
@@ -103,6 +104,7 @@ struct alignas(64) TcProblem {
     int64_t pairs_begin;    // first work item of this problem in a batched launch
     int64_t pairs;          // work items: (pair of point tiles, row tile)
     int it, ni, kblocks, tx_bytes;
+    int kb_lo[2], kb_hi[2];  // per row tile: k-blocks with a nonzero matrix piece
     uint16_t *out;
     const float *rho;       // fixed-point row scales
     TcScales sc;

@@ -175,6 +175,29 @@ mm_status tc_matrix_host(const double *E, int64_t m, int64_t n, int npieces, boo
             }
         }
     }
+    // k-block band of each row tile: blocks outside it are exactly zero in
+    // every piece, so their products add nothing and are skipped
+    const int64_t kbs = M.k_pad / 16;
+    for (int tile = 0; tile < M.ni; ++tile) {
+        int lo = int(kbs), hi = 0;
+        for (int p = 0; p < npieces; ++p)
+            for (int64_t kb = 0; kb < kbs; ++kb) {
+                const int64_t row0 = (((int64_t(p) * M.ni + tile) * kbs + kb) * kBlocks) * M.it;
+                const uint16_t *blk = h.data() + size_t(row0 * 16);
+                bool any = false;
+                for (int64_t q = 0; q < int64_t(kBlocks) * M.it * 16 && !any; ++q) any = (blk[q] & 0x7fffu) != 0;
+                if (any) {
+                    lo = std::min(lo, int(kb));
+                    hi = std::max(hi, int(kb) + 1);
+                }
+            }
+        if (lo >= hi) {  // an all-zero tile still runs one block (of zeros) to define its accumulators
+            lo = 0;
+            hi = 1;
+        }
+        M.kb_lo[tile] = lo;
+        M.kb_hi[tile] = hi;
+    }
     *geom = M;
     return MM_OK;
 }
@@ -427,6 +450,7 @@ struct TcArgs {
     int64_t pairs;          // work items of a CTA pair: (pair of point tiles, row tile)
     int64_t tiles;          // point tiles
     int it, ni, kblocks;
+    int kb_lo[2], kb_hi[2];  // k-blocks where the row tile's matrix pieces are not all zero
     int stage_bytes, tx_bytes, e_offset;
     float tb;               // tau * beta for the nonlinear epilogue
     uint16_t *out;
@@ -519,7 +543,7 @@ __global__ void __launch_bounds__(kThreads, 1)
                 const int e_row0 = h * a.kblocks * kBlocks * a.it;
                 const int e_pstride = a.ni * a.kblocks * kBlocks * a.it;
                 const int k_row = int(tile * kTileM);
-                for (int kb = 0; kb < a.kblocks; ++kb, ++gk) {
+                for (int kb = a.kb_lo[h]; kb < a.kb_hi[h]; ++kb, ++gk) {
                     const int s = int(gk % kStages);
                     const uint32_t ph = (gk / kStages) & 1u;
                     if (!mbar_wait(&empty[s], ph ^ 1u, a.err, MM_ERR_TIMEOUT)) {
@@ -558,13 +582,14 @@ __global__ void __launch_bounds__(kThreads, 1)
             const uint32_t idesc_half_neg = idesc_half | (1u << 13);  // negate A
             uint32_t gk = 0, lt = 0;
             for (int64_t P = cid; P < a.pairs && !*abort_flag; P += nclusters, ++lt) {
+                const int h = int(P % a.ni);
                 if (lt > 0 && !mbar_wait(tmem_empty, (lt - 1) & 1u, a.err, MM_ERR_TIMEOUT)) {
                     *abort_flag = 1;
                     break;
                 }
                 tc_fence_after();
                 bool started[2] = {false, false};
-                for (int kb = 0; kb < a.kblocks; ++kb, ++gk) {
+                for (int kb = a.kb_lo[h]; kb < a.kb_hi[h]; ++kb, ++gk) {
                     const int s = int(gk % kStages);
                     const uint32_t ph = (gk / kStages) & 1u;
                     if (!mbar_wait(&full[s], ph, a.err, MM_ERR_TIMEOUT)) {
@@ -866,7 +891,7 @@ __global__ void __launch_bounds__(kThreads, 1)
                 const int e_row0 = h * kblocks * kBlocks * it;
                 const int e_pstride = ni * kblocks * kBlocks * it;
                 const int k_row = int(tile * kTileM);
-                for (int kb = 0; kb < kblocks; ++kb, ++gk) {
+                for (int kb = pr.kb_lo[h]; kb < pr.kb_hi[h]; ++kb, ++gk) {
                     const int s = int(gk % kStages);
                     const uint32_t ph = (gk / kStages) & 1u;
                     if (!mbar_wait(&empty[s], ph ^ 1u, a.err, MM_ERR_TIMEOUT)) {
@@ -901,7 +926,9 @@ __global__ void __launch_bounds__(kThreads, 1)
             uint32_t gk = 0, lt = 0;
             for (int64_t P = cid; P < a.total_pairs && !*abort_flag; P += nclusters, ++lt) {
                 const TcProblem &pr = problem_of<BATCH>(P, one, many, a.nprob);
-                const int it = pr.it, acc_cols = 2 * it, kblocks = pr.kblocks;
+                const int it = pr.it, acc_cols = 2 * it;
+                const int hh = int((P - pr.pairs_begin) % pr.ni);
+                const int kb_lo = pr.kb_lo[hh], kb_hi = pr.kb_hi[hh];
                 const uint32_t idesc_full = FX ? idesc_f16_f32(kTileM, 2 * it, !KMAJOR, false)
                                                : idesc_bf16_f32(kTileM, 2 * it, !KMAJOR, false);
                 const uint32_t idesc_half = FX ? idesc_f16_f32(kTileM, it, !KMAJOR, false)
@@ -913,7 +940,7 @@ __global__ void __launch_bounds__(kThreads, 1)
                 }
                 tc_fence_after();
                 bool started[2] = {false, false};
-                for (int kb = 0; kb < kblocks; ++kb, ++gk) {
+                for (int kb = kb_lo; kb < kb_hi; ++kb, ++gk) {
                     const int s = int(gk % kStages);
                     const uint32_t ph = (gk / kStages) & 1u;
                     if (!mbar_wait(&full[s], ph, a.err, MM_ERR_TIMEOUT)) {
@@ -1219,6 +1246,10 @@ cudaError_t tc_mode_product(const TcState &si, const TcState &so, int mu, const 
     a.it = M.it;
     a.ni = M.ni;
     a.kblocks = int(a.kp / kBK);
+    for (int h = 0; h < 2; ++h) {
+        a.kb_lo[h] = h < M.ni ? M.kb_lo[h] : 0;
+        a.kb_hi[h] = h < M.ni ? M.kb_hi[h] : 1;
+    }
     a.e_offset = 2 * NP * kDataTileBytes;
     a.tx_bytes = a.e_offset + NP * kBlocks * M.it * 32;
     a.stage_bytes = (a.tx_bytes + 1023) / 1024 * 1024;
@@ -1325,6 +1356,10 @@ cudaError_t tc_problem_build(const TcState &si, const TcState &so, int mu, const
     q.it = M.it;
     q.ni = M.ni;
     q.kblocks = int(kp / kBK);
+    for (int h = 0; h < 2; ++h) {
+        q.kb_lo[h] = h < M.ni ? M.kb_lo[h] : 0;
+        q.kb_hi[h] = h < M.ni ? M.kb_hi[h] : 1;
+    }
     q.tx_bytes = 2 * NP * kDataTileBytes + NP * kBlocks * M.it * 32;
     q.out = (uint16_t *)out_pieces;
     q.rho = M.rho;
