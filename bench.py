@@ -255,10 +255,9 @@ def main():
     value = world * args.steps / (ms / 1e3)
     ms_per_step = ms / args.steps
     kern_avg_s = kern_ms / max(kern_n, 1) / 1e3
-    pieces = {"f16x6": 3, "bf16x6": 3, "bf16x3": 2, "bf16": 1}.get(args.prec, 0)
-    products = {3: 6, 2: 3, 1: 1}.get(pieces, 1)
     achieved = FLOP_PER_MODE / kern_avg_s / 1e12
-    issued = achieved * products
+    issued_per_step = plan.issued_flops()
+    issued = issued_per_step / 3 / kern_avg_s / 1e12
 
     # end to end through the public host API: one 50-step trajectory per call
     u_host = torch.from_numpy(u0.copy()).pin_memory()
@@ -324,6 +323,7 @@ def main():
                          "frac": achieved / tc_peak, "traffic": None,
                          "kernel": "tc_mode_kernel (one mode product)", "peak_source": f"bf16 burst (f16 same rate), {peak_src}",
                          "issued_tflops": issued, "issued_frac": issued / tc_peak,
+                         "issued_flop_per_step": issued_per_step,
                          "alg_bytes_per_launch": ALG_BYTES_PER_MODE,
                          "hbm_frac_alg": ALG_BYTES_PER_MODE / kern_avg_s / 1e9 / hbm_peak,
                          "kernel_avg_us": kern_avg_s * 1e6, "kernel_launches_timed": kern_n,

@@ -241,6 +241,12 @@ void mm_plan_destroy(mm_plan *plan);
  * kernel timing is on.  Turning graphs off frees the cached graphs. */
 mm_status mm_plan_set_graphs(mm_plan *plan, int enable);
 
+/* Tensor-core flops (2 M N K summed over the issued MMAs) of one step of a
+ * tensor-core Tucker plan: all piece products, the zero padding, and none
+ * of the matrix blocks skipped because every piece of them is zero.  For
+ * roofline accounting.  MM_ERR_INVALID_ARG for other plans. */
+mm_status mm_plan_issued_flops(const mm_plan *plan, double *flops_per_step);
+
 /* ---------------------------------------------------------------------
  * Batches of independent problems (not in the paper): many Tucker plans of
  * different sizes stepped together, every direction of every problem in

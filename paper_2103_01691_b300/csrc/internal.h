@@ -94,7 +94,7 @@ cudaError_t tc_merge(const TcState &st, int npieces, bool fixed, const void *pie
 // One problem of a tensor-core launch: its two tensor maps (64-byte
 // aligned, as TMA requires of a tensor map in memory) and its sizes,
 // buffers and scales.  Built by tc_problem_build.
-struct alignas(64) TcProblem {
+struct TcProblem {  // the CUtensorMap members carry the 64-byte alignment TMA needs
     CUtensorMap mapX;       // split input state
     CUtensorMap mapE;       // matrix pieces
     int64_t left, right;    // padded sizes of the fast / slow index groups
@@ -120,6 +120,9 @@ struct TcEpilogue {
 cudaError_t tc_mode_product(const TcState &st_in, const TcState &st_out, int mu, const TcMatrix &M,
                             mm_prec prec, const void *in_pieces, void *out_pieces,
                             const TcEpilogue &epi, const TcScales &sc, int *d_err, cudaStream_t s);
+// Tensor-core flops (2 M N K per MMA) one product issues, padding and the
+// skipped zero blocks included.
+double tc_issued_flops(const TcState &st_in, int mu, const TcMatrix &M, mm_prec prec);
 // The record of one such product, for a batched launch (kmajor: direction 1).
 cudaError_t tc_problem_build(const TcState &st_in, const TcState &st_out, int mu, const TcMatrix &M, mm_prec prec,
                              const void *in_pieces, void *out_pieces, const TcScales &sc, TcProblem *pr, bool *kmajor);

@@ -482,6 +482,19 @@ mm_status run_graphed(mm_plan *p, int kind, const void *ptr, int64_t nsteps, cud
 
 extern "C" {
 
+mm_status mm_plan_issued_flops(const mm_plan *p, double *flops_per_step)
+{
+    if (!p || !flops_per_step) return fail(MM_ERR_INVALID_ARG, "NULL argument");
+    if (!p->tc || p->hermite) return fail(MM_ERR_INVALID_ARG, "needs a tensor-core Tucker plan");
+    double f = 0.0;
+    for (int q = 0; q < p->d; ++q) {
+        const int mu = p->order[q];
+        f += mm::tc_issued_flops(p->st, mu, p->Etc[mu - 1], p->prec);
+    }
+    *flops_per_step = f;
+    return MM_OK;
+}
+
 mm_status mm_plan_set_graphs(mm_plan *p, int enable)
 {
     if (!p) return fail(MM_ERR_INVALID_ARG, "plan is NULL");

@@ -1425,4 +1425,22 @@ cudaError_t tc_mode_product_batched(const TcProblem *host_probs, const TcProblem
     return launch_batched(NP, tc_fixed(prec), kmajor, epi.kind, host_probs[0], dev_probs, a, smem, s);
 }
 
+// Tensor-core flops one product issues: every MMA counted as 2 M N K, per
+// work item its k-block band times the products of the precision.
+double tc_issued_flops(const TcState &si, int mu, const TcMatrix &M, mm_prec prec)
+{
+    const int NP = tc_pieces(prec);
+    int64_t left = 1, right = 1;
+    for (int v = 0; v < mu - 1; ++v) left *= si.np[v];
+    for (int v = mu; v < si.d; ++v) right *= si.np[v];
+    const int64_t aps = (left + 63) / 64;
+    const int64_t tiles = left == 1 ? (right + kTileM - 1) / kTileM : (right * aps + 1) / 2;
+    const int64_t tiles_run = (tiles + 1) / 2 * 2;  // CTA pairs
+    double per_kb = 0.0;  // one k-block of one item: re plane N = 2 it, im plane 2 x N = it, K = 16
+    per_kb = double(num_terms(NP)) * (2.0 * kTileM * (2 * M.it) * kBK + 2.0 * (2.0 * kTileM * M.it * kBK));
+    double total = 0.0;
+    for (int h = 0; h < M.ni; ++h) total += double(tiles_run) * double(M.kb_hi[h] - M.kb_lo[h]) * per_kb;
+    return total;
+}
+
 }  // namespace mm

@@ -47,6 +47,7 @@ SIGNATURES = {
     "mumode_step_host": (_i, [_vp, _vp, _i64, _vp]),
     "mm_plan_destroy": (None, [_vp]),
     "mm_plan_set_graphs": (_i, [_vp, _i]),
+    "mm_plan_issued_flops": (_i, [_vp, _dp]),
     "mumode_batch_create": (_i, [_vp, ctypes.POINTER(_vp), _i, ctypes.POINTER(_vp)]),
     "mumode_batch_step": (_i, [_vp, ctypes.POINTER(_vp), _i64, _vp]),
     "mm_batch_destroy": (None, [_vp]),
@@ -261,6 +262,12 @@ class TuckerPlan:
         _check(lib().mumode_plan_create(ctx.handle, d, self.dims.ctypes.data_as(_i64p), ptrs, int(cplx), code,
                                         PREC[prec], optr, ctypes.byref(h)))
         self.handle = h
+
+    def issued_flops(self) -> float:
+        """Tensor-core flops issued per step (see mm_plan_issued_flops)."""
+        f = ctypes.c_double()
+        _check(lib().mm_plan_issued_flops(self.handle, ctypes.byref(f)))
+        return f.value
 
     def set_graphs(self, enable: bool):
         _check(lib().mm_plan_set_graphs(self.handle, int(enable)))
