@@ -105,6 +105,25 @@ def dist_env():
     return rank, world, local
 
 
+def max_over_ranks(value: float, dist) -> float:
+    """Largest value over all ranks (the timed region of the slowest rank)."""
+    if dist is None or not dist.is_initialized() or dist.get_world_size() == 1:
+        return value
+    import torch
+
+    dev = "cuda" if dist.get_backend() == "nccl" else "cpu"
+    t = torch.tensor([value], dtype=torch.float64, device=dev)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
+def shard(count: int, rank: int, world: int) -> range:
+    """Contiguous share of `count` independent units for `rank` (no collective needed)."""
+    base, extra = divmod(count, world)
+    start = rank * base + min(rank, extra)
+    return range(start, start + base + (1 if rank < extra else 0))
+
+
 def oracle_step_sample(u0: np.ndarray, E: np.ndarray, frac_slabs: int):
     """FP64 CPU oracle on 1/frac of one full step: directions 1 and 2 on
     256/frac of the i3-slabs, direction 3 on 1/frac of the (i1, i2) pencils.
@@ -250,10 +269,7 @@ def main():
     kern_ms, kern_n = ctx.kernel_timing_read()
     ctx.kernel_timing(False)
     ctx.status()
-    if dist:
-        t = torch.tensor([ms], device="cuda")
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        ms = float(t.item())
+    ms = max_over_ranks(ms, dist)
 
     value = world * args.steps / (ms / 1e3)
     ms_per_step = ms / args.steps
