@@ -59,6 +59,7 @@
 #include <algorithm>
 #include <cmath>
 #include <cstdint>
+#include <cstdlib>
 #include <cstring>
 #include <vector>
 
@@ -202,24 +203,111 @@ mm_status tc_matrix_host(const double *E, int64_t m, int64_t n, int npieces, boo
     return MM_OK;
 }
 
+// Row tile of the CTA-pair kernel: at most 64 rows (N = 128 MMAs, two
+// accumulator sets in tensor memory, so an item's MMAs overlap the drain of
+// the previous item), or with MM_PAIR_TILE=128 in the environment at most
+// 128 (N = 256 MMAs, one accumulator set), kept for comparison.  Read when
+// a matrix is created.
+static int64_t pair_tile_rows()
+{
+    const char *v = std::getenv("MM_PAIR_TILE");
+    return (v && std::atoi(v) == 128) ? 128 : 64;
+}
+
+// Rearrange the pieces for the CTA-pair kernel, which tiles the rows in
+// ni2 tiles of it2 rows: per (piece, row tile, k-block) CTA rank r of
+// the pair gets the rows r it2/2 .. (r + 1) it2/2 - 1 of the tile as three
+// blocks -S, C, S, so that [C; S] and [-S; C] are windows of it2 rows at the
+// same offsets in both CTAs.  Each 32-byte block row holds two 16-byte
+// halves, swapped in rows whose bit 2 is set: the order a TMA copy with
+// 32-byte swizzling would produce, so a plain copy of 128-byte lines gives
+// the MMA its layout.  Also sets the k-block band of every pair row tile.
+static void tc_pair_layout(TcMatrix &M, const std::vector<uint16_t> &h, std::vector<uint16_t> &h2)
+{
+    const int64_t kbs = M.k_pad / 16, m_pad = round16(M.n_out);
+    const int64_t tmax = pair_tile_rows();
+    M.ni2 = int((m_pad + tmax - 1) / tmax);
+    M.it2 = int((m_pad + M.ni2 - 1) / M.ni2 + 31) / 32 * 32;
+    const int64_t half = M.it2 / 2;
+    h2.assign(size_t(int64_t(M.npieces) * M.ni2 * kbs * 2 * 3 * half * 16), 0);
+    for (int tile = 0; tile < M.ni2; ++tile) {
+        int lo = int(kbs), hi = 0;
+        for (int p = 0; p < M.npieces; ++p)
+            for (int64_t kb = 0; kb < kbs; ++kb) {
+                bool any = false;
+                for (int r = 0; r < 2; ++r) {
+                    const int64_t blk = (((int64_t(p) * M.ni2 + tile) * kbs + kb) * 2 + r) * 3 * half;  // first row
+                    for (int b = 0; b < 3; ++b)
+                        for (int64_t j = 0; j < half; ++j) {
+                            const int64_t i = int64_t(tile) * M.it2 + r * half + j;  // matrix row
+                            if (i >= int64_t(M.ni) * M.it) continue;                 // padding: zero
+                            const int w = b == 1 ? 0 : 1;  // C is block 0 of a tile, S block 1
+                            const int64_t src =
+                                ((((int64_t(p) * M.ni + i / M.it) * kbs + kb) * kBlocks + w) * M.it + i % M.it) * 16;
+                            const int64_t row = b * half + j;
+                            for (int e = 0; e < 16; ++e) {
+                                uint16_t v = h[size_t(src + e)];
+                                any = any || (v & 0x7fffu) != 0;
+                                if (b == 0 && (v & 0x7fffu)) v ^= 0x8000u;  // -S
+                                const int chunk = (e / 8) ^ int((row >> 2) & 1);
+                                h2[size_t((blk + row) * 16 + chunk * 8 + e % 8)] = v;
+                            }
+                        }
+                }
+                if (any) {
+                    lo = std::min(lo, int(kb));
+                    hi = std::max(hi, int(kb) + 1);
+                }
+            }
+        if (lo >= hi) {  // an all-zero tile still runs one block (of zeros) to define its accumulators
+            lo = 0;
+            hi = 1;
+        }
+        M.kb_lo2[tile] = lo;
+        M.kb_hi2[tile] = hi;
+    }
+}
+
 mm_status tc_matrix_create(const double *E, int64_t m, int64_t n, int npieces, bool fixed, TcMatrix *out)
 {
     TcMatrix M;
-    std::vector<uint16_t> h;
+    std::vector<uint16_t> h, h2;
     std::vector<float> rho;
     mm_status st = tc_matrix_host(E, m, n, npieces, fixed, &M, h, rho);
     if (st) return st;
-    if (cudaMalloc(&M.pieces, h.size() * 2) != cudaSuccess)
+    tc_pair_layout(M, h, h2);
+    auto release = [&]() {
+        if (M.pieces) cudaFree(M.pieces);
+        if (M.pieces2) cudaFree(M.pieces2);
+        if (M.rho) cudaFree(M.rho);
+    };
+    if (cudaMalloc(&M.pieces, h.size() * 2) != cudaSuccess) {
+        M.pieces = nullptr;
         return fail(MM_ERR_OOM, "cudaMalloc of %zu bytes for matrix pieces failed", h.size() * 2);
+    }
     if (cudaMemcpy(M.pieces, h.data(), h.size() * 2, cudaMemcpyHostToDevice) != cudaSuccess) {
-        cudaFree(M.pieces);
+        release();
         return fail(MM_ERR_CUDA, "upload of matrix pieces failed");
     }
+    if (!h2.empty()) {
+        if (cudaMalloc(&M.pieces2, h2.size() * 2) != cudaSuccess) {
+            M.pieces2 = nullptr;
+            release();
+            return fail(MM_ERR_OOM, "cudaMalloc of %zu bytes for matrix pieces failed", h2.size() * 2);
+        }
+        if (cudaMemcpy(M.pieces2, h2.data(), h2.size() * 2, cudaMemcpyHostToDevice) != cudaSuccess) {
+            release();
+            return fail(MM_ERR_CUDA, "upload of matrix pieces failed");
+        }
+    }
     if (fixed) {
-        if (cudaMalloc(&M.rho, rho.size() * sizeof(float)) != cudaSuccess ||
-            cudaMemcpy(M.rho, rho.data(), rho.size() * sizeof(float), cudaMemcpyHostToDevice) != cudaSuccess) {
-            cudaFree(M.pieces);
-            if (M.rho) cudaFree(M.rho);
+        if (cudaMalloc(&M.rho, rho.size() * sizeof(float)) != cudaSuccess) {
+            M.rho = nullptr;
+            release();
+            return fail(MM_ERR_OOM, "row scales upload failed");
+        }
+        if (cudaMemcpy(M.rho, rho.data(), rho.size() * sizeof(float), cudaMemcpyHostToDevice) != cudaSuccess) {
+            release();
             return fail(MM_ERR_OOM, "row scales upload failed");
         }
     }
@@ -231,8 +319,10 @@ void tc_matrix_destroy(TcMatrix *M)
 {
     if (!M) return;
     if (M->pieces) cudaFree(M->pieces);
+    if (M->pieces2) cudaFree(M->pieces2);
     if (M->rho) cudaFree(M->rho);
     M->pieces = nullptr;
+    M->pieces2 = nullptr;
     M->rho = nullptr;
 }
 
@@ -450,7 +540,7 @@ struct TcArgs {
     int64_t pairs;          // work items of a CTA pair: (pair of point tiles, row tile)
     int64_t tiles;          // point tiles
     int it, ni, kblocks;
-    int kb_lo[2], kb_hi[2];  // k-blocks where the row tile's matrix pieces are not all zero
+    int kb_lo[4], kb_hi[4];  // k-blocks where the row tile's matrix pieces are not all zero
     int stage_bytes, tx_bytes, e_offset;
     float tb;               // tau * beta for the nonlinear epilogue
     uint16_t *out;
@@ -468,6 +558,108 @@ __host__ __device__ constexpr int term_b(int t) { return t == 1 ? 1 : (t == 3 ? 
 constexpr int kEpiWarps = 16;      // four per TMEM lane quarter
 constexpr int kThreads = 32 * (2 + kEpiWarps);  // warp 0 TMA, warp 1 TMEM + MMA, then the epilogue warps
 constexpr int kChunksPerWarp = 2;  // 16-row chunks each epilogue warp drains (IT <= 128)
+
+// Epilogue of one work item for one thread: its point is row `row` of
+// point tile `tile`, and v[q] holds the drained sums of output rows
+// i0 = h it + 16 (grp + 4 q) .. i0 + 15 (16 real, then 16 imaginary
+// values).  Scales them (fixed point), applies the nonlinear phase (EPI 1),
+// tracks the maximum and the range, splits them into pieces and stores.
+template <int NP, bool KMAJOR, int EPI, bool FX, int CH>
+__device__ __forceinline__ void epi_store(const TcArgs &a, float (&v)[CH][32], int64_t tile, int h, int row, int grp,
+                                          int nchunks, float s_in, float inv_out, float lim, float &local_max,
+                                          bool &range_ok)
+{
+    // this thread's point
+    bool valid;
+    int64_t r, l = 0;
+    if (KMAJOR) {
+        r = tile * kTileM + row;
+        valid = r < a.right;
+    } else {
+        const int64_t atom = 2 * tile + row / 64;
+        r = atom / a.aps;
+        l = (atom % a.aps) * 64 + row % 64;
+        valid = r < a.right && l < a.left;
+    }
+#pragma unroll
+    for (int q = 0; q < CH; ++q) {
+        const int ch = grp + 4 * q;
+        if (ch >= nchunks || !valid) continue;
+        const int64_t i0 = int64_t(h) * a.it + ch * 16;
+        if (i0 >= a.mp) continue;
+        // scale (fixed point), nonlinear phase, range and maximum, in place
+#pragma unroll
+        for (int k = 0; k < 16; ++k) {
+            float xr = v[q][k], xi = v[q][16 + k];
+            if (FX) {
+                const float g = __ldg(a.rho + i0 + k) * s_in;  // power of two: exact
+                xr *= g;
+                xi *= g;
+            }
+            if (EPI == 1) {
+                const float th = a.tb * (xr * xr + xi * xi);
+                float sn, cs;
+                sincosf(th, &sn, &cs);
+                const float yr = xr * cs + xi * sn, yi = xi * cs - xr * sn;
+                xr = yr;
+                xi = yi;
+            }
+            if (FX) {
+                const float ar = fabsf(xr), ai = fabsf(xi);
+                local_max = fmaxf(local_max, fmaxf(ar, ai));
+                range_ok &= ar < lim && ai < lim;
+                xr *= inv_out;
+                xi *= inv_out;
+            }
+            v[q][k] = xr;
+            v[q][16 + k] = xi;
+        }
+        // pieces of one value: fixed point (already divided by the grid) or floating BF16
+        auto pieces_of = [&](float x, uint16_t *b) {
+            if (FX) {
+                split_fx_scaled(x, b[0], b[1], b[2]);
+            } else {
+#pragma unroll
+                for (int p = 0; p < NP; ++p) {
+                    const __nv_bfloat16 h16 = __float2bfloat16_rn(x);
+                    b[p] = __bfloat16_as_ushort(h16);
+                    x -= __bfloat162float(h16);
+                }
+            }
+        };
+        if (KMAJOR) {
+            // 16 consecutive outputs of one row: one 32-byte store per (plane, piece)
+            const int64_t base = r * a.mp + i0;
+#pragma unroll
+            for (int c = 0; c < 2; ++c) {
+                uint32_t w[3][8];
+#pragma unroll
+                for (int k2 = 0; k2 < 8; ++k2) {
+                    uint16_t b0[3], b1[3];
+                    pieces_of(v[q][16 * c + 2 * k2], b0);
+                    pieces_of(v[q][16 * c + 2 * k2 + 1], b1);
+#pragma unroll
+                    for (int p = 0; p < NP; ++p) w[p][k2] = uint32_t(b0[p]) | (uint32_t(b1[p]) << 16);
+                }
+#pragma unroll
+                for (int p = 0; p < NP; ++p) st_global_v8(a.out + int64_t(c * NP + p) * a.plane_out + base, w[p]);
+            }
+        } else {
+#pragma unroll
+            for (int k = 0; k < 16; ++k) {
+                uint16_t br[3], bi[3];
+                pieces_of(v[q][k], br);
+                pieces_of(v[q][16 + k], bi);
+                const int64_t off = (r * a.mp + i0 + k) * a.left + l;
+#pragma unroll
+                for (int p = 0; p < NP; ++p) {
+                    a.out[int64_t(p) * a.plane_out + off] = br[p];
+                    a.out[int64_t(NP + p) * a.plane_out + off] = bi[p];
+                }
+            }
+        }
+    }
+}
 
 // Persistent kernel in clusters of two CTAs.  Cluster c processes work
 // items P = c, c + #clusters, ...; item P is the row tile h = P % ni of the
@@ -671,96 +863,8 @@ __global__ void __launch_bounds__(kThreads, 1)
             __syncwarp();
             if (lane == 0) mbarrier_arrive(tmem_empty);
             if (!acc_ready) break;
-            // this thread's point
-            bool valid;
-            int64_t r, l = 0;
-            if (KMAJOR) {
-                r = tile * kTileM + row;
-                valid = r < a.right;
-            } else {
-                const int64_t atom = 2 * tile + row / 64;
-                r = atom / a.aps;
-                l = (atom % a.aps) * 64 + row % 64;
-                valid = r < a.right && l < a.left;
-            }
-#pragma unroll
-            for (int q = 0; q < kChunksPerWarp; ++q) {
-                const int ch = grp + 4 * q;
-                if (ch >= nchunks || !valid) continue;
-                const int64_t i0 = int64_t(h) * a.it + ch * 16;
-                if (i0 >= a.mp) continue;
-                // scale (fixed point), nonlinear phase, range and maximum, in place
-#pragma unroll
-                for (int k = 0; k < 16; ++k) {
-                    float xr = v[q][k], xi = v[q][16 + k];
-                    if (FX) {
-                        const float g = __ldg(a.rho + i0 + k) * s_in;  // power of two: exact
-                        xr *= g;
-                        xi *= g;
-                    }
-                    if (EPI == 1) {
-                        const float th = a.tb * (xr * xr + xi * xi);
-                        float sn, cs;
-                        sincosf(th, &sn, &cs);
-                        const float yr = xr * cs + xi * sn, yi = xi * cs - xr * sn;
-                        xr = yr;
-                        xi = yi;
-                    }
-                    if (FX) {
-                        const float ar = fabsf(xr), ai = fabsf(xi);
-                        local_max = fmaxf(local_max, fmaxf(ar, ai));
-                        range_ok &= ar < lim && ai < lim;
-                        xr *= inv_out;
-                        xi *= inv_out;
-                    }
-                    v[q][k] = xr;
-                    v[q][16 + k] = xi;
-                }
-                // pieces of one value: fixed point (already divided by the grid) or floating BF16
-                auto pieces_of = [&](float x, uint16_t *b) {
-                    if (FX) {
-                        split_fx_scaled(x, b[0], b[1], b[2]);
-                    } else {
-#pragma unroll
-                        for (int p = 0; p < NP; ++p) {
-                            const __nv_bfloat16 h16 = __float2bfloat16_rn(x);
-                            b[p] = __bfloat16_as_ushort(h16);
-                            x -= __bfloat162float(h16);
-                        }
-                    }
-                };
-                if (KMAJOR) {
-                    // 16 consecutive outputs of one row: one 32-byte store per (plane, piece)
-                    const int64_t base = r * a.mp + i0;
-#pragma unroll
-                    for (int c = 0; c < 2; ++c) {
-                        uint32_t w[3][8];
-#pragma unroll
-                        for (int k2 = 0; k2 < 8; ++k2) {
-                            uint16_t b0[3], b1[3];
-                            pieces_of(v[q][16 * c + 2 * k2], b0);
-                            pieces_of(v[q][16 * c + 2 * k2 + 1], b1);
-#pragma unroll
-                            for (int p = 0; p < NP; ++p) w[p][k2] = uint32_t(b0[p]) | (uint32_t(b1[p]) << 16);
-                        }
-#pragma unroll
-                        for (int p = 0; p < NP; ++p) st_global_v8(a.out + int64_t(c * NP + p) * a.plane_out + base, w[p]);
-                    }
-                } else {
-#pragma unroll
-                    for (int k = 0; k < 16; ++k) {
-                        uint16_t br[3], bi[3];
-                        pieces_of(v[q][k], br);
-                        pieces_of(v[q][16 + k], bi);
-                        const int64_t off = (r * a.mp + i0 + k) * a.left + l;
-#pragma unroll
-                        for (int p = 0; p < NP; ++p) {
-                            a.out[int64_t(p) * a.plane_out + off] = br[p];
-                            a.out[int64_t(NP + p) * a.plane_out + off] = bi[p];
-                        }
-                    }
-                }
-            }
+            epi_store<NP, KMAJOR, EPI, FX, kChunksPerWarp>(a, v, tile, h, row, grp, nchunks, s_in, inv_out, lim,
+                                                          local_max, range_ok);
         }
         if (FX) {
             const unsigned m = __reduce_max_sync(0xffffffffu, __float_as_uint(local_max));
@@ -774,6 +878,266 @@ __global__ void __launch_bounds__(kThreads, 1)
     if (warp == 1) {
         tc_fence_after();
         tmem_dealloc(tmem, ncols);
+    }
+}
+
+// Pipeline stages of the pair kernel: 6 of 33 KB for row tiles of 64, 5 of
+// 42 KB for row tiles of 128 (CH = 2).
+__host__ __device__ constexpr int pair_stages(int CH) { return CH == 2 ? 5 : 6; }
+
+// The same product with the tensor cores of the two SMs of a cluster
+// working as one (tcgen05 cta_group::2): the leader CTA (rank 0) issues
+// MMAs of M = 256 points, rows 0..127 from its own shared memory and
+// 128..255 from its peer's at the same offsets; each CTA holds half of the
+// N = 2 IT matrix columns and receives its own 128 x N accumulator in its
+// tensor memory.  The rows are tiled in row tiles of IT <= 64 (TcMatrix
+// ni2 / it2), which keeps one item's two accumulators within 256 of the
+// 512 tensor-memory columns: items alternate between two accumulator sets,
+// so the MMAs of an item run while the epilogue drains the previous one.
+// The matrix half of rank r covers output rows r IT/2 .. (r + 1) IT/2 - 1
+// of the tile as the blocks [-S; C; S], so the real plane is one MMA over
+// the window [C; S] and the imaginary plane one over [-S; C]: two
+// N = 2 IT MMAs per piece product, every MMA reading one half of B per SM.
+// Accumulator columns of a CTA: [re | im] of rows 0 .. IT/2 - 1, then
+// [re | im] of rows IT/2 .. IT - 1.  Both CTAs' TMA loads complete on the
+// leader's stage barriers; the leader's commits release the stages and
+// signal the accumulators in both CTAs.  The leader's MMAs reuse an
+// accumulator set once the epilogue warps of both CTAs have drained it:
+// the peer's warps arrive on their own barrier, which one thread of the
+// peer relays to the leader's.
+template <int NP, bool KMAJOR, int EPI, bool FX, int CH>
+__global__ void __launch_bounds__(kThreads, 1)
+    tc_pair_kernel(const __grid_constant__ CUtensorMap mapX, const __grid_constant__ CUtensorMap mapE, TcArgs a)
+{
+    constexpr int kSt = pair_stages(CH);
+    extern __shared__ __align__(1024) uint8_t smem_raw[];
+    uint8_t *smem = reinterpret_cast<uint8_t *>((reinterpret_cast<uintptr_t>(smem_raw) + 1023) & ~uintptr_t(1023));
+    uint64_t *full = reinterpret_cast<uint64_t *>(smem + kSt * a.stage_bytes);
+    uint64_t *empty = full + kSt;
+    uint64_t *accf = empty + kSt;  // [2]: accumulator set b holds a finished item
+    uint64_t *tmem_empty = accf + 2;       // [2]: accumulator set b has been drained
+    uint32_t *tmem_slot = reinterpret_cast<uint32_t *>(tmem_empty + 2);
+    volatile int *abort_flag = reinterpret_cast<volatile int *>(tmem_slot + 1);
+
+    const int warp = threadIdx.x / 32, lane = threadIdx.x % 32;
+    const int rank = int(blockIdx.x & 1);
+    const int acc_cols = 2 * a.it;                          // one accumulator: [re | im] of IT rows
+    const int set_cols = NP > 1 ? 2 * acc_cols : acc_cols;  // leading and correction accumulators
+    const int nsets = 2 * set_cols <= 512 ? 2 : 1;          // two sets when they fit in tensor memory
+    const int need = nsets * set_cols;
+    const uint32_t ncols = need <= 32 ? 32 : (need <= 64 ? 64 : (need <= 128 ? 128 : (need <= 256 ? 256 : 512)));
+
+    if (threadIdx.x == 0) {
+        for (int s = 0; s < kSt; ++s) {
+            mbar_init(&full[s], 1);   // the leader's producer (expecting both CTAs' bytes)
+            mbar_init(&empty[s], 1);  // the leader's commit
+        }
+        for (int b = 0; b < 2; ++b) {
+            mbar_init(&accf[b], 1);
+            // this CTA's epilogue warps, and in the leader the peer's relay
+            mbar_init(&tmem_empty[b], kEpiWarps + (rank == 0 ? 1 : 0));
+        }
+        *abort_flag = 0;
+        mbar_fence_init();
+        tma_prefetch_desc(&mapX);
+        tma_prefetch_desc(&mapE);
+    }
+    if (warp == 1) {
+        tmem_alloc_pair(tmem_slot, ncols);
+        tmem_relinquish_pair();
+    }
+    tc_fence_before();
+    __syncthreads();
+    cluster_sync();  // both CTAs' barriers and tensor memory exist before either uses the other's
+    tc_fence_after();
+    const uint32_t tmem = *tmem_slot;
+    const int64_t cid = blockIdx.x / 2, nclusters = gridDim.x / 2;
+    const int half = a.it / 2;
+    const int e_bytes = 3 * half * 32;  // one piece's [-S; C; S] blocks in a stage
+    const uint32_t full_lead = mapa_shared(smem_u32(full), 0);
+    const uint32_t tmem_empty_lead = mapa_shared(smem_u32(tmem_empty), 0);
+
+    if (warp == 0) {
+        if (lane == 0) {
+            // ---------------- TMA producer (both CTAs) ----------------
+            uint32_t gk = 0;
+            const int e_rows = 3 * half / 4;  // 128-byte rows of one block triple
+            for (int64_t P = cid; P < a.pairs && !*abort_flag; P += nclusters) {
+                const int64_t tile = (P / a.ni) * 2 + rank;
+                const int h = int(P % a.ni);
+                int ac_l[2] = {0, 0}, ac_r[2] = {0, 0};
+                if (!KMAJOR) {
+                    for (int q = 0; q < 2; ++q) {
+                        const int64_t atom = 2 * tile + q;
+                        int64_t r = atom / a.aps;
+                        if (r > a.right) r = a.right;  // past the end: zero fill
+                        ac_r[q] = int(r);
+                        ac_l[q] = int((atom % a.aps) * 64);
+                    }
+                }
+                const int k_row = int(tile * kTileM);
+                for (int kb = a.kb_lo[h]; kb < a.kb_hi[h]; ++kb, ++gk) {
+                    const int s = int(gk % kSt);
+                    const uint32_t ph = (gk / kSt) & 1u;
+                    if (!mbar_wait(&empty[s], ph ^ 1u, a.err, MM_ERR_TIMEOUT)) {
+                        *abort_flag = 1;
+                        break;
+                    }
+                    uint8_t *st = smem + s * a.stage_bytes;
+                    const uint32_t fb = full_lead + uint32_t(s) * 8u;
+                    if (rank == 0) mbar_arrive_expect_tx(&full[s], uint32_t(a.tx_bytes));
+                    for (int c = 0; c < 2; ++c)
+                        for (int p = 0; p < NP; ++p) {
+                            uint8_t *dst = st + (c * NP + p) * kDataTileBytes;
+                            if (KMAJOR) {
+                                tma_load_3d_pair(&mapX, fb, dst, kb * kBK, k_row, c * NP + p);
+                            } else {
+                                tma_load_4d_pair(&mapX, fb, dst, ac_l[0], kb * kBK, ac_r[0], c * NP + p);
+                                tma_load_4d_pair(&mapX, fb, dst + 2048, ac_l[1], kb * kBK, ac_r[1], c * NP + p);
+                            }
+                        }
+                    for (int p = 0; p < NP; ++p) {
+                        const int blk = ((p * a.ni + h) * a.kblocks + kb) * 2 + rank;
+                        tma_load_2d_pair(&mapE, fb, st + a.e_offset + p * e_bytes, 0, blk * e_rows);
+                    }
+                }
+            }
+        }
+    } else if (warp == 1) {
+        if (lane == 0 && rank == 1) {
+            // ---------------- relay (peer only) ----------------
+            // One cluster-scope arrival on the leader's barrier once all of this
+            // CTA's epilogue warps have drained an accumulator set (their own
+            // arrivals stay CTA-scope, which does not wait for their stores).
+            uint32_t lt = 0;
+            for (int64_t P = cid; P < a.pairs; P += nclusters, ++lt) {
+                const int b = int(lt % uint32_t(nsets));
+                if (!mbar_wait(&tmem_empty[b], (lt / uint32_t(nsets)) & 1u, a.err, MM_ERR_TIMEOUT)) {
+                    *abort_flag = 1;
+                    break;
+                }
+                mbar_arrive_cluster(tmem_empty_lead + uint32_t(b) * 8u);
+            }
+        }
+        if (lane == 0 && rank == 0) {
+            // ---------------- MMA issuer (leader only) ----------------
+            const uint32_t idesc = FX ? idesc_f16_f32(2 * kTileM, 2 * a.it, !KMAJOR, false)
+                                      : idesc_bf16_f32(2 * kTileM, 2 * a.it, !KMAJOR, false);
+            uint32_t gk = 0, lt = 0;
+            for (int64_t P = cid; P < a.pairs && !*abort_flag; P += nclusters, ++lt) {
+                const int h = int(P % a.ni);
+                const int b = int(lt % uint32_t(nsets));
+                const uint32_t use = lt / uint32_t(nsets);
+                if (use > 0 && !mbar_wait<true>(&tmem_empty[b], (use - 1) & 1u, a.err, MM_ERR_TIMEOUT)) {
+                    *abort_flag = 1;
+                    break;
+                }
+                tc_fence_after();
+                const uint32_t tset = tmem + uint32_t(b * set_cols);
+                bool started[2] = {false, false};
+                for (int kb = a.kb_lo[h]; kb < a.kb_hi[h]; ++kb, ++gk) {
+                    const int s = int(gk % kSt);
+                    const uint32_t ph = (gk / kSt) & 1u;
+                    if (!mbar_wait(&full[s], ph, a.err, MM_ERR_TIMEOUT)) {
+                        *abort_flag = 1;
+                        break;
+                    }
+                    tc_fence_after();
+                    const uint32_t st = smem_u32(smem + s * a.stage_bytes);
+                    const uint32_t est = st + a.e_offset;
+#pragma unroll
+                    for (int t = 0; t < num_terms(NP); ++t) {
+                        const int pa = term_a(t), pb = term_b(t);
+                        const int acc = (NP > 1 && (pa != 0 || pb != 0)) ? 1 : 0;
+                        const uint32_t dcol = tset + uint32_t(acc * acc_cols);
+                        const uint32_t eb = est + pa * e_bytes;
+                        const uint64_t b_im = smem_desc(eb, 16, 256, kSwz32);              // [-S; C]
+                        const uint64_t b_re = smem_desc(eb + half * 32, 16, 256, kSwz32);  // [C; S]
+                        const uint32_t xre = st + (0 * NP + pb) * kDataTileBytes;
+                        const uint32_t xim = st + (1 * NP + pb) * kDataTileBytes;
+                        const uint64_t are = KMAJOR ? smem_desc(xre, 16, 256, kSwz32) : smem_desc(xre, 2048, 1024, kSwz128);
+                        const uint64_t aim = KMAJOR ? smem_desc(xim, 16, 256, kSwz32) : smem_desc(xim, 2048, 1024, kSwz128);
+                        umma_f16_pair(dcol, are, b_re, idesc, started[acc] ? 1u : 0u);
+                        started[acc] = true;
+                        umma_f16_pair(dcol, aim, b_im, idesc, 1u);
+                    }
+                    umma_commit_pair_mc(&empty[s], 0x3);
+                }
+                umma_commit_pair_mc(&accf[b], 0x3);
+            }
+        }
+    } else {
+        // ---------------- epilogue warps (both CTAs) ----------------
+        const int ew = warp - 2;
+        const int quarter = warp % 4;
+        const int grp = ew / 4;  // the warp's chunks of 16 output rows: grp, grp + 4, ..
+        const uint32_t tbase = tmem + (uint32_t(quarter * 32) << 16);
+        const int nchunks = a.it / 16;
+        float s_in = 1.0f, inv_out = 1.0f, lim = 0.0f;
+        int es_out = 0;
+        if (FX) {
+            s_in = *a.sc.s_in;
+            es_out = grid_exponent(__uint_as_float(*a.sc.max_prev));
+            inv_out = ldexpf(1.0f, -es_out);
+            lim = ldexpf(16384.0f, es_out);
+            if (blockIdx.x == 0 && ew == 0 && lane == 0) *a.sc.s_out = ldexpf(1.0f, es_out);
+        }
+        float local_max = 0.0f;
+        bool range_ok = true;
+        uint32_t lt = 0;
+        for (int64_t P = cid; P < a.pairs; P += nclusters, ++lt) {
+            const int64_t tile = (P / a.ni) * 2 + rank;
+            const int h = int(P % a.ni);
+            const int b = int(lt % uint32_t(nsets));
+            const bool acc_ready =
+                !*abort_flag && mbar_wait(&accf[b], (lt / uint32_t(nsets)) & 1u, a.err, MM_ERR_TIMEOUT);
+            if (!acc_ready) *abort_flag = 1;
+            tc_fence_after();
+            const uint32_t tset = tbase + uint32_t(b * set_cols);
+            // drain: the leading accumulator straight into v, the corrections added (no spills on this path)
+            float v[CH][32];
+#pragma unroll
+            for (int q = 0; q < CH; ++q) {
+                const int ch = grp + 4 * q;
+                if (ch < nchunks) {
+                    const int i0 = ch * 16;
+                    const int cre = i0 + (i0 >= half ? half : 0), cim = cre + half;
+                    float t1[16];
+                    tmem_ld16_to(tset + uint32_t(cre), &v[q][0]);
+                    if (NP > 1) tmem_ld16_to(tset + uint32_t(acc_cols + cre), t1);
+                    tmem_ld_wait();
+                    if (NP > 1) {
+#pragma unroll
+                        for (int k = 0; k < 16; ++k) v[q][k] += t1[k];
+                    }
+                    tmem_ld16_to(tset + uint32_t(cim), &v[q][16]);
+                    if (NP > 1) tmem_ld16_to(tset + uint32_t(acc_cols + cim), t1);
+                    tmem_ld_wait();
+                    if (NP > 1) {
+#pragma unroll
+                        for (int k = 0; k < 16; ++k) v[q][16 + k] += t1[k];
+                    }
+                }
+            }
+            tc_fence_before();
+            __syncwarp();
+            if (lane == 0) mbarrier_arrive(&tmem_empty[b]);
+            if (!acc_ready) break;
+            epi_store<NP, KMAJOR, EPI, FX, CH>(a, v, tile, h, quarter * 32 + lane, grp, nchunks, s_in, inv_out, lim,
+                                               local_max, range_ok);
+        }
+        if (FX) {
+            const unsigned m = __reduce_max_sync(0xffffffffu, __float_as_uint(local_max));
+            if (lane == 0 && m) atomicMax(a.sc.max_cur, m);
+            if (!range_ok && a.err) atomicCAS(a.err, 0, MM_ERR_RANGE);
+        }
+    }
+    tc_fence_before();
+    __syncthreads();
+    cluster_sync();  // the leader's MMAs no longer read the peer's shared memory or write its tensor memory
+    if (warp == 1) {
+        tc_fence_after();
+        tmem_dealloc_pair(tmem, ncols);
     }
 }
 
@@ -1185,13 +1549,10 @@ static bool encode(CUtensorMap *map, void *base, int rank, const cuuint64_t *dim
               CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE) == CUDA_SUCCESS;
 }
 
-template <int NP, bool KM, int EPI, bool FX>
+template <int NP, bool KM, int EPI, bool FX, bool PAIR>
 static cudaError_t launch_tc(const CUtensorMap &mx, const CUtensorMap &me, const TcArgs &a, int grid, int smem,
                              cudaStream_t s)
 {
-    auto kern = tc_mode_kernel<NP, KM, EPI, FX>;
-    cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
-    if (e != cudaSuccess) return e;
     cudaLaunchConfig_t cfg = {};
     cfg.gridDim = dim3(unsigned(grid));
     cfg.blockDim = dim3(kThreads);
@@ -1204,25 +1565,49 @@ static cudaError_t launch_tc(const CUtensorMap &mx, const CUtensorMap &me, const
     attr[0].val.clusterDim.z = 1;
     cfg.attrs = attr;
     cfg.numAttrs = 1;
-    // persistent grid: no more clusters than can be resident at once
-    int active = 0;
-    if (cudaOccupancyMaxActiveClusters(&active, kern, &cfg) == cudaSuccess && active > 0 && 2 * active < grid)
-        cfg.gridDim = dim3(unsigned(2 * active));
-    e = cudaLaunchKernelEx(&cfg, kern, mx, me, a);
+    cudaError_t e;
+    if constexpr (PAIR) {
+        auto kern = a.it > 64 ? tc_pair_kernel<NP, KM, EPI, FX, 2> : tc_pair_kernel<NP, KM, EPI, FX, 1>;
+        e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
+        if (e != cudaSuccess) return e;
+        // persistent grid: no more clusters than can be resident at once
+        int active = 0;
+        if (cudaOccupancyMaxActiveClusters(&active, kern, &cfg) == cudaSuccess && active > 0 && 2 * active < grid)
+            cfg.gridDim = dim3(unsigned(2 * active));
+        e = cudaLaunchKernelEx(&cfg, kern, mx, me, a);
+    } else {
+        auto kern = tc_mode_kernel<NP, KM, EPI, FX>;
+        e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
+        if (e != cudaSuccess) return e;
+        int active = 0;
+        if (cudaOccupancyMaxActiveClusters(&active, kern, &cfg) == cudaSuccess && active > 0 && 2 * active < grid)
+            cfg.gridDim = dim3(unsigned(2 * active));
+        e = cudaLaunchKernelEx(&cfg, kern, mx, me, a);
+    }
     count_launch();
     if (e != cudaSuccess) return e;
     return cudaGetLastError();
 }
 
-template <int NP, bool FX>
+template <int NP, bool FX, bool PAIR>
 static cudaError_t dispatch_np(bool km, int epi, const CUtensorMap &mx, const CUtensorMap &me, const TcArgs &a,
                                int grid, int smem, cudaStream_t s)
 {
     if (km)
-        return epi ? launch_tc<NP, true, 1, FX>(mx, me, a, grid, smem, s)
-                   : launch_tc<NP, true, 0, FX>(mx, me, a, grid, smem, s);
-    return epi ? launch_tc<NP, false, 1, FX>(mx, me, a, grid, smem, s)
-               : launch_tc<NP, false, 0, FX>(mx, me, a, grid, smem, s);
+        return epi ? launch_tc<NP, true, 1, FX, PAIR>(mx, me, a, grid, smem, s)
+                   : launch_tc<NP, true, 0, FX, PAIR>(mx, me, a, grid, smem, s);
+    return epi ? launch_tc<NP, false, 1, FX, PAIR>(mx, me, a, grid, smem, s)
+               : launch_tc<NP, false, 0, FX, PAIR>(mx, me, a, grid, smem, s);
+}
+
+// The CTA-pair kernel runs where the matrix has its pair layout, unless the
+// environment variable MM_TC_1SM is set to a value other than 0 (the
+// one-SM kernel, kept for comparison).
+static bool use_pair_kernel(const TcMatrix &M)
+{
+    if (!M.pieces2) return false;
+    const char *v = std::getenv("MM_TC_1SM");
+    return !(v && v[0] && !(v[0] == '0' && v[1] == 0));
 }
 
 cudaError_t tc_mode_product(const TcState &si, const TcState &so, int mu, const TcMatrix &M, mm_prec prec,
@@ -1246,7 +1631,7 @@ cudaError_t tc_mode_product(const TcState &si, const TcState &so, int mu, const 
     a.it = M.it;
     a.ni = M.ni;
     a.kblocks = int(a.kp / kBK);
-    for (int h = 0; h < 2; ++h) {
+    for (int h = 0; h < 4; ++h) {
         a.kb_lo[h] = h < M.ni ? M.kb_lo[h] : 0;
         a.kb_hi[h] = h < M.ni ? M.kb_hi[h] : 1;
     }
@@ -1273,7 +1658,25 @@ cudaError_t tc_mode_product(const TcState &si, const TcState &so, int mu, const 
         cuuint32_t box[4] = {64, kBK, 1, 1};
         if (!encode(&mx, xin, 4, dims, str, box, CU_TENSOR_MAP_SWIZZLE_128B)) return cudaErrorInvalidValue;
     }
-    {
+    const bool pair = use_pair_kernel(M);
+    if (pair) {
+        // the pair kernel's row tiles: ni2 tiles of it2 rows
+        a.it = M.it2;
+        a.ni = M.ni2;
+        for (int h = 0; h < 4; ++h) {
+            a.kb_lo[h] = h < M.ni2 ? M.kb_lo2[h] : 0;
+            a.kb_hi[h] = h < M.ni2 ? M.kb_hi2[h] : 1;
+        }
+        // blocks [-S; C; S] of it2 / 2 rows per (piece, row tile, k-block, rank), copied as 128-byte lines
+        const int e_bytes = 3 * (M.it2 / 2) * 32;
+        a.tx_bytes = 2 * (a.e_offset + NP * e_bytes);  // both CTAs' loads complete on the leader's barrier
+        a.stage_bytes = (a.e_offset + NP * e_bytes + 1023) / 1024 * 1024;
+        const int64_t lines = int64_t(NP) * M.ni2 * (M.k_pad / 16) * 2 * e_bytes / 128;
+        cuuint64_t dims[2] = {64, cuuint64_t(lines)};
+        cuuint64_t str[1] = {128};
+        cuuint32_t box[2] = {64, cuuint32_t(e_bytes / 128)};
+        if (!encode(&me, M.pieces2, 2, dims, str, box, CU_TENSOR_MAP_SWIZZLE_NONE)) return cudaErrorInvalidValue;
+    } else {
         const int64_t rows = int64_t(NP) * M.ni * (M.k_pad / 16) * kBlocks * M.it;
         cuuint64_t dims[2] = {16, cuuint64_t(rows)};
         cuuint64_t str[1] = {32};
@@ -1286,12 +1689,20 @@ cudaError_t tc_mode_product(const TcState &si, const TcState &so, int mu, const 
     a.tiles = tiles;
     a.pairs = (tiles + 1) / 2 * a.ni;
     int64_t grid = 2 * (a.pairs < num_sms() / 2 ? a.pairs : num_sms() / 2);
-    const int smem = kStages * a.stage_bytes + 1024 + 256;
-    if (fx) return dispatch_np<3, true>(km, epi.kind, mx, me, a, int(grid), smem, s);
+    const int smem = (pair ? pair_stages(a.it > 64 ? 2 : 1) : kStages) * a.stage_bytes + 1024 + 256;
+    if (pair) {
+        if (fx) return dispatch_np<3, true, true>(km, epi.kind, mx, me, a, int(grid), smem, s);
+        switch (NP) {
+        case 3: return dispatch_np<3, false, true>(km, epi.kind, mx, me, a, int(grid), smem, s);
+        case 2: return dispatch_np<2, false, true>(km, epi.kind, mx, me, a, int(grid), smem, s);
+        default: return dispatch_np<1, false, true>(km, epi.kind, mx, me, a, int(grid), smem, s);
+        }
+    }
+    if (fx) return dispatch_np<3, true, false>(km, epi.kind, mx, me, a, int(grid), smem, s);
     switch (NP) {
-    case 3: return dispatch_np<3, false>(km, epi.kind, mx, me, a, int(grid), smem, s);
-    case 2: return dispatch_np<2, false>(km, epi.kind, mx, me, a, int(grid), smem, s);
-    default: return dispatch_np<1, false>(km, epi.kind, mx, me, a, int(grid), smem, s);
+    case 3: return dispatch_np<3, false, false>(km, epi.kind, mx, me, a, int(grid), smem, s);
+    case 2: return dispatch_np<2, false, false>(km, epi.kind, mx, me, a, int(grid), smem, s);
+    default: return dispatch_np<1, false, false>(km, epi.kind, mx, me, a, int(grid), smem, s);
     }
 }
 
@@ -1436,10 +1847,15 @@ double tc_issued_flops(const TcState &si, int mu, const TcMatrix &M, mm_prec pre
     const int64_t aps = (left + 63) / 64;
     const int64_t tiles = left == 1 ? (right + kTileM - 1) / kTileM : (right * aps + 1) / 2;
     const int64_t tiles_run = (tiles + 1) / 2 * 2;  // CTA pairs
-    double per_kb = 0.0;  // one k-block of one item: re plane N = 2 it, im plane 2 x N = it, K = 16
-    per_kb = double(num_terms(NP)) * (2.0 * kTileM * (2 * M.it) * kBK + 2.0 * (2.0 * kTileM * M.it * kBK));
+    // the kernel that runs and its row tiling
+    const bool pair = use_pair_kernel(M);
+    const int it = pair ? M.it2 : M.it, ni = pair ? M.ni2 : M.ni;
+    const int *lo = pair ? M.kb_lo2 : M.kb_lo, *hi = pair ? M.kb_hi2 : M.kb_hi;
+    // one k-block of one point tile: per piece product 2 M N K over N = 4 it columns (one-SM kernel: the
+    // real plane with N = 2 it and the imaginary plane as two of N = it; pair kernel: two of N = 2 it)
+    const double per_kb = double(num_terms(NP)) * 2.0 * kTileM * (4.0 * it) * kBK;
     double total = 0.0;
-    for (int h = 0; h < M.ni; ++h) total += double(tiles_run) * double(M.kb_hi[h] - M.kb_lo[h]) * per_kb;
+    for (int h = 0; h < ni; ++h) total += double(tiles_run) * double(hi[h] - lo[h]) * per_kb;
     return total;
 }
 

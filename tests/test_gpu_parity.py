@@ -213,6 +213,71 @@ def test_gpe_strang_steps(env, orc, prec):
     assert abs(n1 / n0 - 1) <= (1e-12 if prec == "fp64" else 1e-6)
 
 
+# ------------------------------------------- CTA-pair kernel vs one-SM kernel
+
+@pytest.mark.parametrize("tile", [64, 128])
+@pytest.mark.parametrize("dims", [(256, 64, 32), (32, 256, 96), (64, 32, 256)])
+@pytest.mark.parametrize("prec", ["f16x6", "bf16x3"])
+def test_pair_kernel_matches_one_sm_kernel(env, monkeypatch, dims, prec, tile):
+    """The CTA-pair kernel (M = 256 over the two SMs of a cluster) issues the
+    same piece products as the one-SM kernel, in the same order for every
+    output (the real plane's product, then the imaginary plane's, with -S
+    stored negated instead of the MMA's negate bit; k-blocks outside a row
+    tile's band only add exact zeros): the results agree bit for bit, for
+    row tiles of 64 (two accumulator sets) and of 128 (MM_PAIR_TILE=128).
+    MM_TC_1SM=1 selects the one-SM kernel."""
+    mm, ctx, torch = env
+    monkeypatch.setenv("MM_PAIR_TILE", str(tile))
+    tau = 1e-4
+    Es = [fd_schrodinger_E(mm, n, tau) for n in dims]
+    u0 = inputs.complex_normal(dims[::-1], seed=6).astype(np.complex64)
+
+    def run():
+        plan = mm.TuckerPlan(ctx, dims, Es, prec=prec)
+        plan.set_graphs(False)
+        u = to_gpu(torch, u0, torch.complex64)
+        plan.step(u, 2)
+        torch.cuda.synchronize()
+        return u.cpu().numpy()
+
+    monkeypatch.delenv("MM_TC_1SM", raising=False)
+    pair = run()
+    monkeypatch.setenv("MM_TC_1SM", "1")
+    one = run()
+    monkeypatch.delenv("MM_TC_1SM")
+    print(f"pair (tile {tile}) vs one-SM {prec} dims={dims}: max |diff| = {np.abs(pair - one).max():.3e}, "
+          f"rel = {rel(pair, one):.3e}")
+    assert np.array_equal(pair.view(np.uint32), one.view(np.uint32))
+
+
+def test_pair_kernel_gpe_epilogue(env, orc, monkeypatch):
+    """The nonlinear-phase epilogue in the CTA-pair kernel (m = 32 quadrature
+    points: row tiles of 32): against the oracle and bit for bit against the
+    one-SM kernel."""
+    mm, ctx, torch = env
+    m, beta, tau, steps = 32, 100.0, 1e-3, 6
+    xo, _, Wo = orc.gauss_hermite(m)
+    psi0 = inputs.gpe_psi0(xo, Wo, seed=4).astype(np.complex64)
+
+    def run():
+        plan = mm.HermitePlan(ctx, [m] * 3, prec="f16x6")
+        psi = to_gpu(torch, psi0, torch.complex64)
+        plan.gpe_step(psi, beta, tau, steps)
+        torch.cuda.synchronize()
+        return psi.cpu().numpy()
+
+    monkeypatch.delenv("MM_TC_1SM", raising=False)
+    pair = run()
+    monkeypatch.setenv("MM_TC_1SM", "1")
+    one = run()
+    monkeypatch.delenv("MM_TC_1SM")
+    ref = orc.gpe_steps(psi0.astype(complex), xo, Wo, beta, tau, steps)
+    err = orc.rel_l2(pair, ref, orc.weight3(Wo))
+    print(f"GPE pair m={m} rel_err={err:.3e}, pair vs one-SM max |diff| = {np.abs(pair - one).max():.3e}")
+    assert err <= 1e-6
+    assert np.array_equal(pair.view(np.uint32), one.view(np.uint32))
+
+
 # ------------------------------------------------- full size, sampled (n = 256)
 
 def test_free_schrodinger_n256_50_steps_sampled(env, orc):
