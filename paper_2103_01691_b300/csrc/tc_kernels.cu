@@ -542,6 +542,7 @@ struct TcArgs {
     int it, ni, kblocks;
     int kb_lo[4], kb_hi[4];  // k-blocks where the row tile's matrix pieces are not all zero
     int stage_bytes, tx_bytes, e_offset;
+    int x5d;                // MN-major input through the 5-D map (both atoms of a tile in one box)
     float tb;               // tau * beta for the nonlinear epilogue
     uint16_t *out;
     int *err;
@@ -587,14 +588,25 @@ __device__ __forceinline__ void epi_store(const TcArgs &a, float (&v)[CH][32], i
         if (ch >= nchunks || !valid) continue;
         const int64_t i0 = int64_t(h) * a.it + ch * 16;
         if (i0 >= a.mp) continue;
-        // scale (fixed point), nonlinear phase, range and maximum, in place
+        // scale (fixed point), nonlinear phase, range and maximum, in place; the 16 row scales
+        // (powers of two, 64-byte aligned) come in four vector loads
+        float g16[16];
+        if (FX) {
+#pragma unroll
+            for (int k4 = 0; k4 < 4; ++k4) {
+                const float4 r4 = __ldg(reinterpret_cast<const float4 *>(a.rho + i0) + k4);
+                g16[4 * k4 + 0] = r4.x * s_in;
+                g16[4 * k4 + 1] = r4.y * s_in;
+                g16[4 * k4 + 2] = r4.z * s_in;
+                g16[4 * k4 + 3] = r4.w * s_in;
+            }
+        }
 #pragma unroll
         for (int k = 0; k < 16; ++k) {
             float xr = v[q][k], xi = v[q][16 + k];
             if (FX) {
-                const float g = __ldg(a.rho + i0 + k) * s_in;  // power of two: exact
-                xr *= g;
-                xi *= g;
+                xr *= g16[k];  // exact
+                xi *= g16[k];
             }
             if (EPI == 1) {
                 const float th = a.tb * (xr * xr + xi * xi);
@@ -960,12 +972,14 @@ __global__ void __launch_bounds__(kThreads, 1)
     if (warp == 0) {
         if (lane == 0) {
             // ---------------- TMA producer (both CTAs) ----------------
-            uint32_t gk = 0;
+            int s = 0;
+            uint32_t ph = 0;  // ring position
             const int e_rows = 3 * half / 4;  // 128-byte rows of one block triple
             for (int64_t P = cid; P < a.pairs && !*abort_flag; P += nclusters) {
                 const int64_t tile = (P / a.ni) * 2 + rank;
                 const int h = int(P % a.ni);
                 int ac_l[2] = {0, 0}, ac_r[2] = {0, 0};
+                int x5_pair = 0, x5_r = 0;  // 5-D map: atom pair within the slab, slab row (plane 0)
                 if (!KMAJOR) {
                     for (int q = 0; q < 2; ++q) {
                         const int64_t atom = 2 * tile + q;
@@ -974,11 +988,16 @@ __global__ void __launch_bounds__(kThreads, 1)
                         ac_r[q] = int(r);
                         ac_l[q] = int((atom % a.aps) * 64);
                     }
+                    // past the end: a slab-row coordinate beyond the merged (plane, row) extent, zero fill
+                    x5_pair = int(((2 * tile) % a.aps) / 2);
+                    x5_r = ac_r[0] < a.right ? ac_r[0] : int(a.right * 2 * NP);
                 }
                 const int k_row = int(tile * kTileM);
-                for (int kb = a.kb_lo[h]; kb < a.kb_hi[h]; ++kb, ++gk) {
-                    const int s = int(gk % kSt);
-                    const uint32_t ph = (gk / kSt) & 1u;
+                // first 128-byte row of piece 0's block triple at k-block 0; piece p adds
+                // p ni kblocks 2 e_rows, k-block kb adds kb 2 e_rows
+                const int e_row0 = ((h * a.kblocks) * 2 + rank) * e_rows;
+                const int e_prow = a.ni * a.kblocks * 2 * e_rows;
+                for (int kb = a.kb_lo[h]; kb < a.kb_hi[h]; ++kb) {
                     if (!mbar_wait(&empty[s], ph ^ 1u, a.err, MM_ERR_TIMEOUT)) {
                         *abort_flag = 1;
                         break;
@@ -986,19 +1005,27 @@ __global__ void __launch_bounds__(kThreads, 1)
                     uint8_t *st = smem + s * a.stage_bytes;
                     const uint32_t fb = full_lead + uint32_t(s) * 8u;
                     if (rank == 0) mbar_arrive_expect_tx(&full[s], uint32_t(a.tx_bytes));
+#pragma unroll
                     for (int c = 0; c < 2; ++c)
+#pragma unroll
                         for (int p = 0; p < NP; ++p) {
                             uint8_t *dst = st + (c * NP + p) * kDataTileBytes;
                             if (KMAJOR) {
                                 tma_load_3d_pair(&mapX, fb, dst, kb * kBK, k_row, c * NP + p);
+                            } else if (a.x5d) {
+                                const int rp = x5_r < a.right ? (c * NP + p) * int(a.right) + x5_r : x5_r;
+                                tma_load_5d_pair(&mapX, fb, dst, 0, kb * kBK, 0, x5_pair, rp);
                             } else {
                                 tma_load_4d_pair(&mapX, fb, dst, ac_l[0], kb * kBK, ac_r[0], c * NP + p);
                                 tma_load_4d_pair(&mapX, fb, dst + 2048, ac_l[1], kb * kBK, ac_r[1], c * NP + p);
                             }
                         }
-                    for (int p = 0; p < NP; ++p) {
-                        const int blk = ((p * a.ni + h) * a.kblocks + kb) * 2 + rank;
-                        tma_load_2d_pair(&mapE, fb, st + a.e_offset + p * e_bytes, 0, blk * e_rows);
+#pragma unroll
+                    for (int p = 0; p < NP; ++p)
+                        tma_load_2d_pair(&mapE, fb, st + a.e_offset + p * e_bytes, 0, e_row0 + p * e_prow + kb * 2 * e_rows);
+                    if (++s == kSt) {
+                        s = 0;
+                        ph ^= 1u;
                     }
                 }
             }
@@ -1021,9 +1048,26 @@ __global__ void __launch_bounds__(kThreads, 1)
         }
         if (lane == 0 && rank == 0) {
             // ---------------- MMA issuer (leader only) ----------------
+            // The operand descriptors of stage 0 are built once; stage s adds s stage_bytes / 16 to
+            // their start-address field (bits 0..13, wide enough for every shared-memory address of
+            // the CTA).  This thread shares its SM sub-partition with four busy epilogue warps, so
+            // few instructions per MMA keep the tensor pipe fed.
             const uint32_t idesc = FX ? idesc_f16_f32(2 * kTileM, 2 * a.it, !KMAJOR, false)
                                       : idesc_bf16_f32(2 * kTileM, 2 * a.it, !KMAJOR, false);
-            uint32_t gk = 0, lt = 0;
+            const uint32_t st0 = smem_u32(smem), est0 = st0 + uint32_t(a.e_offset);
+            uint64_t adesc[2][NP], bdesc[2][NP];  // [real plane, imaginary plane][piece]
+#pragma unroll
+            for (int p = 0; p < NP; ++p) {
+                const uint32_t xre = st0 + uint32_t(p * kDataTileBytes), xim = st0 + uint32_t((NP + p) * kDataTileBytes);
+                adesc[0][p] = KMAJOR ? smem_desc(xre, 16, 256, kSwz32) : smem_desc(xre, 2048, 1024, kSwz128);
+                adesc[1][p] = KMAJOR ? smem_desc(xim, 16, 256, kSwz32) : smem_desc(xim, 2048, 1024, kSwz128);
+                const uint32_t eb = est0 + uint32_t(p * e_bytes);
+                bdesc[0][p] = smem_desc(eb + uint32_t(half * 32), 16, 256, kSwz32);  // [C; S]
+                bdesc[1][p] = smem_desc(eb, 16, 256, kSwz32);                        // [-S; C]
+            }
+            const uint64_t stage_step = uint64_t(uint32_t(a.stage_bytes) >> 4);
+            int s = 0;
+            uint32_t ph = 0, lt = 0;  // ring position, advanced with the producer's
             for (int64_t P = cid; P < a.pairs && !*abort_flag; P += nclusters, ++lt) {
                 const int h = int(P % a.ni);
                 const int b = int(lt % uint32_t(nsets));
@@ -1033,35 +1077,28 @@ __global__ void __launch_bounds__(kThreads, 1)
                     break;
                 }
                 tc_fence_after();
-                const uint32_t tset = tmem + uint32_t(b * set_cols);
-                bool started[2] = {false, false};
-                for (int kb = a.kb_lo[h]; kb < a.kb_hi[h]; ++kb, ++gk) {
-                    const int s = int(gk % kSt);
-                    const uint32_t ph = (gk / kSt) & 1u;
+                const uint32_t d0 = tmem + uint32_t(b * set_cols), d1 = d0 + uint32_t(acc_cols);
+                const int kb_lo = a.kb_lo[h], kb_hi = a.kb_hi[h];
+                for (int kb = kb_lo; kb < kb_hi; ++kb) {
                     if (!mbar_wait(&full[s], ph, a.err, MM_ERR_TIMEOUT)) {
                         *abort_flag = 1;
                         break;
                     }
                     tc_fence_after();
-                    const uint32_t st = smem_u32(smem + s * a.stage_bytes);
-                    const uint32_t est = st + a.e_offset;
+                    const uint64_t so = uint64_t(s) * stage_step;
+                    const uint32_t first = kb == kb_lo ? 0u : 1u;  // each accumulator starts at its first product
 #pragma unroll
                     for (int t = 0; t < num_terms(NP); ++t) {
                         const int pa = term_a(t), pb = term_b(t);
-                        const int acc = (NP > 1 && (pa != 0 || pb != 0)) ? 1 : 0;
-                        const uint32_t dcol = tset + uint32_t(acc * acc_cols);
-                        const uint32_t eb = est + pa * e_bytes;
-                        const uint64_t b_im = smem_desc(eb, 16, 256, kSwz32);              // [-S; C]
-                        const uint64_t b_re = smem_desc(eb + half * 32, 16, 256, kSwz32);  // [C; S]
-                        const uint32_t xre = st + (0 * NP + pb) * kDataTileBytes;
-                        const uint32_t xim = st + (1 * NP + pb) * kDataTileBytes;
-                        const uint64_t are = KMAJOR ? smem_desc(xre, 16, 256, kSwz32) : smem_desc(xre, 2048, 1024, kSwz128);
-                        const uint64_t aim = KMAJOR ? smem_desc(xim, 16, 256, kSwz32) : smem_desc(xim, 2048, 1024, kSwz128);
-                        umma_f16_pair(dcol, are, b_re, idesc, started[acc] ? 1u : 0u);
-                        started[acc] = true;
-                        umma_f16_pair(dcol, aim, b_im, idesc, 1u);
+                        const uint32_t dcol = (NP > 1 && (pa != 0 || pb != 0)) ? d1 : d0;
+                        umma_f16_pair(dcol, adesc[0][pb] + so, bdesc[0][pa] + so, idesc, t <= 1 ? first : 1u);
+                        umma_f16_pair(dcol, adesc[1][pb] + so, bdesc[1][pa] + so, idesc, 1u);
                     }
                     umma_commit_pair_mc(&empty[s], 0x3);
+                    if (++s == kSt) {
+                        s = 0;
+                        ph ^= 1u;
+                    }
                 }
                 umma_commit_pair_mc(&accf[b], 0x3);
             }
@@ -1659,6 +1696,18 @@ cudaError_t tc_mode_product(const TcState &si, const TcState &so, int mu, const 
         if (!encode(&mx, xin, 4, dims, str, box, CU_TENSOR_MAP_SWIZZLE_128B)) return cudaErrorInvalidValue;
     }
     const bool pair = use_pair_kernel(M);
+    if (pair && !km && a.left % 128 == 0) {
+        // both 64-point atoms of a point tile in one box: (l mod 64, k, atom of the pair, pair in
+        // the slab, plane x right + slab row); the smem image is [atom][k][64 points] as before
+        cuuint64_t dims[5] = {64, cuuint64_t(a.kp), 2, cuuint64_t(a.left / 128), cuuint64_t(a.right * 2 * NP)};
+        cuuint64_t str[4] = {cuuint64_t(a.left * 2), 128, 256, cuuint64_t(a.left * a.kp * 2)};
+        cuuint32_t box[5] = {64, kBK, 2, 1, 1};
+        CUtensorMap m5;
+        if (encode(&m5, xin, 5, dims, str, box, CU_TENSOR_MAP_SWIZZLE_128B)) {
+            mx = m5;
+            a.x5d = 1;
+        }
+    }
     if (pair) {
         // the pair kernel's row tiles: ni2 tiles of it2 rows
         a.it = M.it2;
