@@ -56,8 +56,8 @@ struct TcMatrix {
     int ni = 0, it = 0;             // number of row tiles, rows per tile
     void *pieces = nullptr;         // [p][tile][k_pad/16][2 blocks (C, S)][it][16], bf16 or fp16
     // The same pieces for the CTA-pair kernel, tiled in ni2 row tiles of it2
-    // rows (it2 a multiple of 32, at most 64):
-    // [p][tile][k_pad/16][rank][3 blocks (-S, C, S)][it2/2][16], rank r
+    // rows (it2 a multiple of 32):
+    // [tile][k_pad/16][rank][p][3 blocks (-S, C, S)][it2/2][16], rank r
     // holding rows r it2/2 .. of the tile, each block row 32 bytes, stored in
     // the 32-byte swizzled order the MMA reads from shared memory.
     void *pieces2 = nullptr;

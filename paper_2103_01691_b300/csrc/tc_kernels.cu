@@ -215,10 +215,11 @@ static int64_t pair_tile_rows()
 }
 
 // Rearrange the pieces for the CTA-pair kernel, which tiles the rows in
-// ni2 tiles of it2 rows: per (piece, row tile, k-block) CTA rank r of
-// the pair gets the rows r it2/2 .. (r + 1) it2/2 - 1 of the tile as three
-// blocks -S, C, S, so that [C; S] and [-S; C] are windows of it2 rows at the
-// same offsets in both CTAs.  Each 32-byte block row holds two 16-byte
+// ni2 tiles of it2 rows: per (row tile, k-block) CTA rank r of the pair
+// gets, for each piece, the rows r it2/2 .. (r + 1) it2/2 - 1 of the tile as
+// three blocks -S, C, S, so that [C; S] and [-S; C] are windows of it2 rows
+// at the same offsets in both CTAs; the pieces of one (row tile, k-block,
+// rank) are contiguous and arrive in one copy.  Each 32-byte block row holds two 16-byte
 // halves, swapped in rows whose bit 2 is set: the order a TMA copy with
 // 32-byte swizzling would produce, so a plain copy of 128-byte lines gives
 // the MMA its layout.  Also sets the k-block band of every pair row tile.
@@ -236,7 +237,7 @@ static void tc_pair_layout(TcMatrix &M, const std::vector<uint16_t> &h, std::vec
             for (int64_t kb = 0; kb < kbs; ++kb) {
                 bool any = false;
                 for (int r = 0; r < 2; ++r) {
-                    const int64_t blk = (((int64_t(p) * M.ni2 + tile) * kbs + kb) * 2 + r) * 3 * half;  // first row
+                    const int64_t blk = (((int64_t(tile) * kbs + kb) * 2 + r) * M.npieces + p) * 3 * half;  // first row
                     for (int b = 0; b < 3; ++b)
                         for (int64_t j = 0; j < half; ++j) {
                             const int64_t i = int64_t(tile) * M.it2 + r * half + j;  // matrix row
@@ -542,7 +543,6 @@ struct TcArgs {
     int it, ni, kblocks;
     int kb_lo[4], kb_hi[4];  // k-blocks where the row tile's matrix pieces are not all zero
     int stage_bytes, tx_bytes, e_offset;
-    int x5d;                // MN-major input through the 5-D map (both atoms of a tile in one box)
     float tb;               // tau * beta for the nonlinear epilogue
     uint16_t *out;
     int *err;
@@ -776,6 +776,7 @@ __global__ void __launch_bounds__(kThreads, 1)
                 }
             }
         }
+        __syncwarp();  // the role's other lanes wait for it: the warp meets the block barrier converged
     } else if (warp == 1) {
         if (lane == 0) {
             // ---------------- MMA issuer ----------------
@@ -826,6 +827,7 @@ __global__ void __launch_bounds__(kThreads, 1)
                 umma_commit(accf);
             }
         }
+        __syncwarp();
     } else {
         // ---------------- epilogue warps ----------------
         const int ew = warp - 2;          // 0 .. kEpiWarps - 1
@@ -893,9 +895,160 @@ __global__ void __launch_bounds__(kThreads, 1)
     }
 }
 
-// Pipeline stages of the pair kernel: 6 of 33 KB for row tiles of 64, 5 of
-// 42 KB for row tiles of 128 (CH = 2).
-__host__ __device__ constexpr int pair_stages(int CH) { return CH == 2 ? 5 : 6; }
+// Per-warp staging of the pair kernel's output boxes: one plane's three pieces, 1 KB each.
+constexpr int kStageBoxBytes = 1024;
+constexpr int kStagingPerWarp = 3 * kStageBoxBytes;
+
+// Epilogue of one work item for one warp of the pair kernel with row tiles of at most 64:
+// the warp's 32 points (TMEM lanes 32 quarter ..) and output rows i0 = h it + 16 grp .. + 15.
+// vr / vi[hh] hold the drained real / imaginary sums in the matrix-fragment order of
+// tmem_ld_frag16 for the lanes 16 hh .. 16 hh + 15: value k is point 16 hh + t/4 + 8 ((k >> 1) & 1)
+// at output 8 (k >> 2) + 2 (t % 4) + (k & 1) (t = lane).  The values are scaled, given the
+// nonlinear phase (EPI 1), checked and split as in epi_store; each piece plane's 32 x 16 box is
+// written to shared memory by stmatrix (two instructions per piece) and stored by TMA: for
+// direction 1 (K-major output) as [point][output] rows of 32 bytes in the 32-byte swizzled order,
+// otherwise transposed to [output][point] rows of 64 bytes in the 64-byte swizzled order.
+// Parts of a box outside the padded tensor are clipped by the TMA unit; boxes wholly outside
+// are not issued.
+template <int NP, bool KMAJOR, int EPI, bool FX>
+__device__ __forceinline__ void epi_frag_store(const TcArgs &a, const CUtensorMap *mapY, uint8_t *stg,
+                                               float (&vr)[2][8], float (&vi)[2][8], int64_t tile, int h,
+                                               int quarter, int lane, int grp, int nchunks, float s_in,
+                                               float inv_out, float lim, float &local_max, bool &range_ok)
+{
+    if (grp >= nchunks) return;
+    const int i0 = h * a.it + grp * 16;
+    if (i0 >= a.mp) return;
+    const int t4 = lane / 4, tc = lane % 4;
+    // the warp's box origin and the validity of this thread's four points (hh, s)
+    bool box_ok, valid[2][2];
+    int64_t rr;
+    int l0 = 0;
+    if (KMAJOR) {
+        rr = tile * kTileM + quarter * 32;
+        box_ok = rr < a.right;
+#pragma unroll
+        for (int hh = 0; hh < 2; ++hh)
+#pragma unroll
+            for (int s = 0; s < 2; ++s) valid[hh][s] = rr + 16 * hh + 8 * s + t4 < a.right;
+    } else {
+        const int64_t atom = 2 * tile + quarter / 2;
+        rr = atom / a.aps;
+        l0 = int((atom % a.aps) * 64 + (quarter & 1) * 32);
+        box_ok = rr < a.right && l0 < a.left;
+#pragma unroll
+        for (int hh = 0; hh < 2; ++hh)
+#pragma unroll
+            for (int s = 0; s < 2; ++s) valid[hh][s] = rr < a.right && l0 + 16 * hh + 8 * s + t4 < a.left;
+    }
+    // row scales of this thread's four outputs (pairs at 2 tc and 8 + 2 tc)
+    float g[2][2] = {{1.0f, 1.0f}, {1.0f, 1.0f}};
+    if (FX) {
+#pragma unroll
+        for (int cb = 0; cb < 2; ++cb) {
+            const float2 r2 = __ldg(reinterpret_cast<const float2 *>(a.rho + i0 + 8 * cb + 2 * tc));
+            g[cb][0] = r2.x * s_in;
+            g[cb][1] = r2.y * s_in;
+        }
+    }
+#pragma unroll
+    for (int hh = 0; hh < 2; ++hh)
+#pragma unroll
+        for (int k = 0; k < 8; ++k) {
+            float xr = vr[hh][k], xi = vi[hh][k];
+            if (FX) {
+                xr *= g[k >> 2][k & 1];  // power of two: exact
+                xi *= g[k >> 2][k & 1];
+            }
+            if (EPI == 1) {
+                const float th = a.tb * (xr * xr + xi * xi);
+                float sn, cs;
+                sincosf(th, &sn, &cs);
+                const float yr = xr * cs + xi * sn, yi = xi * cs - xr * sn;
+                xr = yr;
+                xi = yi;
+            }
+            if (FX) {
+                const float ar = fabsf(xr), ai = fabsf(xi);
+                if (valid[hh][(k >> 1) & 1]) {
+                    local_max = fmaxf(local_max, fmaxf(ar, ai));
+                    range_ok &= ar < lim && ai < lim;
+                }
+                xr *= inv_out;
+                xi *= inv_out;
+            }
+            vr[hh][k] = xr;
+            vi[hh][k] = xi;
+        }
+    auto pieces_of = [&](float x, uint16_t *b) {
+        if (FX) {
+            split_fx_scaled(x, b[0], b[1], b[2]);
+        } else {
+#pragma unroll
+            for (int p = 0; p < NP; ++p) {
+                const __nv_bfloat16 h16 = __float2bfloat16_rn(x);
+                b[p] = __bfloat16_as_ushort(h16);
+                x -= __bfloat162float(h16);
+            }
+        }
+    };
+    // the shared-memory row this thread addresses for stmatrix: matrix j = lane / 8 is (s, cb) =
+    // (j & 1, j >> 1), row r = lane % 8
+    const int mj = lane / 8, mr = lane % 8, ms = mj & 1, mcb = mj >> 1;
+    const uint32_t sbase = smem_u32(stg);
+    uint32_t row_off[2];
+#pragma unroll
+    for (int hh = 0; hh < 2; ++hh) {
+        if (KMAJOR) {
+            const int pr = 16 * hh + 8 * ms + mr;  // point row of the [32][16] box
+            row_off[hh] = uint32_t(pr * 32 + ((mcb ^ ((pr >> 2) & 1)) * 16));
+        } else {
+            const int ir = 8 * mcb + mr;  // output row of the [16][32] box
+            row_off[hh] = uint32_t(ir * 64 + (((2 * hh + ms) ^ ((ir >> 1) & 3)) * 16));
+        }
+    }
+#pragma unroll
+    for (int c = 0; c < 2; ++c) {
+        // pack the pieces of output pairs (2 tc, 2 tc + 1): pk[p][hh][j], matrix j = s + 2 cb
+        uint32_t pk[3][2][4];
+#pragma unroll
+        for (int hh = 0; hh < 2; ++hh)
+#pragma unroll
+            for (int j = 0; j < 4; ++j) {
+                uint16_t b0[3], b1[3];
+                const int k = 2 * j;  // values k, k + 1: s = j & 1, cb = j >> 1
+                pieces_of(c == 0 ? vr[hh][k] : vi[hh][k], b0);
+                pieces_of(c == 0 ? vr[hh][k + 1] : vi[hh][k + 1], b1);
+#pragma unroll
+                for (int p = 0; p < NP; ++p) pk[p][hh][j] = uint32_t(b0[p]) | (uint32_t(b1[p]) << 16);
+            }
+        if (lane == 0) bulk_wait_read0();  // the previous boxes have left the staging buffer
+        __syncwarp();
+#pragma unroll
+        for (int p = 0; p < NP; ++p)
+#pragma unroll
+            for (int hh = 0; hh < 2; ++hh) {
+                const uint32_t ad = sbase + uint32_t(p * kStageBoxBytes) + row_off[hh];
+                if (KMAJOR) stmatrix_x4(ad, pk[p][hh][0], pk[p][hh][1], pk[p][hh][2], pk[p][hh][3]);
+                else stmatrix_x4_trans(ad, pk[p][hh][0], pk[p][hh][1], pk[p][hh][2], pk[p][hh][3]);
+            }
+        fence_proxy_async_smem();
+        __syncwarp();
+        if (lane == 0 && box_ok) {
+#pragma unroll
+            for (int p = 0; p < NP; ++p) {
+                if (KMAJOR) tma_store_3d(mapY, stg + p * kStageBoxBytes, i0, int(rr), c * NP + p);
+                else tma_store_4d(mapY, stg + p * kStageBoxBytes, l0, i0, int(rr), c * NP + p);
+            }
+            bulk_commit();
+        }
+    }
+}
+
+// Pipeline stages of the pair kernel: 5 of 33 KB for row tiles of 64 (with
+// 48 KB of output staging), 5 of 42 KB for row tiles of 128 (CH = 2).
+__host__ __device__ constexpr int pair_stages(int CH) { return CH == 2 ? 5 : 5; }
+__host__ __device__ constexpr int pair_staging_bytes(int CH) { return CH == 1 ? kEpiWarps * kStagingPerWarp : 0; }
 
 // The same product with the tensor cores of the two SMs of a cluster
 // working as one (tcgen05 cta_group::2): the leader CTA (rank 0) issues
@@ -919,12 +1072,14 @@ __host__ __device__ constexpr int pair_stages(int CH) { return CH == 2 ? 5 : 6; 
 // peer relays to the leader's.
 template <int NP, bool KMAJOR, int EPI, bool FX, int CH>
 __global__ void __launch_bounds__(kThreads, 1)
-    tc_pair_kernel(const __grid_constant__ CUtensorMap mapX, const __grid_constant__ CUtensorMap mapE, TcArgs a)
+    tc_pair_kernel(const __grid_constant__ CUtensorMap mapX, const __grid_constant__ CUtensorMap mapE,
+                   const __grid_constant__ CUtensorMap mapY, TcArgs a)
 {
     constexpr int kSt = pair_stages(CH);
     extern __shared__ __align__(1024) uint8_t smem_raw[];
     uint8_t *smem = reinterpret_cast<uint8_t *>((reinterpret_cast<uintptr_t>(smem_raw) + 1023) & ~uintptr_t(1023));
-    uint64_t *full = reinterpret_cast<uint64_t *>(smem + kSt * a.stage_bytes);
+    uint8_t *staging = smem + kSt * a.stage_bytes;  // CH == 1: kEpiWarps x kStagingPerWarp
+    uint64_t *full = reinterpret_cast<uint64_t *>(staging + pair_staging_bytes(CH));
     uint64_t *empty = full + kSt;
     uint64_t *accf = empty + kSt;  // [2]: accumulator set b holds a finished item
     uint64_t *tmem_empty = accf + 2;       // [2]: accumulator set b has been drained
@@ -953,6 +1108,7 @@ __global__ void __launch_bounds__(kThreads, 1)
         mbar_fence_init();
         tma_prefetch_desc(&mapX);
         tma_prefetch_desc(&mapE);
+        if (CH == 1) tma_prefetch_desc(&mapY);
     }
     if (warp == 1) {
         tmem_alloc_pair(tmem_slot, ncols);
@@ -978,25 +1134,21 @@ __global__ void __launch_bounds__(kThreads, 1)
             for (int64_t P = cid; P < a.pairs && !*abort_flag; P += nclusters) {
                 const int64_t tile = (P / a.ni) * 2 + rank;
                 const int h = int(P % a.ni);
+                // MN-major: the two 64-point atoms of the tile (slab row, first point), past the end zero fill
                 int ac_l[2] = {0, 0}, ac_r[2] = {0, 0};
-                int x5_pair = 0, x5_r = 0;  // 5-D map: atom pair within the slab, slab row (plane 0)
                 if (!KMAJOR) {
                     for (int q = 0; q < 2; ++q) {
                         const int64_t atom = 2 * tile + q;
                         int64_t r = atom / a.aps;
-                        if (r > a.right) r = a.right;  // past the end: zero fill
+                        if (r > a.right) r = a.right;
                         ac_r[q] = int(r);
                         ac_l[q] = int((atom % a.aps) * 64);
                     }
-                    // past the end: a slab-row coordinate beyond the merged (plane, row) extent, zero fill
-                    x5_pair = int(((2 * tile) % a.aps) / 2);
-                    x5_r = ac_r[0] < a.right ? ac_r[0] : int(a.right * 2 * NP);
                 }
                 const int k_row = int(tile * kTileM);
-                // first 128-byte row of piece 0's block triple at k-block 0; piece p adds
-                // p ni kblocks 2 e_rows, k-block kb adds kb 2 e_rows
-                const int e_row0 = ((h * a.kblocks) * 2 + rank) * e_rows;
-                const int e_prow = a.ni * a.kblocks * 2 * e_rows;
+                // the matrix blocks of all pieces for (row tile h, k-block kb, rank): one box of 128-byte rows
+                const int e_box_rows = NP * e_rows;
+                const int e_row0 = (h * a.kblocks * 2 + rank) * e_box_rows;
                 for (int kb = a.kb_lo[h]; kb < a.kb_hi[h]; ++kb) {
                     if (!mbar_wait(&empty[s], ph ^ 1u, a.err, MM_ERR_TIMEOUT)) {
                         *abort_flag = 1;
@@ -1005,24 +1157,15 @@ __global__ void __launch_bounds__(kThreads, 1)
                     uint8_t *st = smem + s * a.stage_bytes;
                     const uint32_t fb = full_lead + uint32_t(s) * 8u;
                     if (rank == 0) mbar_arrive_expect_tx(&full[s], uint32_t(a.tx_bytes));
-#pragma unroll
-                    for (int c = 0; c < 2; ++c)
-#pragma unroll
-                        for (int p = 0; p < NP; ++p) {
-                            uint8_t *dst = st + (c * NP + p) * kDataTileBytes;
-                            if (KMAJOR) {
-                                tma_load_3d_pair(&mapX, fb, dst, kb * kBK, k_row, c * NP + p);
-                            } else if (a.x5d) {
-                                const int rp = x5_r < a.right ? (c * NP + p) * int(a.right) + x5_r : x5_r;
-                                tma_load_5d_pair(&mapX, fb, dst, 0, kb * kBK, 0, x5_pair, rp);
-                            } else {
-                                tma_load_4d_pair(&mapX, fb, dst, ac_l[0], kb * kBK, ac_r[0], c * NP + p);
-                                tma_load_4d_pair(&mapX, fb, dst + 2048, ac_l[1], kb * kBK, ac_r[1], c * NP + p);
-                            }
-                        }
-#pragma unroll
-                    for (int p = 0; p < NP; ++p)
-                        tma_load_2d_pair(&mapE, fb, st + a.e_offset + p * e_bytes, 0, e_row0 + p * e_prow + kb * 2 * e_rows);
+                    // all 2 NP piece planes in one box (K-major: [plane][128 points][16]) or one box per
+                    // atom (MN-major: [atom][plane][16 k][64 points])
+                    if (KMAJOR) {
+                        tma_load_3d_pair(&mapX, fb, st, kb * kBK, k_row, 0);
+                    } else {
+                        tma_load_4d_pair(&mapX, fb, st, ac_l[0], kb * kBK, ac_r[0], 0);
+                        tma_load_4d_pair(&mapX, fb, st + 2 * NP * 2048, ac_l[1], kb * kBK, ac_r[1], 0);
+                    }
+                    tma_load_2d_pair(&mapE, fb, st + a.e_offset, 0, e_row0 + kb * 2 * e_box_rows);
                     if (++s == kSt) {
                         s = 0;
                         ph ^= 1u;
@@ -1030,6 +1173,7 @@ __global__ void __launch_bounds__(kThreads, 1)
                 }
             }
         }
+        __syncwarp();  // the role's other lanes wait for it: the warp meets the block barrier converged
     } else if (warp == 1) {
         if (lane == 0 && rank == 1) {
             // ---------------- relay (peer only) ----------------
@@ -1058,9 +1202,11 @@ __global__ void __launch_bounds__(kThreads, 1)
             uint64_t adesc[2][NP], bdesc[2][NP];  // [real plane, imaginary plane][piece]
 #pragma unroll
             for (int p = 0; p < NP; ++p) {
-                const uint32_t xre = st0 + uint32_t(p * kDataTileBytes), xim = st0 + uint32_t((NP + p) * kDataTileBytes);
-                adesc[0][p] = KMAJOR ? smem_desc(xre, 16, 256, kSwz32) : smem_desc(xre, 2048, 1024, kSwz128);
-                adesc[1][p] = KMAJOR ? smem_desc(xim, 16, 256, kSwz32) : smem_desc(xim, 2048, 1024, kSwz128);
+                // K-major: plane tiles of 4 KB; MN-major: plane tiles of 2 KB per atom, atoms 2 NP x 2 KB apart
+                const uint32_t pb = KMAJOR ? uint32_t(kDataTileBytes) : 2048u;
+                const uint32_t xre = st0 + uint32_t(p) * pb, xim = st0 + uint32_t(NP + p) * pb;
+                adesc[0][p] = KMAJOR ? smem_desc(xre, 16, 256, kSwz32) : smem_desc(xre, 2 * NP * 2048, 1024, kSwz128);
+                adesc[1][p] = KMAJOR ? smem_desc(xim, 16, 256, kSwz32) : smem_desc(xim, 2 * NP * 2048, 1024, kSwz128);
                 const uint32_t eb = est0 + uint32_t(p * e_bytes);
                 bdesc[0][p] = smem_desc(eb + uint32_t(half * 32), 16, 256, kSwz32);  // [C; S]
                 bdesc[1][p] = smem_desc(eb, 16, 256, kSwz32);                        // [-S; C]
@@ -1103,6 +1249,7 @@ __global__ void __launch_bounds__(kThreads, 1)
                 umma_commit_pair_mc(&accf[b], 0x3);
             }
         }
+        __syncwarp();
     } else {
         // ---------------- epilogue warps (both CTAs) ----------------
         const int ew = warp - 2;
@@ -1126,43 +1273,80 @@ __global__ void __launch_bounds__(kThreads, 1)
             const int64_t tile = (P / a.ni) * 2 + rank;
             const int h = int(P % a.ni);
             const int b = int(lt % uint32_t(nsets));
-            const bool acc_ready =
-                !*abort_flag && mbar_wait(&accf[b], (lt / uint32_t(nsets)) & 1u, a.err, MM_ERR_TIMEOUT);
+            // the same decision in every lane: the warp stays converged for its collective instructions
+            const bool acc_ready = __all_sync(
+                0xffffffffu, !*abort_flag && mbar_wait(&accf[b], (lt / uint32_t(nsets)) & 1u, a.err, MM_ERR_TIMEOUT));
             if (!acc_ready) *abort_flag = 1;
             tc_fence_after();
             const uint32_t tset = tbase + uint32_t(b * set_cols);
-            // drain: the leading accumulator straight into v, the corrections added (no spills on this path)
-            float v[CH][32];
-#pragma unroll
-            for (int q = 0; q < CH; ++q) {
-                const int ch = grp + 4 * q;
-                if (ch < nchunks) {
-                    const int i0 = ch * 16;
+            if constexpr (CH == 1) {
+                // drain in the matrix-fragment order, two 16-lane halves, leading + corrections
+                float vr[2][8], vi[2][8];
+                if (grp < nchunks) {
+                    const int i0 = grp * 16;
                     const int cre = i0 + (i0 >= half ? half : 0), cim = cre + half;
-                    float t1[16];
-                    tmem_ld16_to(tset + uint32_t(cre), &v[q][0]);
-                    if (NP > 1) tmem_ld16_to(tset + uint32_t(acc_cols + cre), t1);
-                    tmem_ld_wait();
-                    if (NP > 1) {
 #pragma unroll
-                        for (int k = 0; k < 16; ++k) v[q][k] += t1[k];
-                    }
-                    tmem_ld16_to(tset + uint32_t(cim), &v[q][16]);
-                    if (NP > 1) tmem_ld16_to(tset + uint32_t(acc_cols + cim), t1);
-                    tmem_ld_wait();
-                    if (NP > 1) {
+                    for (int hh = 0; hh < 2; ++hh) {
+                        const uint32_t ta = tmem + (uint32_t(quarter * 32 + hh * 16) << 16) + uint32_t(b * set_cols);
+                        float t1[8];
+                        tmem_ld_frag16(ta + uint32_t(cre), vr[hh]);
+                        if (NP > 1) tmem_ld_frag16(ta + uint32_t(acc_cols + cre), t1);
+                        tmem_ld_wait();
+                        if (NP > 1) {
 #pragma unroll
-                        for (int k = 0; k < 16; ++k) v[q][16 + k] += t1[k];
+                            for (int k = 0; k < 8; ++k) vr[hh][k] += t1[k];
+                        }
+                        tmem_ld_frag16(ta + uint32_t(cim), vi[hh]);
+                        if (NP > 1) tmem_ld_frag16(ta + uint32_t(acc_cols + cim), t1);
+                        tmem_ld_wait();
+                        if (NP > 1) {
+#pragma unroll
+                            for (int k = 0; k < 8; ++k) vi[hh][k] += t1[k];
+                        }
                     }
                 }
+                tc_fence_before();
+                __syncwarp();
+                if (lane == 0) mbarrier_arrive(&tmem_empty[b]);
+                if (!acc_ready) break;
+                epi_frag_store<NP, KMAJOR, EPI, FX>(a, &mapY, staging + ew * kStagingPerWarp, vr, vi, tile, h,
+                                                    quarter, lane, grp, nchunks, s_in, inv_out, lim, local_max,
+                                                    range_ok);
+            } else {
+                // drain: the leading accumulator straight into v, the corrections added (no spills on this path)
+                float v[CH][32];
+#pragma unroll
+                for (int q = 0; q < CH; ++q) {
+                    const int ch = grp + 4 * q;
+                    if (ch < nchunks) {
+                        const int i0 = ch * 16;
+                        const int cre = i0 + (i0 >= half ? half : 0), cim = cre + half;
+                        float t1[16];
+                        tmem_ld16_to(tset + uint32_t(cre), &v[q][0]);
+                        if (NP > 1) tmem_ld16_to(tset + uint32_t(acc_cols + cre), t1);
+                        tmem_ld_wait();
+                        if (NP > 1) {
+#pragma unroll
+                            for (int k = 0; k < 16; ++k) v[q][k] += t1[k];
+                        }
+                        tmem_ld16_to(tset + uint32_t(cim), &v[q][16]);
+                        if (NP > 1) tmem_ld16_to(tset + uint32_t(acc_cols + cim), t1);
+                        tmem_ld_wait();
+                        if (NP > 1) {
+#pragma unroll
+                            for (int k = 0; k < 16; ++k) v[q][16 + k] += t1[k];
+                        }
+                    }
+                }
+                tc_fence_before();
+                __syncwarp();
+                if (lane == 0) mbarrier_arrive(&tmem_empty[b]);
+                if (!acc_ready) break;
+                epi_store<NP, KMAJOR, EPI, FX, CH>(a, v, tile, h, quarter * 32 + lane, grp, nchunks, s_in, inv_out,
+                                                   lim, local_max, range_ok);
             }
-            tc_fence_before();
-            __syncwarp();
-            if (lane == 0) mbarrier_arrive(&tmem_empty[b]);
-            if (!acc_ready) break;
-            epi_store<NP, KMAJOR, EPI, FX, CH>(a, v, tile, h, quarter * 32 + lane, grp, nchunks, s_in, inv_out, lim,
-                                               local_max, range_ok);
         }
+        if (CH == 1 && lane == 0) bulk_wait0();  // this warp's stores are complete
         if (FX) {
             const unsigned m = __reduce_max_sync(0xffffffffu, __float_as_uint(local_max));
             if (lane == 0 && m) atomicMax(a.sc.max_cur, m);
@@ -1171,7 +1355,10 @@ __global__ void __launch_bounds__(kThreads, 1)
     }
     tc_fence_before();
     __syncthreads();
-    cluster_sync();  // the leader's MMAs no longer read the peer's shared memory or write its tensor memory
+    // Every MMA (waited through the accumulator barriers), every load into either CTA's shared
+    // memory and every store has completed: the CTAs only wait for each other before freeing
+    // tensor memory and exiting.
+    cluster_sync_relaxed();
     if (warp == 1) {
         tc_fence_after();
         tmem_dealloc_pair(tmem, ncols);
@@ -1321,6 +1508,7 @@ __global__ void __launch_bounds__(kThreads, 1)
                 }
             }
         }
+        __syncwarp();  // the role's other lanes wait for it: the warp meets the block barrier converged
     } else if (warp == 1) {
         if (lane == 0) {
             // ---------------- MMA issuer ----------------
@@ -1374,6 +1562,7 @@ __global__ void __launch_bounds__(kThreads, 1)
                 umma_commit(accf);
             }
         }
+        __syncwarp();
     } else {
         // ---------------- epilogue warps ----------------
         const int ew = warp - 2;          // 0 .. kEpiWarps - 1
@@ -1587,8 +1776,8 @@ static bool encode(CUtensorMap *map, void *base, int rank, const cuuint64_t *dim
 }
 
 template <int NP, bool KM, int EPI, bool FX, bool PAIR>
-static cudaError_t launch_tc(const CUtensorMap &mx, const CUtensorMap &me, const TcArgs &a, int grid, int smem,
-                             cudaStream_t s)
+static cudaError_t launch_tc(const CUtensorMap &mx, const CUtensorMap &me, const CUtensorMap &my, const TcArgs &a,
+                             int grid, int smem, cudaStream_t s)
 {
     cudaLaunchConfig_t cfg = {};
     cfg.gridDim = dim3(unsigned(grid));
@@ -1611,7 +1800,7 @@ static cudaError_t launch_tc(const CUtensorMap &mx, const CUtensorMap &me, const
         int active = 0;
         if (cudaOccupancyMaxActiveClusters(&active, kern, &cfg) == cudaSuccess && active > 0 && 2 * active < grid)
             cfg.gridDim = dim3(unsigned(2 * active));
-        e = cudaLaunchKernelEx(&cfg, kern, mx, me, a);
+        e = cudaLaunchKernelEx(&cfg, kern, mx, me, my, a);
     } else {
         auto kern = tc_mode_kernel<NP, KM, EPI, FX>;
         e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
@@ -1627,14 +1816,14 @@ static cudaError_t launch_tc(const CUtensorMap &mx, const CUtensorMap &me, const
 }
 
 template <int NP, bool FX, bool PAIR>
-static cudaError_t dispatch_np(bool km, int epi, const CUtensorMap &mx, const CUtensorMap &me, const TcArgs &a,
-                               int grid, int smem, cudaStream_t s)
+static cudaError_t dispatch_np(bool km, int epi, const CUtensorMap &mx, const CUtensorMap &me, const CUtensorMap &my,
+                               const TcArgs &a, int grid, int smem, cudaStream_t s)
 {
     if (km)
-        return epi ? launch_tc<NP, true, 1, FX, PAIR>(mx, me, a, grid, smem, s)
-                   : launch_tc<NP, true, 0, FX, PAIR>(mx, me, a, grid, smem, s);
-    return epi ? launch_tc<NP, false, 1, FX, PAIR>(mx, me, a, grid, smem, s)
-               : launch_tc<NP, false, 0, FX, PAIR>(mx, me, a, grid, smem, s);
+        return epi ? launch_tc<NP, true, 1, FX, PAIR>(mx, me, my, a, grid, smem, s)
+                   : launch_tc<NP, true, 0, FX, PAIR>(mx, me, my, a, grid, smem, s);
+    return epi ? launch_tc<NP, false, 1, FX, PAIR>(mx, me, my, a, grid, smem, s)
+               : launch_tc<NP, false, 0, FX, PAIR>(mx, me, my, a, grid, smem, s);
 }
 
 // The CTA-pair kernel runs where the matrix has its pair layout, unless the
@@ -1696,16 +1885,18 @@ cudaError_t tc_mode_product(const TcState &si, const TcState &so, int mu, const 
         if (!encode(&mx, xin, 4, dims, str, box, CU_TENSOR_MAP_SWIZZLE_128B)) return cudaErrorInvalidValue;
     }
     const bool pair = use_pair_kernel(M);
-    if (pair && !km && a.left % 128 == 0) {
-        // both 64-point atoms of a point tile in one box: (l mod 64, k, atom of the pair, pair in
-        // the slab, plane x right + slab row); the smem image is [atom][k][64 points] as before
-        cuuint64_t dims[5] = {64, cuuint64_t(a.kp), 2, cuuint64_t(a.left / 128), cuuint64_t(a.right * 2 * NP)};
-        cuuint64_t str[4] = {cuuint64_t(a.left * 2), 128, 256, cuuint64_t(a.left * a.kp * 2)};
-        cuuint32_t box[5] = {64, kBK, 2, 1, 1};
-        CUtensorMap m5;
-        if (encode(&m5, xin, 5, dims, str, box, CU_TENSOR_MAP_SWIZZLE_128B)) {
-            mx = m5;
-            a.x5d = 1;
+    if (pair) {
+        // the pair kernel loads all 2 NP piece planes of a tile in one box
+        if (km) {
+            cuuint64_t dims[3] = {cuuint64_t(a.kp), cuuint64_t(a.right), cuuint64_t(2 * NP)};
+            cuuint64_t str[2] = {cuuint64_t(a.kp * 2), cuuint64_t(si.plane * 2)};
+            cuuint32_t box[3] = {kBK, kTileM, cuuint32_t(2 * NP)};
+            if (!encode(&mx, xin, 3, dims, str, box, CU_TENSOR_MAP_SWIZZLE_32B)) return cudaErrorInvalidValue;
+        } else {
+            cuuint64_t dims[4] = {cuuint64_t(a.left), cuuint64_t(a.kp), cuuint64_t(a.right), cuuint64_t(2 * NP)};
+            cuuint64_t str[3] = {cuuint64_t(a.left * 2), cuuint64_t(a.left * a.kp * 2), cuuint64_t(si.plane * 2)};
+            cuuint32_t box[4] = {64, kBK, 1, cuuint32_t(2 * NP)};
+            if (!encode(&mx, xin, 4, dims, str, box, CU_TENSOR_MAP_SWIZZLE_128B)) return cudaErrorInvalidValue;
         }
     }
     if (pair) {
@@ -1723,7 +1914,7 @@ cudaError_t tc_mode_product(const TcState &si, const TcState &so, int mu, const 
         const int64_t lines = int64_t(NP) * M.ni2 * (M.k_pad / 16) * 2 * e_bytes / 128;
         cuuint64_t dims[2] = {64, cuuint64_t(lines)};
         cuuint64_t str[1] = {128};
-        cuuint32_t box[2] = {64, cuuint32_t(e_bytes / 128)};
+        cuuint32_t box[2] = {64, cuuint32_t(NP * e_bytes / 128)};  // all pieces of (row tile, k-block, rank)
         if (!encode(&me, M.pieces2, 2, dims, str, box, CU_TENSOR_MAP_SWIZZLE_NONE)) return cudaErrorInvalidValue;
     } else {
         const int64_t rows = int64_t(NP) * M.ni * (M.k_pad / 16) * kBlocks * M.it;
@@ -1738,20 +1929,39 @@ cudaError_t tc_mode_product(const TcState &si, const TcState &so, int mu, const 
     a.tiles = tiles;
     a.pairs = (tiles + 1) / 2 * a.ni;
     int64_t grid = 2 * (a.pairs < num_sms() / 2 ? a.pairs : num_sms() / 2);
-    const int smem = (pair ? pair_stages(a.it > 64 ? 2 : 1) : kStages) * a.stage_bytes + 1024 + 256;
-    if (pair) {
-        if (fx) return dispatch_np<3, true, true>(km, epi.kind, mx, me, a, int(grid), smem, s);
-        switch (NP) {
-        case 3: return dispatch_np<3, false, true>(km, epi.kind, mx, me, a, int(grid), smem, s);
-        case 2: return dispatch_np<2, false, true>(km, epi.kind, mx, me, a, int(grid), smem, s);
-        default: return dispatch_np<1, false, true>(km, epi.kind, mx, me, a, int(grid), smem, s);
+    // output map of the pair kernel's TMA stores (row tiles of at most 64): boxes of 32 points x 16
+    // outputs per (plane, piece)
+    CUtensorMap my;
+    std::memset(&my, 0, sizeof my);
+    const int ch = a.it > 64 ? 2 : 1;
+    if (pair && ch == 1) {
+        if (km) {
+            cuuint64_t dims[3] = {cuuint64_t(a.mp), cuuint64_t(a.right), cuuint64_t(2 * NP)};
+            cuuint64_t str[2] = {cuuint64_t(a.mp * 2), cuuint64_t(so.plane * 2)};
+            cuuint32_t box[3] = {16, 32, 1};
+            if (!encode(&my, out_pieces, 3, dims, str, box, CU_TENSOR_MAP_SWIZZLE_32B)) return cudaErrorInvalidValue;
+        } else {
+            cuuint64_t dims[4] = {cuuint64_t(a.left), cuuint64_t(a.mp), cuuint64_t(a.right), cuuint64_t(2 * NP)};
+            cuuint64_t str[3] = {cuuint64_t(a.left * 2), cuuint64_t(a.left * a.mp * 2), cuuint64_t(so.plane * 2)};
+            cuuint32_t box[4] = {32, 16, 1, 1};
+            if (!encode(&my, out_pieces, 4, dims, str, box, CU_TENSOR_MAP_SWIZZLE_64B)) return cudaErrorInvalidValue;
         }
     }
-    if (fx) return dispatch_np<3, true, false>(km, epi.kind, mx, me, a, int(grid), smem, s);
+    const int smem = pair ? pair_stages(ch) * a.stage_bytes + pair_staging_bytes(ch) + 1024 + 256
+                          : kStages * a.stage_bytes + 1024 + 256;
+    if (pair) {
+        if (fx) return dispatch_np<3, true, true>(km, epi.kind, mx, me, my, a, int(grid), smem, s);
+        switch (NP) {
+        case 3: return dispatch_np<3, false, true>(km, epi.kind, mx, me, my, a, int(grid), smem, s);
+        case 2: return dispatch_np<2, false, true>(km, epi.kind, mx, me, my, a, int(grid), smem, s);
+        default: return dispatch_np<1, false, true>(km, epi.kind, mx, me, my, a, int(grid), smem, s);
+        }
+    }
+    if (fx) return dispatch_np<3, true, false>(km, epi.kind, mx, me, my, a, int(grid), smem, s);
     switch (NP) {
-    case 3: return dispatch_np<3, false, false>(km, epi.kind, mx, me, a, int(grid), smem, s);
-    case 2: return dispatch_np<2, false, false>(km, epi.kind, mx, me, a, int(grid), smem, s);
-    default: return dispatch_np<1, false, false>(km, epi.kind, mx, me, a, int(grid), smem, s);
+    case 3: return dispatch_np<3, false, false>(km, epi.kind, mx, me, my, a, int(grid), smem, s);
+    case 2: return dispatch_np<2, false, false>(km, epi.kind, mx, me, my, a, int(grid), smem, s);
+    default: return dispatch_np<1, false, false>(km, epi.kind, mx, me, my, a, int(grid), smem, s);
     }
 }
 
