@@ -76,6 +76,7 @@ struct TcScales {
     float *s_out = nullptr;               // written: scale chosen for the output pieces
     const unsigned *max_prev = nullptr;   // max |output| of the previous sweep (float bits) or a bound
     unsigned *max_cur = nullptr;          // atomicMax of |output| (float bits), zero before the launch
+    unsigned *zero_next = nullptr;        // if set: a word the kernel clears for the next launch's max_cur
 };
 
 int tc_pieces(mm_prec p);

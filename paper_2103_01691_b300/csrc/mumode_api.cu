@@ -234,14 +234,15 @@ mm_status tc_sweep(mm_plan *p, mm::TcMatrix *const *M, int &cur, const mm::TcEpi
         if (q == p->d - 1) epi = last_epi;
         mm::TcScales sc;
         if (p->fixed) {
-            const int t = int(p->sweep & 1);
-            unsigned *cur_word = p->d_max + t * p->d + q;
-            cudaError_t e = cudaMemsetAsync(cur_word, 0, sizeof(unsigned), s);
-            if (e != cudaSuccess) return cuda_fail(e, "scale word reset");
+            // W[t][q] = d_max[t d + q]: launch (sweep, q) accumulates into W[t][q] and reads W[1-t][q];
+            // it clears the word the next launch accumulates into, whose last reader has finished:
+            // W[1-t][q-1] for q >= 1, W[t][d-1] for q = 0 (tc_begin clears W[0][*] for sweep 0)
+            const int t = int(p->sweep & 1), d = p->d;
             sc.s_in = p->d_scale + q;
-            sc.s_out = p->d_scale + (q + 1) % p->d;
-            sc.max_prev = p->d_max + (1 - t) * p->d + q;
-            sc.max_cur = cur_word;
+            sc.s_out = p->d_scale + (q + 1) % d;
+            sc.max_prev = p->d_max + (1 - t) * d + q;
+            sc.max_cur = p->d_max + t * d + q;
+            sc.zero_next = (q + 1 < d) ? p->d_max + t * d + (q + 1) : p->d_max + (1 - t) * d + 0;
         }
         cudaEvent_t ev0 = timing_event(p->ctx, true);
         if (ev0) cudaEventRecord(ev0, s);
@@ -267,6 +268,10 @@ mm_status tc_begin(mm_plan *p, mm::TcMatrix *const *M, const void *u, cudaStream
         bounds[q] = acc;
     }
     p->sweep = 0;
+    if (p->d_max) {  // the maximum words of sweep 0 (later sweeps' words are cleared by the launches)
+        cudaError_t e0 = cudaMemsetAsync(p->d_max, 0, sizeof(unsigned) * p->d, s);
+        if (e0 != cudaSuccess) return cuda_fail(e0, "scale word reset");
+    }
     cudaError_t e = mm::tc_split(p->st, p->npieces, p->fixed, u, p->work[0], p->d_work, p->d_scale,
                                  p->d_max ? p->d_max + p->d : nullptr, bounds, p->d, s);
     if (e != cudaSuccess) return cuda_fail(e, "split");

@@ -721,6 +721,11 @@ __global__ void __launch_bounds__(kThreads, 1)
     cluster_sync();  // the peer's barriers are initialised before any multicast reaches them
     tc_fence_after();
     const uint32_t tmem = *tmem_slot;
+    // The next kernel of the stream may start its own set-up now; everything below reads or
+    // writes data of the previous kernel (input pieces, scale words) only after it has completed.
+    if (threadIdx.x == 0) griddep_launch_dependents();
+    griddep_wait();
+    if (FX && blockIdx.x == 0 && threadIdx.x == 0 && a.sc.zero_next) *a.sc.zero_next = 0u;
     const int rank = int(blockIdx.x & 1);
     const int64_t cid = blockIdx.x / 2, nclusters = gridDim.x / 2;
     const int half_rows = a.it / 2;
@@ -1119,6 +1124,11 @@ __global__ void __launch_bounds__(kThreads, 1)
     cluster_sync();  // both CTAs' barriers and tensor memory exist before either uses the other's
     tc_fence_after();
     const uint32_t tmem = *tmem_slot;
+    // The next kernel of the stream may start its own set-up now; everything below reads or
+    // writes data of the previous kernel (input pieces, scale words) only after it has completed.
+    if (threadIdx.x == 0) griddep_launch_dependents();
+    griddep_wait();
+    if (FX && blockIdx.x == 0 && threadIdx.x == 0 && a.sc.zero_next) *a.sc.zero_next = 0u;
     const int64_t cid = blockIdx.x / 2, nclusters = gridDim.x / 2;
     const int half = a.it / 2;
     const int e_bytes = 3 * half * 32;  // one piece's [-S; C; S] blocks in a stage
@@ -1784,13 +1794,16 @@ static cudaError_t launch_tc(const CUtensorMap &mx, const CUtensorMap &me, const
     cfg.blockDim = dim3(kThreads);
     cfg.dynamicSmemBytes = size_t(smem);
     cfg.stream = s;
-    cudaLaunchAttribute attr[1];
+    cudaLaunchAttribute attr[2];
     attr[0].id = cudaLaunchAttributeClusterDimension;
     attr[0].val.clusterDim.x = 2;
     attr[0].val.clusterDim.y = 1;
     attr[0].val.clusterDim.z = 1;
+    // may overlap the tail of the previous kernel in the stream (the kernel waits for it, griddepcontrol)
+    attr[1].id = cudaLaunchAttributeProgrammaticStreamSerialization;
+    attr[1].val.programmaticStreamSerializationAllowed = 1;
     cfg.attrs = attr;
-    cfg.numAttrs = 1;
+    cfg.numAttrs = 2;
     cudaError_t e;
     if constexpr (PAIR) {
         auto kern = a.it > 64 ? tc_pair_kernel<NP, KM, EPI, FX, 2> : tc_pair_kernel<NP, KM, EPI, FX, 1>;
