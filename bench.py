@@ -35,8 +35,8 @@ STATE_BYTES = N**3 * 8                   # complex64
 ALG_BYTES_PER_MODE = 2 * STATE_BYTES     # read + write the state once
 WORKLOAD = "free Schroedinger n=256^3 complex64, Dirichlet FD, E=expm(i*1e-4*A), u0 complex normal seed 2"
 # DRAM bytes (read + write) per mode-product launch from the ncu capture in
-# profiles/tc_mode_kernel_f16x6_n256.md; None once the kernel changes.
-NCU_TRAFFIC_BYTES = 375.6e6
+# profiles/tc_pair_kernel_f16x6_n256.md; None once the kernel changes.
+NCU_TRAFFIC_BYTES = 357.5e6
 
 
 def peaks():
@@ -341,7 +341,7 @@ def main():
             "roofline": {"bound": "tensor", "achieved": achieved, "peak": tc_peak, "unit": "TFLOP/s",
                          "frac": achieved / tc_peak,
                          "traffic": NCU_TRAFFIC_BYTES if args.prec == "f16x6" else None,
-                         "kernel": "tc_mode_kernel (one mode product)", "peak_source": f"bf16 burst (f16 same rate), {peak_src}",
+                         "kernel": "tc_pair_kernel (one mode product)", "peak_source": f"bf16 burst (f16 same rate), {peak_src}",
                          "issued_tflops": issued, "issued_frac": issued / tc_peak,
                          "issued_flop_per_step": issued_per_step,
                          "alg_bytes_per_launch": ALG_BYTES_PER_MODE,
