@@ -169,10 +169,10 @@ def run_reference(args, rank, world):
     print(json.dumps(line), flush=True)
 
 
-def cpu_baseline_leg(min_seconds: float = 10.0, max_samples: int = 64):
+def cpu_baseline_leg(min_seconds: float = 10.0, max_samples: int = 320):
     """The oracle timed on the host cores on a bounded sample: 1/16-step
     samples repeated until about min_seconds of CPU work (at most
-    max_samples of them, four full steps)."""
+    max_samples of them, twenty full steps)."""
     from oracle import oracle as orc
     from paper_2103_01691_b300 import inputs
 
@@ -302,7 +302,7 @@ def main():
     extra = {}
     if not args.no_fp64 and rank == 0:
         E50 = mm.expm(A, 1j * TAU * STEPS_PER_TRAJECTORY)
-        p64 = mm.TuckerPlan(ctx, [N] * 3, [E50] * 3, prec="fp64")
+        p64 = mm.TuckerPlan(ctx, [N] * 3, [E50] * 3, prec="fp64dmma")
         u64 = torch.from_numpy(u0.astype(np.complex128)).cuda()
         p64.step(u64, 1)
         torch.cuda.synchronize()
@@ -312,19 +312,27 @@ def main():
         err = float(torch.linalg.vector_norm(us.to(torch.complex128) - u64) / torch.linalg.vector_norm(u64))
         drift = abs(plan.norm2(us) / plan.norm2(torch.from_numpy(u0).cuda()) - 1)
         del us
-        pf = mm.TuckerPlan(ctx, [N] * 3, [E] * 3, prec="fp64")
-        e0 = torch.cuda.Event(enable_timing=True)
-        e1 = torch.cuda.Event(enable_timing=True)
-        e0.record(stream)
-        pf.step(u64, 1)
-        e1.record(stream)
-        torch.cuda.synchronize()
-        fp64_ms = e0.elapsed_time(e1)
+        # both FP64 GPU forms: FMA on the CUDA cores and the warp-level FP64 MMA (one warm step, then two)
+        fp64 = {}
+        for name, prec in (("simt", "fp64"), ("dmma", "fp64dmma")):
+            pf = mm.TuckerPlan(ctx, [N] * 3, [E] * 3, prec=prec)
+            pf.step(u64, 1)
+            e0 = torch.cuda.Event(enable_timing=True)
+            e1 = torch.cuda.Event(enable_timing=True)
+            e0.record(stream)
+            pf.step(u64, 2)
+            e1.record(stream)
+            torch.cuda.synchronize()
+            ms64 = e0.elapsed_time(e1) / 2
+            fp64[name] = {"steps_per_s": 1e3 / ms64, "ms_per_step": ms64,
+                          "tflops": FLOP_PER_STEP / (ms64 / 1e3) / 1e12}
+            del pf
+        fp64_ms = min(v["ms_per_step"] for v in fp64.values())
         extra = {"rel_err_50_steps_vs_fp64": err, "norm_drift_50_steps": drift,
                  "fp64_gpu": {"steps_per_s": 1e3 / fp64_ms, "ms_per_step": fp64_ms,
-                              "tflops": FLOP_PER_STEP / (fp64_ms / 1e3) / 1e12},
+                              "tflops": FLOP_PER_STEP / (fp64_ms / 1e3) / 1e12, "forms": fp64},
                  "speedup_vs_fp64_gpu": fp64_ms / ms_per_step}
-        del p64, pf, u64
+        del p64, u64
 
     cpu = None
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
@@ -408,12 +416,12 @@ def other_workload(args):
         line.update(value=K / (ms / 1e3), steps=K, precision="fp64", config="heat FD2 n=32^3 real, tau=1e-3")
     elif args.workload == "ho128":
         n, tau, K = 128, 0.01, 100
-        for prec in ("f16x6", "fp64"):
+        for prec in ("f16x6", "fp64", "fp64dmma"):
             plan = mm.HermitePlan(ctx, [n] * 3, prec=prec)
             x, W = plan.nodes(1)
-            dt = torch.complex128 if prec == "fp64" else torch.complex64
+            dt = torch.complex128 if prec.startswith("fp64") else torch.complex64
             psi = torch.from_numpy(inputs.harmonic_psi0(x, W, seed=1)).to(dt).cuda()
-            k = K if prec != "fp64" else 2
+            k = K if not prec.startswith("fp64") else 2
             plan.ho_step(psi, tau, k)
             ms = _time(lambda: plan.ho_step(psi, tau, k), stream)
             line[prec] = {"steps_per_s": k / (ms / 1e3), "steps": k}
@@ -452,12 +460,12 @@ def other_workload(args):
 
         each()
         ms_e = _time(each, stream)
-        # plain FP64 per-instance launches, one step each
+        # FP64 (warp-level FP64 MMA) per-instance launches, one step each
         p64 = []
         for (n1, n2, n3), u0 in zip(dims, u0s):
             nd = (int(n1), int(n2), int(n3))
             Es = [mm.expm(mm.fd_laplacian_dirichlet(v), 1j * tau) for v in nd]
-            p64.append((mm.TuckerPlan(ctx, nd, Es, prec="fp64"), torch.from_numpy(u0).cuda()))
+            p64.append((mm.TuckerPlan(ctx, nd, Es, prec="fp64dmma"), torch.from_numpy(u0).cuda()))
         ms_64 = _time(lambda: [p.step(u, 1) for p, u in p64], stream)
         flop = sum(8.0 * float(np.prod(d)) * float(np.sum(d)) for d in dims)
         line.update(value=K / (ms_b / 1e3), steps=K, precision="f16x6", problems=64,

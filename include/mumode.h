@@ -87,14 +87,29 @@ typedef enum {
  *                    sweep to sweep), so the leading product is summed
  *                    exactly; two FP16 pieces carry the remainders and the
  *                    five correction products go to a second accumulator.
- *                    Relative L2 error <= 1e-6 after 50 steps at n = 256. */
+ *                    Relative L2 error <= 1e-6 after 50 steps at n = 256.
+ * MM_PREC_FP64_DMMA  FP64 on the tensor cores through the warp-level MMA
+ *                    (m8n8k4, the only FP64 MMA form; tcgen05 has no FP64
+ *                    kind); state MM_R64 or MM_C128, same accuracy as
+ *                    MM_PREC_FP64_SIMT.
+ * MM_PREC_AUTO       chosen from the data type and sizes when the plan or
+ *                    product is created: MM_C64 -> MM_PREC_F16X6 when every
+ *                    n_mu (and m) is at most 256, else MM_PREC_FP32_SIMT;
+ *                    MM_R32 -> MM_PREC_FP32_SIMT; MM_R64, MM_C128 ->
+ *                    MM_PREC_FP64_DMMA.
+ * Not provided: split TF32 modes.  The tcgen05 FP32 accumulator truncates,
+ * so floating TF32 pieces carry the same bias as MM_PREC_BF16X6, and a
+ * fixed-point TF32 split equals MM_PREC_F16X6 with twice the bytes at half
+ * the tensor rate. */
 typedef enum {
     MM_PREC_FP64_SIMT = 0,
     MM_PREC_FP32_SIMT = 1,
     MM_PREC_BF16X6 = 2,
     MM_PREC_BF16X3 = 3,
     MM_PREC_BF16 = 4,
-    MM_PREC_F16X6 = 5
+    MM_PREC_F16X6 = 5,
+    MM_PREC_FP64_DMMA = 6,
+    MM_PREC_AUTO = 7
 } mm_prec;
 
 /* ---------------------------------------------------------------------
@@ -263,6 +278,12 @@ mm_status mumode_batch_create(mm_ctx *ctx, mm_plan *const *plans, int nprob, mm_
  * Results equal those of mumode_step on each plan. */
 mm_status mumode_batch_step(mm_batch *batch, void *const *u_dev, int64_t nsteps, void *stream);
 void mm_batch_destroy(mm_batch *batch);
+/* The same in one call: a batch over plans[0..nprob) made, stepped nsteps
+ * times with u_dev[k] in place, and released (the batch's set-up, tensor
+ * maps and records, is repeated on every call; keep a batch for many
+ * calls).  Errors as mumode_batch_create and mumode_batch_step. */
+mm_status mumode_step_batched(mm_ctx *ctx, mm_plan *const *plans, void *const *u_dev, int nprob, int64_t nsteps,
+                              void *stream);
 
 /* ---------------------------------------------------------------------
  * Hermite spectral method (section 3; section 4.3 HKP) for d = 3 with

@@ -28,6 +28,9 @@ void count_launch(int k = 1);
 // element type as the data.  fp64 selects double, otherwise float.
 cudaError_t simt_mode_product(bool fp64, bool complex_data, int64_t left, int64_t n, int64_t right,
                               int64_t m, const void *L, const void *X, void *Y, cudaStream_t s);
+// The same contraction in FP64 on the tensor cores (warp MMA m8n8k4).
+cudaError_t dmma_mode_product(bool complex_data, int64_t left, int64_t n, int64_t right, int64_t m, const void *L,
+                              const void *X, void *Y, cudaStream_t s);
 // psi *= exp(-i tb |psi|^2) for count complex elements.
 cudaError_t simt_nonlinear_phase(bool fp64, int64_t count, double tb, void *psi, cudaStream_t s);
 // g <- adjoint of the nonlinear phase at psi (psi: state before the phase).

@@ -124,10 +124,23 @@ mm_status check_ptr(const void *p, const char *name)
     return MM_OK;
 }
 
+// MM_PREC_AUTO -> a concrete precision for data type dt; tc_fits: every
+// contraction and output length within the tensor-core limit (256).
+mm_prec resolve_prec(mm_prec pr, mm_dtype dt, bool tc_fits)
+{
+    if (pr != MM_PREC_AUTO) return pr;
+    switch (dt) {
+    case MM_C64: return tc_fits ? MM_PREC_F16X6 : MM_PREC_FP32_SIMT;
+    case MM_R32: return MM_PREC_FP32_SIMT;
+    default: return MM_PREC_FP64_DMMA;
+    }
+}
+
 mm_status check_combo(mm_dtype dt, mm_prec pr, bool matrix_complex)
 {
     switch (pr) {
     case MM_PREC_FP64_SIMT:
+    case MM_PREC_FP64_DMMA:
         if (dt == MM_C128 || (dt == MM_R64 && !matrix_complex)) return MM_OK;
         break;
     case MM_PREC_FP32_SIMT:
@@ -297,7 +310,10 @@ mm_status simt_sweep(mm_plan *p, void *const *Ed, void *u, cudaStream_t s)
         left_right(p->d, p->n, mu, &left, &right);
         cudaEvent_t ev0 = timing_event(p->ctx, true);
         if (ev0) cudaEventRecord(ev0, s);
-        cudaError_t e = mm::simt_mode_product(fp64, cplx, left, p->n[mu - 1], right, p->n[mu - 1], Ed[mu - 1], src, dst, s);
+        cudaError_t e = p->prec == MM_PREC_FP64_DMMA
+                            ? mm::dmma_mode_product(cplx, left, p->n[mu - 1], right, p->n[mu - 1], Ed[mu - 1], src, dst, s)
+                            : mm::simt_mode_product(fp64, cplx, left, p->n[mu - 1], right, p->n[mu - 1], Ed[mu - 1], src,
+                                                    dst, s);
         if (ev0) cudaEventRecord(timing_event(p->ctx, false), s);
         if (e != cudaSuccess) return cuda_fail(e, "SIMT mode product launch");
         std::swap(src, dst);
@@ -352,6 +368,9 @@ mm_status plan_common(mm_ctx *ctx, int d, const int64_t *n, mm_dtype dtype, mm_p
     if (!out) return fail(MM_ERR_INVALID_ARG, "out is NULL");
     mm_status st = check_dims(d, n);
     if (st) return st;
+    bool fits = true;
+    for (int v = 0; v < d; ++v) fits = fits && n[v] <= 256;
+    prec = resolve_prec(prec, dtype, fits);
     st = check_combo(dtype, prec, matrix_complex);
     if (st) return st;
     const bool tc = mm::tc_prec(prec);
@@ -632,6 +651,7 @@ mm_status mumode_product(mm_ctx *ctx, int d, const int64_t *n, int mu, const dou
     if (m < 1 || m > (int64_t(1) << 24)) return fail(MM_ERR_SHAPE, "m = %lld out of range", (long long)m);
     if (!L) return fail(MM_ERR_INVALID_ARG, "L is NULL");
     if ((st = check_ptr(u_dev, "u_dev")) || (st = check_ptr(s_dev, "s_dev"))) return st;
+    prec = resolve_prec(prec, dtype, n[mu - 1] <= 256 && m <= 256);
     if ((st = check_combo(dtype, prec, L_is_complex != 0))) return st;
     int64_t nout[mm::kMaxDims];
     int64_t cnt_in = 1, cnt_out = 1;
@@ -651,7 +671,9 @@ mm_status mumode_product(mm_ctx *ctx, int d, const int64_t *n, int mu, const dou
         int64_t left, right;
         left_right(d, n, mu, &left, &right);
         const bool fp64 = dtype == MM_R64 || dtype == MM_C128;
-        cudaError_t e = mm::simt_mode_product(fp64, is_complex(dtype), left, nmu, right, m, Ld, u_dev, s_dev, s);
+        cudaError_t e = prec == MM_PREC_FP64_DMMA
+                            ? mm::dmma_mode_product(is_complex(dtype), left, nmu, right, m, Ld, u_dev, s_dev, s)
+                            : mm::simt_mode_product(fp64, is_complex(dtype), left, nmu, right, m, Ld, u_dev, s_dev, s);
         cudaError_t e2 = cudaStreamSynchronize(s);
         cudaFree(Ld);
         if (e != cudaSuccess) return cuda_fail(e, "SIMT mode product");
@@ -1255,4 +1277,19 @@ extern "C" void mm_batch_destroy(mm_batch *b)
         for (int t = 0; t < 2; ++t)
             if (b->dev[q][t]) cudaFree(b->dev[q][t]);
     delete b;
+}
+
+extern "C" mm_status mumode_step_batched(mm_ctx *ctx, mm_plan *const *plans, void *const *u_dev, int nprob,
+                                          int64_t nsteps, void *stream)
+{
+    mm_batch *b = nullptr;
+    mm_status st = mumode_batch_create(ctx, plans, nprob, &b);
+    if (st) return st;
+    st = mumode_batch_step(b, u_dev, nsteps, stream);
+    // the batch's device records stay in use until its launches finish
+    const cudaError_t e = cudaStreamSynchronize((cudaStream_t)stream);
+    mm_batch_destroy(b);
+    if (st) return st;
+    if (e != cudaSuccess) return cuda_fail(e, "batched step (sync)");
+    return MM_OK;
 }

@@ -112,6 +112,114 @@ __global__ void __launch_bounds__(NT) simt_mode_kernel(int64_t left, int64_t n, 
     }
 }
 
+// ---- FP64 on the tensor cores (legacy warp MMA m8n8k4, the only FP64 MMA form) -------
+//
+// D (8 x 8) += A (8 x 4) B (4 x 8) per instruction: lane t holds A[t/4][t%4], B[t%4][t/4] and
+// D[t/4][2 (t%4)], D[t/4][2 (t%4) + 1].  One CTA of 8 warps computes a 64 x 64 tile of Y (rows i,
+// columns c = (r, l)); warp w covers rows 16 (w % 4) .. + 15 and columns 32 (w / 4) .. + 31, as
+// 2 x 4 MMA tiles.  Complex data take four real products per tile and k-step.
+__device__ __forceinline__ void dmma_8x8x4(double (&d)[2], double a, double b)
+{
+    asm volatile("mma.sync.aligned.m8n8k4.row.col.f64.f64.f64.f64 {%0, %1}, {%2}, {%3}, {%0, %1};"
+                 : "+d"(d[0]), "+d"(d[1])
+                 : "d"(a), "d"(b));
+}
+
+template <bool C>
+__global__ void __launch_bounds__(NT) dmma_mode_kernel(int64_t left, int64_t n, int64_t right, int64_t m,
+                                                       const double *__restrict__ L, const double *__restrict__ X,
+                                                       double *__restrict__ Y)
+{
+    constexpr int NC = C ? 2 : 1;  // real and imaginary planes
+    __shared__ double sL[NC][BM][BK + 1];
+    __shared__ double sX[NC][BK][BN + 1];
+    const int t = threadIdx.x, warp = t / 32, lane = t % 32;
+    const int g = lane / 4, q = lane % 4;
+    const int wi = (warp % 4) * 16, wc = (warp / 4) * 32;
+    const int64_t i0 = int64_t(blockIdx.y) * BM;
+    const int64_t c0 = int64_t(blockIdx.x) * BN;
+    const int64_t ncols = left * right;
+    const bool fiber_contig = (left == 1);
+    double acc[NC][2][4][2];  // [plane][row tile][column tile][2 values]
+#pragma unroll
+    for (int p = 0; p < NC; ++p)
+#pragma unroll
+        for (int a = 0; a < 2; ++a)
+#pragma unroll
+            for (int b = 0; b < 4; ++b) acc[p][a][b][0] = acc[p][a][b][1] = 0.0;
+
+    for (int64_t k0 = 0; k0 < n; k0 += BK) {
+#pragma unroll
+        for (int s = 0; s < (BK * BM) / NT; ++s) {
+            const int e = t + NT * s;
+            const int kk = e % BK, ii = e / BK;
+            const int64_t i = i0 + ii, j = k0 + kk;
+            const bool ok = i < m && j < n;
+#pragma unroll
+            for (int p = 0; p < NC; ++p) sL[p][ii][kk] = ok ? L[(i * n + j) * NC + p] : 0.0;
+        }
+#pragma unroll
+        for (int s = 0; s < (BK * BN) / NT; ++s) {
+            const int e = t + NT * s;
+            int kk, cc;
+            if (fiber_contig) { kk = e % BK; cc = e / BK; }
+            else { cc = e % BN; kk = e / BN; }
+            const int64_t c = c0 + cc, j = k0 + kk;
+            const bool ok = c < ncols && j < n;
+            int64_t src = 0;
+            if (ok) {
+                const int64_t r = c / left, l = c - r * left;
+                src = (r * n + j) * left + l;
+            }
+#pragma unroll
+            for (int p = 0; p < NC; ++p) sX[p][kk][cc] = ok ? X[src * NC + p] : 0.0;
+        }
+        __syncthreads();
+#pragma unroll
+        for (int kk = 0; kk < BK; kk += 4) {
+            double a[NC][2], b[NC][4];
+#pragma unroll
+            for (int p = 0; p < NC; ++p) {
+#pragma unroll
+                for (int ti = 0; ti < 2; ++ti) a[p][ti] = sL[p][wi + 8 * ti + g][kk + q];
+#pragma unroll
+                for (int tj = 0; tj < 4; ++tj) b[p][tj] = sX[p][kk + q][wc + 8 * tj + g];
+            }
+#pragma unroll
+            for (int ti = 0; ti < 2; ++ti)
+#pragma unroll
+                for (int tj = 0; tj < 4; ++tj) {
+                    if (C) {
+                        // re += Lr Xr - Li Xi ; im += Lr Xi + Li Xr
+                        dmma_8x8x4(acc[0][ti][tj], a[0][ti], b[0][tj]);
+                        dmma_8x8x4(acc[0][ti][tj], -a[NC - 1][ti], b[NC - 1][tj]);
+                        dmma_8x8x4(acc[NC - 1][ti][tj], a[0][ti], b[NC - 1][tj]);
+                        dmma_8x8x4(acc[NC - 1][ti][tj], a[NC - 1][ti], b[0][tj]);
+                    } else {
+                        dmma_8x8x4(acc[0][ti][tj], a[0][ti], b[0][tj]);
+                    }
+                }
+        }
+        __syncthreads();
+    }
+#pragma unroll
+    for (int ti = 0; ti < 2; ++ti) {
+        const int64_t i = i0 + wi + 8 * ti + g;
+        if (i >= m) continue;
+#pragma unroll
+        for (int tj = 0; tj < 4; ++tj)
+#pragma unroll
+            for (int h = 0; h < 2; ++h) {
+                const int64_t c = c0 + wc + 8 * tj + 2 * q + h;
+                if (c >= ncols) continue;
+                const int64_t r = c / left, l = c - r * left;
+                const int64_t dst = (r * m + i) * left + l;
+#pragma unroll
+                for (int p = 0; p < NC; ++p) Y[dst * NC + p] = acc[p][ti][tj][h];
+            }
+    }
+}
+
 template <typename R>
 __global__ void nonlinear_phase_kernel(int64_t count, double tb, Elem<R, true> *psi)
 {
@@ -200,6 +308,22 @@ cudaError_t simt_mode_product(bool fp64, bool cplx, int64_t left, int64_t n, int
     else if (cplx) MM_LAUNCH(float, true);
     else MM_LAUNCH(float, false);
 #undef MM_LAUNCH
+    count_launch();
+    return cudaGetLastError();
+}
+
+cudaError_t dmma_mode_product(bool cplx, int64_t left, int64_t n, int64_t right, int64_t m, const void *L,
+                              const void *X, void *Y, cudaStream_t s)
+{
+    const int64_t ncols = left * right;
+    dim3 grid(unsigned((ncols + BN - 1) / BN), unsigned((m + BM - 1) / BM));
+    if (grid.y > 65535u) return cudaErrorInvalidConfiguration;
+    if (cplx)
+        dmma_mode_kernel<true><<<grid, NT, 0, s>>>(left, n, right, m, (const double *)L, (const double *)X,
+                                                  (double *)Y);
+    else
+        dmma_mode_kernel<false><<<grid, NT, 0, s>>>(left, n, right, m, (const double *)L, (const double *)X,
+                                                   (double *)Y);
     count_launch();
     return cudaGetLastError();
 }

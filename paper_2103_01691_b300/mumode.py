@@ -19,7 +19,7 @@ _HERE = os.path.dirname(os.path.abspath(__file__))
 LIB_PATH = os.path.join(_HERE, "libmumode.so")
 
 MM_R64, MM_C64, MM_C128, MM_R32 = 0, 1, 2, 3
-PREC = {"fp64": 0, "fp32": 1, "bf16x6": 2, "bf16x3": 3, "bf16": 4, "f16x6": 5}
+PREC = {"fp64": 0, "fp32": 1, "bf16x6": 2, "bf16x3": 3, "bf16": 4, "f16x6": 5, "fp64dmma": 6, "auto": 7}
 STATUS = {0: "MM_OK", 1: "MM_ERR_INVALID_ARG", 2: "MM_ERR_SHAPE", 3: "MM_ERR_DTYPE", 4: "MM_ERR_ALIGN",
           5: "MM_ERR_OOM", 6: "MM_ERR_CUDA", 7: "MM_ERR_TIMEOUT", 8: "MM_ERR_UNSUPPORTED", 9: "MM_ERR_RANGE"}
 
@@ -51,6 +51,7 @@ SIGNATURES = {
     "mumode_batch_create": (_i, [_vp, ctypes.POINTER(_vp), _i, ctypes.POINTER(_vp)]),
     "mumode_batch_step": (_i, [_vp, ctypes.POINTER(_vp), _i64, _vp]),
     "mm_batch_destroy": (None, [_vp]),
+    "mumode_step_batched": (_i, [_vp, ctypes.POINTER(_vp), ctypes.POINTER(_vp), _i, _i64, _vp]),
     "hermite_plan_create": (_i, [_vp, _i, _i64p, _i, _i, ctypes.POINTER(_vp)]),
     "hermite_nodes": (_i, [_vp, _i, _dp, _dp]),
     "hermite_forward": (_i, [_vp, _vp, _vp, _vp]),
@@ -254,7 +255,7 @@ class TuckerPlan:
                        else np.ascontiguousarray(E, dtype=np.float64)) for E in Es]
         ptrs = (_dp * d)(*[_dptr(M) for M in self._mats])
         if dtype is None:
-            dtype = torch.complex128 if prec == "fp64" else torch.complex64
+            dtype = torch.complex128 if prec in ("fp64", "fp64dmma") else torch.complex64
         self.dtype = dtype
         code = {torch.complex64: MM_C64, torch.complex128: MM_C128, torch.float64: MM_R64, torch.float32: MM_R32}[dtype]
         optr = (_i * d)(*order) if order is not None else None
@@ -303,6 +304,17 @@ class TuckerPlan:
             pass
 
 
+def step_batched(ctx: Context, plans, us, nsteps: int = 1, stream=None):
+    """mumode_step_batched: plans stepped together in one call (the batch is
+    made and released inside; keep a Batch for repeated calls)."""
+    for u in us:
+        _need_cuda(u)
+    parr = (_vp * len(plans))(*[p.handle.value for p in plans])
+    uarr = (_vp * len(us))(*[u.data_ptr() for u in us])
+    _check(lib().mumode_step_batched(ctx.handle, parr, uarr, len(plans), int(nsteps), _stream(stream)))
+    return us
+
+
 class Batch:
     """Independent Tucker plans stepped together, one launch per direction."""
 
@@ -342,7 +354,7 @@ class HermitePlan:
         self.ctx = ctx
         self.dims = np.array(dims, dtype=np.int64)
         if dtype is None:
-            dtype = torch.complex128 if prec == "fp64" else torch.complex64
+            dtype = torch.complex128 if prec in ("fp64", "fp64dmma") else torch.complex64
         self.dtype = dtype
         code = MM_C128 if dtype == torch.complex128 else MM_C64
         h = ctypes.c_void_p()

@@ -51,13 +51,15 @@ def to_gpu(torch, a, dtype):
 
 # ------------------------------------------------------------------ FP64 paths
 
-def test_heat_fp64_n32(env, orc):
-    """Real FP64 heat equation, n = 32, tau = 1e-3, 10 steps."""
+@pytest.mark.parametrize("prec", ["fp64", "fp64dmma"])
+def test_heat_fp64_n32(env, orc, prec):
+    """Real FP64 heat equation, n = 32, tau = 1e-3, 10 steps, on the CUDA
+    cores and on the tensor cores (warp MMA m8n8k4)."""
     mm, ctx, torch = env
     n, tau = 32, 1e-3
     u0 = inputs.heat_u0(n, seed=0)
     E = mm.expm(mm.fd_laplacian_dirichlet(n), tau).real
-    plan = mm.TuckerPlan(ctx, [n] * 3, [E] * 3, prec="fp64", dtype=torch.float64)
+    plan = mm.TuckerPlan(ctx, [n] * 3, [E] * 3, prec=prec, dtype=torch.float64)
     u = to_gpu(torch, u0, torch.float64)
     plan.step(u, 10)
     Eo = orc.expm_dirichlet_fd(n, tau)
@@ -65,14 +67,15 @@ def test_heat_fp64_n32(env, orc):
     assert rel(u.cpu().numpy(), ref) <= 1e-12
 
 
+@pytest.mark.parametrize("prec", ["fp64", "fp64dmma"])
 @pytest.mark.parametrize("dims,order", [((20, 24, 17), None), ((20, 24, 17), (3, 1, 2)), ((7, 5), None),
-                                        ((9,), None), ((5, 6, 4, 3), (2, 4, 1, 3))])
-def test_complex_fp64_ragged(env, orc, dims, order):
+                                        ((9,), None), ((5, 6, 4, 3), (2, 4, 1, 3)), ((70, 33, 66), None)])
+def test_complex_fp64_ragged(env, orc, dims, order, prec):
     mm, ctx, torch = env
     tau = 1e-4
     Es = [fd_schrodinger_E(mm, n, tau) for n in dims]
     u0 = inputs.complex_normal(dims[::-1], seed=2)
-    plan = mm.TuckerPlan(ctx, dims, Es, prec="fp64", order=order)
+    plan = mm.TuckerPlan(ctx, dims, Es, prec=prec, order=order)
     u = to_gpu(torch, u0, torch.complex128)
     plan.step(u, 3)
     Eo = [orc.expm_dirichlet_fd(n, 1j * tau) for n in dims]
@@ -116,22 +119,22 @@ def test_tc_tucker_steps(env, orc, dims, prec):
     assert err <= tol
 
 
-@pytest.mark.parametrize("prec", ["f16x6", "bf16x6", "fp64", "fp32"])
+@pytest.mark.parametrize("prec", ["f16x6", "bf16x6", "fp64", "fp64dmma", "fp32"])
 @pytest.mark.parametrize("dims", [(40, 24, 18), (17, 64, 9)])
 def test_mumode_product_rectangular(env, orc, prec, dims):
     """Definition 2.1 with a rectangular complex (and a real) L."""
     mm, ctx, torch = env
     rng = np.random.default_rng(12)
     u0 = inputs.complex_normal(dims[::-1], seed=3)
-    dt = torch.complex128 if prec == "fp64" else torch.complex64
-    tol = {"fp64": 1e-13, "fp32": 1e-5, "bf16x6": 3e-7, "f16x6": 1.5e-7}[prec]
+    dt = torch.complex128 if prec in ("fp64", "fp64dmma") else torch.complex64
+    tol = {"fp64": 1e-13, "fp64dmma": 1e-13, "fp32": 1e-5, "bf16x6": 3e-7, "f16x6": 1.5e-7}[prec]
     for mu in range(1, 4):
         for m in (dims[mu - 1] + 8, max(1, dims[mu - 1] - 5)):
             for cplx in (True, False):
                 L = rng.standard_normal((m, dims[mu - 1]))
                 if cplx:
                     L = L + 1j * rng.standard_normal(L.shape)
-                uin = u0 if prec == "fp64" else u0.astype(np.complex64)
+                uin = u0 if prec in ("fp64", "fp64dmma") else u0.astype(np.complex64)
                 s = mm.mumode_product(ctx, to_gpu(torch, uin, dt), mu, L, prec=prec)
                 ref = orc.mode_product(uin.astype(complex), mu, L.astype(complex))
                 err = rel(s.cpu().numpy(), ref)
@@ -191,26 +194,27 @@ def test_harmonic_oscillator_steps(env, orc, prec):
     assert err <= tol
 
 
-@pytest.mark.parametrize("prec", ["f16x6", "fp64"])
+@pytest.mark.parametrize("prec", ["f16x6", "fp64", "fp64dmma"])
 def test_gpe_strang_steps(env, orc, prec):
     mm, ctx, torch = env
     m, beta, tau, steps = 16, 100.0, 1e-3, 20
     plan = mm.HermitePlan(ctx, [m] * 3, prec=prec)
     xo, _, Wo = orc.gauss_hermite(m)
     psi0 = inputs.gpe_psi0(xo, Wo, seed=4)
-    dt = torch.complex128 if prec == "fp64" else torch.complex64
-    pin = psi0 if prec == "fp64" else psi0.astype(np.complex64)
+    f64 = prec in ("fp64", "fp64dmma")
+    dt = torch.complex128 if f64 else torch.complex64
+    pin = psi0 if f64 else psi0.astype(np.complex64)
     psi = to_gpu(torch, pin, dt)
     plan.gpe_step(psi, beta, tau, steps)
     ref = orc.gpe_steps(pin.astype(complex), xo, Wo, beta, tau, steps)
     w3 = orc.weight3(Wo)
-    tol = 1e-11 if prec == "fp64" else 1e-6
+    tol = 1e-11 if f64 else 1e-6
     err = orc.rel_l2(psi.cpu().numpy(), ref, w3)
     print(f"GPE {prec} m={m} steps={steps} rel_err={err:.3e}")
     assert err <= tol
     n0 = plan.norm2(to_gpu(torch, pin, dt))
     n1 = plan.norm2(psi)
-    assert abs(n1 / n0 - 1) <= (1e-12 if prec == "fp64" else 1e-6)
+    assert abs(n1 / n0 - 1) <= (1e-12 if f64 else 1e-6)
 
 
 # ------------------------------------------- CTA-pair kernel vs one-SM kernel
@@ -425,3 +429,45 @@ def test_batched_uneven_problems(env, orc):
         ref = orc.tucker(us0[k].astype(np.complex64).astype(complex),
                          [orc.expm_dirichlet_fd(n, 1j * tau) for n in nd], nsteps=steps)
         assert rel(us[k].cpu().numpy(), ref) <= TOL_MODE["f16x6"] * 3 * steps
+
+
+# ------------------------------------------------------- AUTO precision, one-call batch
+
+def test_auto_precision_resolves(env):
+    """MM_PREC_AUTO picks F16X6 for complex64 data within the tensor-core
+    sizes and FP64 on the tensor cores for complex128: the results equal
+    those precisions bit for bit."""
+    mm, ctx, torch = env
+    dims, tau = (48, 40, 32), 1e-4
+    Es = [fd_schrodinger_E(mm, n, tau) for n in dims]
+    u0 = inputs.complex_normal(dims[::-1], seed=2)
+    for dt, concrete in ((torch.complex64, "f16x6"), (torch.complex128, "fp64dmma")):
+        out = []
+        for prec in ("auto", concrete):
+            plan = mm.TuckerPlan(ctx, dims, Es, prec=prec, dtype=dt)
+            plan.set_graphs(False)
+            u = to_gpu(torch, u0, dt)
+            plan.step(u, 2)
+            out.append(u)
+        torch.cuda.synchronize()
+        assert torch.equal(out[0], out[1]), concrete
+
+
+def test_step_batched_one_call(env):
+    """mumode_step_batched (the batch made and released in the call) equals
+    a kept batch object."""
+    mm, ctx, torch = env
+    dims = inputs.batched_dims(count=64, seed=3)[:4]
+    us0 = inputs.batched_u0(inputs.batched_dims(count=64, seed=3), seed=3)[:4]
+    tau, steps = 1e-4, 2
+    plans, a, b = [], [], []
+    for (n1, n2, n3), u0 in zip(dims, us0):
+        nd = (int(n1), int(n2), int(n3))
+        plans.append(mm.TuckerPlan(ctx, nd, [fd_schrodinger_E(mm, n, tau) for n in nd], prec="f16x6"))
+        a.append(to_gpu(torch, u0.astype(np.complex64), torch.complex64))
+        b.append(to_gpu(torch, u0.astype(np.complex64), torch.complex64))
+    mm.step_batched(ctx, plans, a, steps)
+    mm.Batch(ctx, plans).step(b, steps)
+    torch.cuda.synchronize()
+    for k in range(len(plans)):
+        assert torch.equal(a[k], b[k]), k
