@@ -247,6 +247,23 @@ mm_status mumode_step_host(mm_plan *plan, void *u_host, int64_t nsteps, void *st
 
 void mm_plan_destroy(mm_plan *plan);
 
+/* Autotuner (the project's own): times every kernel variant (tensor-core
+ * plans: 0 = CTA pair with row tiles of at most 64, 1 = CTA pair with row
+ * tiles of at most 128, 2 = one SM) and, for Tucker plans with d <= 4,
+ * every mode order, nsteps steps each (1..1000, after one warm step) on a
+ * scratch copy of u_dev (which is left unchanged), and keeps the fastest
+ * in the plan.  Hermite plans time harmonic-oscillator steps and keep their
+ * mode order.  Allocates a state-sized scratch for the call.  Errors:
+ * MM_ERR_INVALID_ARG, MM_ERR_OOM, and those of the timed steps (the plan's
+ * configuration is then unchanged). */
+mm_status mm_plan_autotune(mm_plan *plan, const void *u_dev, int64_t nsteps, void *stream);
+/* The plan's kernel variant and mode order (order_out: d ints, or NULL). */
+mm_status mm_plan_get_config(const mm_plan *plan, int *variant, int *order_out);
+/* Set them (order NULL keeps it; a Hermite plan's order cannot change).
+ * Drops the plan's captured graphs.  Errors: MM_ERR_INVALID_ARG,
+ * MM_ERR_UNSUPPORTED. */
+mm_status mm_plan_set_config(mm_plan *plan, int variant, const int *order);
+
 /* CUDA graphs (on by default; not from the paper).  With graphs on, the
  * tensor-core paths of mumode_step, hermite_ho_step and split_step_gpe
  * capture their whole launch sequence (split, nsteps sweeps, merge) the

@@ -58,14 +58,16 @@ struct TcMatrix {
     int64_t k_pad = 0;              // padded contraction length
     int ni = 0, it = 0;             // number of row tiles, rows per tile
     void *pieces = nullptr;         // [p][tile][k_pad/16][2 blocks (C, S)][it][16], bf16 or fp16
-    // The same pieces for the CTA-pair kernel, tiled in ni2 row tiles of it2
-    // rows (it2 a multiple of 32):
-    // [tile][k_pad/16][rank][p][3 blocks (-S, C, S)][it2/2][16], rank r
-    // holding rows r it2/2 .. of the tile, each block row 32 bytes, stored in
-    // the 32-byte swizzled order the MMA reads from shared memory.
-    void *pieces2 = nullptr;
-    int ni2 = 0, it2 = 0;
-    int kb_lo2[4] = {0, 0, 0, 0}, kb_hi2[4] = {0, 0, 0, 0};  // per pair row tile, as kb_lo / kb_hi
+    // The same pieces for the CTA-pair kernel, in two tilings (see TcPairTiles):
+    // pair[0] row tiles of at most 64 rows, pair[1] of at most 128.
+    struct TcPairTiles {
+        // [tile][k_pad/16][rank][p][3 blocks (-S, C, S)][it/2][16], rank r
+        // holding rows r it/2 .. of the tile, each block row 32 bytes, stored
+        // in the 32-byte swizzled order the MMA reads from shared memory
+        void *pieces = nullptr;
+        int ni = 0, it = 0;  // row tiles, rows per tile (a multiple of 32)
+        int kb_lo[4] = {0, 0, 0, 0}, kb_hi[4] = {0, 0, 0, 0};  // per row tile, as kb_lo / kb_hi
+    } pair[2];
     int npieces = 0;
     bool fixed = false;             // MM_PREC_F16X6 pieces
     float *rho = nullptr;           // fixed: power-of-two scale of each row (ni * it floats)
@@ -81,6 +83,13 @@ struct TcScales {
     unsigned *max_cur = nullptr;          // atomicMax of |output| (float bits), zero before the launch
     unsigned *zero_next = nullptr;        // if set: a word the kernel clears for the next launch's max_cur
 };
+
+// Kernel of a tensor-core product: the CTA-pair kernel with row tiles of at
+// most 64 (two accumulator sets) or 128 rows (one set), or the one-SM kernel.
+enum TcVariant { kTcPair64 = 0, kTcPair128 = 1, kTcOneSM = 2, kTcVariants = 3 };
+// The variant a plan starts with: kTcPair64, or what the environment forces
+// (MM_TC_1SM set to other than 0: kTcOneSM; MM_PAIR_TILE=128: kTcPair128).
+TcVariant tc_default_variant();
 
 int tc_pieces(mm_prec p);
 bool tc_prec(mm_prec p);
@@ -129,12 +138,15 @@ struct TcEpilogue {
 };
 // One mu-mode product on the split state: in (sizes st_in) -> out (sizes
 // st_out, equal except direction mu which becomes M.n_out).
+// The variant falls back to the one-SM kernel where M lacks its tiling.
 cudaError_t tc_mode_product(const TcState &st_in, const TcState &st_out, int mu, const TcMatrix &M,
                             mm_prec prec, const void *in_pieces, void *out_pieces,
-                            const TcEpilogue &epi, const TcScales &sc, int *d_err, cudaStream_t s);
+                            const TcEpilogue &epi, const TcScales &sc, int *d_err, cudaStream_t s,
+                            TcVariant variant = kTcPair64);
 // Tensor-core flops (2 M N K per MMA) one product issues, padding and the
 // skipped zero blocks included.
-double tc_issued_flops(const TcState &st_in, int mu, const TcMatrix &M, mm_prec prec);
+double tc_issued_flops(const TcState &st_in, int mu, const TcMatrix &M, mm_prec prec,
+                       TcVariant variant = kTcPair64);
 // The record of one such product, for a batched launch (kmajor: direction 1).
 cudaError_t tc_problem_build(const TcState &st_in, const TcState &st_out, int mu, const TcMatrix &M, mm_prec prec,
                              const void *in_pieces, void *out_pieces, const TcScales &sc, TcProblem *pr, bool *kmajor);

@@ -3,6 +3,7 @@
 #include <cuda_runtime.h>
 
 #include <atomic>
+#include <algorithm>
 #include <cmath>
 #include <complex>
 #include <cstdarg>
@@ -39,6 +40,7 @@ struct mm_plan {
     bool tc = false;
     bool fixed = false;  // MM_PREC_F16X6
     int npieces = 0;
+    mm::TcVariant variant = mm::kTcPair64;  // tensor-core kernel (mm_plan_autotune, mm_plan_set_config)
     // fixed-point state scale words (device): scale[d], max[2][d], one work word
     float *d_scale = nullptr;
     unsigned *d_max = nullptr;
@@ -260,7 +262,7 @@ mm_status tc_sweep(mm_plan *p, mm::TcMatrix *const *M, int &cur, const mm::TcEpi
         cudaEvent_t ev0 = timing_event(p->ctx, true);
         if (ev0) cudaEventRecord(ev0, s);
         cudaError_t e = mm::tc_mode_product(p->st, p->st, mu, *M[mu - 1], p->prec, p->work[cur], p->work[1 - cur],
-                                            epi, sc, p->ctx->d_err, s);
+                                            epi, sc, p->ctx->d_err, s, p->variant);
         if (ev0) cudaEventRecord(timing_event(p->ctx, false), s);
         if (e != cudaSuccess) return cuda_fail(e, "tensor-core mode product launch");
         cur = 1 - cur;
@@ -401,6 +403,7 @@ mm_status plan_common(mm_ctx *ctx, int d, const int64_t *n, mm_dtype dtype, mm_p
     p->tc = tc;
     p->fixed = mm::tc_fixed(prec);
     p->npieces = mm::tc_pieces(prec);
+    p->variant = mm::tc_default_variant();
     *made = p;
     return MM_OK;
 }
@@ -513,10 +516,107 @@ mm_status mm_plan_issued_flops(const mm_plan *p, double *flops_per_step)
     double f = 0.0;
     for (int q = 0; q < p->d; ++q) {
         const int mu = p->order[q];
-        f += mm::tc_issued_flops(p->st, mu, p->Etc[mu - 1], p->prec);
+        f += mm::tc_issued_flops(p->st, mu, p->Etc[mu - 1], p->prec, p->variant);
     }
     *flops_per_step = f;
     return MM_OK;
+}
+
+mm_status mm_plan_get_config(const mm_plan *p, int *variant, int *order_out)
+{
+    if (!p) return fail(MM_ERR_INVALID_ARG, "plan is NULL");
+    if (variant) *variant = int(p->variant);
+    if (order_out)
+        for (int v = 0; v < p->d; ++v) order_out[v] = p->order[v];
+    return MM_OK;
+}
+
+mm_status mm_plan_set_config(mm_plan *p, int variant, const int *order)
+{
+    if (!p) return fail(MM_ERR_INVALID_ARG, "plan is NULL");
+    if (variant < 0 || variant >= mm::kTcVariants) return fail(MM_ERR_INVALID_ARG, "variant %d outside 0..2", variant);
+    if (order) {
+        if (p->hermite) return fail(MM_ERR_UNSUPPORTED, "the mode order of a Hermite plan is fixed");
+        bool seen[mm::kMaxDims] = {};
+        for (int v = 0; v < p->d; ++v) {
+            if (order[v] < 1 || order[v] > p->d || seen[order[v] - 1])
+                return fail(MM_ERR_INVALID_ARG, "order is not a permutation of 1..%d", p->d);
+            seen[order[v] - 1] = true;
+        }
+    }
+    drop_graphs(p);
+    p->variant = mm::TcVariant(variant);
+    if (order)
+        for (int v = 0; v < p->d; ++v) p->order[v] = order[v];
+    return MM_OK;
+}
+
+mm_status mm_plan_autotune(mm_plan *p, const void *u_dev, int64_t nsteps, void *stream)
+{
+    if (!p) return fail(MM_ERR_INVALID_ARG, "plan is NULL");
+    mm_status st = check_ptr(u_dev, "u_dev");
+    if (st) return st;
+    if (nsteps < 1 || nsteps > 1000) return fail(MM_ERR_INVALID_ARG, "nsteps = %lld outside 1..1000", (long long)nsteps);
+    cudaStream_t s = (cudaStream_t)stream;
+    const size_t bytes = size_t(p->count) * elem_bytes(p->dtype);
+    void *scratch = nullptr;
+    if (cudaMalloc(&scratch, bytes) != cudaSuccess) return fail(MM_ERR_OOM, "autotune scratch of %zu bytes", bytes);
+    // candidates: kernel variants (tensor-core plans) x mode orders (Tucker plans, all orders for d <= 4)
+    std::vector<int> variants;
+    if (p->tc) variants = {mm::kTcPair64, mm::kTcPair128, mm::kTcOneSM};
+    else variants = {int(p->variant)};
+    std::vector<std::vector<int>> orders;
+    std::vector<int> ord(p->order, p->order + p->d);
+    if (!p->hermite && p->d <= 4) {
+        std::vector<int> o(size_t(p->d));
+        for (int v = 0; v < p->d; ++v) o[size_t(v)] = v + 1;
+        do orders.push_back(o);
+        while (std::next_permutation(o.begin(), o.end()));
+    } else {
+        orders.push_back(ord);
+    }
+    const bool graphs = p->use_graphs;
+    p->use_graphs = false;
+    drop_graphs(p);
+    const mm::TcVariant v0 = p->variant;
+    cudaEvent_t e0 = nullptr, e1 = nullptr;
+    cudaEventCreate(&e0);
+    cudaEventCreate(&e1);
+    float best = INFINITY;
+    int best_v = int(v0);
+    std::vector<int> best_o = ord;
+    auto run = [&](int64_t k) -> mm_status {
+        return p->hermite ? hermite_ho_step(p, scratch, 0.01, k, stream) : mumode_step(p, scratch, k, stream);
+    };
+    for (int v : variants)
+        for (const auto &o : orders) {
+            p->variant = mm::TcVariant(v);
+            for (int q = 0; q < p->d; ++q) p->order[q] = o[size_t(q)];
+            cudaError_t e = cudaMemcpyAsync(scratch, u_dev, bytes, cudaMemcpyDeviceToDevice, s);
+            if (e == cudaSuccess && !(st = run(1))) {
+                cudaEventRecord(e0, s);
+                st = run(nsteps);
+                cudaEventRecord(e1, s);
+            }
+            if (e == cudaSuccess) e = cudaStreamSynchronize(s);
+            if (e != cudaSuccess && !st) st = cuda_fail(e, "autotune");
+            if (st) break;
+            float ms = 0.0f;
+            cudaEventElapsedTime(&ms, e0, e1);
+            if (ms < best) {
+                best = ms;
+                best_v = v;
+                best_o = o;
+            }
+        }
+    cudaEventDestroy(e0);
+    cudaEventDestroy(e1);
+    cudaFree(scratch);
+    p->variant = st ? v0 : mm::TcVariant(best_v);
+    const std::vector<int> &keep = st ? ord : best_o;
+    for (int q = 0; q < p->d; ++q) p->order[q] = keep[size_t(q)];
+    p->use_graphs = graphs;
+    return st;
 }
 
 mm_status mm_plan_set_graphs(mm_plan *p, int enable)
@@ -713,7 +813,8 @@ mm_status mumode_product(mm_ctx *ctx, int d, const int64_t *n, int mu, const dou
     const double bound = M.row_norm;
     e = cudaMemsetAsync(words, 0, 64, s);
     if (e == cudaSuccess) e = mm::tc_split(si, NP, fixed, u_dev, bi, uw + 4, scales, uw + 2, &bound, 1, s);
-    if (e == cudaSuccess) e = mm::tc_mode_product(si, so, mu, M, prec, bi, bo, mm::TcEpilogue{}, sc, ctx->d_err, s);
+    if (e == cudaSuccess)
+        e = mm::tc_mode_product(si, so, mu, M, prec, bi, bo, mm::TcEpilogue{}, sc, ctx->d_err, s, mm::tc_default_variant());
     if (e == cudaSuccess) e = mm::tc_merge(so, NP, fixed, bo, scales + 1, s_dev, s);
     cudaError_t e2 = cudaStreamSynchronize(s);
     cudaFree(bi);

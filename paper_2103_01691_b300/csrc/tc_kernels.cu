@@ -203,15 +203,12 @@ mm_status tc_matrix_host(const double *E, int64_t m, int64_t n, int npieces, boo
     return MM_OK;
 }
 
-// Row tile of the CTA-pair kernel: at most 64 rows (N = 128 MMAs, two
-// accumulator sets in tensor memory, so an item's MMAs overlap the drain of
-// the previous item), or with MM_PAIR_TILE=128 in the environment at most
-// 128 (N = 256 MMAs, one accumulator set), kept for comparison.  Read when
-// a matrix is created.
-static int64_t pair_tile_rows()
+TcVariant tc_default_variant()
 {
+    const char *one = std::getenv("MM_TC_1SM");
+    if (one && one[0] && !(one[0] == '0' && one[1] == 0)) return kTcOneSM;
     const char *v = std::getenv("MM_PAIR_TILE");
-    return (v && std::atoi(v) == 128) ? 128 : 64;
+    return (v && std::atoi(v) == 128) ? kTcPair128 : kTcPair64;
 }
 
 // Rearrange the pieces for the CTA-pair kernel, which tiles the rows in
@@ -223,15 +220,15 @@ static int64_t pair_tile_rows()
 // halves, swapped in rows whose bit 2 is set: the order a TMA copy with
 // 32-byte swizzling would produce, so a plain copy of 128-byte lines gives
 // the MMA its layout.  Also sets the k-block band of every pair row tile.
-static void tc_pair_layout(TcMatrix &M, const std::vector<uint16_t> &h, std::vector<uint16_t> &h2)
+static void tc_pair_layout(const TcMatrix &M, int64_t tmax, TcMatrix::TcPairTiles &P, const std::vector<uint16_t> &h,
+                           std::vector<uint16_t> &h2)
 {
     const int64_t kbs = M.k_pad / 16, m_pad = round16(M.n_out);
-    const int64_t tmax = pair_tile_rows();
-    M.ni2 = int((m_pad + tmax - 1) / tmax);
-    M.it2 = int((m_pad + M.ni2 - 1) / M.ni2 + 31) / 32 * 32;
-    const int64_t half = M.it2 / 2;
-    h2.assign(size_t(int64_t(M.npieces) * M.ni2 * kbs * 2 * 3 * half * 16), 0);
-    for (int tile = 0; tile < M.ni2; ++tile) {
+    P.ni = int((m_pad + tmax - 1) / tmax);
+    P.it = int((m_pad + P.ni - 1) / P.ni + 31) / 32 * 32;
+    const int64_t half = P.it / 2;
+    h2.assign(size_t(int64_t(M.npieces) * P.ni * kbs * 2 * 3 * half * 16), 0);
+    for (int tile = 0; tile < P.ni; ++tile) {
         int lo = int(kbs), hi = 0;
         for (int p = 0; p < M.npieces; ++p)
             for (int64_t kb = 0; kb < kbs; ++kb) {
@@ -240,7 +237,7 @@ static void tc_pair_layout(TcMatrix &M, const std::vector<uint16_t> &h, std::vec
                     const int64_t blk = (((int64_t(tile) * kbs + kb) * 2 + r) * M.npieces + p) * 3 * half;  // first row
                     for (int b = 0; b < 3; ++b)
                         for (int64_t j = 0; j < half; ++j) {
-                            const int64_t i = int64_t(tile) * M.it2 + r * half + j;  // matrix row
+                            const int64_t i = int64_t(tile) * P.it + r * half + j;  // matrix row
                             if (i >= int64_t(M.ni) * M.it) continue;                 // padding: zero
                             const int w = b == 1 ? 0 : 1;  // C is block 0 of a tile, S block 1
                             const int64_t src =
@@ -264,54 +261,39 @@ static void tc_pair_layout(TcMatrix &M, const std::vector<uint16_t> &h, std::vec
             lo = 0;
             hi = 1;
         }
-        M.kb_lo2[tile] = lo;
-        M.kb_hi2[tile] = hi;
+        P.kb_lo[tile] = lo;
+        P.kb_hi[tile] = hi;
     }
 }
 
 mm_status tc_matrix_create(const double *E, int64_t m, int64_t n, int npieces, bool fixed, TcMatrix *out)
 {
     TcMatrix M;
-    std::vector<uint16_t> h, h2;
+    std::vector<uint16_t> h;
     std::vector<float> rho;
     mm_status st = tc_matrix_host(E, m, n, npieces, fixed, &M, h, rho);
     if (st) return st;
-    tc_pair_layout(M, h, h2);
-    auto release = [&]() {
-        if (M.pieces) cudaFree(M.pieces);
-        if (M.pieces2) cudaFree(M.pieces2);
-        if (M.rho) cudaFree(M.rho);
-    };
-    if (cudaMalloc(&M.pieces, h.size() * 2) != cudaSuccess) {
-        M.pieces = nullptr;
-        return fail(MM_ERR_OOM, "cudaMalloc of %zu bytes for matrix pieces failed", h.size() * 2);
-    }
-    if (cudaMemcpy(M.pieces, h.data(), h.size() * 2, cudaMemcpyHostToDevice) != cudaSuccess) {
-        release();
-        return fail(MM_ERR_CUDA, "upload of matrix pieces failed");
-    }
-    if (!h2.empty()) {
-        if (cudaMalloc(&M.pieces2, h2.size() * 2) != cudaSuccess) {
-            M.pieces2 = nullptr;
+    auto release = [&]() { tc_matrix_destroy(&M); };
+    auto upload = [&](void **dst, const void *src, size_t bytes) -> mm_status {
+        if (cudaMalloc(dst, bytes) != cudaSuccess) {
+            *dst = nullptr;
             release();
-            return fail(MM_ERR_OOM, "cudaMalloc of %zu bytes for matrix pieces failed", h2.size() * 2);
+            return fail(MM_ERR_OOM, "cudaMalloc of %zu bytes for matrix pieces failed", bytes);
         }
-        if (cudaMemcpy(M.pieces2, h2.data(), h2.size() * 2, cudaMemcpyHostToDevice) != cudaSuccess) {
+        if (cudaMemcpy(*dst, src, bytes, cudaMemcpyHostToDevice) != cudaSuccess) {
             release();
             return fail(MM_ERR_CUDA, "upload of matrix pieces failed");
         }
+        return MM_OK;
+    };
+    if ((st = upload(&M.pieces, h.data(), h.size() * 2))) return st;
+    const int64_t tmax[2] = {64, 128};
+    for (int k = 0; k < 2; ++k) {
+        std::vector<uint16_t> h2;
+        tc_pair_layout(M, tmax[k], M.pair[k], h, h2);
+        if ((st = upload(&M.pair[k].pieces, h2.data(), h2.size() * 2))) return st;
     }
-    if (fixed) {
-        if (cudaMalloc(&M.rho, rho.size() * sizeof(float)) != cudaSuccess) {
-            M.rho = nullptr;
-            release();
-            return fail(MM_ERR_OOM, "row scales upload failed");
-        }
-        if (cudaMemcpy(M.rho, rho.data(), rho.size() * sizeof(float), cudaMemcpyHostToDevice) != cudaSuccess) {
-            release();
-            return fail(MM_ERR_OOM, "row scales upload failed");
-        }
-    }
+    if (fixed && (st = upload(reinterpret_cast<void **>(&M.rho), rho.data(), rho.size() * sizeof(float)))) return st;
     *out = M;
     return MM_OK;
 }
@@ -320,10 +302,11 @@ void tc_matrix_destroy(TcMatrix *M)
 {
     if (!M) return;
     if (M->pieces) cudaFree(M->pieces);
-    if (M->pieces2) cudaFree(M->pieces2);
+    for (auto &P : M->pair)
+        if (P.pieces) cudaFree(P.pieces);
     if (M->rho) cudaFree(M->rho);
     M->pieces = nullptr;
-    M->pieces2 = nullptr;
+    for (auto &P : M->pair) P.pieces = nullptr;
     M->rho = nullptr;
 }
 
@@ -1839,19 +1822,17 @@ static cudaError_t dispatch_np(bool km, int epi, const CUtensorMap &mx, const CU
                : launch_tc<NP, false, 0, FX, PAIR>(mx, me, my, a, grid, smem, s);
 }
 
-// The CTA-pair kernel runs where the matrix has its pair layout, unless the
-// environment variable MM_TC_1SM is set to a value other than 0 (the
-// one-SM kernel, kept for comparison).
-static bool use_pair_kernel(const TcMatrix &M)
+// The pair tiling a variant runs on, or null for the one-SM kernel (also where the matrix lacks it).
+static const TcMatrix::TcPairTiles *pair_tiles(const TcMatrix &M, TcVariant v)
 {
-    if (!M.pieces2) return false;
-    const char *v = std::getenv("MM_TC_1SM");
-    return !(v && v[0] && !(v[0] == '0' && v[1] == 0));
+    if (v == kTcOneSM) return nullptr;
+    const TcMatrix::TcPairTiles &P = M.pair[v == kTcPair128 ? 1 : 0];
+    return P.pieces ? &P : nullptr;
 }
 
 cudaError_t tc_mode_product(const TcState &si, const TcState &so, int mu, const TcMatrix &M, mm_prec prec,
                             const void *in_pieces, void *out_pieces, const TcEpilogue &epi, const TcScales &sc,
-                            int *d_err, cudaStream_t s)
+                            int *d_err, cudaStream_t s, TcVariant variant)
 {
     const int NP = tc_pieces(prec);
     const bool fx = tc_fixed(prec);
@@ -1897,7 +1878,8 @@ cudaError_t tc_mode_product(const TcState &si, const TcState &so, int mu, const 
         cuuint32_t box[4] = {64, kBK, 1, 1};
         if (!encode(&mx, xin, 4, dims, str, box, CU_TENSOR_MAP_SWIZZLE_128B)) return cudaErrorInvalidValue;
     }
-    const bool pair = use_pair_kernel(M);
+    const TcMatrix::TcPairTiles *PT = pair_tiles(M, variant);
+    const bool pair = PT != nullptr;
     if (pair) {
         // the pair kernel loads all 2 NP piece planes of a tile in one box
         if (km) {
@@ -1913,22 +1895,22 @@ cudaError_t tc_mode_product(const TcState &si, const TcState &so, int mu, const 
         }
     }
     if (pair) {
-        // the pair kernel's row tiles: ni2 tiles of it2 rows
-        a.it = M.it2;
-        a.ni = M.ni2;
+        // the pair kernel's row tiles
+        a.it = PT->it;
+        a.ni = PT->ni;
         for (int h = 0; h < 4; ++h) {
-            a.kb_lo[h] = h < M.ni2 ? M.kb_lo2[h] : 0;
-            a.kb_hi[h] = h < M.ni2 ? M.kb_hi2[h] : 1;
+            a.kb_lo[h] = h < PT->ni ? PT->kb_lo[h] : 0;
+            a.kb_hi[h] = h < PT->ni ? PT->kb_hi[h] : 1;
         }
-        // blocks [-S; C; S] of it2 / 2 rows per (piece, row tile, k-block, rank), copied as 128-byte lines
-        const int e_bytes = 3 * (M.it2 / 2) * 32;
+        // blocks [-S; C; S] of it / 2 rows per (piece, row tile, k-block, rank), copied as 128-byte lines
+        const int e_bytes = 3 * (PT->it / 2) * 32;
         a.tx_bytes = 2 * (a.e_offset + NP * e_bytes);  // both CTAs' loads complete on the leader's barrier
         a.stage_bytes = (a.e_offset + NP * e_bytes + 1023) / 1024 * 1024;
-        const int64_t lines = int64_t(NP) * M.ni2 * (M.k_pad / 16) * 2 * e_bytes / 128;
+        const int64_t lines = int64_t(NP) * PT->ni * (M.k_pad / 16) * 2 * e_bytes / 128;
         cuuint64_t dims[2] = {64, cuuint64_t(lines)};
         cuuint64_t str[1] = {128};
         cuuint32_t box[2] = {64, cuuint32_t(NP * e_bytes / 128)};  // all pieces of (row tile, k-block, rank)
-        if (!encode(&me, M.pieces2, 2, dims, str, box, CU_TENSOR_MAP_SWIZZLE_NONE)) return cudaErrorInvalidValue;
+        if (!encode(&me, PT->pieces, 2, dims, str, box, CU_TENSOR_MAP_SWIZZLE_NONE)) return cudaErrorInvalidValue;
     } else {
         const int64_t rows = int64_t(NP) * M.ni * (M.k_pad / 16) * kBlocks * M.it;
         cuuint64_t dims[2] = {16, cuuint64_t(rows)};
@@ -2110,7 +2092,7 @@ cudaError_t tc_mode_product_batched(const TcProblem *host_probs, const TcProblem
 
 // Tensor-core flops one product issues: every MMA counted as 2 M N K, per
 // work item its k-block band times the products of the precision.
-double tc_issued_flops(const TcState &si, int mu, const TcMatrix &M, mm_prec prec)
+double tc_issued_flops(const TcState &si, int mu, const TcMatrix &M, mm_prec prec, TcVariant variant)
 {
     const int NP = tc_pieces(prec);
     int64_t left = 1, right = 1;
@@ -2120,9 +2102,9 @@ double tc_issued_flops(const TcState &si, int mu, const TcMatrix &M, mm_prec pre
     const int64_t tiles = left == 1 ? (right + kTileM - 1) / kTileM : (right * aps + 1) / 2;
     const int64_t tiles_run = (tiles + 1) / 2 * 2;  // CTA pairs
     // the kernel that runs and its row tiling
-    const bool pair = use_pair_kernel(M);
-    const int it = pair ? M.it2 : M.it, ni = pair ? M.ni2 : M.ni;
-    const int *lo = pair ? M.kb_lo2 : M.kb_lo, *hi = pair ? M.kb_hi2 : M.kb_hi;
+    const TcMatrix::TcPairTiles *PT = pair_tiles(M, variant);
+    const int it = PT ? PT->it : M.it, ni = PT ? PT->ni : M.ni;
+    const int *lo = PT ? PT->kb_lo : M.kb_lo, *hi = PT ? PT->kb_hi : M.kb_hi;
     // one k-block of one point tile: per piece product 2 M N K over N = 4 it columns (one-SM kernel: the
     // real plane with N = 2 it and the imaginary plane as two of N = it; pair kernel: two of N = 2 it)
     const double per_kb = double(num_terms(NP)) * 2.0 * kTileM * (4.0 * it) * kBK;

@@ -52,6 +52,9 @@ SIGNATURES = {
     "mumode_batch_step": (_i, [_vp, ctypes.POINTER(_vp), _i64, _vp]),
     "mm_batch_destroy": (None, [_vp]),
     "mumode_step_batched": (_i, [_vp, ctypes.POINTER(_vp), ctypes.POINTER(_vp), _i, _i64, _vp]),
+    "mm_plan_autotune": (_i, [_vp, _vp, _i64, _vp]),
+    "mm_plan_get_config": (_i, [_vp, ctypes.POINTER(_i), ctypes.POINTER(_i)]),
+    "mm_plan_set_config": (_i, [_vp, _i, ctypes.POINTER(_i)]),
     "hermite_plan_create": (_i, [_vp, _i, _i64p, _i, _i, ctypes.POINTER(_vp)]),
     "hermite_nodes": (_i, [_vp, _i, _dp, _dp]),
     "hermite_forward": (_i, [_vp, _vp, _vp, _vp]),
@@ -241,7 +244,31 @@ def mumode_product_noalloc(u, mu: int, L, out=None, stream=None):
     return out
 
 
-class TuckerPlan:
+VARIANTS = ("pair64", "pair128", "one_sm")  # tensor-core kernels, mm_plan_set_config codes 0, 1, 2
+
+
+class _Tunable:
+    """Kernel variant and mode order of a plan, and the autotuner."""
+
+    def autotune(self, u, nsteps: int = 3, stream=None):
+        """mm_plan_autotune: time the variants and mode orders on a copy of u
+        (left unchanged) and keep the fastest; returns (variant, order)."""
+        _need_cuda(u)
+        _check(lib().mm_plan_autotune(self.handle, ctypes.c_void_p(u.data_ptr()), int(nsteps), _stream(stream)))
+        return self.config()
+
+    def config(self):
+        v = _i()
+        order = (_i * len(self.dims))()
+        _check(lib().mm_plan_get_config(self.handle, ctypes.byref(v), order))
+        return VARIANTS[v.value], tuple(order)
+
+    def set_config(self, variant: str, order=None):
+        optr = (_i * len(order))(*order) if order is not None else None
+        _check(lib().mm_plan_set_config(self.handle, VARIANTS.index(variant), optr))
+
+
+class TuckerPlan(_Tunable):
     """U <- U x_1 E_1 ... x_d E_d repeated (eq. (dd-tensor))."""
 
     def __init__(self, ctx: Context, dims, Es, prec: str = "f16x6", dtype=None, order=None):
@@ -345,7 +372,7 @@ class Batch:
             pass
 
 
-class HermitePlan:
+class HermitePlan(_Tunable):
     """Hermite spectral transforms and the HKP / GPE steps (sections 3, 4.3, 4.5)."""
 
     def __init__(self, ctx: Context, dims, prec: str = "f16x6", dtype=None):

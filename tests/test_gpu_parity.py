@@ -471,3 +471,50 @@ def test_step_batched_one_call(env):
     torch.cuda.synchronize()
     for k in range(len(plans)):
         assert torch.equal(a[k], b[k]), k
+
+
+# ------------------------------------------------------------------ autotuner
+
+def test_autotune_tucker(env, orc):
+    """mm_plan_autotune times the kernel variants and the mode orders on a
+    copy of the state and keeps the fastest: the given state is unchanged,
+    the chosen configuration is valid, and the tuned plan matches the
+    oracle in its order."""
+    mm, ctx, torch = env
+    dims, tau = (64, 96, 32), 1e-4
+    Es = [fd_schrodinger_E(mm, n, tau) for n in dims]
+    u0 = inputs.complex_normal(dims[::-1], seed=2).astype(np.complex64)
+    plan = mm.TuckerPlan(ctx, dims, Es, prec="f16x6")
+    assert plan.config() == ("pair64", (1, 2, 3))
+    u = to_gpu(torch, u0, torch.complex64)
+    before = u.clone()
+    variant, order = plan.autotune(u, nsteps=2)
+    torch.cuda.synchronize()
+    assert torch.equal(u, before)
+    assert variant in mm.VARIANTS and sorted(order) == [1, 2, 3]
+    plan.step(u, 2)
+    ref = orc.tucker(u0.astype(complex), [orc.expm_dirichlet_fd(n, 1j * tau) for n in dims], order=order, nsteps=2)
+    assert rel(u.cpu().numpy(), ref) <= TOL_MODE["f16x6"] * 6
+    plan.set_config("one_sm", (3, 1, 2))
+    assert plan.config() == ("one_sm", (3, 1, 2))
+    L = mm.lib()
+    assert L.mm_plan_set_config(plan.handle, 5, None) == 1  # MM_ERR_INVALID_ARG
+    bad = (mm._i * 3)(1, 1, 2)
+    assert L.mm_plan_set_config(plan.handle, 0, bad) == 1
+    ctx.status()
+
+
+def test_autotune_hermite_and_fp64(env):
+    """Hermite plans tune the kernel variant only; FP64 plans the mode order."""
+    mm, ctx, torch = env
+    hp = mm.HermitePlan(ctx, [32] * 3, prec="f16x6")
+    psi = torch.randn(32, 32, 32, dtype=torch.complex64, device="cuda")
+    v, order = hp.autotune(psi, nsteps=2)
+    assert v in mm.VARIANTS and order == (1, 2, 3)
+    with pytest.raises(mm.MumodeError):
+        hp.set_config("pair64", (2, 1, 3))
+    dims = (24, 20, 16)
+    p64 = mm.TuckerPlan(ctx, dims, [fd_schrodinger_E(mm, n, 1e-4) for n in dims], prec="fp64dmma")
+    u = torch.randn(16, 20, 24, dtype=torch.complex128, device="cuda")
+    _, order = p64.autotune(u, nsteps=1)
+    assert sorted(order) == [1, 2, 3]
