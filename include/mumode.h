@@ -301,6 +301,14 @@ void mm_batch_destroy(mm_batch *batch);
  * calls).  Errors as mumode_batch_create and mumode_batch_step. */
 mm_status mumode_step_batched(mm_ctx *ctx, mm_plan *const *plans, void *const *u_dev, int nprob, int64_t nsteps,
                               void *stream);
+/* Autotuner for batches: times every mode order (d <= 4) of a batch over
+ * plans[0..nprob), nsteps steps each (1..1000, after one warm step), on
+ * scratch copies of u_dev[k] (left unchanged), and sets the fastest order
+ * on every plan; order_out (d ints, or NULL) receives it.  Allocates the
+ * scratch copies for the call.  Errors: MM_ERR_INVALID_ARG, MM_ERR_OOM, and
+ * those of the batch calls (the plans' order is then unchanged). */
+mm_status mumode_batch_autotune(mm_ctx *ctx, mm_plan *const *plans, void *const *u_dev, int nprob, int64_t nsteps,
+                                int *order_out, void *stream);
 
 /* ---------------------------------------------------------------------
  * Hermite spectral method (section 3; section 4.3 HKP) for d = 3 with

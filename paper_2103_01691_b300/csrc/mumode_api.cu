@@ -1394,3 +1394,75 @@ extern "C" mm_status mumode_step_batched(mm_ctx *ctx, mm_plan *const *plans, voi
     if (e != cudaSuccess) return cuda_fail(e, "batched step (sync)");
     return MM_OK;
 }
+
+extern "C" mm_status mumode_batch_autotune(mm_ctx *ctx, mm_plan *const *plans, void *const *u_dev, int nprob,
+                                           int64_t nsteps, int *order_out, void *stream)
+{
+    if (!ctx || !plans || !u_dev || nprob < 1) return fail(MM_ERR_INVALID_ARG, "ctx, plans or u_dev missing");
+    if (nsteps < 1 || nsteps > 1000) return fail(MM_ERR_INVALID_ARG, "nsteps = %lld outside 1..1000", (long long)nsteps);
+    for (int k = 0; k < nprob; ++k) {
+        if (!plans[k] || !u_dev[k]) return fail(MM_ERR_INVALID_ARG, "plans[%d] or u_dev[%d] is NULL", k, k);
+        if (plans[k]->hermite || !plans[k]->tc || plans[k]->d != plans[0]->d)
+            return fail(MM_ERR_INVALID_ARG, "plan %d is not a tensor-core Tucker plan of plan 0's d", k);
+    }
+    const int d = plans[0]->d;
+    cudaStream_t s = (cudaStream_t)stream;
+    std::vector<void *> scratch(size_t(nprob), nullptr);
+    auto release = [&]() {
+        for (void *q : scratch)
+            if (q) cudaFree(q);
+    };
+    for (int k = 0; k < nprob; ++k)
+        if (cudaMalloc(&scratch[size_t(k)], size_t(plans[k]->count) * elem_bytes(plans[k]->dtype)) != cudaSuccess) {
+            scratch[size_t(k)] = nullptr;
+            release();
+            return fail(MM_ERR_OOM, "batch autotune scratch");
+        }
+    std::vector<int> ord(plans[0]->order, plans[0]->order + d), best_o = ord;
+    std::vector<std::vector<int>> orders;
+    if (d <= 4) {
+        std::vector<int> o(static_cast<size_t>(d), 0);
+        for (int v = 0; v < d; ++v) o[size_t(v)] = v + 1;
+        do orders.push_back(o);
+        while (std::next_permutation(o.begin(), o.end()));
+    } else {
+        orders.push_back(ord);
+    }
+    cudaEvent_t e0 = nullptr, e1 = nullptr;
+    cudaEventCreate(&e0);
+    cudaEventCreate(&e1);
+    float best = INFINITY;
+    mm_status st = MM_OK;
+    for (const auto &o : orders) {
+        for (int k = 0; k < nprob && !st; ++k) st = mm_plan_set_config(plans[k], int(plans[k]->variant), o.data());
+        mm_batch *b = nullptr;
+        if (!st) st = mumode_batch_create(ctx, plans, nprob, &b);
+        cudaError_t e = cudaSuccess;
+        for (int k = 0; k < nprob && !st && e == cudaSuccess; ++k)
+            e = cudaMemcpyAsync(scratch[size_t(k)], u_dev[k], size_t(plans[k]->count) * elem_bytes(plans[k]->dtype),
+                                cudaMemcpyDeviceToDevice, s);
+        if (!st && e == cudaSuccess && !(st = mumode_batch_step(b, scratch.data(), 1, stream))) {
+            cudaEventRecord(e0, s);
+            st = mumode_batch_step(b, scratch.data(), nsteps, stream);
+            cudaEventRecord(e1, s);
+        }
+        if (e == cudaSuccess) e = cudaStreamSynchronize(s);
+        if (b) mm_batch_destroy(b);
+        if (e != cudaSuccess && !st) st = cuda_fail(e, "batch autotune");
+        if (st) break;
+        float ms = 0.0f;
+        cudaEventElapsedTime(&ms, e0, e1);
+        if (ms < best) {
+            best = ms;
+            best_o = o;
+        }
+    }
+    cudaEventDestroy(e0);
+    cudaEventDestroy(e1);
+    release();
+    const std::vector<int> &keep = st ? ord : best_o;
+    for (int k = 0; k < nprob; ++k) mm_plan_set_config(plans[k], int(plans[k]->variant), keep.data());
+    if (order_out && !st)
+        for (int v = 0; v < d; ++v) order_out[v] = keep[size_t(v)];
+    return st;
+}

@@ -53,6 +53,7 @@ SIGNATURES = {
     "mm_batch_destroy": (None, [_vp]),
     "mumode_step_batched": (_i, [_vp, ctypes.POINTER(_vp), ctypes.POINTER(_vp), _i, _i64, _vp]),
     "mm_plan_autotune": (_i, [_vp, _vp, _i64, _vp]),
+    "mumode_batch_autotune": (_i, [_vp, ctypes.POINTER(_vp), ctypes.POINTER(_vp), _i, _i64, ctypes.POINTER(_i), _vp]),
     "mm_plan_get_config": (_i, [_vp, ctypes.POINTER(_i), ctypes.POINTER(_i)]),
     "mm_plan_set_config": (_i, [_vp, _i, ctypes.POINTER(_i)]),
     "hermite_plan_create": (_i, [_vp, _i, _i64p, _i, _i, ctypes.POINTER(_vp)]),
@@ -340,6 +341,18 @@ def step_batched(ctx: Context, plans, us, nsteps: int = 1, stream=None):
     uarr = (_vp * len(us))(*[u.data_ptr() for u in us])
     _check(lib().mumode_step_batched(ctx.handle, parr, uarr, len(plans), int(nsteps), _stream(stream)))
     return us
+
+
+def batch_autotune(ctx: Context, plans, us, nsteps: int = 3, stream=None):
+    """mumode_batch_autotune: the fastest common mode order of a batch over
+    plans, timed on copies of us (left unchanged) and set on every plan."""
+    for u in us:
+        _need_cuda(u)
+    parr = (_vp * len(plans))(*[p.handle.value for p in plans])
+    uarr = (_vp * len(us))(*[u.data_ptr() for u in us])
+    order = (_i * len(plans[0].dims))()
+    _check(lib().mumode_batch_autotune(ctx.handle, parr, uarr, len(plans), int(nsteps), order, _stream(stream)))
+    return tuple(order)
 
 
 class Batch:

@@ -475,6 +475,38 @@ def test_step_batched_one_call(env):
 
 # ------------------------------------------------------------------ autotuner
 
+def test_batch_autotune(env, orc):
+    """mumode_batch_autotune sets one mode order on every plan of a batch,
+    leaves the states unchanged, and the tuned batch matches the oracle in
+    that order."""
+    mm, ctx, torch = env
+    dims = inputs.batched_dims(count=64, seed=3)[:3]
+    us0 = inputs.batched_u0(inputs.batched_dims(count=64, seed=3), seed=3)[:3]
+    tau, steps = 1e-4, 2
+    plans, us = [], []
+    for (n1, n2, n3), u0 in zip(dims, us0):
+        nd = (int(n1), int(n2), int(n3))
+        plans.append(mm.TuckerPlan(ctx, nd, [fd_schrodinger_E(mm, n, tau) for n in nd], prec="f16x6"))
+        us.append(to_gpu(torch, u0.astype(np.complex64), torch.complex64))
+    before = [u.clone() for u in us]
+    order = mm.batch_autotune(ctx, plans, us, nsteps=2)
+    torch.cuda.synchronize()
+    assert sorted(order) == [1, 2, 3]
+    for p, u, b in zip(plans, us, before):
+        assert p.config()[1] == order
+        assert torch.equal(u, b)
+    mm.Batch(ctx, plans).step(us, steps)
+    for (n1, n2, n3), u0, u in zip(dims, us0, us):
+        nd = (int(n1), int(n2), int(n3))
+        ref = orc.tucker(u0.astype(complex), [orc.expm_dirichlet_fd(n, 1j * tau) for n in nd], order=order,
+                         nsteps=steps)
+        assert rel(u.cpu().numpy(), ref) <= TOL_MODE["f16x6"] * 6
+    hp = mm.HermitePlan(ctx, [32] * 3, prec="f16x6")
+    with pytest.raises(mm.MumodeError):
+        mm.batch_autotune(ctx, [plans[0], hp], us[:2], nsteps=1)
+    ctx.status()
+
+
 def test_autotune_tucker(env, orc):
     """mm_plan_autotune times the kernel variants and the mode orders on a
     copy of the state and keeps the fastest: the given state is unchanged,
