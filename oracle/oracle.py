@@ -55,6 +55,9 @@ def lib():
         L.or_ho_steps.argtypes = [i, _f64, _f64, d, i64, _c128]
         L.or_gpe_steps.argtypes = [i, _f64, _f64, d, d, i64, _c128]
         L.or_gpe_adjoint.argtypes = [i, _f64, _f64, d, d, i64, _c128, _c128, _c128]
+        L.or_hkp_hamiltonian.argtypes = [i, _f64, _f64, _f64, _f64]
+        L.or_hkp_steps.argtypes = [_i64, ctypes.POINTER(vp), ctypes.POINTER(vp), ctypes.POINTER(vp), d, i64,
+                                   _c128]
         _lib = L
     return _lib
 
@@ -202,6 +205,30 @@ def gpe_adjoint(psi0, gT, x, W, beta: float, tau: float, nsteps: int):
     lib().or_gpe_adjoint(psi0.shape[0], _f(x), _f(W), float(beta), float(tau), int(nsteps),
                          psi0, gT, g0)
     return g0
+
+
+def hkp_hamiltonian(x, W, V):
+    """H[j, k] = (k + 1/2) delta_jk + sum_l W_l phi_j(x_l) (V_l - x_l^2/2) phi_k(x_l)
+    (section 4.3: one direction's Hamiltonian in the Hermite basis)."""
+    x, W, V = _f(x), _f(W), _f(V)
+    H = np.empty((x.size, x.size))
+    lib().or_hkp_hamiltonian(x.size, x, W, V, H)
+    return H
+
+
+def hkp_steps(psi, xs, Ws, Vs, tau: float, nsteps: int = 1):
+    """nsteps HKP steps (section 4.3) for the Kronecker potential whose
+    direction-mu values at the nodes xs[mu-1] are Vs[mu-1]; psi has shape
+    (n_3, n_2, n_1)."""
+    psi = _c(psi).copy()
+    n = _dims(psi)
+    keep = [_f(a) for a in (*xs, *Ws, *Vs)]
+    for v in range(3):
+        assert keep[v].size == keep[3 + v].size == keep[6 + v].size == n[v]
+    ptr = [a.ctypes.data_as(ctypes.c_void_p) for a in keep]
+    arr = lambda k: (ctypes.c_void_p * 3)(*ptr[3 * k:3 * k + 3])
+    lib().or_hkp_steps(n, arr(0), arr(1), arr(2), float(tau), int(nsteps), psi)
+    return psi
 
 
 def _f(a):

@@ -88,3 +88,17 @@ def batched_u0(dims: np.ndarray, seed: int = 3) -> list:
 def direction(shape, seed: int = 5) -> np.ndarray:
     """Random complex direction for finite-difference checks."""
     return complex_normal(shape, seed)
+
+
+def hkp_potentials(x1: np.ndarray, x2: np.ndarray, x3: np.ndarray):
+    """Values at the nodes of the Kronecker potential of section 4.3:
+    V_1 = cos(2 pi x_1), V_2 = x_2^2/2, V_3 = x_3^2/2."""
+    return np.cos(2.0 * np.pi * x1), 0.5 * x2 * x2, 0.5 * x3 * x3
+
+
+def hkp_psi0(x1: np.ndarray, x2: np.ndarray, x3: np.ndarray) -> np.ndarray:
+    """Initial datum of section 4.3 on the tensor grid of the nodes,
+    2^{-5/2} pi^{-3/4} (x_1 + i x_2) exp(-|x|^2/4), shape (n_3, n_2, n_1)."""
+    g1, g2, g3 = np.exp(-0.25 * x1 * x1), np.exp(-0.25 * x2 * x2), np.exp(-0.25 * x3 * x3)
+    lin = x1[None, None, :] + 1j * x2[None, :, None]
+    return 2.0 ** -2.5 * np.pi ** -0.75 * lin * g3[:, None, None] * g2[None, :, None] * g1[None, None, :]

@@ -307,3 +307,96 @@ def test_gpe_adjoint_finite_differences(orc):
     fd = (J(psi0 + eps * delta) - J(psi0 - eps * delta)) / (2 * eps)
     an = float(np.real(np.vdot(g0, delta)))
     assert abs(fd - an) <= 1e-7 * max(abs(an), 1e-12) + 1e-12
+
+
+# ---------------------------------------------------------------------- HKP
+
+def _cos_matrix_closed_form(nmax: int, q: float) -> np.ndarray:
+    """<j| cos(q x) |k> in the Hermite functions, from the matrix elements of
+    the displacement operator D(a), a = i q / sqrt(2), between number
+    states: for j >= k, sqrt(k!/j!) a^(j-k) e^{-|a|^2/2} L_k^(j-k)(|a|^2);
+    the cosine keeps the even differences j - k = 2p, with a^(2p) =
+    (-1)^p (q^2/2)^p."""
+    r = q * q / 2.0
+    C = np.zeros((nmax, nmax))
+    for j in range(nmax):
+        for k in range(j + 1):
+            if (j - k) % 2:
+                continue
+            p = (j - k) // 2
+            lg = 0.5 * (math.lgamma(k + 1) - math.lgamma(j + 1))
+            C[j, k] = C[k, j] = ((-1) ** p * math.exp(lg + p * math.log(r) - r / 2)
+                                 * scipy.special.eval_genlaguerre(k, j - k, r))
+    return C
+
+
+def test_hkp_hamiltonian_closed_form(orc):
+    """Section 4.3 Hamiltonian of direction 1 (V_1 = cos(2 pi x)) in the
+    Hermite basis against closed forms for the leading block: the kinetic
+    part -1/2 d^2/dx^2 = p^2/2 from the ladder operators (diagonal
+    (2k+1)/4, second off-diagonals -sqrt((k+1)(k+2))/4) plus the cosine's
+    matrix elements from the displacement operator."""
+    m, nmax = 80, 14
+    x, _, W = orc.gauss_hermite(m)
+    H = orc.hkp_hamiltonian(x, W, np.cos(2 * np.pi * x))[:nmax, :nmax]
+    k = np.arange(nmax, dtype=float)
+    T = np.diag((2 * k + 1) / 4)
+    off = -np.sqrt((k[:-2] + 1) * (k[:-2] + 2)) / 4
+    T += np.diag(off, 2) + np.diag(off, -2)
+    ref = T + _cos_matrix_closed_form(nmax, 2 * np.pi)
+    assert np.max(np.abs(H - ref)) < 1e-11
+    assert np.max(np.abs(H - H.T)) < 1e-13
+
+
+def test_hkp_harmonic_potential_is_ho(orc):
+    """With V_mu = x^2/2 in every direction the HKP step is the harmonic
+    oscillator step (the Hamiltonian is diagonal, section 3)."""
+    m = 10
+    x, _, W = orc.gauss_hermite(m)
+    psi0 = inputs.harmonic_psi0(x, W, seed=1)
+    V = 0.5 * x * x
+    got = orc.hkp_steps(psi0, [x] * 3, [W] * 3, [V] * 3, 0.3, 2)
+    ref = orc.ho_steps(psi0, x, W, 0.3, 2)
+    assert np.max(np.abs(got - ref)) < 1e-12
+
+
+def test_hkp_eigenstate_phase(orc):
+    """An eigenvector v of H_1 (numpy eigh) times phi_2(x_2) phi_1(x_3) is an
+    eigenstate with energy lambda + 5/2 + 3/2; one HKP step of any length
+    multiplies it by exp(-i E tau) (the method is exact in time)."""
+    n = (24, 20, 16)
+    xs, Ws = [], []
+    for v in n:
+        x, _, W = orc.gauss_hermite(v)
+        xs.append(x)
+        Ws.append(W)
+    Vs = inputs.hkp_potentials(*xs)
+    lam, vec = np.linalg.eigh(orc.hkp_hamiltonian(xs[0], Ws[0], Vs[0]))
+    f1 = orc.hermite_functions(n[0], xs[0]).T @ vec[:, 3]
+    f2 = orc.hermite_functions(n[1], xs[1])[2]
+    f3 = orc.hermite_functions(n[2], xs[2])[1]
+    psi0 = (f3[:, None, None] * f2[None, :, None] * f1[None, None, :]).astype(complex)
+    E, tau = lam[3] + 2.5 + 1.5, 0.8
+    got = orc.hkp_steps(psi0, xs, Ws, Vs, tau, 1)
+    assert np.max(np.abs(got - np.exp(-1j * E * tau) * psi0)) < 1e-11 * np.max(np.abs(psi0))
+
+
+def test_hkp_norm_and_group_property(orc):
+    """The paper's initial datum: its discrete weighted norm is 2^{-5/2}
+    (closed form of the Gaussian integral), the flow conserves it, and one
+    step to T = 1 equals two steps of 1/2."""
+    n = (40, 36, 32)
+    xs, Ws = [], []
+    for v in n:
+        x, _, W = orc.gauss_hermite(v)
+        xs.append(x)
+        Ws.append(W)
+    w3 = Ws[2][:, None, None] * Ws[1][None, :, None] * Ws[0][None, None, :]
+    psi0 = inputs.hkp_psi0(*xs)
+    nrm0 = np.sum(np.abs(psi0) ** 2 * w3)
+    assert abs(nrm0 - 2 ** -2.5) < 1e-10
+    Vs = inputs.hkp_potentials(*xs)
+    one = orc.hkp_steps(psi0, xs, Ws, Vs, 1.0, 1)
+    two = orc.hkp_steps(psi0, xs, Ws, Vs, 0.5, 2)
+    assert abs(np.sum(np.abs(one) ** 2 * w3) / nrm0 - 1) < 1e-12
+    assert np.linalg.norm(one - two) <= 1e-11 * np.linalg.norm(one)
