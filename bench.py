@@ -203,7 +203,7 @@ def main():
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-fp64", action="store_true")
     ap.add_argument("--workload", default="free256",
-                    choices=["free256", "heat32", "ho128", "batched64", "gpe192"],
+                    choices=["free256", "heat32", "ho128", "batched64", "gpe192", "hkp"],
                     help="free256 (default) is the headline line; the others time the remaining workloads")
     args = ap.parse_args()
     rank, world, local = dist_env()
@@ -430,6 +430,39 @@ def other_workload(args):
             line[prec] = {"steps_per_s": k / (ms / 1e3), "steps": k}
         line.update(value=line["f16x6"]["steps_per_s"], precision="f16x6",
                     config="harmonic oscillator, Hermite n=128^3 complex64, tau=0.01 (folded propagators)")
+    elif args.workload == "hkp":
+        # section 4.3: V = cos(2 pi x_1) + x_2^2/2 + x_3^2/2, one step to T = 1
+        _, tc_peak, _, _ = peaks()
+        for n in (127, 255):
+            x, _ = mm.gauss_hermite(n)
+            Vs = list(inputs.hkp_potentials(x, x, x))
+            psi0 = inputs.hkp_psi0(x, x, x)
+            res = {}
+            for prec in ("f16x6", "fp64dmma"):
+                t0 = time.perf_counter()
+                plan = mm.HKPPlan(ctx, [n] * 3, Vs, 1.0, prec=prec)
+                setup_ms = (time.perf_counter() - t0) * 1e3
+                f64 = prec.startswith("fp64")
+                psi = torch.from_numpy(psi0).to(torch.complex128 if f64 else torch.complex64).cuda()
+                if not f64:
+                    plan.autotune(psi, nsteps=3)
+                k = 2 if f64 else 100
+                plan.step(psi, k)
+                ms = _time(lambda: plan.step(psi, k), stream)
+                res[prec] = {"ms_per_step": ms / k, "setup_ms": setup_ms,
+                             "algorithmic_tflops": 3 * 8.0 * n ** 4 / (ms / k * 1e-3) / 1e12}
+                if not f64:
+                    variant, order = plan.config()
+                    issued = plan.issued_flops() / (ms / k * 1e-3) / 1e12
+                    res[prec].update(kernel_variant=variant, mode_order=list(order), issued_tc_tflops=issued,
+                                     issued_frac_of_measured_bf16_burst=issued / tc_peak)
+                del plan, psi
+            line[f"n{n}"] = res
+        line.update(value=1e3 / line["n255"]["f16x6"]["ms_per_step"], precision="f16x6",
+                    paper_gpu_ms_per_step={"n127": {"single": 0.64, "double": 1.27},
+                                           "n255": {"single": 8.11, "double": 16.02}},
+                    config="HKP, V = cos(2 pi x1) + x2^2/2 + x3^2/2, Hermite n^3 complex, one step to T = 1; "
+                           "value = steps/s at n = 255 (setup_ms: host FP64 Hamiltonian, expm and folding)")
     elif args.workload == "gpe192":
         n, beta, tau, K = 192, 100.0, 1e-3, 500
         plan = mm.HermitePlan(ctx, [n] * 3, prec="f16x6")

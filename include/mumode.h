@@ -337,6 +337,33 @@ mm_status hermite_backward(mm_plan *plan, const void *coeffs_dev, void *values_d
  * so a step is three complex mu-mode products.  In place. */
 mm_status hermite_ho_step(mm_plan *plan, void *psi_dev, double tau, int64_t nsteps, void *stream);
 
+/* HKP with a potential in Kronecker form (section 4.3),
+ *   i psi_t = -1/2 Lap psi + (V_1(x_1) + ... + V_d(x_d)) psi.
+ *
+ * mm_hermite_hamiltonian: the Hamiltonian of one direction in the m
+ * Hermite functions, m x m real symmetric, row-major into H_out:
+ *   H[j][k] = (k + 1/2) delta_jk + sum_l phi_j(x_l) W_l (V_l - x_l^2/2) phi_k(x_l),
+ * i.e. the harmonic part -1/2 d^2/dx^2 + x^2/2 (diagonal, section 3) plus
+ * the Gauss-Hermite Galerkin matrix of V - x^2/2.  V_nodes holds V at the
+ * m nodes of mm_gauss_hermite(m), ascending; NULL means V = x^2/2 (H is
+ * then diagonal).
+ *
+ * hkp_plan_create: a Tucker plan (use mumode_step, mm_plan_autotune, ...)
+ * whose direction-mu matrix is the values-space propagator
+ *   M_mu = Psi_mu exp(-i tau H_mu) Phi_mu^W
+ * (backward transform, exact flow in coefficient space, forward transform,
+ * folded into one complex n_mu x n_mu matrix in FP64 on the host; exp by
+ * mm_expm).  A step advances psi, given by its values on the tensor grid
+ * of the Gauss-Hermite nodes (n[mu-1] nodes in direction mu, i_1 fastest),
+ * by tau with no time-discretisation error.  V_nodes[mu-1] as above (NULL,
+ * or V_nodes NULL, for harmonic directions).  dtype, prec and mode_order
+ * as for mumode_plan_create (complex dtypes only; tensor-core precisions
+ * need n_mu <= 256).  Errors: MM_ERR_SHAPE for n_mu outside 1..4096, those
+ * of mumode_plan_create. */
+mm_status mm_hermite_hamiltonian(int m, const double *V_nodes, double *H_out);
+mm_status hkp_plan_create(mm_ctx *ctx, int d, const int64_t *n, const double *const *V_nodes, double tau,
+                          mm_dtype dtype, mm_prec prec, const int *mode_order, mm_plan **out);
+
 /* nsteps Strang steps of i psi_t = -1/2 Lap psi + |x|^2/2 psi + beta |psi|^2 psi
  * (section 4.5): half linear step, exact nonlinear phase
  * psi <- psi exp(-i tau beta |psi|^2), half linear step.  Adjacent linear

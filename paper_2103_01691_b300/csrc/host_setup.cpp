@@ -207,4 +207,68 @@ void hermite_matrices(int m, const double *x, const double *W, double *fwd, doub
     }
 }
 
+// Hamiltonian of one direction of i psi_t = -1/2 Lap psi + V psi in the
+// Hermite functions (section 4.3, HKP).  -1/2 d^2/dx^2 + x^2/2 is diagonal
+// with eigenvalues k + 1/2 (section 3); the remainder V - x^2/2 enters by
+// its Galerkin matrix under the Gauss-Hermite rule of eq. (quadrature):
+//   H[j][k] = (k + 1/2) delta_jk + sum_l phi_j(x_l) W_l (V_l - x_l^2/2) phi_k(x_l).
+// V == nullptr means the harmonic potential itself (H diagonal).
+void hermite_hamiltonian(int m, const double *x, const double *W, const double *V, double *H)
+{
+    std::fill(H, H + size_t(m) * m, 0.0);
+    for (int k = 0; k < m; ++k) H[size_t(k) * m + k] = k + 0.5;
+    if (!V) return;
+    std::vector<double> phi(size_t(m) * m), g(m), col(m);  // phi[l][k] = phi_k(x_l)
+    for (int l = 0; l < m; ++l) {
+        hermite_values(m, x[l], phi.data() + size_t(l) * m);
+        g[l] = W[l] * (V[l] - 0.5 * x[l] * x[l]);
+    }
+    for (int l = 0; l < m; ++l) {
+        const double *p = phi.data() + size_t(l) * m;
+        if (g[l] == 0.0) continue;
+        for (int j = 0; j < m; ++j) {
+            const double a = g[l] * p[j];
+            double *hrow = H + size_t(j) * m;
+            for (int k = 0; k < m; ++k) hrow[k] += a * p[k];
+        }
+    }
+}
+
+// Values-space propagator of one direction over time tau (section 4.3):
+// M = Psi exp(-i tau H) Phi^W with Psi[l][k] = phi_k(x_l) and
+// Phi^W[k][l] = phi_k(x_l) W_l, so that a mu-mode product with M takes the
+// values at the nodes through the forward transform, the exact flow in
+// coefficient space and the backward transform at once.  M is m x m
+// complex, row-major.  Returns false if the exponential fails.
+bool hkp_propagator(int m, const double *V, double tau, cd *M)
+{
+    std::vector<double> x(m), W(m), fwd(size_t(m) * m), bwd(size_t(m) * m), H(size_t(m) * m);
+    gauss_hermite(m, x.data(), W.data());
+    hermite_matrices(m, x.data(), W.data(), fwd.data(), bwd.data());
+    std::vector<cd> E(size_t(m) * m, cd(0)), T(size_t(m) * m, cd(0));
+    if (V) {
+        hermite_hamiltonian(m, x.data(), W.data(), V, H.data());
+        if (!expm(m, H.data(), nullptr, cd(0.0, -tau), E.data())) return false;
+    } else {
+        for (int k = 0; k < m; ++k) E[size_t(k) * m + k] = std::polar(1.0, -tau * (k + 0.5));
+    }
+    for (int j = 0; j < m; ++j)  // T = E Phi^W
+        for (int k = 0; k < m; ++k) {
+            const cd e = E[size_t(j) * m + k];
+            if (e == cd(0)) continue;
+            const double *f = fwd.data() + size_t(k) * m;
+            cd *trow = T.data() + size_t(j) * m;
+            for (int l = 0; l < m; ++l) trow[l] += e * f[l];
+        }
+    std::fill(M, M + size_t(m) * m, cd(0));
+    for (int l = 0; l < m; ++l)  // M = Psi T
+        for (int j = 0; j < m; ++j) {
+            const double b = bwd[size_t(l) * m + j];
+            const cd *trow = T.data() + size_t(j) * m;
+            cd *mrow = M + size_t(l) * m;
+            for (int q = 0; q < m; ++q) mrow[q] += b * trow[q];
+        }
+    return true;
+}
+
 }  // namespace mm

@@ -17,6 +17,8 @@ void fd_laplacian_dirichlet(int n, double *A);
 bool expm(int n, const double *Are, const double *Aim, std::complex<double> z, std::complex<double> *E);
 bool gauss_hermite(int m, double *x, double *W);
 void hermite_matrices(int m, const double *x, const double *W, double *fwd, double *bwd);
+void hermite_hamiltonian(int m, const double *x, const double *W, const double *V, double *H);
+bool hkp_propagator(int m, const double *V, double tau, std::complex<double> *M);
 
 // ---- error reporting (mumode_api.cu) --------------------------------------
 mm_status fail(mm_status st, const char *fmt, ...);

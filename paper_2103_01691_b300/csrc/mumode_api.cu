@@ -741,6 +741,36 @@ mm_status mm_hermite_matrices(int m, double *fwd, double *bwd)
     return MM_OK;
 }
 
+mm_status mm_hermite_hamiltonian(int m, const double *V_nodes, double *H_out)
+{
+    if (m < 1 || m > 4096) return fail(MM_ERR_SHAPE, "m = %d outside 1..4096", m);
+    if (!H_out) return fail(MM_ERR_INVALID_ARG, "H_out is NULL");
+    std::vector<double> x(m), W(m);
+    mm::gauss_hermite(m, x.data(), W.data());
+    mm::hermite_hamiltonian(m, x.data(), W.data(), V_nodes, H_out);
+    return MM_OK;
+}
+
+mm_status hkp_plan_create(mm_ctx *ctx, int d, const int64_t *n, const double *const *V_nodes, double tau,
+                          mm_dtype dtype, mm_prec prec, const int *mode_order, mm_plan **out)
+{
+    if (!ctx || !n || !out) return fail(MM_ERR_INVALID_ARG, "NULL argument");
+    if (d < 1 || d > mm::kMaxDims) return fail(MM_ERR_SHAPE, "d = %d outside 1..%d", d, mm::kMaxDims);
+    if (!std::isfinite(tau)) return fail(MM_ERR_INVALID_ARG, "tau is not finite");
+    if (!is_complex(dtype)) return fail(MM_ERR_DTYPE, "HKP plans need complex data");
+    std::vector<std::vector<cd>> M(static_cast<size_t>(d));
+    std::vector<const double *> ptr(static_cast<size_t>(d), nullptr);
+    for (int v = 0; v < d; ++v) {
+        if (n[v] < 1 || n[v] > 4096) return fail(MM_ERR_SHAPE, "n[%d] = %lld outside 1..4096", v, (long long)n[v]);
+        const int m = int(n[v]);
+        M[size_t(v)].resize(size_t(m) * m);
+        if (!mm::hkp_propagator(m, V_nodes ? V_nodes[v] : nullptr, tau, M[size_t(v)].data()))
+            return fail(MM_ERR_INVALID_ARG, "expm of direction %d failed", v + 1);
+        ptr[size_t(v)] = reinterpret_cast<const double *>(M[size_t(v)].data());
+    }
+    return mumode_plan_create(ctx, d, n, ptr.data(), 1, dtype, prec, mode_order, out);
+}
+
 mm_status mumode_product(mm_ctx *ctx, int d, const int64_t *n, int mu, const double *L, int64_t m, int L_is_complex,
                          mm_dtype dtype, mm_prec prec, const void *u_dev, void *s_dev, void *stream)
 {

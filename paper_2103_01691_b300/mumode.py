@@ -57,6 +57,9 @@ SIGNATURES = {
     "mm_plan_get_config": (_i, [_vp, ctypes.POINTER(_i), ctypes.POINTER(_i)]),
     "mm_plan_set_config": (_i, [_vp, _i, ctypes.POINTER(_i)]),
     "hermite_plan_create": (_i, [_vp, _i, _i64p, _i, _i, ctypes.POINTER(_vp)]),
+    "mm_hermite_hamiltonian": (_i, [_i, _dp, _dp]),
+    "hkp_plan_create": (_i, [_vp, _i, _i64p, ctypes.POINTER(_dp), ctypes.c_double, _i, _i, ctypes.POINTER(_i),
+                             ctypes.POINTER(_vp)]),
     "hermite_nodes": (_i, [_vp, _i, _dp, _dp]),
     "hermite_forward": (_i, [_vp, _vp, _vp, _vp]),
     "hermite_backward": (_i, [_vp, _vp, _vp, _vp]),
@@ -199,6 +202,15 @@ def hermite_matrices(m: int):
     F, B = np.empty((m, m)), np.empty((m, m))
     _check(lib().mm_hermite_matrices(m, _dptr(F), _dptr(B)))
     return F, B
+
+
+def hermite_hamiltonian(m: int, V=None):
+    """mm_hermite_hamiltonian: one direction's Hamiltonian in the m Hermite
+    functions for the potential values V at the nodes (None: harmonic)."""
+    H = np.empty((m, m))
+    Vc = None if V is None else np.ascontiguousarray(V, dtype=np.float64)
+    _check(lib().mm_hermite_hamiltonian(m, _dptr(Vc) if Vc is not None else None, _dptr(H)))
+    return H
 
 
 # ------------------------------------------------------------- mu-mode product
@@ -383,6 +395,32 @@ class Batch:
             self.close()
         except Exception:
             pass
+
+
+class HKPPlan(TuckerPlan):
+    """hkp_plan_create: Tucker plan of the values-space propagators
+    Psi_mu exp(-i tau H_mu) Phi_mu^W of a Kronecker potential (section 4.3).
+    Vs[mu-1] holds V_mu at the Gauss-Hermite nodes of direction mu (see
+    gauss_hermite), or None for the harmonic x^2/2.  step() advances the
+    values at the nodes by nsteps * tau."""
+
+    def __init__(self, ctx: Context, dims, Vs, tau: float, prec: str = "f16x6", dtype=None, order=None):
+        import torch
+
+        self.ctx = ctx
+        self.dims = np.array(dims, dtype=np.int64)
+        d = len(self.dims)
+        self._mats = [None if V is None else np.ascontiguousarray(V, dtype=np.float64) for V in Vs]
+        ptrs = (_dp * d)(*[_dptr(V) if V is not None else None for V in self._mats])
+        if dtype is None:
+            dtype = torch.complex128 if prec in ("fp64", "fp64dmma") else torch.complex64
+        self.dtype = dtype
+        code = {torch.complex64: MM_C64, torch.complex128: MM_C128}[dtype]
+        optr = (_i * d)(*order) if order is not None else None
+        h = ctypes.c_void_p()
+        _check(lib().hkp_plan_create(ctx.handle, d, self.dims.ctypes.data_as(_i64p), ptrs, float(tau), code,
+                                     PREC[prec], optr, ctypes.byref(h)))
+        self.handle = h
 
 
 class HermitePlan(_Tunable):

@@ -98,7 +98,7 @@ def test_fp32_simt(env, orc):
 # ------------------------------------------------------------ tensor-core paths
 
 TC_DIMS = [(16, 16, 16), (32, 48, 16), (17, 33, 20), (64, 64, 64), (100, 37, 48), (128, 128, 64), (256, 16, 16),
-           (16, 256, 16), (16, 16, 256), (160, 48, 80), (9,), (40, 24)]
+           (16, 256, 16), (16, 16, 256), (160, 48, 80), (9,), (40, 24), (241, 20, 16), (16, 20, 255)]
 
 
 @pytest.mark.parametrize("dims", TC_DIMS)
@@ -308,6 +308,101 @@ def test_free_schrodinger_n256_50_steps_sampled(env, orc):
     print(f"n=256 50 steps f16x6 sampled rel_err={err:.3e} norm drift={abs(nrm1 / nrm0 - 1):.3e}")
     assert err <= 1e-6
     assert abs(nrm1 / nrm0 - 1) <= 1e-6
+
+
+# ------------------------------------------------------------- HKP (section 4.3)
+
+def _hkp_nodes(orc, n):
+    xs, Ws = [], []
+    for v in n:
+        x, _, W = orc.gauss_hermite(v)
+        xs.append(x)
+        Ws.append(W)
+    return xs, Ws
+
+
+@pytest.mark.parametrize("prec,tau,steps", [("f16x6", 1.0, 1), ("f16x6", 0.5, 2), ("bf16x6", 1.0, 1),
+                                            ("fp64", 1.0, 1), ("fp64dmma", 0.5, 2)])
+def test_hkp_kronecker_potential(env, orc, prec, tau, steps):
+    """HKP plan (V_1 = cos(2 pi x_1), V_2 = V_3 = x^2/2; direction 2 passed
+    as harmonic, direction 3 by its values) against the oracle's literal
+    forward / exp(-i tau H) / backward steps, to T = 1 on ragged sizes."""
+    mm, ctx, torch = env
+    n = (72, 48, 40)
+    xs, Ws = _hkp_nodes(orc, n)
+    psi0 = inputs.hkp_psi0(*xs)
+    f64 = prec in ("fp64", "fp64dmma")
+    pin = psi0 if f64 else psi0.astype(np.complex64)
+    ref = orc.hkp_steps(pin.astype(complex), xs, Ws, inputs.hkp_potentials(*xs), tau, steps)
+    xl = [mm.gauss_hermite(v)[0] for v in n]
+    Vl = inputs.hkp_potentials(*xl)
+    plan = mm.HKPPlan(ctx, n, [Vl[0], None, Vl[2]], tau, prec=prec)
+    psi = to_gpu(torch, pin, torch.complex128 if f64 else torch.complex64)
+    plan.step(psi, steps)
+    w3 = Ws[2][:, None, None] * Ws[1][None, :, None] * Ws[0][None, None, :]
+    err = orc.rel_l2(psi.cpu().numpy(), ref, w3)
+    print(f"HKP {prec} n={n} tau={tau} steps={steps} rel_err={err:.3e}")
+    assert err <= (1e-12 if f64 else 1e-6)
+
+
+def test_hkp_hamiltonian_matches_oracle(env, orc):
+    """mm_hermite_hamiltonian (library, FP64 host) equals the oracle's."""
+    mm, ctx, torch = env
+    for m in (1, 17, 64):
+        xl, _ = mm.gauss_hermite(m)
+        xo, _, Wo = orc.gauss_hermite(m)
+        H = mm.hermite_hamiltonian(m, np.cos(2 * np.pi * xl))
+        ref = orc.hkp_hamiltonian(xo, Wo, np.cos(2 * np.pi * xo))
+        assert np.max(np.abs(H - ref)) <= 1e-12 * max(1.0, np.max(np.abs(ref)))
+        assert np.array_equal(mm.hermite_hamiltonian(m, None), np.diag(np.arange(m) + 0.5))
+    with pytest.raises(mm.MumodeError):
+        mm.HKPPlan(ctx, (8, 8, 8), [None] * 3, float("nan"))
+
+
+def test_hkp_full_size_sampled(env, orc):
+    """The paper's largest single-GPU HKP size that the tensor-core path
+    takes, n = 255 per direction, one step to T = 1 in F16x6: sampled
+    entries against the oracle's Tucker operator with each direction's
+    forward transform, exp(-i H) (oracle Taylor) and backward transform
+    multiplied out, and the weighted norm against its initial value."""
+    mm, ctx, torch = env
+    n = (255, 255, 255)
+    xs, Ws = _hkp_nodes(orc, n)
+    Vs = inputs.hkp_potentials(*xs)
+    psi0 = inputs.hkp_psi0(*xs).astype(np.complex64)
+    xl = mm.gauss_hermite(255)[0]
+    Vl = inputs.hkp_potentials(xl, xl, xl)
+    plan = mm.HKPPlan(ctx, n, list(Vl), 1.0, prec="f16x6")
+    psi = to_gpu(torch, psi0, torch.complex64)
+    plan.step(psi, 1)
+    got = psi.cpu().numpy()
+    P = orc.hermite_functions(255, xs[0])
+    E1 = orc.expm_taylor(orc.hkp_hamiltonian(xs[0], Ws[0], Vs[0]), -1j)
+    M1 = P.T @ E1 @ (P * Ws[0][None, :])
+    M2 = P.T @ np.diag(np.exp(-1j * (np.arange(255) + 0.5))) @ (P * Ws[0][None, :])
+    # the packet lives at |x| < ~5 (node indices 127 +- 35); the grid reaches
+    # |x| ~ 22, where the values are tiny and the fixed-point pieces (whose
+    # error is relative to the maximum) bound the absolute error only
+    # samples: three full grid lines through the packet, one along each
+    # direction, and 40 points of its bulk, so that the sample's norm is
+    # carried by the large values like the norm of the whole tensor
+    rng = np.random.default_rng(22)
+    a = np.arange(255)
+    c = np.full(255, 127)
+    lines = [np.stack([a, c + 4, c - 3], 1), np.stack([c - 2, a, c + 5], 1), np.stack([c + 3, c - 4, a], 1)]
+    near = np.concatenate(lines + [127 + rng.integers(-35, 36, size=(40, 3))])
+    far = rng.integers(0, 255, size=(24, 3))
+    far[0] = (254, 0, 254)
+    ref_n = orc.tucker3_entries(psi0.astype(complex), M1, M2, M2, near)
+    ref_f = orc.tucker3_entries(psi0.astype(complex), M1, M2, M2, far)
+    err = rel(got[near[:, 2], near[:, 1], near[:, 0]], ref_n)
+    far_err = np.max(np.abs(got[far[:, 2], far[:, 1], far[:, 0]] - ref_f)) / np.max(np.abs(got))
+    w3 = Ws[2][:, None, None] * Ws[1][None, :, None] * Ws[0][None, None, :]
+    drift = abs(np.sum(np.abs(got) ** 2 * w3) / np.sum(np.abs(psi0.astype(complex)) ** 2 * w3) - 1)
+    print(f"HKP n=255 f16x6 sampled rel_err={err:.3e} far abs/max={far_err:.3e} norm drift={drift:.3e}")
+    assert err <= 1e-5
+    assert far_err <= 1e-6
+    assert drift <= 1e-6
 
 
 def test_fixed_point_wide_dynamic_range(env, orc):
