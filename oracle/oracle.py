@@ -56,6 +56,9 @@ def lib():
         L.or_gpe_steps.argtypes = [i, _f64, _f64, d, d, i64, _c128]
         L.or_gpe_adjoint.argtypes = [i, _f64, _f64, d, d, i64, _c128, _c128, _c128]
         L.or_hkp_hamiltonian.argtypes = [i, _f64, _f64, _f64, _f64]
+        L.or_hermite_galerkin.argtypes = [i, _f64, _f64, _f64, _f64]
+        L.or_hkmp_steps.argtypes = [_i64, ctypes.POINTER(vp), ctypes.POINTER(vp), ctypes.POINTER(vp),
+                                    ctypes.POINTER(vp), d, i64, _f64, _c128]
         L.or_hkp_steps.argtypes = [_i64, ctypes.POINTER(vp), ctypes.POINTER(vp), ctypes.POINTER(vp), d, i64,
                                    _c128]
         _lib = L
@@ -228,6 +231,33 @@ def hkp_steps(psi, xs, Ws, Vs, tau: float, nsteps: int = 1):
     ptr = [a.ctypes.data_as(ctypes.c_void_p) for a in keep]
     arr = lambda k: (ctypes.c_void_p * 3)(*ptr[3 * k:3 * k + 3])
     lib().or_hkp_steps(n, arr(0), arr(1), arr(2), float(tau), int(nsteps), psi)
+    return psi
+
+
+def hermite_galerkin(x, W, U):
+    """G[j, k] = sum_l W_l phi_j(x_l) U_l phi_k(x_l): the Galerkin matrix of
+    the multiplication by U under the Gauss-Hermite rule."""
+    x, W, U = _f(x), _f(W), _f(U)
+    G = np.empty((x.size, x.size))
+    lib().or_hermite_galerkin(x.size, x, W, U, G)
+    return G
+
+
+def hkmp_steps(psi, xs, Ws, Vs, Us, tau: float, f_mid):
+    """len(f_mid) Magnus steps (section 4.4, eq. (mag2)) for the potential
+    V_mu(x_mu) + f(t) U_mu(x_mu); Us[mu-1] may be None; f_mid[s] = f(t_s + tau/2)."""
+    psi = _c(psi).copy()
+    n = _dims(psi)
+    f_mid = _f(f_mid)
+    keep = [_f(a) for a in (*xs, *Ws, *Vs)]
+    ukeep = [None if u is None else _f(u) for u in Us]
+    for v in range(3):
+        assert keep[v].size == keep[3 + v].size == keep[6 + v].size == n[v]
+        assert ukeep[v] is None or ukeep[v].size == n[v]
+    ptr = [a.ctypes.data_as(ctypes.c_void_p) for a in keep]
+    arr = lambda k: (ctypes.c_void_p * 3)(*ptr[3 * k:3 * k + 3])
+    uarr = (ctypes.c_void_p * 3)(*[None if u is None else u.ctypes.data_as(ctypes.c_void_p) for u in ukeep])
+    lib().or_hkmp_steps(n, arr(0), arr(1), arr(2), uarr, float(tau), int(f_mid.size), f_mid, psi)
     return psi
 
 

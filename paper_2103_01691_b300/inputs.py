@@ -102,3 +102,16 @@ def hkp_psi0(x1: np.ndarray, x2: np.ndarray, x3: np.ndarray) -> np.ndarray:
     g1, g2, g3 = np.exp(-0.25 * x1 * x1), np.exp(-0.25 * x2 * x2), np.exp(-0.25 * x3 * x3)
     lin = x1[None, None, :] + 1j * x2[None, :, None]
     return 2.0 ** -2.5 * np.pi ** -0.75 * lin * g3[:, None, None] * g2[None, :, None] * g1[None, None, :]
+
+
+def hkmp_potentials(x1: np.ndarray, x2: np.ndarray, x3: np.ndarray):
+    """Potential of section 4.4 split as V_mu + f(t) U_mu at the nodes: the
+    Hamiltonian (i/2)(Lap - |x|^2 - 2 x_3 sin^2 t) of the equation
+    psi_t = H psi is i psi_t = -1/2 Lap psi + (|x|^2/2 + x_3 sin^2 t) psi,
+    so V_mu = x_mu^2/2, U_3 = x_3, U_1 = U_2 = None, f(t) = sin^2 t."""
+    return (0.5 * x1 * x1, 0.5 * x2 * x2, 0.5 * x3 * x3), (None, None, np.array(x3, dtype=np.float64))
+
+
+def hkmp_f_mid(tau: float, nsteps: int, t0: float = 0.0) -> np.ndarray:
+    """f(t) = sin^2 t at the step midpoints t0 + (s + 1/2) tau (eq. (mag2))."""
+    return np.sin(t0 + (np.arange(nsteps) + 0.5) * tau) ** 2

@@ -400,3 +400,68 @@ def test_hkp_norm_and_group_property(orc):
     two = orc.hkp_steps(psi0, xs, Ws, Vs, 0.5, 2)
     assert abs(np.sum(np.abs(one) ** 2 * w3) / nrm0 - 1) < 1e-12
     assert np.linalg.norm(one - two) <= 1e-11 * np.linalg.norm(one)
+
+
+# --------------------------------------------------------------------- HKMP
+
+def test_hermite_galerkin_closed_form(orc):
+    """Galerkin matrices of x and x^2 in the Hermite functions: x is exactly
+    tridiagonal with sqrt((k+1)/2) (ladder operators; the quadrature is exact
+    for every entry), x^2 has (2k+1)/2 on the diagonal and
+    sqrt((k+1)(k+2))/2 two off (exact away from the last row)."""
+    m = 12
+    x, _, W = orc.gauss_hermite(m)
+    k = np.arange(m, dtype=float)
+    X = orc.hermite_galerkin(x, W, x)
+    ref = np.diag(np.sqrt((k[:-1] + 1) / 2), 1)
+    ref = ref + ref.T
+    assert np.max(np.abs(X - ref)) < 1e-13
+    X2 = orc.hermite_galerkin(x, W, x * x)[: m - 1, : m - 1]
+    k = k[: m - 1]
+    ref2 = np.diag((2 * k + 1) / 2) + np.diag(np.sqrt((k[:-2] + 1) * (k[:-2] + 2)) / 2, 2)
+    ref2 = ref2 + np.triu(ref2, 1).T
+    assert np.max(np.abs(X2 - ref2)) < 1e-13
+
+
+def _hkmp_grid(orc, n):
+    xs, Ws = [], []
+    for v in n:
+        x, _, W = orc.gauss_hermite(v)
+        xs.append(x)
+        Ws.append(W)
+    return xs, Ws
+
+
+def test_hkmp_reduces_to_hkp(orc):
+    """With f = 0 the Magnus steps are HKP steps of V; with a constant f = c
+    the midpoint rule is exact and equals HKP with V + c U."""
+    n = (10, 12, 14)
+    xs, Ws = _hkmp_grid(orc, n)
+    Vs, Us = inputs.hkmp_potentials(*xs)
+    psi0 = inputs.hkp_psi0(*xs)
+    tau, steps = 0.3, 3
+    got0 = orc.hkmp_steps(psi0, xs, Ws, Vs, Us, tau, np.zeros(steps))
+    ref0 = orc.hkp_steps(psi0, xs, Ws, Vs, tau, steps)
+    assert np.max(np.abs(got0 - ref0)) < 1e-12
+    c = 0.7
+    gotc = orc.hkmp_steps(psi0, xs, Ws, Vs, Us, tau, np.full(steps, c))
+    Vc = (Vs[0], Vs[1], Vs[2] + c * Us[2])
+    refc = orc.hkp_steps(psi0, xs, Ws, Vc, tau * steps, 1)
+    assert np.max(np.abs(gotc - refc)) < 1e-12
+
+
+def test_hkmp_second_order_and_norm(orc):
+    """f = sin^2 t: the error at T = 1 against a run with tau = 1/128 falls by
+    ~4 when tau halves (order two, eq. (mag2)); the weighted norm is
+    conserved (unitary exponentials)."""
+    n = (12, 10, 14)
+    xs, Ws = _hkmp_grid(orc, n)
+    Vs, Us = inputs.hkmp_potentials(*xs)
+    psi0 = inputs.hkp_psi0(*xs)
+    run = lambda k: orc.hkmp_steps(psi0, xs, Ws, Vs, Us, 1.0 / k, inputs.hkmp_f_mid(1.0 / k, k))
+    ref = run(128)
+    e8, e16 = np.linalg.norm(run(8) - ref), np.linalg.norm(run(16) - ref)
+    assert 3.5 < e8 / e16 < 4.5
+    w3 = Ws[2][:, None, None] * Ws[1][None, :, None] * Ws[0][None, None, :]
+    nrm = lambda p: np.sum(np.abs(p) ** 2 * w3)
+    assert abs(nrm(ref) / nrm(psi0) - 1) < 1e-12
