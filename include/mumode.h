@@ -224,6 +224,37 @@ mm_status mumode_product_noalloc(int d, const int64_t *n, int mu, const double *
                                  int L_is_complex, const void *u_dev, void *s_dev, void *stream);
 
 /* ---------------------------------------------------------------------
+ * Device exponentials and matrices that change between steps (section
+ * 4.4: with a time-dependent operator the exponentials change every step,
+ * so they are computed on the GPU as well).
+ * ------------------------------------------------------------------- */
+
+/* E = exp(z (A + f B)) in FP64 on the device.  A_dev, B_dev: real n x n,
+ * row-major, device (B_dev may be NULL); E_dev: n x n complex interleaved
+ * (2 n^2 doubles), device, overlapping neither.  Scaling and squaring of
+ * the degree-18 Taylor polynomial (Paterson-Stockmeyer evaluation; the
+ * products are cuBLAS ZGEMMs).  norm_bound >= ||A + f B||_1 picks the
+ * scaling; norm_bound <= 0 has the call compute the norm on the device and
+ * synchronise the stream.  Otherwise stream-ordered.  Calls on one context
+ * share its workspace (allocated on first use): serialise them.
+ * Errors: MM_ERR_SHAPE for n outside 1..4096, MM_ERR_INVALID_ARG,
+ * MM_ERR_OOM, MM_ERR_CUDA. */
+mm_status mm_expm_device(mm_ctx *ctx, int n, const double *A_dev, const double *B_dev, double f, double z_re,
+                         double z_im, double norm_bound, double *E_dev, void *stream);
+
+/* Replace direction mu's matrix of a Tucker plan by E_dev (n_mu x n_mu
+ * complex interleaved FP64, row-major, device memory), in stream order:
+ * the plan's later steps use it.  Tensor-core plans split it into their
+ * pieces on the device (from then on no k-block of that direction is
+ * skipped); FP64 plans (MM_C128) copy it.  row_norm_bound >= max_i sum_j
+ * |E_ij| bounds the first product of a step call (fixed-point scaling);
+ * row_norm_bound <= 0 has the call read E back to compute it (synchronising
+ * the stream).  Errors: MM_ERR_INVALID_ARG (Hermite plan, mu outside 1..d),
+ * MM_ERR_DTYPE (FP32 or real SIMT plans), MM_ERR_CUDA. */
+mm_status mm_plan_set_matrix_device(mm_plan *plan, int mu, const double *E_dev, double row_norm_bound,
+                                    void *stream);
+
+/* ---------------------------------------------------------------------
  * Tucker-operator plan: U <- U x_{o_1} E_{o_1} ... x_{o_d} E_{o_d}
  * (section 2, eq. (dd-tensor)), repeated nsteps times (a marching scheme
  * with constant step).  E_host[mu-1] is the n_mu x n_mu matrix for
@@ -363,6 +394,33 @@ mm_status hermite_ho_step(mm_plan *plan, void *psi_dev, double tau, int64_t nste
 mm_status mm_hermite_hamiltonian(int m, const double *V_nodes, double *H_out);
 mm_status hkp_plan_create(mm_ctx *ctx, int d, const int64_t *n, const double *const *V_nodes, double tau,
                           mm_dtype dtype, mm_prec prec, const int *mode_order, mm_plan **out);
+
+/* HKMP (section 4.4): a time-dependent potential in Kronecker form,
+ *   i psi_t = -1/2 Lap psi + sum_mu (V_mu(x_mu) + f(t) U_mu(x_mu)) psi,
+ * Hermite pseudospectral in space and the order-two Magnus integrator
+ * (eq. (mag2), exponential midpoint rule) in time.  In coefficient space
+ * the midpoint operator is in Kronecker form, so a step is the Tucker
+ * operator of exp(-i tau (H_mu + f_mid G_mu)), H_mu as in
+ * mm_hermite_hamiltonian (from V_mu) and G_mu the Gauss-Hermite Galerkin
+ * matrix of U_mu.
+ *
+ * hkmp_plan_create: V_nodes[mu-1] (NULL, or V_nodes NULL: harmonic) and
+ * U_nodes[mu-1] (NULL, or U_nodes NULL: no time dependence in direction
+ * mu) at the mm_gauss_hermite nodes.  Directions without U keep their
+ * exponential, computed once on the host; those with U recompute it on the
+ * GPU every step (mm_expm_device's algorithm, bound from the host 1-norms
+ * of H and G) and, on the tensor cores, re-split it there.  Precisions:
+ * tensor-core ones with MM_C64, or MM_PREC_FP64_SIMT / MM_PREC_FP64_DMMA
+ * with MM_C128.  The plan is also a Hermite plan (hermite_forward, ...).
+ *
+ * hkmp_evolve: psi_dev holds the values at the nodes (i_1 fastest); the
+ * call transforms them forward, takes nsteps Magnus steps of the plan's
+ * tau in coefficient space with f_mid[k] = f(t_k + tau/2) (host array of
+ * nsteps doubles), and transforms back, in place.  The fixed-point state
+ * and the coefficients stay on the device between steps. */
+mm_status hkmp_plan_create(mm_ctx *ctx, int d, const int64_t *n, const double *const *V_nodes,
+                           const double *const *U_nodes, double tau, mm_dtype dtype, mm_prec prec, mm_plan **out);
+mm_status hkmp_evolve(mm_plan *plan, void *psi_dev, int64_t nsteps, const double *f_mid, void *stream);
 
 /* nsteps Strang steps of i psi_t = -1/2 Lap psi + |x|^2/2 psi + beta |psi|^2 psi
  * (section 4.5): half linear step, exact nonlinear phase

@@ -10,7 +10,7 @@ HERE = os.path.dirname(os.path.abspath(__file__))
 ROOT = os.path.dirname(HERE)
 CSRC = os.path.join(HERE, "csrc")
 LIB = os.path.join(HERE, "libmumode.so")
-SOURCES = ["mumode_api.cu", "simt_kernels.cu", "tc_kernels.cu", "noalloc.cu", "host_setup.cpp"]
+SOURCES = ["mumode_api.cu", "simt_kernels.cu", "tc_kernels.cu", "noalloc.cu", "host_setup.cpp", "expm_device.cu"]
 HEADERS = ["internal.h", "tc_ptx.cuh"]
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 
@@ -46,7 +46,7 @@ def build(force: bool = False, verbose: bool = False) -> str:
         if p.returncode != 0:
             raise RuntimeError("nvcc failed: " + " ".join(cmd))
     tmp = LIB + f".tmp{os.getpid()}"
-    subprocess.check_call([nvcc, *ARCH, "-shared", "-cudart", "shared", "-o", tmp, *objs])
+    subprocess.check_call([nvcc, *ARCH, "-shared", "-cudart", "shared", "-o", tmp, *objs, "-lcublas"])
     os.replace(tmp, LIB)
     return LIB
 

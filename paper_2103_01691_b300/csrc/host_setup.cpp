@@ -234,6 +234,24 @@ void hermite_hamiltonian(int m, const double *x, const double *W, const double *
     }
 }
 
+// Galerkin matrix of the multiplication by U under the Gauss-Hermite rule:
+// G[j][k] = sum_l phi_j(x_l) W_l U_l phi_k(x_l).
+void hermite_galerkin(int m, const double *x, const double *W, const double *U, double *G)
+{
+    std::fill(G, G + size_t(m) * m, 0.0);
+    std::vector<double> phi(static_cast<size_t>(m), 0.0);
+    for (int l = 0; l < m; ++l) {
+        hermite_values(m, x[l], phi.data());
+        const double g = W[l] * U[l];
+        if (g == 0.0) continue;
+        for (int j = 0; j < m; ++j) {
+            const double a = g * phi[size_t(j)];
+            double *grow = G + size_t(j) * m;
+            for (int k = 0; k < m; ++k) grow[k] += a * phi[size_t(k)];
+        }
+    }
+}
+
 // Values-space propagator of one direction over time tau (section 4.3):
 // M = Psi exp(-i tau H) Phi^W with Psi[l][k] = phi_k(x_l) and
 // Phi^W[k][l] = phi_k(x_l) W_l, so that a mu-mode product with M takes the

@@ -18,6 +18,7 @@ bool expm(int n, const double *Are, const double *Aim, std::complex<double> z, s
 bool gauss_hermite(int m, double *x, double *W);
 void hermite_matrices(int m, const double *x, const double *W, double *fwd, double *bwd);
 void hermite_hamiltonian(int m, const double *x, const double *W, const double *V, double *H);
+void hermite_galerkin(int m, const double *x, const double *W, const double *U, double *G);
 bool hkp_propagator(int m, const double *V, double tau, std::complex<double> *M);
 
 // ---- error reporting (mumode_api.cu) --------------------------------------
@@ -99,6 +100,26 @@ bool tc_fixed(mm_prec p);
 // Build the pieces of an m x n complex matrix (interleaved FP64, row-major).
 mm_status tc_matrix_create(const double *E, int64_t m, int64_t n, int npieces, bool fixed, TcMatrix *out);
 void tc_matrix_destroy(TcMatrix *M);
+// Rewrite the pieces (all layouts) and row scales of M from a device
+// matrix E (n_out x n_in complex FP64, row-major), in stream order.  The
+// k-block bands are not touched: call tc_matrix_full_bands once first.
+cudaError_t tc_matrix_update(TcMatrix &M, const double2 *E, cudaStream_t s);
+void tc_matrix_full_bands(TcMatrix &M);
+// Device FP64 matrix exponential E = exp(z (A + f B)) (expm_device.cu).
+struct ExpmWorkspace {
+    int n = 0;
+    void *blas = nullptr;            // cublasHandle_t
+    double2 *buf[6] = {};            // n x n complex each
+    double *sums = nullptr;          // n column sums
+};
+cudaError_t expm_workspace_init(ExpmWorkspace *w, int n);
+void expm_workspace_destroy(ExpmWorkspace *w);
+// ||A + f B||_1 (max column sum), computed on the device; synchronises s.
+cudaError_t expm_norm1_device(ExpmWorkspace *w, int n, const double *A, const double *B, double f, double *norm,
+                              cudaStream_t s);
+// norm_bound >= ||A + f B||_1; B may be null.  E (n x n complex) must not be a workspace buffer.
+cudaError_t expm_device(ExpmWorkspace *w, int n, const double *A, const double *B, double f, double zr, double zi,
+                        double norm_bound, double2 *E, cudaStream_t s);
 // Host half of tc_matrix_create: geometry (pieces/rho left null) and the
 // host images of the pieces and row scales.
 mm_status tc_matrix_host(const double *E, int64_t m, int64_t n, int npieces, bool fixed, TcMatrix *geom,

@@ -26,6 +26,7 @@ struct mm_ctx {
     bool timing = false;
     std::vector<std::pair<cudaEvent_t, cudaEvent_t>> events;
     size_t events_used = 0;
+    mm::ExpmWorkspace expm;  // mm_expm_device
 };
 
 struct mm_plan {
@@ -64,6 +65,17 @@ struct mm_plan {
     double prop_s[2] = {NAN, NAN};
     void *Pdev[2][mm::kMaxDims] = {};
     mm::TcMatrix Ptc[2][mm::kMaxDims] = {};
+    // HKMP (hkmp_plan_create): per direction the Hamiltonian H0 and the
+    // Galerkin matrix G of the time-dependent part (device, FP64), their
+    // 1-norms, and the step's exponential exp(-i tau (H0 + f G))
+    bool hkmp = false;
+    double tau = 0.0;
+    double *H0dev[mm::kMaxDims] = {}, *Gdev[mm::kMaxDims] = {};
+    double h0norm[mm::kMaxDims] = {}, gnorm[mm::kMaxDims] = {};
+    double2 *Edyn[mm::kMaxDims] = {};
+    void *coef = nullptr;  // coefficient tensor of hkmp_evolve
+    mm::ExpmWorkspace expm;
+    bool full_bands[mm::kMaxDims] = {};  // a device update switched direction v's bands to full
     // CUDA graphs of whole step sequences, keyed by (call, tensor, nsteps, stream, tau, beta)
     bool use_graphs = true;
     std::map<std::tuple<int, const void *, int64_t, cudaStream_t, double, double>,
@@ -689,6 +701,7 @@ void mm_ctx_destroy(mm_ctx *ctx)
     }
     cudaFree(ctx->d_err);
     cudaFree(ctx->d_scratch);
+    mm::expm_workspace_destroy(&ctx->expm);
     delete ctx;
 }
 
@@ -953,8 +966,17 @@ void mm_plan_destroy(mm_plan *p)
     if (p->d_scale) cudaFree(p->d_scale);
     if (p->d_max) cudaFree(p->d_max);
     if (p->d_work) cudaFree(p->d_work);
+    for (int v = 0; v < mm::kMaxDims; ++v) {
+        if (p->H0dev[v]) cudaFree(p->H0dev[v]);
+        if (p->Gdev[v]) cudaFree(p->Gdev[v]);
+        if (p->Edyn[v] && p->tc) cudaFree(p->Edyn[v]);  // SIMT plans alias Edev
+    }
+    if (p->coef) cudaFree(p->coef);
+    mm::expm_workspace_destroy(&p->expm);
     delete p;
 }
+
+static mm_status hermite_setup(mm_plan *p);
 
 mm_status hermite_plan_create(mm_ctx *ctx, int d, const int64_t *n, mm_dtype dtype, mm_prec prec, mm_plan **out)
 {
@@ -965,9 +987,21 @@ mm_status hermite_plan_create(mm_ctx *ctx, int d, const int64_t *n, mm_dtype dty
         delete p;
         return fail(MM_ERR_DTYPE, "Hermite plans need complex data");
     }
+    if ((st = hermite_setup(p))) {
+        mm_plan_destroy(p);
+        return st;
+    }
+    *out = p;
+    return MM_OK;
+}
+
+// Nodes, weights and transform matrices of every direction, and the workspace.
+static mm_status hermite_setup(mm_plan *p)
+{
+    mm_status st;
     p->hermite = true;
-    for (int v = 0; v < d; ++v) {
-        const int m = int(n[v]);
+    for (int v = 0; v < p->d; ++v) {
+        const int m = int(p->n[v]);
         p->x[v].resize(m);
         p->W[v].resize(m);
         p->fwd[v].resize(size_t(m) * m);
@@ -975,22 +1009,13 @@ mm_status hermite_plan_create(mm_ctx *ctx, int d, const int64_t *n, mm_dtype dty
         mm::gauss_hermite(m, p->x[v].data(), p->W[v].data());
         mm::hermite_matrices(m, p->x[v].data(), p->W[v].data(), p->fwd[v].data(), p->bwd[v].data());
         if (cudaMalloc(&p->Wdev[v], sizeof(double) * m) != cudaSuccess ||
-            cudaMemcpy(p->Wdev[v], p->W[v].data(), sizeof(double) * m, cudaMemcpyHostToDevice) != cudaSuccess) {
-            mm_plan_destroy(p);
+            cudaMemcpy(p->Wdev[v], p->W[v].data(), sizeof(double) * m, cudaMemcpyHostToDevice) != cudaSuccess)
             return fail(MM_ERR_OOM, "weights upload");
-        }
         if ((st = upload_matrix(p, p->fwd[v].data(), m, m, false, &p->Fdev[v], &p->Ftc[v])) ||
-            (st = upload_matrix(p, p->bwd[v].data(), m, m, false, &p->Bdev[v], &p->Btc[v]))) {
-            mm_plan_destroy(p);
+            (st = upload_matrix(p, p->bwd[v].data(), m, m, false, &p->Bdev[v], &p->Btc[v])))
             return st;
-        }
     }
-    if ((st = alloc_workspace(p))) {
-        mm_plan_destroy(p);
-        return st;
-    }
-    *out = p;
-    return MM_OK;
+    return alloc_workspace(p);
 }
 
 mm_status hermite_nodes(const mm_plan *p, int mu, double *x_out, double *W_out)
@@ -1495,4 +1520,201 @@ extern "C" mm_status mumode_batch_autotune(mm_ctx *ctx, mm_plan *const *plans, v
     if (order_out && !st)
         for (int v = 0; v < d; ++v) order_out[v] = keep[size_t(v)];
     return st;
+}
+
+// ---------------------------------------------------------------------------
+// Device exponentials, device matrix updates and HKMP (section 4.4)
+
+static double norm1_host(int m, const double *A)
+{
+    double best = 0.0;
+    for (int j = 0; j < m; ++j) {
+        double s = 0.0;
+        for (int i = 0; i < m; ++i) s += std::fabs(A[size_t(i) * m + j]);
+        best = std::max(best, s);
+    }
+    return best;
+}
+
+extern "C" mm_status mm_expm_device(mm_ctx *ctx, int n, const double *A_dev, const double *B_dev, double f, double z_re,
+                                    double z_im, double norm_bound, double *E_dev, void *stream)
+{
+    if (!ctx) return fail(MM_ERR_INVALID_ARG, "ctx is NULL");
+    if (n < 1 || n > 4096) return fail(MM_ERR_SHAPE, "n = %d outside 1..4096", n);
+    mm_status st;
+    if ((st = check_ptr(A_dev, "A_dev")) || (st = check_ptr(E_dev, "E_dev"))) return st;
+    if (B_dev && (st = check_ptr(B_dev, "B_dev"))) return st;
+    if (!std::isfinite(f) || !std::isfinite(z_re) || !std::isfinite(z_im) || !std::isfinite(norm_bound))
+        return fail(MM_ERR_INVALID_ARG, "f, z or norm_bound is not finite");
+    cudaStream_t s = (cudaStream_t)stream;
+    cudaError_t e = mm::expm_workspace_init(&ctx->expm, n);
+    if (e != cudaSuccess) return fail(MM_ERR_OOM, "expm workspace (%s)", cudaGetErrorString(e));
+    if (norm_bound <= 0.0) {
+        e = mm::expm_norm1_device(&ctx->expm, n, A_dev, B_dev, f, &norm_bound, s);
+        if (e != cudaSuccess) return cuda_fail(e, "expm norm");
+    }
+    e = mm::expm_device(&ctx->expm, n, A_dev, B_dev, f, z_re, z_im, norm_bound, reinterpret_cast<double2 *>(E_dev), s);
+    if (e != cudaSuccess) return cuda_fail(e, "device expm");
+    return MM_OK;
+}
+
+// Replace direction mu's matrix by a device matrix, in stream order.
+static mm_status set_matrix_device(mm_plan *p, int mu, const double2 *E, double row_norm_bound, cudaStream_t s)
+{
+    const int v = mu - 1;
+    if (p->tc) {
+        if (!p->full_bands[v]) {
+            drop_graphs(p);  // captured launches carry the old bands
+            mm::tc_matrix_full_bands(p->Etc[v]);
+            p->full_bands[v] = true;
+        }
+        p->Etc[v].row_norm = row_norm_bound;
+        cudaError_t e = mm::tc_matrix_update(p->Etc[v], E, s);
+        if (e != cudaSuccess) return cuda_fail(e, "matrix update");
+        return MM_OK;
+    }
+    if (p->dtype != MM_C128) return fail(MM_ERR_DTYPE, "device matrices need MM_C128 data on the FP64 paths");
+    if (reinterpret_cast<const void *>(E) == p->Edev[v]) return MM_OK;
+    cudaError_t e = cudaMemcpyAsync(p->Edev[v], E, sizeof(double2) * size_t(p->n[v] * p->n[v]), cudaMemcpyDeviceToDevice,
+                                    s);
+    if (e != cudaSuccess) return cuda_fail(e, "matrix copy");
+    return MM_OK;
+}
+
+extern "C" mm_status mm_plan_set_matrix_device(mm_plan *p, int mu, const double *E_dev, double row_norm_bound,
+                                               void *stream)
+{
+    if (!p) return fail(MM_ERR_INVALID_ARG, "plan is NULL");
+    if (p->hermite) return fail(MM_ERR_INVALID_ARG, "needs a Tucker plan");
+    if (mu < 1 || mu > p->d) return fail(MM_ERR_INVALID_ARG, "mu = %d outside 1..%d", mu, p->d);
+    mm_status st = check_ptr(E_dev, "E_dev");
+    if (st) return st;
+    if (!std::isfinite(row_norm_bound)) return fail(MM_ERR_INVALID_ARG, "row_norm_bound is not finite");
+    cudaStream_t s = (cudaStream_t)stream;
+    if (row_norm_bound <= 0.0 && p->tc) {
+        // max_i sum_j |E_ij| from the device copy (synchronises the stream)
+        const int64_t m = p->n[mu - 1];
+        std::vector<double> h(size_t(2 * m * m));
+        cudaError_t e = cudaMemcpyAsync(h.data(), E_dev, sizeof(double) * h.size(), cudaMemcpyDeviceToHost, s);
+        if (e == cudaSuccess) e = cudaStreamSynchronize(s);
+        if (e != cudaSuccess) return cuda_fail(e, "matrix read-back");
+        for (int64_t i = 0; i < m; ++i) {
+            double r = 0.0;
+            for (int64_t j = 0; j < m; ++j) r += std::hypot(h[size_t(2 * (i * m + j))], h[size_t(2 * (i * m + j) + 1)]);
+            row_norm_bound = std::max(row_norm_bound, r);
+        }
+    }
+    return set_matrix_device(p, mu, reinterpret_cast<const double2 *>(E_dev), row_norm_bound, s);
+}
+
+extern "C" mm_status hkmp_plan_create(mm_ctx *ctx, int d, const int64_t *n, const double *const *V_nodes,
+                                      const double *const *U_nodes, double tau, mm_dtype dtype, mm_prec prec,
+                                      mm_plan **out)
+{
+    if (!std::isfinite(tau)) return fail(MM_ERR_INVALID_ARG, "tau is not finite");
+    mm_plan *p = nullptr;
+    mm_status st = plan_common(ctx, d, n, dtype, prec, nullptr, true, out, &p);
+    if (st) return st;
+    if (!(p->tc || (dtype == MM_C128 && (p->prec == MM_PREC_FP64_SIMT || p->prec == MM_PREC_FP64_DMMA)))) {
+        delete p;
+        return fail(MM_ERR_DTYPE, "HKMP plans need a tensor-core precision (MM_C64) or an FP64 one (MM_C128)");
+    }
+    if ((st = hermite_setup(p))) {
+        mm_plan_destroy(p);
+        return st;
+    }
+    p->hkmp = true;
+    p->tau = tau;
+    int nmax = 0;
+    for (int v = 0; v < d; ++v) {
+        const int m = int(n[v]);
+        std::vector<double> H(size_t(m) * m), G(size_t(m) * m, 0.0);
+        mm::hermite_hamiltonian(m, p->x[v].data(), p->W[v].data(), V_nodes ? V_nodes[v] : nullptr, H.data());
+        std::vector<cd> E(size_t(m) * m);
+        if (!mm::expm(m, H.data(), nullptr, cd(0.0, -tau), E.data())) {
+            mm_plan_destroy(p);
+            return fail(MM_ERR_INVALID_ARG, "expm of direction %d failed", v + 1);
+        }
+        // the constant directions keep this exponential; the time-dependent
+        // ones start from it (f = 0) and are rewritten every step
+        if ((st = upload_matrix(p, reinterpret_cast<const double *>(E.data()), m, m, true, &p->Edev[v], &p->Etc[v]))) {
+            mm_plan_destroy(p);
+            return st;
+        }
+        const double *U = U_nodes ? U_nodes[v] : nullptr;
+        if (!U) continue;
+        mm::hermite_galerkin(m, p->x[v].data(), p->W[v].data(), U, G.data());
+        p->h0norm[v] = norm1_host(m, H.data());
+        p->gnorm[v] = norm1_host(m, G.data());
+        const size_t bytes = sizeof(double) * size_t(m) * m;
+        if (cudaMalloc(&p->H0dev[v], bytes) != cudaSuccess || cudaMalloc(&p->Gdev[v], bytes) != cudaSuccess ||
+            cudaMemcpy(p->H0dev[v], H.data(), bytes, cudaMemcpyHostToDevice) != cudaSuccess ||
+            cudaMemcpy(p->Gdev[v], G.data(), bytes, cudaMemcpyHostToDevice) != cudaSuccess) {
+            mm_plan_destroy(p);
+            return fail(MM_ERR_OOM, "HKMP matrices");
+        }
+        if (p->tc) {
+            if (cudaMalloc(&p->Edyn[v], 2 * bytes) != cudaSuccess) {
+                mm_plan_destroy(p);
+                return fail(MM_ERR_OOM, "HKMP exponential");
+            }
+            mm::tc_matrix_full_bands(p->Etc[v]);
+            p->full_bands[v] = true;
+            p->Etc[v].row_norm = std::sqrt(double(m));  // bound for a unitary matrix: sum_j |E_ij| <= sqrt(m)
+        } else {
+            p->Edyn[v] = static_cast<double2 *>(p->Edev[v]);
+        }
+        nmax = std::max(nmax, m);
+    }
+    cudaError_t e = cudaMalloc(&p->coef, size_t(p->count) * elem_bytes(dtype));
+    if (e == cudaSuccess && nmax > 0) e = mm::expm_workspace_init(&p->expm, nmax);
+    if (e != cudaSuccess) {
+        mm_plan_destroy(p);
+        return fail(MM_ERR_OOM, "HKMP workspace");
+    }
+    *out = p;
+    return MM_OK;
+}
+
+extern "C" mm_status hkmp_evolve(mm_plan *p, void *psi, int64_t nsteps, const double *f_mid, void *stream)
+{
+    if (!p || !p->hkmp) return fail(MM_ERR_INVALID_ARG, "not an HKMP plan");
+    mm_status st = check_ptr(psi, "psi_dev");
+    if (st) return st;
+    if (nsteps < 0) return fail(MM_ERR_INVALID_ARG, "nsteps < 0");
+    if (nsteps > 0 && !f_mid) return fail(MM_ERR_INVALID_ARG, "f_mid is NULL");
+    for (int64_t k = 0; k < nsteps; ++k)
+        if (!std::isfinite(f_mid[k])) return fail(MM_ERR_INVALID_ARG, "f_mid[%lld] is not finite", (long long)k);
+    if (nsteps == 0) return MM_OK;
+    cudaStream_t s = (cudaStream_t)stream;
+    // the step's exponentials exp(-i tau (H0 + f G)) of the time-dependent directions
+    auto exps = [&](double f) -> mm_status {
+        for (int v = 0; v < p->d; ++v) {
+            if (!p->H0dev[v]) continue;
+            const int m = int(p->n[v]);
+            const double bound = p->h0norm[v] + std::fabs(f) * p->gnorm[v];
+            cudaError_t e = mm::expm_device(&p->expm, m, p->H0dev[v], p->Gdev[v], f, 0.0, -p->tau, bound, p->Edyn[v], s);
+            if (e != cudaSuccess) return cuda_fail(e, "device expm");
+            if (p->tc && (e = mm::tc_matrix_update(p->Etc[v], p->Edyn[v], s)) != cudaSuccess)
+                return cuda_fail(e, "matrix update");
+        }
+        return MM_OK;
+    };
+    if ((st = hermite_apply(p, true, psi, p->coef, stream))) return st;
+    if (p->tc) {
+        int cur = 0;
+        mm::TcMatrix *M[mm::kMaxDims];
+        for (int v = 0; v < p->d; ++v) M[v] = &p->Etc[v];
+        if ((st = exps(f_mid[0]))) return st;
+        if ((st = tc_begin(p, M, p->coef, s))) return st;
+        for (int64_t k = 0; k < nsteps; ++k) {
+            if (k > 0 && (st = exps(f_mid[k]))) return st;
+            if ((st = tc_sweep(p, M, cur, mm::TcEpilogue{}, s))) return st;
+        }
+        if ((st = tc_end(p, cur, p->coef, s))) return st;
+    } else {
+        for (int64_t k = 0; k < nsteps; ++k)
+            if ((st = exps(f_mid[k])) || (st = simt_sweep(p, p->Edev, p->coef, s))) return st;
+    }
+    return hermite_apply(p, false, p->coef, psi, stream);
 }

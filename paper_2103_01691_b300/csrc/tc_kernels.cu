@@ -88,41 +88,78 @@ constexpr int kBlocks = 2;
 
 // ---- host: BF16 pieces of the matrix ----------------------------------------------
 
+// Piece arithmetic shared by the host set-up and the device update kernel
+// (tc_matrix_update), so that both produce the same bits.  rint rounds to
+// nearest with ties to even (the default rounding mode on the host).
+
 // Round a double to the nearest BF16 value (ties to even), returned as a double.
-static double bf16_round(double v)
+__host__ __device__ static double bf16_round(double v)
 {
-    if (v == 0.0 || !std::isfinite(v)) return 0.0;
-    int e = std::ilogb(v);
+    if (v == 0.0 || !isfinite(v)) return 0.0;
+    int e = ilogb(v);
     if (e < -126) return 0.0;  // below the BF16 normal range: flush
-    double scaled = std::ldexp(v, 7 - e);  // |scaled| in [128, 256)
-    double r = std::nearbyint(scaled);     // default rounding mode: nearest, ties to even
-    return std::ldexp(r, e - 7);
+    double scaled = ldexp(v, 7 - e);  // |scaled| in [128, 256)
+    double r = rint(scaled);
+    return ldexp(r, e - 7);
 }
-static uint16_t bf16_bits(double exact_bf16_value)
+__host__ __device__ static uint16_t bf16_bits(double exact_bf16_value)
 {
     float f = float(exact_bf16_value);
+#ifdef __CUDA_ARCH__
+    uint32_t u = __float_as_uint(f);
+#else
     uint32_t u;
     std::memcpy(&u, &f, 4);
+#endif
     return uint16_t(u >> 16);
 }
 
 // Round a double to the nearest FP16 value (ties to even, subnormals kept).
-static double f16_round(double v)
+__host__ __device__ static double f16_round(double v)
 {
-    if (v == 0.0 || !std::isfinite(v)) return 0.0;
-    const int e = std::ilogb(v);
-    if (e < -14) return std::nearbyint(std::ldexp(v, 24)) * std::ldexp(1.0, -24);  // subnormal grid 2^-24
-    return std::ldexp(std::nearbyint(std::ldexp(v, 10 - e)), e - 10);
+    if (v == 0.0 || !isfinite(v)) return 0.0;
+    const int e = ilogb(v);
+    if (e < -14) return rint(ldexp(v, 24)) * ldexp(1.0, -24);  // subnormal grid 2^-24
+    return ldexp(rint(ldexp(v, 10 - e)), e - 10);
 }
-static uint16_t f16_bits(double exact)
+__host__ __device__ static uint16_t f16_bits(double exact)
 {
     if (exact == 0.0) return 0;
     const uint16_t sign = exact < 0 ? 0x8000u : 0u;
-    const double a = std::fabs(exact);
-    if (a < std::ldexp(1.0, -14)) return uint16_t(sign | uint16_t(std::ldexp(a, 24)));
-    const int e = std::ilogb(a);
-    const uint16_t mant = uint16_t(std::ldexp(a, -e) * 1024.0 - 1024.0);
+    const double a = fabs(exact);
+    if (a < ldexp(1.0, -14)) return uint16_t(sign | uint16_t(ldexp(a, 24)));
+    const int e = ilogb(a);
+    const uint16_t mant = uint16_t(ldexp(a, -e) * 1024.0 - 1024.0);
     return uint16_t(sign | uint16_t((e + 15) << 10) | mant);
+}
+
+// Fixed-point row scale: the power of two 2^ceil(log2(sum_abs / 4096)) (1 for
+// an empty row), by frexp so that host and device agree exactly.
+__host__ __device__ static double row_scale(double sum_abs)
+{
+    if (!(sum_abs > 0.0)) return 1.0;
+    int e = 0;
+    const double mant = frexp(sum_abs / 4096.0, &e);  // sum / 4096 = mant 2^e, mant in [1/2, 1)
+    return ldexp(1.0, mant == 0.5 ? e - 1 : e);
+}
+
+// The pieces of one complex entry (C, S) / r: bits[p][0] (C), bits[p][1] (S).
+__host__ __device__ static void entry_pieces(double c, double s, double r, int npieces, bool fixed, uint16_t bits[3][2])
+{
+    double rest[2] = {c, s};
+    if (fixed) {
+        rest[0] /= r;
+        rest[1] /= r;
+    }
+    for (int p = 0; p < npieces; ++p)
+        for (int q = 0; q < 2; ++q) {
+            double piece;
+            if (!fixed) piece = bf16_round(rest[q]);
+            else if (p == 0) piece = f16_round(rint(rest[q]));  // integer, exact below 2048
+            else piece = f16_round(rest[q]);
+            rest[q] -= piece;
+            bits[p][q] = fixed ? f16_bits(piece) : bf16_bits(piece);
+        }
 }
 
 mm_status tc_matrix_host(const double *E, int64_t m, int64_t n, int npieces, bool fixed, TcMatrix *geom,
@@ -148,32 +185,19 @@ mm_status tc_matrix_host(const double *E, int64_t m, int64_t n, int npieces, boo
             sum_mod += std::hypot(c, sv);
         }
         M.row_norm = std::max(M.row_norm, sum_mod);
-        double r = 1.0;
-        if (fixed && sum_abs > 0.0) r = std::ldexp(1.0, int(std::ceil(std::log2(sum_abs / 4096.0))));
+        const double r = fixed ? row_scale(sum_abs) : 1.0;
         rho[size_t(i)] = float(r);
         const int64_t tile = i / M.it, il = i % M.it;
         for (int64_t j = 0; j < n; ++j) {
-            double rest[2] = {E[2 * (i * n + j)], E[2 * (i * n + j) + 1]};  // C, S
-            if (fixed) {
-                rest[0] /= r;
-                rest[1] /= r;
-            }
-            for (int p = 0; p < npieces; ++p) {
-                double piece[2];
-                for (int q = 0; q < 2; ++q) {
-                    if (!fixed) piece[q] = bf16_round(rest[q]);
-                    else if (p == 0) piece[q] = f16_round(std::nearbyint(rest[q]));  // integer, exact below 2048
-                    else piece[q] = f16_round(rest[q]);
-                    rest[q] -= piece[q];
-                }
-                // blocks: 0 = C, 1 = S; stored tile by tile (see TcMatrix)
-                const double vals[kBlocks] = {piece[0], piece[1]};
-                const int64_t kb = j / 16, jj = j % 16, kbs = M.k_pad / 16;
+            uint16_t bits[3][2];
+            entry_pieces(E[2 * (i * n + j)], E[2 * (i * n + j) + 1], r, npieces, fixed, bits);
+            // blocks: 0 = C, 1 = S; stored tile by tile (see TcMatrix)
+            const int64_t kb = j / 16, jj = j % 16, kbs = M.k_pad / 16;
+            for (int p = 0; p < npieces; ++p)
                 for (int w = 0; w < kBlocks; ++w) {
                     const int64_t row = (((int64_t(p) * M.ni + tile) * kbs + kb) * kBlocks + w) * M.it + il;
-                    h[size_t(row * 16 + jj)] = fixed ? f16_bits(vals[w]) : bf16_bits(vals[w]);
+                    h[size_t(row * 16 + jj)] = bits[p][w];
                 }
-            }
         }
     }
     // k-block band of each row tile: blocks outside it are exactly zero in
@@ -308,6 +332,84 @@ void tc_matrix_destroy(TcMatrix *M)
     M->pieces = nullptr;
     for (auto &P : M->pair) P.pieces = nullptr;
     M->rho = nullptr;
+}
+
+// ---- device: matrix pieces from a device matrix ----------------------------------
+
+// One block per matrix row i < m: the row scale (one thread sums the row in
+// the host's order, so the scale is the one tc_matrix_host picks), then the
+// pieces of every entry into the one-SM layout and both pair layouts, at the
+// positions tc_matrix_host and tc_pair_layout give them.  Entries of the
+// padding are never written and keep the zeros of the matrix's creation.
+__global__ void matrix_update_kernel(const double2 *__restrict__ E, int64_t m, int64_t n, int npieces, bool fixed,
+                                     int ni, int it, int64_t kbs, uint16_t *pieces, float *rho, uint16_t *pp0,
+                                     int it0, uint16_t *pp1, int it1)
+{
+    const int64_t i = blockIdx.x;
+    if (i >= m) return;
+    __shared__ double r_sh;
+    if (threadIdx.x == 0) {
+        double sum_abs = 0.0;
+        for (int64_t j = 0; j < n; ++j) sum_abs += fabs(E[i * n + j].x) + fabs(E[i * n + j].y);
+        const double r = fixed ? row_scale(sum_abs) : 1.0;
+        r_sh = r;
+        if (rho) rho[i] = float(r);
+    }
+    __syncthreads();
+    const double r = r_sh;
+    const int64_t tile = i / it, il = i % it;
+    for (int64_t j = threadIdx.x; j < n; j += blockDim.x) {
+        uint16_t bits[3][2];
+        const double2 e = E[i * n + j];
+        entry_pieces(e.x, e.y, r, npieces, fixed, bits);
+        const int64_t kb = j / 16, jj = j % 16;
+        for (int p = 0; p < npieces; ++p)
+            for (int w = 0; w < kBlocks; ++w) {
+                const int64_t row = (((int64_t(p) * ni + tile) * kbs + kb) * kBlocks + w) * it + il;
+                pieces[row * 16 + jj] = bits[p][w];
+            }
+        for (int k = 0; k < 2; ++k) {
+            uint16_t *pp = k == 0 ? pp0 : pp1;
+            const int itk = k == 0 ? it0 : it1;
+            if (!pp) continue;
+            const int64_t half = itk / 2, tile2 = i / itk, i2 = i % itk, rr = i2 / half, jrow = i2 % half;
+            for (int p = 0; p < npieces; ++p) {
+                const int64_t blk = (((tile2 * kbs + kb) * 2 + rr) * npieces + p) * 3 * half;
+                for (int b = 0; b < 3; ++b) {
+                    uint16_t v = b == 1 ? bits[p][0] : bits[p][1];
+                    if (b == 0 && (v & 0x7fffu)) v ^= 0x8000u;  // -S
+                    const int64_t row = b * half + jrow;
+                    const int64_t chunk = (jj / 8) ^ ((row >> 2) & 1);
+                    pp[(blk + row) * 16 + chunk * 8 + jj % 8] = v;
+                }
+            }
+        }
+    }
+}
+
+cudaError_t tc_matrix_update(TcMatrix &M, const double2 *E, cudaStream_t s)
+{
+    if (!M.pieces || !E || (M.fixed && !M.rho)) return cudaErrorInvalidValue;
+    matrix_update_kernel<<<unsigned(M.n_out), 128, 0, s>>>(
+        E, M.n_out, M.n_in, M.npieces, M.fixed, M.ni, M.it, M.k_pad / 16, static_cast<uint16_t *>(M.pieces), M.rho,
+        static_cast<uint16_t *>(M.pair[0].pieces), M.pair[0].it, static_cast<uint16_t *>(M.pair[1].pieces),
+        M.pair[1].it);
+    count_launch();
+    return cudaGetLastError();
+}
+
+void tc_matrix_full_bands(TcMatrix &M)
+{
+    const int kbs = int(M.k_pad / 16);
+    for (int t = 0; t < M.ni; ++t) {
+        M.kb_lo[t] = 0;
+        M.kb_hi[t] = kbs;
+    }
+    for (auto &P : M.pair)
+        for (int t = 0; t < P.ni; ++t) {
+            P.kb_lo[t] = 0;
+            P.kb_hi[t] = kbs;
+        }
 }
 
 // ---- device: splitting, merging -----------------------------------------------------

@@ -58,6 +58,12 @@ SIGNATURES = {
     "mm_plan_set_config": (_i, [_vp, _i, ctypes.POINTER(_i)]),
     "hermite_plan_create": (_i, [_vp, _i, _i64p, _i, _i, ctypes.POINTER(_vp)]),
     "mm_hermite_hamiltonian": (_i, [_i, _dp, _dp]),
+    "mm_expm_device": (_i, [_vp, _i, _vp, _vp, ctypes.c_double, ctypes.c_double, ctypes.c_double, ctypes.c_double,
+                            _vp, _vp]),
+    "mm_plan_set_matrix_device": (_i, [_vp, _i, _vp, ctypes.c_double, _vp]),
+    "hkmp_plan_create": (_i, [_vp, _i, _i64p, ctypes.POINTER(_dp), ctypes.POINTER(_dp), ctypes.c_double, _i, _i,
+                              ctypes.POINTER(_vp)]),
+    "hkmp_evolve": (_i, [_vp, _vp, _i64, _dp, _vp]),
     "hkp_plan_create": (_i, [_vp, _i, _i64p, ctypes.POINTER(_dp), ctypes.c_double, _i, _i, ctypes.POINTER(_i),
                              ctypes.POINTER(_vp)]),
     "hermite_nodes": (_i, [_vp, _i, _dp, _dp]),
@@ -213,6 +219,29 @@ def hermite_hamiltonian(m: int, V=None):
     return H
 
 
+def expm_device(ctx: Context, A, B=None, f: float = 0.0, z: complex = 1.0, norm_bound: float = 0.0, out=None,
+                stream=None):
+    """mm_expm_device: exp(z (A + f B)) in FP64 on the GPU for real CUDA
+    float64 matrices A, B (n x n); returns (or fills) a complex128 CUDA tensor."""
+    import torch
+
+    _need_cuda(A)
+    n = A.shape[0]
+    if A.dtype != torch.float64 or A.shape != (n, n) or not A.is_contiguous():
+        raise ValueError("A must be a contiguous square float64 tensor")
+    if B is not None:
+        _need_cuda(B)
+        if B.dtype != torch.float64 or B.shape != (n, n) or not B.is_contiguous():
+            raise ValueError("B must match A")
+    if out is None:
+        out = torch.empty((n, n), dtype=torch.complex128, device=A.device)
+    z = complex(z)
+    _check(lib().mm_expm_device(ctx.handle, n, ctypes.c_void_p(A.data_ptr()),
+                                ctypes.c_void_p(B.data_ptr()) if B is not None else None, float(f), z.real, z.imag,
+                                float(norm_bound), ctypes.c_void_p(out.data_ptr()), _stream(stream)))
+    return out
+
+
 # ------------------------------------------------------------- mu-mode product
 
 def mumode_product(ctx: Context, u, mu: int, L, prec: str = "f16x6", out=None, stream=None):
@@ -303,6 +332,13 @@ class TuckerPlan(_Tunable):
         _check(lib().mumode_plan_create(ctx.handle, d, self.dims.ctypes.data_as(_i64p), ptrs, int(cplx), code,
                                         PREC[prec], optr, ctypes.byref(h)))
         self.handle = h
+
+    def set_matrix_device(self, mu: int, E, row_norm_bound: float = 0.0, stream=None):
+        """mm_plan_set_matrix_device: direction mu's matrix from a CUDA
+        complex128 tensor (n_mu x n_mu), used by the following steps."""
+        _need_cuda(E)
+        _check(lib().mm_plan_set_matrix_device(self.handle, int(mu), ctypes.c_void_p(E.data_ptr()),
+                                               float(row_norm_bound), _stream(stream)))
 
     def issued_flops(self) -> float:
         """Tensor-core flops issued per step (see mm_plan_issued_flops)."""
@@ -421,6 +457,50 @@ class HKPPlan(TuckerPlan):
         _check(lib().hkp_plan_create(ctx.handle, d, self.dims.ctypes.data_as(_i64p), ptrs, float(tau), code,
                                      PREC[prec], optr, ctypes.byref(h)))
         self.handle = h
+
+
+class HKMPPlan:
+    """hkmp_plan_create / hkmp_evolve (section 4.4): Magnus steps for the
+    potential V_mu(x_mu) + f(t) U_mu(x_mu).  Vs, Us: values at the
+    Gauss-Hermite nodes per direction (None: harmonic / no time dependence)."""
+
+    def __init__(self, ctx: Context, dims, Vs, Us, tau: float, prec: str = "f16x6", dtype=None):
+        import torch
+
+        self.ctx = ctx
+        self.dims = np.array(dims, dtype=np.int64)
+        d = len(self.dims)
+        self._v = [None if V is None else np.ascontiguousarray(V, dtype=np.float64) for V in Vs]
+        self._u = [None if U is None else np.ascontiguousarray(U, dtype=np.float64) for U in Us]
+        vp = (_dp * d)(*[_dptr(V) if V is not None else None for V in self._v])
+        up = (_dp * d)(*[_dptr(U) if U is not None else None for U in self._u])
+        if dtype is None:
+            dtype = torch.complex128 if prec in ("fp64", "fp64dmma") else torch.complex64
+        self.dtype = dtype
+        code = {torch.complex64: MM_C64, torch.complex128: MM_C128}[dtype]
+        h = ctypes.c_void_p()
+        _check(lib().hkmp_plan_create(ctx.handle, d, self.dims.ctypes.data_as(_i64p), vp, up, float(tau), code,
+                                      PREC[prec], ctypes.byref(h)))
+        self.handle = h
+
+    def evolve(self, psi, f_mid, stream=None):
+        """len(f_mid) Magnus steps on the values psi (in place); f_mid[k] = f(t_k + tau/2)."""
+        _need_cuda(psi)
+        f = np.ascontiguousarray(f_mid, dtype=np.float64)
+        _check(lib().hkmp_evolve(self.handle, ctypes.c_void_p(psi.data_ptr()), int(f.size), _dptr(f),
+                                 _stream(stream)))
+        return psi
+
+    def close(self):
+        if self.handle:
+            lib().mm_plan_destroy(self.handle)
+            self.handle = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
 
 
 class HermitePlan(_Tunable):

@@ -26,7 +26,7 @@ def mm():
 def header_functions():
     text = open(os.path.join(ROOT, "include", "mumode.h")).read()
     text = re.sub(r"/\*.*?\*/", "", text, flags=re.S)
-    return sorted(set(re.findall(r"\b(mm_\w+|mumode_\w+|hermite_\w+|hkp_\w+|split_step_\w+)\s*\(", text)))
+    return sorted(set(re.findall(r"\b(mm_\w+|mumode_\w+|hermite_\w+|hkp_\w+|hkmp_\w+|split_step_\w+)\s*\(", text)))
 
 
 def test_every_declared_symbol_is_exported(mm):

@@ -405,6 +405,104 @@ def test_hkp_full_size_sampled(env, orc):
     assert drift <= 1e-6
 
 
+# ------------------------------------------- device exponentials, HKMP (section 4.4)
+
+@pytest.mark.parametrize("n", [1, 40, 97, 200])
+def test_expm_device(env, orc, n):
+    """mm_expm_device, exp(z (A + f B)) in FP64 on the GPU, against the
+    oracle's Taylor exponential, for an imaginary and a real z, with the
+    norm bound given and computed by the call."""
+    mm, ctx, torch = env
+    rng = np.random.default_rng(n)
+    A = rng.standard_normal((n, n)) * 3.0
+    A = A + A.T  # symmetric: exp(-i s A) is unitary, as in the Magnus steps
+    B = rng.standard_normal((n, n))
+    B = B + B.T
+    f = 0.3
+    Ad = torch.from_numpy(A).cuda()
+    Bd = torch.from_numpy(B).cuda()
+    for z in (-0.05j, 0.01):
+        ref = orc.expm_taylor(A + f * B, z)
+        bound = np.abs(A + f * B).sum(axis=0).max()
+        for nb in (bound, 0.0):
+            E = mm.expm_device(ctx, Ad, Bd, f, z, norm_bound=nb).cpu().numpy()
+            err = np.linalg.norm(E - ref) / np.linalg.norm(ref)
+            print(f"expm_device n={n} z={z} bound={nb:.1f} rel_err={err:.2e}")
+            assert err <= 1e-11, (z, nb)
+    E0 = mm.expm_device(ctx, Ad, None, 0.0, 0.01).cpu().numpy()
+    ref0 = orc.expm_taylor(A, 0.01)
+    assert np.linalg.norm(E0 - ref0) <= 1e-11 * np.linalg.norm(ref0)
+
+
+@pytest.mark.parametrize("prec,variant", [("f16x6", "pair64"), ("f16x6", "pair128"), ("f16x6", "one_sm"),
+                                          ("bf16x3", "pair64"), ("fp64", None)])
+def test_set_matrix_device_matches_host_matrix(env, prec, variant):
+    """A matrix split on the device (mm_plan_set_matrix_device) gives the same
+    bits as the host-built one: a plan created with other matrices and then
+    given E on the device steps exactly like a plan created with E."""
+    mm, ctx, torch = env
+    dims, tau = (72, 40, 33), 1e-4
+    Es = [fd_schrodinger_E(mm, n, tau) for n in dims]
+    other = [fd_schrodinger_E(mm, n, 3 * tau) for n in dims]
+    f64 = prec == "fp64"
+    u0 = inputs.complex_normal(dims[::-1], seed=4)
+    if not f64:
+        u0 = u0.astype(np.complex64)
+    a = mm.TuckerPlan(ctx, dims, Es, prec=prec)
+    b = mm.TuckerPlan(ctx, dims, other, prec=prec)
+    if variant:
+        a.set_config(variant, (1, 2, 3))
+        b.set_config(variant, (1, 2, 3))
+    for mu, E in enumerate(Es, start=1):
+        b.set_matrix_device(mu, torch.from_numpy(np.ascontiguousarray(E)).cuda(), row_norm_bound=0.0)
+    dt = torch.complex128 if f64 else torch.complex64
+    ua, ub = to_gpu(torch, u0, dt), to_gpu(torch, u0, dt)
+    a.step(ua, 3)
+    b.step(ub, 3)
+    torch.cuda.synchronize()
+    assert torch.equal(ua, ub)
+
+
+def _hkmp_case(orc, n):
+    xs, Ws = [], []
+    for v in n:
+        x, _, W = orc.gauss_hermite(v)
+        xs.append(x)
+        Ws.append(W)
+    return xs, Ws
+
+
+@pytest.mark.parametrize("prec,tdir", [("f16x6", 3), ("f16x6", 1), ("fp64", 3), ("fp64dmma", 1)])
+def test_hkmp_vs_oracle(env, orc, prec, tdir):
+    """HKMP (the section 4.4 potential |x|^2/2 + x_3 sin^2 t, or with the
+    time dependence moved to direction 1) against the oracle's literal
+    Magnus steps: 12 steps of 0.05 on ragged sizes."""
+    mm, ctx, torch = env
+    n = (72, 40, 48)
+    xs, Ws = _hkmp_case(orc, n)
+    Vs, Us = inputs.hkmp_potentials(*xs)
+    if tdir == 1:
+        Us = (np.array(xs[0]), None, None)
+    tau, steps = 0.05, 12
+    f_mid = inputs.hkmp_f_mid(tau, steps)
+    f64 = prec in ("fp64", "fp64dmma")
+    psi0 = inputs.hkp_psi0(*xs)
+    pin = psi0 if f64 else psi0.astype(np.complex64)
+    ref = orc.hkmp_steps(pin.astype(complex), xs, Ws, Vs, Us, tau, f_mid)
+    xl = [mm.gauss_hermite(v)[0] for v in n]
+    Vl, Ul = inputs.hkmp_potentials(*xl)
+    if tdir == 1:
+        Ul = (np.array(xl[0]), None, None)
+    plan = mm.HKMPPlan(ctx, n, [None, Vl[1], Vl[2]], list(Ul), tau, prec=prec)
+    psi = to_gpu(torch, pin, torch.complex128 if f64 else torch.complex64)
+    plan.evolve(psi, f_mid)
+    w3 = Ws[2][:, None, None] * Ws[1][None, :, None] * Ws[0][None, None, :]
+    err = orc.rel_l2(psi.cpu().numpy(), ref, w3)
+    print(f"HKMP {prec} dir {tdir} n={n} steps={steps} rel_err={err:.3e}")
+    assert err <= (1e-12 if f64 else 5e-6)
+    ctx.status()
+
+
 def test_fixed_point_wide_dynamic_range(env, orc):
     """F16x6 keeps a relative L2 accuracy when magnitudes span 1e-6 .. 1:
     the fixed-point leading piece is relative to the maximum, the FP16
