@@ -203,7 +203,7 @@ def main():
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-fp64", action="store_true")
     ap.add_argument("--workload", default="free256",
-                    choices=["free256", "heat32", "ho128", "batched64", "gpe192", "hkp"],
+                    choices=["free256", "heat32", "ho128", "batched64", "gpe192", "hkp", "hkmp"],
                     help="free256 (default) is the headline line; the others time the remaining workloads")
     args = ap.parse_args()
     rank, world, local = dist_env()
@@ -463,6 +463,43 @@ def other_workload(args):
                                            "n255": {"single": 8.11, "double": 16.02}},
                     config="HKP, V = cos(2 pi x1) + x2^2/2 + x3^2/2, Hermite n^3 complex, one step to T = 1; "
                            "value = steps/s at n = 255 (setup_ms: host FP64 Hamiltonian, expm and folding)")
+    elif args.workload == "hkmp":
+        # section 4.4: |x|^2/2 + x_3 sin^2 t, tau = 0.02, 50 Magnus steps to T = 1
+        tau, K = 0.02, 50
+        f_mid = inputs.hkmp_f_mid(tau, K)
+        for n in (127, 255):
+            x, _ = mm.gauss_hermite(n)
+            Vs, Us = inputs.hkmp_potentials(x, x, x)
+            psi0 = inputs.hkp_psi0(x, x, x)
+            res = {}
+            for prec in ("f16x6", "fp64dmma"):
+                f64 = prec.startswith("fp64")
+                t0 = time.perf_counter()
+                plan = mm.HKMPPlan(ctx, [n] * 3, [None, None, None], list(Us), tau, prec=prec)
+                setup_ms = (time.perf_counter() - t0) * 1e3
+                psi = torch.from_numpy(psi0).to(torch.complex128 if f64 else torch.complex64).cuda()
+                k = 4 if f64 else K
+                plan.evolve(psi, f_mid[:k])
+                ms = _time(lambda: plan.evolve(psi, f_mid[:k]), stream)
+                res[prec] = {"ms_per_step": ms / k, "steps": k, "setup_ms": setup_ms}
+                del plan, psi
+            # the per-step exponential alone (the paper's "exp (int)" column)
+            H0 = torch.from_numpy(mm.hermite_hamiltonian(n, None)).cuda()
+            G = torch.diag(torch.from_numpy(np.sqrt(np.arange(1, n) / 2.0)), 1).cuda()
+            G = (G + G.T).contiguous()
+            bound = float(n - 0.5 + 2 * np.sqrt(n / 2.0))
+            E = mm.expm_device(ctx, H0, G, 0.5, -1j * tau, norm_bound=bound)
+            ms_e = _time(lambda: mm.expm_device(ctx, H0, G, 0.5, -1j * tau, norm_bound=bound, out=E), stream)
+            res["exp_int_ms"] = ms_e
+            line[f"n{n}"] = res
+        line.update(value=1e3 / line["n255"]["f16x6"]["ms_per_step"], precision="f16x6",
+                    paper_gpu_ms_per_step={"n127": {"double": {"exp_int": 0.37, "mu_mode": 1.05},
+                                                    "single": {"exp_int": 0.25, "mu_mode": 0.54}},
+                                           "n255": {"double": {"exp_int": 0.66, "mu_mode": 13.79},
+                                                    "single": {"exp_int": 0.34, "mu_mode": 7.01}}},
+                    config="HKMP, V = |x|^2/2 + x3 sin^2 t, Hermite n^3 complex, tau = 0.02, 50 steps to T = 1; "
+                           "value = steps/s at n = 255 (each step: FP64 device exp of direction 3, its split, "
+                           "three mode products; transforms once per call)")
     elif args.workload == "gpe192":
         n, beta, tau, K = 192, 100.0, 1e-3, 500
         plan = mm.HermitePlan(ctx, [n] * 3, prec="f16x6")

@@ -233,7 +233,11 @@ mm_status mumode_product_noalloc(int d, const int64_t *n, int mu, const double *
  * row-major, device (B_dev may be NULL); E_dev: n x n complex interleaved
  * (2 n^2 doubles), device, overlapping neither.  Scaling and squaring of
  * the degree-18 Taylor polynomial (Paterson-Stockmeyer evaluation; the
- * products are cuBLAS ZGEMMs).  norm_bound >= ||A + f B||_1 picks the
+ * products are cuBLAS ZGEMMs).  For a purely imaginary z = i w the call
+ * computes cos(w M) + i sin(w M), M = A + f B, instead: degree-9
+ * polynomials in (w M / 2^s)^2 and s angle doublings, all in real
+ * arithmetic (cuBLAS DGEMMs), about a third of the flops.
+ * norm_bound >= ||A + f B||_1 picks the
  * scaling; norm_bound <= 0 has the call compute the norm on the device and
  * synchronise the stream.  Otherwise stream-ordered.  Calls on one context
  * share its workspace (allocated on first use): serialise them.
@@ -417,7 +421,11 @@ mm_status hkp_plan_create(mm_ctx *ctx, int d, const int64_t *n, const double *co
  * call transforms them forward, takes nsteps Magnus steps of the plan's
  * tau in coefficient space with f_mid[k] = f(t_k + tau/2) (host array of
  * nsteps doubles), and transforms back, in place.  The fixed-point state
- * and the coefficients stay on the device between steps. */
+ * and the coefficients stay on the device between steps.  Since every
+ * f_mid is known at the call, the exponentials of up to 64 steps are
+ * computed together (batched real products, see mm_expm_device).  The
+ * call synchronises the stream before returning (f_mid is then no longer
+ * read). */
 mm_status hkmp_plan_create(mm_ctx *ctx, int d, const int64_t *n, const double *const *V_nodes,
                            const double *const *U_nodes, double tau, mm_dtype dtype, mm_prec prec, mm_plan **out);
 mm_status hkmp_evolve(mm_plan *plan, void *psi_dev, int64_t nsteps, const double *f_mid, void *stream);

@@ -188,4 +188,191 @@ cudaError_t expm_device(ExpmWorkspace *w, int n, const double *A, const double *
     return cudaGetLastError();
 }
 
+// ---- imaginary z: cos / sin in real arithmetic, batched over several f ----------
+//
+// For real M and z = i w, exp(z M) = cos(w M) + i sin(w M).  With
+// X = w M / 2^s (||X||_1 <= 1) and Y = X^2:
+//   cos X = sum_{j<=9} (-1)^j Y^j / (2j)!,   sin X = X sum_{j<=9} (-1)^j Y^j / (2j+1)!,
+// whose truncation errors are below 1/20! and 1/21!.  Each degree-9
+// polynomial in Y is evaluated by Paterson-Stockmeyer with Y^3 as the
+// Horner variable (2 products each, given Y, Y^2, Y^3), and the angle is
+// doubled s times by cos 2a = 2 cos^2 a - 1, sin 2a = 2 sin a cos a (2
+// products each).  All products are real (cuBLAS DGEMM, strided-batched
+// over the batch of f values): 8 + 2 s real products, against 10 + s
+// complex ones (40 + 4 s real) for the general series.
+
+namespace {
+
+// f: count device values, or null for the single value f0
+__global__ void form_x_batch(int64_t nn, int count, const double *A, const double *B, const double *f, double f0,
+                             double w, double *X)
+{
+    const int64_t total = nn * count;
+    for (int64_t q = blockIdx.x * int64_t(blockDim.x) + threadIdx.x; q < total;
+         q += int64_t(gridDim.x) * blockDim.x) {
+        const int64_t k = q / nn, e = q % nn;
+        X[q] = w * (A[e] + (B ? (f ? f[k] : f0) * B[e] : 0.0));
+    }
+}
+
+// out = a0 I + a1 Y + a2 Y2 + a3 Y3 (batched; Y3 may be null when a3 = 0)
+__global__ void combo_batch(int n, int count, double a0, double a1, double a2, double a3, const double *Y,
+                            const double *Y2, const double *Y3, double *out)
+{
+    const int64_t nn = int64_t(n) * n, total = nn * count;
+    for (int64_t q = blockIdx.x * int64_t(blockDim.x) + threadIdx.x; q < total;
+         q += int64_t(gridDim.x) * blockDim.x) {
+        const int64_t e = q % nn;
+        double v = a1 * Y[q] + a2 * Y2[q];
+        if (Y3) v += a3 * Y3[q];
+        if (e / n == e % n) v += a0;
+        out[q] = v;
+    }
+}
+
+// C <- 2 C - I (after C = cos^2), S <- 2 S (after S = sin cos)
+__global__ void double_angle(int n, int count, double *C, double *S)
+{
+    const int64_t nn = int64_t(n) * n, total = nn * count;
+    for (int64_t q = blockIdx.x * int64_t(blockDim.x) + threadIdx.x; q < total;
+         q += int64_t(gridDim.x) * blockDim.x) {
+        const int64_t e = q % nn;
+        C[q] = 2.0 * C[q] - (e / n == e % n ? 1.0 : 0.0);
+        S[q] = 2.0 * S[q];
+    }
+}
+
+__global__ void interleave(int64_t total, const double *C, const double *S, double2 *E)
+{
+    for (int64_t q = blockIdx.x * int64_t(blockDim.x) + threadIdx.x; q < total;
+         q += int64_t(gridDim.x) * blockDim.x)
+        E[q] = make_double2(C[q], S[q]);
+}
+
+// C_k = P_k Q_k for row-major n x n matrices, k < count (column-major Q^T-view times P^T-view)
+cublasStatus_t gemm_batch(cublasHandle_t h, int n, int count, const double *P, const double *Q, double *C,
+                          bool accumulate)
+{
+    const double one = 1.0, beta = accumulate ? 1.0 : 0.0;
+    const long long stride = (long long)n * n;
+    return cublasDgemmStridedBatched(h, CUBLAS_OP_N, CUBLAS_OP_N, n, n, n, &one, Q, n, stride, P, n, stride, &beta, C,
+                                     n, stride, count);
+}
+
+}  // namespace
+
+void expm_batch_destroy(ExpmBatch *w)
+{
+    if (!w) return;
+    for (auto &b : w->buf)
+        if (b) {
+            cudaFree(b);
+            b = nullptr;
+        }
+    if (w->f) cudaFree(w->f);
+    w->f = nullptr;
+    if (w->blas) cublasDestroy(static_cast<cublasHandle_t>(w->blas));
+    w->blas = nullptr;
+    w->n = w->cap = 0;
+}
+
+cudaError_t expm_batch_init(ExpmBatch *w, int n, int cap)
+{
+    if (w->n >= n && w->cap >= cap && w->blas) return cudaSuccess;
+    expm_batch_destroy(w);
+    cublasHandle_t h = nullptr;
+    if (cublasCreate(&h) != CUBLAS_STATUS_SUCCESS) return cudaErrorUnknown;
+    w->blas = h;
+    const size_t bytes = sizeof(double) * size_t(n) * n * size_t(cap);
+    for (auto &b : w->buf) {
+        cudaError_t e = cudaMalloc(&b, bytes);
+        if (e != cudaSuccess) {
+            b = nullptr;
+            expm_batch_destroy(w);
+            return e;
+        }
+    }
+    cudaError_t e = cudaMalloc(&w->f, sizeof(double) * size_t(cap));
+    if (e != cudaSuccess) {
+        w->f = nullptr;
+        expm_batch_destroy(w);
+        return e;
+    }
+    w->n = n;
+    w->cap = cap;
+    return cudaSuccess;
+}
+
+int expm_batch_capacity(int n)
+{
+    const double per = 8.0 * 8.0 * double(n) * double(n);  // eight real n x n buffers per batch entry
+    return int(std::max(1.0, std::min(64.0, 1.0e9 / per)));
+}
+
+cudaError_t expm_imag_batched(ExpmBatch *w, int n, const double *A, const double *B, const double *f_host, int count,
+                              double wim, double norm_bound, double2 *E, cudaStream_t s)
+{
+    if (w->n < n || w->cap < count || count < 1 || !w->blas) return cudaErrorInvalidValue;
+    cublasHandle_t h = static_cast<cublasHandle_t>(w->blas);
+    if (cublasSetStream(h, s) != CUBLAS_STATUS_SUCCESS) return cudaErrorUnknown;
+    const double za = std::fabs(wim) * norm_bound;
+    int sq = 0;
+    if (za > 1.0) sq = int(std::ceil(std::log2(za)));
+    while (std::ldexp(za, -sq) > 1.0) ++sq;
+    cudaError_t e = cudaSuccess;
+    if (count > 1 && (e = cudaMemcpyAsync(w->f, f_host, sizeof(double) * size_t(count), cudaMemcpyHostToDevice, s)) !=
+                         cudaSuccess)
+        return e;
+    double *X = w->buf[0], *Y = w->buf[1], *Y2 = w->buf[2], *Y3 = w->buf[3], *T0 = w->buf[4], *T1 = w->buf[5],
+           *C = w->buf[6], *S = w->buf[7];
+    const int64_t nn = int64_t(n) * n, total = nn * count;
+    const int g = blocks_for(total);
+    form_x_batch<<<g, 256, 0, s>>>(nn, count, A, B, count > 1 ? w->f : nullptr, f_host[0], std::ldexp(wim, -sq), X);
+    count_launch();
+    if ((e = cudaGetLastError()) != cudaSuccess) return e;
+    if (gemm_batch(h, n, count, X, X, Y, false) != CUBLAS_STATUS_SUCCESS ||
+        gemm_batch(h, n, count, Y, Y, Y2, false) != CUBLAS_STATUS_SUCCESS ||
+        gemm_batch(h, n, count, Y2, Y, Y3, false) != CUBLAS_STATUS_SUCCESS)
+        return cudaErrorUnknown;
+    // a[j] = (-1)^j / (2j)! (cos) and (-1)^j / (2j+1)! (sin), j <= 9
+    double ac[10], as[10];
+    double fact = 1.0;  // k!
+    for (int k = 0; k <= 19; ++k) {
+        if (k > 0) fact *= double(k);
+        const double sgn = ((k / 2) % 2) ? -1.0 : 1.0;
+        if (k % 2 == 0) ac[k / 2] = sgn / fact;
+        else as[k / 2] = sgn / fact;
+    }
+    // p(Y) = Q0 + Y3 (Q1 + Y3 (Q2 + a9 Y3)), Q_i = a_{3i} I + a_{3i+1} Y + a_{3i+2} Y2
+    auto poly = [&](const double *a, double *out) -> cudaError_t {
+        combo_batch<<<g, 256, 0, s>>>(n, count, a[6], a[7], a[8], a[9], Y, Y2, Y3, T0);
+        count_launch();
+        combo_batch<<<g, 256, 0, s>>>(n, count, a[3], a[4], a[5], 0.0, Y, Y2, nullptr, T1);
+        count_launch();
+        if (gemm_batch(h, n, count, Y3, T0, T1, true) != CUBLAS_STATUS_SUCCESS) return cudaErrorUnknown;
+        combo_batch<<<g, 256, 0, s>>>(n, count, a[0], a[1], a[2], 0.0, Y, Y2, nullptr, out);
+        count_launch();
+        if (gemm_batch(h, n, count, Y3, T1, out, true) != CUBLAS_STATUS_SUCCESS) return cudaErrorUnknown;
+        return cudaGetLastError();
+    };
+    if ((e = poly(ac, C)) != cudaSuccess) return e;
+    // the sin polynomial goes into Y2: its last combination reads Y2 element by element in place,
+    // and Y2 is not needed after it
+    if ((e = poly(as, Y2)) != cudaSuccess) return e;
+    if (gemm_batch(h, n, count, X, Y2, S, false) != CUBLAS_STATUS_SUCCESS) return cudaErrorUnknown;
+    for (int k = 0; k < sq; ++k) {
+        // C' = 2 C C - I, S' = 2 S C
+        if (gemm_batch(h, n, count, C, C, T0, false) != CUBLAS_STATUS_SUCCESS ||
+            gemm_batch(h, n, count, S, C, T1, false) != CUBLAS_STATUS_SUCCESS)
+            return cudaErrorUnknown;
+        std::swap(C, T0);
+        std::swap(S, T1);
+        double_angle<<<g, 256, 0, s>>>(n, count, C, S);
+        count_launch();
+    }
+    interleave<<<g, 256, 0, s>>>(total, C, S, E);
+    count_launch();
+    return cudaGetLastError();
+}
+
 }  // namespace mm

@@ -120,6 +120,22 @@ cudaError_t expm_norm1_device(ExpmWorkspace *w, int n, const double *A, const do
 // norm_bound >= ||A + f B||_1; B may be null.  E (n x n complex) must not be a workspace buffer.
 cudaError_t expm_device(ExpmWorkspace *w, int n, const double *A, const double *B, double f, double zr, double zi,
                         double norm_bound, double2 *E, cudaStream_t s);
+// exp(i w (A + f_k B)) = cos + i sin for real A, B and count values f_k (host
+// array), in real arithmetic, batched: E holds count n x n complex matrices.
+// With count > 1 the f values are copied to the device in stream order (the
+// host array must stay valid until that copy has run); a single f is passed
+// by value.
+struct ExpmBatch {
+    int n = 0, cap = 0;
+    void *blas = nullptr;    // cublasHandle_t
+    double *buf[8] = {};     // cap real n x n matrices each
+    double *f = nullptr;     // cap doubles
+};
+cudaError_t expm_batch_init(ExpmBatch *w, int n, int cap);
+void expm_batch_destroy(ExpmBatch *w);
+int expm_batch_capacity(int n);  // batch entries that keep the workspace near 1 GB (1..64)
+cudaError_t expm_imag_batched(ExpmBatch *w, int n, const double *A, const double *B, const double *f_host, int count,
+                              double wim, double norm_bound, double2 *E, cudaStream_t s);
 // Host half of tc_matrix_create: geometry (pieces/rho left null) and the
 // host images of the pieces and row scales.
 mm_status tc_matrix_host(const double *E, int64_t m, int64_t n, int npieces, bool fixed, TcMatrix *geom,

@@ -26,7 +26,8 @@ struct mm_ctx {
     bool timing = false;
     std::vector<std::pair<cudaEvent_t, cudaEvent_t>> events;
     size_t events_used = 0;
-    mm::ExpmWorkspace expm;  // mm_expm_device
+    mm::ExpmWorkspace expm;  // mm_expm_device, complex z
+    mm::ExpmBatch expmb;     // mm_expm_device, imaginary z
 };
 
 struct mm_plan {
@@ -72,9 +73,9 @@ struct mm_plan {
     double tau = 0.0;
     double *H0dev[mm::kMaxDims] = {}, *Gdev[mm::kMaxDims] = {};
     double h0norm[mm::kMaxDims] = {}, gnorm[mm::kMaxDims] = {};
-    double2 *Edyn[mm::kMaxDims] = {};
+    double2 *Ebatch[mm::kMaxDims] = {};  // the exponentials of a chunk of steps (expmb.cap matrices)
     void *coef = nullptr;  // coefficient tensor of hkmp_evolve
-    mm::ExpmWorkspace expm;
+    mm::ExpmBatch expmb;
     bool full_bands[mm::kMaxDims] = {};  // a device update switched direction v's bands to full
     // CUDA graphs of whole step sequences, keyed by (call, tensor, nsteps, stream, tau, beta)
     bool use_graphs = true;
@@ -702,6 +703,7 @@ void mm_ctx_destroy(mm_ctx *ctx)
     cudaFree(ctx->d_err);
     cudaFree(ctx->d_scratch);
     mm::expm_workspace_destroy(&ctx->expm);
+    mm::expm_batch_destroy(&ctx->expmb);
     delete ctx;
 }
 
@@ -969,10 +971,10 @@ void mm_plan_destroy(mm_plan *p)
     for (int v = 0; v < mm::kMaxDims; ++v) {
         if (p->H0dev[v]) cudaFree(p->H0dev[v]);
         if (p->Gdev[v]) cudaFree(p->Gdev[v]);
-        if (p->Edyn[v] && p->tc) cudaFree(p->Edyn[v]);  // SIMT plans alias Edev
+        if (p->Ebatch[v]) cudaFree(p->Ebatch[v]);
     }
     if (p->coef) cudaFree(p->coef);
-    mm::expm_workspace_destroy(&p->expm);
+    mm::expm_batch_destroy(&p->expmb);
     delete p;
 }
 
@@ -1553,7 +1555,15 @@ extern "C" mm_status mm_expm_device(mm_ctx *ctx, int n, const double *A_dev, con
         e = mm::expm_norm1_device(&ctx->expm, n, A_dev, B_dev, f, &norm_bound, s);
         if (e != cudaSuccess) return cuda_fail(e, "expm norm");
     }
-    e = mm::expm_device(&ctx->expm, n, A_dev, B_dev, f, z_re, z_im, norm_bound, reinterpret_cast<double2 *>(E_dev), s);
+    if (z_re == 0.0) {  // cos + i sin in real arithmetic
+        if ((e = mm::expm_batch_init(&ctx->expmb, n, 1)) != cudaSuccess)
+            return fail(MM_ERR_OOM, "expm workspace (%s)", cudaGetErrorString(e));
+        e = mm::expm_imag_batched(&ctx->expmb, n, A_dev, B_dev, &f, 1, z_im, norm_bound,
+                                  reinterpret_cast<double2 *>(E_dev), s);
+    } else {
+        e = mm::expm_device(&ctx->expm, n, A_dev, B_dev, f, z_re, z_im, norm_bound, reinterpret_cast<double2 *>(E_dev),
+                            s);
+    }
     if (e != cudaSuccess) return cuda_fail(e, "device expm");
     return MM_OK;
 }
@@ -1654,20 +1664,20 @@ extern "C" mm_status hkmp_plan_create(mm_ctx *ctx, int d, const int64_t *n, cons
             return fail(MM_ERR_OOM, "HKMP matrices");
         }
         if (p->tc) {
-            if (cudaMalloc(&p->Edyn[v], 2 * bytes) != cudaSuccess) {
-                mm_plan_destroy(p);
-                return fail(MM_ERR_OOM, "HKMP exponential");
-            }
             mm::tc_matrix_full_bands(p->Etc[v]);
             p->full_bands[v] = true;
             p->Etc[v].row_norm = std::sqrt(double(m));  // bound for a unitary matrix: sum_j |E_ij| <= sqrt(m)
-        } else {
-            p->Edyn[v] = static_cast<double2 *>(p->Edev[v]);
         }
         nmax = std::max(nmax, m);
     }
     cudaError_t e = cudaMalloc(&p->coef, size_t(p->count) * elem_bytes(dtype));
-    if (e == cudaSuccess && nmax > 0) e = mm::expm_workspace_init(&p->expm, nmax);
+    if (e == cudaSuccess && nmax > 0) {
+        const int cap = mm::expm_batch_capacity(nmax);
+        e = mm::expm_batch_init(&p->expmb, nmax, cap);
+        for (int v = 0; v < d && e == cudaSuccess; ++v)
+            if (p->H0dev[v])
+                e = cudaMalloc(&p->Ebatch[v], sizeof(double2) * size_t(cap) * size_t(p->n[v] * p->n[v]));
+    }
     if (e != cudaSuccess) {
         mm_plan_destroy(p);
         return fail(MM_ERR_OOM, "HKMP workspace");
@@ -1687,34 +1697,58 @@ extern "C" mm_status hkmp_evolve(mm_plan *p, void *psi, int64_t nsteps, const do
         if (!std::isfinite(f_mid[k])) return fail(MM_ERR_INVALID_ARG, "f_mid[%lld] is not finite", (long long)k);
     if (nsteps == 0) return MM_OK;
     cudaStream_t s = (cudaStream_t)stream;
-    // the step's exponentials exp(-i tau (H0 + f G)) of the time-dependent directions
-    auto exps = [&](double f) -> mm_status {
+    // The exponentials exp(-i tau (H0 + f G)) of the time-dependent directions
+    // for a chunk of steps [k0, k0 + cnt), computed together (batched).
+    const int cap = p->expmb.cap;
+    auto chunk = [&](int64_t k0, int cnt) -> mm_status {
+        double fmax = 0.0;
+        for (int q = 0; q < cnt; ++q) fmax = std::max(fmax, std::fabs(f_mid[k0 + q]));
         for (int v = 0; v < p->d; ++v) {
             if (!p->H0dev[v]) continue;
-            const int m = int(p->n[v]);
-            const double bound = p->h0norm[v] + std::fabs(f) * p->gnorm[v];
-            cudaError_t e = mm::expm_device(&p->expm, m, p->H0dev[v], p->Gdev[v], f, 0.0, -p->tau, bound, p->Edyn[v], s);
+            const double bound = p->h0norm[v] + fmax * p->gnorm[v];
+            cudaError_t e = mm::expm_imag_batched(&p->expmb, int(p->n[v]), p->H0dev[v], p->Gdev[v], f_mid + k0, cnt,
+                                                  -p->tau, bound, p->Ebatch[v], s);
             if (e != cudaSuccess) return cuda_fail(e, "device expm");
-            if (p->tc && (e = mm::tc_matrix_update(p->Etc[v], p->Edyn[v], s)) != cudaSuccess)
-                return cuda_fail(e, "matrix update");
+        }
+        return MM_OK;
+    };
+    // step k's matrices: the batch slot of each time-dependent direction
+    void *Ed[mm::kMaxDims];
+    auto select = [&](int slot) -> mm_status {
+        for (int v = 0; v < p->d; ++v) {
+            Ed[v] = p->Edev[v];
+            if (!p->H0dev[v]) continue;
+            double2 *E = p->Ebatch[v] + size_t(slot) * size_t(p->n[v] * p->n[v]);
+            if (!p->tc) {
+                Ed[v] = E;
+                continue;
+            }
+            cudaError_t e = mm::tc_matrix_update(p->Etc[v], E, s);
+            if (e != cudaSuccess) return cuda_fail(e, "matrix update");
         }
         return MM_OK;
     };
     if ((st = hermite_apply(p, true, psi, p->coef, stream))) return st;
-    if (p->tc) {
-        int cur = 0;
-        mm::TcMatrix *M[mm::kMaxDims];
-        for (int v = 0; v < p->d; ++v) M[v] = &p->Etc[v];
-        if ((st = exps(f_mid[0]))) return st;
-        if ((st = tc_begin(p, M, p->coef, s))) return st;
-        for (int64_t k = 0; k < nsteps; ++k) {
-            if (k > 0 && (st = exps(f_mid[k]))) return st;
+    int cur = 0;
+    mm::TcMatrix *M[mm::kMaxDims];
+    for (int v = 0; v < p->d; ++v) M[v] = &p->Etc[v];
+    for (int64_t k0 = 0; k0 < nsteps; k0 += cap) {
+        const int cnt = int(std::min<int64_t>(cap, nsteps - k0));
+        if ((st = chunk(k0, cnt))) return st;
+        for (int q = 0; q < cnt; ++q) {
+            if ((st = select(q))) return st;
+            if (!p->tc) {
+                if ((st = simt_sweep(p, Ed, p->coef, s))) return st;
+                continue;
+            }
+            if (k0 == 0 && q == 0 && (st = tc_begin(p, M, p->coef, s))) return st;
             if ((st = tc_sweep(p, M, cur, mm::TcEpilogue{}, s))) return st;
         }
-        if ((st = tc_end(p, cur, p->coef, s))) return st;
-    } else {
-        for (int64_t k = 0; k < nsteps; ++k)
-            if ((st = exps(f_mid[k])) || (st = simt_sweep(p, p->Edev, p->coef, s))) return st;
     }
+    if (p->tc && (st = tc_end(p, cur, p->coef, s))) return st;
+    // f_mid is read by the batched exponentials' host-to-device copies, which
+    // may still be queued: finish them before the caller may free the array
+    cudaError_t e = cudaStreamSynchronize(s);
+    if (e != cudaSuccess) return cuda_fail(e, "HKMP steps");
     return hermite_apply(p, false, p->coef, psi, stream);
 }
