@@ -685,3 +685,59 @@ void or_hkmp_steps(const int64_t *n, const double *const *x, const double *const
     free(a);
     free(b);
 }
+
+/* ------------------------------------------------------------------------
+ * Pipe flow (section 4.2): c_t = alpha (c_rr + c_r / r + c_zz) - s(z) c_z,
+ * radially symmetric, second-order centred differences with n nodes per
+ * direction.  The operator is the Kronecker sum of a radial and an axial
+ * one (the coefficient 1/r depends on r only, s on z only), so the
+ * mu-mode integrator applies (section 2, eq. (tensor-structure)).
+ *
+ * Grids (the paper gives only "n points per direction"; this reading):
+ *   r_j = r_min + j h_r, j = 0..n-1, h_r = (r_max - r_min)/(n-1), both ends
+ *     Neumann (c_r = 0) by reflection: ghost c_{-1} = c_1, c_n = c_{n-2};
+ *   z_j = j h_z, j = 1..n, h_z = z_max / n: z = 0 carries the Dirichlet
+ *     value 0 and is not an unknown; z_max is Neumann by reflection
+ *     (ghost c_{n+1} = c_{n-1}).
+ * ---------------------------------------------------------------------- */
+
+/* A = alpha (D2 + diag(1/r) D1) on the radial grid; first = 0 drops the
+ * 1/r D1 term. */
+void or_pipe_radial(int n, double rmin, double rmax, double alpha, int first, double *A)
+{
+    double h = (rmax - rmin) / (n - 1);
+    memset(A, 0, sizeof(double) * (size_t)n * n);
+    for (int j = 0; j < n; ++j) {
+        double r = rmin + j * h;
+        /* coefficients of c_{j-1}, c_j, c_{j+1} before reflection */
+        double lo = 1.0 / (h * h), mid = -2.0 / (h * h), hi = 1.0 / (h * h);
+        if (first) {
+            lo -= 1.0 / (r * 2.0 * h);
+            hi += 1.0 / (r * 2.0 * h);
+        }
+        int jl = j - 1, jh = j + 1;
+        if (jl < 0) jl = 1;          /* ghost c_{-1} = c_1 */
+        if (jh > n - 1) jh = n - 2;  /* ghost c_n = c_{n-2} */
+        A[(size_t)j * n + j] += alpha * mid;
+        A[(size_t)j * n + jl] += alpha * lo;
+        A[(size_t)j * n + jh] += alpha * hi;
+    }
+}
+
+/* A = alpha D2 - diag(s) D1 on the axial grid; s holds s(z_j), j = 1..n,
+ * or is NULL (pure diffusion). */
+void or_pipe_axial(int n, double zmax, double alpha, const double *s, double *A)
+{
+    double h = zmax / n;
+    memset(A, 0, sizeof(double) * (size_t)n * n);
+    for (int q = 0; q < n; ++q) { /* unknown q is z_{q+1} */
+        double sv = s ? s[q] : 0.0;
+        double lo = alpha / (h * h) + sv / (2.0 * h);
+        double mid = -2.0 * alpha / (h * h);
+        double hi = alpha / (h * h) - sv / (2.0 * h);
+        A[(size_t)q * n + q] += mid;
+        if (q > 0) A[(size_t)q * n + q - 1] += lo; /* q == 0: neighbour z_0 = 0 is the Dirichlet value */
+        if (q < n - 1) A[(size_t)q * n + q + 1] += hi;
+        else A[(size_t)q * n + q - 1] += hi; /* ghost c_{n+1} = c_{n-1} */
+    }
+}

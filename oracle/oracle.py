@@ -57,6 +57,8 @@ def lib():
         L.or_gpe_adjoint.argtypes = [i, _f64, _f64, d, d, i64, _c128, _c128, _c128]
         L.or_hkp_hamiltonian.argtypes = [i, _f64, _f64, _f64, _f64]
         L.or_hermite_galerkin.argtypes = [i, _f64, _f64, _f64, _f64]
+        L.or_pipe_radial.argtypes = [i, d, d, d, i, _f64]
+        L.or_pipe_axial.argtypes = [i, d, d, vp, _f64]
         L.or_hkmp_steps.argtypes = [_i64, ctypes.POINTER(vp), ctypes.POINTER(vp), ctypes.POINTER(vp),
                                     ctypes.POINTER(vp), d, i64, _f64, _c128]
         L.or_hkp_steps.argtypes = [_i64, ctypes.POINTER(vp), ctypes.POINTER(vp), ctypes.POINTER(vp), d, i64,
@@ -259,6 +261,23 @@ def hkmp_steps(psi, xs, Ws, Vs, Us, tau: float, f_mid):
     uarr = (ctypes.c_void_p * 3)(*[None if u is None else u.ctypes.data_as(ctypes.c_void_p) for u in ukeep])
     lib().or_hkmp_steps(n, arr(0), arr(1), arr(2), uarr, float(tau), int(f_mid.size), f_mid, psi)
     return psi
+
+
+# --- pipe flow (section 4.2) ---------------------------------------------
+
+def pipe_radial(n: int, rmin: float, rmax: float, alpha: float, first: bool = True) -> np.ndarray:
+    """alpha (D2 + diag(1/r) D1), Neumann at both ends, nodes r_min..r_max."""
+    A = np.empty((n, n))
+    lib().or_pipe_radial(n, float(rmin), float(rmax), float(alpha), int(first), A)
+    return A
+
+
+def pipe_axial(n: int, zmax: float, alpha: float, s=None) -> np.ndarray:
+    """alpha D2 - diag(s) D1 on z_j = j z_max / n, j = 1..n (Dirichlet at 0, Neumann at z_max)."""
+    A = np.empty((n, n))
+    keep = None if s is None else _f(s)
+    lib().or_pipe_axial(n, float(zmax), float(alpha), None if keep is None else keep.ctypes.data, A)
+    return A
 
 
 def _f(a):

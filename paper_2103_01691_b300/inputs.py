@@ -115,3 +115,19 @@ def hkmp_potentials(x1: np.ndarray, x2: np.ndarray, x3: np.ndarray):
 def hkmp_f_mid(tau: float, nsteps: int, t0: float = 0.0) -> np.ndarray:
     """f(t) = sin^2 t at the step midpoints t0 + (s + 1/2) tau (eq. (mag2))."""
     return np.sin(t0 + (np.arange(nsteps) + 0.5) * tau) ** 2
+
+
+# pipe flow (section 4.2): parameters and data as the paper states them
+PIPE = {"rmin": 0.1, "rmax": 5.0, "zmax": 8.0, "alpha": 1.0 / 90.0, "z0": 1.5, "T": 4.0}
+PIPE["r0"] = 0.5 * (PIPE["rmin"] + PIPE["rmax"])
+
+
+def pipe_velocity(z: np.ndarray) -> np.ndarray:
+    """Advection velocity s(z) = 2 + tanh(4 (z - 5/2)) - tanh(4 (z - 5))."""
+    return 2.0 + np.tanh(4.0 * (z - 2.5)) - np.tanh(4.0 * (z - 5.0))
+
+
+def pipe_c0(r: np.ndarray, z: np.ndarray) -> np.ndarray:
+    """Initial concentration exp(-8 (r - r0)^2 - 8 (z - z0)^2) on the tensor
+    grid, shape (n_z, n_r) (r is direction 1, fastest)."""
+    return np.exp(-8.0 * (z[:, None] - PIPE["z0"]) ** 2 - 8.0 * (r[None, :] - PIPE["r0"]) ** 2)

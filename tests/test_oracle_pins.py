@@ -465,3 +465,48 @@ def test_hkmp_second_order_and_norm(orc):
     w3 = Ws[2][:, None, None] * Ws[1][None, :, None] * Ws[0][None, None, :]
     nrm = lambda p: np.sum(np.abs(p) ** 2 * w3)
     assert abs(nrm(ref) / nrm(psi0) - 1) < 1e-12
+
+
+# ---------------------------------------------------------------- pipe flow
+
+def test_pipe_second_differences_closed_form(orc):
+    """Without first-derivative terms the two operators have closed-form
+    eigenvectors: Neumann-Neumann (reflection) D2 on n nodes, cos(k pi j/(n-1))
+    with -4 sin^2(k pi/(2(n-1)))/h^2; Dirichlet-Neumann D2 on z_j = j h,
+    sin((2k-1) pi j/(2n)) with -4 sin^2((2k-1) pi/(4n))/h^2."""
+    n, rmin, rmax, zmax = 17, 0.1, 5.0, 8.0
+    A = orc.pipe_radial(n, rmin, rmax, 1.0, first=False)
+    h = (rmax - rmin) / (n - 1)
+    j = np.arange(n)
+    for k in (0, 1, 5, 16):
+        v = np.cos(k * np.pi * j / (n - 1))
+        lam = -4.0 * np.sin(k * np.pi / (2 * (n - 1))) ** 2 / h ** 2
+        assert np.max(np.abs(A @ v - lam * v)) < 1e-10
+    B = orc.pipe_axial(n, zmax, 1.0)
+    h = zmax / n
+    j = np.arange(1, n + 1)
+    for k in (1, 2, 9, n):
+        th = (2 * k - 1) * np.pi / (2 * n)
+        v = np.sin(th * j)
+        lam = -4.0 * np.sin(th / 2) ** 2 / h ** 2
+        assert np.max(np.abs(B @ v - lam * v)) < 1e-10
+
+
+def test_pipe_first_derivative_terms_on_quadratics(orc):
+    """Centred differences are exact on quadratics at interior nodes:
+    alpha (c_rr + c_r / r) of r^2 is 4 alpha; alpha c_zz - s c_z of z^2 is
+    2 alpha - 2 s z.  Constants are steady under the radial operator (both
+    ends Neumann), so exp(t A_r) 1 = 1."""
+    from paper_2103_01691_b300 import inputs as inp
+
+    n, rmin, rmax, zmax, alpha = 23, 0.1, 5.0, 8.0, 1.0 / 90.0
+    r = rmin + (rmax - rmin) / (n - 1) * np.arange(n)
+    A = orc.pipe_radial(n, rmin, rmax, alpha)
+    assert np.max(np.abs((A @ r ** 2)[1:-1] - 4 * alpha)) < 1e-11
+    assert np.max(np.abs(A @ np.ones(n))) < 1e-12
+    E = orc.expm_taylor(A, 4.0)
+    assert np.max(np.abs(E @ np.ones(n) - 1)) < 1e-12
+    z = zmax / n * np.arange(1, n + 1)
+    s = inp.pipe_velocity(z)
+    B = orc.pipe_axial(n, zmax, alpha, s)
+    assert np.max(np.abs((B @ z ** 2)[1:-1] - (2 * alpha - 2 * s * z)[1:-1])) < 1e-11
