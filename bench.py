@@ -203,7 +203,7 @@ def main():
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-fp64", action="store_true")
     ap.add_argument("--workload", default="free256",
-                    choices=["free256", "heat32", "ho128", "batched64", "gpe192", "hkp", "hkmp"],
+                    choices=["free256", "heat32", "ho128", "batched64", "gpe192", "hkp", "hkmp", "pipe"],
                     help="free256 (default) is the headline line; the others time the remaining workloads")
     args = ap.parse_args()
     rank, world, local = dist_env()
@@ -500,6 +500,35 @@ def other_workload(args):
                     config="HKMP, V = |x|^2/2 + x3 sin^2 t, Hermite n^3 complex, tau = 0.02, 50 steps to T = 1; "
                            "value = steps/s at n = 255 (each step: FP64 device exp of direction 3, its split, "
                            "three mode products; transforms once per call)")
+    elif args.workload == "pipe":
+        # section 4.2: d = 2, n x n, one exact step to T = 4; the paper reports wall-clock seconds
+        P = inputs.PIPE
+        paper_s = {500: 0.6763, 600: 1.0928, 700: 1.5674, 800: 1.9183, 900: 2.5244}
+        zw = P["zmax"] / 64 * np.arange(1, 65)  # warm-up: library handles and first-use allocations
+        mm.PipePlan(ctx, 64, 64, P["rmin"], P["rmax"], P["zmax"], P["alpha"], inputs.pipe_velocity(zw), P["T"],
+                    prec="fp64dmma").close()
+        for n in (500, 700, 900):
+            r = P["rmin"] + (P["rmax"] - P["rmin"]) / (n - 1) * np.arange(n)
+            z = P["zmax"] / n * np.arange(1, n + 1)
+            s = inputs.pipe_velocity(z)
+            c0 = torch.from_numpy(inputs.pipe_c0(r, z)).cuda()
+            res = {}
+            for prec in ("fp64dmma", "fp64"):
+                torch.cuda.synchronize()
+                t0 = time.perf_counter()
+                plan = mm.PipePlan(ctx, n, n, P["rmin"], P["rmax"], P["zmax"], P["alpha"], s, P["T"], prec=prec)
+                c = c0.clone()
+                plan.step(c, 1)
+                torch.cuda.synchronize()
+                total_ms = (time.perf_counter() - t0) * 1e3
+                ms = _time(lambda: plan.step(c, 1), stream)
+                res[prec] = {"total_ms": total_ms, "step_ms": ms}
+                del plan
+            res["paper_cpu_matlab_s"] = paper_s[n]
+            line[f"n{n}"] = res
+        line.update(value=1e3 / line["n900"]["fp64dmma"]["total_ms"], unit="solves/s", precision="fp64dmma",
+                    config="pipe flow, d = 2, n x n, T = 4 in one exact step; total_ms: operators, two "
+                           "device exponentials, plan, one step (value: solves/s at n = 900)")
     elif args.workload == "gpe192":
         n, beta, tau, K = 192, 100.0, 1e-3, 500
         plan = mm.HermitePlan(ctx, [n] * 3, prec="f16x6")

@@ -229,7 +229,8 @@ mm_status mumode_product_noalloc(int d, const int64_t *n, int mu, const double *
  * so they are computed on the GPU as well).
  * ------------------------------------------------------------------- */
 
-/* E = exp(z (A + f B)) in FP64 on the device.  A_dev, B_dev: real n x n,
+/* E = exp(z (A + f B)) in FP64 on the device (for real z the same
+ * series in real arithmetic, DGEMMs).  A_dev, B_dev: real n x n,
  * row-major, device (B_dev may be NULL); E_dev: n x n complex interleaved
  * (2 n^2 doubles), device, overlapping neither.  Scaling and squaring of
  * the degree-18 Taylor polynomial (Paterson-Stockmeyer evaluation; the
@@ -257,6 +258,29 @@ mm_status mm_expm_device(mm_ctx *ctx, int n, const double *A_dev, const double *
  * MM_ERR_DTYPE (FP32 or real SIMT plans), MM_ERR_CUDA. */
 mm_status mm_plan_set_matrix_device(mm_plan *plan, int mu, const double *E_dev, double row_norm_bound,
                                     void *stream);
+
+/* ---------------------------------------------------------------------
+ * Pipe flow (section 4.2): c_t = alpha (c_rr + c_r / r + c_zz) - s(z) c_z
+ * on [r_min, r_max] x [0, z_max], radially symmetric, centred second-order
+ * differences; a Kronecker sum of a radial and an axial operator, so the
+ * exact solution at T is the Tucker operator of exp(T A_r), exp(T A_z).
+ * Grids: r_j = r_min + j (r_max - r_min)/(n_r - 1), j < n_r, with c_r = 0
+ * at both ends (mirrored neighbour); z_j = j z_max / n_z, j = 1..n_z, with
+ * c = 0 at z = 0 (not an unknown) and c_z = 0 at z_max (mirrored).
+ *
+ * mm_pipe_operators: A_r (n_r x n_r) and A_z (n_z x n_z), row-major, host,
+ * caller-allocated (either may be NULL); s_nodes[j] = s(z_{j+1}) (n_z
+ * values, or NULL for no advection).
+ *
+ * pipe_plan_create: a d = 2 Tucker plan (real MM_R64 data, direction 1 = r,
+ * fastest) whose step is the solution operator over T: the operators as
+ * above, exp(T A) of each on the device (mm_expm_device, real series),
+ * FP64 precisions only (MM_PREC_FP64_SIMT, MM_PREC_FP64_DMMA; any n).
+ * Synchronises the default stream. */
+mm_status mm_pipe_operators(int n_r, int n_z, double rmin, double rmax, double zmax, double alpha,
+                            const double *s_nodes, double *A_r, double *A_z);
+mm_status pipe_plan_create(mm_ctx *ctx, int n_r, int n_z, double rmin, double rmax, double zmax, double alpha,
+                           const double *s_nodes, double T, mm_prec prec, mm_plan **out);
 
 /* ---------------------------------------------------------------------
  * Tucker-operator plan: U <- U x_{o_1} E_{o_1} ... x_{o_d} E_{o_d}

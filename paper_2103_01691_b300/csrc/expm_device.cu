@@ -242,11 +242,12 @@ __global__ void double_angle(int n, int count, double *C, double *S)
     }
 }
 
+// E = C + i S (S null: real E)
 __global__ void interleave(int64_t total, const double *C, const double *S, double2 *E)
 {
     for (int64_t q = blockIdx.x * int64_t(blockDim.x) + threadIdx.x; q < total;
          q += int64_t(gridDim.x) * blockDim.x)
-        E[q] = make_double2(C[q], S[q]);
+        E[q] = make_double2(C[q], S ? S[q] : 0.0);
 }
 
 // C_k = P_k Q_k for row-major n x n matrices, k < count (column-major Q^T-view times P^T-view)
@@ -371,6 +372,53 @@ cudaError_t expm_imag_batched(ExpmBatch *w, int n, const double *A, const double
         count_launch();
     }
     interleave<<<g, 256, 0, s>>>(total, C, S, E);
+    count_launch();
+    return cudaGetLastError();
+}
+
+// ---- real z: the Taylor series in real arithmetic ----------------------------------
+//
+// For real M and real z the series of expm_device runs on real matrices
+// (DGEMM): X = z M / 2^s, T = B_0 + X^4 (B_1 + X^4 (B_2 + X^4 (B_3 + X^4 B_4))),
+// E = T^(2^s).  Squaring keeps the small entries of decaying flows (a
+// cosh / sinh split would cancel them).
+cudaError_t expm_real_device(ExpmBatch *w, int n, const double *A, const double *B, double f, double z,
+                             double norm_bound, double2 *E, cudaStream_t s)
+{
+    if (w->n < n || w->cap < 1 || !w->blas) return cudaErrorInvalidValue;
+    cublasHandle_t h = static_cast<cublasHandle_t>(w->blas);
+    if (cublasSetStream(h, s) != CUBLAS_STATUS_SUCCESS) return cudaErrorUnknown;
+    const double za = std::fabs(z) * norm_bound;
+    int sq = 0;
+    if (za > 1.0) sq = int(std::ceil(std::log2(za)));
+    while (std::ldexp(za, -sq) > 1.0) ++sq;
+    double *X = w->buf[0], *X2 = w->buf[1], *X3 = w->buf[2], *X4 = w->buf[3], *cur = w->buf[4], *nxt = w->buf[5];
+    const int64_t nn = int64_t(n) * n;
+    const int g = blocks_for(nn);
+    form_x_batch<<<g, 256, 0, s>>>(nn, 1, A, B, nullptr, f, std::ldexp(z, -sq), X);
+    count_launch();
+    cudaError_t e = cudaGetLastError();
+    if (e != cudaSuccess) return e;
+    if (gemm_batch(h, n, 1, X, X, X2, false) != CUBLAS_STATUS_SUCCESS ||
+        gemm_batch(h, n, 1, X2, X, X3, false) != CUBLAS_STATUS_SUCCESS ||
+        gemm_batch(h, n, 1, X2, X2, X4, false) != CUBLAS_STATUS_SUCCESS)
+        return cudaErrorUnknown;
+    double c[19];
+    c[0] = 1.0;
+    for (int k = 1; k <= 18; ++k) c[k] = c[k - 1] / double(k);
+    combo_batch<<<g, 256, 0, s>>>(n, 1, c[16], c[17], c[18], 0.0, X, X2, nullptr, cur);
+    count_launch();
+    for (int j = 3; j >= 0; --j) {
+        combo_batch<<<g, 256, 0, s>>>(n, 1, c[4 * j], c[4 * j + 1], c[4 * j + 2], c[4 * j + 3], X, X2, X3, nxt);
+        count_launch();
+        if (gemm_batch(h, n, 1, X4, cur, nxt, true) != CUBLAS_STATUS_SUCCESS) return cudaErrorUnknown;
+        std::swap(cur, nxt);
+    }
+    for (int k = 0; k < sq; ++k) {
+        if (gemm_batch(h, n, 1, cur, cur, nxt, false) != CUBLAS_STATUS_SUCCESS) return cudaErrorUnknown;
+        std::swap(cur, nxt);
+    }
+    interleave<<<g, 256, 0, s>>>(nn, cur, nullptr, E);
     count_launch();
     return cudaGetLastError();
 }

@@ -252,6 +252,41 @@ void hermite_galerkin(int m, const double *x, const double *W, const double *U, 
     }
 }
 
+// Pipe flow (section 4.2), centred second-order differences.  Radial
+// operator alpha (d^2/dr^2 + (1/r) d/dr) on r_j = r_min + j h, j < n,
+// h = (r_max - r_min)/(n - 1), with c_r = 0 at both ends imposed by
+// mirroring the neighbour (the ghost value equals the value one node in).
+void pipe_radial(int n, double rmin, double rmax, double alpha, double *A)
+{
+    std::fill(A, A + size_t(n) * n, 0.0);
+    const double h = (rmax - rmin) / double(n - 1), d2 = alpha / (h * h);
+    for (int j = 0; j < n; ++j) {
+        const double d1 = alpha / ((rmin + j * h) * 2.0 * h);
+        const int left = j == 0 ? 1 : j - 1, right = j == n - 1 ? n - 2 : j + 1;
+        double *row = A + size_t(j) * n;
+        row[j] += -2.0 * d2;
+        row[left] += d2 - d1;
+        row[right] += d2 + d1;
+    }
+}
+
+// Axial operator alpha d^2/dz^2 - s(z) d/dz on z_j = j h, j = 1..n,
+// h = z_max / n: c = 0 at z = 0 (not an unknown) and c_z = 0 at z_max by
+// mirroring.  s holds s(z_j) for the n unknowns.
+void pipe_axial(int n, double zmax, double alpha, const double *s, double *A)
+{
+    std::fill(A, A + size_t(n) * n, 0.0);
+    const double h = zmax / double(n), d2 = alpha / (h * h);
+    for (int q = 0; q < n; ++q) {
+        const double d1 = (s ? s[q] : 0.0) / (2.0 * h);
+        double *row = A + size_t(q) * n;
+        row[q] += -2.0 * d2;
+        if (q > 0) row[q - 1] += d2 + d1;
+        const int right = q == n - 1 ? n - 2 : q + 1;
+        if (right >= 0) row[right] += d2 - d1;
+    }
+}
+
 // Values-space propagator of one direction over time tau (section 4.3):
 // M = Psi exp(-i tau H) Phi^W with Psi[l][k] = phi_k(x_l) and
 // Phi^W[k][l] = phi_k(x_l) W_l, so that a mu-mode product with M takes the

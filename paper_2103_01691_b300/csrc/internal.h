@@ -136,6 +136,12 @@ void expm_batch_destroy(ExpmBatch *w);
 int expm_batch_capacity(int n);  // batch entries that keep the workspace near 1 GB (1..64)
 cudaError_t expm_imag_batched(ExpmBatch *w, int n, const double *A, const double *B, const double *f_host, int count,
                               double wim, double norm_bound, double2 *E, cudaStream_t s);
+// exp(z (A + f B)) for real z, Taylor series in real arithmetic; E complex with zero imaginary parts.
+cudaError_t expm_real_device(ExpmBatch *w, int n, const double *A, const double *B, double f, double z,
+                             double norm_bound, double2 *E, cudaStream_t s);
+// Pipe-flow operators (host_setup.cpp)
+void pipe_radial(int n, double rmin, double rmax, double alpha, double *A);
+void pipe_axial(int n, double zmax, double alpha, const double *s, double *A);
 // Host half of tc_matrix_create: geometry (pieces/rho left null) and the
 // host images of the pieces and row scales.
 mm_status tc_matrix_host(const double *E, int64_t m, int64_t n, int npieces, bool fixed, TcMatrix *geom,

@@ -1555,11 +1555,13 @@ extern "C" mm_status mm_expm_device(mm_ctx *ctx, int n, const double *A_dev, con
         e = mm::expm_norm1_device(&ctx->expm, n, A_dev, B_dev, f, &norm_bound, s);
         if (e != cudaSuccess) return cuda_fail(e, "expm norm");
     }
-    if (z_re == 0.0) {  // cos + i sin in real arithmetic
+    if (z_re == 0.0 || z_im == 0.0) {  // real arithmetic: cos + i sin, or the real series
         if ((e = mm::expm_batch_init(&ctx->expmb, n, 1)) != cudaSuccess)
             return fail(MM_ERR_OOM, "expm workspace (%s)", cudaGetErrorString(e));
-        e = mm::expm_imag_batched(&ctx->expmb, n, A_dev, B_dev, &f, 1, z_im, norm_bound,
-                                  reinterpret_cast<double2 *>(E_dev), s);
+        e = z_re == 0.0 ? mm::expm_imag_batched(&ctx->expmb, n, A_dev, B_dev, &f, 1, z_im, norm_bound,
+                                                reinterpret_cast<double2 *>(E_dev), s)
+                        : mm::expm_real_device(&ctx->expmb, n, A_dev, B_dev, f, z_re, norm_bound,
+                                               reinterpret_cast<double2 *>(E_dev), s);
     } else {
         e = mm::expm_device(&ctx->expm, n, A_dev, B_dev, f, z_re, z_im, norm_bound, reinterpret_cast<double2 *>(E_dev),
                             s);
@@ -1751,4 +1753,55 @@ extern "C" mm_status hkmp_evolve(mm_plan *p, void *psi, int64_t nsteps, const do
     cudaError_t e = cudaStreamSynchronize(s);
     if (e != cudaSuccess) return cuda_fail(e, "HKMP steps");
     return hermite_apply(p, false, p->coef, psi, stream);
+}
+
+// ---------------------------------------------------------------------------
+// Pipe flow (section 4.2)
+
+extern "C" mm_status mm_pipe_operators(int n_r, int n_z, double rmin, double rmax, double zmax, double alpha,
+                                       const double *s_nodes, double *A_r, double *A_z)
+{
+    if (n_r < 2 || n_r > 4096 || n_z < 2 || n_z > 4096) return fail(MM_ERR_SHAPE, "n_r, n_z must be in 2..4096");
+    if (!(rmin > 0.0) || !(rmax > rmin) || !(zmax > 0.0) || !(alpha > 0.0) || !std::isfinite(rmax) ||
+        !std::isfinite(zmax) || !std::isfinite(alpha))
+        return fail(MM_ERR_INVALID_ARG, "need 0 < r_min < r_max, z_max > 0, alpha > 0");
+    if (A_r) mm::pipe_radial(n_r, rmin, rmax, alpha, A_r);
+    if (A_z) mm::pipe_axial(n_z, zmax, alpha, s_nodes, A_z);
+    return MM_OK;
+}
+
+extern "C" mm_status pipe_plan_create(mm_ctx *ctx, int n_r, int n_z, double rmin, double rmax, double zmax,
+                                      double alpha, const double *s_nodes, double T, mm_prec prec, mm_plan **out)
+{
+    if (!ctx || !out) return fail(MM_ERR_INVALID_ARG, "NULL argument");
+    if (!std::isfinite(T)) return fail(MM_ERR_INVALID_ARG, "T is not finite");
+    if (prec != MM_PREC_FP64_SIMT && prec != MM_PREC_FP64_DMMA)
+        return fail(MM_ERR_UNSUPPORTED, "pipe flow runs on the FP64 paths (MM_PREC_FP64_SIMT or MM_PREC_FP64_DMMA)");
+    const int nn[2] = {n_r, n_z};
+    std::vector<double> A[2] = {std::vector<double>(size_t(n_r) * n_r), std::vector<double>(size_t(n_z) * n_z)};
+    mm_status st = mm_pipe_operators(n_r, n_z, rmin, rmax, zmax, alpha, s_nodes, A[0].data(), A[1].data());
+    if (st) return st;
+    // exp(T A) of both directions on the device (real Taylor series), then the plan's real matrices
+    std::vector<double> E[2];
+    cudaStream_t s = nullptr;
+    for (int v = 0; v < 2; ++v) {
+        const int m = nn[v];
+        double *Ad = nullptr, *Ed = nullptr;
+        cudaError_t e = cudaMalloc(&Ad, sizeof(double) * size_t(m) * m);
+        if (e == cudaSuccess) e = cudaMalloc(&Ed, 2 * sizeof(double) * size_t(m) * m);
+        if (e == cudaSuccess) e = cudaMemcpy(Ad, A[v].data(), sizeof(double) * size_t(m) * m, cudaMemcpyHostToDevice);
+        if (e == cudaSuccess)
+            st = mm_expm_device(ctx, m, Ad, nullptr, 0.0, T, 0.0, norm1_host(m, A[v].data()), Ed, s);
+        std::vector<double> Ec(size_t(2) * m * m);
+        if (e == cudaSuccess && !st) e = cudaMemcpy(Ec.data(), Ed, sizeof(double) * Ec.size(), cudaMemcpyDeviceToHost);
+        if (Ad) cudaFree(Ad);
+        if (Ed) cudaFree(Ed);
+        if (st) return st;
+        if (e != cudaSuccess) return cuda_fail(e, "pipe-flow exponential");
+        E[v].resize(size_t(m) * m);
+        for (size_t q = 0; q < E[v].size(); ++q) E[v][q] = Ec[2 * q];
+    }
+    const int64_t n64[2] = {n_r, n_z};
+    const double *Ep[2] = {E[0].data(), E[1].data()};
+    return mumode_plan_create(ctx, 2, n64, Ep, 0, MM_R64, prec, nullptr, out);
 }

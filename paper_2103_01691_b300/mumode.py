@@ -64,6 +64,10 @@ SIGNATURES = {
     "hkmp_plan_create": (_i, [_vp, _i, _i64p, ctypes.POINTER(_dp), ctypes.POINTER(_dp), ctypes.c_double, _i, _i,
                               ctypes.POINTER(_vp)]),
     "hkmp_evolve": (_i, [_vp, _vp, _i64, _dp, _vp]),
+    "mm_pipe_operators": (_i, [_i, _i, ctypes.c_double, ctypes.c_double, ctypes.c_double, ctypes.c_double, _dp, _dp,
+                               _dp]),
+    "pipe_plan_create": (_i, [_vp, _i, _i, ctypes.c_double, ctypes.c_double, ctypes.c_double, ctypes.c_double, _dp,
+                              ctypes.c_double, _i, ctypes.POINTER(_vp)]),
     "hkp_plan_create": (_i, [_vp, _i, _i64p, ctypes.POINTER(_dp), ctypes.c_double, _i, _i, ctypes.POINTER(_i),
                              ctypes.POINTER(_vp)]),
     "hermite_nodes": (_i, [_vp, _i, _dp, _dp]),
@@ -456,6 +460,34 @@ class HKPPlan(TuckerPlan):
         h = ctypes.c_void_p()
         _check(lib().hkp_plan_create(ctx.handle, d, self.dims.ctypes.data_as(_i64p), ptrs, float(tau), code,
                                      PREC[prec], optr, ctypes.byref(h)))
+        self.handle = h
+
+
+def pipe_operators(n_r: int, n_z: int, rmin: float, rmax: float, zmax: float, alpha: float, s=None):
+    """mm_pipe_operators: the radial and axial operators of the pipe flow (section 4.2)."""
+    Ar, Az = np.empty((n_r, n_r)), np.empty((n_z, n_z))
+    sc = None if s is None else np.ascontiguousarray(s, dtype=np.float64)
+    _check(lib().mm_pipe_operators(n_r, n_z, float(rmin), float(rmax), float(zmax), float(alpha),
+                                   _dptr(sc) if sc is not None else None, _dptr(Ar), _dptr(Az)))
+    return Ar, Az
+
+
+class PipePlan(TuckerPlan):
+    """pipe_plan_create: the pipe-flow solution operator over T as a d = 2
+    real FP64 Tucker plan (direction 1 = r).  step(c) advances c, a CUDA
+    float64 tensor of shape (n_z, n_r), by T."""
+
+    def __init__(self, ctx: Context, n_r: int, n_z: int, rmin: float, rmax: float, zmax: float, alpha: float, s,
+                 T: float, prec: str = "fp64dmma"):
+        import torch
+
+        self.ctx = ctx
+        self.dims = np.array([n_r, n_z], dtype=np.int64)
+        self.dtype = torch.float64
+        self._s = np.ascontiguousarray(s, dtype=np.float64)
+        h = ctypes.c_void_p()
+        _check(lib().pipe_plan_create(ctx.handle, n_r, n_z, float(rmin), float(rmax), float(zmax), float(alpha),
+                                      _dptr(self._s), float(T), PREC[prec], ctypes.byref(h)))
         self.handle = h
 
 

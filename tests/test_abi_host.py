@@ -26,7 +26,7 @@ def mm():
 def header_functions():
     text = open(os.path.join(ROOT, "include", "mumode.h")).read()
     text = re.sub(r"/\*.*?\*/", "", text, flags=re.S)
-    return sorted(set(re.findall(r"\b(mm_\w+|mumode_\w+|hermite_\w+|hkp_\w+|hkmp_\w+|split_step_\w+)\s*\(", text)))
+    return sorted(set(re.findall(r"\b(mm_\w+|mumode_\w+|hermite_\w+|hkp_\w+|hkmp_\w+|pipe_\w+|split_step_\w+)\s*\(", text)))
 
 
 def test_every_declared_symbol_is_exported(mm):
@@ -86,3 +86,30 @@ def test_hermite_matrices_match_oracle(mm, orc, m):
     H = orc.hermite_functions(m, xo)
     assert np.max(np.abs(B - H.T)) < 1e-11
     assert np.max(np.abs(F - H * Wo)) < 1e-11 * np.max(np.abs(H * Wo))
+
+
+@pytest.mark.parametrize("m", [1, 16, 96])
+def test_hermite_hamiltonian_and_galerkin_match_oracle(mm, orc, m):
+    """Host set-up of HKP / HKMP: mm_hermite_hamiltonian against the oracle's."""
+    x, _ = mm.gauss_hermite(m)
+    xo, _, Wo = orc.gauss_hermite(m)
+    H = mm.hermite_hamiltonian(m, np.cos(2 * np.pi * x))
+    ref = orc.hkp_hamiltonian(xo, Wo, np.cos(2 * np.pi * xo))
+    assert np.max(np.abs(H - ref)) <= 1e-12 * max(1.0, np.max(np.abs(ref)))
+
+
+@pytest.mark.parametrize("n_r,n_z", [(2, 3), (17, 40), (128, 96)])
+def test_pipe_operators_match_oracle(mm, orc, n_r, n_z):
+    from paper_2103_01691_b300 import inputs
+
+    P = inputs.PIPE
+    z = P["zmax"] / n_z * np.arange(1, n_z + 1)
+    s = inputs.pipe_velocity(z)
+    Ar, Az = mm.pipe_operators(n_r, n_z, P["rmin"], P["rmax"], P["zmax"], P["alpha"], s)
+    ref_r = orc.pipe_radial(n_r, P["rmin"], P["rmax"], P["alpha"])
+    ref_z = orc.pipe_axial(n_z, P["zmax"], P["alpha"], s)
+    assert np.max(np.abs(Ar - ref_r)) <= 1e-13 * np.max(np.abs(ref_r))
+    assert np.max(np.abs(Az - ref_z)) <= 1e-13 * np.max(np.abs(ref_z))
+    L = mm.lib()
+    assert L.mm_pipe_operators(1, 4, 0.1, 5.0, 8.0, 0.01, None, None, None) == 2  # MM_ERR_SHAPE
+    assert L.mm_pipe_operators(4, 4, 0.0, 5.0, 8.0, 0.01, None, None, None) == 1  # r_min must be > 0

@@ -503,6 +503,34 @@ def test_hkmp_vs_oracle(env, orc, prec, tdir):
     ctx.status()
 
 
+# ---------------------------------------------------------- pipe flow (section 4.2)
+
+@pytest.mark.parametrize("prec,n_r,n_z,T", [("fp64dmma", 40, 56, 4.0), ("fp64", 40, 56, 4.0),
+                                             ("fp64dmma", 257, 301, 1.0), ("fp64", 257, 301, 4.0)])
+def test_pipe_flow_vs_oracle(env, orc, prec, n_r, n_z, T):
+    """pipe_plan_create (operators on the host, exp(T A) on the device) and
+    one step to T against the oracle's operators, Taylor exponentials and
+    Tucker operator.  The pulse crosses the pipe (speed 2 to 4) and leaves
+    through z_max by t ~ 3, so at T = 4 on a fine grid only small tails
+    remain; T = 1 compares the pulse inside the pipe."""
+    mm, ctx, torch = env
+    P = dict(inputs.PIPE)
+    P["T"] = T
+    r = P["rmin"] + (P["rmax"] - P["rmin"]) / (n_r - 1) * np.arange(n_r)
+    z = P["zmax"] / n_z * np.arange(1, n_z + 1)
+    s = inputs.pipe_velocity(z)
+    c0 = inputs.pipe_c0(r, z)
+    plan = mm.PipePlan(ctx, n_r, n_z, P["rmin"], P["rmax"], P["zmax"], P["alpha"], s, P["T"], prec=prec)
+    c = torch.from_numpy(c0).cuda()
+    plan.step(c, 1)
+    Er = orc.expm_taylor(orc.pipe_radial(n_r, P["rmin"], P["rmax"], P["alpha"]), P["T"])
+    Ez = orc.expm_taylor(orc.pipe_axial(n_z, P["zmax"], P["alpha"], s), P["T"])
+    ref = orc.tucker(c0.astype(complex), [Er, Ez]).real
+    err = rel(c.cpu().numpy(), ref)
+    print(f"pipe {prec} n=({n_r},{n_z}) rel_err={err:.3e} max c(T)={ref.max():.4f}")
+    assert err <= 1e-12
+
+
 def test_fixed_point_wide_dynamic_range(env, orc):
     """F16x6 keeps a relative L2 accuracy when magnitudes span 1e-6 .. 1:
     the fixed-point leading piece is relative to the maximum, the FP16
