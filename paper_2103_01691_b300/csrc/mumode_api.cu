@@ -262,15 +262,17 @@ mm_status tc_sweep(mm_plan *p, mm::TcMatrix *const *M, int &cur, const mm::TcEpi
         if (q == p->d - 1) epi = last_epi;
         mm::TcScales sc;
         if (p->fixed) {
-            // W[t][q] = d_max[t d + q]: launch (sweep, q) accumulates into W[t][q] and reads W[1-t][q];
-            // it clears the word the next launch accumulates into, whose last reader has finished:
-            // W[1-t][q-1] for q >= 1, W[t][d-1] for q = 0 (tc_begin clears W[0][*] for sweep 0)
-            const int t = int(p->sweep & 1), d = p->d;
+            // Three sets of maximum words, W[t][q] = d_max[t d + q], rotate with the sweep k (t = k mod 3):
+            // launch (k, q) reads W[t-1][q] (sweep k-1's maximum), accumulates into W[t][q] and clears
+            // W[t+1][q] for sweep k+1.  That word was last read by launch (k-1, q), which has completed,
+            // and the launch itself neither reads nor writes it, whatever d is (with two sets and
+            // d = 1 it would be the word the launch reads).  tc_begin clears W[0][*] for sweep 0.
+            const int t = int(p->sweep % 3), d = p->d;
             sc.s_in = p->d_scale + q;
             sc.s_out = p->d_scale + (q + 1) % d;
-            sc.max_prev = p->d_max + (1 - t) * d + q;
+            sc.max_prev = p->d_max + ((t + 2) % 3) * d + q;
             sc.max_cur = p->d_max + t * d + q;
-            sc.zero_next = (q + 1 < d) ? p->d_max + t * d + (q + 1) : p->d_max + (1 - t) * d + 0;
+            sc.zero_next = p->d_max + ((t + 1) % 3) * d + q;
         }
         cudaEvent_t ev0 = timing_event(p->ctx, true);
         if (ev0) cudaEventRecord(ev0, s);
@@ -300,8 +302,9 @@ mm_status tc_begin(mm_plan *p, mm::TcMatrix *const *M, const void *u, cudaStream
         cudaError_t e0 = cudaMemsetAsync(p->d_max, 0, sizeof(unsigned) * p->d, s);
         if (e0 != cudaSuccess) return cuda_fail(e0, "scale word reset");
     }
+    // sweep 0 reads its maximum words from set 2: the split writes the bounds there
     cudaError_t e = mm::tc_split(p->st, p->npieces, p->fixed, u, p->work[0], p->d_work, p->d_scale,
-                                 p->d_max ? p->d_max + p->d : nullptr, bounds, p->d, s);
+                                 p->d_max ? p->d_max + 2 * p->d : nullptr, bounds, p->d, s);
     if (e != cudaSuccess) return cuda_fail(e, "split");
     return MM_OK;
 }
@@ -354,9 +357,9 @@ mm_status alloc_workspace(mm_plan *p)
         }
         if (p->fixed) {
             e = cudaMalloc(&p->d_scale, sizeof(float) * p->d);
-            if (e == cudaSuccess) e = cudaMalloc(&p->d_max, sizeof(unsigned) * 2 * p->d);
+            if (e == cudaSuccess) e = cudaMalloc(&p->d_max, sizeof(unsigned) * 3 * p->d);
             if (e == cudaSuccess) e = cudaMalloc(&p->d_work, sizeof(unsigned));
-            if (e == cudaSuccess) e = cudaMemset(p->d_max, 0, sizeof(unsigned) * 2 * p->d);
+            if (e == cudaSuccess) e = cudaMemset(p->d_max, 0, sizeof(unsigned) * 3 * p->d);
             if (e != cudaSuccess) return fail(MM_ERR_OOM, "scale words");
         }
     } else {
@@ -1312,9 +1315,11 @@ struct mm_batch {
     int d = 0;
     mm_prec prec = MM_PREC_F16X6;
     bool fixed = false;
-    // problem records for sweep position q and sweep parity t: host copy and device array
-    std::vector<mm::TcProblem> host[mm::kMaxDims][2];
-    mm::TcProblem *dev[mm::kMaxDims][2] = {};
+    // problem records for sweep position q and sweep k mod 6 (the input buffer follows k d + q mod 2,
+    // the maximum words k mod 3): host copy and device array
+    static constexpr int kPhases = 6;
+    std::vector<mm::TcProblem> host[mm::kMaxDims][kPhases];
+    mm::TcProblem *dev[mm::kMaxDims][kPhases] = {};
     bool kmajor[mm::kMaxDims] = {};
 };
 
@@ -1342,11 +1347,12 @@ extern "C" mm_status mumode_batch_create(mm_ctx *ctx, mm_plan *const *plans, int
     b->fixed = p0->fixed;
     const int d = b->d;
     for (int q = 0; q < d; ++q)
-        for (int t = 0; t < 2; ++t) {
-            auto &vec = b->host[q][t];
+        for (int ph = 0; ph < mm_batch::kPhases; ++ph) {
+            auto &vec = b->host[q][ph];
             vec.resize(size_t(nprob));
             int64_t begin = 0;
-            const int cur = (t * d + q) % 2;  // buffer holding the input of this launch
+            const int cur = (ph * d + q) % 2;  // buffer holding the input of this launch
+            const int t = ph % 3;              // maximum-word set (as in tc_sweep)
             for (int k = 0; k < nprob; ++k) {
                 mm_plan *p = plans[k];
                 const int mu = p->order[q];
@@ -1355,10 +1361,9 @@ extern "C" mm_status mumode_batch_create(mm_ctx *ctx, mm_plan *const *plans, int
                 if (p->fixed) {
                     sc.s_in = p->d_scale + q;
                     sc.s_out = p->d_scale + (q + 1) % d;
-                    sc.max_prev = p->d_max + (1 - t) * d + q;
+                    sc.max_prev = p->d_max + ((t + 2) % 3) * d + q;
                     sc.max_cur = p->d_max + t * d + q;
-                    // the max word of this position's output is cleared by the launch one position later
-                    zero = (q >= 1) ? p->d_max + (1 - t) * d + (q - 1) : p->d_max + t * d + (d - 1);
+                    zero = p->d_max + ((t + 1) % 3) * d + q;  // sweep k+1's word (see tc_sweep)
                 }
                 bool km = false;
                 cudaError_t e = mm::tc_problem_build(p->st, p->st, mu, p->Etc[mu - 1], p->prec, p->work[cur],
@@ -1377,11 +1382,11 @@ extern "C" mm_status mumode_batch_create(mm_ctx *ctx, mm_plan *const *plans, int
                 }
             }
             const size_t bytes = sizeof(mm::TcProblem) * size_t(nprob);
-            if (cudaMalloc(&b->dev[q][t], bytes) != cudaSuccess) {
+            if (cudaMalloc(&b->dev[q][ph], bytes) != cudaSuccess) {
                 mm_batch_destroy(b);
                 return fail(MM_ERR_OOM, "problem records");
             }
-            cudaError_t e = cudaMemcpy(b->dev[q][t], vec.data(), bytes, cudaMemcpyHostToDevice);
+            cudaError_t e = cudaMemcpy(b->dev[q][ph], vec.data(), bytes, cudaMemcpyHostToDevice);
             if (e != cudaSuccess) {
                 mm_batch_destroy(b);
                 return cuda_fail(e, "problem records upload");
@@ -1414,10 +1419,10 @@ extern "C" mm_status mumode_batch_step(mm_batch *b, void *const *u_dev, int64_t 
     }
     for (int64_t t = 0; t < nsteps; ++t)
         for (int q = 0; q < d; ++q) {
-            const int par = int(t & 1);
+            const int ph = int(t % mm_batch::kPhases);
             cudaEvent_t ev0 = timing_event(b->ctx, true);
             if (ev0) cudaEventRecord(ev0, s);
-            cudaError_t e = mm::tc_mode_product_batched(b->host[q][par].data(), b->dev[q][par], int(b->plans.size()),
+            cudaError_t e = mm::tc_mode_product_batched(b->host[q][ph].data(), b->dev[q][ph], int(b->plans.size()),
                                                         b->kmajor[q], b->prec, mm::TcEpilogue{}, b->ctx->d_err, s);
             if (ev0) cudaEventRecord(timing_event(b->ctx, false), s);
             if (e != cudaSuccess) return cuda_fail(e, "batched mode product");
@@ -1432,8 +1437,8 @@ extern "C" void mm_batch_destroy(mm_batch *b)
 {
     if (!b) return;
     for (int q = 0; q < mm::kMaxDims; ++q)
-        for (int t = 0; t < 2; ++t)
-            if (b->dev[q][t]) cudaFree(b->dev[q][t]);
+        for (int ph = 0; ph < mm_batch::kPhases; ++ph)
+            if (b->dev[q][ph]) cudaFree(b->dev[q][ph]);
     delete b;
 }
 
