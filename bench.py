@@ -205,6 +205,7 @@ def main():
     ap.add_argument("--workload", default="free256",
                     choices=["free256", "heat32", "ho128", "batched64", "gpe192", "hkp", "hkmp", "pipe"],
                     help="free256 (default) is the headline line; the others time the remaining workloads")
+    ap.add_argument("--sizes", default="", help="hkp / hkmp / pipe: comma-separated sizes n (default: the paper's)")
     args = ap.parse_args()
     rank, world, local = dist_env()
     if args.workload != "free256":
@@ -409,6 +410,8 @@ def other_workload(args):
     stream = torch.cuda.Stream()
     torch.cuda.set_stream(stream)
     line = {"workload": args.workload, "unit": "steps/s", "higher_is_better": True, "data": "synthetic"}
+    sizes = tuple(int(v) for v in args.sizes.split(",") if v)
+    precs = ("f16x6",) if args.no_fp64 else ("f16x6", "fp64dmma")
     if args.workload == "heat32":
         n, tau, K = 32, 1e-3, 10
         E = mm.expm(mm.fd_laplacian_dirichlet(n), tau).real
@@ -433,12 +436,12 @@ def other_workload(args):
     elif args.workload == "hkp":
         # section 4.3: V = cos(2 pi x_1) + x_2^2/2 + x_3^2/2, one step to T = 1
         _, tc_peak, _, _ = peaks()
-        for n in (127, 255):
+        for n in sizes or (127, 255):
             x, _ = mm.gauss_hermite(n)
             Vs = list(inputs.hkp_potentials(x, x, x))
             psi0 = inputs.hkp_psi0(x, x, x)
             res = {}
-            for prec in ("f16x6", "fp64dmma"):
+            for prec in precs:
                 t0 = time.perf_counter()
                 plan = mm.HKPPlan(ctx, [n] * 3, Vs, 1.0, prec=prec)
                 setup_ms = (time.perf_counter() - t0) * 1e3
@@ -458,7 +461,7 @@ def other_workload(args):
                                      issued_frac_of_measured_bf16_burst=issued / tc_peak)
                 del plan, psi
             line[f"n{n}"] = res
-        line.update(value=1e3 / line["n255"]["f16x6"]["ms_per_step"], precision="f16x6",
+        line.update(value=1e3 / line[f"n{(sizes or (255,))[-1]}"]["f16x6"]["ms_per_step"], precision="f16x6",
                     paper_gpu_ms_per_step={"n127": {"single": 0.64, "double": 1.27},
                                            "n255": {"single": 8.11, "double": 16.02}},
                     config="HKP, V = cos(2 pi x1) + x2^2/2 + x3^2/2, Hermite n^3 complex, one step to T = 1; "
@@ -467,12 +470,12 @@ def other_workload(args):
         # section 4.4: |x|^2/2 + x_3 sin^2 t, tau = 0.02, 50 Magnus steps to T = 1
         tau, K = 0.02, 50
         f_mid = inputs.hkmp_f_mid(tau, K)
-        for n in (127, 255):
+        for n in sizes or (127, 255):
             x, _ = mm.gauss_hermite(n)
             Vs, Us = inputs.hkmp_potentials(x, x, x)
             psi0 = inputs.hkp_psi0(x, x, x)
             res = {}
-            for prec in ("f16x6", "fp64dmma"):
+            for prec in precs:
                 f64 = prec.startswith("fp64")
                 t0 = time.perf_counter()
                 plan = mm.HKMPPlan(ctx, [n] * 3, [None, None, None], list(Us), tau, prec=prec)
@@ -492,7 +495,7 @@ def other_workload(args):
             ms_e = _time(lambda: mm.expm_device(ctx, H0, G, 0.5, -1j * tau, norm_bound=bound, out=E), stream)
             res["exp_int_ms"] = ms_e
             line[f"n{n}"] = res
-        line.update(value=1e3 / line["n255"]["f16x6"]["ms_per_step"], precision="f16x6",
+        line.update(value=1e3 / line[f"n{(sizes or (255,))[-1]}"]["f16x6"]["ms_per_step"], precision="f16x6",
                     paper_gpu_ms_per_step={"n127": {"double": {"exp_int": 0.37, "mu_mode": 1.05},
                                                     "single": {"exp_int": 0.25, "mu_mode": 0.54}},
                                            "n255": {"double": {"exp_int": 0.66, "mu_mode": 13.79},
@@ -507,7 +510,7 @@ def other_workload(args):
         zw = P["zmax"] / 64 * np.arange(1, 65)  # warm-up: library handles and first-use allocations
         mm.PipePlan(ctx, 64, 64, P["rmin"], P["rmax"], P["zmax"], P["alpha"], inputs.pipe_velocity(zw), P["T"],
                     prec="fp64dmma").close()
-        for n in (500, 700, 900):
+        for n in sizes or (500, 700, 900):
             r = P["rmin"] + (P["rmax"] - P["rmin"]) / (n - 1) * np.arange(n)
             z = P["zmax"] / n * np.arange(1, n + 1)
             s = inputs.pipe_velocity(z)
@@ -526,7 +529,8 @@ def other_workload(args):
                 del plan
             res["paper_cpu_matlab_s"] = paper_s[n]
             line[f"n{n}"] = res
-        line.update(value=1e3 / line["n900"]["fp64dmma"]["total_ms"], unit="solves/s", precision="fp64dmma",
+        line.update(value=1e3 / line[f"n{(sizes or (900,))[-1]}"]["fp64dmma"]["total_ms"], unit="solves/s",
+                    precision="fp64dmma",
                     config="pipe flow, d = 2, n x n, T = 4 in one exact step; total_ms: operators, two "
                            "device exponentials, plan, one step (value: solves/s at n = 900)")
     elif args.workload == "gpe192":
