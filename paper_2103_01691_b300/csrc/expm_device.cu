@@ -203,15 +203,15 @@ cudaError_t expm_device(ExpmWorkspace *w, int n, const double *A, const double *
 
 namespace {
 
-// f: count device values, or null for the single value f0
-__global__ void form_x_batch(int64_t nn, int count, const double *A, const double *B, const double *f, double f0,
-                             double w, double *X)
+// X_k = w (A + f_k B - mu I); f: count device values, or null for the single value f0
+__global__ void form_x_batch(int64_t nn, int n, int count, const double *A, const double *B, const double *f,
+                             double f0, double mu, double w, double *X)
 {
     const int64_t total = nn * count;
     for (int64_t q = blockIdx.x * int64_t(blockDim.x) + threadIdx.x; q < total;
          q += int64_t(gridDim.x) * blockDim.x) {
         const int64_t k = q / nn, e = q % nn;
-        X[q] = w * (A[e] + (B ? (f ? f[k] : f0) * B[e] : 0.0));
+        X[q] = w * (A[e] + (B ? (f ? f[k] : f0) * B[e] : 0.0) - (e / n == e % n ? mu : 0.0));
     }
 }
 
@@ -242,12 +242,14 @@ __global__ void double_angle(int n, int count, double *C, double *S)
     }
 }
 
-// E = C + i S (S null: real E)
-__global__ void interleave(int64_t total, const double *C, const double *S, double2 *E)
+// E = (pr + i pi) (C + i S) (S null: real C)
+__global__ void interleave(int64_t total, const double *C, const double *S, double pr, double pi, double2 *E)
 {
     for (int64_t q = blockIdx.x * int64_t(blockDim.x) + threadIdx.x; q < total;
-         q += int64_t(gridDim.x) * blockDim.x)
-        E[q] = make_double2(C[q], S ? S[q] : 0.0);
+         q += int64_t(gridDim.x) * blockDim.x) {
+        const double c = C[q], s = S ? S[q] : 0.0;
+        E[q] = make_double2(pr * c - pi * s, pr * s + pi * c);
+    }
 }
 
 // C_k = P_k Q_k for row-major n x n matrices, k < count (column-major Q^T-view times P^T-view)
@@ -311,8 +313,9 @@ int expm_batch_capacity(int n)
 }
 
 cudaError_t expm_imag_batched(ExpmBatch *w, int n, const double *A, const double *B, const double *f_host, int count,
-                              double wim, double norm_bound, double2 *E, cudaStream_t s)
+                              double wim, double norm_bound, double2 *E, cudaStream_t s, double mu)
 {
+    // exp(i w M) = exp(i w mu) exp(i w (M - mu I)): norm_bound bounds ||M - mu I||_1
     if (w->n < n || w->cap < count || count < 1 || !w->blas) return cudaErrorInvalidValue;
     cublasHandle_t h = static_cast<cublasHandle_t>(w->blas);
     if (cublasSetStream(h, s) != CUBLAS_STATUS_SUCCESS) return cudaErrorUnknown;
@@ -328,7 +331,8 @@ cudaError_t expm_imag_batched(ExpmBatch *w, int n, const double *A, const double
            *C = w->buf[6], *S = w->buf[7];
     const int64_t nn = int64_t(n) * n, total = nn * count;
     const int g = blocks_for(total);
-    form_x_batch<<<g, 256, 0, s>>>(nn, count, A, B, count > 1 ? w->f : nullptr, f_host[0], std::ldexp(wim, -sq), X);
+    form_x_batch<<<g, 256, 0, s>>>(nn, n, count, A, B, count > 1 ? w->f : nullptr, f_host[0], mu, std::ldexp(wim, -sq),
+                                   X);
     count_launch();
     if ((e = cudaGetLastError()) != cudaSuccess) return e;
     if (gemm_batch(h, n, count, X, X, Y, false) != CUBLAS_STATUS_SUCCESS ||
@@ -371,7 +375,7 @@ cudaError_t expm_imag_batched(ExpmBatch *w, int n, const double *A, const double
         double_angle<<<g, 256, 0, s>>>(n, count, C, S);
         count_launch();
     }
-    interleave<<<g, 256, 0, s>>>(total, C, S, E);
+    interleave<<<g, 256, 0, s>>>(total, C, S, std::cos(wim * mu), std::sin(wim * mu), E);
     count_launch();
     return cudaGetLastError();
 }
@@ -395,7 +399,7 @@ cudaError_t expm_real_device(ExpmBatch *w, int n, const double *A, const double 
     double *X = w->buf[0], *X2 = w->buf[1], *X3 = w->buf[2], *X4 = w->buf[3], *cur = w->buf[4], *nxt = w->buf[5];
     const int64_t nn = int64_t(n) * n;
     const int g = blocks_for(nn);
-    form_x_batch<<<g, 256, 0, s>>>(nn, 1, A, B, nullptr, f, std::ldexp(z, -sq), X);
+    form_x_batch<<<g, 256, 0, s>>>(nn, n, 1, A, B, nullptr, f, 0.0, std::ldexp(z, -sq), X);
     count_launch();
     cudaError_t e = cudaGetLastError();
     if (e != cudaSuccess) return e;
@@ -418,7 +422,7 @@ cudaError_t expm_real_device(ExpmBatch *w, int n, const double *A, const double 
         if (gemm_batch(h, n, 1, cur, cur, nxt, false) != CUBLAS_STATUS_SUCCESS) return cudaErrorUnknown;
         std::swap(cur, nxt);
     }
-    interleave<<<g, 256, 0, s>>>(nn, cur, nullptr, E);
+    interleave<<<g, 256, 0, s>>>(nn, cur, nullptr, 1.0, 0.0, E);
     count_launch();
     return cudaGetLastError();
 }

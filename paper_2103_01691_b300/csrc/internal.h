@@ -134,8 +134,9 @@ struct ExpmBatch {
 cudaError_t expm_batch_init(ExpmBatch *w, int n, int cap);
 void expm_batch_destroy(ExpmBatch *w);
 int expm_batch_capacity(int n);  // batch entries that keep the workspace near 1 GB (1..64)
+// mu: a diagonal shift taken out as the phase exp(i w mu); norm_bound then bounds ||A + f_k B - mu I||_1.
 cudaError_t expm_imag_batched(ExpmBatch *w, int n, const double *A, const double *B, const double *f_host, int count,
-                              double wim, double norm_bound, double2 *E, cudaStream_t s);
+                              double wim, double norm_bound, double2 *E, cudaStream_t s, double mu = 0.0);
 // exp(z (A + f B)) for real z, Taylor series in real arithmetic; E complex with zero imaginary parts.
 cudaError_t expm_real_device(ExpmBatch *w, int n, const double *A, const double *B, double f, double z,
                              double norm_bound, double2 *E, cudaStream_t s);

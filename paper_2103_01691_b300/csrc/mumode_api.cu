@@ -72,7 +72,8 @@ struct mm_plan {
     bool hkmp = false;
     double tau = 0.0;
     double *H0dev[mm::kMaxDims] = {}, *Gdev[mm::kMaxDims] = {};
-    double h0norm[mm::kMaxDims] = {}, gnorm[mm::kMaxDims] = {};
+    double h0norm[mm::kMaxDims] = {}, gnorm[mm::kMaxDims] = {};  // ||H0 - mu I||_1, ||G||_1
+    double hshift[mm::kMaxDims] = {};  // mu: the middle of H0's diagonal range, taken out as a phase
     double2 *Ebatch[mm::kMaxDims] = {};  // the exponentials of a chunk of steps (expmb.cap matrices)
     void *coef = nullptr;  // coefficient tensor of hkmp_evolve
     mm::ExpmBatch expmb;
@@ -1661,7 +1662,15 @@ extern "C" mm_status hkmp_plan_create(mm_ctx *ctx, int d, const int64_t *n, cons
         const double *U = U_nodes ? U_nodes[v] : nullptr;
         if (!U) continue;
         mm::hermite_galerkin(m, p->x[v].data(), p->W[v].data(), U, G.data());
-        p->h0norm[v] = norm1_host(m, H.data());
+        double dmin = H[0], dmax = H[0];
+        for (int k = 0; k < m; ++k) {
+            dmin = std::min(dmin, H[size_t(k) * m + k]);
+            dmax = std::max(dmax, H[size_t(k) * m + k]);
+        }
+        p->hshift[v] = 0.5 * (dmin + dmax);
+        std::vector<double> Hs(H);
+        for (int k = 0; k < m; ++k) Hs[size_t(k) * m + k] -= p->hshift[v];
+        p->h0norm[v] = norm1_host(m, Hs.data());
         p->gnorm[v] = norm1_host(m, G.data());
         const size_t bytes = sizeof(double) * size_t(m) * m;
         if (cudaMalloc(&p->H0dev[v], bytes) != cudaSuccess || cudaMalloc(&p->Gdev[v], bytes) != cudaSuccess ||
@@ -1714,7 +1723,7 @@ extern "C" mm_status hkmp_evolve(mm_plan *p, void *psi, int64_t nsteps, const do
             if (!p->H0dev[v]) continue;
             const double bound = p->h0norm[v] + fmax * p->gnorm[v];
             cudaError_t e = mm::expm_imag_batched(&p->expmb, int(p->n[v]), p->H0dev[v], p->Gdev[v], f_mid + k0, cnt,
-                                                  -p->tau, bound, p->Ebatch[v], s);
+                                                  -p->tau, bound, p->Ebatch[v], s, p->hshift[v]);
             if (e != cudaSuccess) return cuda_fail(e, "device expm");
         }
         return MM_OK;

@@ -347,10 +347,13 @@ __global__ void matrix_update_kernel(const double2 *__restrict__ E, int64_t m, i
 {
     const int64_t i = blockIdx.x;
     if (i >= m) return;
+    extern __shared__ double absrow[];  // |C_ij| + |S_ij| of the row (n doubles)
     __shared__ double r_sh;
+    for (int64_t j = threadIdx.x; j < n; j += blockDim.x) absrow[j] = fabs(E[i * n + j].x) + fabs(E[i * n + j].y);
+    __syncthreads();
     if (threadIdx.x == 0) {
         double sum_abs = 0.0;
-        for (int64_t j = 0; j < n; ++j) sum_abs += fabs(E[i * n + j].x) + fabs(E[i * n + j].y);
+        for (int64_t j = 0; j < n; ++j) sum_abs += absrow[j];  // the host's order
         const double r = fixed ? row_scale(sum_abs) : 1.0;
         r_sh = r;
         if (rho) rho[i] = float(r);
@@ -390,7 +393,9 @@ __global__ void matrix_update_kernel(const double2 *__restrict__ E, int64_t m, i
 cudaError_t tc_matrix_update(TcMatrix &M, const double2 *E, cudaStream_t s)
 {
     if (!M.pieces || !E || (M.fixed && !M.rho)) return cudaErrorInvalidValue;
-    matrix_update_kernel<<<unsigned(M.n_out), 128, 0, s>>>(
+    const size_t smem = sizeof(double) * size_t(M.n_in);
+    if (smem > 48 * 1024) return cudaErrorInvalidValue;  // n_in <= 6144
+    matrix_update_kernel<<<unsigned(M.n_out), 128, smem, s>>>(
         E, M.n_out, M.n_in, M.npieces, M.fixed, M.ni, M.it, M.k_pad / 16, static_cast<uint16_t *>(M.pieces), M.rho,
         static_cast<uint16_t *>(M.pair[0].pieces), M.pair[0].it, static_cast<uint16_t *>(M.pair[1].pieces),
         M.pair[1].it);
