@@ -113,3 +113,23 @@ def test_pipe_operators_match_oracle(mm, orc, n_r, n_z):
     L = mm.lib()
     assert L.mm_pipe_operators(1, 4, 0.1, 5.0, 8.0, 0.01, None, None, None) == 2  # MM_ERR_SHAPE
     assert L.mm_pipe_operators(4, 4, 0.0, 5.0, 8.0, 0.01, None, None, None) == 1  # r_min must be > 0
+
+
+def test_new_entry_points_reject_bad_arguments_without_gpu(mm):
+    """HKP, HKMP, pipe flow, device exponentials and device matrices validate
+    their arguments before touching the device."""
+    L = mm.lib()
+    n3 = (ctypes.c_int64 * 3)(8, 8, 8)
+    out = ctypes.c_void_p()
+    assert L.hkp_plan_create(None, 3, n3, None, 1.0, 1, 5, None, ctypes.byref(out)) == 1
+    assert L.hkmp_plan_create(None, 3, n3, None, None, 0.1, 1, 5, ctypes.byref(out)) == 1
+    assert L.hkmp_evolve(None, None, 1, None, None) == 1
+    assert L.pipe_plan_create(None, 8, 8, 0.1, 5.0, 8.0, 0.01, None, 4.0, 6, ctypes.byref(out)) == 1
+    assert L.mm_expm_device(None, 4, None, None, 0.0, 1.0, 0.0, 0.0, None, None) == 1
+    assert L.mm_plan_set_matrix_device(None, 1, None, 0.0, None) == 1
+    assert L.mm_hermite_hamiltonian(0, None, None) == 2
+    assert L.mm_hermite_hamiltonian(4, None, None) == 1
+    assert L.mumode_batch_autotune(None, None, None, 0, 1, None, None) == 1
+    H = np.empty((5, 5))
+    assert L.mm_hermite_hamiltonian(5, None, H.ctypes.data_as(ctypes.POINTER(ctypes.c_double))) == 0
+    assert np.array_equal(H, np.diag(np.arange(5) + 0.5))
