@@ -1322,7 +1322,58 @@ struct mm_batch {
     std::vector<mm::TcProblem> host[mm::kMaxDims][kPhases];
     mm::TcProblem *dev[mm::kMaxDims][kPhases] = {};
     bool kmajor[mm::kMaxDims] = {};
+    // the same for the CTA-pair kernel (records opaque, mm::tc_pair_record_bytes() each), used when
+    // every problem has a pair tiling with row tiles of the same size
+    bool pair = false;
+    std::vector<uint8_t> phost[mm::kMaxDims][kPhases];
+    void *pdev[mm::kMaxDims][kPhases] = {};
 };
+
+// Pair-kernel records of all (position, phase) of a batch; false if some product has no such tiling.
+static bool build_pair_records(mm_batch *b, mm_plan *const *plans, int nprob)
+{
+    if (mm::tc_default_variant() == mm::kTcOneSM) return false;
+    const size_t rb = mm::tc_pair_record_bytes();
+    const int d = b->d;
+    for (int q = 0; q < d; ++q)
+        for (int ph = 0; ph < mm_batch::kPhases; ++ph) {
+            auto &buf = b->phost[q][ph];
+            buf.assign(rb * size_t(nprob), 0);
+            const int cur = (ph * d + q) % 2;
+            const int t = ph % 3;
+            int64_t begin = 0;
+            for (int k = 0; k < nprob; ++k) {
+                mm_plan *p = plans[k];
+                const int mu = p->order[q];
+                mm::TcScales sc;
+                if (p->fixed) {
+                    sc.s_in = p->d_scale + q;
+                    sc.s_out = p->d_scale + (q + 1) % d;
+                    sc.max_prev = p->d_max + ((t + 2) % 3) * d + q;
+                    sc.max_cur = p->d_max + t * d + q;
+                    sc.zero_next = p->d_max + ((t + 1) % 3) * d + q;  // sweep k+1's word (see tc_sweep)
+                }
+                bool km = false;
+                int64_t items = 0;
+                void *rec = buf.data() + rb * size_t(k);
+                if (mm::tc_pair_record_build(p->st, p->st, mu, p->Etc[mu - 1], p->prec, p->work[cur], p->work[1 - cur],
+                                             sc, rec, &km, &items) != cudaSuccess ||
+                    km != b->kmajor[q])
+                    return false;
+                mm::tc_pair_record_set_begin(rec, begin);
+                begin += items;
+            }
+            if (!mm::tc_pair_batch_compatible(buf.data(), nprob)) return false;
+        }
+    for (int q = 0; q < d; ++q)
+        for (int ph = 0; ph < mm_batch::kPhases; ++ph) {
+            const auto &buf = b->phost[q][ph];
+            if (cudaMalloc(&b->pdev[q][ph], buf.size()) != cudaSuccess ||
+                cudaMemcpy(b->pdev[q][ph], buf.data(), buf.size(), cudaMemcpyHostToDevice) != cudaSuccess)
+                return false;
+        }
+    return true;
+}
 
 extern "C" mm_status mumode_batch_create(mm_ctx *ctx, mm_plan *const *plans, int nprob, mm_batch **out)
 {
@@ -1393,6 +1444,7 @@ extern "C" mm_status mumode_batch_create(mm_ctx *ctx, mm_plan *const *plans, int
                 return cuda_fail(e, "problem records upload");
             }
         }
+    b->pair = build_pair_records(b, plans, nprob);
     *out = b;
     return MM_OK;
 }
@@ -1423,8 +1475,12 @@ extern "C" mm_status mumode_batch_step(mm_batch *b, void *const *u_dev, int64_t 
             const int ph = int(t % mm_batch::kPhases);
             cudaEvent_t ev0 = timing_event(b->ctx, true);
             if (ev0) cudaEventRecord(ev0, s);
-            cudaError_t e = mm::tc_mode_product_batched(b->host[q][ph].data(), b->dev[q][ph], int(b->plans.size()),
-                                                        b->kmajor[q], b->prec, mm::TcEpilogue{}, b->ctx->d_err, s);
+            cudaError_t e = b->pair ? mm::tc_pair_batch_launch(b->phost[q][ph].data(), b->pdev[q][ph],
+                                                               int(b->plans.size()), b->kmajor[q], b->prec,
+                                                               b->ctx->d_err, s)
+                                    : mm::tc_mode_product_batched(b->host[q][ph].data(), b->dev[q][ph],
+                                                                  int(b->plans.size()), b->kmajor[q], b->prec,
+                                                                  mm::TcEpilogue{}, b->ctx->d_err, s);
             if (ev0) cudaEventRecord(timing_event(b->ctx, false), s);
             if (e != cudaSuccess) return cuda_fail(e, "batched mode product");
         }
@@ -1438,8 +1494,10 @@ extern "C" void mm_batch_destroy(mm_batch *b)
 {
     if (!b) return;
     for (int q = 0; q < mm::kMaxDims; ++q)
-        for (int ph = 0; ph < mm_batch::kPhases; ++ph)
+        for (int ph = 0; ph < mm_batch::kPhases; ++ph) {
             if (b->dev[q][ph]) cudaFree(b->dev[q][ph]);
+            if (b->pdev[q][ph]) cudaFree(b->pdev[q][ph]);
+        }
     delete b;
 }
 

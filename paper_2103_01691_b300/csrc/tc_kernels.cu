@@ -646,6 +646,26 @@ __host__ __device__ constexpr int num_terms(int NP) { return NP == 3 ? 6 : (NP =
 __host__ __device__ constexpr int term_a(int t) { return t == 2 ? 1 : (t == 4 ? 1 : (t == 5 ? 2 : 0)); }
 __host__ __device__ constexpr int term_b(int t) { return t == 1 ? 1 : (t == 3 ? 2 : (t == 4 ? 1 : 0)); }
 
+// One problem of a batched CTA-pair launch: its tensor maps (read by TMA from
+// global memory), its kernel arguments and its first work item.
+struct alignas(64) TcPairProblem {
+    CUtensorMap mapX, mapE, mapY;
+    TcArgs a;
+    int64_t pairs_begin;
+};
+
+// The problem of work item P (records sorted by pairs_begin, the first at 0).
+__device__ __forceinline__ const TcPairProblem &pair_problem(const TcPairProblem *many, int nprob, int64_t P)
+{
+    int lo = 0, hi = nprob - 1;
+    while (lo < hi) {
+        const int mid = (lo + hi + 1) / 2;
+        if (many[mid].pairs_begin <= P) lo = mid;
+        else hi = mid - 1;
+    }
+    return many[lo];
+}
+
 constexpr int kEpiWarps = 16;      // four per TMEM lane quarter
 constexpr int kThreads = 32 * (2 + kEpiWarps);  // warp 0 TMA, warp 1 TMEM + MMA, then the epilogue warps
 constexpr int kChunksPerWarp = 2;  // 16-row chunks each epilogue warp drains (IT <= 128)
@@ -1165,11 +1185,15 @@ __host__ __device__ constexpr int pair_staging_bytes(int CH) { return CH == 1 ? 
 // accumulator set once the epilogue warps of both CTAs have drained it:
 // the peer's warps arrive on their own barrier, which one thread of the
 // peer relays to the leader's.
-template <int NP, bool KMAJOR, int EPI, bool FX, int CH>
+template <int NP, bool KMAJOR, int EPI, bool FX, int CH, bool BATCH>
 __global__ void __launch_bounds__(kThreads, 1)
     tc_pair_kernel(const __grid_constant__ CUtensorMap mapX, const __grid_constant__ CUtensorMap mapE,
-                   const __grid_constant__ CUtensorMap mapY, TcArgs a)
+                   const __grid_constant__ CUtensorMap mapY, TcArgs a, const TcPairProblem *__restrict__ many,
+                   int nprob, int64_t total)
 {
+    // BATCH: items P < total of many problems (records `many`, sorted by pairs_begin); `a` then
+    // carries only what all problems share (row tiles of the same size, stage layout, error word)
+    const int64_t items = BATCH ? total : a.pairs;
     constexpr int kSt = pair_stages(CH);
     extern __shared__ __align__(1024) uint8_t smem_raw[];
     uint8_t *smem = reinterpret_cast<uint8_t *>((reinterpret_cast<uintptr_t>(smem_raw) + 1023) & ~uintptr_t(1023));
@@ -1201,9 +1225,11 @@ __global__ void __launch_bounds__(kThreads, 1)
         }
         *abort_flag = 0;
         mbar_fence_init();
-        tma_prefetch_desc(&mapX);
-        tma_prefetch_desc(&mapE);
-        if (CH == 1) tma_prefetch_desc(&mapY);
+        if (!BATCH) {
+            tma_prefetch_desc(&mapX);
+            tma_prefetch_desc(&mapE);
+            if (CH == 1) tma_prefetch_desc(&mapY);
+        }
     }
     if (warp == 1) {
         tmem_alloc_pair(tmem_slot, ncols);
@@ -1218,7 +1244,14 @@ __global__ void __launch_bounds__(kThreads, 1)
     // writes data of the previous kernel (input pieces, scale words) only after it has completed.
     if (threadIdx.x == 0) griddep_launch_dependents();
     griddep_wait();
-    if (FX && blockIdx.x == 0 && threadIdx.x == 0 && a.sc.zero_next) *a.sc.zero_next = 0u;
+    if (FX && blockIdx.x == 0 && threadIdx.x == 0) {
+        if (!BATCH) {
+            if (a.sc.zero_next) *a.sc.zero_next = 0u;
+        } else {
+            for (int q = 0; q < nprob; ++q)
+                if (many[q].a.sc.zero_next) *many[q].a.sc.zero_next = 0u;
+        }
+    }
     const int64_t cid = blockIdx.x / 2, nclusters = gridDim.x / 2;
     const int half = a.it / 2;
     const int e_bytes = 3 * half * 32;  // one piece's [-S; C; S] blocks in a stage
@@ -1231,25 +1264,30 @@ __global__ void __launch_bounds__(kThreads, 1)
             int s = 0;
             uint32_t ph = 0;  // ring position
             const int e_rows = 3 * half / 4;  // 128-byte rows of one block triple
-            for (int64_t P = cid; P < a.pairs && !*abort_flag; P += nclusters) {
-                const int64_t tile = (P / a.ni) * 2 + rank;
-                const int h = int(P % a.ni);
+            for (int64_t P = cid; P < items && !*abort_flag; P += nclusters) {
+                const TcPairProblem *pr = BATCH ? &pair_problem(many, nprob, P) : nullptr;
+                const TcArgs &A = BATCH ? pr->a : a;
+                const CUtensorMap *mx = BATCH ? &pr->mapX : &mapX, *me = BATCH ? &pr->mapE : &mapE;
+                const int64_t Pl = BATCH ? P - pr->pairs_begin : P;
+                const int64_t tile = (Pl / A.ni) * 2 + rank;
+                const int h = int(Pl % A.ni);
                 // MN-major: the two 64-point atoms of the tile (slab row, first point), past the end zero fill
                 int ac_l[2] = {0, 0}, ac_r[2] = {0, 0};
                 if (!KMAJOR) {
                     for (int q = 0; q < 2; ++q) {
                         const int64_t atom = 2 * tile + q;
-                        int64_t r = atom / a.aps;
-                        if (r > a.right) r = a.right;
+                        int64_t r = atom / A.aps;
+                        if (r > A.right) r = A.right;
                         ac_r[q] = int(r);
-                        ac_l[q] = int((atom % a.aps) * 64);
+                        ac_l[q] = int((atom % A.aps) * 64);
                     }
                 }
                 const int k_row = int(tile * kTileM);
                 // the matrix blocks of all pieces for (row tile h, k-block kb, rank): one box of 128-byte rows
                 const int e_box_rows = NP * e_rows;
-                const int e_row0 = (h * a.kblocks * 2 + rank) * e_box_rows;
-                for (int kb = a.kb_lo[h]; kb < a.kb_hi[h]; ++kb) {
+                const int e_row0 = (h * A.kblocks * 2 + rank) * e_box_rows;
+                const int kb_end = A.kb_hi[h];
+                for (int kb = A.kb_lo[h]; kb < kb_end; ++kb) {
                     if (!mbar_wait(&empty[s], ph ^ 1u, a.err, MM_ERR_TIMEOUT)) {
                         *abort_flag = 1;
                         break;
@@ -1260,12 +1298,12 @@ __global__ void __launch_bounds__(kThreads, 1)
                     // all 2 NP piece planes in one box (K-major: [plane][128 points][16]) or one box per
                     // atom (MN-major: [atom][plane][16 k][64 points])
                     if (KMAJOR) {
-                        tma_load_3d_pair(&mapX, fb, st, kb * kBK, k_row, 0);
+                        tma_load_3d_pair(mx, fb, st, kb * kBK, k_row, 0);
                     } else {
-                        tma_load_4d_pair(&mapX, fb, st, ac_l[0], kb * kBK, ac_r[0], 0);
-                        tma_load_4d_pair(&mapX, fb, st + 2 * NP * 2048, ac_l[1], kb * kBK, ac_r[1], 0);
+                        tma_load_4d_pair(mx, fb, st, ac_l[0], kb * kBK, ac_r[0], 0);
+                        tma_load_4d_pair(mx, fb, st + 2 * NP * 2048, ac_l[1], kb * kBK, ac_r[1], 0);
                     }
-                    tma_load_2d_pair(&mapE, fb, st + a.e_offset, 0, e_row0 + kb * 2 * e_box_rows);
+                    tma_load_2d_pair(me, fb, st + a.e_offset, 0, e_row0 + kb * 2 * e_box_rows);
                     if (++s == kSt) {
                         s = 0;
                         ph ^= 1u;
@@ -1281,7 +1319,7 @@ __global__ void __launch_bounds__(kThreads, 1)
             // CTA's epilogue warps have drained an accumulator set (their own
             // arrivals stay CTA-scope, which does not wait for their stores).
             uint32_t lt = 0;
-            for (int64_t P = cid; P < a.pairs; P += nclusters, ++lt) {
+            for (int64_t P = cid; P < items; P += nclusters, ++lt) {
                 const int b = int(lt % uint32_t(nsets));
                 if (!mbar_wait(&tmem_empty[b], (lt / uint32_t(nsets)) & 1u, a.err, MM_ERR_TIMEOUT)) {
                     *abort_flag = 1;
@@ -1314,8 +1352,10 @@ __global__ void __launch_bounds__(kThreads, 1)
             const uint64_t stage_step = uint64_t(uint32_t(a.stage_bytes) >> 4);
             int s = 0;
             uint32_t ph = 0, lt = 0;  // ring position, advanced with the producer's
-            for (int64_t P = cid; P < a.pairs && !*abort_flag; P += nclusters, ++lt) {
-                const int h = int(P % a.ni);
+            for (int64_t P = cid; P < items && !*abort_flag; P += nclusters, ++lt) {
+                const TcPairProblem *pr = BATCH ? &pair_problem(many, nprob, P) : nullptr;
+                const TcArgs &A = BATCH ? pr->a : a;
+                const int h = int((BATCH ? P - pr->pairs_begin : P) % A.ni);
                 const int b = int(lt % uint32_t(nsets));
                 const uint32_t use = lt / uint32_t(nsets);
                 if (use > 0 && !mbar_wait<true>(&tmem_empty[b], (use - 1) & 1u, a.err, MM_ERR_TIMEOUT)) {
@@ -1324,7 +1364,7 @@ __global__ void __launch_bounds__(kThreads, 1)
                 }
                 tc_fence_after();
                 const uint32_t d0 = tmem + uint32_t(b * set_cols), d1 = d0 + uint32_t(acc_cols);
-                const int kb_lo = a.kb_lo[h], kb_hi = a.kb_hi[h];
+                const int kb_lo = A.kb_lo[h], kb_hi = A.kb_hi[h];
                 for (int kb = kb_lo; kb < kb_hi; ++kb) {
                     if (!mbar_wait(&full[s], ph, a.err, MM_ERR_TIMEOUT)) {
                         *abort_flag = 1;
@@ -1359,19 +1399,34 @@ __global__ void __launch_bounds__(kThreads, 1)
         const int nchunks = a.it / 16;
         float s_in = 1.0f, inv_out = 1.0f, lim = 0.0f;
         int es_out = 0;
-        if (FX) {
-            s_in = *a.sc.s_in;
-            es_out = grid_exponent(__uint_as_float(*a.sc.max_prev));
-            inv_out = ldexpf(1.0f, -es_out);
-            lim = ldexpf(16384.0f, es_out);
-            if (blockIdx.x == 0 && ew == 0 && lane == 0) *a.sc.s_out = ldexpf(1.0f, es_out);
-        }
         float local_max = 0.0f;
         bool range_ok = true;
+        // the fixed-point scales of the problem being stored (BATCH: they change with the problem,
+        // and the maximum gathered so far goes to the previous problem's word first)
+        const TcArgs *cur = nullptr;
+        auto scales_for = [&](const TcArgs &A, bool first_item) {
+            if (!FX || cur == &A) return;
+            if (cur) {
+                const unsigned m = __reduce_max_sync(0xffffffffu, __float_as_uint(local_max));
+                if (lane == 0 && m) atomicMax(cur->sc.max_cur, m);
+                local_max = 0.0f;
+            }
+            cur = &A;
+            s_in = *A.sc.s_in;
+            es_out = grid_exponent(__uint_as_float(*A.sc.max_prev));
+            inv_out = ldexpf(1.0f, -es_out);
+            lim = ldexpf(16384.0f, es_out);
+            if (first_item && ew == 0 && lane == 0) *A.sc.s_out = ldexpf(1.0f, es_out);
+        };
+        if (!BATCH) scales_for(a, blockIdx.x == 0);
         uint32_t lt = 0;
-        for (int64_t P = cid; P < a.pairs; P += nclusters, ++lt) {
-            const int64_t tile = (P / a.ni) * 2 + rank;
-            const int h = int(P % a.ni);
+        for (int64_t P = cid; P < items; P += nclusters, ++lt) {
+            const TcPairProblem *pr = BATCH ? &pair_problem(many, nprob, P) : nullptr;
+            const TcArgs &A = BATCH ? pr->a : a;
+            const int64_t Pl = BATCH ? P - pr->pairs_begin : P;
+            if (BATCH) scales_for(A, Pl == 0 && rank == 0);
+            const int64_t tile = (Pl / A.ni) * 2 + rank;
+            const int h = int(Pl % A.ni);
             const int b = int(lt % uint32_t(nsets));
             // the same decision in every lane: the warp stays converged for its collective instructions
             const bool acc_ready = __all_sync(
@@ -1409,9 +1464,9 @@ __global__ void __launch_bounds__(kThreads, 1)
                 __syncwarp();
                 if (lane == 0) mbarrier_arrive(&tmem_empty[b]);
                 if (!acc_ready) break;
-                epi_frag_store<NP, KMAJOR, EPI, FX>(a, &mapY, staging + ew * kStagingPerWarp, vr, vi, tile, h,
-                                                    quarter, lane, grp, nchunks, s_in, inv_out, lim, local_max,
-                                                    range_ok);
+                epi_frag_store<NP, KMAJOR, EPI, FX>(A, BATCH ? &pr->mapY : &mapY, staging + ew * kStagingPerWarp,
+                                                    vr, vi, tile, h, quarter, lane, grp, nchunks, s_in, inv_out,
+                                                    lim, local_max, range_ok);
             } else {
                 // drain: the leading accumulator straight into v, the corrections added (no spills on this path)
                 float v[CH][32];
@@ -1442,14 +1497,14 @@ __global__ void __launch_bounds__(kThreads, 1)
                 __syncwarp();
                 if (lane == 0) mbarrier_arrive(&tmem_empty[b]);
                 if (!acc_ready) break;
-                epi_store<NP, KMAJOR, EPI, FX, CH>(a, v, tile, h, quarter * 32 + lane, grp, nchunks, s_in, inv_out,
+                epi_store<NP, KMAJOR, EPI, FX, CH>(A, v, tile, h, quarter * 32 + lane, grp, nchunks, s_in, inv_out,
                                                    lim, local_max, range_ok);
             }
         }
         if (CH == 1 && lane == 0) bulk_wait0();  // this warp's stores are complete
         if (FX) {
             const unsigned m = __reduce_max_sync(0xffffffffu, __float_as_uint(local_max));
-            if (lane == 0 && m) atomicMax(a.sc.max_cur, m);
+            if (lane == 0 && m && cur) atomicMax(cur->sc.max_cur, m);
             if (!range_ok && a.err) atomicCAS(a.err, 0, MM_ERR_RANGE);
         }
     }
@@ -1896,14 +1951,15 @@ static cudaError_t launch_tc(const CUtensorMap &mx, const CUtensorMap &me, const
     cfg.numAttrs = 2;
     cudaError_t e;
     if constexpr (PAIR) {
-        auto kern = a.it > 64 ? tc_pair_kernel<NP, KM, EPI, FX, 2> : tc_pair_kernel<NP, KM, EPI, FX, 1>;
+        auto kern = a.it > 64 ? tc_pair_kernel<NP, KM, EPI, FX, 2, false> : tc_pair_kernel<NP, KM, EPI, FX, 1, false>;
         e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
         if (e != cudaSuccess) return e;
         // persistent grid: no more clusters than can be resident at once
         int active = 0;
         if (cudaOccupancyMaxActiveClusters(&active, kern, &cfg) == cudaSuccess && active > 0 && 2 * active < grid)
             cfg.gridDim = dim3(unsigned(2 * active));
-        e = cudaLaunchKernelEx(&cfg, kern, mx, me, my, a);
+        e = cudaLaunchKernelEx(&cfg, kern, mx, me, my, a, static_cast<const TcPairProblem *>(nullptr), 0,
+                               int64_t(0));
     } else {
         auto kern = tc_mode_kernel<NP, KM, EPI, FX>;
         e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
@@ -1937,15 +1993,25 @@ static const TcMatrix::TcPairTiles *pair_tiles(const TcMatrix &M, TcVariant v)
     return P.pieces ? &P : nullptr;
 }
 
-cudaError_t tc_mode_product(const TcState &si, const TcState &so, int mu, const TcMatrix &M, mm_prec prec,
+// Everything a launch of one product needs: tensor maps, kernel arguments,
+// which kernel (K-major or not, pair or one-SM), grid and shared memory.
+struct TcLaunch {
+    CUtensorMap mx, me, my;
+    TcArgs a;
+    bool km = false, pair = false, fx = false;
+    int np = 0, grid = 0, smem = 0;
+};
+
+static cudaError_t tc_setup(const TcState &si, const TcState &so, int mu, const TcMatrix &M, mm_prec prec,
                             const void *in_pieces, void *out_pieces, const TcEpilogue &epi, const TcScales &sc,
-                            int *d_err, cudaStream_t s, TcVariant variant)
+                            int *d_err, TcVariant variant, TcLaunch *L)
 {
     const int NP = tc_pieces(prec);
     const bool fx = tc_fixed(prec);
     if (NP == 0 || NP != M.npieces || fx != M.fixed) return cudaErrorInvalidValue;
     if (fx && (!sc.s_in || !sc.s_out || !sc.max_prev || !sc.max_cur || !M.rho)) return cudaErrorInvalidValue;
-    TcArgs a{};
+    TcArgs &a = L->a;
+    a = TcArgs{};
     a.left = 1;
     a.right = 1;
     for (int v = 0; v < mu - 1; ++v) a.left *= si.np[v];
@@ -1972,7 +2038,7 @@ cudaError_t tc_mode_product(const TcState &si, const TcState &so, int mu, const 
     a.sc = sc;
     const bool km = a.left == 1;
 
-    CUtensorMap mx, me;
+    CUtensorMap &mx = L->mx, &me = L->me;
     void *xin = const_cast<void *>(in_pieces);
     if (km) {
         cuuint64_t dims[3] = {cuuint64_t(a.kp), cuuint64_t(a.right), cuuint64_t(2 * NP)};
@@ -2033,7 +2099,7 @@ cudaError_t tc_mode_product(const TcState &si, const TcState &so, int mu, const 
     int64_t grid = 2 * (a.pairs < num_sms() / 2 ? a.pairs : num_sms() / 2);
     // output map of the pair kernel's TMA stores (row tiles of at most 64): boxes of 32 points x 16
     // outputs per (plane, piece)
-    CUtensorMap my;
+    CUtensorMap &my = L->my;
     std::memset(&my, 0, sizeof my);
     const int ch = a.it > 64 ? 2 : 1;
     if (pair && ch == 1) {
@@ -2051,19 +2117,37 @@ cudaError_t tc_mode_product(const TcState &si, const TcState &so, int mu, const 
     }
     const int smem = pair ? pair_stages(ch) * a.stage_bytes + pair_staging_bytes(ch) + 1024 + 256
                           : kStages * a.stage_bytes + 1024 + 256;
-    if (pair) {
-        if (fx) return dispatch_np<3, true, true>(km, epi.kind, mx, me, my, a, int(grid), smem, s);
-        switch (NP) {
-        case 3: return dispatch_np<3, false, true>(km, epi.kind, mx, me, my, a, int(grid), smem, s);
-        case 2: return dispatch_np<2, false, true>(km, epi.kind, mx, me, my, a, int(grid), smem, s);
-        default: return dispatch_np<1, false, true>(km, epi.kind, mx, me, my, a, int(grid), smem, s);
+    L->km = km;
+    L->pair = pair;
+    L->fx = fx;
+    L->np = NP;
+    L->grid = int(grid);
+    L->smem = smem;
+    return cudaSuccess;
+}
+
+cudaError_t tc_mode_product(const TcState &si, const TcState &so, int mu, const TcMatrix &M, mm_prec prec,
+                            const void *in_pieces, void *out_pieces, const TcEpilogue &epi, const TcScales &sc,
+                            int *d_err, cudaStream_t s, TcVariant variant)
+{
+    TcLaunch L;
+    cudaError_t e = tc_setup(si, so, mu, M, prec, in_pieces, out_pieces, epi, sc, d_err, variant, &L);
+    if (e != cudaSuccess) return e;
+    const TcArgs &a = L.a;
+    const int kind = epi.kind;
+    if (L.pair) {
+        if (L.fx) return dispatch_np<3, true, true>(L.km, kind, L.mx, L.me, L.my, a, L.grid, L.smem, s);
+        switch (L.np) {
+        case 3: return dispatch_np<3, false, true>(L.km, kind, L.mx, L.me, L.my, a, L.grid, L.smem, s);
+        case 2: return dispatch_np<2, false, true>(L.km, kind, L.mx, L.me, L.my, a, L.grid, L.smem, s);
+        default: return dispatch_np<1, false, true>(L.km, kind, L.mx, L.me, L.my, a, L.grid, L.smem, s);
         }
     }
-    if (fx) return dispatch_np<3, true, false>(km, epi.kind, mx, me, my, a, int(grid), smem, s);
-    switch (NP) {
-    case 3: return dispatch_np<3, false, false>(km, epi.kind, mx, me, my, a, int(grid), smem, s);
-    case 2: return dispatch_np<2, false, false>(km, epi.kind, mx, me, my, a, int(grid), smem, s);
-    default: return dispatch_np<1, false, false>(km, epi.kind, mx, me, my, a, int(grid), smem, s);
+    if (L.fx) return dispatch_np<3, true, false>(L.km, kind, L.mx, L.me, L.my, a, L.grid, L.smem, s);
+    switch (L.np) {
+    case 3: return dispatch_np<3, false, false>(L.km, kind, L.mx, L.me, L.my, a, L.grid, L.smem, s);
+    case 2: return dispatch_np<2, false, false>(L.km, kind, L.mx, L.me, L.my, a, L.grid, L.smem, s);
+    default: return dispatch_np<1, false, false>(L.km, kind, L.mx, L.me, L.my, a, L.grid, L.smem, s);
     }
 }
 
@@ -2199,6 +2283,97 @@ cudaError_t tc_mode_product_batched(const TcProblem *host_probs, const TcProblem
 
 // Tensor-core flops one product issues: every MMA counted as 2 M N K, per
 // work item its k-block band times the products of the precision.
+// ---- batched CTA-pair launches ---------------------------------------------------
+
+size_t tc_pair_record_bytes() { return sizeof(TcPairProblem); }
+
+cudaError_t tc_pair_record_build(const TcState &si, const TcState &so, int mu, const TcMatrix &M, mm_prec prec,
+                                 const void *in_pieces, void *out_pieces, const TcScales &sc, void *rec, bool *kmajor,
+                                 int64_t *items)
+{
+    TcLaunch L;
+    cudaError_t e = tc_setup(si, so, mu, M, prec, in_pieces, out_pieces, TcEpilogue{}, sc, nullptr, kTcPair64, &L);
+    if (e != cudaSuccess) return e;
+    if (!L.pair || L.a.it > 64) return cudaErrorNotSupported;  // the batched pair kernel stores with TMA (CH = 1)
+    TcPairProblem r;
+    std::memset(&r, 0, sizeof r);
+    r.mapX = L.mx;
+    r.mapE = L.me;
+    r.mapY = L.my;
+    r.a = L.a;
+    r.pairs_begin = 0;
+    std::memcpy(rec, &r, sizeof r);
+    *kmajor = L.km;
+    *items = L.a.pairs;
+    return cudaSuccess;
+}
+
+void tc_pair_record_set_begin(void *rec, int64_t begin)
+{
+    reinterpret_cast<TcPairProblem *>(rec)->pairs_begin = begin;
+}
+
+bool tc_pair_batch_compatible(const void *host_recs, int nprob)
+{
+    const auto *h = reinterpret_cast<const TcPairProblem *>(host_recs);
+    for (int q = 1; q < nprob; ++q)
+        if (h[q].a.it != h[0].a.it || h[q].a.stage_bytes != h[0].a.stage_bytes) return false;
+    return nprob >= 1;
+}
+
+// The records must agree on what the kernel's launch arguments fix: the row
+// tile size (stage layout) and the input layout.
+cudaError_t tc_pair_batch_launch(const void *host_recs, const void *dev_recs, int nprob, bool kmajor, mm_prec prec,
+                                 int *d_err, cudaStream_t s)
+{
+    const auto *h = reinterpret_cast<const TcPairProblem *>(host_recs);
+    if (nprob < 1) return cudaErrorInvalidValue;
+    TcArgs a = h[0].a;
+    int64_t total = 0;
+    for (int q = 0; q < nprob; ++q) {
+        if (h[q].a.it != a.it || h[q].a.stage_bytes != a.stage_bytes || h[q].pairs_begin != total)
+            return cudaErrorInvalidValue;
+        total += h[q].a.pairs;
+    }
+    a.err = d_err;
+    const int NP = tc_pieces(prec);
+    const bool fx = tc_fixed(prec);
+    const int smem = pair_stages(1) * a.stage_bytes + pair_staging_bytes(1) + 1024 + 256;
+    const int64_t grid = 2 * (total < num_sms() / 2 ? total : num_sms() / 2);
+    const auto *dev = reinterpret_cast<const TcPairProblem *>(dev_recs);
+    auto go = [&](auto kern) -> cudaError_t {
+        cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
+        if (e != cudaSuccess) return e;
+        cudaLaunchConfig_t cfg = {};
+        cfg.gridDim = dim3(unsigned(grid));
+        cfg.blockDim = dim3(kThreads);
+        cfg.dynamicSmemBytes = size_t(smem);
+        cfg.stream = s;
+        cudaLaunchAttribute attr[2];
+        attr[0].id = cudaLaunchAttributeClusterDimension;
+        attr[0].val.clusterDim.x = 2;
+        attr[0].val.clusterDim.y = 1;
+        attr[0].val.clusterDim.z = 1;
+        attr[1].id = cudaLaunchAttributeProgrammaticStreamSerialization;
+        attr[1].val.programmaticStreamSerializationAllowed = 1;
+        cfg.attrs = attr;
+        cfg.numAttrs = 2;
+        int active = 0;
+        if (cudaOccupancyMaxActiveClusters(&active, kern, &cfg) == cudaSuccess && active > 0 && 2 * active < grid)
+            cfg.gridDim = dim3(unsigned(2 * active));
+        e = cudaLaunchKernelEx(&cfg, kern, h[0].mapX, h[0].mapE, h[0].mapY, a, dev, nprob, total);
+        count_launch();
+        if (e != cudaSuccess) return e;
+        return cudaGetLastError();
+    };
+    if (fx) return kmajor ? go(tc_pair_kernel<3, true, 0, true, 1, true>) : go(tc_pair_kernel<3, false, 0, true, 1, true>);
+    switch (NP) {
+    case 3: return kmajor ? go(tc_pair_kernel<3, true, 0, false, 1, true>) : go(tc_pair_kernel<3, false, 0, false, 1, true>);
+    case 2: return kmajor ? go(tc_pair_kernel<2, true, 0, false, 1, true>) : go(tc_pair_kernel<2, false, 0, false, 1, true>);
+    default: return kmajor ? go(tc_pair_kernel<1, true, 0, false, 1, true>) : go(tc_pair_kernel<1, false, 0, false, 1, true>);
+    }
+}
+
 double tc_issued_flops(const TcState &si, int mu, const TcMatrix &M, mm_prec prec, TcVariant variant)
 {
     const int NP = tc_pieces(prec);

@@ -674,6 +674,29 @@ def test_auto_precision_resolves(env):
         assert torch.equal(out[0], out[1]), concrete
 
 
+def test_batched_pair_kernel_matches_one_sm_batch(env, monkeypatch):
+    """Batched launches run the CTA-pair kernel over the problem records; the
+    older one-SM-style batched kernel (forced with MM_TC_1SM=1 at batch
+    creation) gives the same bits."""
+    mm, ctx, torch = env
+    dims = inputs.batched_dims(count=64, seed=3)[:6]
+    us0 = inputs.batched_u0(inputs.batched_dims(count=64, seed=3), seed=3)[:6]
+    tau, steps = 1e-4, 3
+    plans, a, b = [], [], []
+    for (n1, n2, n3), u0 in zip(dims, us0):
+        nd = (int(n1), int(n2), int(n3))
+        plans.append(mm.TuckerPlan(ctx, nd, [fd_schrodinger_E(mm, n, tau) for n in nd], prec="f16x6"))
+        a.append(to_gpu(torch, u0.astype(np.complex64), torch.complex64))
+        b.append(to_gpu(torch, u0.astype(np.complex64), torch.complex64))
+    mm.Batch(ctx, plans).step(a, steps)
+    monkeypatch.setenv("MM_TC_1SM", "1")
+    mm.Batch(ctx, plans).step(b, steps)
+    monkeypatch.delenv("MM_TC_1SM")
+    torch.cuda.synchronize()
+    for k in range(len(plans)):
+        assert torch.equal(a[k], b[k]), k
+
+
 def test_step_batched_one_call(env):
     """mumode_step_batched (the batch made and released in the call) equals
     a kept batch object."""
