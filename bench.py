@@ -541,6 +541,7 @@ def other_workload(args):
         x, W = plan.nodes(1)
         psi0 = torch.from_numpy(inputs.gpe_psi0(x, W, seed=4).astype(np.complex64)).cuda()
         psi = psi0.clone()
+        line["kernel_variant"] = plan.gpe_autotune(psi, beta, tau, nsteps=5)[0]
         plan.gpe_step(psi, beta, tau, K)
         ms = _time(lambda: plan.gpe_step(psi, beta, tau, K), stream)
         gT = torch.randn_like(psi0)

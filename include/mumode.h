@@ -310,8 +310,9 @@ void mm_plan_destroy(mm_plan *plan);
  * plans: 0 = CTA pair with row tiles of at most 64, 1 = CTA pair with row
  * tiles of at most 128, 2 = one SM) and, for Tucker plans with d <= 4,
  * every mode order, nsteps steps each (1..1000, after one warm step) on a
- * scratch copy of u_dev (which is left unchanged), and keeps the fastest
- * in the plan.  Hermite plans time harmonic-oscillator steps and keep their
+ * scratch copy of u_dev (which is left unchanged), in two passes whose
+ * faster time counts (the first pass also brings an idle GPU to its
+ * clocks), and keeps the fastest in the plan.  Hermite plans time harmonic-oscillator steps and keep their
  * mode order.  Allocates a state-sized scratch for the call.  Errors:
  * MM_ERR_INVALID_ARG, MM_ERR_OOM, and those of the timed steps (the plan's
  * configuration is then unchanged). */
@@ -478,6 +479,12 @@ mm_status split_step_gpe(mm_plan *plan, void *psi_dev, double beta, double tau, 
 mm_status split_step_gpe_adjoint(mm_plan *plan, const void *psi0_dev, const void *gT_dev, void *g0_dev,
                                  double beta, double tau, int64_t nsteps, int64_t ckpt_every,
                                  void *stream);
+
+/* The autotuner (mm_plan_autotune) timing GPE steps with this beta and tau
+ * instead of harmonic-oscillator steps: the nonlinear epilogue changes
+ * which kernel variant is fastest.  Same arguments and errors otherwise. */
+mm_status split_step_gpe_autotune(mm_plan *plan, const void *psi_dev, double beta, double tau, int64_t nsteps,
+                                  void *stream);
 
 /* FP64 sum of |u|^2 (times w_l = W_l1 W_l2 W_l3 for a Hermite plan when
  * weighted != 0) over the plan's tensor; the result is written to

@@ -568,7 +568,11 @@ mm_status mm_plan_set_config(mm_plan *p, int variant, const int *order)
     return MM_OK;
 }
 
-mm_status mm_plan_autotune(mm_plan *p, const void *u_dev, int64_t nsteps, void *stream)
+// The tuner's loop; step(scratch, k) runs k steps of the kind being tuned on the scratch copy.
+extern "C++" {
+template <typename Step>
+mm_status autotune_with(mm_plan *p, const void *u_dev, int64_t nsteps, void *stream, bool orders_too,
+                               Step step)
 {
     if (!p) return fail(MM_ERR_INVALID_ARG, "plan is NULL");
     mm_status st = check_ptr(u_dev, "u_dev");
@@ -584,7 +588,7 @@ mm_status mm_plan_autotune(mm_plan *p, const void *u_dev, int64_t nsteps, void *
     else variants = {int(p->variant)};
     std::vector<std::vector<int>> orders;
     std::vector<int> ord(p->order, p->order + p->d);
-    if (!p->hermite && p->d <= 4) {
+    if (orders_too && !p->hermite && p->d <= 4) {
         std::vector<int> o(size_t(p->d));
         for (int v = 0; v < p->d; ++v) o[size_t(v)] = v + 1;
         do orders.push_back(o);
@@ -602,30 +606,36 @@ mm_status mm_plan_autotune(mm_plan *p, const void *u_dev, int64_t nsteps, void *
     float best = INFINITY;
     int best_v = int(v0);
     std::vector<int> best_o = ord;
-    auto run = [&](int64_t k) -> mm_status {
-        return p->hermite ? hermite_ho_step(p, scratch, 0.01, k, stream) : mumode_step(p, scratch, k, stream);
-    };
-    for (int v : variants)
-        for (const auto &o : orders) {
-            p->variant = mm::TcVariant(v);
-            for (int q = 0; q < p->d; ++q) p->order[q] = o[size_t(q)];
-            cudaError_t e = cudaMemcpyAsync(scratch, u_dev, bytes, cudaMemcpyDeviceToDevice, s);
-            if (e == cudaSuccess && !(st = run(1))) {
-                cudaEventRecord(e0, s);
-                st = run(nsteps);
-                cudaEventRecord(e1, s);
+    auto run = [&](int64_t k) -> mm_status { return step(scratch, k); };
+    // Two passes over the candidates, each keeping its faster time: the first pass also brings an
+    // idle GPU up to its clocks, which would otherwise penalise the candidates timed first.
+    std::vector<float> tbest(variants.size() * orders.size(), INFINITY);
+    for (int pass = 0; pass < 2 && !st; ++pass)
+        for (size_t iv = 0; iv < variants.size() && !st; ++iv)
+            for (size_t io = 0; io < orders.size(); ++io) {
+                const int v = variants[iv];
+                const auto &o = orders[io];
+                p->variant = mm::TcVariant(v);
+                for (int q = 0; q < p->d; ++q) p->order[q] = o[size_t(q)];
+                cudaError_t e = cudaMemcpyAsync(scratch, u_dev, bytes, cudaMemcpyDeviceToDevice, s);
+                if (e == cudaSuccess && !(st = run(1))) {
+                    cudaEventRecord(e0, s);
+                    st = run(nsteps);
+                    cudaEventRecord(e1, s);
+                }
+                if (e == cudaSuccess) e = cudaStreamSynchronize(s);
+                if (e != cudaSuccess && !st) st = cuda_fail(e, "autotune");
+                if (st) break;
+                float ms = 0.0f;
+                cudaEventElapsedTime(&ms, e0, e1);
+                float &tb = tbest[iv * orders.size() + io];
+                tb = std::min(tb, ms);
+                if (pass == 1 && tb < best) {
+                    best = tb;
+                    best_v = v;
+                    best_o = o;
+                }
             }
-            if (e == cudaSuccess) e = cudaStreamSynchronize(s);
-            if (e != cudaSuccess && !st) st = cuda_fail(e, "autotune");
-            if (st) break;
-            float ms = 0.0f;
-            cudaEventElapsedTime(&ms, e0, e1);
-            if (ms < best) {
-                best = ms;
-                best_v = v;
-                best_o = o;
-            }
-        }
     cudaEventDestroy(e0);
     cudaEventDestroy(e1);
     cudaFree(scratch);
@@ -634,6 +644,25 @@ mm_status mm_plan_autotune(mm_plan *p, const void *u_dev, int64_t nsteps, void *
     for (int q = 0; q < p->d; ++q) p->order[q] = keep[size_t(q)];
     p->use_graphs = graphs;
     return st;
+}
+
+}  // extern "C++"
+
+mm_status mm_plan_autotune(mm_plan *p, const void *u_dev, int64_t nsteps, void *stream)
+{
+    if (!p) return fail(MM_ERR_INVALID_ARG, "plan is NULL");
+    return autotune_with(p, u_dev, nsteps, stream, true, [&](void *u, int64_t k) {
+        return p->hermite ? hermite_ho_step(p, u, 0.01, k, stream) : mumode_step(p, u, k, stream);
+    });
+}
+
+mm_status split_step_gpe_autotune(mm_plan *p, const void *psi_dev, double beta, double tau, int64_t nsteps,
+                                  void *stream)
+{
+    if (!p || !p->hermite) return fail(MM_ERR_INVALID_ARG, "not a Hermite plan");
+    if (!std::isfinite(beta) || !std::isfinite(tau)) return fail(MM_ERR_INVALID_ARG, "beta or tau is not finite");
+    return autotune_with(p, psi_dev, nsteps, stream, false,
+                         [&](void *u, int64_t k) { return split_step_gpe(p, u, beta, tau, k, stream); });
 }
 
 mm_status mm_plan_set_graphs(mm_plan *p, int enable)

@@ -53,6 +53,7 @@ SIGNATURES = {
     "mm_batch_destroy": (None, [_vp]),
     "mumode_step_batched": (_i, [_vp, ctypes.POINTER(_vp), ctypes.POINTER(_vp), _i, _i64, _vp]),
     "mm_plan_autotune": (_i, [_vp, _vp, _i64, _vp]),
+    "split_step_gpe_autotune": (_i, [_vp, _vp, ctypes.c_double, ctypes.c_double, _i64, _vp]),
     "mumode_batch_autotune": (_i, [_vp, ctypes.POINTER(_vp), ctypes.POINTER(_vp), _i, _i64, ctypes.POINTER(_i), _vp]),
     "mm_plan_get_config": (_i, [_vp, ctypes.POINTER(_i), ctypes.POINTER(_i)]),
     "mm_plan_set_config": (_i, [_vp, _i, ctypes.POINTER(_i)]),
@@ -587,6 +588,13 @@ class HermitePlan(_Tunable):
         _check(lib().split_step_gpe(self.handle, ctypes.c_void_p(psi.data_ptr()), float(beta), float(tau),
                                     int(nsteps), _stream(stream)))
         return psi
+
+    def gpe_autotune(self, psi, beta: float, tau: float, nsteps: int = 3, stream=None):
+        """split_step_gpe_autotune: the kernel variant timed on GPE steps (on a copy of psi)."""
+        _need_cuda(psi)
+        _check(lib().split_step_gpe_autotune(self.handle, ctypes.c_void_p(psi.data_ptr()), float(beta), float(tau),
+                                             int(nsteps), _stream(stream)))
+        return self.config()
 
     def gpe_adjoint(self, psi0, gT, beta: float, tau: float, nsteps: int, ckpt_every: int = 50, out=None,
                     stream=None):

@@ -780,6 +780,24 @@ def test_autotune_tucker(env, orc):
     ctx.status()
 
 
+def test_gpe_autotune(env, orc):
+    """split_step_gpe_autotune keeps psi, picks a variant, and the tuned plan
+    still matches the oracle's Strang steps."""
+    mm, ctx, torch = env
+    m, beta, tau, steps = 16, 100.0, 1e-3, 6
+    plan = mm.HermitePlan(ctx, [m] * 3, prec="f16x6")
+    xo, _, Wo = orc.gauss_hermite(m)
+    psi0 = inputs.gpe_psi0(xo, Wo, seed=4).astype(np.complex64)
+    psi = to_gpu(torch, psi0, torch.complex64)
+    before = psi.clone()
+    variant, _ = plan.gpe_autotune(psi, beta, tau, nsteps=2)
+    torch.cuda.synchronize()
+    assert torch.equal(psi, before) and variant in mm.VARIANTS
+    plan.gpe_step(psi, beta, tau, steps)
+    ref = orc.gpe_steps(psi0.astype(complex), xo, Wo, beta, tau, steps)
+    assert orc.rel_l2(psi.cpu().numpy(), ref, orc.weight3(Wo)) <= 1e-5
+
+
 def test_autotune_hermite_and_fp64(env):
     """Hermite plans tune the kernel variant only; FP64 plans the mode order."""
     mm, ctx, torch = env
