@@ -190,11 +190,12 @@ cudaError_t tc_mode_product(const TcState &st_in, const TcState &st_out, int mu,
                             const TcEpilogue &epi, const TcScales &sc, int *d_err, cudaStream_t s,
                             TcVariant variant = kTcPair64);
 // Batched launches of the CTA-pair kernel: one record per problem (opaque,
-// tc_pair_record_bytes() bytes, 64-byte aligned), built for one direction,
+// tc_pair_record_bytes() bytes, tc_pair_record_align() aligned), built for one direction,
 // with its first work item set by tc_pair_record_set_begin (records in order,
 // the first at 0).  cudaErrorNotSupported: the product has no pair tiling
 // with row tiles of at most 64 (use tc_mode_product_batched).
 size_t tc_pair_record_bytes();
+size_t tc_pair_record_align();
 cudaError_t tc_pair_record_build(const TcState &si, const TcState &so, int mu, const TcMatrix &M, mm_prec prec,
                                  const void *in_pieces, void *out_pieces, const TcScales &sc, void *rec, bool *kmajor,
                                  int64_t *items);

@@ -1354,8 +1354,13 @@ struct mm_batch {
     // the same for the CTA-pair kernel (records opaque, mm::tc_pair_record_bytes() each), used when
     // every problem has a pair tiling with row tiles of the same size
     bool pair = false;
-    std::vector<uint8_t> phost[mm::kMaxDims][kPhases];
+    std::vector<uint8_t> phost[mm::kMaxDims][kPhases];  // records start at recs(), aligned for their type
     void *pdev[mm::kMaxDims][kPhases] = {};
+    uint8_t *recs(int q, int ph)
+    {
+        const uintptr_t a = mm::tc_pair_record_align(), p = reinterpret_cast<uintptr_t>(phost[q][ph].data());
+        return reinterpret_cast<uint8_t *>((p + a - 1) / a * a);
+    }
 };
 
 // Pair-kernel records of all (position, phase) of a batch; false if some product has no such tiling.
@@ -1366,8 +1371,9 @@ static bool build_pair_records(mm_batch *b, mm_plan *const *plans, int nprob)
     const int d = b->d;
     for (int q = 0; q < d; ++q)
         for (int ph = 0; ph < mm_batch::kPhases; ++ph) {
-            auto &buf = b->phost[q][ph];
-            buf.assign(rb * size_t(nprob), 0);
+            auto &store = b->phost[q][ph];
+            store.assign(rb * size_t(nprob) + mm::tc_pair_record_align(), 0);
+            uint8_t *buf = b->recs(q, ph);
             const int cur = (ph * d + q) % 2;
             const int t = ph % 3;
             int64_t begin = 0;
@@ -1384,7 +1390,7 @@ static bool build_pair_records(mm_batch *b, mm_plan *const *plans, int nprob)
                 }
                 bool km = false;
                 int64_t items = 0;
-                void *rec = buf.data() + rb * size_t(k);
+                void *rec = buf + rb * size_t(k);
                 if (mm::tc_pair_record_build(p->st, p->st, mu, p->Etc[mu - 1], p->prec, p->work[cur], p->work[1 - cur],
                                              sc, rec, &km, &items) != cudaSuccess ||
                     km != b->kmajor[q])
@@ -1392,13 +1398,13 @@ static bool build_pair_records(mm_batch *b, mm_plan *const *plans, int nprob)
                 mm::tc_pair_record_set_begin(rec, begin);
                 begin += items;
             }
-            if (!mm::tc_pair_batch_compatible(buf.data(), nprob)) return false;
+            if (!mm::tc_pair_batch_compatible(buf, nprob)) return false;
         }
     for (int q = 0; q < d; ++q)
         for (int ph = 0; ph < mm_batch::kPhases; ++ph) {
-            const auto &buf = b->phost[q][ph];
-            if (cudaMalloc(&b->pdev[q][ph], buf.size()) != cudaSuccess ||
-                cudaMemcpy(b->pdev[q][ph], buf.data(), buf.size(), cudaMemcpyHostToDevice) != cudaSuccess)
+            const size_t bytes = rb * size_t(nprob);
+            if (cudaMalloc(&b->pdev[q][ph], bytes) != cudaSuccess ||
+                cudaMemcpy(b->pdev[q][ph], b->recs(q, ph), bytes, cudaMemcpyHostToDevice) != cudaSuccess)
                 return false;
         }
     return true;
@@ -1504,7 +1510,7 @@ extern "C" mm_status mumode_batch_step(mm_batch *b, void *const *u_dev, int64_t 
             const int ph = int(t % mm_batch::kPhases);
             cudaEvent_t ev0 = timing_event(b->ctx, true);
             if (ev0) cudaEventRecord(ev0, s);
-            cudaError_t e = b->pair ? mm::tc_pair_batch_launch(b->phost[q][ph].data(), b->pdev[q][ph],
+            cudaError_t e = b->pair ? mm::tc_pair_batch_launch(b->recs(q, ph), b->pdev[q][ph],
                                                                int(b->plans.size()), b->kmajor[q], b->prec,
                                                                b->ctx->d_err, s)
                                     : mm::tc_mode_product_batched(b->host[q][ph].data(), b->dev[q][ph],

@@ -647,8 +647,9 @@ __host__ __device__ constexpr int term_a(int t) { return t == 2 ? 1 : (t == 4 ? 
 __host__ __device__ constexpr int term_b(int t) { return t == 1 ? 1 : (t == 3 ? 2 : (t == 4 ? 1 : 0)); }
 
 // One problem of a batched CTA-pair launch: its tensor maps (read by TMA from
-// global memory), its kernel arguments and its first work item.
-struct alignas(64) TcPairProblem {
+// global memory; CUtensorMap carries the alignment TMA needs), its kernel
+// arguments and its first work item.
+struct TcPairProblem {
     CUtensorMap mapX, mapE, mapY;
     TcArgs a;
     int64_t pairs_begin;
@@ -2286,6 +2287,7 @@ cudaError_t tc_mode_product_batched(const TcProblem *host_probs, const TcProblem
 // ---- batched CTA-pair launches ---------------------------------------------------
 
 size_t tc_pair_record_bytes() { return sizeof(TcPairProblem); }
+size_t tc_pair_record_align() { return alignof(TcPairProblem); }
 
 cudaError_t tc_pair_record_build(const TcState &si, const TcState &so, int mu, const TcMatrix &M, mm_prec prec,
                                  const void *in_pieces, void *out_pieces, const TcScales &sc, void *rec, bool *kmajor,
