@@ -412,10 +412,12 @@ mm_status hermite_ho_step(mm_plan *plan, void *psi_dev, double tau, int64_t nste
  * whose direction-mu matrix is the values-space propagator
  *   M_mu = Psi_mu exp(-i tau H_mu) Phi_mu^W
  * (backward transform, exact flow in coefficient space, forward transform,
- * folded into one complex n_mu x n_mu matrix in FP64 on the host; exp by
- * mm_expm).  A step advances psi, given by its values on the tensor grid
- * of the Gauss-Hermite nodes (n[mu-1] nodes in direction mu, i_1 fastest),
- * by tau with no time-discretisation error.  V_nodes[mu-1] as above (NULL,
+ * folded into one complex n_mu x n_mu matrix in FP64; the Hamiltonian, the
+ * exponential (as mm_expm_device) and the foldings run on the GPU, which
+ * the call synchronises).  A step advances psi, given by its values on the
+ * tensor grid of the Gauss-Hermite nodes (n[mu-1] nodes in direction mu,
+ * i_1 fastest), by tau with no time-discretisation error.  V_nodes[mu-1]
+ * as above (NULL,
  * or V_nodes NULL, for harmonic directions).  dtype, prec and mode_order
  * as for mumode_plan_create (complex dtypes only; tensor-core precisions
  * need n_mu <= 256).  Errors: MM_ERR_SHAPE for n_mu outside 1..4096, those

@@ -196,10 +196,11 @@ cudaError_t expm_device(ExpmWorkspace *w, int n, const double *A, const double *
 // whose truncation errors are below 1/20! and 1/21!.  Each degree-9
 // polynomial in Y is evaluated by Paterson-Stockmeyer with Y^3 as the
 // Horner variable (2 products each, given Y, Y^2, Y^3), and the angle is
-// doubled s times by cos 2a = 2 cos^2 a - 1, sin 2a = 2 sin a cos a (2
-// products each).  All products are real (cuBLAS DGEMM, strided-batched
-// over the batch of f values): 8 + 2 s real products, against 10 + s
-// complex ones (40 + 4 s real) for the general series.
+// doubled s times by cos 2a = cos^2 a - sin^2 a, sin 2a = 2 sin a cos a (3
+// products each; errors then grow as in a complex squaring).  All products
+// are real (cuBLAS DGEMM, strided-batched over the batch of f values):
+// 8 + 3 s real products, against 10 + s complex ones (40 + 4 s real) for
+// the general series.
 
 namespace {
 
@@ -230,15 +231,13 @@ __global__ void combo_batch(int n, int count, double a0, double a1, double a2, d
     }
 }
 
-// C <- 2 C - I (after C = cos^2), S <- 2 S (after S = sin cos)
-__global__ void double_angle(int n, int count, double *C, double *S)
+// C <- cos^2 - sin^2, S <- 2 sin cos (from the three products)
+__global__ void double_angle(int64_t total, const double *CC, const double *SS, const double *SC, double *C, double *S)
 {
-    const int64_t nn = int64_t(n) * n, total = nn * count;
     for (int64_t q = blockIdx.x * int64_t(blockDim.x) + threadIdx.x; q < total;
          q += int64_t(gridDim.x) * blockDim.x) {
-        const int64_t e = q % nn;
-        C[q] = 2.0 * C[q] - (e / n == e % n ? 1.0 : 0.0);
-        S[q] = 2.0 * S[q];
+        C[q] = CC[q] - SS[q];
+        S[q] = 2.0 * SC[q];
     }
 }
 
@@ -365,18 +364,74 @@ cudaError_t expm_imag_batched(ExpmBatch *w, int n, const double *A, const double
     // and Y2 is not needed after it
     if ((e = poly(as, Y2)) != cudaSuccess) return e;
     if (gemm_batch(h, n, count, X, Y2, S, false) != CUBLAS_STATUS_SUCCESS) return cudaErrorUnknown;
+    // X, Y and Y3 are free now: products of the doublings
+    double *CC = X, *SS = Y, *SC = Y3;
     for (int k = 0; k < sq; ++k) {
-        // C' = 2 C C - I, S' = 2 S C
-        if (gemm_batch(h, n, count, C, C, T0, false) != CUBLAS_STATUS_SUCCESS ||
-            gemm_batch(h, n, count, S, C, T1, false) != CUBLAS_STATUS_SUCCESS)
+        // C' = C C - S S, S' = 2 S C (errors grow as in a complex squaring; the shorter
+        // C' = 2 C C - I assumes C C + S S = I and lets them grow twice as fast)
+        if (gemm_batch(h, n, count, C, C, CC, false) != CUBLAS_STATUS_SUCCESS ||
+            gemm_batch(h, n, count, S, S, SS, false) != CUBLAS_STATUS_SUCCESS ||
+            gemm_batch(h, n, count, S, C, SC, false) != CUBLAS_STATUS_SUCCESS)
             return cudaErrorUnknown;
-        std::swap(C, T0);
-        std::swap(S, T1);
-        double_angle<<<g, 256, 0, s>>>(n, count, C, S);
+        double_angle<<<g, 256, 0, s>>>(total, CC, SS, SC, C, S);
         count_launch();
     }
     interleave<<<g, 256, 0, s>>>(total, C, S, std::cos(wim * mu), std::sin(wim * mu), E);
     count_launch();
+    return cudaGetLastError();
+}
+
+// ---- HKP propagators on the device (section 4.3) --------------------------------------
+//
+// M = Psi exp(-i tau H) Phi^W for one direction: H = diag(k + 1/2) + P^T diag(g) P
+// with P[l][k] = phi_k(x_l) and g_l = W_l (V_l - x_l^2/2) (host-computed values),
+// the exponential by the cos / sin series, then two complex products.
+__global__ void add_half_diag(int n, double *H)
+{
+    for (int k = blockIdx.x * blockDim.x + threadIdx.x; k < n; k += gridDim.x * blockDim.x)
+        H[int64_t(k) * n + k] += k + 0.5;
+}
+__global__ void real_to_complex(int64_t total, const double *A, double2 *B)
+{
+    for (int64_t q = blockIdx.x * int64_t(blockDim.x) + threadIdx.x; q < total; q += int64_t(gridDim.x) * blockDim.x)
+        B[q] = make_double2(A[q], 0.0);
+}
+
+cudaError_t hkp_propagator_device(ExpmWorkspace *wz, ExpmBatch *wb, int m, const double *P_host, const double *GP_host,
+                                  const double *fwd_host, double tau, double2 *M, cudaStream_t s)
+{
+    if (wz->n < m || wb->n < m || wb->cap < 1) return cudaErrorInvalidValue;
+    cublasHandle_t h = static_cast<cublasHandle_t>(wz->blas);
+    if (cublasSetStream(h, s) != CUBLAS_STATUS_SUCCESS) return cudaErrorUnknown;
+    const size_t nn = size_t(m) * m;
+    // staging in the batch workspace (real); Psi and Phi^W go to the complex workspace before the
+    // exponential, which reuses every real buffer of the batch workspace
+    double *P = wb->buf[0], *GP = wb->buf[1], *H = wb->buf[2], *F = wb->buf[3];
+    double2 *Bc = wz->buf[0], *Fc = wz->buf[1], *E = wz->buf[4], *T = wz->buf[5];
+    cudaError_t e = cudaMemcpyAsync(P, P_host, sizeof(double) * nn, cudaMemcpyHostToDevice, s);
+    if (e == cudaSuccess && GP_host) e = cudaMemcpyAsync(GP, GP_host, sizeof(double) * nn, cudaMemcpyHostToDevice, s);
+    if (e == cudaSuccess) e = cudaMemcpyAsync(F, fwd_host, sizeof(double) * nn, cudaMemcpyHostToDevice, s);
+    if (e != cudaSuccess) return e;
+    // H = P^T (G P) (symmetric, so the column-major view of the product needs no transpose)
+    const double one = 1.0, zero = 0.0;
+    if (GP_host) {
+        if (cublasDgemm(h, CUBLAS_OP_N, CUBLAS_OP_T, m, m, m, &one, GP, m, P, m, &zero, H, m) != CUBLAS_STATUS_SUCCESS)
+            return cudaErrorUnknown;
+    } else if ((e = cudaMemsetAsync(H, 0, sizeof(double) * nn, s)) != cudaSuccess) {
+        return e;
+    }
+    add_half_diag<<<blocks_for(m), 256, 0, s>>>(m, H);
+    count_launch();
+    real_to_complex<<<blocks_for(int64_t(nn)), 256, 0, s>>>(int64_t(nn), P, Bc);
+    count_launch();
+    real_to_complex<<<blocks_for(int64_t(nn)), 256, 0, s>>>(int64_t(nn), F, Fc);
+    count_launch();
+    double nrm = 0.0;  // ||H||_1, read back once
+    if ((e = expm_norm1_device(wz, m, H, nullptr, 0.0, &nrm, s)) != cudaSuccess) return e;
+    if ((e = expm_imag_batched(wb, m, H, nullptr, &zero, 1, -tau, nrm, E, s)) != cudaSuccess) return e;
+    // M = Psi (E Phi^W), Psi = P
+    if (gemm(h, m, E, Fc, T, false) != CUBLAS_STATUS_SUCCESS || gemm(h, m, Bc, T, M, false) != CUBLAS_STATUS_SUCCESS)
+        return cudaErrorUnknown;
     return cudaGetLastError();
 }
 

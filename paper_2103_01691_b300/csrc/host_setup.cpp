@@ -287,41 +287,4 @@ void pipe_axial(int n, double zmax, double alpha, const double *s, double *A)
     }
 }
 
-// Values-space propagator of one direction over time tau (section 4.3):
-// M = Psi exp(-i tau H) Phi^W with Psi[l][k] = phi_k(x_l) and
-// Phi^W[k][l] = phi_k(x_l) W_l, so that a mu-mode product with M takes the
-// values at the nodes through the forward transform, the exact flow in
-// coefficient space and the backward transform at once.  M is m x m
-// complex, row-major.  Returns false if the exponential fails.
-bool hkp_propagator(int m, const double *V, double tau, cd *M)
-{
-    std::vector<double> x(m), W(m), fwd(size_t(m) * m), bwd(size_t(m) * m), H(size_t(m) * m);
-    gauss_hermite(m, x.data(), W.data());
-    hermite_matrices(m, x.data(), W.data(), fwd.data(), bwd.data());
-    std::vector<cd> E(size_t(m) * m, cd(0)), T(size_t(m) * m, cd(0));
-    if (V) {
-        hermite_hamiltonian(m, x.data(), W.data(), V, H.data());
-        if (!expm(m, H.data(), nullptr, cd(0.0, -tau), E.data())) return false;
-    } else {
-        for (int k = 0; k < m; ++k) E[size_t(k) * m + k] = std::polar(1.0, -tau * (k + 0.5));
-    }
-    for (int j = 0; j < m; ++j)  // T = E Phi^W
-        for (int k = 0; k < m; ++k) {
-            const cd e = E[size_t(j) * m + k];
-            if (e == cd(0)) continue;
-            const double *f = fwd.data() + size_t(k) * m;
-            cd *trow = T.data() + size_t(j) * m;
-            for (int l = 0; l < m; ++l) trow[l] += e * f[l];
-        }
-    std::fill(M, M + size_t(m) * m, cd(0));
-    for (int l = 0; l < m; ++l)  // M = Psi T
-        for (int j = 0; j < m; ++j) {
-            const double b = bwd[size_t(l) * m + j];
-            const cd *trow = T.data() + size_t(j) * m;
-            cd *mrow = M + size_t(l) * m;
-            for (int q = 0; q < m; ++q) mrow[q] += b * trow[q];
-        }
-    return true;
-}
-
 }  // namespace mm

@@ -19,7 +19,6 @@ bool gauss_hermite(int m, double *x, double *W);
 void hermite_matrices(int m, const double *x, const double *W, double *fwd, double *bwd);
 void hermite_hamiltonian(int m, const double *x, const double *W, const double *V, double *H);
 void hermite_galerkin(int m, const double *x, const double *W, const double *U, double *G);
-bool hkp_propagator(int m, const double *V, double tau, std::complex<double> *M);
 
 // ---- error reporting (mumode_api.cu) --------------------------------------
 mm_status fail(mm_status st, const char *fmt, ...);
@@ -137,6 +136,12 @@ int expm_batch_capacity(int n);  // batch entries that keep the workspace near 1
 // mu: a diagonal shift taken out as the phase exp(i w mu); norm_bound then bounds ||A + f_k B - mu I||_1.
 cudaError_t expm_imag_batched(ExpmBatch *w, int n, const double *A, const double *B, const double *f_host, int count,
                               double wim, double norm_bound, double2 *E, cudaStream_t s, double mu = 0.0);
+// HKP propagator of one direction on the device: M = Psi exp(-i tau H) Phi^W,
+// H = diag(k + 1/2) + P^T GP (GP = diag(g) P, NULL for the harmonic case),
+// P[l][k] = phi_k(x_l), fwd = Phi^W (host, m x m row-major).  Both workspaces
+// must hold m x m matrices; synchronises the stream once (norm of H).
+cudaError_t hkp_propagator_device(ExpmWorkspace *wz, ExpmBatch *wb, int m, const double *P_host, const double *GP_host,
+                                  const double *fwd_host, double tau, double2 *M, cudaStream_t s);
 // exp(z (A + f B)) for real z, Taylor series in real arithmetic; E complex with zero imaginary parts.
 cudaError_t expm_real_device(ExpmBatch *w, int n, const double *A, const double *B, double f, double z,
                              double norm_bound, double2 *E, cudaStream_t s);

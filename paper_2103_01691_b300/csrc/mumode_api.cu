@@ -806,16 +806,45 @@ mm_status hkp_plan_create(mm_ctx *ctx, int d, const int64_t *n, const double *co
     if (d < 1 || d > mm::kMaxDims) return fail(MM_ERR_SHAPE, "d = %d outside 1..%d", d, mm::kMaxDims);
     if (!std::isfinite(tau)) return fail(MM_ERR_INVALID_ARG, "tau is not finite");
     if (!is_complex(dtype)) return fail(MM_ERR_DTYPE, "HKP plans need complex data");
-    std::vector<std::vector<cd>> M(static_cast<size_t>(d));
-    std::vector<const double *> ptr(static_cast<size_t>(d), nullptr);
+    // the propagators Psi exp(-i tau H) Phi^W are built on the device (FP64: the Galerkin matrix
+    // and the two foldings as cuBLAS products, the exponential as in mm_expm_device), then split
+    // into the plan's form on the host like any Tucker matrix
+    int nmax = 0;
     for (int v = 0; v < d; ++v) {
         if (n[v] < 1 || n[v] > 4096) return fail(MM_ERR_SHAPE, "n[%d] = %lld outside 1..4096", v, (long long)n[v]);
+        nmax = std::max(nmax, int(n[v]));
+    }
+    cudaError_t e = mm::expm_workspace_init(&ctx->expm, nmax);
+    if (e == cudaSuccess) e = mm::expm_batch_init(&ctx->expmb, nmax, 1);
+    if (e != cudaSuccess) return fail(MM_ERR_OOM, "expm workspace (%s)", cudaGetErrorString(e));
+    double2 *Md = nullptr;
+    if (cudaMalloc(&Md, sizeof(double2) * size_t(nmax) * nmax) != cudaSuccess) return fail(MM_ERR_OOM, "HKP matrix");
+    std::vector<std::vector<cd>> M(static_cast<size_t>(d));
+    std::vector<const double *> ptr(static_cast<size_t>(d), nullptr);
+    mm_status st = MM_OK;
+    for (int v = 0; v < d && !st; ++v) {
         const int m = int(n[v]);
+        std::vector<double> x(m), W(m), fwd(size_t(m) * m), bwd(size_t(m) * m), GP;
+        mm::gauss_hermite(m, x.data(), W.data());
+        mm::hermite_matrices(m, x.data(), W.data(), fwd.data(), bwd.data());  // bwd[l][k] = phi_k(x_l)
+        const double *V = V_nodes ? V_nodes[v] : nullptr;
+        if (V) {
+            GP.resize(size_t(m) * m);
+            for (int l = 0; l < m; ++l) {
+                const double g = W[size_t(l)] * (V[l] - 0.5 * x[size_t(l)] * x[size_t(l)]);
+                for (int k = 0; k < m; ++k) GP[size_t(l) * m + k] = g * bwd[size_t(l) * m + k];
+            }
+        }
+        e = mm::hkp_propagator_device(&ctx->expm, &ctx->expmb, m, bwd.data(), V ? GP.data() : nullptr, fwd.data(), tau,
+                                      Md, nullptr);
         M[size_t(v)].resize(size_t(m) * m);
-        if (!mm::hkp_propagator(m, V_nodes ? V_nodes[v] : nullptr, tau, M[size_t(v)].data()))
-            return fail(MM_ERR_INVALID_ARG, "expm of direction %d failed", v + 1);
+        if (e == cudaSuccess)
+            e = cudaMemcpy(M[size_t(v)].data(), Md, sizeof(double2) * size_t(m) * m, cudaMemcpyDeviceToHost);
+        if (e != cudaSuccess) st = cuda_fail(e, "HKP propagator");
         ptr[size_t(v)] = reinterpret_cast<const double *>(M[size_t(v)].data());
     }
+    cudaFree(Md);
+    if (st) return st;
     return mumode_plan_create(ctx, d, n, ptr.data(), 1, dtype, prec, mode_order, out);
 }
 
