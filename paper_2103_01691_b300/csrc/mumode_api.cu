@@ -268,9 +268,12 @@ mm_status tc_sweep(mm_plan *p, mm::TcMatrix *const *M, int &cur, const mm::TcEpi
             // W[t+1][q] for sweep k+1.  That word was last read by launch (k-1, q), which has completed,
             // and the launch itself neither reads nor writes it, whatever d is (with two sets and
             // d = 1 it would be the word the launch reads).  tc_begin clears W[0][*] for sweep 0.
-            const int t = int(p->sweep % 3), d = p->d;
-            sc.s_in = p->d_scale + q;
-            sc.s_out = p->d_scale + (q + 1) % d;
+            const int t = int(p->sweep % 3), d = p->d, par = int(p->sweep & 1);
+            // state scales S[par][q] = d_scale[par d + q]: launch (k, q) reads S[k mod 2][q] and writes
+            // the next position's, S[k mod 2][q + 1] or, after the last position, S[k + 1 mod 2][0]
+            // (never the word it reads, also for d = 1)
+            sc.s_in = p->d_scale + par * d + q;
+            sc.s_out = (q + 1 < d) ? p->d_scale + par * d + q + 1 : p->d_scale + (1 - par) * d;
             sc.max_prev = p->d_max + ((t + 2) % 3) * d + q;
             sc.max_cur = p->d_max + t * d + q;
             sc.zero_next = p->d_max + ((t + 1) % 3) * d + q;
@@ -312,7 +315,9 @@ mm_status tc_begin(mm_plan *p, mm::TcMatrix *const *M, const void *u, cudaStream
 
 mm_status tc_end(mm_plan *p, int cur, void *u, cudaStream_t s)
 {
-    cudaError_t e = mm::tc_merge(p->st, p->npieces, p->fixed, p->work[cur], p->d_scale, u, s);
+    // the state's scale after p->sweep sweeps (see tc_sweep)
+    float *scale = p->d_scale ? p->d_scale + (p->sweep & 1) * p->d : nullptr;
+    cudaError_t e = mm::tc_merge(p->st, p->npieces, p->fixed, p->work[cur], scale, u, s);
     if (e != cudaSuccess) return cuda_fail(e, "merge");
     return MM_OK;
 }
@@ -357,7 +362,7 @@ mm_status alloc_workspace(mm_plan *p)
             if (e != cudaSuccess) return cuda_fail(e, "workspace memset");
         }
         if (p->fixed) {
-            e = cudaMalloc(&p->d_scale, sizeof(float) * p->d);
+            e = cudaMalloc(&p->d_scale, sizeof(float) * 2 * p->d);
             if (e == cudaSuccess) e = cudaMalloc(&p->d_max, sizeof(unsigned) * 3 * p->d);
             if (e == cudaSuccess) e = cudaMalloc(&p->d_work, sizeof(unsigned));
             if (e == cudaSuccess) e = cudaMemset(p->d_max, 0, sizeof(unsigned) * 3 * p->d);
@@ -1411,8 +1416,9 @@ static bool build_pair_records(mm_batch *b, mm_plan *const *plans, int nprob)
                 const int mu = p->order[q];
                 mm::TcScales sc;
                 if (p->fixed) {
-                    sc.s_in = p->d_scale + q;
-                    sc.s_out = p->d_scale + (q + 1) % d;
+                    const int par = ph & 1;  // sweep parity (kPhases is even)
+                    sc.s_in = p->d_scale + par * d + q;
+                    sc.s_out = (q + 1 < d) ? p->d_scale + par * d + q + 1 : p->d_scale + (1 - par) * d;
                     sc.max_prev = p->d_max + ((t + 2) % 3) * d + q;
                     sc.max_cur = p->d_max + t * d + q;
                     sc.zero_next = p->d_max + ((t + 1) % 3) * d + q;  // sweep k+1's word (see tc_sweep)
@@ -1475,8 +1481,9 @@ extern "C" mm_status mumode_batch_create(mm_ctx *ctx, mm_plan *const *plans, int
                 mm::TcScales sc;
                 unsigned *zero = nullptr;
                 if (p->fixed) {
-                    sc.s_in = p->d_scale + q;
-                    sc.s_out = p->d_scale + (q + 1) % d;
+                    const int par = ph & 1;  // sweep parity (kPhases is even)
+                    sc.s_in = p->d_scale + par * d + q;
+                    sc.s_out = (q + 1 < d) ? p->d_scale + par * d + q + 1 : p->d_scale + (1 - par) * d;
                     sc.max_prev = p->d_max + ((t + 2) % 3) * d + q;
                     sc.max_cur = p->d_max + t * d + q;
                     zero = p->d_max + ((t + 1) % 3) * d + q;  // sweep k+1's word (see tc_sweep)
@@ -1549,8 +1556,10 @@ extern "C" mm_status mumode_batch_step(mm_batch *b, void *const *u_dev, int64_t 
             if (e != cudaSuccess) return cuda_fail(e, "batched mode product");
         }
     const int cur = int((nsteps * d) % 2);
-    for (size_t k = 0; k < b->plans.size(); ++k)
+    for (size_t k = 0; k < b->plans.size(); ++k) {
+        b->plans[k]->sweep = nsteps;  // the batched launches ran nsteps sweeps of every plan
         if ((st = tc_end(b->plans[k], cur, u_dev[k], s))) return st;
+    }
     return MM_OK;
 }
 

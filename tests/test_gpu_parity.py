@@ -531,6 +531,24 @@ def test_pipe_flow_vs_oracle(env, orc, prec, n_r, n_z, T):
     assert err <= 1e-12
 
 
+@pytest.mark.parametrize("dims", [(200,), (72, 40)])
+def test_fixed_point_scale_changes_every_sweep(env, orc, dims):
+    """A growing flow (E = 2.5 x the Schroedinger propagator in every
+    direction) moves the fixed-point state scale to a new power of two at
+    every sweep; the result still matches the oracle (also for d = 1, where
+    one launch both reads the input scale and sets the output scale)."""
+    mm, ctx, torch = env
+    tau, steps = 1e-4, 7
+    Es = [2.5 * fd_schrodinger_E(mm, n, tau) for n in dims]
+    u0 = inputs.complex_normal(dims[::-1], seed=9).astype(np.complex64)
+    plan = mm.TuckerPlan(ctx, dims, Es, prec="f16x6")
+    u = to_gpu(torch, u0, torch.complex64)
+    plan.step(u, steps)
+    ref = orc.tucker(u0.astype(complex), [2.5 * orc.expm_dirichlet_fd(n, 1j * tau) for n in dims], nsteps=steps)
+    assert rel(u.cpu().numpy(), ref) <= TOL_MODE["f16x6"] * steps * len(dims) * 2
+    ctx.status()
+
+
 def test_fixed_point_wide_dynamic_range(env, orc):
     """F16x6 keeps a relative L2 accuracy when magnitudes span 1e-6 .. 1:
     the fixed-point leading piece is relative to the maximum, the FP16
