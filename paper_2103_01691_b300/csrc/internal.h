@@ -184,8 +184,13 @@ struct TcProblem {  // the CUtensorMap members carry the 64-byte alignment TMA n
 };
 
 struct TcEpilogue {
-    int kind = 0;      // 0: store pieces, 1: nonlinear phase then store pieces
+    int kind = 0;      // 0: store pieces, 1: nonlinear phase then store pieces, 2: point phase then store
     double tb = 0.0;   // tau * beta for kind 1
+    // kind 2 (CTA-pair kernel with row tiles of at most 64): every output at point (l, r) (the
+    // non-contracted index groups left and right of the direction) is multiplied by
+    // pl0[l % ldiv] pl1[l / ldiv] pr0[r % rdiv] pr1[r / rdiv] (device tables, null: factor 1)
+    const double2 *pl0 = nullptr, *pl1 = nullptr, *pr0 = nullptr, *pr1 = nullptr;
+    int64_t ldiv = 1, rdiv = 1;
 };
 // One mu-mode product on the split state: in (sizes st_in) -> out (sizes
 // st_out, equal except direction mu which becomes M.n_out).

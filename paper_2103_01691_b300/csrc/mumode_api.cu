@@ -77,6 +77,10 @@ struct mm_plan {
     double2 *Ebatch[mm::kMaxDims] = {};  // the exponentials of a chunk of steps (expmb.cap matrices)
     void *coef = nullptr;  // coefficient tensor of hkmp_evolve
     mm::ExpmBatch expmb;
+    // HKMP with one time-dependent direction and harmonic others: a step is that direction's
+    // product with the others' phases e^{-i tau (k + 1/2)} multiplied in its epilogue
+    int hk_fuse = -1;                           // the time-dependent direction (0-based), or -1
+    double2 *hk_phase[mm::kMaxDims] = {};       // per harmonic direction, padded length
     bool full_bands[mm::kMaxDims] = {};  // a device update switched direction v's bands to full
     // CUDA graphs of whole step sequences, keyed by (call, tensor, nsteps, stream, tau, beta)
     bool use_graphs = true;
@@ -293,6 +297,8 @@ mm_status tc_sweep(mm_plan *p, mm::TcMatrix *const *M, int &cur, const mm::TcEpi
 // Split the user's complex64 tensor into the plan's piece buffer 0.  The
 // fixed-point mode also sets the state scale and, for the first sweep, the
 // bounds max|u| * prod_{r<=q} ||E_{o_r}||_inf on each position's output.
+mm_status tc_begin_bounds(mm_plan *p, const double *bounds, const void *u, cudaStream_t s);
+
 mm_status tc_begin(mm_plan *p, mm::TcMatrix *const *M, const void *u, cudaStream_t s)
 {
     double bounds[mm::kMaxDims];
@@ -301,6 +307,12 @@ mm_status tc_begin(mm_plan *p, mm::TcMatrix *const *M, const void *u, cudaStream
         acc *= M[p->order[q] - 1]->row_norm;
         bounds[q] = acc;
     }
+    return tc_begin_bounds(p, bounds, u, s);
+}
+
+// tc_begin with the first sweep's bounds given: bounds[q] >= max|output of position q| / max|u|.
+mm_status tc_begin_bounds(mm_plan *p, const double *bounds, const void *u, cudaStream_t s)
+{
     p->sweep = 0;
     if (p->d_max) {  // the maximum words of sweep 0 (later sweeps' words are cleared by the launches)
         cudaError_t e0 = cudaMemsetAsync(p->d_max, 0, sizeof(unsigned) * p->d, s);
@@ -1041,6 +1053,8 @@ void mm_plan_destroy(mm_plan *p)
         if (p->Ebatch[v]) cudaFree(p->Ebatch[v]);
     }
     if (p->coef) cudaFree(p->coef);
+    for (int v = 0; v < mm::kMaxDims; ++v)
+        if (p->hk_phase[v]) cudaFree(p->hk_phase[v]);
     mm::expm_batch_destroy(&p->expmb);
     delete p;
 }
@@ -1817,6 +1831,38 @@ extern "C" mm_status hkmp_plan_create(mm_ctx *ctx, int d, const int64_t *n, cons
         }
         nmax = std::max(nmax, m);
     }
+    // fusion: tensor cores, the pair kernel's tilings, d <= 3, one time-dependent direction, the
+    // others harmonic (their exponentials are the diagonal phases)
+    {
+        int td = -1, ntd = 0;
+        bool others_harmonic = true;
+        for (int v = 0; v < d; ++v) {
+            if (p->H0dev[v]) {
+                td = v;
+                ++ntd;
+            } else if (V_nodes && V_nodes[v]) {
+                others_harmonic = false;
+            }
+        }
+        if (p->tc && d <= 3 && ntd == 1 && others_harmonic) {
+            p->hk_fuse = td;
+            for (int v = 0; v < d && p->hk_fuse >= 0; ++v) {
+                if (v == td) continue;
+                const int64_t np = (n[v] + 15) / 16 * 16;
+                std::vector<double2> ph(size_t(np), make_double2(1.0, 0.0));
+                for (int64_t k = 0; k < n[v]; ++k) {
+                    const double a = -tau * (double(k) + 0.5);
+                    ph[size_t(k)] = make_double2(std::cos(a), std::sin(a));
+                }
+                if (cudaMalloc(&p->hk_phase[v], sizeof(double2) * size_t(np)) != cudaSuccess ||
+                    cudaMemcpy(p->hk_phase[v], ph.data(), sizeof(double2) * size_t(np), cudaMemcpyHostToDevice) !=
+                        cudaSuccess) {
+                    mm_plan_destroy(p);
+                    return fail(MM_ERR_OOM, "HKMP phases");
+                }
+            }
+        }
+    }
     cudaError_t e = cudaMalloc(&p->coef, size_t(p->count) * elem_bytes(dtype));
     if (e == cudaSuccess && nmax > 0) {
         const int cap = mm::expm_batch_capacity(nmax);
@@ -1879,6 +1925,44 @@ extern "C" mm_status hkmp_evolve(mm_plan *p, void *psi, int64_t nsteps, const do
     int cur = 0;
     mm::TcMatrix *M[mm::kMaxDims];
     for (int v = 0; v < p->d; ++v) M[v] = &p->Etc[v];
+    const bool fused = p->hk_fuse >= 0 && p->variant == mm::kTcPair64;
+    mm::TcEpilogue epi2;  // fused: the other directions' phases at every output point
+    if (fused) {
+        const int v = p->hk_fuse, d = p->d;
+        const int64_t np[3] = {p->st.np[0], d > 1 ? p->st.np[1] : 1, d > 2 ? p->st.np[2] : 1};
+        epi2.kind = 2;
+        if (v == 0) {  // points: right index over directions 2, 3
+            epi2.pr0 = p->hk_phase[1];
+            epi2.pr1 = d > 2 ? p->hk_phase[2] : nullptr;
+            epi2.rdiv = np[1];
+        } else if (v == 1) {  // left: direction 1; right: direction 3
+            epi2.pl0 = p->hk_phase[0];
+            epi2.ldiv = np[0];
+            epi2.pr0 = d > 2 ? p->hk_phase[2] : nullptr;
+            epi2.rdiv = d > 2 ? np[2] : 1;
+        } else {  // left index over directions 1, 2
+            epi2.pl0 = p->hk_phase[0];
+            epi2.pl1 = p->hk_phase[1];
+            epi2.ldiv = np[0];
+        }
+    }
+    // one product per step (fused): a one-position sweep of direction hk_fuse + 1
+    auto fused_step = [&]() -> mm_status {
+        mm::TcScales sc;
+        const int t = int(p->sweep % 3), par = int(p->sweep & 1), d = p->d;
+        sc.s_in = p->d_scale + par * d;
+        sc.s_out = p->d_scale + (1 - par) * d;
+        sc.max_prev = p->d_max + ((t + 2) % 3) * d;
+        sc.max_cur = p->d_max + t * d;
+        sc.zero_next = p->d_max + ((t + 1) % 3) * d;
+        const int mu = p->hk_fuse + 1;
+        cudaError_t e = mm::tc_mode_product(p->st, p->st, mu, p->Etc[mu - 1], p->prec, p->work[cur], p->work[1 - cur],
+                                            epi2, sc, p->ctx->d_err, s, p->variant);
+        if (e != cudaSuccess) return cuda_fail(e, "HKMP fused product");
+        cur = 1 - cur;
+        ++p->sweep;
+        return MM_OK;
+    };
     for (int64_t k0 = 0; k0 < nsteps; k0 += cap) {
         const int cnt = int(std::min<int64_t>(cap, nsteps - k0));
         if ((st = chunk(k0, cnt))) return st;
@@ -1888,8 +1972,17 @@ extern "C" mm_status hkmp_evolve(mm_plan *p, void *psi, int64_t nsteps, const do
                 if ((st = simt_sweep(p, Ed, p->coef, s))) return st;
                 continue;
             }
-            if (k0 == 0 && q == 0 && (st = tc_begin(p, M, p->coef, s))) return st;
-            if ((st = tc_sweep(p, M, cur, mm::TcEpilogue{}, s))) return st;
+            if (k0 == 0 && q == 0) {
+                if (fused) {
+                    double b[mm::kMaxDims];  // one position per sweep: its product; the phases have modulus 1
+                    for (int v = 0; v < mm::kMaxDims; ++v) b[v] = p->Etc[p->hk_fuse].row_norm;
+                    st = tc_begin_bounds(p, b, p->coef, s);
+                } else {
+                    st = tc_begin(p, M, p->coef, s);
+                }
+                if (st) return st;
+            }
+            if ((st = fused ? fused_step() : tc_sweep(p, M, cur, mm::TcEpilogue{}, s))) return st;
         }
     }
     if (p->tc && (st = tc_end(p, cur, p->coef, s))) return st;

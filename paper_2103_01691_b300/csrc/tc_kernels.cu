@@ -634,6 +634,8 @@ struct TcArgs {
     int kb_lo[4], kb_hi[4];  // k-blocks where the row tile's matrix pieces are not all zero
     int stage_bytes, tx_bytes, e_offset;
     float tb;               // tau * beta for the nonlinear epilogue
+    const double2 *pl0, *pl1, *pr0, *pr1;  // point-phase epilogue (TcEpilogue kind 2)
+    int64_t ldiv, rdiv;
     uint16_t *out;
     int *err;
     // fixed-point mode
@@ -1057,6 +1059,31 @@ __device__ __forceinline__ void epi_frag_store(const TcArgs &a, const CUtensorMa
 #pragma unroll
             for (int s = 0; s < 2; ++s) valid[hh][s] = rr < a.right && l0 + 16 * hh + 8 * s + t4 < a.left;
     }
+    // point phases of this thread's four points (EPI 2), formed in FP64
+    float2 ph[2][2] = {{{1.0f, 0.0f}, {1.0f, 0.0f}}, {{1.0f, 0.0f}, {1.0f, 0.0f}}};
+    if (EPI == 2) {
+#pragma unroll
+        for (int hh = 0; hh < 2; ++hh)
+#pragma unroll
+            for (int s = 0; s < 2; ++s) {
+                if (!valid[hh][s]) continue;
+                const int64_t pidx = (KMAJOR ? rr : int64_t(l0)) + 16 * hh + 8 * s + t4;
+                const int64_t l = KMAJOR ? 0 : pidx, r = KMAJOR ? pidx : rr;
+                double fr = 1.0, fi = 0.0;
+                auto mul = [&](const double2 *tab, int64_t i) {
+                    if (!tab) return;
+                    const double2 z = tab[i];
+                    const double nr = fr * z.x - fi * z.y;
+                    fi = fr * z.y + fi * z.x;
+                    fr = nr;
+                };
+                mul(a.pl0, l % a.ldiv);
+                mul(a.pl1, l / a.ldiv);
+                mul(a.pr0, r % a.rdiv);
+                mul(a.pr1, r / a.rdiv);
+                ph[hh][s] = make_float2(float(fr), float(fi));
+            }
+    }
     // row scales of this thread's four outputs (pairs at 2 tc and 8 + 2 tc)
     float g[2][2] = {{1.0f, 1.0f}, {1.0f, 1.0f}};
     if (FX) {
@@ -1081,6 +1108,12 @@ __device__ __forceinline__ void epi_frag_store(const TcArgs &a, const CUtensorMa
                 float sn, cs;
                 sincosf(th, &sn, &cs);
                 const float yr = xr * cs + xi * sn, yi = xi * cs - xr * sn;
+                xr = yr;
+                xi = yi;
+            }
+            if (EPI == 2) {
+                const float2 f = ph[hh][(k >> 1) & 1];
+                const float yr = xr * f.x - xi * f.y, yi = xr * f.y + xi * f.x;
                 xr = yr;
                 xi = yi;
             }
@@ -1979,6 +2012,14 @@ template <int NP, bool FX, bool PAIR>
 static cudaError_t dispatch_np(bool km, int epi, const CUtensorMap &mx, const CUtensorMap &me, const CUtensorMap &my,
                                const TcArgs &a, int grid, int smem, cudaStream_t s)
 {
+    if (epi == 2) {  // the point-phase epilogue: CTA-pair kernel, row tiles of at most 64 (TMA stores)
+        if constexpr (PAIR && NP == 3 && FX) {
+            if (a.it > 64) return cudaErrorNotSupported;
+            return km ? launch_tc<NP, true, 2, FX, PAIR>(mx, me, my, a, grid, smem, s)
+                      : launch_tc<NP, false, 2, FX, PAIR>(mx, me, my, a, grid, smem, s);
+        }
+        return cudaErrorNotSupported;
+    }
     if (km)
         return epi ? launch_tc<NP, true, 1, FX, PAIR>(mx, me, my, a, grid, smem, s)
                    : launch_tc<NP, true, 0, FX, PAIR>(mx, me, my, a, grid, smem, s);
@@ -2033,6 +2074,12 @@ static cudaError_t tc_setup(const TcState &si, const TcState &so, int mu, const 
     a.tx_bytes = a.e_offset + NP * kBlocks * M.it * 32;
     a.stage_bytes = (a.tx_bytes + 1023) / 1024 * 1024;
     a.tb = float(epi.tb);
+    a.pl0 = epi.pl0;
+    a.pl1 = epi.pl1;
+    a.pr0 = epi.pr0;
+    a.pr1 = epi.pr1;
+    a.ldiv = epi.ldiv > 0 ? epi.ldiv : 1;
+    a.rdiv = epi.rdiv > 0 ? epi.rdiv : 1;
     a.out = (uint16_t *)out_pieces;
     a.err = d_err;
     a.rho = M.rho;

@@ -472,8 +472,9 @@ def _hkmp_case(orc, n):
     return xs, Ws
 
 
-@pytest.mark.parametrize("prec,tdir", [("f16x6", 3), ("f16x6", 1), ("fp64", 3), ("fp64dmma", 1)])
-def test_hkmp_vs_oracle(env, orc, prec, tdir):
+@pytest.mark.parametrize("prec,tdir,variant", [("f16x6", 3, None), ("f16x6", 1, None), ("f16x6", 2, None),
+                                               ("f16x6", 3, "one_sm"), ("fp64", 3, None), ("fp64dmma", 1, None)])
+def test_hkmp_vs_oracle(env, orc, prec, tdir, variant):
     """HKMP (the section 4.4 potential |x|^2/2 + x_3 sin^2 t, or with the
     time dependence moved to direction 1) against the oracle's literal
     Magnus steps: 12 steps of 0.05 on ragged sizes."""
@@ -481,8 +482,8 @@ def test_hkmp_vs_oracle(env, orc, prec, tdir):
     n = (72, 40, 48)
     xs, Ws = _hkmp_case(orc, n)
     Vs, Us = inputs.hkmp_potentials(*xs)
-    if tdir == 1:
-        Us = (np.array(xs[0]), None, None)
+    if tdir != 3:  # move the time dependence: U = x in direction tdir
+        Us = tuple(np.array(xs[v]) if v == tdir - 1 else None for v in range(3))
     tau, steps = 0.05, 12
     f_mid = inputs.hkmp_f_mid(tau, steps)
     f64 = prec in ("fp64", "fp64dmma")
@@ -491,14 +492,18 @@ def test_hkmp_vs_oracle(env, orc, prec, tdir):
     ref = orc.hkmp_steps(pin.astype(complex), xs, Ws, Vs, Us, tau, f_mid)
     xl = [mm.gauss_hermite(v)[0] for v in n]
     Vl, Ul = inputs.hkmp_potentials(*xl)
-    if tdir == 1:
-        Ul = (np.array(xl[0]), None, None)
-    plan = mm.HKMPPlan(ctx, n, [None, Vl[1], Vl[2]], list(Ul), tau, prec=prec)
+    if tdir != 3:
+        Ul = tuple(np.array(xl[v]) if v == tdir - 1 else None for v in range(3))
+    # harmonic directions passed as None: the tensor-core plan then fuses their phases into the
+    # time-dependent direction's product (one product per step); one_sm runs the three products
+    plan = mm.HKMPPlan(ctx, n, [None, None, None], list(Ul), tau, prec=prec)
+    if variant:
+        assert mm.lib().mm_plan_set_config(plan.handle, mm.VARIANTS.index(variant), None) == 0
     psi = to_gpu(torch, pin, torch.complex128 if f64 else torch.complex64)
     plan.evolve(psi, f_mid)
     w3 = Ws[2][:, None, None] * Ws[1][None, :, None] * Ws[0][None, None, :]
     err = orc.rel_l2(psi.cpu().numpy(), ref, w3)
-    print(f"HKMP {prec} dir {tdir} n={n} steps={steps} rel_err={err:.3e}")
+    print(f"HKMP {prec} dir {tdir} {variant or 'default'} n={n} steps={steps} rel_err={err:.3e}")
     assert err <= (1e-12 if f64 else 5e-6)
     ctx.status()
 
