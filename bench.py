@@ -117,6 +117,18 @@ def max_over_ranks(value: float, dist) -> float:
     return float(t.item())
 
 
+def deal_by_cost(costs, world: int):
+    """Independent problems dealt to ranks by cost (greedy, largest first, to
+    the least loaded rank): a list of sorted problem indices per rank."""
+    load = [0.0] * world
+    out = [[] for _ in range(world)]
+    for i in sorted(range(len(costs)), key=lambda k: (-costs[k], k)):
+        r = min(range(world), key=lambda k: (load[k], k))
+        out[r].append(i)
+        load[r] += float(costs[i])
+    return [sorted(o) for o in out]
+
+
 def shard(count: int, rank: int, world: int) -> range:
     """Contiguous share of `count` independent units for `rank` (no collective needed)."""
     base, extra = divmod(count, world)
@@ -403,10 +415,24 @@ def other_workload(args):
     from paper_2103_01691_b300 import build as mmbuild
     from paper_2103_01691_b300 import inputs
 
-    mmbuild.build()
+    rank, world, local = dist_env()
+    if world > 1 and args.workload != "batched64":
+        # the other workloads are one tensor each: one rank runs them, the others have no work
+        if rank != 0:
+            return
+        world = 1
+    if rank == 0:
+        mmbuild.build()
+    dist = None
+    if world > 1:
+        import torch.distributed as dist
+
+        dist.init_process_group("nccl", device_id=torch.device("cuda", local))
+        dist.barrier()
+    torch.cuda.set_device(local)
     from paper_2103_01691_b300 import mumode as mm
 
-    ctx = mm.Context(0)
+    ctx = mm.Context(local)
     stream = torch.cuda.Stream()
     torch.cuda.set_stream(stream)
     line = {"workload": args.workload, "unit": "steps/s", "higher_is_better": True, "data": "synthetic"}
@@ -549,6 +575,33 @@ def other_workload(args):
         line.update(value=K / (ms / 1e3), steps=K, precision="f16x6",
                     adjoint_ms_per_step=ms_adj / 100,
                     config="GPE Strang, Hermite n=192^3 complex64, beta=100, tau=1e-3; adjoint 100 steps, ckpt 50")
+    elif world > 1:  # batched64 over several GPUs: the problems dealt by flop count, no exchange
+        dims_all = inputs.batched_dims(64, seed=3)
+        u0_all = inputs.batched_u0(dims_all, seed=3)
+        costs = [8.0 * float(np.prod(d)) * float(np.sum(d)) for d in dims_all]
+        mine = deal_by_cost(costs, world)[rank]
+        tau, K = 1e-4, 200
+        plans, us = [], []
+        for i in mine:
+            nd = tuple(int(v) for v in dims_all[i])
+            Es = [mm.expm(mm.fd_laplacian_dirichlet(v), 1j * tau) for v in nd]
+            plans.append(mm.TuckerPlan(ctx, nd, Es, prec="f16x6"))
+            us.append(torch.from_numpy(u0_all[i].astype(np.complex64)).cuda())
+        mm.batch_autotune(ctx, plans, us, nsteps=5)
+        batch = mm.Batch(ctx, plans)
+        batch.step(us, 5)
+        dist.barrier()
+        torch.cuda.synchronize()
+        ms = max_over_ranks(_time(lambda: batch.step(us, K), stream), dist)
+        dist.barrier()
+        if rank == 0:
+            line.update(value=K / (ms / 1e3), steps=K, precision="f16x6", problems=64, n_gpus=world,
+                        scaling="strong", parallelism=f"problems dealt by flop count over {world} GPUs",
+                        tflops_algorithmic=sum(costs) * K / (ms / 1e3) / 1e12,
+                        config="64 FD Schroedinger problems, sizes 48..160 per direction (seed 3), tau=1e-4")
+            print(json.dumps(line), flush=True)
+        dist.destroy_process_group()
+        return
     else:  # batched64
         dims = inputs.batched_dims(64, seed=3)
         u0s = inputs.batched_u0(dims, seed=3)
