@@ -98,7 +98,8 @@ def test_fp32_simt(env, orc):
 # ------------------------------------------------------------ tensor-core paths
 
 TC_DIMS = [(16, 16, 16), (32, 48, 16), (17, 33, 20), (64, 64, 64), (100, 37, 48), (128, 128, 64), (256, 16, 16),
-           (16, 256, 16), (16, 16, 256), (160, 48, 80), (9,), (40, 24), (241, 20, 16), (16, 20, 255)]
+           (16, 256, 16), (16, 16, 256), (160, 48, 80), (9,), (40, 24), (241, 20, 16), (16, 20, 255),
+           (20, 16, 24, 18), (9, 12, 7, 10, 8)]
 
 
 @pytest.mark.parametrize("dims", TC_DIMS)
