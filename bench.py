@@ -464,7 +464,7 @@ def other_workload(args):
     elif args.workload == "hkp":
         # section 4.3: V = cos(2 pi x_1) + x_2^2/2 + x_3^2/2, one step to T = 1
         _, tc_peak, _, _ = peaks()
-        for n in sizes or (127, 255):
+        for n in sizes or (127, 255, 511):
             x, _ = mm.gauss_hermite(n)
             Vs = list(inputs.hkp_potentials(x, x, x))
             psi0 = inputs.hkp_psi0(x, x, x)
@@ -491,14 +491,15 @@ def other_workload(args):
             line[f"n{n}"] = res
         line.update(value=1e3 / line[f"n{(sizes or (255,))[-1]}"]["f16x6"]["ms_per_step"], precision="f16x6",
                     paper_gpu_ms_per_step={"n127": {"single": 0.64, "double": 1.27},
-                                           "n255": {"single": 8.11, "double": 16.02}},
+                                           "n255": {"single": 8.11, "double": 16.02},
+                                           "n511": {"single": 119.46, "double": 219.13}},
                     config="HKP, V = cos(2 pi x1) + x2^2/2 + x3^2/2, Hermite n^3 complex, one step to T = 1; "
                            "value = steps/s at n = 255 (setup_ms: host FP64 Hamiltonian, expm and folding)")
     elif args.workload == "hkmp":
         # section 4.4: |x|^2/2 + x_3 sin^2 t, tau = 0.02, 50 Magnus steps to T = 1
         tau, K = 0.02, 50
         f_mid = inputs.hkmp_f_mid(tau, K)
-        for n in sizes or (127, 255):
+        for n in sizes or (127, 255, 511):
             x, _ = mm.gauss_hermite(n)
             Vs, Us = inputs.hkmp_potentials(x, x, x)
             psi0 = inputs.hkp_psi0(x, x, x)
@@ -527,10 +528,12 @@ def other_workload(args):
                     paper_gpu_ms_per_step={"n127": {"double": {"exp_int": 0.37, "mu_mode": 1.05},
                                                     "single": {"exp_int": 0.25, "mu_mode": 0.54}},
                                            "n255": {"double": {"exp_int": 0.66, "mu_mode": 13.79},
-                                                    "single": {"exp_int": 0.34, "mu_mode": 7.01}}},
+                                                    "single": {"exp_int": 0.34, "mu_mode": 7.01}},
+                                           "n511": {"double": {"exp_int": 2.38, "mu_mode": 213.21},
+                                                    "single": {"exp_int": 1.09, "mu_mode": 108.31}}},
                     config="HKMP, V = |x|^2/2 + x3 sin^2 t, Hermite n^3 complex, tau = 0.02, 50 steps to T = 1; "
-                           "value = steps/s at n = 255 (each step: FP64 device exp of direction 3, its split, "
-                           "three mode products; transforms once per call)")
+                           "value = steps/s at n = 255 (each step: FP64 device exp of direction 3, its split, one "
+                           "mode product with the harmonic directions' phases fused; transforms once per call)")
     elif args.workload == "pipe":
         # section 4.2: d = 2, n x n, one exact step to T = 4; the paper reports wall-clock seconds
         P = inputs.PIPE

@@ -94,7 +94,7 @@ typedef enum {
  *                    MM_PREC_FP64_SIMT.
  * MM_PREC_AUTO       chosen from the data type and sizes when the plan or
  *                    product is created: MM_C64 -> MM_PREC_F16X6 when every
- *                    n_mu (and m) is at most 256, else MM_PREC_FP32_SIMT;
+ *                    n_mu (and m) is at most 512, else MM_PREC_FP32_SIMT;
  *                    MM_R32 -> MM_PREC_FP32_SIMT; MM_R64, MM_C128 ->
  *                    MM_PREC_FP64_DMMA.
  * Not provided: split TF32 modes.  The tcgen05 FP32 accumulator truncates,
@@ -184,7 +184,7 @@ mm_status mm_hermite_matrices(int m, double *fwd, double *bwd);
  * m.  u_dev and s_dev must not overlap.  dtype / prec:
  *   MM_PREC_FP64_SIMT with MM_C128 (or MM_R64 if L is real),
  *   MM_PREC_FP32_SIMT with MM_C64 (or MM_R32 if L is real),
- *   MM_PREC_BF16* with MM_C64; tensor-core paths need n_mu, m <= 256.
+ *   MM_PREC_BF16* with MM_C64; tensor-core paths need n_mu, m <= 512.
  * The matrix is uploaded on every call (use a plan for repeated use);
  * the call allocates and frees its temporaries, so it synchronises the
  * stream before returning.
@@ -420,7 +420,7 @@ mm_status hermite_ho_step(mm_plan *plan, void *psi_dev, double tau, int64_t nste
  * as above (NULL,
  * or V_nodes NULL, for harmonic directions).  dtype, prec and mode_order
  * as for mumode_plan_create (complex dtypes only; tensor-core precisions
- * need n_mu <= 256).  Errors: MM_ERR_SHAPE for n_mu outside 1..4096, those
+ * need n_mu <= 512).  Errors: MM_ERR_SHAPE for n_mu outside 1..4096, those
  * of mumode_plan_create. */
 mm_status mm_hermite_hamiltonian(int m, const double *V_nodes, double *H_out);
 mm_status hkp_plan_create(mm_ctx *ctx, int d, const int64_t *n, const double *const *V_nodes, double tau,

@@ -68,13 +68,13 @@ struct TcMatrix {
         // in the 32-byte swizzled order the MMA reads from shared memory
         void *pieces = nullptr;
         int ni = 0, it = 0;  // row tiles, rows per tile (a multiple of 32)
-        int kb_lo[4] = {0, 0, 0, 0}, kb_hi[4] = {0, 0, 0, 0};  // per row tile, as kb_lo / kb_hi
+        int kb_lo[8] = {}, kb_hi[8] = {};  // per row tile (n_out <= 512: at most 8 tiles of 64)
     } pair[2];
     int npieces = 0;
     bool fixed = false;             // MM_PREC_F16X6 pieces
     float *rho = nullptr;           // fixed: power-of-two scale of each row (ni * it floats)
     double row_norm = 0.0;          // max_i sum_j |E_ij|, bounds the growth of one product
-    int kb_lo[2] = {0, 0}, kb_hi[2] = {0, 0};  // per row tile: k-blocks with a nonzero piece
+    int kb_lo[4] = {}, kb_hi[4] = {};  // per row tile (at most 4 of 128): k-blocks with a nonzero piece
 };
 
 // Device words that carry the state scale of MM_PREC_F16X6 through a sweep.
@@ -176,7 +176,7 @@ struct TcProblem {  // the CUtensorMap members carry the 64-byte alignment TMA n
     int64_t pairs_begin;    // first work item of this problem in a batched launch
     int64_t pairs;          // work items: (pair of point tiles, row tile)
     int it, ni, kblocks, tx_bytes;
-    int kb_lo[2], kb_hi[2];  // per row tile: k-blocks with a nonzero matrix piece
+    int kb_lo[4], kb_hi[4];  // per row tile: k-blocks with a nonzero matrix piece
     uint16_t *out;
     const float *rho;       // fixed-point row scales
     TcScales sc;

@@ -405,7 +405,7 @@ mm_status plan_common(mm_ctx *ctx, int d, const int64_t *n, mm_dtype dtype, mm_p
     mm_status st = check_dims(d, n);
     if (st) return st;
     bool fits = true;
-    for (int v = 0; v < d; ++v) fits = fits && n[v] <= 256;
+    for (int v = 0; v < d; ++v) fits = fits && n[v] <= 512;
     prec = resolve_prec(prec, dtype, fits);
     st = check_combo(dtype, prec, matrix_complex);
     if (st) return st;
@@ -415,7 +415,7 @@ mm_status plan_common(mm_ctx *ctx, int d, const int64_t *n, mm_dtype dtype, mm_p
             return fail(MM_ERR_UNSUPPORTED, "tensor-core precisions need an sm_103 device (have sm_%d%d)", ctx->sm_major,
                         ctx->sm_minor);
         for (int v = 0; v < d; ++v)
-            if (n[v] > 256) return fail(MM_ERR_SHAPE, "tensor-core path supports n_mu <= 256 (n[%d] = %lld)", v, (long long)n[v]);
+            if (n[v] > 512) return fail(MM_ERR_SHAPE, "tensor-core path supports n_mu <= 512 (n[%d] = %lld)", v, (long long)n[v]);
     }
     bool seen[mm::kMaxDims] = {};
     auto *p = new mm_plan;
@@ -875,7 +875,7 @@ mm_status mumode_product(mm_ctx *ctx, int d, const int64_t *n, int mu, const dou
     if (m < 1 || m > (int64_t(1) << 24)) return fail(MM_ERR_SHAPE, "m = %lld out of range", (long long)m);
     if (!L) return fail(MM_ERR_INVALID_ARG, "L is NULL");
     if ((st = check_ptr(u_dev, "u_dev")) || (st = check_ptr(s_dev, "s_dev"))) return st;
-    prec = resolve_prec(prec, dtype, n[mu - 1] <= 256 && m <= 256);
+    prec = resolve_prec(prec, dtype, n[mu - 1] <= 512 && m <= 512);
     if ((st = check_combo(dtype, prec, L_is_complex != 0))) return st;
     int64_t nout[mm::kMaxDims];
     int64_t cnt_in = 1, cnt_out = 1;
@@ -906,7 +906,7 @@ mm_status mumode_product(mm_ctx *ctx, int d, const int64_t *n, int mu, const dou
     }
     if (!(ctx->sm_major == 10 && ctx->sm_minor == 3))
         return fail(MM_ERR_UNSUPPORTED, "tensor-core precisions need an sm_103 device");
-    if (nmu > 256 || m > 256) return fail(MM_ERR_SHAPE, "tensor-core path supports n_mu, m <= 256");
+    if (nmu > 512 || m > 512) return fail(MM_ERR_SHAPE, "tensor-core path supports n_mu, m <= 512");
     const int NP = mm::tc_pieces(prec);
     const bool fixed = mm::tc_fixed(prec);
     std::vector<double> Lc = as_complex(L, m * nmu, L_is_complex != 0);

@@ -165,6 +165,7 @@ __host__ __device__ static void entry_pieces(double c, double s, double r, int n
 mm_status tc_matrix_host(const double *E, int64_t m, int64_t n, int npieces, bool fixed, TcMatrix *geom,
                          std::vector<uint16_t> &h, std::vector<float> &rho)
 {
+    if (m < 1 || n < 1 || m > 512 || n > 512) return fail(MM_ERR_SHAPE, "tensor-core matrices need sizes in 1..512");
     TcMatrix M;
     M.n_in = n;
     M.n_out = m;
@@ -631,7 +632,7 @@ struct TcArgs {
     int64_t pairs;          // work items of a CTA pair: (pair of point tiles, row tile)
     int64_t tiles;          // point tiles
     int it, ni, kblocks;
-    int kb_lo[4], kb_hi[4];  // k-blocks where the row tile's matrix pieces are not all zero
+    int kb_lo[8], kb_hi[8];  // k-blocks where the row tile's matrix pieces are not all zero
     int stage_bytes, tx_bytes, e_offset;
     float tb;               // tau * beta for the nonlinear epilogue
     const double2 *pl0, *pl1, *pr0, *pr1;  // point-phase epilogue (TcEpilogue kind 2)
@@ -2066,7 +2067,7 @@ static cudaError_t tc_setup(const TcState &si, const TcState &so, int mu, const 
     a.it = M.it;
     a.ni = M.ni;
     a.kblocks = int(a.kp / kBK);
-    for (int h = 0; h < 4; ++h) {
+    for (int h = 0; h < 8; ++h) {
         a.kb_lo[h] = h < M.ni ? M.kb_lo[h] : 0;
         a.kb_hi[h] = h < M.ni ? M.kb_hi[h] : 1;
     }
@@ -2119,7 +2120,7 @@ static cudaError_t tc_setup(const TcState &si, const TcState &so, int mu, const 
         // the pair kernel's row tiles
         a.it = PT->it;
         a.ni = PT->ni;
-        for (int h = 0; h < 4; ++h) {
+        for (int h = 0; h < 8; ++h) {
             a.kb_lo[h] = h < PT->ni ? PT->kb_lo[h] : 0;
             a.kb_hi[h] = h < PT->ni ? PT->kb_hi[h] : 1;
         }
@@ -2260,7 +2261,7 @@ cudaError_t tc_problem_build(const TcState &si, const TcState &so, int mu, const
     q.it = M.it;
     q.ni = M.ni;
     q.kblocks = int(kp / kBK);
-    for (int h = 0; h < 2; ++h) {
+    for (int h = 0; h < 4; ++h) {
         q.kb_lo[h] = h < M.ni ? M.kb_lo[h] : 0;
         q.kb_hi[h] = h < M.ni ? M.kb_hi[h] : 1;
     }

@@ -99,7 +99,7 @@ def test_fp32_simt(env, orc):
 
 TC_DIMS = [(16, 16, 16), (32, 48, 16), (17, 33, 20), (64, 64, 64), (100, 37, 48), (128, 128, 64), (256, 16, 16),
            (16, 256, 16), (16, 16, 256), (160, 48, 80), (9,), (40, 24), (241, 20, 16), (16, 20, 255),
-           (20, 16, 24, 18), (9, 12, 7, 10, 8)]
+           (20, 16, 24, 18), (9, 12, 7, 10, 8), (300, 20, 16), (16, 20, 511), (400, 33, 24)]
 
 
 @pytest.mark.parametrize("dims", TC_DIMS)
@@ -346,6 +346,23 @@ def test_hkp_kronecker_potential(env, orc, prec, tau, steps):
     assert err <= (1e-12 if f64 else 1e-6)
 
 
+def test_hkp_above_256(env, orc):
+    """HKP on the tensor cores with a direction of more than 256 nodes."""
+    mm, ctx, torch = env
+    n = (300, 24, 20)
+    xs, Ws = _hkp_nodes(orc, n)
+    psi0 = inputs.hkp_psi0(*xs).astype(np.complex64)
+    ref = orc.hkp_steps(psi0.astype(complex), xs, Ws, inputs.hkp_potentials(*xs), 1.0, 1)
+    xl = [mm.gauss_hermite(v)[0] for v in n]
+    plan = mm.HKPPlan(ctx, n, [inputs.hkp_potentials(*xl)[0], None, None], 1.0, prec="f16x6")
+    psi = to_gpu(torch, psi0, torch.complex64)
+    plan.step(psi, 1)
+    w3 = Ws[2][:, None, None] * Ws[1][None, :, None] * Ws[0][None, None, :]
+    err = orc.rel_l2(psi.cpu().numpy(), ref, w3)
+    print(f"HKP f16x6 n={n} rel_err={err:.3e}")
+    assert err <= 1e-6
+
+
 def test_hkp_hamiltonian_matches_oracle(env, orc):
     """mm_hermite_hamiltonian (library, FP64 host) equals the oracle's."""
     mm, ctx, torch = env
@@ -535,6 +552,41 @@ def test_pipe_flow_vs_oracle(env, orc, prec, n_r, n_z, T):
     err = rel(c.cpu().numpy(), ref)
     print(f"pipe {prec} n=({n_r},{n_z}) rel_err={err:.3e} max c(T)={ref.max():.4f}")
     assert err <= 1e-12
+
+
+def test_hkp_511_sampled(env, orc):
+    """The paper's largest HKP size, n = 511 per direction (133 M points, 6.4 GB
+    of split state), one step to T = 1 in F16x6: three full grid lines through
+    the packet and 40 bulk points against the oracle's Tucker operator with
+    each direction's transforms and exp(-i H) multiplied out."""
+    mm, ctx, torch = env
+    m = 511
+    x, _, W = orc.gauss_hermite(m)
+    V1 = inputs.hkp_potentials(x, x, x)[0]
+    psi0 = inputs.hkp_psi0(x, x, x).astype(np.complex64)
+    xl = mm.gauss_hermite(m)[0]
+    plan = mm.HKPPlan(ctx, (m, m, m), [inputs.hkp_potentials(xl, xl, xl)[0], None, None], 1.0, prec="f16x6")
+    psi = to_gpu(torch, psi0, torch.complex64)
+    del psi0
+    plan.step(psi, 1)
+    P = orc.hermite_functions(m, x)
+    M1 = P.T @ orc.expm_taylor(orc.hkp_hamiltonian(x, W, V1), -1j) @ (P * W[None, :])
+    M2 = P.T @ np.diag(np.exp(-1j * (np.arange(m) + 0.5))) @ (P * W[None, :])
+    rng = np.random.default_rng(23)
+    a = np.arange(m)
+    c = np.full(m, m // 2)
+    near = np.concatenate([np.stack([a, c + 7, c - 5], 1), np.stack([c - 3, a, c + 9], 1),
+                           np.stack([c + 6, c - 8, a], 1), m // 2 + rng.integers(-60, 61, size=(40, 3))])
+    # the oracle's entries from the initial datum (recomputed in FP64 from its complex64 values)
+    u0 = inputs.hkp_psi0(x, x, x).astype(np.complex64).astype(complex)
+    ref = orc.tucker3_entries(u0, M1, M2, M2, near)
+    del u0
+    ix = [torch.from_numpy(np.ascontiguousarray(near[:, k])).cuda() for k in (2, 1, 0)]
+    got = psi[ix[0], ix[1], ix[2]].cpu().numpy()
+    err = rel(got, ref)
+    print(f"HKP n=511 f16x6 sampled rel_err={err:.3e}")
+    assert err <= 1e-5
+    ctx.status()
 
 
 @pytest.mark.parametrize("dims", [(200,), (72, 40)])
