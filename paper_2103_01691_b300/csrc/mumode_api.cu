@@ -1925,7 +1925,7 @@ extern "C" mm_status hkmp_evolve(mm_plan *p, void *psi, int64_t nsteps, const do
     int cur = 0;
     mm::TcMatrix *M[mm::kMaxDims];
     for (int v = 0; v < p->d; ++v) M[v] = &p->Etc[v];
-    const bool fused = p->hk_fuse >= 0 && p->variant == mm::kTcPair64;
+    const bool fused = p->hk_fuse >= 0 && p->variant != mm::kTcOneSM;
     mm::TcEpilogue epi2;  // fused: the other directions' phases at every output point
     if (fused) {
         const int v = p->hk_fuse, d = p->d;

@@ -469,6 +469,21 @@ __device__ __forceinline__ void split_fx_scaled(float xs, uint16_t &b0, uint16_t
     b2 = __half_as_ushort(h2);
 }
 
+// split_fx_scaled of two values at once, the pieces packed as FP16 pairs (x in the low half):
+// the same roundings, with paired conversions.
+__device__ __forceinline__ void split_fx_pair(float x, float y, uint32_t &p0, uint32_t &p1, uint32_t &p2)
+{
+    const __half2 h0 = __floats2half2_rn(rintf(x), rintf(y));
+    const float2 f0 = __half22float2(h0);
+    const float rx = x - f0.x, ry = y - f0.y;
+    const __half2 h1 = __floats2half2_rn(rx, ry);
+    const float2 f1 = __half22float2(h1);
+    const __half2 h2 = __floats2half2_rn(rx - f1.x, ry - f1.y);
+    p0 = *reinterpret_cast<const uint32_t *>(&h0);
+    p1 = *reinterpret_cast<const uint32_t *>(&h1);
+    p2 = *reinterpret_cast<const uint32_t *>(&h2);
+}
+
 // Grid exponent for a tensor whose largest magnitude is m: s = 2^es with m / s < 1024.
 __device__ __forceinline__ int grid_exponent(float m)
 {
@@ -1159,29 +1174,33 @@ __device__ __forceinline__ void epi_frag_store(const TcArgs &a, const CUtensorMa
     }
 #pragma unroll
     for (int c = 0; c < 2; ++c) {
-        // pack the pieces of output pairs (2 tc, 2 tc + 1): pk[p][hh][j], matrix j = s + 2 cb
-        uint32_t pk[3][2][4];
-#pragma unroll
-        for (int hh = 0; hh < 2; ++hh)
-#pragma unroll
-            for (int j = 0; j < 4; ++j) {
-                uint16_t b0[3], b1[3];
-                const int k = 2 * j;  // values k, k + 1: s = j & 1, cb = j >> 1
-                pieces_of(c == 0 ? vr[hh][k] : vi[hh][k], b0);
-                pieces_of(c == 0 ? vr[hh][k + 1] : vi[hh][k + 1], b1);
-#pragma unroll
-                for (int p = 0; p < NP; ++p) pk[p][hh][j] = uint32_t(b0[p]) | (uint32_t(b1[p]) << 16);
-            }
         if (lane == 0) bulk_wait_read0();  // the previous boxes have left the staging buffer
         __syncwarp();
 #pragma unroll
-        for (int p = 0; p < NP; ++p)
+        for (int hh = 0; hh < 2; ++hh) {
+            // pack the pieces of output pairs (2 tc, 2 tc + 1): pk[p][j], matrix j = s + 2 cb
+            uint32_t pk[3][4];
 #pragma unroll
-            for (int hh = 0; hh < 2; ++hh) {
-                const uint32_t ad = sbase + uint32_t(p * kStageBoxBytes) + row_off[hh];
-                if (KMAJOR) stmatrix_x4(ad, pk[p][hh][0], pk[p][hh][1], pk[p][hh][2], pk[p][hh][3]);
-                else stmatrix_x4_trans(ad, pk[p][hh][0], pk[p][hh][1], pk[p][hh][2], pk[p][hh][3]);
+            for (int j = 0; j < 4; ++j) {
+                const int k = 2 * j;  // values k, k + 1: s = j & 1, cb = j >> 1
+                const float x0 = c == 0 ? vr[hh][k] : vi[hh][k], x1 = c == 0 ? vr[hh][k + 1] : vi[hh][k + 1];
+                if (FX) {
+                    split_fx_pair(x0, x1, pk[0][j], pk[1][j], pk[2][j]);
+                } else {
+                    uint16_t b0[3], b1[3];
+                    pieces_of(x0, b0);
+                    pieces_of(x1, b1);
+#pragma unroll
+                    for (int p = 0; p < NP; ++p) pk[p][j] = uint32_t(b0[p]) | (uint32_t(b1[p]) << 16);
+                }
             }
+#pragma unroll
+            for (int p = 0; p < NP; ++p) {
+                const uint32_t ad = sbase + uint32_t(p * kStageBoxBytes) + row_off[hh];
+                if (KMAJOR) stmatrix_x4(ad, pk[p][0], pk[p][1], pk[p][2], pk[p][3]);
+                else stmatrix_x4_trans(ad, pk[p][0], pk[p][1], pk[p][2], pk[p][3]);
+            }
+        }
         fence_proxy_async_smem();
         __syncwarp();
         if (lane == 0 && box_ok) {
@@ -1195,10 +1214,10 @@ __device__ __forceinline__ void epi_frag_store(const TcArgs &a, const CUtensorMa
     }
 }
 
-// Pipeline stages of the pair kernel: 5 of 33 KB for row tiles of 64 (with
-// 48 KB of output staging), 5 of 42 KB for row tiles of 128 (CH = 2).
-__host__ __device__ constexpr int pair_stages(int CH) { return CH == 2 ? 5 : 5; }
-__host__ __device__ constexpr int pair_staging_bytes(int CH) { return CH == 1 ? kEpiWarps * kStagingPerWarp : 0; }
+// Pipeline stages of the pair kernel: 5 of 33 KB for row tiles of 64, 4 of
+// 42 KB for row tiles of 128 (CH = 2); both with 48 KB of output staging.
+__host__ __device__ constexpr int pair_stages(int CH) { return CH == 2 ? 4 : 5; }
+__host__ __device__ constexpr int pair_staging_bytes(int) { return kEpiWarps * kStagingPerWarp; }
 
 // The same product with the tensor cores of the two SMs of a cluster
 // working as one (tcgen05 cta_group::2): the leader CTA (rank 0) issues
@@ -1232,7 +1251,7 @@ __global__ void __launch_bounds__(kThreads, 1)
     constexpr int kSt = pair_stages(CH);
     extern __shared__ __align__(1024) uint8_t smem_raw[];
     uint8_t *smem = reinterpret_cast<uint8_t *>((reinterpret_cast<uintptr_t>(smem_raw) + 1023) & ~uintptr_t(1023));
-    uint8_t *staging = smem + kSt * a.stage_bytes;  // CH == 1: kEpiWarps x kStagingPerWarp
+    uint8_t *staging = smem + kSt * a.stage_bytes;  // kEpiWarps x kStagingPerWarp
     uint64_t *full = reinterpret_cast<uint64_t *>(staging + pair_staging_bytes(CH));
     uint64_t *empty = full + kSt;
     uint64_t *accf = empty + kSt;  // [2]: accumulator set b holds a finished item
@@ -1263,7 +1282,7 @@ __global__ void __launch_bounds__(kThreads, 1)
         if (!BATCH) {
             tma_prefetch_desc(&mapX);
             tma_prefetch_desc(&mapE);
-            if (CH == 1) tma_prefetch_desc(&mapY);
+            tma_prefetch_desc(&mapY);
         }
     }
     if (warp == 1) {
@@ -1430,7 +1449,6 @@ __global__ void __launch_bounds__(kThreads, 1)
         const int ew = warp - 2;
         const int quarter = warp % 4;
         const int grp = ew / 4;  // the warp's chunks of 16 output rows: grp, grp + 4, ..
-        const uint32_t tbase = tmem + (uint32_t(quarter * 32) << 16);
         const int nchunks = a.it / 16;
         float s_in = 1.0f, inv_out = 1.0f, lim = 0.0f;
         int es_out = 0;
@@ -1468,75 +1486,48 @@ __global__ void __launch_bounds__(kThreads, 1)
                 0xffffffffu, !*abort_flag && mbar_wait(&accf[b], (lt / uint32_t(nsets)) & 1u, a.err, MM_ERR_TIMEOUT));
             if (!acc_ready) *abort_flag = 1;
             tc_fence_after();
-            const uint32_t tset = tbase + uint32_t(b * set_cols);
-            if constexpr (CH == 1) {
-                // drain in the matrix-fragment order, two 16-lane halves, leading + corrections
-                float vr[2][8], vi[2][8];
-                if (grp < nchunks) {
-                    const int i0 = grp * 16;
+            // drain in the matrix-fragment order: the warp's chunks of 16 output rows (grp, grp + 4 ..),
+            // each as two 16-lane halves, leading + corrections; tensor memory is released before
+            // the values are scaled, split and stored
+            float vr[CH][2][8], vi[CH][2][8];
+#pragma unroll
+            for (int q = 0; q < CH; ++q) {
+                const int ch = grp + 4 * q;
+                if (ch < nchunks) {
+                    const int i0 = ch * 16;
                     const int cre = i0 + (i0 >= half ? half : 0), cim = cre + half;
 #pragma unroll
                     for (int hh = 0; hh < 2; ++hh) {
                         const uint32_t ta = tmem + (uint32_t(quarter * 32 + hh * 16) << 16) + uint32_t(b * set_cols);
                         float t1[8];
-                        tmem_ld_frag16(ta + uint32_t(cre), vr[hh]);
+                        tmem_ld_frag16(ta + uint32_t(cre), vr[q][hh]);
                         if (NP > 1) tmem_ld_frag16(ta + uint32_t(acc_cols + cre), t1);
                         tmem_ld_wait();
                         if (NP > 1) {
 #pragma unroll
-                            for (int k = 0; k < 8; ++k) vr[hh][k] += t1[k];
+                            for (int k = 0; k < 8; ++k) vr[q][hh][k] += t1[k];
                         }
-                        tmem_ld_frag16(ta + uint32_t(cim), vi[hh]);
+                        tmem_ld_frag16(ta + uint32_t(cim), vi[q][hh]);
                         if (NP > 1) tmem_ld_frag16(ta + uint32_t(acc_cols + cim), t1);
                         tmem_ld_wait();
                         if (NP > 1) {
 #pragma unroll
-                            for (int k = 0; k < 8; ++k) vi[hh][k] += t1[k];
+                            for (int k = 0; k < 8; ++k) vi[q][hh][k] += t1[k];
                         }
                     }
                 }
-                tc_fence_before();
-                __syncwarp();
-                if (lane == 0) mbarrier_arrive(&tmem_empty[b]);
-                if (!acc_ready) break;
-                epi_frag_store<NP, KMAJOR, EPI, FX>(A, BATCH ? &pr->mapY : &mapY, staging + ew * kStagingPerWarp,
-                                                    vr, vi, tile, h, quarter, lane, grp, nchunks, s_in, inv_out,
-                                                    lim, local_max, range_ok);
-            } else {
-                // drain: the leading accumulator straight into v, the corrections added (no spills on this path)
-                float v[CH][32];
-#pragma unroll
-                for (int q = 0; q < CH; ++q) {
-                    const int ch = grp + 4 * q;
-                    if (ch < nchunks) {
-                        const int i0 = ch * 16;
-                        const int cre = i0 + (i0 >= half ? half : 0), cim = cre + half;
-                        float t1[16];
-                        tmem_ld16_to(tset + uint32_t(cre), &v[q][0]);
-                        if (NP > 1) tmem_ld16_to(tset + uint32_t(acc_cols + cre), t1);
-                        tmem_ld_wait();
-                        if (NP > 1) {
-#pragma unroll
-                            for (int k = 0; k < 16; ++k) v[q][k] += t1[k];
-                        }
-                        tmem_ld16_to(tset + uint32_t(cim), &v[q][16]);
-                        if (NP > 1) tmem_ld16_to(tset + uint32_t(acc_cols + cim), t1);
-                        tmem_ld_wait();
-                        if (NP > 1) {
-#pragma unroll
-                            for (int k = 0; k < 16; ++k) v[q][16 + k] += t1[k];
-                        }
-                    }
-                }
-                tc_fence_before();
-                __syncwarp();
-                if (lane == 0) mbarrier_arrive(&tmem_empty[b]);
-                if (!acc_ready) break;
-                epi_store<NP, KMAJOR, EPI, FX, CH>(A, v, tile, h, quarter * 32 + lane, grp, nchunks, s_in, inv_out,
-                                                   lim, local_max, range_ok);
             }
+            tc_fence_before();
+            __syncwarp();
+            if (lane == 0) mbarrier_arrive(&tmem_empty[b]);
+            if (!acc_ready) break;
+#pragma unroll
+            for (int q = 0; q < CH; ++q)
+                epi_frag_store<NP, KMAJOR, EPI, FX>(A, BATCH ? &pr->mapY : &mapY, staging + ew * kStagingPerWarp,
+                                                    vr[q], vi[q], tile, h, quarter, lane, grp + 4 * q, nchunks, s_in,
+                                                    inv_out, lim, local_max, range_ok);
         }
-        if (CH == 1 && lane == 0) bulk_wait0();  // this warp's stores are complete
+        if (lane == 0) bulk_wait0();  // this warp's stores are complete
         if (FX) {
             const unsigned m = __reduce_max_sync(0xffffffffu, __float_as_uint(local_max));
             if (lane == 0 && m && cur) atomicMax(cur->sc.max_cur, m);
@@ -2013,9 +2004,8 @@ template <int NP, bool FX, bool PAIR>
 static cudaError_t dispatch_np(bool km, int epi, const CUtensorMap &mx, const CUtensorMap &me, const CUtensorMap &my,
                                const TcArgs &a, int grid, int smem, cudaStream_t s)
 {
-    if (epi == 2) {  // the point-phase epilogue: CTA-pair kernel, row tiles of at most 64 (TMA stores)
+    if (epi == 2) {  // the point-phase epilogue: CTA-pair kernel only
         if constexpr (PAIR && NP == 3 && FX) {
-            if (a.it > 64) return cudaErrorNotSupported;
             return km ? launch_tc<NP, true, 2, FX, PAIR>(mx, me, my, a, grid, smem, s)
                       : launch_tc<NP, false, 2, FX, PAIR>(mx, me, my, a, grid, smem, s);
         }
@@ -2146,12 +2136,11 @@ static cudaError_t tc_setup(const TcState &si, const TcState &so, int mu, const 
     a.tiles = tiles;
     a.pairs = (tiles + 1) / 2 * a.ni;
     int64_t grid = 2 * (a.pairs < num_sms() / 2 ? a.pairs : num_sms() / 2);
-    // output map of the pair kernel's TMA stores (row tiles of at most 64): boxes of 32 points x 16
-    // outputs per (plane, piece)
+    // output map of the pair kernel's TMA stores: boxes of 32 points x 16 outputs per (plane, piece)
     CUtensorMap &my = L->my;
     std::memset(&my, 0, sizeof my);
     const int ch = a.it > 64 ? 2 : 1;
-    if (pair && ch == 1) {
+    if (pair) {
         if (km) {
             cuuint64_t dims[3] = {cuuint64_t(a.mp), cuuint64_t(a.right), cuuint64_t(2 * NP)};
             cuuint64_t str[2] = {cuuint64_t(a.mp * 2), cuuint64_t(so.plane * 2)};

@@ -255,12 +255,15 @@ def test_pair_kernel_matches_one_sm_kernel(env, monkeypatch, dims, prec, tile):
     assert np.array_equal(pair.view(np.uint32), one.view(np.uint32))
 
 
-def test_pair_kernel_gpe_epilogue(env, orc, monkeypatch):
+@pytest.mark.parametrize("m,tile", [(32, 64), (96, 128)])
+def test_pair_kernel_gpe_epilogue(env, orc, monkeypatch, m, tile):
     """The nonlinear-phase epilogue in the CTA-pair kernel (m = 32 quadrature
-    points: row tiles of 32): against the oracle and bit for bit against the
-    one-SM kernel."""
+    points: one row tile of 32; m = 96 with MM_PAIR_TILE=128: one row tile of
+    96, two chunks of 16 rows per epilogue warp): against the oracle and bit
+    for bit against the one-SM kernel."""
     mm, ctx, torch = env
-    m, beta, tau, steps = 32, 100.0, 1e-3, 6
+    monkeypatch.setenv("MM_PAIR_TILE", str(tile))
+    beta, tau, steps = 100.0, 1e-3, 6
     xo, _, Wo = orc.gauss_hermite(m)
     psi0 = inputs.gpe_psi0(xo, Wo, seed=4).astype(np.complex64)
 
@@ -491,7 +494,8 @@ def _hkmp_case(orc, n):
 
 
 @pytest.mark.parametrize("prec,tdir,variant", [("f16x6", 3, None), ("f16x6", 1, None), ("f16x6", 2, None),
-                                               ("f16x6", 3, "one_sm"), ("fp64", 3, None), ("fp64dmma", 1, None)])
+                                               ("f16x6", 3, "one_sm"), ("f16x6", 3, "pair128"),
+                                               ("f16x6", 1, "pair128"), ("fp64", 3, None), ("fp64dmma", 1, None)])
 def test_hkmp_vs_oracle(env, orc, prec, tdir, variant):
     """HKMP (the section 4.4 potential |x|^2/2 + x_3 sin^2 t, or with the
     time dependence moved to direction 1) against the oracle's literal
@@ -749,6 +753,25 @@ def test_auto_precision_resolves(env):
         torch.cuda.synchronize()
         assert torch.equal(out[0], out[1]), concrete
 
+
+
+def test_tensor_core_size_limit(env, orc):
+    """n_mu = 513 is past the tensor-core range (row tiles cover at most 512
+    rows): an explicit tensor-core precision is refused with MM_ERR_SHAPE
+    before any launch, and MM_PREC_AUTO falls back to FP32 on CUDA cores,
+    which still agrees with the oracle."""
+    mm, ctx, torch = env
+    dims, tau = (513, 3, 2), 1e-4
+    Es = [fd_schrodinger_E(mm, n, tau) for n in dims]
+    with pytest.raises(RuntimeError, match="512"):
+        mm.TuckerPlan(ctx, dims, Es, prec="f16x6")
+    u0 = inputs.complex_normal(dims[::-1], seed=2).astype(np.complex64)
+    plan = mm.TuckerPlan(ctx, dims, Es, prec="auto")
+    u = to_gpu(torch, u0, torch.complex64)
+    plan.step(u, 2)
+    ref = orc.tucker(u0.astype(complex), [orc.expm_dirichlet_fd(n, 1j * tau) for n in dims], nsteps=2)
+    assert rel(u.cpu().numpy(), ref) <= TOL_STEP["fp32"]
+    ctx.status()
 
 def test_batched_pair_kernel_matches_one_sm_batch(env, monkeypatch):
     """Batched launches run the CTA-pair kernel over the problem records; the
