@@ -218,6 +218,11 @@ def main():
                     choices=["free256", "heat32", "ho128", "batched64", "gpe192", "hkp", "hkmp", "pipe"],
                     help="free256 (default) is the headline line; the others time the remaining workloads")
     ap.add_argument("--sizes", default="", help="hkp / hkmp / pipe: comma-separated sizes n (default: the paper's)")
+    ap.add_argument("--no-autotune", action="store_true",
+                    help="ho128 / gpe192: keep the plan's default kernel variant and mode order")
+    ap.add_argument("--no-graphs", action="store_true",
+                    help="ho128 / gpe192: launch every product directly instead of replaying CUDA graphs "
+                         "(so that a profiler attributes each launch)")
     args = ap.parse_args()
     rank, world, local = dist_env()
     if args.workload != "free256":
@@ -448,14 +453,16 @@ def other_workload(args):
         line.update(value=K / (ms / 1e3), steps=K, precision="fp64", config="heat FD2 n=32^3 real, tau=1e-3")
     elif args.workload == "ho128":
         n, tau, K = 128, 0.01, 100
-        for prec in ("f16x6", "fp64", "fp64dmma"):
+        for prec in ("f16x6",) if args.no_fp64 else ("f16x6", "fp64", "fp64dmma"):
             plan = mm.HermitePlan(ctx, [n] * 3, prec=prec)
+            if args.no_graphs:
+                plan.set_graphs(False)
             x, W = plan.nodes(1)
             dt = torch.complex128 if prec.startswith("fp64") else torch.complex64
             psi = torch.from_numpy(inputs.harmonic_psi0(x, W, seed=1)).to(dt).cuda()
             k = K if not prec.startswith("fp64") else 2
             if not prec.startswith("fp64"):
-                line["kernel_variant"] = plan.autotune(psi, nsteps=5)[0]
+                line["kernel_variant"] = plan.config()[0] if args.no_autotune else plan.autotune(psi, nsteps=5)[0]
             plan.ho_step(psi, tau, k)
             ms = _time(lambda: plan.ho_step(psi, tau, k), stream)
             line[prec] = {"steps_per_s": k / (ms / 1e3), "steps": k}
@@ -567,10 +574,13 @@ def other_workload(args):
     elif args.workload == "gpe192":
         n, beta, tau, K = 192, 100.0, 1e-3, 500
         plan = mm.HermitePlan(ctx, [n] * 3, prec="f16x6")
+        if args.no_graphs:
+            plan.set_graphs(False)
         x, W = plan.nodes(1)
         psi0 = torch.from_numpy(inputs.gpe_psi0(x, W, seed=4).astype(np.complex64)).cuda()
         psi = psi0.clone()
-        line["kernel_variant"] = plan.gpe_autotune(psi, beta, tau, nsteps=5)[0]
+        line["kernel_variant"] = (plan.config()[0] if args.no_autotune
+                                  else plan.gpe_autotune(psi, beta, tau, nsteps=5)[0])
         plan.gpe_step(psi, beta, tau, K)
         ms = _time(lambda: plan.gpe_step(psi, beta, tau, K), stream)
         gT = torch.randn_like(psi0)

@@ -310,6 +310,9 @@ class _Tunable:
         _check(lib().mm_plan_get_config(self.handle, ctypes.byref(v), order))
         return VARIANTS[v.value], tuple(order)
 
+    def set_graphs(self, enable: bool):
+        _check(lib().mm_plan_set_graphs(self.handle, int(enable)))
+
     def set_config(self, variant: str, order=None):
         optr = (_i * len(order))(*order) if order is not None else None
         _check(lib().mm_plan_set_config(self.handle, VARIANTS.index(variant), optr))
@@ -350,9 +353,6 @@ class TuckerPlan(_Tunable):
         f = ctypes.c_double()
         _check(lib().mm_plan_issued_flops(self.handle, ctypes.byref(f)))
         return f.value
-
-    def set_graphs(self, enable: bool):
-        _check(lib().mm_plan_set_graphs(self.handle, int(enable)))
 
     def step(self, u, nsteps: int = 1, stream=None):
         _need_cuda(u)
