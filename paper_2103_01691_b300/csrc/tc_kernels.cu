@@ -1214,10 +1214,16 @@ __device__ __forceinline__ void epi_frag_store(const TcArgs &a, const CUtensorMa
     }
 }
 
-// Pipeline stages of the pair kernel: 5 of 33 KB for row tiles of 64, 4 of
-// 42 KB for row tiles of 128 (CH = 2); both with 48 KB of output staging.
-__host__ __device__ constexpr int pair_stages(int CH) { return CH == 2 ? 4 : 5; }
-__host__ __device__ constexpr int pair_staging_bytes(int) { return kEpiWarps * kStagingPerWarp; }
+// Epilogue warps of the pair kernel: 8 (two per tensor-memory lane quarter, two chunks of 16
+// output rows each) for row tiles of 64, which spreads their shared-memory traffic over the
+// item and leaves the MMA issue freer; 16 for row tiles of 128 and for the nonlinear-phase
+// epilogue (EPI 1), whose per-value arithmetic needs the extra warps.
+__host__ __device__ constexpr int pair_epi_warps(int CH, int EPI) { return CH == 1 && EPI != 1 ? 8 : 16; }
+__host__ __device__ constexpr int pair_threads(int CH, int EPI) { return 32 * (2 + pair_epi_warps(CH, EPI)); }
+// Pipeline stages: with row tiles of 64, 6 of 33 KB (8 epilogue warps, 24 KB of output staging)
+// or 5 (16 warps, 48 KB); with row tiles of 128, 4 of 42 KB (48 KB of staging).
+__host__ __device__ constexpr int pair_stages(int CH, int EPI) { return CH == 2 ? 4 : (pair_epi_warps(CH, EPI) == 8 ? 6 : 5); }
+__host__ __device__ constexpr int pair_staging_bytes(int CH, int EPI) { return pair_epi_warps(CH, EPI) * kStagingPerWarp; }
 
 // The same product with the tensor cores of the two SMs of a cluster
 // working as one (tcgen05 cta_group::2): the leader CTA (rank 0) issues
@@ -1240,7 +1246,7 @@ __host__ __device__ constexpr int pair_staging_bytes(int) { return kEpiWarps * k
 // the peer's warps arrive on their own barrier, which one thread of the
 // peer relays to the leader's.
 template <int NP, bool KMAJOR, int EPI, bool FX, int CH, bool BATCH>
-__global__ void __launch_bounds__(kThreads, 1)
+__global__ void __launch_bounds__(pair_threads(CH, EPI), 1)
     tc_pair_kernel(const __grid_constant__ CUtensorMap mapX, const __grid_constant__ CUtensorMap mapE,
                    const __grid_constant__ CUtensorMap mapY, TcArgs a, const TcPairProblem *__restrict__ many,
                    int nprob, int64_t total)
@@ -1248,11 +1254,11 @@ __global__ void __launch_bounds__(kThreads, 1)
     // BATCH: items P < total of many problems (records `many`, sorted by pairs_begin); `a` then
     // carries only what all problems share (row tiles of the same size, stage layout, error word)
     const int64_t items = BATCH ? total : a.pairs;
-    constexpr int kSt = pair_stages(CH);
+    constexpr int kSt = pair_stages(CH, EPI);
     extern __shared__ __align__(1024) uint8_t smem_raw[];
     uint8_t *smem = reinterpret_cast<uint8_t *>((reinterpret_cast<uintptr_t>(smem_raw) + 1023) & ~uintptr_t(1023));
-    uint8_t *staging = smem + kSt * a.stage_bytes;  // kEpiWarps x kStagingPerWarp
-    uint64_t *full = reinterpret_cast<uint64_t *>(staging + pair_staging_bytes(CH));
+    uint8_t *staging = smem + kSt * a.stage_bytes;  // pair_epi_warps(CH, EPI) x kStagingPerWarp
+    uint64_t *full = reinterpret_cast<uint64_t *>(staging + pair_staging_bytes(CH, EPI));
     uint64_t *empty = full + kSt;
     uint64_t *accf = empty + kSt;  // [2]: accumulator set b holds a finished item
     uint64_t *tmem_empty = accf + 2;       // [2]: accumulator set b has been drained
@@ -1275,7 +1281,7 @@ __global__ void __launch_bounds__(kThreads, 1)
         for (int b = 0; b < 2; ++b) {
             mbar_init(&accf[b], 1);
             // this CTA's epilogue warps, and in the leader the peer's relay
-            mbar_init(&tmem_empty[b], kEpiWarps + (rank == 0 ? 1 : 0));
+            mbar_init(&tmem_empty[b], pair_epi_warps(CH, EPI) + (rank == 0 ? 1 : 0));
         }
         *abort_flag = 0;
         mbar_fence_init();
@@ -1448,7 +1454,9 @@ __global__ void __launch_bounds__(kThreads, 1)
         // ---------------- epilogue warps (both CTAs) ----------------
         const int ew = warp - 2;
         const int quarter = warp % 4;
-        const int grp = ew / 4;  // the warp's chunks of 16 output rows: grp, grp + 4, ..
+        constexpr int kGroups = pair_epi_warps(CH, EPI) / 4;  // warps per lane quarter
+        constexpr int kPerWarp = 4 * CH / kGroups;       // chunks of 16 output rows per warp
+        const int grp = ew / 4;  // the warp's chunks: grp, grp + kGroups, ..
         const int nchunks = a.it / 16;
         float s_in = 1.0f, inv_out = 1.0f, lim = 0.0f;
         int es_out = 0;
@@ -1486,13 +1494,13 @@ __global__ void __launch_bounds__(kThreads, 1)
                 0xffffffffu, !*abort_flag && mbar_wait(&accf[b], (lt / uint32_t(nsets)) & 1u, a.err, MM_ERR_TIMEOUT));
             if (!acc_ready) *abort_flag = 1;
             tc_fence_after();
-            // drain in the matrix-fragment order: the warp's chunks of 16 output rows (grp, grp + 4 ..),
-            // each as two 16-lane halves, leading + corrections; tensor memory is released before
-            // the values are scaled, split and stored
-            float vr[CH][2][8], vi[CH][2][8];
+            // drain in the matrix-fragment order: the warp's chunks of 16 output rows
+            // (grp, grp + kGroups ..), each as two 16-lane halves, leading + corrections; tensor
+            // memory is released before the values are scaled, split and stored
+            float vr[kPerWarp][2][8], vi[kPerWarp][2][8];
 #pragma unroll
-            for (int q = 0; q < CH; ++q) {
-                const int ch = grp + 4 * q;
+            for (int q = 0; q < kPerWarp; ++q) {
+                const int ch = grp + kGroups * q;
                 if (ch < nchunks) {
                     const int i0 = ch * 16;
                     const int cre = i0 + (i0 >= half ? half : 0), cim = cre + half;
@@ -1522,10 +1530,10 @@ __global__ void __launch_bounds__(kThreads, 1)
             if (lane == 0) mbarrier_arrive(&tmem_empty[b]);
             if (!acc_ready) break;
 #pragma unroll
-            for (int q = 0; q < CH; ++q)
+            for (int q = 0; q < kPerWarp; ++q)
                 epi_frag_store<NP, KMAJOR, EPI, FX>(A, BATCH ? &pr->mapY : &mapY, staging + ew * kStagingPerWarp,
-                                                    vr[q], vi[q], tile, h, quarter, lane, grp + 4 * q, nchunks, s_in,
-                                                    inv_out, lim, local_max, range_ok);
+                                                    vr[q], vi[q], tile, h, quarter, lane, grp + kGroups * q, nchunks,
+                                                    s_in, inv_out, lim, local_max, range_ok);
         }
         if (lane == 0) bulk_wait0();  // this warp's stores are complete
         if (FX) {
@@ -1962,7 +1970,7 @@ static cudaError_t launch_tc(const CUtensorMap &mx, const CUtensorMap &me, const
 {
     cudaLaunchConfig_t cfg = {};
     cfg.gridDim = dim3(unsigned(grid));
-    cfg.blockDim = dim3(kThreads);
+    cfg.blockDim = dim3(PAIR ? pair_threads(a.it > 64 ? 2 : 1, EPI) : kThreads);
     cfg.dynamicSmemBytes = size_t(smem);
     cfg.stream = s;
     cudaLaunchAttribute attr[2];
@@ -2153,7 +2161,7 @@ static cudaError_t tc_setup(const TcState &si, const TcState &so, int mu, const 
             if (!encode(&my, out_pieces, 4, dims, str, box, CU_TENSOR_MAP_SWIZZLE_64B)) return cudaErrorInvalidValue;
         }
     }
-    const int smem = pair ? pair_stages(ch) * a.stage_bytes + pair_staging_bytes(ch) + 1024 + 256
+    const int smem = pair ? pair_stages(ch, epi.kind) * a.stage_bytes + pair_staging_bytes(ch, epi.kind) + 1024 + 256
                           : kStages * a.stage_bytes + 1024 + 256;
     L->km = km;
     L->pair = pair;
@@ -2377,7 +2385,7 @@ cudaError_t tc_pair_batch_launch(const void *host_recs, const void *dev_recs, in
     a.err = d_err;
     const int NP = tc_pieces(prec);
     const bool fx = tc_fixed(prec);
-    const int smem = pair_stages(1) * a.stage_bytes + pair_staging_bytes(1) + 1024 + 256;
+    const int smem = pair_stages(1, 0) * a.stage_bytes + pair_staging_bytes(1, 0) + 1024 + 256;
     const int64_t grid = 2 * (total < num_sms() / 2 ? total : num_sms() / 2);
     const auto *dev = reinterpret_cast<const TcPairProblem *>(dev_recs);
     auto go = [&](auto kern) -> cudaError_t {
@@ -2385,7 +2393,7 @@ cudaError_t tc_pair_batch_launch(const void *host_recs, const void *dev_recs, in
         if (e != cudaSuccess) return e;
         cudaLaunchConfig_t cfg = {};
         cfg.gridDim = dim3(unsigned(grid));
-        cfg.blockDim = dim3(kThreads);
+        cfg.blockDim = dim3(pair_threads(1, 0));
         cfg.dynamicSmemBytes = size_t(smem);
         cfg.stream = s;
         cudaLaunchAttribute attr[2];
