@@ -1220,9 +1220,20 @@ __device__ __forceinline__ void epi_frag_store(const TcArgs &a, const CUtensorMa
 // epilogue (EPI 1), whose per-value arithmetic needs the extra warps.
 __host__ __device__ constexpr int pair_epi_warps(int CH, int EPI) { return CH == 1 && EPI != 1 ? 8 : 16; }
 __host__ __device__ constexpr int pair_threads(int CH, int EPI) { return 32 * (2 + pair_epi_warps(CH, EPI)); }
-// Pipeline stages: with row tiles of 64, 6 of 33 KB (8 epilogue warps, 24 KB of output staging)
-// or 5 (16 warps, 48 KB); with row tiles of 128, 4 of 42 KB (48 KB of staging).
-__host__ __device__ constexpr int pair_stages(int CH, int EPI) { return CH == 2 ? 4 : (pair_epi_warps(CH, EPI) == 8 ? 6 : 5); }
+// k-blocks of 16 per pipeline stage: 2 for K-major data with 8 epilogue warps (the data box
+// then has 64-byte rows, 64-byte swizzled: half as many row requests per byte as 32-byte rows),
+// else 1.
+__host__ __device__ constexpr int pair_kb_per_stage(int CH, int EPI, bool KM)
+{
+    return KM && pair_epi_warps(CH, EPI) == 8 ? 2 : 1;
+}
+// Pipeline stages: with row tiles of 64, 6 of 33 KB (8 epilogue warps, 24 KB of output staging;
+// K-major: 3 of 66 KB, two k-blocks each) or 5 (16 warps, 48 KB); with row tiles of 128, 4 of
+// 42 KB (48 KB of staging).
+__host__ __device__ constexpr int pair_stages(int CH, int EPI, bool KM)
+{
+    return CH == 2 ? 4 : (pair_epi_warps(CH, EPI) == 8 ? 6 / pair_kb_per_stage(CH, EPI, KM) : 5);
+}
 __host__ __device__ constexpr int pair_staging_bytes(int CH, int EPI) { return pair_epi_warps(CH, EPI) * kStagingPerWarp; }
 
 // The same product with the tensor cores of the two SMs of a cluster
@@ -1254,7 +1265,8 @@ __global__ void __launch_bounds__(pair_threads(CH, EPI), 1)
     // BATCH: items P < total of many problems (records `many`, sorted by pairs_begin); `a` then
     // carries only what all problems share (row tiles of the same size, stage layout, error word)
     const int64_t items = BATCH ? total : a.pairs;
-    constexpr int kSt = pair_stages(CH, EPI);
+    constexpr int kSt = pair_stages(CH, EPI, KMAJOR);
+    constexpr int KB = pair_kb_per_stage(CH, EPI, KMAJOR);  // k-blocks per stage
     extern __shared__ __align__(1024) uint8_t smem_raw[];
     uint8_t *smem = reinterpret_cast<uint8_t *>((reinterpret_cast<uintptr_t>(smem_raw) + 1023) & ~uintptr_t(1023));
     uint8_t *staging = smem + kSt * a.stage_bytes;  // pair_epi_warps(CH, EPI) x kStagingPerWarp
@@ -1347,23 +1359,30 @@ __global__ void __launch_bounds__(pair_threads(CH, EPI), 1)
                 const int e_box_rows = NP * e_rows;
                 const int e_row0 = (h * A.kblocks * 2 + rank) * e_box_rows;
                 const int kb_end = A.kb_hi[h];
-                for (int kb = A.kb_lo[h]; kb < kb_end; ++kb) {
+                for (int kb = A.kb_lo[h]; kb < kb_end; kb += KB) {
                     if (!mbar_wait(&empty[s], ph ^ 1u, a.err, MM_ERR_TIMEOUT)) {
                         *abort_flag = 1;
                         break;
                     }
+                    const int nk = KB == 1 || kb + 1 == kb_end ? 1 : 2;  // k-blocks of the item in this stage
                     uint8_t *st = smem + s * a.stage_bytes;
                     const uint32_t fb = full_lead + uint32_t(s) * 8u;
-                    if (rank == 0) mbar_arrive_expect_tx(&full[s], uint32_t(a.tx_bytes));
-                    // all 2 NP piece planes in one box (K-major: [plane][128 points][16]) or one box per
-                    // atom (MN-major: [atom][plane][16 k][64 points])
+                    // both CTAs' bytes: the data box (always whole, zero-filled past the tensor) and the
+                    // matrix boxes of the stage's k-blocks
+                    if (rank == 0)
+                        mbar_arrive_expect_tx(&full[s], KB == 1 ? uint32_t(a.tx_bytes)
+                                                                : uint32_t(2 * (a.e_offset + nk * NP * e_bytes)));
+                    // all 2 NP piece planes in one box (K-major: [plane][128 points][16 KB k]) or one box
+                    // per atom (MN-major: [atom][plane][16 k][64 points])
                     if (KMAJOR) {
                         tma_load_3d_pair(mx, fb, st, kb * kBK, k_row, 0);
                     } else {
                         tma_load_4d_pair(mx, fb, st, ac_l[0], kb * kBK, ac_r[0], 0);
                         tma_load_4d_pair(mx, fb, st + 2 * NP * 2048, ac_l[1], kb * kBK, ac_r[1], 0);
                     }
-                    tma_load_2d_pair(me, fb, st + a.e_offset, 0, e_row0 + kb * 2 * e_box_rows);
+                    for (int j = 0; j < nk; ++j)
+                        tma_load_2d_pair(me, fb, st + a.e_offset + j * NP * e_bytes, 0,
+                                         e_row0 + (kb + j) * 2 * e_box_rows);
                     if (++s == kSt) {
                         s = 0;
                         ph ^= 1u;
@@ -1400,11 +1419,13 @@ __global__ void __launch_bounds__(pair_threads(CH, EPI), 1)
             uint64_t adesc[2][NP], bdesc[2][NP];  // [real plane, imaginary plane][piece]
 #pragma unroll
             for (int p = 0; p < NP; ++p) {
-                // K-major: plane tiles of 4 KB; MN-major: plane tiles of 2 KB per atom, atoms 2 NP x 2 KB apart
-                const uint32_t pb = KMAJOR ? uint32_t(kDataTileBytes) : 2048u;
+                // K-major: plane tiles of KB x 4 KB (rows of 32 KB bytes, 8-row swizzle atoms of 256 KB
+                // bytes); MN-major: plane tiles of 2 KB per atom, atoms 2 NP x 2 KB apart
+                const uint32_t pb = KMAJOR ? uint32_t(KB * kDataTileBytes) : 2048u;
                 const uint32_t xre = st0 + uint32_t(p) * pb, xim = st0 + uint32_t(NP + p) * pb;
-                adesc[0][p] = KMAJOR ? smem_desc(xre, 16, 256, kSwz32) : smem_desc(xre, 2 * NP * 2048, 1024, kSwz128);
-                adesc[1][p] = KMAJOR ? smem_desc(xim, 16, 256, kSwz32) : smem_desc(xim, 2 * NP * 2048, 1024, kSwz128);
+                constexpr uint32_t kmswz = KB == 2 ? kSwz64 : kSwz32;
+                adesc[0][p] = KMAJOR ? smem_desc(xre, 16, 256 * KB, kmswz) : smem_desc(xre, 2 * NP * 2048, 1024, kSwz128);
+                adesc[1][p] = KMAJOR ? smem_desc(xim, 16, 256 * KB, kmswz) : smem_desc(xim, 2 * NP * 2048, 1024, kSwz128);
                 const uint32_t eb = est0 + uint32_t(p * e_bytes);
                 bdesc[0][p] = smem_desc(eb + uint32_t(half * 32), 16, 256, kSwz32);  // [C; S]
                 bdesc[1][p] = smem_desc(eb, 16, 256, kSwz32);                        // [-S; C]
@@ -1425,20 +1446,25 @@ __global__ void __launch_bounds__(pair_threads(CH, EPI), 1)
                 tc_fence_after();
                 const uint32_t d0 = tmem + uint32_t(b * set_cols), d1 = d0 + uint32_t(acc_cols);
                 const int kb_lo = A.kb_lo[h], kb_hi = A.kb_hi[h];
-                for (int kb = kb_lo; kb < kb_hi; ++kb) {
+                for (int kb = kb_lo; kb < kb_hi; kb += KB) {
                     if (!mbar_wait(&full[s], ph, a.err, MM_ERR_TIMEOUT)) {
                         *abort_flag = 1;
                         break;
                     }
                     tc_fence_after();
                     const uint64_t so = uint64_t(s) * stage_step;
-                    const uint32_t first = kb == kb_lo ? 0u : 1u;  // each accumulator starts at its first product
+                    const int nk = KB == 1 || kb + 1 == kb_hi ? 1 : 2;
+                    for (int j = 0; j < nk; ++j) {
+                        // k-block kb + j: its 32 bytes of every data row, its matrix blocks
+                        const uint64_t ao = so + uint64_t(j * 2), bo = so + uint64_t(j * (NP * e_bytes >> 4));
+                        const uint32_t first = kb + j == kb_lo ? 0u : 1u;  // each accumulator starts at its first product
 #pragma unroll
-                    for (int t = 0; t < num_terms(NP); ++t) {
-                        const int pa = term_a(t), pb = term_b(t);
-                        const uint32_t dcol = (NP > 1 && (pa != 0 || pb != 0)) ? d1 : d0;
-                        umma_f16_pair(dcol, adesc[0][pb] + so, bdesc[0][pa] + so, idesc, t <= 1 ? first : 1u);
-                        umma_f16_pair(dcol, adesc[1][pb] + so, bdesc[1][pa] + so, idesc, 1u);
+                        for (int t = 0; t < num_terms(NP); ++t) {
+                            const int pa = term_a(t), pb = term_b(t);
+                            const uint32_t dcol = (NP > 1 && (pa != 0 || pb != 0)) ? d1 : d0;
+                            umma_f16_pair(dcol, adesc[0][pb] + ao, bdesc[0][pa] + bo, idesc, t <= 1 ? first : 1u);
+                            umma_f16_pair(dcol, adesc[1][pb] + ao, bdesc[1][pa] + bo, idesc, 1u);
+                        }
                     }
                     umma_commit_pair_mc(&empty[s], 0x3);
                     if (++s == kSt) {
@@ -2100,13 +2126,17 @@ static cudaError_t tc_setup(const TcState &si, const TcState &so, int mu, const 
     }
     const TcMatrix::TcPairTiles *PT = pair_tiles(M, variant);
     const bool pair = PT != nullptr;
+    // pair kernel, K-major data: k-blocks per stage (two: 64-byte rows, 64-byte swizzle)
+    const int kbs = pair ? pair_kb_per_stage(PT->it > 64 ? 2 : 1, epi.kind, km) : 1;
     if (pair) {
         // the pair kernel loads all 2 NP piece planes of a tile in one box
         if (km) {
             cuuint64_t dims[3] = {cuuint64_t(a.kp), cuuint64_t(a.right), cuuint64_t(2 * NP)};
             cuuint64_t str[2] = {cuuint64_t(a.kp * 2), cuuint64_t(si.plane * 2)};
-            cuuint32_t box[3] = {kBK, kTileM, cuuint32_t(2 * NP)};
-            if (!encode(&mx, xin, 3, dims, str, box, CU_TENSOR_MAP_SWIZZLE_32B)) return cudaErrorInvalidValue;
+            cuuint32_t box[3] = {cuuint32_t(kBK * kbs), kTileM, cuuint32_t(2 * NP)};
+            if (!encode(&mx, xin, 3, dims, str, box, kbs == 2 ? CU_TENSOR_MAP_SWIZZLE_64B : CU_TENSOR_MAP_SWIZZLE_32B))
+                return cudaErrorInvalidValue;
+            a.e_offset = kbs * 2 * NP * kDataTileBytes;
         } else {
             cuuint64_t dims[4] = {cuuint64_t(a.left), cuuint64_t(a.kp), cuuint64_t(a.right), cuuint64_t(2 * NP)};
             cuuint64_t str[3] = {cuuint64_t(a.left * 2), cuuint64_t(a.left * a.kp * 2), cuuint64_t(si.plane * 2)};
@@ -2125,7 +2155,7 @@ static cudaError_t tc_setup(const TcState &si, const TcState &so, int mu, const 
         // blocks [-S; C; S] of it / 2 rows per (piece, row tile, k-block, rank), copied as 128-byte lines
         const int e_bytes = 3 * (PT->it / 2) * 32;
         a.tx_bytes = 2 * (a.e_offset + NP * e_bytes);  // both CTAs' loads complete on the leader's barrier
-        a.stage_bytes = (a.e_offset + NP * e_bytes + 1023) / 1024 * 1024;
+        a.stage_bytes = (a.e_offset + kbs * NP * e_bytes + 1023) / 1024 * 1024;
         const int64_t lines = int64_t(NP) * PT->ni * (M.k_pad / 16) * 2 * e_bytes / 128;
         cuuint64_t dims[2] = {64, cuuint64_t(lines)};
         cuuint64_t str[1] = {128};
@@ -2161,7 +2191,7 @@ static cudaError_t tc_setup(const TcState &si, const TcState &so, int mu, const 
             if (!encode(&my, out_pieces, 4, dims, str, box, CU_TENSOR_MAP_SWIZZLE_64B)) return cudaErrorInvalidValue;
         }
     }
-    const int smem = pair ? pair_stages(ch, epi.kind) * a.stage_bytes + pair_staging_bytes(ch, epi.kind) + 1024 + 256
+    const int smem = pair ? pair_stages(ch, epi.kind, km) * a.stage_bytes + pair_staging_bytes(ch, epi.kind) + 1024 + 256
                           : kStages * a.stage_bytes + 1024 + 256;
     L->km = km;
     L->pair = pair;
@@ -2385,7 +2415,7 @@ cudaError_t tc_pair_batch_launch(const void *host_recs, const void *dev_recs, in
     a.err = d_err;
     const int NP = tc_pieces(prec);
     const bool fx = tc_fixed(prec);
-    const int smem = pair_stages(1, 0) * a.stage_bytes + pair_staging_bytes(1, 0) + 1024 + 256;
+    const int smem = pair_stages(1, 0, kmajor) * a.stage_bytes + pair_staging_bytes(1, 0) + 1024 + 256;
     const int64_t grid = 2 * (total < num_sms() / 2 ? total : num_sms() / 2);
     const auto *dev = reinterpret_cast<const TcPairProblem *>(dev_recs);
     auto go = [&](auto kern) -> cudaError_t {

@@ -240,7 +240,7 @@ __device__ __forceinline__ uint64_t smem_desc(uint32_t saddr, uint32_t lbo, uint
     d |= uint64_t(swz & 7u) << 61;
     return d;
 }
-constexpr uint32_t kSwz32 = 6, kSwz128 = 2;
+constexpr uint32_t kSwz32 = 6, kSwz64 = 4, kSwz128 = 2;
 
 // Instruction descriptor, kind::f16 with BF16 A/B and FP32 D.
 __host__ __device__ constexpr uint32_t idesc_bf16_f32(int M, int N, bool a_mn_major, bool b_mn_major)
