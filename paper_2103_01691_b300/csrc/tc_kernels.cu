@@ -1220,12 +1220,12 @@ __device__ __forceinline__ void epi_frag_store(const TcArgs &a, const CUtensorMa
 // epilogue (EPI 1), whose per-value arithmetic needs the extra warps.
 __host__ __device__ constexpr int pair_epi_warps(int CH, int EPI) { return CH == 1 && EPI != 1 ? 8 : 16; }
 __host__ __device__ constexpr int pair_threads(int CH, int EPI) { return 32 * (2 + pair_epi_warps(CH, EPI)); }
-// k-blocks of 16 per pipeline stage: 2 for K-major data with 8 epilogue warps (the data box
-// then has 64-byte rows, 64-byte swizzled: half as many row requests per byte as 32-byte rows),
-// else 1.
-__host__ __device__ constexpr int pair_kb_per_stage(int CH, int EPI, bool KM)
+// k-blocks of 16 per pipeline stage: 2 with 8 epilogue warps (K-major data boxes then have
+// 64-byte rows, 64-byte swizzled: half as many row requests per byte as 32-byte rows; MN-major
+// boxes 32 k-rows of 128 bytes), else 1.
+__host__ __device__ constexpr int pair_kb_per_stage(int CH, int EPI, bool)
 {
-    return KM && pair_epi_warps(CH, EPI) == 8 ? 2 : 1;
+    return pair_epi_warps(CH, EPI) == 8 ? 2 : 1;
 }
 // Pipeline stages: with row tiles of 64, 6 of 33 KB (8 epilogue warps, 24 KB of output staging;
 // K-major: 3 of 66 KB, two k-blocks each) or 5 (16 warps, 48 KB); with row tiles of 128, 4 of
@@ -1378,7 +1378,7 @@ __global__ void __launch_bounds__(pair_threads(CH, EPI), 1)
                         tma_load_3d_pair(mx, fb, st, kb * kBK, k_row, 0);
                     } else {
                         tma_load_4d_pair(mx, fb, st, ac_l[0], kb * kBK, ac_r[0], 0);
-                        tma_load_4d_pair(mx, fb, st + 2 * NP * 2048, ac_l[1], kb * kBK, ac_r[1], 0);
+                        tma_load_4d_pair(mx, fb, st + KB * 2 * NP * 2048, ac_l[1], kb * kBK, ac_r[1], 0);
                     }
                     for (int j = 0; j < nk; ++j)
                         tma_load_2d_pair(me, fb, st + a.e_offset + j * NP * e_bytes, 0,
@@ -1420,12 +1420,13 @@ __global__ void __launch_bounds__(pair_threads(CH, EPI), 1)
 #pragma unroll
             for (int p = 0; p < NP; ++p) {
                 // K-major: plane tiles of KB x 4 KB (rows of 32 KB bytes, 8-row swizzle atoms of 256 KB
-                // bytes); MN-major: plane tiles of 2 KB per atom, atoms 2 NP x 2 KB apart
-                const uint32_t pb = KMAJOR ? uint32_t(KB * kDataTileBytes) : 2048u;
+                // bytes); MN-major: plane tiles of KB x 2 KB (16 KB k-rows of 128 bytes) per atom, atoms
+                // 2 NP KB x 2 KB apart
+                const uint32_t pb = KMAJOR ? uint32_t(KB * kDataTileBytes) : uint32_t(KB * 2048);
                 const uint32_t xre = st0 + uint32_t(p) * pb, xim = st0 + uint32_t(NP + p) * pb;
                 constexpr uint32_t kmswz = KB == 2 ? kSwz64 : kSwz32;
-                adesc[0][p] = KMAJOR ? smem_desc(xre, 16, 256 * KB, kmswz) : smem_desc(xre, 2 * NP * 2048, 1024, kSwz128);
-                adesc[1][p] = KMAJOR ? smem_desc(xim, 16, 256 * KB, kmswz) : smem_desc(xim, 2 * NP * 2048, 1024, kSwz128);
+                adesc[0][p] = KMAJOR ? smem_desc(xre, 16, 256 * KB, kmswz) : smem_desc(xre, 2 * NP * 2048 * KB, 1024, kSwz128);
+                adesc[1][p] = KMAJOR ? smem_desc(xim, 16, 256 * KB, kmswz) : smem_desc(xim, 2 * NP * 2048 * KB, 1024, kSwz128);
                 const uint32_t eb = est0 + uint32_t(p * e_bytes);
                 bdesc[0][p] = smem_desc(eb + uint32_t(half * 32), 16, 256, kSwz32);  // [C; S]
                 bdesc[1][p] = smem_desc(eb, 16, 256, kSwz32);                        // [-S; C]
@@ -1455,8 +1456,9 @@ __global__ void __launch_bounds__(pair_threads(CH, EPI), 1)
                     const uint64_t so = uint64_t(s) * stage_step;
                     const int nk = KB == 1 || kb + 1 == kb_hi ? 1 : 2;
                     for (int j = 0; j < nk; ++j) {
-                        // k-block kb + j: its 32 bytes of every data row, its matrix blocks
-                        const uint64_t ao = so + uint64_t(j * 2), bo = so + uint64_t(j * (NP * e_bytes >> 4));
+                        // k-block kb + j: its 32 bytes of every data row (K-major) or its 16 k-rows of
+                        // 128 bytes (MN-major), its matrix blocks
+                        const uint64_t ao = so + uint64_t(j * (KMAJOR ? 2 : 128)), bo = so + uint64_t(j * (NP * e_bytes >> 4));
                         const uint32_t first = kb + j == kb_lo ? 0u : 1u;  // each accumulator starts at its first product
 #pragma unroll
                         for (int t = 0; t < num_terms(NP); ++t) {
@@ -2126,7 +2128,7 @@ static cudaError_t tc_setup(const TcState &si, const TcState &so, int mu, const 
     }
     const TcMatrix::TcPairTiles *PT = pair_tiles(M, variant);
     const bool pair = PT != nullptr;
-    // pair kernel, K-major data: k-blocks per stage (two: 64-byte rows, 64-byte swizzle)
+    // pair kernel: k-blocks per stage (two with 8 epilogue warps: one data box covers both)
     const int kbs = pair ? pair_kb_per_stage(PT->it > 64 ? 2 : 1, epi.kind, km) : 1;
     if (pair) {
         // the pair kernel loads all 2 NP piece planes of a tile in one box
@@ -2140,8 +2142,9 @@ static cudaError_t tc_setup(const TcState &si, const TcState &so, int mu, const 
         } else {
             cuuint64_t dims[4] = {cuuint64_t(a.left), cuuint64_t(a.kp), cuuint64_t(a.right), cuuint64_t(2 * NP)};
             cuuint64_t str[3] = {cuuint64_t(a.left * 2), cuuint64_t(a.left * a.kp * 2), cuuint64_t(si.plane * 2)};
-            cuuint32_t box[4] = {64, kBK, 1, cuuint32_t(2 * NP)};
+            cuuint32_t box[4] = {64, cuuint32_t(kBK * kbs), 1, cuuint32_t(2 * NP)};
             if (!encode(&mx, xin, 4, dims, str, box, CU_TENSOR_MAP_SWIZZLE_128B)) return cudaErrorInvalidValue;
+            a.e_offset = kbs * 2 * NP * kDataTileBytes;
         }
     }
     if (pair) {
