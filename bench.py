@@ -36,7 +36,7 @@ ALG_BYTES_PER_MODE = 2 * STATE_BYTES     # read + write the state once
 WORKLOAD = "free Schroedinger n=256^3 complex64, Dirichlet FD, E=expm(i*1e-4*A), u0 complex normal seed 2"
 # DRAM bytes (read + write) per mode-product launch from the ncu capture in
 # profiles/tc_pair_kernel_f16x6_n256.md; None once the kernel changes.
-NCU_TRAFFIC_BYTES = 354.9e6  # dram read + write per launch, mean of the three directions (ncu, see profiles)
+NCU_TRAFFIC_BYTES = 355.1e6  # dram read + write per launch, mean of the three directions (ncu, see profiles)
 
 
 def peaks():

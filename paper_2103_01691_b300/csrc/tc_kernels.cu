@@ -504,8 +504,34 @@ __global__ void max_abs_kernel(int64_t count, const float2 *__restrict__ u, unsi
     if ((threadIdx.x & 31) == 0 && b) atomicMax(out, b);
 }
 
-// Padded-index loop: reads the logical complex64 tensor, writes all pieces.
-template <bool FX>
+// Logical offset of the first point of padded row r (the padded index over directions 2..d),
+// and whether the row lies inside the logical tensor.  I: 32-bit when the padded plane fits.
+template <typename I>
+__device__ __forceinline__ I row_offset(const Dims &dm, I r, bool &inside)
+{
+    I lin = 0, mul = I(dm.n[0]);
+    inside = true;
+    for (int v = 1; v < dm.d; ++v) {
+        const I np = I(dm.np[v]);
+        const I c = r % np;
+        r /= np;
+        inside &= c < I(dm.n[v]);
+        lin += c * mul;
+        mul *= I(dm.n[v]);
+    }
+    return lin;
+}
+
+__device__ __forceinline__ uint4 pack8(const uint16_t (&b)[8])
+{
+    return make_uint4(uint32_t(b[0]) | (uint32_t(b[1]) << 16), uint32_t(b[2]) | (uint32_t(b[3]) << 16),
+                      uint32_t(b[4]) | (uint32_t(b[5]) << 16), uint32_t(b[6]) | (uint32_t(b[7]) << 16));
+}
+
+// Reads the logical complex64 tensor, writes all pieces of the padded one.  Each thread takes
+// 8 consecutive padded points of a row (the padded first direction is a multiple of 16): one
+// index decomposition and one 16-byte store per piece plane for the 8.
+template <bool FX, typename I>
 __global__ void split_kernel(Dims dm, int64_t plane, int npieces, const float2 *__restrict__ u,
                              uint16_t *__restrict__ pieces, const unsigned *maxw, float *scale_out,
                              unsigned *bound_words, Bounds bounds, int nb)
@@ -522,56 +548,73 @@ __global__ void split_kernel(Dims dm, int64_t plane, int npieces, const float2 *
             }
         }
     }
-    for (int64_t q = blockIdx.x * int64_t(blockDim.x) + threadIdx.x; q < plane; q += int64_t(gridDim.x) * blockDim.x) {
-        int64_t rem = q, lin = 0, mul = 1;
-        bool inside = true;
-        for (int v = 0; v < dm.d; ++v) {
-            const int64_t c = rem % dm.np[v];
-            rem /= dm.np[v];
-            inside &= c < dm.n[v];
-            lin += c * mul;
-            mul *= dm.n[v];
-        }
-        const float2 x = inside ? u[lin] : make_float2(0.f, 0.f);
-        if (FX) {
-            uint16_t b[6];
-            split_fx(x.x, es, b[0], b[1], b[2]);
-            split_fx(x.y, es, b[3], b[4], b[5]);
+    const I np0 = I(dm.np[0]), n0 = I(dm.n[0]), groups = I(plane / 8);
+    for (I g = I(blockIdx.x) * blockDim.x + threadIdx.x; g < groups; g += I(gridDim.x) * blockDim.x) {
+        const I q0 = g * 8, c0 = q0 % np0;
+        bool inside;
+        const I lin = row_offset<I>(dm, q0 / np0, inside) + c0;
+        float2 x[8];
 #pragma unroll
-            for (int k = 0; k < 6; ++k) pieces[k * plane + q] = b[k];
+        for (int k = 0; k < 8; ++k) x[k] = inside && c0 + I(k) < n0 ? u[lin + I(k)] : make_float2(0.f, 0.f);
+        if (FX) {
+            uint16_t b[6][8];
+#pragma unroll
+            for (int k = 0; k < 8; ++k) {
+                split_fx(x[k].x, es, b[0][k], b[1][k], b[2][k]);
+                split_fx(x[k].y, es, b[3][k], b[4][k], b[5][k]);
+            }
+#pragma unroll
+            for (int c = 0; c < 6; ++c) *reinterpret_cast<uint4 *>(pieces + int64_t(c) * plane + q0) = pack8(b[c]);
         } else {
-            split_bf16(x.x, npieces, pieces + q, plane);
-            split_bf16(x.y, npieces, pieces + int64_t(npieces) * plane + q, plane);
+            uint16_t br[3][8], bi[3][8];
+#pragma unroll
+            for (int k = 0; k < 8; ++k) {
+                split_bf16(x[k].x, npieces, &br[0][k], 8);
+                split_bf16(x[k].y, npieces, &bi[0][k], 8);
+            }
+            for (int p = 0; p < npieces; ++p) {
+                *reinterpret_cast<uint4 *>(pieces + int64_t(p) * plane + q0) = pack8(br[p]);
+                *reinterpret_cast<uint4 *>(pieces + int64_t(npieces + p) * plane + q0) = pack8(bi[p]);
+            }
         }
     }
 }
 
-// Logical-index loop: sums the pieces back (exact for three BF16 pieces).
-template <bool FX>
+// Sums the pieces back (exact for three BF16 pieces), 8 padded points per thread as in
+// split_kernel; padding is skipped.
+template <bool FX, typename I>
 __global__ void merge_kernel(Dims dm, int64_t plane, int npieces, const uint16_t *__restrict__ pieces,
-                             const float *scale, float2 *__restrict__ u, int64_t count)
+                             const float *scale, float2 *__restrict__ u)
 {
     const float s = FX ? *scale : 1.0f;
-    for (int64_t q = blockIdx.x * int64_t(blockDim.x) + threadIdx.x; q < count; q += int64_t(gridDim.x) * blockDim.x) {
-        int64_t rem = q, pad = 0, mul = 1;
-        for (int v = 0; v < dm.d; ++v) {
-            const int64_t c = rem % dm.n[v];
-            rem /= dm.n[v];
-            pad += c * mul;
-            mul *= dm.np[v];
-        }
-        float re = 0.f, im = 0.f;
+    const I np0 = I(dm.np[0]), n0 = I(dm.n[0]), groups = I(plane / 8);
+    for (I g = I(blockIdx.x) * blockDim.x + threadIdx.x; g < groups; g += I(gridDim.x) * blockDim.x) {
+        const I q0 = g * 8, c0 = q0 % np0;
+        bool inside;
+        const I lin = row_offset<I>(dm, q0 / np0, inside) + c0;
+        if (!inside || c0 >= n0) continue;
+        float re[8], im[8];
+#pragma unroll
+        for (int k = 0; k < 8; ++k) re[k] = im[k] = 0.f;
         for (int p = npieces - 1; p >= 0; --p) {
-            const uint16_t br = pieces[p * plane + pad], bi = pieces[(npieces + p) * plane + pad];
-            if (FX) {
-                re += __half2float(__ushort_as_half(br));
-                im += __half2float(__ushort_as_half(bi));
-            } else {
-                re += __bfloat162float(__ushort_as_bfloat16(br));
-                im += __bfloat162float(__ushort_as_bfloat16(bi));
+            const uint4 wr = *reinterpret_cast<const uint4 *>(pieces + int64_t(p) * plane + q0);
+            const uint4 wi = *reinterpret_cast<const uint4 *>(pieces + int64_t(npieces + p) * plane + q0);
+            const uint32_t ar[4] = {wr.x, wr.y, wr.z, wr.w}, ai[4] = {wi.x, wi.y, wi.z, wi.w};
+#pragma unroll
+            for (int k = 0; k < 8; ++k) {
+                const uint16_t br = uint16_t(ar[k / 2] >> (16 * (k & 1))), bi = uint16_t(ai[k / 2] >> (16 * (k & 1)));
+                if (FX) {
+                    re[k] += __half2float(__ushort_as_half(br));
+                    im[k] += __half2float(__ushort_as_half(bi));
+                } else {
+                    re[k] += __bfloat162float(__ushort_as_bfloat16(br));
+                    im[k] += __bfloat162float(__ushort_as_bfloat16(bi));
+                }
             }
         }
-        u[q] = make_float2(re * s, im * s);
+#pragma unroll
+        for (int k = 0; k < 8; ++k)
+            if (c0 + I(k) < n0) u[lin + I(k)] = make_float2(re[k] * s, im[k] * s);
     }
 }
 
@@ -595,6 +638,7 @@ static int grid_for(int64_t count)
 cudaError_t tc_split(const TcState &st, int npieces, bool fixed, const void *u_c64, void *pieces, unsigned *work,
                      float *scale_out, unsigned *bound_words, const double *bounds, int nbounds, cudaStream_t s)
 {
+    if ((reinterpret_cast<uintptr_t>(pieces) & 15) || st.plane % 8) return cudaErrorMisalignedAddress;
     Bounds bd{};
     for (int q = 0; q < nbounds && q < kMaxDims; ++q) bd.b[q] = bounds[q];
     if (fixed) {
@@ -604,13 +648,23 @@ cudaError_t tc_split(const TcState &st, int npieces, bool fixed, const void *u_c
         if (e != cudaSuccess) return e;
         max_abs_kernel<<<grid_for(count), 256, 0, s>>>(count, (const float2 *)u_c64, work);
         count_launch();
-        split_kernel<true><<<grid_for(st.plane), 256, 0, s>>>(make_dims(st), st.plane, npieces, (const float2 *)u_c64,
-                                                            (uint16_t *)pieces, work, scale_out, bound_words, bd,
-                                                            nbounds);
+        if (st.plane < (int64_t(1) << 31))
+            split_kernel<true, uint32_t><<<grid_for(st.plane / 8), 256, 0, s>>>(
+                make_dims(st), st.plane, npieces, (const float2 *)u_c64, (uint16_t *)pieces, work, scale_out,
+                bound_words, bd, nbounds);
+        else
+            split_kernel<true, int64_t><<<grid_for(st.plane / 8), 256, 0, s>>>(
+                make_dims(st), st.plane, npieces, (const float2 *)u_c64, (uint16_t *)pieces, work, scale_out,
+                bound_words, bd, nbounds);
     } else {
-        split_kernel<false><<<grid_for(st.plane), 256, 0, s>>>(make_dims(st), st.plane, npieces,
-                                                             (const float2 *)u_c64, (uint16_t *)pieces, nullptr,
-                                                             nullptr, nullptr, bd, 0);
+        if (st.plane < (int64_t(1) << 31))
+            split_kernel<false, uint32_t><<<grid_for(st.plane / 8), 256, 0, s>>>(
+                make_dims(st), st.plane, npieces, (const float2 *)u_c64, (uint16_t *)pieces, nullptr, nullptr, nullptr,
+                bd, 0);
+        else
+            split_kernel<false, int64_t><<<grid_for(st.plane / 8), 256, 0, s>>>(
+                make_dims(st), st.plane, npieces, (const float2 *)u_c64, (uint16_t *)pieces, nullptr, nullptr, nullptr,
+                bd, 0);
     }
     count_launch();
     return cudaGetLastError();
@@ -619,14 +673,24 @@ cudaError_t tc_split(const TcState &st, int npieces, bool fixed, const void *u_c
 cudaError_t tc_merge(const TcState &st, int npieces, bool fixed, const void *pieces, const float *scale, void *u_c64,
                      cudaStream_t s)
 {
-    int64_t count = 1;
-    for (int v = 0; v < st.d; ++v) count *= st.n[v];
-    if (fixed)
-        merge_kernel<true><<<grid_for(count), 256, 0, s>>>(make_dims(st), st.plane, npieces, (const uint16_t *)pieces,
-                                                         scale, (float2 *)u_c64, count);
-    else
-        merge_kernel<false><<<grid_for(count), 256, 0, s>>>(make_dims(st), st.plane, npieces, (const uint16_t *)pieces,
-                                                          nullptr, (float2 *)u_c64, count);
+    if ((reinterpret_cast<uintptr_t>(pieces) & 15) || st.plane % 8) return cudaErrorMisalignedAddress;
+    const bool narrow = st.plane < (int64_t(1) << 31);
+    const int grid = grid_for(st.plane / 8);
+    if (fixed) {
+        if (narrow)
+            merge_kernel<true, uint32_t><<<grid, 256, 0, s>>>(make_dims(st), st.plane, npieces,
+                                                              (const uint16_t *)pieces, scale, (float2 *)u_c64);
+        else
+            merge_kernel<true, int64_t><<<grid, 256, 0, s>>>(make_dims(st), st.plane, npieces,
+                                                             (const uint16_t *)pieces, scale, (float2 *)u_c64);
+    } else {
+        if (narrow)
+            merge_kernel<false, uint32_t><<<grid, 256, 0, s>>>(make_dims(st), st.plane, npieces,
+                                                               (const uint16_t *)pieces, nullptr, (float2 *)u_c64);
+        else
+            merge_kernel<false, int64_t><<<grid, 256, 0, s>>>(make_dims(st), st.plane, npieces,
+                                                              (const uint16_t *)pieces, nullptr, (float2 *)u_c64);
+    }
     count_launch();
     return cudaGetLastError();
 }
