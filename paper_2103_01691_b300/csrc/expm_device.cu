@@ -191,9 +191,10 @@ cudaError_t expm_device(ExpmWorkspace *w, int n, const double *A, const double *
 // ---- imaginary z: cos / sin in real arithmetic, batched over several f ----------
 //
 // For real M and z = i w, exp(z M) = cos(w M) + i sin(w M).  With
-// X = w M / 2^s (||X||_1 <= 1) and Y = X^2:
+// X = w M / 2^s (||X||_1 <= theta, theta = 1 or 2) and Y = X^2:
 //   cos X = sum_{j<=9} (-1)^j Y^j / (2j)!,   sin X = X sum_{j<=9} (-1)^j Y^j / (2j+1)!,
-// whose truncation errors are below 1/20! and 1/21!.  Each degree-9
+// whose truncation errors are below theta^20/20! and theta^21/21! (below
+// 1e-18 for theta = 1, 5e-13 for theta = 2).  Each degree-9
 // polynomial in Y is evaluated by Paterson-Stockmeyer with Y^3 as the
 // Horner variable (2 products each, given Y, Y^2, Y^3), and the angle is
 // doubled s times by cos 2a = cos^2 a - sin^2 a, sin 2a = 2 sin a cos a (3
@@ -312,16 +313,17 @@ int expm_batch_capacity(int n)
 }
 
 cudaError_t expm_imag_batched(ExpmBatch *w, int n, const double *A, const double *B, const double *f_host, int count,
-                              double wim, double norm_bound, double2 *E, cudaStream_t s, double mu)
+                              double wim, double norm_bound, double2 *E, cudaStream_t s, double mu, double theta)
 {
     // exp(i w M) = exp(i w mu) exp(i w (M - mu I)): norm_bound bounds ||M - mu I||_1
     if (w->n < n || w->cap < count || count < 1 || !w->blas) return cudaErrorInvalidValue;
     cublasHandle_t h = static_cast<cublasHandle_t>(w->blas);
     if (cublasSetStream(h, s) != CUBLAS_STATUS_SUCCESS) return cudaErrorUnknown;
+    if (!(theta >= 1.0 && theta <= 2.0)) return cudaErrorInvalidValue;
     const double za = std::fabs(wim) * norm_bound;
     int sq = 0;
-    if (za > 1.0) sq = int(std::ceil(std::log2(za)));
-    while (std::ldexp(za, -sq) > 1.0) ++sq;
+    if (za > theta) sq = int(std::ceil(std::log2(za / theta)));
+    while (std::ldexp(za, -sq) > theta) ++sq;
     cudaError_t e = cudaSuccess;
     if (count > 1 && (e = cudaMemcpyAsync(w->f, f_host, sizeof(double) * size_t(count), cudaMemcpyHostToDevice, s)) !=
                          cudaSuccess)

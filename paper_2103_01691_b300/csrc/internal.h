@@ -134,8 +134,12 @@ cudaError_t expm_batch_init(ExpmBatch *w, int n, int cap);
 void expm_batch_destroy(ExpmBatch *w);
 int expm_batch_capacity(int n);  // batch entries that keep the workspace near 1 GB (1..64)
 // mu: a diagonal shift taken out as the phase exp(i w mu); norm_bound then bounds ||A + f_k B - mu I||_1.
+// theta: the largest scaled norm ||X||_1 the series may see.  1 gives full FP64 accuracy
+// (truncation below 1e-19); 2 bounds the truncation by 2^20 / 20! < 5e-13, enough for matrices
+// that are split into tensor-core pieces (about 2^-34 of a row's scale), with one doubling fewer.
 cudaError_t expm_imag_batched(ExpmBatch *w, int n, const double *A, const double *B, const double *f_host, int count,
-                              double wim, double norm_bound, double2 *E, cudaStream_t s, double mu = 0.0);
+                              double wim, double norm_bound, double2 *E, cudaStream_t s, double mu = 0.0,
+                              double theta = 1.0);
 // HKP propagator of one direction on the device: M = Psi exp(-i tau H) Phi^W,
 // H = diag(k + 1/2) + P^T GP (GP = diag(g) P, NULL for the harmonic case),
 // P[l][k] = phi_k(x_l), fwd = Phi^W (host, m x m row-major).  Both workspaces

@@ -1899,8 +1899,9 @@ extern "C" mm_status hkmp_evolve(mm_plan *p, void *psi, int64_t nsteps, const do
         for (int v = 0; v < p->d; ++v) {
             if (!p->H0dev[v]) continue;
             const double bound = p->h0norm[v] + fmax * p->gnorm[v];
+            // tensor-core plans split the exponentials into pieces: scaled norms up to 2 suffice
             cudaError_t e = mm::expm_imag_batched(&p->expmb, int(p->n[v]), p->H0dev[v], p->Gdev[v], f_mid + k0, cnt,
-                                                  -p->tau, bound, p->Ebatch[v], s, p->hshift[v]);
+                                                  -p->tau, bound, p->Ebatch[v], s, p->hshift[v], p->tc ? 2.0 : 1.0);
             if (e != cudaSuccess) return cuda_fail(e, "device expm");
         }
         return MM_OK;
