@@ -1093,6 +1093,39 @@ __global__ void __launch_bounds__(kThreads, 1)
     }
 }
 
+// Point phase (EPI 2) of point `lane` of the warp's 32 points (TMEM lanes 32 quarter ..) in
+// work item `tile`, formed in FP64 from the per-direction tables; 1 outside the tensor.
+template <bool KMAJOR>
+__device__ __forceinline__ float2 point_phase(const TcArgs &a, int64_t tile, int quarter, int lane)
+{
+    int64_t l, r;
+    bool valid;
+    if (KMAJOR) {
+        l = 0;
+        r = tile * kTileM + quarter * 32 + lane;
+        valid = r < a.right;
+    } else {
+        const int64_t atom = 2 * tile + quarter / 2;
+        r = atom / a.aps;
+        l = (atom % a.aps) * 64 + (quarter & 1) * 32 + lane;
+        valid = r < a.right && l < a.left;
+    }
+    if (!valid) return make_float2(1.0f, 0.0f);
+    double fr = 1.0, fi = 0.0;
+    auto mul = [&](const double2 *tab, int64_t i) {
+        if (!tab) return;
+        const double2 z = tab[i];
+        const double nr = fr * z.x - fi * z.y;
+        fi = fr * z.y + fi * z.x;
+        fr = nr;
+    };
+    mul(a.pl0, l % a.ldiv);
+    mul(a.pl1, l / a.ldiv);
+    mul(a.pr0, r % a.rdiv);
+    mul(a.pr1, r / a.rdiv);
+    return make_float2(float(fr), float(fi));
+}
+
 // Per-warp staging of the pair kernel's output boxes: one plane's three pieces, 1 KB each.
 constexpr int kStageBoxBytes = 1024;
 constexpr int kStagingPerWarp = 3 * kStageBoxBytes;
@@ -1112,7 +1145,8 @@ template <int NP, bool KMAJOR, int EPI, bool FX>
 __device__ __forceinline__ void epi_frag_store(const TcArgs &a, const CUtensorMap *mapY, uint8_t *stg,
                                                float (&vr)[2][8], float (&vi)[2][8], int64_t tile, int h,
                                                int quarter, int lane, int grp, int nchunks, float s_in,
-                                               float inv_out, float lim, float &local_max, bool &range_ok)
+                                               float inv_out, float lim, float &local_max, bool &range_ok,
+                                               float2 phl)
 {
     if (grp >= nchunks) return;
     const int i0 = h * a.it + grp * 16;
@@ -1139,29 +1173,15 @@ __device__ __forceinline__ void epi_frag_store(const TcArgs &a, const CUtensorMa
 #pragma unroll
             for (int s = 0; s < 2; ++s) valid[hh][s] = rr < a.right && l0 + 16 * hh + 8 * s + t4 < a.left;
     }
-    // point phases of this thread's four points (EPI 2), formed in FP64
+    // point phases of this thread's four points (EPI 2): lane 16 hh + 8 s + t4 holds that point's
     float2 ph[2][2] = {{{1.0f, 0.0f}, {1.0f, 0.0f}}, {{1.0f, 0.0f}, {1.0f, 0.0f}}};
     if (EPI == 2) {
 #pragma unroll
         for (int hh = 0; hh < 2; ++hh)
 #pragma unroll
             for (int s = 0; s < 2; ++s) {
-                if (!valid[hh][s]) continue;
-                const int64_t pidx = (KMAJOR ? rr : int64_t(l0)) + 16 * hh + 8 * s + t4;
-                const int64_t l = KMAJOR ? 0 : pidx, r = KMAJOR ? pidx : rr;
-                double fr = 1.0, fi = 0.0;
-                auto mul = [&](const double2 *tab, int64_t i) {
-                    if (!tab) return;
-                    const double2 z = tab[i];
-                    const double nr = fr * z.x - fi * z.y;
-                    fi = fr * z.y + fi * z.x;
-                    fr = nr;
-                };
-                mul(a.pl0, l % a.ldiv);
-                mul(a.pl1, l / a.ldiv);
-                mul(a.pr0, r % a.rdiv);
-                mul(a.pr1, r / a.rdiv);
-                ph[hh][s] = make_float2(float(fr), float(fi));
+                ph[hh][s].x = __shfl_sync(0xffffffffu, phl.x, 16 * hh + 8 * s + t4);
+                ph[hh][s].y = __shfl_sync(0xffffffffu, phl.y, 16 * hh + 8 * s + t4);
             }
     }
     // row scales of this thread's four outputs (pairs at 2 tc and 8 + 2 tc)
@@ -1621,11 +1641,12 @@ __global__ void __launch_bounds__(pair_threads(CH, EPI), 1)
             __syncwarp();
             if (lane == 0) mbarrier_arrive(&tmem_empty[b]);
             if (!acc_ready) break;
+            const float2 phl = EPI == 2 ? point_phase<KMAJOR>(A, tile, quarter, lane) : make_float2(1.0f, 0.0f);
 #pragma unroll
             for (int q = 0; q < kPerWarp; ++q)
                 epi_frag_store<NP, KMAJOR, EPI, FX>(A, BATCH ? &pr->mapY : &mapY, staging + ew * kStagingPerWarp,
                                                     vr[q], vi[q], tile, h, quarter, lane, grp + kGroups * q, nchunks,
-                                                    s_in, inv_out, lim, local_max, range_ok);
+                                                    s_in, inv_out, lim, local_max, range_ok, phl);
         }
         if (lane == 0) bulk_wait0();  // this warp's stores are complete
         if (FX) {
