@@ -476,8 +476,11 @@ mm_status split_step_gpe(mm_plan *plan, void *psi_dev, double beta, double tau, 
  * theta = tau beta |psi|^2, through g = e^{i theta} g' + 2 tau beta
  * Im(conj(g') psi') psi.  Forward states are kept every ckpt_every steps
  * and recomputed within a segment (memory: ceil(nsteps / ckpt_every) +
- * ckpt_every + 1 states, allocated and freed by the call, which
- * synchronises the stream). */
+ * ckpt_every + 1 states).  The first call builds the propagators of the
+ * forward and adjoint half and full steps and allocates the checkpoint
+ * buffers; both stay with the plan (buffers grow when a later call needs
+ * more, matrices are rebuilt when tau changes) until mm_plan_destroy.
+ * Calls on one plan must not overlap.  The call synchronises the stream. */
 mm_status split_step_gpe_adjoint(mm_plan *plan, const void *psi0_dev, const void *gT_dev, void *g0_dev,
                                  double beta, double tau, int64_t nsteps, int64_t ckpt_every,
                                  void *stream);

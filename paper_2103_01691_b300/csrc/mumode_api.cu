@@ -30,6 +30,8 @@ struct mm_ctx {
     mm::ExpmBatch expmb;     // mm_expm_device, imaginary z
 };
 
+struct AdjCache;  // split_step_gpe_adjoint's matrices and buffers, kept with the plan
+
 struct mm_plan {
     mm_ctx *ctx = nullptr;
     bool hermite = false;
@@ -82,6 +84,7 @@ struct mm_plan {
     int hk_fuse = -1;                           // the time-dependent direction (0-based), or -1
     double2 *hk_phase[mm::kMaxDims] = {};       // per harmonic direction, padded length
     bool full_bands[mm::kMaxDims] = {};  // a device update switched direction v's bands to full
+    AdjCache *adj = nullptr;  // built by the first split_step_gpe_adjoint call (and again when tau changes)
     // CUDA graphs of whole step sequences, keyed by (call, tensor, nsteps, stream, tau, beta)
     bool use_graphs = true;
     std::map<std::tuple<int, const void *, int64_t, cudaStream_t, double, double>,
@@ -452,13 +455,19 @@ std::vector<double> harmonic_propagator(const mm_plan *p, int v, double s)
         for (int64_t l = 0; l < m; ++l) tmp[size_t(k * m + l)] = ph * p->fwd[v][size_t(k * m + l)];
     }
     std::vector<double> P(size_t(2 * m * m), 0.0);
-    for (int64_t a = 0; a < m; ++a)
-        for (int64_t b = 0; b < m; ++b) {
-            cd acc = 0;
-            for (int64_t k = 0; k < m; ++k) acc += p->bwd[v][size_t(a * m + k)] * tmp[size_t(k * m + b)];
-            P[size_t(2 * (a * m + b))] = acc.real();
-            P[size_t(2 * (a * m + b) + 1)] = acc.imag();
+    std::vector<cd> row(static_cast<size_t>(m));
+    for (int64_t a = 0; a < m; ++a) {  // row a of bwd tmp, accumulated along rows of tmp (contiguous)
+        std::fill(row.begin(), row.end(), cd(0));
+        for (int64_t k = 0; k < m; ++k) {
+            const double c = p->bwd[v][size_t(a * m + k)];
+            const cd *t = &tmp[size_t(k * m)];
+            for (int64_t b = 0; b < m; ++b) row[size_t(b)] += c * t[b];
         }
+        for (int64_t b = 0; b < m; ++b) {
+            P[size_t(2 * (a * m + b))] = row[size_t(b)].real();
+            P[size_t(2 * (a * m + b) + 1)] = row[size_t(b)].imag();
+        }
+    }
     return P;
 }
 
@@ -1026,10 +1035,13 @@ mm_status mumode_step_host(mm_plan *p, void *u_host, int64_t nsteps, void *strea
     return MM_OK;
 }
 
+void adj_release(mm_plan *p);
+
 void mm_plan_destroy(mm_plan *p)
 {
     if (!p) return;
     drop_graphs(p);
+    adj_release(p);
     for (int v = 0; v < mm::kMaxDims; ++v) {
         if (p->Edev[v]) cudaFree(p->Edev[v]);
         mm::tc_matrix_destroy(&p->Etc[v]);
@@ -1292,6 +1304,48 @@ mm_status apply_set(mm_plan *p, MatSet &S, const void *in, void *out, cudaStream
 
 }  // namespace
 
+struct AdjCache {
+    double tau = NAN;
+    MatSet Fh, Ff, Ah, Af;
+    void *ckpt = nullptr, *mid = nullptr, *tmp = nullptr;
+    size_t ckpt_bytes = 0, mid_bytes = 0, tmp_bytes = 0;
+    void release_sets()
+    {
+        Fh.release();
+        Ff.release();
+        Ah.release();
+        Af.release();
+        tau = NAN;
+    }
+    static bool grow(void *&buf, size_t &have, size_t need)
+    {
+        if (have >= need) return true;
+        if (buf) cudaFree(buf);
+        buf = nullptr;
+        have = 0;
+        if (cudaMalloc(&buf, need) != cudaSuccess) return false;
+        have = need;
+        return true;
+    }
+    bool reserve(size_t ck, size_t md, size_t tp)
+    {
+        return grow(ckpt, ckpt_bytes, ck) && grow(mid, mid_bytes, md) && grow(tmp, tmp_bytes, tp);
+    }
+    ~AdjCache()
+    {
+        release_sets();
+        if (ckpt) cudaFree(ckpt);
+        if (mid) cudaFree(mid);
+        if (tmp) cudaFree(tmp);
+    }
+};
+
+void adj_release(mm_plan *p)
+{
+    delete p->adj;
+    p->adj = nullptr;
+}
+
 extern "C" mm_status split_step_gpe_adjoint(mm_plan *p, const void *psi0, const void *gT, void *g0, double beta,
                                             double tau, int64_t nsteps, int64_t ckpt_every, void *stream)
 {
@@ -1311,51 +1365,38 @@ extern "C" mm_status split_step_gpe_adjoint(mm_plan *p, const void *psi0, const 
     }
     const int64_t nseg = (nsteps + ckpt_every - 1) / ckpt_every;
     const int64_t seglen = std::min(ckpt_every, nsteps);
-    MatSet Fh, Ff, Ah, Af;  // forward half / full, adjoint half / full
-    void *ckpt = nullptr, *mid = nullptr, *tmp = nullptr;
-    auto cleanup = [&]() {
-        Fh.release();
-        Ff.release();
-        Ah.release();
-        Af.release();
-        if (ckpt) cudaFree(ckpt);
-        if (mid) cudaFree(mid);
-        if (tmp) cudaFree(tmp);
-    };
-    if ((st = make_set(p, h, false, &Fh)) || (st = make_set(p, tau, false, &Ff)) || (st = make_set(p, h, true, &Ah)) ||
-        (st = make_set(p, tau, true, &Af))) {
-        cleanup();
-        return st;
+    // matrices of the forward and adjoint half / full steps, built once per tau; checkpoint
+    // buffers grown as needed; both kept with the plan for the next call
+    if (!p->adj) p->adj = new AdjCache;
+    AdjCache &C = *p->adj;
+    if (!(C.tau == tau)) {
+        C.release_sets();
+        if ((st = make_set(p, h, false, &C.Fh)) || (st = make_set(p, tau, false, &C.Ff)) ||
+            (st = make_set(p, h, true, &C.Ah)) || (st = make_set(p, tau, true, &C.Af))) {
+            C.release_sets();
+            return st;
+        }
+        C.tau = tau;
     }
-    if (cudaMalloc(&ckpt, bytes * size_t(nseg)) != cudaSuccess || cudaMalloc(&mid, bytes * size_t(seglen)) != cudaSuccess ||
-        cudaMalloc(&tmp, bytes) != cudaSuccess) {
-        cleanup();
+    MatSet &Fh = C.Fh, &Ff = C.Ff, &Ah = C.Ah, &Af = C.Af;
+    if (!C.reserve(bytes * size_t(nseg), bytes * size_t(seglen), bytes))
         return fail(MM_ERR_OOM, "checkpoint storage (%lld states)", (long long)(nseg + seglen + 1));
-    }
+    void *ckpt = C.ckpt, *mid = C.mid, *tmp = C.tmp;
     auto ck = [&](int64_t k) { return static_cast<char *>(ckpt) + bytes * size_t(k); };
     auto md = [&](int64_t k) { return static_cast<char *>(mid) + bytes * size_t(k); };
     auto nl = [&](void *x) -> mm_status {
         cudaError_t e = mm::simt_nonlinear_phase(fp64, p->count, tb, x, s);
         return e == cudaSuccess ? MM_OK : cuda_fail(e, "nonlinear phase");
     };
-    // forward sweep: checkpoints psi_{k c}; one step is L_h, N, L_h
+    // forward sweep: checkpoints psi_{k c}, each segment by split_step_gpe (the same Strang
+    // steps, the nonlinear phase fused into the last product) on the plan's scratch state
     cudaError_t e = cudaMemcpyAsync(tmp, psi0, bytes, cudaMemcpyDeviceToDevice, s);
-    if (e != cudaSuccess) {
-        cleanup();
-        return cuda_fail(e, "copy");
-    }
+    if (e != cudaSuccess) return cuda_fail(e, "copy");
     for (int64_t k = 0; k < nseg; ++k) {
         e = cudaMemcpyAsync(ck(k), tmp, bytes, cudaMemcpyDeviceToDevice, s);
-        if (e != cudaSuccess) {
-            cleanup();
-            return cuda_fail(e, "checkpoint copy");
-        }
+        if (e != cudaSuccess) return cuda_fail(e, "checkpoint copy");
         if (k == nseg - 1) break;
-        for (int64_t q = 0; q < ckpt_every; ++q)
-            if ((st = apply_set(p, Fh, tmp, tmp, s)) || (st = nl(tmp)) || (st = apply_set(p, Fh, tmp, tmp, s))) {
-                cleanup();
-                return st;
-            }
+        if ((st = split_step_gpe(p, tmp, beta, tau, ckpt_every, stream))) return st;
     }
     // reverse sweep, segment by segment: recompute the states before each
     // nonlinear stage, then g <- L_h^H (N^adj (L_h^H g)) per step, with the
@@ -1378,8 +1419,7 @@ extern "C" mm_status split_step_gpe_adjoint(mm_plan *p, const void *psi0, const 
             if (!st) st = apply_set(p, q > 0 ? Af : Ah, g0, g0, s);
         }
     }
-    cudaError_t e2 = cudaStreamSynchronize(s);  // the temporaries are freed below
-    cleanup();
+    cudaError_t e2 = cudaStreamSynchronize(s);
     if (st) return st;
     if (e2 != cudaSuccess) return cuda_fail(e2, "adjoint (sync)");
     return MM_OK;

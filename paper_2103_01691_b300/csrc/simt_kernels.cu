@@ -220,15 +220,19 @@ __global__ void __launch_bounds__(NT) dmma_mode_kernel(int64_t left, int64_t n, 
     }
 }
 
+__device__ __forceinline__ void sincos_of(float x, float &s, float &c) { sincosf(x, &s, &c); }
+__device__ __forceinline__ void sincos_of(double x, double &s, double &c) { sincos(x, &s, &c); }
+
 template <typename R>
 __global__ void nonlinear_phase_kernel(int64_t count, double tb, Elem<R, true> *psi)
 {
     for (int64_t q = blockIdx.x * int64_t(blockDim.x) + threadIdx.x; q < count;
          q += int64_t(gridDim.x) * blockDim.x) {
         Elem<R, true> v = psi[q];
-        const double th = tb * (double(v.re) * v.re + double(v.im) * v.im);
-        double s, c;
-        sincos(th, &s, &c);
+        // in the state's precision (FP32 for complex64, as in the tensor-core epilogue)
+        const R th = R(tb) * (v.re * v.re + v.im * v.im);
+        R s, c;
+        sincos_of(th, s, c);
         // v * exp(-i th)
         psi[q] = {R(v.re * c + v.im * s), R(v.im * c - v.re * s)};
     }
@@ -242,17 +246,18 @@ __global__ void nonlinear_adjoint_kernel(int64_t count, double tb, const Elem<R,
     for (int64_t q = blockIdx.x * int64_t(blockDim.x) + threadIdx.x; q < count;
          q += int64_t(gridDim.x) * blockDim.x) {
         const Elem<R, true> p = psi[q], gp = g[q];
-        const double th = tb * (double(p.re) * p.re + double(p.im) * p.im);
-        double sn, cs;
-        sincos(th, &sn, &cs);
+        // in the state's precision (FP32 for complex64)
+        const R t = R(tb), th = t * (p.re * p.re + p.im * p.im);
+        R sn, cs;
+        sincos_of(th, sn, cs);
         // psi' = p (cs - i sn)
-        const double pr = p.re * cs + p.im * sn, pi = p.im * cs - p.re * sn;
+        const R pr = p.re * cs + p.im * sn, pi = p.im * cs - p.re * sn;
         // Im(conj(g') psi') = g'.re psi'.im - g'.im psi'.re
-        const double im = double(gp.re) * pi - double(gp.im) * pr;
+        const R im = gp.re * pi - gp.im * pr;
         // e^{i th} g' = (cs + i sn) g'
-        const double gr = gp.re * cs - gp.im * sn + 2.0 * tb * im * p.re;
-        const double gi = gp.re * sn + gp.im * cs + 2.0 * tb * im * p.im;
-        g[q] = {R(gr), R(gi)};
+        const R gr = gp.re * cs - gp.im * sn + R(2) * t * im * p.re;
+        const R gi = gp.re * sn + gp.im * cs + R(2) * t * im * p.im;
+        g[q] = {gr, gi};
     }
 }
 

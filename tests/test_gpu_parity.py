@@ -682,6 +682,43 @@ def test_gpe_adjoint_matches_oracle(env, orc, prec, ckpt):
     assert err <= (1e-10 if prec == "fp64" else 2e-5)
 
 
+@pytest.mark.parametrize("prec", ["f16x6", "fp64"])
+def test_gpe_adjoint_repeated_calls(env, orc, prec):
+    """The adjoint keeps its matrices and checkpoint buffers with the plan:
+    a second call with the same tau gives the same gradient bit for bit, a
+    call with another tau rebuilds the matrices and matches the oracle, and
+    uneven segments (10 steps, checkpoints every 3) are handled."""
+    mm, ctx, torch = env
+    m, beta, steps = 14, 100.0, 10
+    plan = mm.HermitePlan(ctx, [m] * 3, prec=prec)
+    xo, _, Wo = orc.gauss_hermite(m)
+    w3 = orc.weight3(Wo)
+    dt = torch.complex128 if prec == "fp64" else torch.complex64
+    p0 = inputs.gpe_psi0(xo, Wo, seed=4)
+    p0 = p0 if prec == "fp64" else p0.astype(np.complex64)
+    target = inputs.gpe_target(xo, Wo)
+
+    def case(tau):
+        pT = orc.gpe_steps(p0.astype(complex), xo, Wo, beta, tau, steps)
+        gT = 2.0 * w3 * (pT - target)
+        g0 = plan.gpe_adjoint(to_gpu(torch, p0, dt), to_gpu(torch, gT, dt), beta, tau, steps, ckpt_every=3)
+        ref = orc.gpe_adjoint(p0.astype(complex), gT, xo, Wo, beta, tau, steps)
+        return g0.cpu().numpy(), ref
+
+    tol = 1e-10 if prec == "fp64" else 2e-5
+    ga, ref_a = case(1e-3)
+    gb, _ = case(1e-3)
+    assert np.array_equal(ga.view(np.float64 if prec == "fp64" else np.float32),
+                          gb.view(np.float64 if prec == "fp64" else np.float32))
+    gc, ref_c = case(2e-3)
+    gd, _ = case(1e-3)
+    print(f"adjoint repeated {prec}: rel_err tau=1e-3 {rel(ga, ref_a):.3e}, tau=2e-3 {rel(gc, ref_c):.3e}")
+    assert rel(ga, ref_a) <= tol and rel(gc, ref_c) <= tol
+    assert np.array_equal(ga.view(np.float64 if prec == "fp64" else np.float32),
+                          gd.view(np.float64 if prec == "fp64" else np.float32))
+    ctx.status()
+
+
 def test_gpe_autograd_gradient(env, orc):
     """torch.autograd through gpe_evolve gives the oracle's gradient of
     J = sum |psi_T - target|^2 W."""
