@@ -496,12 +496,27 @@ __device__ __forceinline__ int grid_exponent(float m)
 __global__ void max_abs_kernel(int64_t count, const float2 *__restrict__ u, unsigned *out)
 {
     float m = 0.0f;
-    for (int64_t q = blockIdx.x * int64_t(blockDim.x) + threadIdx.x; q < count; q += int64_t(gridDim.x) * blockDim.x) {
-        const float2 v = u[q];
-        m = fmaxf(m, fmaxf(fabsf(v.x), fabsf(v.y)));
+    // points [head, head + 2 pairs) two per 16-byte load; the first point (when u is not on a
+    // 16-byte boundary) and an odd last point one by one
+    const int64_t head = count > 0 && (reinterpret_cast<uintptr_t>(u) & 15) ? 1 : 0;
+    const int64_t pairs = (count - head) / 2;
+    const float4 *u4 = reinterpret_cast<const float4 *>(u + head);
+    const int64_t t0 = blockIdx.x * int64_t(blockDim.x) + threadIdx.x, stride = int64_t(gridDim.x) * blockDim.x;
+    for (int64_t q = t0; q < pairs; q += stride) {
+        const float4 v = u4[q];
+        m = fmaxf(m, fmaxf(fmaxf(fabsf(v.x), fabsf(v.y)), fmaxf(fabsf(v.z), fabsf(v.w))));
     }
-    unsigned b = __reduce_max_sync(0xffffffffu, __float_as_uint(m));
-    if ((threadIdx.x & 31) == 0 && b) atomicMax(out, b);
+    if (t0 == 0 && head) m = fmaxf(m, fmaxf(fabsf(u[0].x), fabsf(u[0].y)));
+    if (t0 == 0 && count > head + 2 * pairs) m = fmaxf(m, fmaxf(fabsf(u[count - 1].x), fabsf(u[count - 1].y)));
+    // one atomic per block: the warps' maxima meet in shared memory (blockDim.x = 256)
+    __shared__ unsigned wmax[8];
+    const unsigned b = __reduce_max_sync(0xffffffffu, __float_as_uint(m));
+    if ((threadIdx.x & 31) == 0) wmax[threadIdx.x / 32] = b;
+    __syncthreads();
+    if (threadIdx.x < 32) {
+        const unsigned c = __reduce_max_sync(0xffffffffu, threadIdx.x < 8 ? wmax[threadIdx.x] : 0u);
+        if (threadIdx.x == 0 && c) atomicMax(out, c);
+    }
 }
 
 // Logical offset of the first point of padded row r (the padded index over directions 2..d),
@@ -612,9 +627,18 @@ __global__ void merge_kernel(Dims dm, int64_t plane, int npieces, const uint16_t
                 }
             }
         }
+        // pairs of points as one 16-byte store where the pair starts on a 16-byte boundary
+        const bool even = (reinterpret_cast<uintptr_t>(u + lin) & 15) == 0;
 #pragma unroll
-        for (int k = 0; k < 8; ++k)
-            if (c0 + I(k) < n0) u[lin + I(k)] = make_float2(re[k] * s, im[k] * s);
+        for (int k = 0; k < 8; k += 2) {
+            if (even && c0 + I(k + 1) < n0) {
+                *reinterpret_cast<float4 *>(u + lin + I(k)) =
+                    make_float4(re[k] * s, im[k] * s, re[k + 1] * s, im[k + 1] * s);
+            } else {
+                if (c0 + I(k) < n0) u[lin + I(k)] = make_float2(re[k] * s, im[k] * s);
+                if (c0 + I(k + 1) < n0) u[lin + I(k + 1)] = make_float2(re[k + 1] * s, im[k + 1] * s);
+            }
+        }
     }
 }
 
@@ -646,7 +670,7 @@ cudaError_t tc_split(const TcState &st, int npieces, bool fixed, const void *u_c
         for (int v = 0; v < st.d; ++v) count *= st.n[v];
         cudaError_t e = cudaMemsetAsync(work, 0, sizeof(unsigned), s);
         if (e != cudaSuccess) return e;
-        max_abs_kernel<<<grid_for(count), 256, 0, s>>>(count, (const float2 *)u_c64, work);
+        max_abs_kernel<<<grid_for(count / 2 + 1), 256, 0, s>>>(count, (const float2 *)u_c64, work);
         count_launch();
         if (st.plane < (int64_t(1) << 31))
             split_kernel<true, uint32_t><<<grid_for(st.plane / 8), 256, 0, s>>>(
