@@ -1324,25 +1324,35 @@ __device__ __forceinline__ void epi_frag_store(const TcArgs &a, const CUtensorMa
 
 // Epilogue warps of the pair kernel: 8 (two per tensor-memory lane quarter, two chunks of 16
 // output rows each) for row tiles of 64, which spreads their shared-memory traffic over the
-// item and leaves the MMA issue freer; 16 for row tiles of 128 and for the nonlinear-phase
-// epilogue (EPI 1), whose per-value arithmetic needs the extra warps.
-__host__ __device__ constexpr int pair_epi_warps(int CH, int EPI) { return CH == 1 && EPI != 1 ? 8 : 16; }
-__host__ __device__ constexpr int pair_threads(int CH, int EPI) { return 32 * (2 + pair_epi_warps(CH, EPI)); }
+// item and leaves the MMA issue freer; 16 for row tiles of 128, for the nonlinear-phase
+// epilogue (EPI 1), whose per-value arithmetic needs the extra warps, and for batches (BATCH),
+// whose small problems give short items with much epilogue work per MMA.
+__host__ __device__ constexpr int pair_epi_warps(int CH, int EPI, bool BATCH)
+{
+    return CH == 1 && EPI != 1 && !BATCH ? 8 : 16;
+}
+__host__ __device__ constexpr int pair_threads(int CH, int EPI, bool BATCH)
+{
+    return 32 * (2 + pair_epi_warps(CH, EPI, BATCH));
+}
 // k-blocks of 16 per pipeline stage: 2 with 8 epilogue warps (K-major data boxes then have
 // 64-byte rows, 64-byte swizzled: half as many row requests per byte as 32-byte rows; MN-major
 // boxes 32 k-rows of 128 bytes), else 1.
-__host__ __device__ constexpr int pair_kb_per_stage(int CH, int EPI, bool)
+__host__ __device__ constexpr int pair_kb_per_stage(int CH, int EPI, bool BATCH)
 {
-    return pair_epi_warps(CH, EPI) == 8 ? 2 : 1;
+    return pair_epi_warps(CH, EPI, BATCH) == 8 ? 2 : 1;
 }
-// Pipeline stages: with row tiles of 64, 6 of 33 KB (8 epilogue warps, 24 KB of output staging;
-// K-major: 3 of 66 KB, two k-blocks each) or 5 (16 warps, 48 KB); with row tiles of 128, 4 of
-// 42 KB (48 KB of staging).
-__host__ __device__ constexpr int pair_stages(int CH, int EPI, bool KM)
+// Pipeline stages: with row tiles of 64, 3 of 66 KB (8 epilogue warps, two k-blocks each, 24 KB
+// of output staging) or 5 of 33 KB (16 warps, 48 KB); with row tiles of 128, 4 of 42 KB (48 KB
+// of staging).
+__host__ __device__ constexpr int pair_stages(int CH, int EPI, bool BATCH)
 {
-    return CH == 2 ? 4 : (pair_epi_warps(CH, EPI) == 8 ? 6 / pair_kb_per_stage(CH, EPI, KM) : 5);
+    return CH == 2 ? 4 : (pair_epi_warps(CH, EPI, BATCH) == 8 ? 3 : 5);
 }
-__host__ __device__ constexpr int pair_staging_bytes(int CH, int EPI) { return pair_epi_warps(CH, EPI) * kStagingPerWarp; }
+__host__ __device__ constexpr int pair_staging_bytes(int CH, int EPI, bool BATCH)
+{
+    return pair_epi_warps(CH, EPI, BATCH) * kStagingPerWarp;
+}
 
 // The same product with the tensor cores of the two SMs of a cluster
 // working as one (tcgen05 cta_group::2): the leader CTA (rank 0) issues
@@ -1365,7 +1375,7 @@ __host__ __device__ constexpr int pair_staging_bytes(int CH, int EPI) { return p
 // the peer's warps arrive on their own barrier, which one thread of the
 // peer relays to the leader's.
 template <int NP, bool KMAJOR, int EPI, bool FX, int CH, bool BATCH>
-__global__ void __launch_bounds__(pair_threads(CH, EPI), 1)
+__global__ void __launch_bounds__(pair_threads(CH, EPI, BATCH), 1)
     tc_pair_kernel(const __grid_constant__ CUtensorMap mapX, const __grid_constant__ CUtensorMap mapE,
                    const __grid_constant__ CUtensorMap mapY, TcArgs a, const TcPairProblem *__restrict__ many,
                    int nprob, int64_t total)
@@ -1373,12 +1383,12 @@ __global__ void __launch_bounds__(pair_threads(CH, EPI), 1)
     // BATCH: items P < total of many problems (records `many`, sorted by pairs_begin); `a` then
     // carries only what all problems share (row tiles of the same size, stage layout, error word)
     const int64_t items = BATCH ? total : a.pairs;
-    constexpr int kSt = pair_stages(CH, EPI, KMAJOR);
-    constexpr int KB = pair_kb_per_stage(CH, EPI, KMAJOR);  // k-blocks per stage
+    constexpr int kSt = pair_stages(CH, EPI, BATCH);
+    constexpr int KB = pair_kb_per_stage(CH, EPI, BATCH);  // k-blocks per stage
     extern __shared__ __align__(1024) uint8_t smem_raw[];
     uint8_t *smem = reinterpret_cast<uint8_t *>((reinterpret_cast<uintptr_t>(smem_raw) + 1023) & ~uintptr_t(1023));
-    uint8_t *staging = smem + kSt * a.stage_bytes;  // pair_epi_warps(CH, EPI) x kStagingPerWarp
-    uint64_t *full = reinterpret_cast<uint64_t *>(staging + pair_staging_bytes(CH, EPI));
+    uint8_t *staging = smem + kSt * a.stage_bytes;  // pair_epi_warps(CH, EPI, BATCH) x kStagingPerWarp
+    uint64_t *full = reinterpret_cast<uint64_t *>(staging + pair_staging_bytes(CH, EPI, BATCH));
     uint64_t *empty = full + kSt;
     uint64_t *accf = empty + kSt;  // [2]: accumulator set b holds a finished item
     uint64_t *tmem_empty = accf + 2;       // [2]: accumulator set b has been drained
@@ -1401,7 +1411,7 @@ __global__ void __launch_bounds__(pair_threads(CH, EPI), 1)
         for (int b = 0; b < 2; ++b) {
             mbar_init(&accf[b], 1);
             // this CTA's epilogue warps, and in the leader the peer's relay
-            mbar_init(&tmem_empty[b], pair_epi_warps(CH, EPI) + (rank == 0 ? 1 : 0));
+            mbar_init(&tmem_empty[b], pair_epi_warps(CH, EPI, BATCH) + (rank == 0 ? 1 : 0));
         }
         *abort_flag = 0;
         mbar_fence_init();
@@ -1590,7 +1600,7 @@ __global__ void __launch_bounds__(pair_threads(CH, EPI), 1)
         // ---------------- epilogue warps (both CTAs) ----------------
         const int ew = warp - 2;
         const int quarter = warp % 4;
-        constexpr int kGroups = pair_epi_warps(CH, EPI) / 4;  // warps per lane quarter
+        constexpr int kGroups = pair_epi_warps(CH, EPI, BATCH) / 4;  // warps per lane quarter
         constexpr int kPerWarp = 4 * CH / kGroups;       // chunks of 16 output rows per warp
         const int grp = ew / 4;  // the warp's chunks: grp, grp + kGroups, ..
         const int nchunks = a.it / 16;
@@ -2107,7 +2117,7 @@ static cudaError_t launch_tc(const CUtensorMap &mx, const CUtensorMap &me, const
 {
     cudaLaunchConfig_t cfg = {};
     cfg.gridDim = dim3(unsigned(grid));
-    cfg.blockDim = dim3(PAIR ? pair_threads(a.it > 64 ? 2 : 1, EPI) : kThreads);
+    cfg.blockDim = dim3(PAIR ? pair_threads(a.it > 64 ? 2 : 1, EPI, false) : kThreads);
     cfg.dynamicSmemBytes = size_t(smem);
     cfg.stream = s;
     cudaLaunchAttribute attr[2];
@@ -2180,9 +2190,10 @@ struct TcLaunch {
     int np = 0, grid = 0, smem = 0;
 };
 
+// batch: the launch is a record of a batched pair launch (its stage layout).
 static cudaError_t tc_setup(const TcState &si, const TcState &so, int mu, const TcMatrix &M, mm_prec prec,
                             const void *in_pieces, void *out_pieces, const TcEpilogue &epi, const TcScales &sc,
-                            int *d_err, TcVariant variant, TcLaunch *L)
+                            int *d_err, TcVariant variant, TcLaunch *L, bool batch = false)
 {
     const int NP = tc_pieces(prec);
     const bool fx = tc_fixed(prec);
@@ -2238,7 +2249,7 @@ static cudaError_t tc_setup(const TcState &si, const TcState &so, int mu, const 
     const TcMatrix::TcPairTiles *PT = pair_tiles(M, variant);
     const bool pair = PT != nullptr;
     // pair kernel: k-blocks per stage (two with 8 epilogue warps: one data box covers both)
-    const int kbs = pair ? pair_kb_per_stage(PT->it > 64 ? 2 : 1, epi.kind, km) : 1;
+    const int kbs = pair ? pair_kb_per_stage(PT->it > 64 ? 2 : 1, epi.kind, batch) : 1;
     if (pair) {
         // the pair kernel loads all 2 NP piece planes of a tile in one box
         if (km) {
@@ -2303,7 +2314,7 @@ static cudaError_t tc_setup(const TcState &si, const TcState &so, int mu, const 
             if (!encode(&my, out_pieces, 4, dims, str, box, CU_TENSOR_MAP_SWIZZLE_64B)) return cudaErrorInvalidValue;
         }
     }
-    const int smem = pair ? pair_stages(ch, epi.kind, km) * a.stage_bytes + pair_staging_bytes(ch, epi.kind) + 1024 + 256
+    const int smem = pair ? pair_stages(ch, epi.kind, batch) * a.stage_bytes + pair_staging_bytes(ch, epi.kind, batch) + 1024 + 256
                           : kStages * a.stage_bytes + 1024 + 256;
     L->km = km;
     L->pair = pair;
@@ -2481,7 +2492,7 @@ cudaError_t tc_pair_record_build(const TcState &si, const TcState &so, int mu, c
                                  int64_t *items)
 {
     TcLaunch L;
-    cudaError_t e = tc_setup(si, so, mu, M, prec, in_pieces, out_pieces, TcEpilogue{}, sc, nullptr, kTcPair64, &L);
+    cudaError_t e = tc_setup(si, so, mu, M, prec, in_pieces, out_pieces, TcEpilogue{}, sc, nullptr, kTcPair64, &L, true);
     if (e != cudaSuccess) return e;
     if (!L.pair || L.a.it > 64) return cudaErrorNotSupported;  // the batched pair kernel stores with TMA (CH = 1)
     TcPairProblem r;
@@ -2527,7 +2538,7 @@ cudaError_t tc_pair_batch_launch(const void *host_recs, const void *dev_recs, in
     a.err = d_err;
     const int NP = tc_pieces(prec);
     const bool fx = tc_fixed(prec);
-    const int smem = pair_stages(1, 0, kmajor) * a.stage_bytes + pair_staging_bytes(1, 0) + 1024 + 256;
+    const int smem = pair_stages(1, 0, true) * a.stage_bytes + pair_staging_bytes(1, 0, true) + 1024 + 256;
     const int64_t grid = 2 * (total < num_sms() / 2 ? total : num_sms() / 2);
     const auto *dev = reinterpret_cast<const TcPairProblem *>(dev_recs);
     auto go = [&](auto kern) -> cudaError_t {
@@ -2535,7 +2546,7 @@ cudaError_t tc_pair_batch_launch(const void *host_recs, const void *dev_recs, in
         if (e != cudaSuccess) return e;
         cudaLaunchConfig_t cfg = {};
         cfg.gridDim = dim3(unsigned(grid));
-        cfg.blockDim = dim3(pair_threads(1, 0));
+        cfg.blockDim = dim3(pair_threads(1, 0, true));
         cfg.dynamicSmemBytes = size_t(smem);
         cfg.stream = s;
         cudaLaunchAttribute attr[2];
