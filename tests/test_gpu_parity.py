@@ -810,6 +810,41 @@ def test_tensor_core_size_limit(env, orc):
     assert rel(u.cpu().numpy(), ref) <= TOL_STEP["fp32"]
     ctx.status()
 
+
+@pytest.mark.parametrize("prec", ["f16x6", "fp64"])
+def test_degenerate_inputs(env, orc, prec):
+    """Degenerate cases of the Tucker step: zero steps leave u untouched (bit
+    for bit); size-1 directions (the product is a scalar factor there) agree
+    with the oracle; an all-zero state stays exactly zero with a clean device
+    status (the fixed-point scale of a zero maximum); a direction of size 0
+    is refused with MM_ERR_SHAPE."""
+    mm, ctx, torch = env
+    tau = 1e-4
+    dt = torch.complex128 if prec == "fp64" else torch.complex64
+    tol = 1e-12 if prec == "fp64" else TOL_STEP["f16x6"]
+    for dims in ((1, 40, 24), (40, 1, 24), (33, 20, 1), (1, 1, 1)):
+        Es = [fd_schrodinger_E(mm, n, tau) for n in dims]
+        u0 = inputs.complex_normal(dims[::-1], seed=7)
+        u0 = u0 if prec == "fp64" else u0.astype(np.complex64)
+        plan = mm.TuckerPlan(ctx, dims, Es, prec=prec, dtype=dt)
+        u = to_gpu(torch, u0, dt)
+        plan.step(u, 0)
+        torch.cuda.synchronize()
+        assert np.array_equal(u.cpu().numpy(), u0), dims
+        plan.step(u, 3)
+        ref = orc.tucker(u0.astype(complex), [orc.expm_dirichlet_fd(n, 1j * tau) for n in dims], nsteps=3)
+        err = rel(u.cpu().numpy(), ref)
+        print(f"degenerate {prec} dims={dims}: rel_err={err:.3e}")
+        assert err <= tol, dims
+        z = torch.zeros_like(u)
+        plan.step(z, 2)
+        torch.cuda.synchronize()
+        assert not torch.any(z != 0), dims
+        ctx.status()
+    Es = [fd_schrodinger_E(mm, n, tau) for n in (4, 4)]
+    with pytest.raises(RuntimeError, match="MM_ERR_SHAPE"):
+        mm.TuckerPlan(ctx, (0, 4, 4), [np.zeros((0, 0))] + Es, prec=prec, dtype=dt)
+
 def test_batched_pair_kernel_matches_one_sm_batch(env, monkeypatch):
     """Batched launches run the CTA-pair kernel over the problem records; the
     older one-SM-style batched kernel (forced with MM_TC_1SM=1 at batch
