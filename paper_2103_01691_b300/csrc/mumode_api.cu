@@ -77,6 +77,10 @@ struct mm_plan {
     double h0norm[mm::kMaxDims] = {}, gnorm[mm::kMaxDims] = {};  // ||H0 - mu I||_1, ||G||_1
     double hshift[mm::kMaxDims] = {};  // mu: the middle of H0's diagonal range, taken out as a phase
     double2 *Ebatch[mm::kMaxDims] = {};  // the exponentials of a chunk of steps (expmb.cap matrices)
+    // tensor-core plans: exponentials at kInterpNodes Chebyshev nodes in f per direction, and the
+    // device interpolation weights of a chunk (cap x kInterpNodes)
+    double2 *hk_nodesE[mm::kMaxDims] = {};
+    double *hk_w = nullptr;
     void *coef = nullptr;  // coefficient tensor of hkmp_evolve
     mm::ExpmBatch expmb;
     // HKMP with one time-dependent direction and harmonic others: a step is that direction's
@@ -1063,8 +1067,10 @@ void mm_plan_destroy(mm_plan *p)
         if (p->H0dev[v]) cudaFree(p->H0dev[v]);
         if (p->Gdev[v]) cudaFree(p->Gdev[v]);
         if (p->Ebatch[v]) cudaFree(p->Ebatch[v]);
+        if (p->hk_nodesE[v]) cudaFree(p->hk_nodesE[v]);
     }
     if (p->coef) cudaFree(p->coef);
+    if (p->hk_w) cudaFree(p->hk_w);
     for (int v = 0; v < mm::kMaxDims; ++v)
         if (p->hk_phase[v]) cudaFree(p->hk_phase[v]);
     mm::expm_batch_destroy(&p->expmb);
@@ -1910,6 +1916,14 @@ extern "C" mm_status hkmp_plan_create(mm_ctx *ctx, int d, const int64_t *n, cons
         for (int v = 0; v < d && e == cudaSuccess; ++v)
             if (p->H0dev[v])
                 e = cudaMalloc(&p->Ebatch[v], sizeof(double2) * size_t(cap) * size_t(p->n[v] * p->n[v]));
+        // interpolation in f (tensor-core plans, when a batch holds the nodes)
+        const int K = mm::kInterpNodes;
+        if (e == cudaSuccess && p->tc && cap > K) {
+            e = cudaMalloc(&p->hk_w, sizeof(double) * size_t(cap) * K);
+            for (int v = 0; v < d && e == cudaSuccess; ++v)
+                if (p->H0dev[v])
+                    e = cudaMalloc(&p->hk_nodesE[v], sizeof(double2) * size_t(K) * size_t(p->n[v] * p->n[v]));
+        }
     }
     if (e != cudaSuccess) {
         mm_plan_destroy(p);
@@ -1933,15 +1947,64 @@ extern "C" mm_status hkmp_evolve(mm_plan *p, void *psi, int64_t nsteps, const do
     // The exponentials exp(-i tau (H0 + f G)) of the time-dependent directions
     // for a chunk of steps [k0, k0 + cnt), computed together (batched).
     const int cap = p->expmb.cap;
+    // Tensor-core plans with more than kInterpNodes steps in a chunk: E(f) = exp(-i tau (H0 + f G))
+    // is an entire function of f whose k-th derivative is at most (tau ||G||)^k in norm, so its
+    // interpolant at K Chebyshev points of [f_lo, f_hi] errs by about
+    // 2 (tau ||G|| (f_hi - f_lo) / 4)^K / K!, below 1e-18 for K = 12 at tau ||G|| < 1 and
+    // f_hi - f_lo <= 1 (the pieces hold 2^-34 of a row's scale).  The chunk then takes K
+    // exponentials and one combination instead of cnt exponentials.  The node values and weights
+    // stay in host memory until the call's final synchronisation (their copies are asynchronous).
+    const int K = mm::kInterpNodes;
+    const bool interp = p->tc && p->hk_w != nullptr;
+    const int64_t nchunks = (nsteps + cap - 1) / cap;
+    std::vector<double> ihost(interp ? size_t(nchunks) * size_t(K + size_t(cap) * K) : 0);
     auto chunk = [&](int64_t k0, int cnt) -> mm_status {
-        double fmax = 0.0;
-        for (int q = 0; q < cnt; ++q) fmax = std::max(fmax, std::fabs(f_mid[k0 + q]));
+        double fmax = 0.0, flo = f_mid[k0], fhi = f_mid[k0];
+        for (int q = 0; q < cnt; ++q) {
+            fmax = std::max(fmax, std::fabs(f_mid[k0 + q]));
+            flo = std::min(flo, f_mid[k0 + q]);
+            fhi = std::max(fhi, f_mid[k0 + q]);
+        }
+        const bool use_interp = interp && cnt > K && fhi > flo;
+        double *nodes = nullptr;
+        if (use_interp) {
+            nodes = ihost.data() + size_t(k0 / cap) * size_t(K + size_t(cap) * K);
+            double *W = nodes + K, bw[mm::kInterpNodes];
+            const double mid = 0.5 * (flo + fhi), half = 0.5 * (fhi - flo), pi = 3.14159265358979323846;
+            for (int j = 0; j < K; ++j) {  // Chebyshev points of the first kind, barycentric weights
+                const double th = (2 * j + 1) * pi / (2 * K);
+                nodes[j] = mid + half * std::cos(th);
+                bw[j] = (j % 2 ? -1.0 : 1.0) * std::sin(th);
+            }
+            for (int q = 0; q < cnt; ++q) {  // Lagrange basis at f_k (barycentric form)
+                const double x = f_mid[k0 + q];
+                double *w = W + size_t(q) * K, sum = 0.0;
+                int hit = -1;
+                for (int j = 0; j < K && hit < 0; ++j)
+                    if (x == nodes[j]) hit = j;
+                for (int j = 0; j < K; ++j) {
+                    w[j] = hit >= 0 ? (j == hit ? 1.0 : 0.0) : bw[j] / (x - nodes[j]);
+                    sum += w[j];
+                }
+                for (int j = 0; j < K; ++j) w[j] /= sum;
+            }
+            cudaError_t e = cudaMemcpyAsync(p->hk_w, W, sizeof(double) * size_t(cnt) * K, cudaMemcpyHostToDevice, s);
+            if (e != cudaSuccess) return cuda_fail(e, "interpolation weights");
+        }
         for (int v = 0; v < p->d; ++v) {
             if (!p->H0dev[v]) continue;
             const double bound = p->h0norm[v] + fmax * p->gnorm[v];
             // tensor-core plans split the exponentials into pieces: scaled norms up to 2 suffice
-            cudaError_t e = mm::expm_imag_batched(&p->expmb, int(p->n[v]), p->H0dev[v], p->Gdev[v], f_mid + k0, cnt,
-                                                  -p->tau, bound, p->Ebatch[v], s, p->hshift[v], p->tc ? 2.0 : 1.0);
+            cudaError_t e;
+            if (use_interp) {
+                e = mm::expm_imag_batched(&p->expmb, int(p->n[v]), p->H0dev[v], p->Gdev[v], nodes, K, -p->tau, bound,
+                                          p->hk_nodesE[v], s, p->hshift[v], 2.0);
+                if (e == cudaSuccess)
+                    e = mm::combine_interp_nodes(int(p->n[v]), cnt, p->hk_w, p->hk_nodesE[v], p->Ebatch[v], s);
+            } else {
+                e = mm::expm_imag_batched(&p->expmb, int(p->n[v]), p->H0dev[v], p->Gdev[v], f_mid + k0, cnt,
+                                          -p->tau, bound, p->Ebatch[v], s, p->hshift[v], p->tc ? 2.0 : 1.0);
+            }
             if (e != cudaSuccess) return cuda_fail(e, "device expm");
         }
         return MM_OK;

@@ -532,6 +532,48 @@ def test_hkmp_vs_oracle(env, orc, prec, tdir, variant):
 
 # ---------------------------------------------------------- pipe flow (section 4.2)
 
+
+@pytest.mark.parametrize("tdir,variant", [(3, None), (1, "one_sm")])
+def test_hkmp_interpolated_exponentials(env, orc, tdir, variant):
+    """Tensor-core HKMP with more than 12 steps in a chunk takes the chunk's
+    exponentials from 12 Chebyshev nodes in f (interpolation error far below
+    the pieces' resolution).  Against the oracle's literal Magnus steps, and
+    against the same evolution in calls of at most 12 steps (each chunk then
+    takes one exponential per step).  The two runs differ mostly by the
+    short calls' extra transforms to and from coefficient space (about 1e-7
+    relative each)."""
+    mm, ctx, torch = env
+    n = (40, 24, 36)
+    xs, Ws = _hkmp_case(orc, n)
+    Vs, Us = inputs.hkmp_potentials(*xs)
+    if tdir != 3:
+        Us = tuple(np.array(xs[v]) if v == tdir - 1 else None for v in range(3))
+    tau, steps = 0.025, 40
+    f_mid = inputs.hkmp_f_mid(tau, steps)
+    psi0 = inputs.hkp_psi0(*xs).astype(np.complex64)
+    ref = orc.hkmp_steps(psi0.astype(complex), xs, Ws, Vs, Us, tau, f_mid)
+    xl = [mm.gauss_hermite(v)[0] for v in n]
+    _, Ul = inputs.hkmp_potentials(*xl)
+    if tdir != 3:
+        Ul = tuple(np.array(xl[v]) if v == tdir - 1 else None for v in range(3))
+    plan = mm.HKMPPlan(ctx, n, [None, None, None], list(Ul), tau, prec="f16x6")
+    if variant:
+        assert mm.lib().mm_plan_set_config(plan.handle, mm.VARIANTS.index(variant), None) == 0
+    psi = to_gpu(torch, psi0, torch.complex64)
+    plan.evolve(psi, f_mid)
+    short = to_gpu(torch, psi0, torch.complex64)
+    for k0 in range(0, steps, 10):
+        plan.evolve(short, f_mid[k0:k0 + 10])
+    w3 = Ws[2][:, None, None] * Ws[1][None, :, None] * Ws[0][None, None, :]
+    got, direct = psi.cpu().numpy(), short.cpu().numpy()
+    err, err_direct = orc.rel_l2(got, ref, w3), orc.rel_l2(direct, ref, w3)
+    diff = orc.rel_l2(got, direct, w3)
+    print(f"HKMP interpolated dir {tdir} {variant or 'default'}: rel_err={err:.3e}, "
+          f"direct={err_direct:.3e}, interpolated vs direct={diff:.3e}")
+    assert err <= 5e-6 and err_direct <= 5e-6
+    assert diff <= 2e-6
+    ctx.status()
+
 @pytest.mark.parametrize("prec,n_r,n_z,T", [("fp64dmma", 40, 56, 4.0), ("fp64", 40, 56, 4.0),
                                              ("fp64dmma", 257, 301, 1.0), ("fp64", 257, 301, 4.0)])
 def test_pipe_flow_vs_oracle(env, orc, prec, n_r, n_z, T):
