@@ -143,13 +143,22 @@ __host__ __device__ static double row_scale(double sum_abs)
     return ldexp(1.0, mant == 0.5 ? e - 1 : e);
 }
 
+// Smallest power of two >= n.
+__host__ __device__ static int64_t pow2_at_least(int64_t n)
+{
+    int64_t p = 1;
+    while (p < n) p *= 2;
+    return p;
+}
+
 // The pieces of one complex entry (C, S) / r: bits[p][0] (C), bits[p][1] (S).
 __host__ __device__ static void entry_pieces(double c, double s, double r, int npieces, bool fixed, uint16_t bits[3][2])
 {
     double rest[2] = {c, s};
-    if (fixed) {
-        rest[0] /= r;
-        rest[1] /= r;
+    if (fixed) {  // r is a power of two: its reciprocal and the products are exact
+        const double inv = 1.0 / r;
+        rest[0] *= inv;
+        rest[1] *= inv;
     }
     for (int p = 0; p < npieces; ++p)
         for (int q = 0; q < 2; ++q) {
@@ -178,13 +187,21 @@ mm_status tc_matrix_host(const double *E, int64_t m, int64_t n, int npieces, boo
     const int64_t rows = int64_t(npieces) * M.ni * kBlocks * M.it;
     h.assign(size_t(rows * M.k_pad), 0);
     rho.assign(size_t(M.ni) * M.it, 1.0f);
+    // the row sums of |C| + |S| by a fixed pairwise tree (zero-padded to a power of two,
+    // s[j] += s[j + h] for h = P/2 .. 1): matrix_update_kernel adds in the same order
+    const int64_t P = pow2_at_least(n);
+    std::vector<double> tree(size_t(P), 0.0);
     for (int64_t i = 0; i < m; ++i) {
-        double sum_abs = 0.0, sum_mod = 0.0;
+        double sum_mod = 0.0;
+        std::fill(tree.begin(), tree.end(), 0.0);
         for (int64_t j = 0; j < n; ++j) {
             const double c = E[2 * (i * n + j)], sv = E[2 * (i * n + j) + 1];
-            sum_abs += std::fabs(c) + std::fabs(sv);
+            tree[size_t(j)] = std::fabs(c) + std::fabs(sv);
             sum_mod += std::hypot(c, sv);
         }
+        for (int64_t h = P / 2; h >= 1; h /= 2)
+            for (int64_t j = 0; j < h; ++j) tree[size_t(j)] += tree[size_t(j + h)];
+        const double sum_abs = tree[0];
         M.row_norm = std::max(M.row_norm, sum_mod);
         const double r = fixed ? row_scale(sum_abs) : 1.0;
         rho[size_t(i)] = float(r);
@@ -348,13 +365,18 @@ __global__ void matrix_update_kernel(const double2 *__restrict__ E, int64_t m, i
 {
     const int64_t i = blockIdx.x;
     if (i >= m) return;
-    extern __shared__ double absrow[];  // |C_ij| + |S_ij| of the row (n doubles)
+    extern __shared__ double absrow[];  // |C_ij| + |S_ij| of the row, zero-padded to a power of two
     __shared__ double r_sh;
-    for (int64_t j = threadIdx.x; j < n; j += blockDim.x) absrow[j] = fabs(E[i * n + j].x) + fabs(E[i * n + j].y);
+    const int64_t P = pow2_at_least(n);
+    for (int64_t j = threadIdx.x; j < P; j += blockDim.x)
+        absrow[j] = j < n ? fabs(E[i * n + j].x) + fabs(E[i * n + j].y) : 0.0;
     __syncthreads();
+    for (int64_t h = P / 2; h >= 1; h /= 2) {  // the host's pairwise tree
+        for (int64_t j = threadIdx.x; j < h; j += blockDim.x) absrow[j] += absrow[j + h];
+        __syncthreads();
+    }
     if (threadIdx.x == 0) {
-        double sum_abs = 0.0;
-        for (int64_t j = 0; j < n; ++j) sum_abs += absrow[j];  // the host's order
+        const double sum_abs = absrow[0];
         const double r = fixed ? row_scale(sum_abs) : 1.0;
         r_sh = r;
         if (rho) rho[i] = float(r);
@@ -394,8 +416,8 @@ __global__ void matrix_update_kernel(const double2 *__restrict__ E, int64_t m, i
 cudaError_t tc_matrix_update(TcMatrix &M, const double2 *E, cudaStream_t s)
 {
     if (!M.pieces || !E || (M.fixed && !M.rho)) return cudaErrorInvalidValue;
-    const size_t smem = sizeof(double) * size_t(M.n_in);
-    if (smem > 48 * 1024) return cudaErrorInvalidValue;  // n_in <= 6144
+    const size_t smem = sizeof(double) * size_t(pow2_at_least(M.n_in));
+    if (smem > 48 * 1024) return cudaErrorInvalidValue;  // n_in <= 4096
     matrix_update_kernel<<<unsigned(M.n_out), 128, smem, s>>>(
         E, M.n_out, M.n_in, M.npieces, M.fixed, M.ni, M.it, M.k_pad / 16, static_cast<uint16_t *>(M.pieces), M.rho,
         static_cast<uint16_t *>(M.pair[0].pieces), M.pair[0].it, static_cast<uint16_t *>(M.pair[1].pieces),
