@@ -308,19 +308,20 @@ cudaError_t expm_batch_init(ExpmBatch *w, int n, int cap)
 
 // E_k = sum_j W[k][j] N_j (complex n x n matrices N_j, real weights): each thread holds one
 // entry of the `nodes` node matrices and writes that entry of the cnt combinations.
-__global__ void combine_nodes(int64_t nn, int cnt, const double *__restrict__ W, const double2 *__restrict__ N,
+__global__ void combine_nodes(int64_t nn, int cnt, int K, const double *__restrict__ W, const double2 *__restrict__ N,
                               double2 *__restrict__ E)
 {
     constexpr int kMax = kInterpNodes;
     for (int64_t e = blockIdx.x * int64_t(blockDim.x) + threadIdx.x; e < nn; e += int64_t(gridDim.x) * blockDim.x) {
         double2 v[kMax];
 #pragma unroll
-        for (int j = 0; j < kMax; ++j) v[j] = N[int64_t(j) * nn + e];
+        for (int j = 0; j < kMax; ++j) v[j] = j < K ? N[int64_t(j) * nn + e] : make_double2(0.0, 0.0);
         for (int k = 0; k < cnt; ++k) {
             double re = 0.0, im = 0.0;
 #pragma unroll
             for (int j = 0; j < kMax; ++j) {
-                const double w = __ldg(W + k * kMax + j);
+                if (j >= K) break;
+                const double w = __ldg(W + k * K + j);
                 re += w * v[j].x;
                 im += w * v[j].y;
             }
@@ -329,10 +330,12 @@ __global__ void combine_nodes(int64_t nn, int cnt, const double *__restrict__ W,
     }
 }
 
-cudaError_t combine_interp_nodes(int n, int cnt, const double *W_dev, const double2 *nodes, double2 *E, cudaStream_t s)
+cudaError_t combine_interp_nodes(int n, int cnt, int K, const double *W_dev, const double2 *nodes, double2 *E,
+                                 cudaStream_t s)
 {
+    if (K < 1 || K > kInterpNodes) return cudaErrorInvalidValue;
     const int64_t nn = int64_t(n) * n;
-    combine_nodes<<<blocks_for(nn), 256, 0, s>>>(nn, cnt, W_dev, nodes, E);
+    combine_nodes<<<blocks_for(nn), 256, 0, s>>>(nn, cnt, K, W_dev, nodes, E);
     count_launch();
     return cudaGetLastError();
 }

@@ -133,11 +133,12 @@ struct ExpmBatch {
 cudaError_t expm_batch_init(ExpmBatch *w, int n, int cap);
 void expm_batch_destroy(ExpmBatch *w);
 int expm_batch_capacity(int n);  // batch entries that keep the workspace near 1 GB (1..64)
-// Interpolation of exp(z (A + f B)) in f: the exponentials at kInterpNodes Chebyshev nodes of a
-// range of f (nodes[j], n x n complex each) and, for cnt values f_k, weights W[k][j] (the
-// Lagrange basis at f_k, device, cnt x kInterpNodes) give E_k = sum_j W[k][j] nodes[j].
+// Interpolation of exp(z (A + f B)) in f: the exponentials at K <= kInterpNodes Chebyshev nodes
+// of a range of f (nodes[j], n x n complex each) and, for cnt values f_k, weights W[k][j] (the
+// Lagrange basis at f_k, device, cnt x K) give E_k = sum_j W[k][j] nodes[j].
 constexpr int kInterpNodes = 12;
-cudaError_t combine_interp_nodes(int n, int cnt, const double *W_dev, const double2 *nodes, double2 *E, cudaStream_t s);
+cudaError_t combine_interp_nodes(int n, int cnt, int K, const double *W_dev, const double2 *nodes, double2 *E,
+                                 cudaStream_t s);
 // mu: a diagonal shift taken out as the phase exp(i w mu); norm_bound then bounds ||A + f_k B - mu I||_1.
 // theta: the largest scaled norm ||X||_1 the series may see.  1 gives full FP64 accuracy
 // (truncation below 1e-19); 2 bounds the truncation by 2^20 / 20! < 5e-13, enough for matrices

@@ -1947,17 +1947,17 @@ extern "C" mm_status hkmp_evolve(mm_plan *p, void *psi, int64_t nsteps, const do
     // The exponentials exp(-i tau (H0 + f G)) of the time-dependent directions
     // for a chunk of steps [k0, k0 + cnt), computed together (batched).
     const int cap = p->expmb.cap;
-    // Tensor-core plans with more than kInterpNodes steps in a chunk: E(f) = exp(-i tau (H0 + f G))
-    // is an entire function of f whose k-th derivative is at most (tau ||G||)^k in norm, so its
-    // interpolant at K Chebyshev points of [f_lo, f_hi] errs by about
-    // 2 (tau ||G|| (f_hi - f_lo) / 4)^K / K!, below 1e-18 for K = 12 at tau ||G|| < 1 and
-    // f_hi - f_lo <= 1 (the pieces hold 2^-34 of a row's scale).  The chunk then takes K
-    // exponentials and one combination instead of cnt exponentials.  The node values and weights
-    // stay in host memory until the call's final synchronisation (their copies are asynchronous).
-    const int K = mm::kInterpNodes;
+    // Tensor-core plans: E(f) = exp(-i tau (H0 + f G)) is an entire function of f whose k-th
+    // derivative is at most (tau ||G||)^k in norm, so its interpolant at K Chebyshev points of
+    // [f_lo, f_hi] errs by at most 2 (tau ||G|| (f_hi - f_lo) / 4)^K / K!.  K is the smallest
+    // (4..12) that puts this below 1e-14 (the pieces hold 2^-34 of a row's scale); a chunk of more
+    // than K steps then takes K exponentials and one combination instead of one exponential per
+    // step.  The node values and weights stay in host memory until the call's final
+    // synchronisation (their copies are asynchronous).
+    const int Kmax = mm::kInterpNodes;
     const bool interp = p->tc && p->hk_w != nullptr;
     const int64_t nchunks = (nsteps + cap - 1) / cap;
-    std::vector<double> ihost(interp ? size_t(nchunks) * size_t(K + size_t(cap) * K) : 0);
+    std::vector<double> ihost(interp ? size_t(nchunks) * size_t(Kmax + size_t(cap) * Kmax) : 0);
     auto chunk = [&](int64_t k0, int cnt) -> mm_status {
         double fmax = 0.0, flo = f_mid[k0], fhi = f_mid[k0];
         for (int q = 0; q < cnt; ++q) {
@@ -1965,11 +1965,25 @@ extern "C" mm_status hkmp_evolve(mm_plan *p, void *psi, int64_t nsteps, const do
             flo = std::min(flo, f_mid[k0 + q]);
             fhi = std::max(fhi, f_mid[k0 + q]);
         }
-        const bool use_interp = interp && cnt > K && fhi > flo;
+        // the fewest nodes whose error bound is below 1e-14, over the time-dependent directions
+        int K = 0;
+        for (int v = 0; v < p->d; ++v) {
+            if (!p->H0dev[v]) continue;
+            const double x = std::fabs(p->tau) * p->gnorm[v] * (fhi - flo) / 4.0;
+            int k = 4;
+            double bound = 2.0 * std::pow(x, 4) / 24.0;
+            while (bound > 1e-14 && k < Kmax) {
+                ++k;
+                bound *= x / k;
+            }
+            if (bound > 1e-14) k = Kmax + 1;  // too wide a range: no interpolation
+            K = std::max(K, k);
+        }
+        const bool use_interp = interp && K <= Kmax && cnt > K && fhi > flo;
         double *nodes = nullptr;
         if (use_interp) {
-            nodes = ihost.data() + size_t(k0 / cap) * size_t(K + size_t(cap) * K);
-            double *W = nodes + K, bw[mm::kInterpNodes];
+            nodes = ihost.data() + size_t(k0 / cap) * size_t(Kmax + size_t(cap) * Kmax);
+            double *W = nodes + Kmax, bw[mm::kInterpNodes];
             const double mid = 0.5 * (flo + fhi), half = 0.5 * (fhi - flo), pi = 3.14159265358979323846;
             for (int j = 0; j < K; ++j) {  // Chebyshev points of the first kind, barycentric weights
                 const double th = (2 * j + 1) * pi / (2 * K);
@@ -2000,7 +2014,7 @@ extern "C" mm_status hkmp_evolve(mm_plan *p, void *psi, int64_t nsteps, const do
                 e = mm::expm_imag_batched(&p->expmb, int(p->n[v]), p->H0dev[v], p->Gdev[v], nodes, K, -p->tau, bound,
                                           p->hk_nodesE[v], s, p->hshift[v], 2.0);
                 if (e == cudaSuccess)
-                    e = mm::combine_interp_nodes(int(p->n[v]), cnt, p->hk_w, p->hk_nodesE[v], p->Ebatch[v], s);
+                    e = mm::combine_interp_nodes(int(p->n[v]), cnt, K, p->hk_w, p->hk_nodesE[v], p->Ebatch[v], s);
             } else {
                 e = mm::expm_imag_batched(&p->expmb, int(p->n[v]), p->H0dev[v], p->Gdev[v], f_mid + k0, cnt,
                                           -p->tau, bound, p->Ebatch[v], s, p->hshift[v], p->tc ? 2.0 : 1.0);
