@@ -1002,9 +1002,12 @@ mm_status mumode_step(mm_plan *p, void *u_dev, int64_t nsteps, void *stream)
     cudaStream_t s = (cudaStream_t)stream;
     if (p->hermite) return fail(MM_ERR_INVALID_ARG, "mumode_step needs a Tucker plan (use hermite_ho_step)");
     if (!p->tc) {
-        for (int64_t k = 0; k < nsteps; ++k)
-            if ((st = simt_sweep(p, p->Edev, u_dev, s))) return st;
-        return MM_OK;
+        return run_graphed(p, 0, u_dev, nsteps, s, 0.0, 0.0, [&]() -> mm_status {
+            mm_status r;
+            for (int64_t k = 0; k < nsteps; ++k)
+                if ((r = simt_sweep(p, p->Edev, u_dev, s))) return r;
+            return MM_OK;
+        });
     }
     return run_graphed(p, 0, u_dev, nsteps, s, 0.0, 0.0, [&]() -> mm_status {
         mm_status r;

@@ -112,6 +112,53 @@ __global__ void __launch_bounds__(NT) simt_mode_kernel(int64_t left, int64_t n, 
     }
 }
 
+// Small products (fewer 64 x 64 tiles than two per SM): 16 x 16 tiles, one output per thread,
+// so that more SMs share the work (B300's FP64 rate per SM is low).  Each output accumulates
+// over j in the same order as in simt_mode_kernel.
+constexpr int SB = 16;
+template <typename R, bool C>
+__global__ void __launch_bounds__(SB * SB) simt_mode_kernel_small(int64_t left, int64_t n, int64_t right, int64_t m,
+                                                                  const Elem<R, C> *__restrict__ L,
+                                                                  const Elem<R, C> *__restrict__ X,
+                                                                  Elem<R, C> *__restrict__ Y)
+{
+    using E = Elem<R, C>;
+    __shared__ E sL[SB][SB + 1];  // [k][row]
+    __shared__ E sX[SB][SB + 1];  // [k][column]
+    const int t = threadIdx.x, tx = t % SB, ty = t / SB;
+    const int64_t i0 = int64_t(blockIdx.y) * SB, c0 = int64_t(blockIdx.x) * SB;
+    const int64_t ncols = left * right;
+    const bool fiber_contig = (left == 1);
+    E acc = E::zero();
+    for (int64_t k0 = 0; k0 < n; k0 += SB) {
+        {
+            const int64_t i = i0 + ty, j = k0 + tx;  // consecutive threads walk j (row-major L)
+            sL[tx][ty] = (i < m && j < n) ? L[i * n + j] : E::zero();
+        }
+        {
+            int kk, cc;
+            if (fiber_contig) { kk = tx; cc = ty; }  // j contiguous in memory
+            else { cc = tx; kk = ty; }               // l contiguous in memory
+            const int64_t c = c0 + cc, j = k0 + kk;
+            E v = E::zero();
+            if (c < ncols && j < n) {
+                const int64_t r = c / left, l = c - r * left;
+                v = X[(r * n + j) * left + l];
+            }
+            sX[kk][cc] = v;
+        }
+        __syncthreads();
+#pragma unroll
+        for (int kk = 0; kk < SB; ++kk) acc.fma(sL[kk][ty], sX[kk][tx]);
+        __syncthreads();
+    }
+    const int64_t i = i0 + ty, c = c0 + tx;
+    if (i < m && c < ncols) {
+        const int64_t r = c / left, l = c - r * left;
+        Y[(r * m + i) * left + l] = acc;
+    }
+}
+
 // ---- FP64 on the tensor cores (legacy warp MMA m8n8k4, the only FP64 MMA form) -------
 //
 // D (8 x 8) += A (8 x 4) B (4 x 8) per instruction: lane t holds A[t/4][t%4], B[t%4][t/4] and
@@ -305,9 +352,24 @@ cudaError_t simt_mode_product(bool fp64, bool cplx, int64_t left, int64_t n, int
     const int64_t ncols = left * right;
     dim3 grid(unsigned((ncols + BN - 1) / BN), unsigned((m + BM - 1) / BM));
     if (grid.y > 65535u) return cudaErrorInvalidConfiguration;
+    static int sms = 0;  // SM count of the device, queried once
+    if (!sms) {
+        int dev = 0;
+        cudaGetDevice(&dev);
+        cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+        if (sms <= 0) sms = 148;
+    }
+    const bool small = int64_t(grid.x) * grid.y < 2 * int64_t(sms) && (m + SB - 1) / SB <= 65535;
+    const dim3 grid_s(unsigned((ncols + SB - 1) / SB), unsigned((m + SB - 1) / SB));
 #define MM_LAUNCH(R, C)                                                                                  \
-    simt_mode_kernel<R, C><<<grid, NT, 0, s>>>(left, n, right, m, (const Elem<R, C> *)L,                 \
-                                               (const Elem<R, C> *)X, (Elem<R, C> *)Y)
+    do {                                                                                                 \
+        if (small)                                                                                       \
+            simt_mode_kernel_small<R, C><<<grid_s, SB * SB, 0, s>>>(                                     \
+                left, n, right, m, (const Elem<R, C> *)L, (const Elem<R, C> *)X, (Elem<R, C> *)Y);       \
+        else                                                                                             \
+            simt_mode_kernel<R, C><<<grid, NT, 0, s>>>(left, n, right, m, (const Elem<R, C> *)L,         \
+                                                       (const Elem<R, C> *)X, (Elem<R, C> *)Y);          \
+    } while (0)
     if (fp64 && cplx) MM_LAUNCH(double, true);
     else if (fp64) MM_LAUNCH(double, false);
     else if (cplx) MM_LAUNCH(float, true);
