@@ -47,10 +47,12 @@
 // same direction produced one sweep earlier (or from a bound in the first
 // sweep) and accumulates the new maximum with atomicMax.
 //
-// Roles (256 threads): warp 0 lane 0 issues TMA loads into a 3-stage ring,
-// warp 1 allocates tensor memory and its lane 0 issues tcgen05.mma, and
-// after the main loop all eight warps drain tensor memory (warp w reads
-// lanes 32 (w % 4) .. + 31, half of the column chunks each).
+// Roles: warp 0 lane 0 issues TMA loads into a ring of stages, warp 1
+// allocates tensor memory and its lane 0 issues tcgen05.mma, and the
+// remaining (epilogue) warps drain tensor memory (warp w reads lanes
+// 32 (w % 4) .. + 31).  The one-SM kernel (tc_mode_kernel) runs 576 threads
+// with 16 epilogue warps and 4 stages; the CTA-pair kernel (tc_pair_kernel)
+// sets its warps and stages per variant (pair_epi_warps, pair_stages).
 #include <cuda.h>
 #include <cuda_bf16.h>
 #include <cuda_fp16.h>
