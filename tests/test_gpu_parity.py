@@ -887,6 +887,33 @@ def test_degenerate_inputs(env, orc, prec):
     with pytest.raises(RuntimeError, match="MM_ERR_SHAPE"):
         mm.TuckerPlan(ctx, (0, 4, 4), [np.zeros((0, 0))] + Es, prec=prec, dtype=dt)
 
+
+@pytest.mark.parametrize("dims", [(37,), (21, 9), (13, 10, 7)])
+def test_state_not_16_byte_aligned(env, dims):
+    """The ABI requires 16-byte aligned states: one that starts 8 bytes past
+    a boundary (a contiguous slice one element into a buffer) is refused with
+    MM_ERR_ALIGN before any launch, and the buffer is left as it was; an
+    aligned copy steps normally."""
+    mm, ctx, torch = env
+    tau = 1e-4
+    Es = [fd_schrodinger_E(mm, n, tau) for n in dims]
+    count = int(np.prod(dims))
+    u0 = inputs.complex_normal(dims[::-1], seed=11).astype(np.complex64)
+    plan = mm.TuckerPlan(ctx, dims, Es, prec="f16x6")
+    buf = torch.zeros(count + 1, dtype=torch.complex64, device="cuda")
+    off = buf[1:].view(*dims[::-1])
+    assert off.data_ptr() % 16 == 8 and off.is_contiguous()
+    off.copy_(torch.from_numpy(u0).cuda())
+    with pytest.raises(RuntimeError, match="MM_ERR_ALIGN"):
+        plan.step(off, 3)
+    torch.cuda.synchronize()
+    assert np.array_equal(off.cpu().numpy(), u0) and buf[0].item() == 0
+    ali = torch.from_numpy(u0).cuda()
+    plan.step(ali, 3)
+    torch.cuda.synchronize()
+    assert not np.array_equal(ali.cpu().numpy(), u0)
+    ctx.status()
+
 def test_batched_pair_kernel_matches_one_sm_batch(env, monkeypatch):
     """Batched launches run the CTA-pair kernel over the problem records; the
     older one-SM-style batched kernel (forced with MM_TC_1SM=1 at batch
