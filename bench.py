@@ -385,6 +385,9 @@ def main():
                          "issued_flop_per_step": issued_per_step,
                          "alg_bytes_per_launch": ALG_BYTES_PER_MODE,
                          "hbm_frac_alg": ALG_BYTES_PER_MODE / kern_avg_s / 1e9 / hbm_peak,
+                         # DRAM bytes the launch actually moves (ncu, split state) over its time
+                         "hbm_frac_traffic": (NCU_TRAFFIC_BYTES / kern_avg_s / 1e9 / hbm_peak
+                                              if args.prec == "f16x6" else None),
                          "kernel_avg_us": kern_avg_s * 1e6, "kernel_launches_timed": kern_n,
                          "kernel_timing": "CUDA events around each mode-product launch over a second timed run of "
                                           f"{k2} steps (same stream, launched without the graph)"},
