@@ -450,7 +450,13 @@ mm_status hkp_plan_create(mm_ctx *ctx, int d, const int64_t *n, const double *co
  * nsteps doubles), and transforms back, in place.  The fixed-point state
  * and the coefficients stay on the device between steps.  Since every
  * f_mid is known at the call, the exponentials of up to 64 steps are
- * computed together (batched real products, see mm_expm_device).  The
+ * computed together (batched real products, see mm_expm_device).  On
+ * tensor-core plans the series is scaled to norm 2 (truncation below
+ * 5e-13), and a chunk of more than K steps takes its exponentials from
+ * K Chebyshev nodes in f over the chunk's f range (K = 4..12, the fewest
+ * whose interpolation error bound 2 (tau ||G||_1 (f_hi - f_lo) / 4)^K / K!
+ * is below 1e-14), both below the resolution of the tensor-core pieces;
+ * FP64 plans compute every step's exponential to full FP64 accuracy.  The
  * call synchronises the stream before returning (f_mid is then no longer
  * read). */
 mm_status hkmp_plan_create(mm_ctx *ctx, int d, const int64_t *n, const double *const *V_nodes,
