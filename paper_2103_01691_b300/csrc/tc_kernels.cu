@@ -917,10 +917,10 @@ __device__ __forceinline__ void epi_store(const TcArgs &a, float (&v)[CH][32], i
 // Persistent kernel in clusters of two CTAs.  Cluster c processes work
 // items P = c, c + #clusters, ...; item P is the row tile h = P % ni of the
 // point tiles 2 (P / ni) + rank, rank = 0, 1, so the two CTAs of a cluster
-// need the same matrix tiles at the same time: each loads half of every
-// matrix tile and multicasts it to both, and each MMA warp releases a
-// stage in both CTAs (the stage is free once both have consumed it).  The
-// TMA warp runs ahead across item boundaries; the epilogue warps copy the
+// need the same matrix tiles at the same time and read them through L2
+// once between them.  Each CTA loads its own stages (data and the whole
+// matrix tile) from this GPU's memory; no CTA touches the other's shared
+// memory.  The TMA warp runs ahead across item boundaries; the epilogue warps copy the
 // two accumulators into registers, release tensor memory to the MMA warp
 // at once, and then scale, split and store while the next item's MMAs run.
 template <int NP, bool KMAJOR, int EPI, bool FX>
@@ -944,7 +944,7 @@ __global__ void __launch_bounds__(kThreads, 1)
     if (threadIdx.x == 0) {
         for (int s = 0; s < kStages; ++s) {
             mbar_init(&full[s], 1);
-            mbar_init(&empty[s], 2);  // released by the MMA warps of both CTAs
+            mbar_init(&empty[s], 1);  // released by this CTA's MMA warp
         }
         mbar_init(accf, 1);
         mbar_init(tmem_empty, kEpiWarps);
@@ -959,7 +959,6 @@ __global__ void __launch_bounds__(kThreads, 1)
     }
     tc_fence_before();
     __syncthreads();
-    cluster_sync();  // the peer's barriers are initialised before any multicast reaches them
     tc_fence_after();
     const uint32_t tmem = *tmem_slot;
     // The next kernel of the stream may start its own set-up now; everything below reads or
@@ -1012,13 +1011,13 @@ __global__ void __launch_bounds__(kThreads, 1)
                                 tma_load_4d(&mapX, &full[s], dst + 2048, ac_l[1], kb * kBK, ac_r[1], c * NP + p);
                             }
                         }
-                    // this CTA's half of every matrix block, to both CTAs
-                    uint8_t *est = st + a.e_offset + rank * half_rows * 32;
+                    // every matrix block, in two boxes of half the rows each
+                    uint8_t *est = st + a.e_offset;
                     for (int p = 0; p < NP; ++p)
                         for (int w = 0; w < kBlocks; ++w)
-                            tma_load_2d_mc(&mapE, &full[s], est + (p * kBlocks + w) * a.it * 32, 0,
-                                           p * e_pstride + e_row0 + (kb * kBlocks + w) * a.it + rank * half_rows,
-                                           0x3);
+                            for (int hr = 0; hr < 2; ++hr)
+                                tma_load_2d(&mapE, &full[s], est + (p * kBlocks + w) * a.it * 32 + hr * half_rows * 32,
+                                            0, p * e_pstride + e_row0 + (kb * kBlocks + w) * a.it + hr * half_rows);
                 }
             }
         }
@@ -1068,7 +1067,7 @@ __global__ void __launch_bounds__(kThreads, 1)
                         umma_f16(dcol, aim, smem_desc(eS, 16, 256, kSwz32), idesc_half_neg, 1u);
                         umma_f16(dcol + uint32_t(a.it), aim, smem_desc(eC, 16, 256, kSwz32), idesc_half, 1u);
                     }
-                    umma_commit_mc(&empty[s], 0x3);
+                    umma_commit(&empty[s]);
                 }
                 umma_commit(accf);
             }
@@ -1134,7 +1133,6 @@ __global__ void __launch_bounds__(kThreads, 1)
     }
     tc_fence_before();
     __syncthreads();
-    cluster_sync();  // no CTA leaves while its peer may still write into its shared memory
     if (warp == 1) {
         tc_fence_after();
         tmem_dealloc(tmem, ncols);
@@ -1754,10 +1752,9 @@ __device__ __forceinline__ const TcProblem &problem_of(int64_t P, const TcProble
 // from the item's problem record.  Cluster c processes work
 // items P = c, c + #clusters, ...; item P of a problem is the row tile
 // h = P % ni of the point tiles 2 (P / ni) + rank, rank = 0, 1, so the two
-// CTAs of a cluster need the same matrix tiles at the same time: each loads
-// half of every matrix tile and multicasts it to both, and each MMA warp
-// releases a stage in both CTAs (the stage is free once both have consumed
-// it).  The TMA warp runs ahead across item boundaries; the epilogue warps
+// CTAs of a cluster need the same matrix tiles at the same time and read
+// them through L2 once between them; each CTA loads its own stages.  The
+// TMA warp runs ahead across item boundaries; the epilogue warps
 // copy the two accumulators into registers, release tensor memory to the
 // MMA warp at once, and then scale, split and store while the next item's
 // MMAs run.  A batched launch (BATCH) covers the same direction of many
@@ -1784,7 +1781,7 @@ __global__ void __launch_bounds__(kThreads, 1)
     if (threadIdx.x == 0) {
         for (int s = 0; s < kStages; ++s) {
             mbar_init(&full[s], 1);
-            mbar_init(&empty[s], 2);  // released by the MMA warps of both CTAs
+            mbar_init(&empty[s], 1);  // released by this CTA's MMA warp
         }
         mbar_init(accf, 1);
         mbar_init(tmem_empty, kEpiWarps);
@@ -1804,7 +1801,6 @@ __global__ void __launch_bounds__(kThreads, 1)
     }
     tc_fence_before();
     __syncthreads();
-    cluster_sync();  // the peer's barriers are initialised before any multicast reaches them
     tc_fence_after();
     const uint32_t tmem = *tmem_slot;
     const int rank = int(blockIdx.x & 1);
@@ -1858,13 +1854,13 @@ __global__ void __launch_bounds__(kThreads, 1)
                                 tma_load_4d(mx, &full[s], dst + 2048, ac_l[1], kb * kBK, ac_r[1], c * NP + p);
                             }
                         }
-                    // this CTA's half of every matrix block, to both CTAs
-                    uint8_t *est = st + a.e_offset + rank * half_rows * 32;
+                    // every matrix block, in two boxes of half the rows each
+                    uint8_t *est = st + a.e_offset;
                     for (int p = 0; p < NP; ++p)
                         for (int w = 0; w < kBlocks; ++w)
-                            tma_load_2d_mc(me, &full[s], est + (p * kBlocks + w) * it * 32, 0,
-                                           p * e_pstride + e_row0 + (kb * kBlocks + w) * it + rank * half_rows,
-                                           0x3);
+                            for (int hr = 0; hr < 2; ++hr)
+                                tma_load_2d(me, &full[s], est + (p * kBlocks + w) * it * 32 + hr * half_rows * 32, 0,
+                                            p * e_pstride + e_row0 + (kb * kBlocks + w) * it + hr * half_rows);
                 }
             }
         }
@@ -1917,7 +1913,7 @@ __global__ void __launch_bounds__(kThreads, 1)
                         umma_f16(dcol, aim, smem_desc(eS, 16, 256, kSwz32), idesc_half_neg, 1u);
                         umma_f16(dcol + uint32_t(it), aim, smem_desc(eC, 16, 256, kSwz32), idesc_half, 1u);
                     }
-                    umma_commit_mc(&empty[s], 0x3);
+                    umma_commit(&empty[s]);
                 }
                 umma_commit(accf);
             }
@@ -2084,7 +2080,6 @@ __global__ void __launch_bounds__(kThreads, 1)
     }
     tc_fence_before();
     __syncthreads();
-    cluster_sync();  // no CTA leaves while its peer may still write into its shared memory
     if (warp == 1) {
         tc_fence_after();
         tmem_dealloc(tmem, ncols);

@@ -111,18 +111,6 @@ __device__ __forceinline__ void tma_load_4d(const CUtensorMap *map, uint64_t *ba
         : "memory");
 }
 
-// The same load delivered to every CTA of the cluster in `mask`, at the same
-// shared-memory offset, completing on the barrier at the same offset in each.
-__device__ __forceinline__ void tma_load_2d_mc(const CUtensorMap *map, uint64_t *bar, void *dst, int c0, int c1,
-                                               uint16_t mask)
-{
-    asm volatile(
-        "cp.async.bulk.tensor.2d.shared::cluster.global.mbarrier::complete_tx::bytes.multicast::cluster [%0], [%1, "
-        "{%3, %4}], [%2], %5;" ::"r"(smem_u32(dst)),
-        "l"(reinterpret_cast<uint64_t>(map)), "r"(smem_u32(bar)), "r"(c0), "r"(c1), "h"(mask)
-        : "memory");
-}
-
 // All threads of all CTAs of the cluster.
 __device__ __forceinline__ void cluster_sync()
 {
@@ -176,16 +164,6 @@ __device__ __forceinline__ void umma_commit(uint64_t *bar)
 {
     asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(smem_u32(bar))
                  : "memory");
-}
-
-// As umma_commit, arriving on the barrier at the same offset in every CTA in `mask`.
-__device__ __forceinline__ void umma_commit_mc(uint64_t *bar, uint16_t mask)
-{
-    asm volatile(
-        "tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.multicast::cluster.b64 [%0], %1;" ::"r"(
-            smem_u32(bar)),
-        "h"(mask)
-        : "memory");
 }
 
 // 32 lanes x 16 consecutive 32-bit columns, one row (lane) per thread.
