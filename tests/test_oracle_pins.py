@@ -286,6 +286,42 @@ def test_gpe_second_order_in_tau(orc):
     assert 3.0 < e1 / e2 < 5.0
 
 
+def _gpe_energy(orc, psi, x, W, beta):
+    """Discrete GPE energy <psi, H psi>_W + (beta/2) sum_l W_l |psi_l|^4, H the harmonic
+    Hamiltonian (eigenvalues k1 + k2 + k3 + 3/2 on the Hermite coefficients, section 3), applied
+    through the oracle's forward and backward transforms."""
+    m = x.size
+    k = np.arange(m, dtype=np.float64)
+    lam = k[:, None, None] + k[None, :, None] + k[None, None, :] + 1.5
+    w3 = orc.weight3(W)
+    h_psi = orc.hermite_backward(lam * orc.hermite_forward(psi, x, W), x, W)
+    return float(np.real(np.sum(w3 * np.conj(psi) * h_psi)) + 0.5 * beta * np.sum(w3 * np.abs(psi) ** 4))
+
+
+def test_gpe_energy_pins_the_nonlinear_direction(orc):
+    """The nodal system i psi' = H psi + beta |psi|^2 psi (section 4.5) is Hamiltonian in the
+    W-weighted inner product and conserves the energy above with the same beta.  Strang splitting
+    with exact subflows keeps it to O(tau^2) over a fixed time, so its drift falls fourfold per
+    halving of tau.  A nonlinear subflow of the wrong direction, psi exp(+i tau beta |psi|^2),
+    is the scheme of -beta: it conserves the energy of -beta instead and leaves that of +beta
+    off by O(1) however small tau is."""
+    m = 10
+    x, _, W = orc.gauss_hermite(m)
+    psi0 = inputs.gpe_psi0(x, W)
+    T = 0.2
+    for beta in (100.0, -100.0):
+        e0 = _gpe_energy(orc, psi0, x, W, beta)
+        e0_other = _gpe_energy(orc, psi0, x, W, -beta)
+        drift, other = [], []
+        for n in (8, 16, 32):
+            p = orc.gpe_steps(psi0, x, W, beta, T / n, n)
+            drift.append(abs(_gpe_energy(orc, p, x, W, beta) - e0) / abs(e0))
+            other.append(abs(_gpe_energy(orc, p, x, W, -beta) - e0_other) / abs(e0_other))
+        assert 3.5 < drift[0] / drift[1] < 4.5 and 3.5 < drift[1] / drift[2] < 4.5, drift
+        assert drift[2] < 5e-4, drift
+        assert min(other) > 0.05, other
+
+
 def test_gpe_adjoint_finite_differences(orc):
     m = 8
     x, _, W = orc.gauss_hermite(m)
