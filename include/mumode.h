@@ -201,8 +201,10 @@ mm_status mumode_product(mm_ctx *ctx, int d, const int64_t *n, int mu, const dou
  * and plugins whose host forbids device allocation.
  *
  * mumode_product_noalloc computes what mumode_product computes with
- * MM_PREC_F16X6 on MM_C64 data, on the current CUDA device, without calling
- * cudaMalloc, cudaFree or any allocating routine.  The caller passes the
+ * MM_PREC_F16X6 on MM_C64 data, on the current CUDA device, with no device
+ * allocation: it calls no cudaMalloc, cudaFree or other routine that
+ * allocates device memory.  (The matrix pieces are built on the host in
+ * ordinary host memory, as in mumode_product.)  The caller passes the
  * input u_dev and the output s_dev as in mumode_product.  All temporaries
  * (the split input and output states, the matrix pieces, the scale and
  * status words) live in one static device array of 64 MiB that every GPU

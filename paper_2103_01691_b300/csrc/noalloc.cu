@@ -1,9 +1,11 @@
 // mumode_product_noalloc: the F16X6 mu-mode product for callers that must
-// not allocate device memory.  Everything the product needs besides the
-// caller's input and output -- the split input and output states, the
-// matrix pieces, the row scales and the scale / status words -- lives in
-// one file-scope device array of fixed size, reserved when the library's
-// device code is loaded on a GPU and kept until the process exits.
+// not allocate device memory.  Everything the product needs on the device
+// besides the caller's input and output -- the split input and output
+// states, the matrix pieces, the row scales and the scale / status words --
+// lives in one file-scope device array of fixed size, reserved when the
+// library's device code is loaded on a GPU and kept until the process
+// exits.  The matrix pieces are built on the host in ordinary host memory
+// (std::vector) and copied into that array; no device memory is allocated.
 #include <cuda_runtime.h>
 
 #include <cstring>
@@ -69,12 +71,17 @@ extern "C" mm_status mumode_product_noalloc(int d, const int64_t *n, int mu, con
     si.d = so.d = d;
     si.plane = so.plane = 1;
     int64_t cnt_in = 1, cnt_out = 1;
+    // Every running product stays below the scratch's point capacity (12 bytes per padded point
+    // and state), so none of them can overflow before the size check below.
+    const int64_t cap_points = int64_t(kScratchBytes / 12);
     for (int v = 0; v < d; ++v) {
         nout[v] = (v == mu - 1) ? m : n[v];
         si.n[v] = n[v];
         so.n[v] = nout[v];
         si.np[v] = (n[v] + 15) / 16 * 16;
         so.np[v] = (nout[v] + 15) / 16 * 16;
+        if (si.np[v] > cap_points / si.plane || so.np[v] > cap_points / so.plane)
+            return fail(MM_ERR_SHAPE, "this product needs more than the %zu bytes of the static scratch", kScratchBytes);
         si.plane *= si.np[v];
         so.plane *= so.np[v];
         cnt_in *= n[v];

@@ -277,17 +277,27 @@ def mumode_product_noalloc(u, mu: int, L, out=None, stream=None):
     _need_cuda(u)
     if u.dtype != torch.complex64:
         raise TypeError("mumode_product_noalloc takes complex64 data")
-    Lf, Lc = _complex_interleaved(L)
-    m = int(np.asarray(L).shape[0])
     dims = _dims(u.shape)
     d = len(dims)
+    if not 1 <= mu <= d:
+        raise ValueError(f"mu = {mu} outside 1..{d}")
+    La = np.asarray(L)
+    if La.ndim != 2 or La.shape[1] != u.shape[d - mu]:
+        raise ValueError(f"L must be 2-D with {u.shape[d - mu]} columns (n_mu), got shape {La.shape}")
+    Lf, Lc = _complex_interleaved(La)
+    m = int(La.shape[0])
     out_shape = list(u.shape)
     out_shape[d - mu] = m
     if out is None:
         out = torch.empty(out_shape, dtype=u.dtype, device=u.device)
-    _check(lib().mumode_product_noalloc(d, dims.ctypes.data_as(_i64p), mu, _dptr(Lf), m, Lc,
-                                        ctypes.c_void_p(u.data_ptr()), ctypes.c_void_p(out.data_ptr()),
-                                        _stream(stream)))
+    elif (out.dtype != torch.complex64 or out.device != u.device or not out.is_contiguous()
+          or list(out.shape) != out_shape):
+        raise ValueError(f"out must be a contiguous complex64 tensor of shape {out_shape} on {u.device}")
+    # the library works on the current device: make it u's
+    with torch.cuda.device(u.device):
+        _check(lib().mumode_product_noalloc(d, dims.ctypes.data_as(_i64p), mu, _dptr(Lf), m, Lc,
+                                            ctypes.c_void_p(u.data_ptr()), ctypes.c_void_p(out.data_ptr()),
+                                            _stream(stream)))
     return out
 
 
