@@ -1,6 +1,7 @@
 """Benchmark: 3D complex mu-mode steps at n = 256 (free Schroedinger
 i u_t = Lap u, Dirichlet FD, E_mu = expm(i tau A_mu), tau = 1e-4), the
-split-precision tensor-core form (BF16x6) against the plain FP64 GPU form.
+split-precision tensor-core form (F16X6 by default) against the plain FP64
+GPU form.
 
   python bench.py [--gpus N] [--steps K] [--warmup W] [--prec bf16x6]
   python bench.py --impl reference ...   (FP64 CPU oracle, bounded sample)
@@ -34,9 +35,42 @@ FLOP_PER_STEP = 3 * FLOP_PER_MODE       # 1.031e11
 STATE_BYTES = N**3 * 8                   # complex64
 ALG_BYTES_PER_MODE = 2 * STATE_BYTES     # read + write the state once
 WORKLOAD = "free Schroedinger n=256^3 complex64, Dirichlet FD, E=expm(i*1e-4*A), u0 complex normal seed 2"
-# DRAM bytes (read + write) per mode-product launch from the ncu capture in
-# profiles/tc_pair_kernel_f16x6_n256.md; None once the kernel changes.
-NCU_TRAFFIC_BYTES = 355.1e6  # dram read + write per launch, mean of the three directions (ncu, see profiles)
+# DRAM bytes (read + write) per mode-product launch come from the ncu capture
+# summarised in this profile, which records them together with the hash of the
+# kernel sources they were measured on (a line "bench-traffic: ...").
+TRAFFIC_PROFILE = os.path.join(ROOT, "profiles", "tc_pair_kernel_f16x6_n256.md")
+KERNEL_SOURCES = ("tc_kernels.cu", "tc_ptx.cuh", "internal.h", "mumode_api.cu")
+
+
+def kernel_source_sha() -> str:
+    """First 16 hex digits of the SHA-256 over the sources that define the
+    mode-product kernel and its launches."""
+    import hashlib
+
+    h = hashlib.sha256()
+    for name in KERNEL_SOURCES:
+        with open(os.path.join(ROOT, "paper_2103_01691_b300", "csrc", name), "rb") as f:
+            h.update(name.encode() + b"\0" + f.read())
+    return h.hexdigest()[:16]
+
+
+def ncu_traffic(prec: str):
+    """(bytes per launch, note): the profile's DRAM traffic if it was measured
+    on the current kernel sources and this precision, else (None, why)."""
+    try:
+        with open(TRAFFIC_PROFILE) as f:
+            rec = [ln for ln in f if ln.startswith("bench-traffic:")]
+    except OSError:
+        return None, "no profile"
+    if not rec:
+        return None, "profile has no bench-traffic record"
+    kv = dict(t.split("=", 1) for t in rec[-1].split()[1:] if "=" in t)
+    sha = kernel_source_sha()
+    if kv.get("source_sha") != sha:
+        return None, f"kernel sources changed since the capture (profile {kv.get('source_sha')}, now {sha})"
+    if kv.get("prec") != prec:
+        return None, f"captured for {kv.get('prec')}, not {prec}"
+    return float(kv["bytes_per_launch"]), f"ncu dram read+write per launch, sources {sha}"
 
 
 def peaks():
@@ -218,7 +252,8 @@ def main():
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-fp64", action="store_true")
     ap.add_argument("--workload", default="free256",
-                    choices=["free256", "heat32", "ho128", "batched64", "gpe192", "hkp", "hkmp", "pipe"],
+                    choices=["free256", "heat32", "ho128", "batched64", "gpe192", "hkp", "hkmp", "pipe",
+                             "sweep256"],
                     help="free256 (default) is the headline line; the others time the remaining workloads")
     ap.add_argument("--sizes", default="", help="hkp / hkmp / pipe: comma-separated sizes n (default: the paper's)")
     ap.add_argument("--no-autotune", action="store_true",
@@ -316,6 +351,8 @@ def main():
     ms_per_step = ms / args.steps
     kern_avg_s = kern_ms / max(kern_n, 1) / 1e3
     achieved = FLOP_PER_MODE / kern_avg_s / 1e12
+    achieved_gbs = ALG_BYTES_PER_MODE / kern_avg_s / 1e9
+    traffic, traffic_note = ncu_traffic(args.prec)
     issued_per_step = plan.issued_flops()
     issued = issued_per_step / 3 / kern_avg_s / 1e12
 
@@ -388,17 +425,22 @@ def main():
                        "parallelism": f"replicas x{world}" if world > 1 else "single GPU",
                        "l2": "working set 537 MB > 126 MB L2, no flush"},
             "tflops_algorithmic": FLOP_PER_STEP * value / world / 1e12,
-            "roofline": {"bound": "tensor", "achieved": achieved, "peak": tc_peak, "unit": "TFLOP/s",
-                         "frac": achieved / tc_peak,
-                         "traffic": NCU_TRAFFIC_BYTES if args.prec == "f16x6" else None,
-                         "kernel": "tc_pair_kernel (one mode product)", "peak_source": f"bf16 burst (f16 same rate), {peak_src}",
+            # The method's own work per launch is 8 n flop and 16 B (complex64 read + write) per point:
+            # 128 flop/B, below the ridge of the measured peaks (~271 flop/B), so HBM is the binding roof.
+            "roofline": {"bound": "hbm", "achieved": achieved_gbs, "peak": hbm_peak, "unit": "GB/s",
+                         "frac": achieved_gbs / hbm_peak, "traffic": traffic,
+                         "traffic_note": traffic_note,
+                         "kernel": "tc_pair_kernel (one mode product)",
+                         "peak_source": f"hbm copy, {peak_src}",
+                         "alg_bytes_per_launch": ALG_BYTES_PER_MODE,
+                         # the same launches against the tensor-core roof
+                         "tensor_alg_tflops": achieved, "tensor_peak_tflops": tc_peak,
+                         "tensor_alg_frac": achieved / tc_peak,
+                         "tensor_peak_source": f"bf16 burst (f16 same rate), {peak_src}",
                          "issued_tflops": issued, "issued_frac": issued / tc_peak,
                          "issued_flop_per_step": issued_per_step,
-                         "alg_bytes_per_launch": ALG_BYTES_PER_MODE,
-                         "hbm_frac_alg": ALG_BYTES_PER_MODE / kern_avg_s / 1e9 / hbm_peak,
                          # DRAM bytes the launch actually moves (ncu, split state) over its time
-                         "hbm_frac_traffic": (NCU_TRAFFIC_BYTES / kern_avg_s / 1e9 / hbm_peak
-                                              if args.prec == "f16x6" else None),
+                         "hbm_frac_traffic": (traffic / kern_avg_s / 1e9 / hbm_peak if traffic else None),
                          "kernel_avg_us": kern_avg_s * 1e6, "kernel_launches_timed": kern_n,
                          "kernel_timing": "CUDA events around each mode-product launch over a second timed run of "
                                           f"{k2} steps (same stream, launched without the graph)"},
@@ -428,6 +470,78 @@ def _time(fn, stream):
     e1.record(stream)
     torch.cuda.synchronize()
     return e0.elapsed_time(e1)
+
+
+SWEEP_PRECS = ("fp64", "fp64dmma", "fp32", "tf32x3", "bf16x3", "bf16x6", "bf16", "f16x6")
+
+
+def sweep256(mm, ctx, torch, stream, args):
+    """The precision sweep on the headline workload (n = 256, tau = 1e-4):
+    for every precision its speed, and after the 50-step trajectory its
+    relative L2 error against the FP64 result and its norm drift.  The FP64
+    reference is one application of E(50 tau) per direction on the FP64
+    tensor-core path (E(tau)^50 = E(50 tau) for the Kronecker sum)."""
+    from paper_2103_01691_b300 import inputs
+
+    hbm_peak, tc_peak, _, peak_src = peaks()
+    A = mm.fd_laplacian_dirichlet(N)
+    E = mm.expm(A, 1j * TAU)
+    u0 = inputs.free_schrodinger_u0(N, seed=2)
+    ref_plan = mm.TuckerPlan(ctx, [N] * 3, [mm.expm(A, 1j * TAU * STEPS_PER_TRAJECTORY)] * 3, prec="fp64dmma")
+    ref = torch.from_numpy(u0).cuda()
+    ref_plan.step(ref, 1)
+    nref = float(torch.linalg.vector_norm(ref))
+    n0 = float(torch.linalg.vector_norm(torch.from_numpy(u0).cuda()))
+    del ref_plan
+    out = {}
+    precs = [p for p in SWEEP_PRECS if p in mm.PREC]
+    for prec in precs:
+        f64 = prec.startswith("fp64")
+        dt = torch.complex128 if f64 else torch.complex64
+        plan = mm.TuckerPlan(ctx, [N] * 3, [E] * 3, prec=prec)
+        u = torch.from_numpy(u0).to(dt).cuda()
+        n0p = float(torch.linalg.vector_norm(u.to(torch.complex128)))
+        plan.step(u, STEPS_PER_TRAJECTORY)  # the trajectory (also the warm-up)
+        torch.cuda.synchronize()
+        uc = u.to(torch.complex128)
+        err = float(torch.linalg.vector_norm(uc - ref)) / nref
+        drift = abs(float(torch.linalg.vector_norm(uc)) / n0p - 1.0)
+        del uc
+        k = 2 if f64 else 50
+        ms = _time(lambda: plan.step(u, k), stream) / k
+        rec = {"steps_per_s": 1e3 / ms, "ms_per_step": ms,
+               "tflops_algorithmic": FLOP_PER_STEP / (ms * 1e-3) / 1e12,
+               "hbm_frac_alg": 3 * ALG_BYTES_PER_MODE / (ms * 1e-3) / 1e9 / hbm_peak,
+               "rel_err_50_steps_vs_fp64": err, "norm_drift_50_steps": drift}
+        if not f64 and prec != "fp32":
+            issued = plan.issued_flops() / (ms * 1e-3) / 1e12
+            rec.update(issued_tc_tflops=issued, issued_frac_of_measured_peak=issued / tc_peak)
+        out[prec] = rec
+        del plan, u
+        torch.cuda.empty_cache()
+    missing = [p for p in SWEEP_PRECS if p not in mm.PREC]
+    return {"value": out["f16x6"]["steps_per_s"], "precision": "all", "modes": out,
+            "not_built": missing, "norm_u0": n0,
+            "config": f"{WORKLOAD}; {STEPS_PER_TRAJECTORY}-step trajectory per mode, error vs FP64 "
+                      f"(one application of E(50 tau), FP64 MMA); hbm_frac_alg: 3 x 268 MB per step over the step "
+                      f"time against the {peak_src} HBM peak; issued fraction against the {peak_src} BF16 burst"}
+
+
+def _hermite_accuracy(mm, ctx, torch, n, got, ref, psi0, steps):
+    """Relative weighted L2 error of a tensor-core trajectory against the FP64
+    GPU trajectory, and the weighted norm drift of both, after `steps`."""
+    x, W = mm.gauss_hermite(n)
+    w = torch.from_numpy(W).cuda()
+    w3 = w[:, None, None] * w[None, :, None] * w[None, None, :]
+    p0 = torch.from_numpy(psi0).cuda()
+
+    def nrm(v):
+        return float(torch.sum(torch.abs(v) ** 2 * w3))
+
+    err = (nrm(got - ref) / nrm(ref)) ** 0.5
+    return {"rel_err_vs_fp64": err, "steps_compared": steps,
+            "norm_drift": abs(nrm(got) / nrm(p0.to(torch.complex64).to(torch.complex128)) - 1),
+            "norm_drift_fp64": abs(nrm(ref) / nrm(p0) - 1)}
 
 
 def other_workload(args):
@@ -470,6 +584,7 @@ def other_workload(args):
         line.update(value=K / (ms / 1e3), steps=K, precision="fp64", config="heat FD2 n=32^3 real, tau=1e-3")
     elif args.workload == "ho128":
         n, tau, K = 128, 0.01, 100
+        finals = {}
         for prec in ("f16x6",) if args.no_fp64 else ("f16x6", "fp64", "fp64dmma"):
             plan = mm.HermitePlan(ctx, [n] * 3, prec=prec)
             if args.no_graphs:
@@ -483,6 +598,14 @@ def other_workload(args):
             plan.ho_step(psi, tau, k)
             ms = _time(lambda: plan.ho_step(psi, tau, k), stream)
             line[prec] = {"steps_per_s": k / (ms / 1e3), "steps": k}
+            if prec in ("f16x6", "fp64dmma"):
+                # the whole 100-step trajectory from psi0, for the accuracy fields below
+                traj = torch.from_numpy(inputs.harmonic_psi0(x, W, seed=1)).to(dt).cuda()
+                plan.ho_step(traj, tau, K)
+                finals[prec] = traj.to(torch.complex128)
+        if "fp64dmma" in finals:
+            line.update(_hermite_accuracy(mm, ctx, torch, n, finals["f16x6"], finals["fp64dmma"],
+                                          inputs.harmonic_psi0(x, W, seed=1), K))
         line.update(value=line["f16x6"]["steps_per_s"], precision="f16x6",
                     config="harmonic oscillator, Hermite n=128^3 complex64, tau=0.01 (folded propagators)")
     elif args.workload == "hkp":
@@ -588,6 +711,8 @@ def other_workload(args):
                     precision="fp64dmma",
                     config="pipe flow, d = 2, n x n, T = 4 in one exact step; total_ms: operators, two "
                            "device exponentials, plan, one step (value: solves/s at n = 900)")
+    elif args.workload == "sweep256":
+        line.update(sweep256(mm, ctx, torch, stream, args))
     elif args.workload == "gpe192":
         n, beta, tau, K = 192, 100.0, 1e-3, 500
         plan = mm.HermitePlan(ctx, [n] * 3, prec="f16x6")
@@ -600,6 +725,17 @@ def other_workload(args):
                                   else plan.gpe_autotune(psi, beta, tau, nsteps=5)[0])
         plan.gpe_step(psi, beta, tau, K)
         ms = _time(lambda: plan.gpe_step(psi, beta, tau, K), stream)
+        if not args.no_fp64:
+            # the whole 500-step trajectory in F16X6 and in FP64 (warp-level FP64 MMA), for the accuracy fields
+            traj = psi0.clone()
+            plan.gpe_step(traj, beta, tau, K)
+            p64 = mm.HermitePlan(ctx, [n] * 3, prec="fp64dmma")
+            t64 = torch.from_numpy(inputs.gpe_psi0(x, W, seed=4)).cuda()
+            ms64 = _time(lambda: p64.gpe_step(t64, beta, tau, K), stream)
+            line.update(_hermite_accuracy(mm, ctx, torch, n, traj.to(torch.complex128), t64,
+                                          inputs.gpe_psi0(x, W, seed=4), K))
+            line["fp64dmma_steps_per_s"] = K / (ms64 / 1e3)
+            del p64, t64, traj
         gT = torch.randn_like(psi0)
         # the first call builds the adjoint's matrices and checkpoint buffers (kept with the plan)
         ms_adj_first = _time(lambda: plan.gpe_adjoint(psi0, gT, beta, tau, 100, ckpt_every=50), stream)
