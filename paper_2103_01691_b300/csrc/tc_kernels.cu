@@ -247,6 +247,24 @@ mm_status tc_matrix_host(const double *E, int64_t m, int64_t n, int npieces, boo
     return MM_OK;
 }
 
+// The bounded waits' limit and the stage-withholding test hook of a launch, from the environment:
+// MM_WAIT_LIMIT_CYCLES (SM clocks, default 4e9, about two seconds) and MM_WITHHOLD_STAGE (the
+// stage of each CTA whose loads the producers skip; unset or negative: none).  The hook lets a
+// test make a wait run out and check that the launch ends with MM_ERR_TIMEOUT and leaves the
+// context usable.
+static void wait_hooks(long long *limit, int64_t *withhold)
+{
+    *limit = 4000000000LL;
+    *withhold = -1;
+    const char *l = std::getenv("MM_WAIT_LIMIT_CYCLES");
+    if (l && l[0]) {
+        const long long v = std::atoll(l);
+        if (v > 0) *limit = v;
+    }
+    const char *w = std::getenv("MM_WITHHOLD_STAGE");
+    if (w && w[0]) *withhold = std::atoll(w);
+}
+
 TcVariant tc_default_variant()
 {
     const char *one = std::getenv("MM_TC_1SM");
@@ -766,6 +784,11 @@ struct TcArgs {
     int64_t ldiv, rdiv;
     uint16_t *out;
     int *err;
+    // bounded waits give up after this many SM clocks (MM_ERR_TIMEOUT)
+    long long wait_limit;
+    // test hook: the stage (counted over the launch, per CTA) whose loads the producers skip,
+    // so that the MMA's wait for it runs out; -1: none
+    int64_t withhold;
     // fixed-point mode
     const float *rho;
     TcScales sc;
@@ -935,6 +958,7 @@ __global__ void __launch_bounds__(kThreads, 1)
     uint64_t *tmem_empty = accf + 1;
     uint32_t *tmem_slot = reinterpret_cast<uint32_t *>(tmem_empty + 1);
     volatile int *abort_flag = reinterpret_cast<volatile int *>(tmem_slot + 1);
+    uint64_t *mma_fin = reinterpret_cast<uint64_t *>(tmem_slot + 2);  // abort: this CTA's MMAs have completed
 
     const int warp = threadIdx.x / 32, lane = threadIdx.x % 32;
     const int acc_cols = 2 * a.it;
@@ -948,6 +972,7 @@ __global__ void __launch_bounds__(kThreads, 1)
         }
         mbar_init(accf, 1);
         mbar_init(tmem_empty, kEpiWarps);
+        mbar_init(mma_fin, 1);
         *abort_flag = 0;
         mbar_fence_init();
         tma_prefetch_desc(&mapX);
@@ -966,6 +991,7 @@ __global__ void __launch_bounds__(kThreads, 1)
     if (threadIdx.x == 0) griddep_launch_dependents();
     griddep_wait();
     if (FX && blockIdx.x == 0 && threadIdx.x == 0 && a.sc.zero_next) *a.sc.zero_next = 0u;
+    uint32_t armed = 0, armed_ph = 0;  // producer: slots armed, and the parity of their last arming
     const int rank = int(blockIdx.x & 1);
     const int64_t cid = blockIdx.x / 2, nclusters = gridDim.x / 2;
     const int half_rows = a.it / 2;
@@ -995,12 +1021,15 @@ __global__ void __launch_bounds__(kThreads, 1)
                 for (int kb = a.kb_lo[h]; kb < a.kb_hi[h]; ++kb, ++gk) {
                     const int s = int(gk % kStages);
                     const uint32_t ph = (gk / kStages) & 1u;
-                    if (!mbar_wait(&empty[s], ph ^ 1u, a.err, MM_ERR_TIMEOUT)) {
+                    if (!mbar_wait(&empty[s], ph ^ 1u, a.err, MM_ERR_TIMEOUT, a.wait_limit)) {
                         *abort_flag = 1;
                         break;
                     }
+                    if (int64_t(gk) == a.withhold) continue;
                     uint8_t *st = smem + s * a.stage_bytes;
                     mbar_arrive_expect_tx(&full[s], uint32_t(a.tx_bytes));
+                    armed |= 1u << s;
+                    armed_ph = (armed_ph & ~(1u << s)) | (ph << s);
                     for (int c = 0; c < 2; ++c)
                         for (int p = 0; p < NP; ++p) {
                             uint8_t *dst = st + (c * NP + p) * kDataTileBytes;
@@ -1033,7 +1062,7 @@ __global__ void __launch_bounds__(kThreads, 1)
             uint32_t gk = 0, lt = 0;
             for (int64_t P = cid; P < a.pairs && !*abort_flag; P += nclusters, ++lt) {
                 const int h = int(P % a.ni);
-                if (lt > 0 && !mbar_wait(tmem_empty, (lt - 1) & 1u, a.err, MM_ERR_TIMEOUT)) {
+                if (lt > 0 && !mbar_wait(tmem_empty, (lt - 1) & 1u, a.err, MM_ERR_TIMEOUT, a.wait_limit)) {
                     *abort_flag = 1;
                     break;
                 }
@@ -1042,7 +1071,7 @@ __global__ void __launch_bounds__(kThreads, 1)
                 for (int kb = a.kb_lo[h]; kb < a.kb_hi[h]; ++kb, ++gk) {
                     const int s = int(gk % kStages);
                     const uint32_t ph = (gk / kStages) & 1u;
-                    if (!mbar_wait(&full[s], ph, a.err, MM_ERR_TIMEOUT)) {
+                    if (!mbar_wait(&full[s], ph, a.err, MM_ERR_TIMEOUT, a.wait_limit)) {
                         *abort_flag = 1;
                         break;
                     }
@@ -1071,6 +1100,10 @@ __global__ void __launch_bounds__(kThreads, 1)
                 }
                 umma_commit(accf);
             }
+            if (*abort_flag) {  // every MMA this thread issued completes before tensor memory is freed
+                umma_commit(mma_fin);
+                mbar_wait(mma_fin, 0u, nullptr, 0, a.wait_limit);
+            }
         }
         __syncwarp();
     } else {
@@ -1096,7 +1129,7 @@ __global__ void __launch_bounds__(kThreads, 1)
         for (int64_t P = cid; P < a.pairs; P += nclusters, ++lt) {
             const int64_t tile = (P / a.ni) * 2 + rank;
             const int h = int(P % a.ni);
-            const bool acc_ready = !*abort_flag && mbar_wait(accf, lt & 1u, a.err, MM_ERR_TIMEOUT);
+            const bool acc_ready = !*abort_flag && mbar_wait(accf, lt & 1u, a.err, MM_ERR_TIMEOUT, a.wait_limit);
             if (!acc_ready) *abort_flag = 1;
             tc_fence_after();
             // drain: up to kChunksPerWarp chunks of 16 rows, real and imaginary, both accumulators summed
@@ -1133,6 +1166,10 @@ __global__ void __launch_bounds__(kThreads, 1)
     }
     tc_fence_before();
     __syncthreads();
+    // A wait ran out (the flag is final here): every load into this CTA lands before it exits (bounded).
+    if (warp == 0 && lane == 0 && *abort_flag)
+        for (int q = 0; q < kStages; ++q)
+            if (armed & (1u << q)) mbar_wait(&full[q], (armed_ph >> q) & 1u, nullptr, 0, a.wait_limit);
     if (warp == 1) {
         tc_fence_after();
         tmem_dealloc(tmem, ncols);
@@ -1416,6 +1453,7 @@ __global__ void __launch_bounds__(pair_threads(CH, EPI, BATCH), 1)
     uint64_t *tmem_empty = accf + 2;       // [2]: accumulator set b has been drained
     uint32_t *tmem_slot = reinterpret_cast<uint32_t *>(tmem_empty + 2);
     volatile int *abort_flag = reinterpret_cast<volatile int *>(tmem_slot + 1);
+    uint64_t *mma_fin = reinterpret_cast<uint64_t *>(tmem_slot + 2);  // abort: the leader's MMAs have completed
 
     const int warp = threadIdx.x / 32, lane = threadIdx.x % 32;
     const int rank = int(blockIdx.x & 1);
@@ -1435,6 +1473,7 @@ __global__ void __launch_bounds__(pair_threads(CH, EPI, BATCH), 1)
             // this CTA's epilogue warps, and in the leader the peer's relay
             mbar_init(&tmem_empty[b], pair_epi_warps(CH, EPI, BATCH) + (rank == 0 ? 1 : 0));
         }
+        mbar_init(mma_fin, 1);
         *abort_flag = 0;
         mbar_fence_init();
         if (!BATCH) {
@@ -1467,6 +1506,7 @@ __global__ void __launch_bounds__(pair_threads(CH, EPI, BATCH), 1)
     const int64_t cid = blockIdx.x / 2, nclusters = gridDim.x / 2;
     const int half = a.it / 2;
     const int e_bytes = 3 * half * 32;  // one piece's [-S; C; S] blocks in a stage
+    uint32_t armed = 0, armed_ph = 0;   // producer of the leader: slots armed, parity of their last arming
     const uint32_t full_lead = mapa_shared(smem_u32(full), 0);
     const uint32_t tmem_empty_lead = mapa_shared(smem_u32(tmem_empty), 0);
 
@@ -1475,6 +1515,7 @@ __global__ void __launch_bounds__(pair_threads(CH, EPI, BATCH), 1)
             // ---------------- TMA producer (both CTAs) ----------------
             int s = 0;
             uint32_t ph = 0;  // ring position
+            int64_t g = 0;    // stages reached over the launch
             const int e_rows = 3 * half / 4;  // 128-byte rows of one block triple
             for (int64_t P = cid; P < items && !*abort_flag; P += nclusters) {
                 const TcPairProblem *pr = BATCH ? &pair_problem(many, nprob, P) : nullptr;
@@ -1500,29 +1541,34 @@ __global__ void __launch_bounds__(pair_threads(CH, EPI, BATCH), 1)
                 const int e_row0 = (h * A.kblocks * 2 + rank) * e_box_rows;
                 const int kb_end = A.kb_hi[h];
                 for (int kb = A.kb_lo[h]; kb < kb_end; kb += KB) {
-                    if (!mbar_wait(&empty[s], ph ^ 1u, a.err, MM_ERR_TIMEOUT)) {
+                    if (!mbar_wait(&empty[s], ph ^ 1u, a.err, MM_ERR_TIMEOUT, a.wait_limit)) {
                         *abort_flag = 1;
                         break;
                     }
                     const int nk = KB == 1 || kb + 1 == kb_end ? 1 : 2;  // k-blocks of the item in this stage
                     uint8_t *st = smem + s * a.stage_bytes;
                     const uint32_t fb = full_lead + uint32_t(s) * 8u;
-                    // both CTAs' bytes: the data box (always whole, zero-filled past the tensor) and the
-                    // matrix boxes of the stage's k-blocks
-                    if (rank == 0)
-                        mbar_arrive_expect_tx(&full[s], KB == 1 ? uint32_t(a.tx_bytes)
-                                                                : uint32_t(2 * (a.e_offset + nk * NP * e_bytes)));
-                    // all 2 NP piece planes in one box (K-major: [plane][128 points][16 KB k]) or one box
-                    // per atom (MN-major: [atom][plane][16 k][64 points])
-                    if (KMAJOR) {
-                        tma_load_3d_pair(mx, fb, st, kb * kBK, k_row, 0);
-                    } else {
-                        tma_load_4d_pair(mx, fb, st, ac_l[0], kb * kBK, ac_r[0], 0);
-                        tma_load_4d_pair(mx, fb, st + KB * 2 * NP * 2048, ac_l[1], kb * kBK, ac_r[1], 0);
+                    if (g++ != a.withhold) {
+                        // both CTAs' bytes: the data box (always whole, zero-filled past the tensor) and the
+                        // matrix boxes of the stage's k-blocks
+                        if (rank == 0) {
+                            mbar_arrive_expect_tx(&full[s], KB == 1 ? uint32_t(a.tx_bytes)
+                                                                    : uint32_t(2 * (a.e_offset + nk * NP * e_bytes)));
+                            armed |= 1u << s;
+                            armed_ph = (armed_ph & ~(1u << s)) | (ph << s);
+                        }
+                        // all 2 NP piece planes in one box (K-major: [plane][128 points][16 KB k]) or one box
+                        // per atom (MN-major: [atom][plane][16 k][64 points])
+                        if (KMAJOR) {
+                            tma_load_3d_pair(mx, fb, st, kb * kBK, k_row, 0);
+                        } else {
+                            tma_load_4d_pair(mx, fb, st, ac_l[0], kb * kBK, ac_r[0], 0);
+                            tma_load_4d_pair(mx, fb, st + KB * 2 * NP * 2048, ac_l[1], kb * kBK, ac_r[1], 0);
+                        }
+                        for (int j = 0; j < nk; ++j)
+                            tma_load_2d_pair(me, fb, st + a.e_offset + j * NP * e_bytes, 0,
+                                             e_row0 + (kb + j) * 2 * e_box_rows);
                     }
-                    for (int j = 0; j < nk; ++j)
-                        tma_load_2d_pair(me, fb, st + a.e_offset + j * NP * e_bytes, 0,
-                                         e_row0 + (kb + j) * 2 * e_box_rows);
                     if (++s == kSt) {
                         s = 0;
                         ph ^= 1u;
@@ -1540,7 +1586,7 @@ __global__ void __launch_bounds__(pair_threads(CH, EPI, BATCH), 1)
             uint32_t lt = 0;
             for (int64_t P = cid; P < items; P += nclusters, ++lt) {
                 const int b = int(lt % uint32_t(nsets));
-                if (!mbar_wait(&tmem_empty[b], (lt / uint32_t(nsets)) & 1u, a.err, MM_ERR_TIMEOUT)) {
+                if (!mbar_wait(&tmem_empty[b], (lt / uint32_t(nsets)) & 1u, a.err, MM_ERR_TIMEOUT, a.wait_limit)) {
                     *abort_flag = 1;
                     break;
                 }
@@ -1580,7 +1626,7 @@ __global__ void __launch_bounds__(pair_threads(CH, EPI, BATCH), 1)
                 const int h = int((BATCH ? P - pr->pairs_begin : P) % A.ni);
                 const int b = int(lt % uint32_t(nsets));
                 const uint32_t use = lt / uint32_t(nsets);
-                if (use > 0 && !mbar_wait<true>(&tmem_empty[b], (use - 1) & 1u, a.err, MM_ERR_TIMEOUT)) {
+                if (use > 0 && !mbar_wait<true>(&tmem_empty[b], (use - 1) & 1u, a.err, MM_ERR_TIMEOUT, a.wait_limit)) {
                     *abort_flag = 1;
                     break;
                 }
@@ -1588,7 +1634,7 @@ __global__ void __launch_bounds__(pair_threads(CH, EPI, BATCH), 1)
                 const uint32_t d0 = tmem + uint32_t(b * set_cols), d1 = d0 + uint32_t(acc_cols);
                 const int kb_lo = A.kb_lo[h], kb_hi = A.kb_hi[h];
                 for (int kb = kb_lo; kb < kb_hi; kb += KB) {
-                    if (!mbar_wait(&full[s], ph, a.err, MM_ERR_TIMEOUT)) {
+                    if (!mbar_wait(&full[s], ph, a.err, MM_ERR_TIMEOUT, a.wait_limit)) {
                         *abort_flag = 1;
                         break;
                     }
@@ -1615,6 +1661,12 @@ __global__ void __launch_bounds__(pair_threads(CH, EPI, BATCH), 1)
                     }
                 }
                 umma_commit_pair_mc(&accf[b], 0x3);
+            }
+            if (*abort_flag) {
+                // every MMA this thread issued (into both CTAs' tensor memory) completes before
+                // either CTA frees it
+                umma_commit_pair_mc(mma_fin, 0x1);
+                mbar_wait(mma_fin, 0u, nullptr, 0, a.wait_limit);
             }
         }
         __syncwarp();
@@ -1659,7 +1711,7 @@ __global__ void __launch_bounds__(pair_threads(CH, EPI, BATCH), 1)
             const int b = int(lt % uint32_t(nsets));
             // the same decision in every lane: the warp stays converged for its collective instructions
             const bool acc_ready = __all_sync(
-                0xffffffffu, !*abort_flag && mbar_wait(&accf[b], (lt / uint32_t(nsets)) & 1u, a.err, MM_ERR_TIMEOUT));
+                0xffffffffu, !*abort_flag && mbar_wait(&accf[b], (lt / uint32_t(nsets)) & 1u, a.err, MM_ERR_TIMEOUT, a.wait_limit));
             if (!acc_ready) *abort_flag = 1;
             tc_fence_after();
             // drain in the matrix-fragment order: the warp's chunks of 16 output rows
@@ -1713,6 +1765,20 @@ __global__ void __launch_bounds__(pair_threads(CH, EPI, BATCH), 1)
     }
     tc_fence_before();
     __syncthreads();
+    if (warp == 0 && lane == 0 && *abort_flag) {
+        // A wait ran out (the flag is final here: every role of this CTA has finished).  No stage
+        // may still be receiving data when the CTAs exit: the leader waits (bounded) for the last
+        // arming of every slot, which completes once both CTAs' loads into that stage have landed;
+        // the peer, whose loads complete on the leader's barriers, gives its last loads the same time.
+        if (rank == 0) {
+            for (int q = 0; q < kSt; ++q)
+                if (armed & (1u << q)) mbar_wait(&full[q], (armed_ph >> q) & 1u, nullptr, 0, a.wait_limit);
+        } else {
+            const long long t0 = clock64();
+            while (clock64() - t0 < a.wait_limit) {
+            }
+        }
+    }
     // Every MMA (waited through the accumulator barriers), every load into either CTA's shared
     // memory and every store has completed: the CTAs only wait for each other before freeing
     // tensor memory and exiting.
@@ -1730,6 +1796,7 @@ struct TcBatchArgs {
     int stage_bytes, e_offset;
     float tb;               // tau * beta for the nonlinear epilogue
     int *err;
+    long long wait_limit;   // bounded waits give up after this many SM clocks
 };
 
 // Problem of work item P: the last problem whose first item is <= P.
@@ -1772,6 +1839,7 @@ __global__ void __launch_bounds__(kThreads, 1)
     uint64_t *tmem_empty = accf + 1;
     uint32_t *tmem_slot = reinterpret_cast<uint32_t *>(tmem_empty + 1);
     volatile int *abort_flag = reinterpret_cast<volatile int *>(tmem_slot + 1);
+    uint64_t *mma_fin = reinterpret_cast<uint64_t *>(tmem_slot + 2);  // abort: this CTA's MMAs have completed
 
     const int warp = threadIdx.x / 32, lane = threadIdx.x % 32;
     const int acc_cols_max = 2 * a.it_max;
@@ -1785,6 +1853,7 @@ __global__ void __launch_bounds__(kThreads, 1)
         }
         mbar_init(accf, 1);
         mbar_init(tmem_empty, kEpiWarps);
+        mbar_init(mma_fin, 1);
         *abort_flag = 0;
         mbar_fence_init();
         if (!BATCH) {
@@ -1803,6 +1872,7 @@ __global__ void __launch_bounds__(kThreads, 1)
     __syncthreads();
     tc_fence_after();
     const uint32_t tmem = *tmem_slot;
+    uint32_t armed = 0, armed_ph = 0;  // producer: slots armed, and the parity of their last arming
     const int rank = int(blockIdx.x & 1);
     const int64_t cid = blockIdx.x / 2, nclusters = gridDim.x / 2;
 
@@ -1838,12 +1908,14 @@ __global__ void __launch_bounds__(kThreads, 1)
                 for (int kb = pr.kb_lo[h]; kb < pr.kb_hi[h]; ++kb, ++gk) {
                     const int s = int(gk % kStages);
                     const uint32_t ph = (gk / kStages) & 1u;
-                    if (!mbar_wait(&empty[s], ph ^ 1u, a.err, MM_ERR_TIMEOUT)) {
+                    if (!mbar_wait(&empty[s], ph ^ 1u, a.err, MM_ERR_TIMEOUT, a.wait_limit)) {
                         *abort_flag = 1;
                         break;
                     }
                     uint8_t *st = smem + s * a.stage_bytes;
                     mbar_arrive_expect_tx(&full[s], tx);
+                    armed |= 1u << s;
+                    armed_ph = (armed_ph & ~(1u << s)) | (ph << s);
                     for (int c = 0; c < 2; ++c)
                         for (int p = 0; p < NP; ++p) {
                             uint8_t *dst = st + (c * NP + p) * kDataTileBytes;
@@ -1879,7 +1951,7 @@ __global__ void __launch_bounds__(kThreads, 1)
                 const uint32_t idesc_half = FX ? idesc_f16_f32(kTileM, it, !KMAJOR, false)
                                                : idesc_bf16_f32(kTileM, it, !KMAJOR, false);
                 const uint32_t idesc_half_neg = idesc_half | (1u << 13);  // negate A
-                if (lt > 0 && !mbar_wait(tmem_empty, (lt - 1) & 1u, a.err, MM_ERR_TIMEOUT)) {
+                if (lt > 0 && !mbar_wait(tmem_empty, (lt - 1) & 1u, a.err, MM_ERR_TIMEOUT, a.wait_limit)) {
                     *abort_flag = 1;
                     break;
                 }
@@ -1888,7 +1960,7 @@ __global__ void __launch_bounds__(kThreads, 1)
                 for (int kb = kb_lo; kb < kb_hi; ++kb, ++gk) {
                     const int s = int(gk % kStages);
                     const uint32_t ph = (gk / kStages) & 1u;
-                    if (!mbar_wait(&full[s], ph, a.err, MM_ERR_TIMEOUT)) {
+                    if (!mbar_wait(&full[s], ph, a.err, MM_ERR_TIMEOUT, a.wait_limit)) {
                         *abort_flag = 1;
                         break;
                     }
@@ -1916,6 +1988,10 @@ __global__ void __launch_bounds__(kThreads, 1)
                     umma_commit(&empty[s]);
                 }
                 umma_commit(accf);
+            }
+            if (*abort_flag) {  // every MMA this thread issued completes before tensor memory is freed
+                umma_commit(mma_fin);
+                mbar_wait(mma_fin, 0u, nullptr, 0, a.wait_limit);
             }
         }
         __syncwarp();
@@ -1958,7 +2034,7 @@ __global__ void __launch_bounds__(kThreads, 1)
                 lim = ldexpf(16384.0f, es_out);
                 if (ew == 0 && lane == 0) *pr.sc.s_out = ldexpf(1.0f, es_out);  // same value from every CTA
             }
-            const bool acc_ready = !*abort_flag && mbar_wait(accf, lt & 1u, a.err, MM_ERR_TIMEOUT);
+            const bool acc_ready = !*abort_flag && mbar_wait(accf, lt & 1u, a.err, MM_ERR_TIMEOUT, a.wait_limit);
             if (!acc_ready) *abort_flag = 1;
             tc_fence_after();
             // drain: up to kChunksPerWarp chunks of 16 rows, real and imaginary, both accumulators summed
@@ -2080,6 +2156,10 @@ __global__ void __launch_bounds__(kThreads, 1)
     }
     tc_fence_before();
     __syncthreads();
+    // A wait ran out (the flag is final here): every load into this CTA lands before it exits (bounded).
+    if (warp == 0 && lane == 0 && *abort_flag)
+        for (int q = 0; q < kStages; ++q)
+            if (armed & (1u << q)) mbar_wait(&full[q], (armed_ph >> q) & 1u, nullptr, 0, a.wait_limit);
     if (warp == 1) {
         tc_fence_after();
         tmem_dealloc(tmem, ncols);
@@ -2248,6 +2328,7 @@ static cudaError_t tc_setup(const TcState &si, const TcState &so, int mu, const 
     a.rdiv = epi.rdiv > 0 ? epi.rdiv : 1;
     a.out = (uint16_t *)out_pieces;
     a.err = d_err;
+    wait_hooks(&a.wait_limit, &a.withhold);
     a.rho = M.rho;
     a.sc = sc;
     const bool km = a.left == 1;
@@ -2495,6 +2576,8 @@ cudaError_t tc_mode_product_batched(const TcProblem *host_probs, const TcProblem
     a.stage_bytes = stage_bytes_for(max_tx);
     a.tb = float(epi.tb);
     a.err = d_err;
+    int64_t unused_withhold = -1;
+    wait_hooks(&a.wait_limit, &unused_withhold);
     const int smem = kStages * a.stage_bytes + 1024 + 256;
     return launch_batched(NP, tc_fixed(prec), kmajor, epi.kind, host_probs[0], dev_probs, a, smem, s);
 }
@@ -2555,6 +2638,7 @@ cudaError_t tc_pair_batch_launch(const void *host_recs, const void *dev_recs, in
         total += h[q].a.pairs;
     }
     a.err = d_err;
+    wait_hooks(&a.wait_limit, &a.withhold);
     const int NP = tc_pieces(prec);
     const bool fx = tc_fixed(prec);
     const int smem = pair_stages(1, 0, true) * a.stage_bytes + pair_staging_bytes(1, 0, true) + 1024 + 256;
