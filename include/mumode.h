@@ -232,14 +232,15 @@ mm_status mumode_product_noalloc(int d, const int64_t *n, int mu, const double *
  * ------------------------------------------------------------------- */
 
 /* E = exp(z (A + f B)) in FP64 on the device (for real z the same
- * series in real arithmetic, DGEMMs).  A_dev, B_dev: real n x n,
+ * series in real arithmetic).  A_dev, B_dev: real n x n,
  * row-major, device (B_dev may be NULL); E_dev: n x n complex interleaved
  * (2 n^2 doubles), device, overlapping neither.  Scaling and squaring of
  * the degree-18 Taylor polynomial (Paterson-Stockmeyer evaluation; the
  * products are cuBLAS ZGEMMs).  For a purely imaginary z = i w the call
  * computes cos(w M) + i sin(w M), M = A + f B, instead: degree-9
  * polynomials in (w M / 2^s)^2 and s angle doublings, all in real
- * arithmetic (cuBLAS DGEMMs), about a third of the flops.
+ * arithmetic (the library's own FP64 tensor-core GEMM, warp MMA), about a
+ * third of the flops; real z also runs on that GEMM.
  * norm_bound >= ||A + f B||_1 picks the
  * scaling; norm_bound <= 0 has the call compute the norm on the device and
  * synchronise the stream.  Otherwise stream-ordered.  Calls on one context

@@ -199,7 +199,8 @@ cudaError_t expm_device(ExpmWorkspace *w, int n, const double *A, const double *
 // Horner variable (2 products each, given Y, Y^2, Y^3), and the angle is
 // doubled s times by cos 2a = cos^2 a - sin^2 a, sin 2a = 2 sin a cos a (3
 // products each; errors then grow as in a complex squaring).  All products
-// are real (cuBLAS DGEMM, strided-batched over the batch of f values):
+// are real FP64 GEMMs batched over the f values (gemm_batch below: the FP64
+// tensor cores through warp MMA):
 // 8 + 3 s real products, against 10 + s complex ones (40 + 4 s real) for
 // the general series.
 
@@ -252,14 +253,113 @@ __global__ void interleave(int64_t total, const double *C, const double *S, doub
     }
 }
 
-// C_k = P_k Q_k for row-major n x n matrices, k < count (column-major Q^T-view times P^T-view)
-cublasStatus_t gemm_batch(cublasHandle_t h, int n, int count, const double *P, const double *Q, double *C,
-                          bool accumulate)
+// C_k = P_k Q_k (+ C_k when accumulating) for row-major n x n FP64 matrices, k < count, on the
+// FP64 tensor cores (warp MMA m8n8k4; tcgen05 has no FP64 kind).  B300 runs FP64 MMAs at a low
+// rate per SM, so the grid is what matters: block (x, y, k) computes the BT x BT tile (y, x) of
+// C_k with one warp per 16 x 16 outputs, and BT (32, or 16 when 32 would leave SMs idle) is
+// chosen so that the launch covers the GPU.  The k-dimension runs in chunks of 32 staged in
+// shared memory; each thread loads its part of the next chunk into registers while the MMAs of
+// the current one run.
+constexpr int kGemmK = 32;
+
+__device__ __forceinline__ void dmma_884(double (&d)[2], double a, double b)
 {
-    const double one = 1.0, beta = accumulate ? 1.0 : 0.0;
-    const long long stride = (long long)n * n;
-    return cublasDgemmStridedBatched(h, CUBLAS_OP_N, CUBLAS_OP_N, n, n, n, &one, Q, n, stride, P, n, stride, &beta, C,
-                                     n, stride, count);
+    asm volatile("mma.sync.aligned.m8n8k4.row.col.f64.f64.f64.f64 {%0, %1}, {%2}, {%3}, {%0, %1};"
+                 : "+d"(d[0]), "+d"(d[1])
+                 : "d"(a), "d"(b));
+}
+
+template <int BT>
+__global__ void __launch_bounds__(BT * BT / 8) dgemm_batched_kernel(int n, const double *__restrict__ P,
+                                                                      const double *__restrict__ Q,
+                                                                      double *__restrict__ C, int accumulate)
+{
+    constexpr int NT = BT * BT / 8;             // one warp per 16 x 16 outputs
+    constexpr int LP = BT * kGemmK / NT;         // elements of each operand a thread stages per chunk
+    __shared__ double sP[BT][kGemmK + 1];
+    __shared__ double sQ[kGemmK][BT + 1];
+    const int64_t off = int64_t(blockIdx.z) * n * n;
+    P += off;
+    Q += off;
+    C += off;
+    const int t = threadIdx.x, warp = t / 32, lane = t % 32;
+    const int g = lane / 4, q = lane % 4;  // fragment row / column group of this lane
+    const int wi = (warp % (BT / 16)) * 16, wc = (warp / (BT / 16)) * 16;
+    const int i0 = int(blockIdx.y) * BT, j0 = int(blockIdx.x) * BT;
+    double acc[2][2][2];
+#pragma unroll
+    for (int a = 0; a < 2; ++a)
+#pragma unroll
+        for (int b = 0; b < 2; ++b) acc[a][b][0] = acc[a][b][1] = 0.0;
+    double rp[LP], rq[LP];
+    auto fetch = [&](int k0) {
+#pragma unroll
+        for (int r = 0; r < LP; ++r) {
+            const int e = t + NT * r;
+            const int pk = e % kGemmK, pi = e / kGemmK;  // P: a row's consecutive k
+            const int qc = e % BT, qk = e / BT;          // Q: a k-row's consecutive columns
+            const int i = i0 + pi, kp = k0 + pk, kq = k0 + qk, j = j0 + qc;
+            rp[r] = (i < n && kp < n) ? P[int64_t(i) * n + kp] : 0.0;
+            rq[r] = (kq < n && j < n) ? Q[int64_t(kq) * n + j] : 0.0;
+        }
+    };
+    fetch(0);
+    for (int k0 = 0; k0 < n; k0 += kGemmK) {
+#pragma unroll
+        for (int r = 0; r < LP; ++r) {
+            const int e = t + NT * r;
+            sP[e / kGemmK][e % kGemmK] = rp[r];
+            sQ[e / BT][e % BT] = rq[r];
+        }
+        __syncthreads();
+        if (k0 + kGemmK < n) fetch(k0 + kGemmK);
+#pragma unroll
+        for (int kk = 0; kk < kGemmK; kk += 4) {
+            double a[2], b[2];
+#pragma unroll
+            for (int ti = 0; ti < 2; ++ti) a[ti] = sP[wi + 8 * ti + g][kk + q];
+#pragma unroll
+            for (int tj = 0; tj < 2; ++tj) b[tj] = sQ[kk + q][wc + 8 * tj + g];
+#pragma unroll
+            for (int ti = 0; ti < 2; ++ti)
+#pragma unroll
+                for (int tj = 0; tj < 2; ++tj) dmma_884(acc[ti][tj], a[ti], b[tj]);
+        }
+        __syncthreads();
+    }
+#pragma unroll
+    for (int ti = 0; ti < 2; ++ti) {
+        const int i = i0 + wi + 8 * ti + g;
+        if (i >= n) continue;
+#pragma unroll
+        for (int tj = 0; tj < 2; ++tj)
+#pragma unroll
+            for (int h = 0; h < 2; ++h) {
+                const int j = j0 + wc + 8 * tj + 2 * q + h;
+                if (j >= n) continue;
+                double *c = C + int64_t(i) * n + j;
+                *c = accumulate ? *c + acc[ti][tj][h] : acc[ti][tj][h];
+            }
+    }
+}
+
+cudaError_t gemm_batch(cudaStream_t s, int n, int count, const double *P, const double *Q, double *C,
+                       bool accumulate)
+{
+    if (count < 1 || count > 65535 || n < 1) return cudaErrorInvalidValue;
+    int sms = 148;
+    int dev = 0;
+    if (cudaGetDevice(&dev) == cudaSuccess) cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+    const int64_t t32 = (n + 31) / 32;
+    if (int64_t(count) * t32 * t32 >= 2 * int64_t(sms)) {
+        dgemm_batched_kernel<32><<<dim3(unsigned(t32), unsigned(t32), unsigned(count)), 128, 0, s>>>(
+            n, P, Q, C, accumulate ? 1 : 0);
+    } else {
+        const unsigned t16 = unsigned((n + 15) / 16);
+        dgemm_batched_kernel<16><<<dim3(t16, t16, unsigned(count)), 32, 0, s>>>(n, P, Q, C, accumulate ? 1 : 0);
+    }
+    count_launch();
+    return cudaGetLastError();
 }
 
 }  // namespace
@@ -274,18 +374,13 @@ void expm_batch_destroy(ExpmBatch *w)
         }
     if (w->f) cudaFree(w->f);
     w->f = nullptr;
-    if (w->blas) cublasDestroy(static_cast<cublasHandle_t>(w->blas));
-    w->blas = nullptr;
     w->n = w->cap = 0;
 }
 
 cudaError_t expm_batch_init(ExpmBatch *w, int n, int cap)
 {
-    if (w->n >= n && w->cap >= cap && w->blas) return cudaSuccess;
+    if (w->n >= n && w->cap >= cap) return cudaSuccess;
     expm_batch_destroy(w);
-    cublasHandle_t h = nullptr;
-    if (cublasCreate(&h) != CUBLAS_STATUS_SUCCESS) return cudaErrorUnknown;
-    w->blas = h;
     const size_t bytes = sizeof(double) * size_t(n) * n * size_t(cap);
     for (auto &b : w->buf) {
         cudaError_t e = cudaMalloc(&b, bytes);
@@ -350,9 +445,7 @@ cudaError_t expm_imag_batched(ExpmBatch *w, int n, const double *A, const double
                               double wim, double norm_bound, double2 *E, cudaStream_t s, double mu, double theta)
 {
     // exp(i w M) = exp(i w mu) exp(i w (M - mu I)): norm_bound bounds ||M - mu I||_1
-    if (w->n < n || w->cap < count || count < 1 || !w->blas) return cudaErrorInvalidValue;
-    cublasHandle_t h = static_cast<cublasHandle_t>(w->blas);
-    if (cublasSetStream(h, s) != CUBLAS_STATUS_SUCCESS) return cudaErrorUnknown;
+    if (w->n < n || w->cap < count || count < 1) return cudaErrorInvalidValue;
     if (!(theta >= 1.0 && theta <= 2.0)) return cudaErrorInvalidValue;
     const double za = std::fabs(wim) * norm_bound;
     int sq = 0;
@@ -370,9 +463,9 @@ cudaError_t expm_imag_batched(ExpmBatch *w, int n, const double *A, const double
                                    X);
     count_launch();
     if ((e = cudaGetLastError()) != cudaSuccess) return e;
-    if (gemm_batch(h, n, count, X, X, Y, false) != CUBLAS_STATUS_SUCCESS ||
-        gemm_batch(h, n, count, Y, Y, Y2, false) != CUBLAS_STATUS_SUCCESS ||
-        gemm_batch(h, n, count, Y2, Y, Y3, false) != CUBLAS_STATUS_SUCCESS)
+    if (gemm_batch(s, n, count, X, X, Y, false) != cudaSuccess ||
+        gemm_batch(s, n, count, Y, Y, Y2, false) != cudaSuccess ||
+        gemm_batch(s, n, count, Y2, Y, Y3, false) != cudaSuccess)
         return cudaErrorUnknown;
     // a[j] = (-1)^j / (2j)! (cos) and (-1)^j / (2j+1)! (sin), j <= 9
     double ac[10], as[10];
@@ -389,25 +482,25 @@ cudaError_t expm_imag_batched(ExpmBatch *w, int n, const double *A, const double
         count_launch();
         combo_batch<<<g, 256, 0, s>>>(n, count, a[3], a[4], a[5], 0.0, Y, Y2, nullptr, T1);
         count_launch();
-        if (gemm_batch(h, n, count, Y3, T0, T1, true) != CUBLAS_STATUS_SUCCESS) return cudaErrorUnknown;
+        if (gemm_batch(s, n, count, Y3, T0, T1, true) != cudaSuccess) return cudaErrorUnknown;
         combo_batch<<<g, 256, 0, s>>>(n, count, a[0], a[1], a[2], 0.0, Y, Y2, nullptr, out);
         count_launch();
-        if (gemm_batch(h, n, count, Y3, T1, out, true) != CUBLAS_STATUS_SUCCESS) return cudaErrorUnknown;
+        if (gemm_batch(s, n, count, Y3, T1, out, true) != cudaSuccess) return cudaErrorUnknown;
         return cudaGetLastError();
     };
     if ((e = poly(ac, C)) != cudaSuccess) return e;
     // the sin polynomial goes into Y2: its last combination reads Y2 element by element in place,
     // and Y2 is not needed after it
     if ((e = poly(as, Y2)) != cudaSuccess) return e;
-    if (gemm_batch(h, n, count, X, Y2, S, false) != CUBLAS_STATUS_SUCCESS) return cudaErrorUnknown;
+    if (gemm_batch(s, n, count, X, Y2, S, false) != cudaSuccess) return cudaErrorUnknown;
     // X, Y and Y3 are free now: products of the doublings
     double *CC = X, *SS = Y, *SC = Y3;
     for (int k = 0; k < sq; ++k) {
         // C' = C C - S S, S' = 2 S C (errors grow as in a complex squaring; the shorter
         // C' = 2 C C - I assumes C C + S S = I and lets them grow twice as fast)
-        if (gemm_batch(h, n, count, C, C, CC, false) != CUBLAS_STATUS_SUCCESS ||
-            gemm_batch(h, n, count, S, S, SS, false) != CUBLAS_STATUS_SUCCESS ||
-            gemm_batch(h, n, count, S, C, SC, false) != CUBLAS_STATUS_SUCCESS)
+        if (gemm_batch(s, n, count, C, C, CC, false) != cudaSuccess ||
+            gemm_batch(s, n, count, S, S, SS, false) != cudaSuccess ||
+            gemm_batch(s, n, count, S, C, SC, false) != cudaSuccess)
             return cudaErrorUnknown;
         double_angle<<<g, 256, 0, s>>>(total, CC, SS, SC, C, S);
         count_launch();
@@ -474,15 +567,13 @@ cudaError_t hkp_propagator_device(ExpmWorkspace *wz, ExpmBatch *wb, int m, const
 // ---- real z: the Taylor series in real arithmetic ----------------------------------
 //
 // For real M and real z the series of expm_device runs on real matrices
-// (DGEMM): X = z M / 2^s, T = B_0 + X^4 (B_1 + X^4 (B_2 + X^4 (B_3 + X^4 B_4))),
+// (gemm_batch): X = z M / 2^s, T = B_0 + X^4 (B_1 + X^4 (B_2 + X^4 (B_3 + X^4 B_4))),
 // E = T^(2^s).  Squaring keeps the small entries of decaying flows (a
 // cosh / sinh split would cancel them).
 cudaError_t expm_real_device(ExpmBatch *w, int n, const double *A, const double *B, double f, double z,
                              double norm_bound, double2 *E, cudaStream_t s)
 {
-    if (w->n < n || w->cap < 1 || !w->blas) return cudaErrorInvalidValue;
-    cublasHandle_t h = static_cast<cublasHandle_t>(w->blas);
-    if (cublasSetStream(h, s) != CUBLAS_STATUS_SUCCESS) return cudaErrorUnknown;
+    if (w->n < n || w->cap < 1) return cudaErrorInvalidValue;
     const double za = std::fabs(z) * norm_bound;
     int sq = 0;
     if (za > 1.0) sq = int(std::ceil(std::log2(za)));
@@ -494,9 +585,9 @@ cudaError_t expm_real_device(ExpmBatch *w, int n, const double *A, const double 
     count_launch();
     cudaError_t e = cudaGetLastError();
     if (e != cudaSuccess) return e;
-    if (gemm_batch(h, n, 1, X, X, X2, false) != CUBLAS_STATUS_SUCCESS ||
-        gemm_batch(h, n, 1, X2, X, X3, false) != CUBLAS_STATUS_SUCCESS ||
-        gemm_batch(h, n, 1, X2, X2, X4, false) != CUBLAS_STATUS_SUCCESS)
+    if (gemm_batch(s, n, 1, X, X, X2, false) != cudaSuccess ||
+        gemm_batch(s, n, 1, X2, X, X3, false) != cudaSuccess ||
+        gemm_batch(s, n, 1, X2, X2, X4, false) != cudaSuccess)
         return cudaErrorUnknown;
     double c[19];
     c[0] = 1.0;
@@ -506,11 +597,11 @@ cudaError_t expm_real_device(ExpmBatch *w, int n, const double *A, const double 
     for (int j = 3; j >= 0; --j) {
         combo_batch<<<g, 256, 0, s>>>(n, 1, c[4 * j], c[4 * j + 1], c[4 * j + 2], c[4 * j + 3], X, X2, X3, nxt);
         count_launch();
-        if (gemm_batch(h, n, 1, X4, cur, nxt, true) != CUBLAS_STATUS_SUCCESS) return cudaErrorUnknown;
+        if (gemm_batch(s, n, 1, X4, cur, nxt, true) != cudaSuccess) return cudaErrorUnknown;
         std::swap(cur, nxt);
     }
     for (int k = 0; k < sq; ++k) {
-        if (gemm_batch(h, n, 1, cur, cur, nxt, false) != CUBLAS_STATUS_SUCCESS) return cudaErrorUnknown;
+        if (gemm_batch(s, n, 1, cur, cur, nxt, false) != cudaSuccess) return cudaErrorUnknown;
         std::swap(cur, nxt);
     }
     interleave<<<g, 256, 0, s>>>(nn, cur, nullptr, 1.0, 0.0, E);

@@ -126,7 +126,6 @@ cudaError_t expm_device(ExpmWorkspace *w, int n, const double *A, const double *
 // by value.
 struct ExpmBatch {
     int n = 0, cap = 0;
-    void *blas = nullptr;    // cublasHandle_t
     double *buf[8] = {};     // cap real n x n matrices each
     double *f = nullptr;     // cap doubles
 };
