@@ -88,7 +88,9 @@ struct TcScales {
 
 // Kernel of a tensor-core product: the CTA-pair kernel with row tiles of at
 // most 64 (two accumulator sets) or 128 rows (one set), or the one-SM kernel.
-enum TcVariant { kTcPair64 = 0, kTcPair128 = 1, kTcOneSM = 2, kTcVariants = 3 };
+// kTcChain: the CTA-pair kernel with row tiles of at most 64, a whole call's products in one
+// persistent launch (Tucker steps with F16X6; elsewhere it launches like kTcPair64).
+enum TcVariant { kTcPair64 = 0, kTcPair128 = 1, kTcOneSM = 2, kTcChain = 3, kTcVariants = 4 };
 // The variant a plan starts with: kTcPair64, or what the environment forces
 // (MM_TC_1SM set to other than 0: kTcOneSM; MM_PAIR_TILE=128: kTcPair128).
 TcVariant tc_default_variant();
@@ -215,9 +217,17 @@ cudaError_t tc_mode_product(const TcState &st_in, const TcState &st_out, int mu,
 // with row tiles of at most 64 (use tc_mode_product_batched).
 size_t tc_pair_record_bytes();
 size_t tc_pair_record_align();
+// chain_pos < 0: a record of a batched launch; >= 0: the product's position in a chain (the
+// single launch's stage layout, F16X6 only).
 cudaError_t tc_pair_record_build(const TcState &si, const TcState &so, int mu, const TcMatrix &M, mm_prec prec,
                                  const void *in_pieces, void *out_pieces, const TcScales &sc, void *rec, bool *kmajor,
-                                 int64_t *items);
+                                 int64_t *items, int chain_pos = -1);
+// One persistent launch over a chain of products (records built with chain positions 0, 1, ..,
+// nprod - 1, their first items set in order); `done`: nprod counters and `tally`: tc_chain_ctas()
+// x nprod words, all zero at the launch.
+cudaError_t tc_pair_chain_launch(const void *host_recs, const void *dev_recs, int nprod, unsigned *done,
+                                 unsigned *tally, int *d_err, cudaStream_t s);
+int tc_chain_ctas();  // the most CTAs a chained launch uses (the SM count)
 void tc_pair_record_set_begin(void *rec, int64_t begin);
 bool tc_pair_batch_compatible(const void *host_recs, int nprob);  // same row tile size in all records
 cudaError_t tc_pair_batch_launch(const void *host_recs, const void *dev_recs, int nprob, bool kmajor, mm_prec prec,

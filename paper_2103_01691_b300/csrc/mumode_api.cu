@@ -25,6 +25,7 @@ struct mm_ctx {
     // optional CUDA-event timing of the mode-product kernels
     bool timing = false;
     std::vector<std::pair<cudaEvent_t, cudaEvent_t>> events;
+    std::vector<int> event_products;  // mode products each event pair brackets (a chained launch: many)
     size_t events_used = 0;
     mm::ExpmWorkspace expm;  // mm_expm_device, complex z
     mm::ExpmBatch expmb;     // mm_expm_device, imaginary z
@@ -45,6 +46,14 @@ struct mm_plan {
     bool fixed = false;  // MM_PREC_F16X6
     int npieces = 0;
     mm::TcVariant variant = mm::kTcPair64;  // tensor-core kernel (mm_plan_autotune, mm_plan_set_config)
+    // kTcChain: the records of a chained call (one launch for all products of nsteps steps) and its
+    // completion counters, kept for the last nsteps used
+    int64_t chain_steps = -1;
+    int chain_order[mm::kMaxDims] = {};
+    int chain_nprod = 0;
+    std::vector<uint8_t> chain_host;
+    void *chain_dev = nullptr;
+    unsigned *chain_done = nullptr;  // nprod completion counters, then tc_chain_ctas() x nprod tally words
     // fixed-point state scale words (device): scale[d], max[2][d], one work word
     float *d_scale = nullptr;
     unsigned *d_max = nullptr;
@@ -245,8 +254,9 @@ void left_right(int d, const int64_t *n, int mu, int64_t *left, int64_t *right)
     for (int v = mu; v < d; ++v) *right *= n[v];
 }
 
-// Events bracketing one mode-product launch when timing is on.
-cudaEvent_t timing_event(mm_ctx *c, bool start)
+// Events bracketing one mode-product launch when timing is on (the end event records how many
+// mode products the launch ran: one, or a chained call's all).
+cudaEvent_t timing_event(mm_ctx *c, bool start, int products = 1)
 {
     if (!c->timing) return nullptr;
     if (start) {
@@ -258,9 +268,11 @@ cudaEvent_t timing_event(mm_ctx *c, bool start)
                 return nullptr;
             }
             c->events.push_back({a, b});
+            c->event_products.push_back(1);
         }
         return c->events[c->events_used].first;
     }
+    c->event_products[c->events_used] = products;
     return c->events[c->events_used++].second;
 }
 
@@ -298,6 +310,83 @@ mm_status tc_sweep(mm_plan *p, mm::TcMatrix *const *M, int &cur, const mm::TcEpi
         cur = 1 - cur;
     }
     ++p->sweep;
+    return MM_OK;
+}
+
+// kTcChain: the records of a chained call of nsteps Tucker steps with the plan's matrices, in
+// the plan's mode order: product k d + q of the call is position q of sweep k, with the buffers and
+// scale words tc_sweep gives it (tc_begin precedes, so sweep 0 and buffer 0 come first).  Built
+// once per (nsteps, order) and kept; a rebuild drops the plan's graphs, which point at the old
+// records.  false: the products cannot be chained (no pair tiling with row tiles of at most 64,
+// row tiles of different sizes, too many products); the caller launches them one by one.
+void drop_graphs(mm_plan *p);
+
+bool chain_prepare(mm_plan *p, int64_t nsteps)
+{
+    const int d = p->d;
+    if (p->chain_steps == nsteps && std::equal(p->order, p->order + d, p->chain_order)) return true;
+    if (!p->tc || !p->fixed || p->hermite || nsteps < 1 || nsteps * d > (int64_t(1) << 20)) return false;
+    const int nprod = int(nsteps * d);
+    const size_t rb = mm::tc_pair_record_bytes(), al = mm::tc_pair_record_align();
+    std::vector<uint8_t> host(rb * size_t(nprod) + al, 0);
+    uint8_t *base = reinterpret_cast<uint8_t *>((reinterpret_cast<uintptr_t>(host.data()) + al - 1) / al * al);
+    int64_t begin = 0;
+    for (int64_t k = 0; k < nsteps; ++k)
+        for (int q = 0; q < d; ++q) {
+            const int pos = int(k * d + q), cur = pos % 2, mu = p->order[q];
+            const int t = int(k % 3), par = int(k & 1);  // as tc_sweep with p->sweep = k
+            mm::TcScales sc;
+            sc.s_in = p->d_scale + par * d + q;
+            sc.s_out = (q + 1 < d) ? p->d_scale + par * d + q + 1 : p->d_scale + (1 - par) * d;
+            sc.max_prev = p->d_max + ((t + 2) % 3) * d + q;
+            sc.max_cur = p->d_max + t * d + q;
+            sc.zero_next = p->d_max + ((t + 1) % 3) * d + q;
+            bool km = false;
+            int64_t items = 0;
+            void *rec = base + rb * size_t(pos);
+            if (mm::tc_pair_record_build(p->st, p->st, mu, p->Etc[mu - 1], p->prec, p->work[cur], p->work[1 - cur], sc,
+                                         rec, &km, &items, pos) != cudaSuccess)
+                return false;
+            mm::tc_pair_record_set_begin(rec, begin);
+            begin += items;
+        }
+    if (!mm::tc_pair_batch_compatible(base, nprod)) return false;
+    void *dev = nullptr;
+    unsigned *done = nullptr;
+    if (cudaMalloc(&dev, rb * size_t(nprod)) != cudaSuccess) return false;
+    const size_t counters = size_t(nprod) * (1 + size_t(mm::tc_chain_ctas()));
+    if (cudaMalloc(&done, sizeof(unsigned) * counters) != cudaSuccess ||
+        cudaMemcpy(dev, base, rb * size_t(nprod), cudaMemcpyHostToDevice) != cudaSuccess) {
+        cudaFree(dev);
+        if (done) cudaFree(done);
+        return false;
+    }
+    drop_graphs(p);
+    if (p->chain_dev) cudaFree(p->chain_dev);
+    if (p->chain_done) cudaFree(p->chain_done);
+    p->chain_host.assign(base, base + rb * size_t(nprod));
+    p->chain_dev = dev;
+    p->chain_done = done;
+    p->chain_nprod = nprod;
+    p->chain_steps = nsteps;
+    std::copy(p->order, p->order + d, p->chain_order);
+    return true;
+}
+
+// The products of a chained call (chain_prepare for nsteps has succeeded), between tc_begin and tc_end.
+mm_status chain_run(mm_plan *p, int &cur, cudaStream_t s)
+{
+    const size_t counters = size_t(p->chain_nprod) * (1 + size_t(mm::tc_chain_ctas()));
+    cudaError_t e = cudaMemsetAsync(p->chain_done, 0, sizeof(unsigned) * counters, s);
+    if (e != cudaSuccess) return cuda_fail(e, "chain counters");
+    cudaEvent_t ev0 = timing_event(p->ctx, true);
+    if (ev0) cudaEventRecord(ev0, s);
+    e = mm::tc_pair_chain_launch(p->chain_host.data(), p->chain_dev, p->chain_nprod, p->chain_done,
+                                 p->chain_done + p->chain_nprod, p->ctx->d_err, s);
+    if (ev0) cudaEventRecord(timing_event(p->ctx, false, p->chain_nprod), s);
+    if (e != cudaSuccess) return cuda_fail(e, "chained tensor-core launch");
+    p->sweep += p->chain_steps;
+    cur = (p->chain_nprod % 2 == 0) ? cur : 1 - cur;
     return MM_OK;
 }
 
@@ -581,7 +670,8 @@ mm_status mm_plan_get_config(const mm_plan *p, int *variant, int *order_out)
 mm_status mm_plan_set_config(mm_plan *p, int variant, const int *order)
 {
     if (!p) return fail(MM_ERR_INVALID_ARG, "plan is NULL");
-    if (variant < 0 || variant >= mm::kTcVariants) return fail(MM_ERR_INVALID_ARG, "variant %d outside 0..2", variant);
+    if (variant < 0 || variant >= mm::kTcVariants)
+        return fail(MM_ERR_INVALID_ARG, "variant %d outside 0..%d", variant, mm::kTcVariants - 1);
     if (order) {
         if (p->hermite) return fail(MM_ERR_UNSUPPORTED, "the mode order of a Hermite plan is fixed");
         bool seen[mm::kMaxDims] = {};
@@ -616,6 +706,7 @@ mm_status autotune_with(mm_plan *p, const void *u_dev, int64_t nsteps, void *str
     std::vector<int> variants;
     if (p->tc) variants = {mm::kTcPair64, mm::kTcPair128, mm::kTcOneSM};
     else variants = {int(p->variant)};
+    if (p->tc && p->fixed && orders_too && !p->hermite) variants.push_back(mm::kTcChain);  // Tucker steps only
     std::vector<std::vector<int>> orders;
     std::vector<int> ord(p->order, p->order + p->d);
     if (orders_too && !p->hermite && p->d <= 4) {
@@ -743,15 +834,17 @@ mm_status mm_kernel_timing_read(mm_ctx *ctx, double *total_ms, int64_t *launches
 {
     if (!ctx || !total_ms || !launches) return fail(MM_ERR_INVALID_ARG, "NULL argument");
     double tot = 0.0;
+    int64_t products = 0;
     for (size_t k = 0; k < ctx->events_used; ++k) {
         cudaError_t e = cudaEventSynchronize(ctx->events[k].second);
         float ms = 0.f;
         if (e == cudaSuccess) e = cudaEventElapsedTime(&ms, ctx->events[k].first, ctx->events[k].second);
         if (e != cudaSuccess) return cuda_fail(e, "event timing");
         tot += ms;
+        products += ctx->event_products[k];
     }
     *total_ms = tot;
-    *launches = int64_t(ctx->events_used);
+    *launches = products;
     ctx->events_used = 0;
     return MM_OK;
 }
@@ -1009,14 +1102,20 @@ mm_status mumode_step(mm_plan *p, void *u_dev, int64_t nsteps, void *stream)
             return MM_OK;
         });
     }
+    // kTcChain: every product of the call in one persistent launch (records prepared outside any capture)
+    const bool chained = p->variant == mm::kTcChain && chain_prepare(p, nsteps);
     return run_graphed(p, 0, u_dev, nsteps, s, 0.0, 0.0, [&]() -> mm_status {
         mm_status r;
         int cur = 0;
         mm::TcMatrix *M[mm::kMaxDims];
         for (int v = 0; v < p->d; ++v) M[v] = &p->Etc[v];
         if ((r = tc_begin(p, M, u_dev, s))) return r;
-        for (int64_t k = 0; k < nsteps; ++k)
-            if ((r = tc_sweep(p, M, cur, mm::TcEpilogue{}, s))) return r;
+        if (chained) {
+            if ((r = chain_run(p, cur, s))) return r;
+        } else {
+            for (int64_t k = 0; k < nsteps; ++k)
+                if ((r = tc_sweep(p, M, cur, mm::TcEpilogue{}, s))) return r;
+        }
         return tc_end(p, cur, u_dev, s);
     });
 }
@@ -1066,6 +1165,8 @@ void mm_plan_destroy(mm_plan *p)
     if (p->d_scale) cudaFree(p->d_scale);
     if (p->d_max) cudaFree(p->d_max);
     if (p->d_work) cudaFree(p->d_work);
+    if (p->chain_dev) cudaFree(p->chain_dev);
+    if (p->chain_done) cudaFree(p->chain_done);
     for (int v = 0; v < mm::kMaxDims; ++v) {
         if (p->H0dev[v]) cudaFree(p->H0dev[v]);
         if (p->Gdev[v]) cudaFree(p->Gdev[v]);

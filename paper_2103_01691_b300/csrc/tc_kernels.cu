@@ -789,6 +789,11 @@ struct TcArgs {
     // test hook: the stage (counted over the launch, per CTA) whose loads the producers skip,
     // so that the MMA's wait for it runs out; -1: none
     int64_t withhold;
+    // chained launches (one launch over a sequence of products): completion counters, one per
+    // product, and the count that marks a product complete (one signal per CTA)
+    unsigned *done;
+    unsigned done_target;
+    unsigned *tally;        // [CTA][product]: the CTA's epilogue warps that have stored the product
     // fixed-point mode
     const float *rho;
     TcScales sc;
@@ -806,6 +811,8 @@ struct TcPairProblem {
     CUtensorMap mapX, mapE, mapY;
     TcArgs a;
     int64_t pairs_begin;
+    int km;    // chained launches: direction 1 (K-major data) or not
+    int prod;  // chained launches: position of the product in the chain
 };
 
 // The problem of work item P (records sorted by pairs_begin, the first at 0).
@@ -818,6 +825,15 @@ __device__ __forceinline__ const TcPairProblem &pair_problem(const TcPairProblem
         else hi = mid - 1;
     }
     return many[lo];
+}
+
+// The same for a role that visits items in increasing order: `at` (start 0) is the record of its
+// previous item, and the search moves forward from there (usually not at all, or by one record).
+__device__ __forceinline__ const TcPairProblem &pair_problem_next(const TcPairProblem *many, int nprob, int64_t P,
+                                                                  int &at)
+{
+    while (at + 1 < nprob && many[at + 1].pairs_begin <= P) ++at;
+    return many[at];
 }
 
 constexpr int kEpiWarps = 16;      // four per TMEM lane quarter
@@ -1433,21 +1449,27 @@ __host__ __device__ constexpr int pair_staging_bytes(int CH, int EPI, bool BATCH
 // accumulator set once the epilogue warps of both CTAs have drained it:
 // the peer's warps arrive on their own barrier, which one thread of the
 // peer relays to the leader's.
-template <int NP, bool KMAJOR, int EPI, bool FX, int CH, bool BATCH>
-__global__ void __launch_bounds__(pair_threads(CH, EPI, BATCH), 1)
+template <int NP, bool KMAJOR, int EPI, bool FX, int CH, bool BATCH, bool CHAIN = false>
+__global__ void __launch_bounds__(pair_threads(CH, EPI, BATCH && !CHAIN), 1)
     tc_pair_kernel(const __grid_constant__ CUtensorMap mapX, const __grid_constant__ CUtensorMap mapE,
                    const __grid_constant__ CUtensorMap mapY, TcArgs a, const TcPairProblem *__restrict__ many,
                    int nprob, int64_t total)
 {
     // BATCH: items P < total of many problems (records `many`, sorted by pairs_begin); `a` then
-    // carries only what all problems share (row tiles of the same size, stage layout, error word)
+    // carries only what all problems share (row tiles of the same size, stage layout, error word).
+    // CHAIN (with BATCH): the records are a sequence of products, each reading what the previous
+    // one wrote; a product's loads wait until every epilogue warp of the grid has signalled the
+    // previous product complete, and the records say per product whether its data is K-major.
+    // Chained launches keep the single launch's warps and stages.
+    static_assert(!CHAIN || (BATCH && EPI == 0), "a chain is a batched launch of plain products");
+    constexpr bool BCFG = BATCH && !CHAIN;  // the batched launches' warp and stage configuration
     const int64_t items = BATCH ? total : a.pairs;
-    constexpr int kSt = pair_stages(CH, EPI, BATCH);
-    constexpr int KB = pair_kb_per_stage(CH, EPI, BATCH);  // k-blocks per stage
+    constexpr int kSt = pair_stages(CH, EPI, BCFG);
+    constexpr int KB = pair_kb_per_stage(CH, EPI, BCFG);  // k-blocks per stage
     extern __shared__ __align__(1024) uint8_t smem_raw[];
     uint8_t *smem = reinterpret_cast<uint8_t *>((reinterpret_cast<uintptr_t>(smem_raw) + 1023) & ~uintptr_t(1023));
-    uint8_t *staging = smem + kSt * a.stage_bytes;  // pair_epi_warps(CH, EPI, BATCH) x kStagingPerWarp
-    uint64_t *full = reinterpret_cast<uint64_t *>(staging + pair_staging_bytes(CH, EPI, BATCH));
+    uint8_t *staging = smem + kSt * a.stage_bytes;  // pair_epi_warps(CH, EPI, BCFG) x kStagingPerWarp
+    uint64_t *full = reinterpret_cast<uint64_t *>(staging + pair_staging_bytes(CH, EPI, BCFG));
     uint64_t *empty = full + kSt;
     uint64_t *accf = empty + kSt;  // [2]: accumulator set b holds a finished item
     uint64_t *tmem_empty = accf + 2;       // [2]: accumulator set b has been drained
@@ -1471,7 +1493,7 @@ __global__ void __launch_bounds__(pair_threads(CH, EPI, BATCH), 1)
         for (int b = 0; b < 2; ++b) {
             mbar_init(&accf[b], 1);
             // this CTA's epilogue warps, and in the leader the peer's relay
-            mbar_init(&tmem_empty[b], pair_epi_warps(CH, EPI, BATCH) + (rank == 0 ? 1 : 0));
+            mbar_init(&tmem_empty[b], pair_epi_warps(CH, EPI, BCFG) + (rank == 0 ? 1 : 0));
         }
         mbar_init(mma_fin, 1);
         *abort_flag = 0;
@@ -1495,7 +1517,7 @@ __global__ void __launch_bounds__(pair_threads(CH, EPI, BATCH), 1)
     // writes data of the previous kernel (input pieces, scale words) only after it has completed.
     if (threadIdx.x == 0) griddep_launch_dependents();
     griddep_wait();
-    if (FX && blockIdx.x == 0 && threadIdx.x == 0) {
+    if (FX && !CHAIN && blockIdx.x == 0 && threadIdx.x == 0) {
         if (!BATCH) {
             if (a.sc.zero_next) *a.sc.zero_next = 0u;
         } else {
@@ -1516,17 +1538,38 @@ __global__ void __launch_bounds__(pair_threads(CH, EPI, BATCH), 1)
             int s = 0;
             uint32_t ph = 0;  // ring position
             int64_t g = 0;    // stages reached over the launch
+            int ready = 0;    // CHAIN: products up to this one may be loaded
+            int rec_at = 0;   // BATCH: the record of the previous item
             const int e_rows = 3 * half / 4;  // 128-byte rows of one block triple
             for (int64_t P = cid; P < items && !*abort_flag; P += nclusters) {
-                const TcPairProblem *pr = BATCH ? &pair_problem(many, nprob, P) : nullptr;
+                const TcPairProblem *pr = BATCH ? &pair_problem_next(many, nprob, P, rec_at) : nullptr;
                 const TcArgs &A = BATCH ? pr->a : a;
                 const CUtensorMap *mx = BATCH ? &pr->mapX : &mapX, *me = BATCH ? &pr->mapE : &mapE;
                 const int64_t Pl = BATCH ? P - pr->pairs_begin : P;
                 const int64_t tile = (Pl / A.ni) * 2 + rank;
                 const int h = int(Pl % A.ni);
+                const bool km = CHAIN ? pr->km != 0 : KMAJOR;
+                if (CHAIN && pr->prod > ready) {
+                    // the product's tensor maps are fetched while the wait below runs, and the next
+                    // product's as well
+                    tma_prefetch_desc(mx);
+                    tma_prefetch_desc(me);
+                    if (pr->prod + 1 < nprob) {
+                        tma_prefetch_desc(&pr[1].mapX);
+                        tma_prefetch_desc(&pr[1].mapE);
+                    }
+                    // the previous product's output is this one's input: wait until every CTA has
+                    // signalled it stored (bounded), then load through TMA
+                    if (!counter_wait(a.done + (pr->prod - 1), a.done_target, a.err, MM_ERR_TIMEOUT, a.wait_limit)) {
+                        *abort_flag = 1;
+                        break;
+                    }
+                    fence_proxy_async_global();
+                    ready = pr->prod;
+                }
                 // MN-major: the two 64-point atoms of the tile (slab row, first point), past the end zero fill
                 int ac_l[2] = {0, 0}, ac_r[2] = {0, 0};
-                if (!KMAJOR) {
+                if (!km) {
                     for (int q = 0; q < 2; ++q) {
                         const int64_t atom = 2 * tile + q;
                         int64_t r = atom / A.aps;
@@ -1559,7 +1602,7 @@ __global__ void __launch_bounds__(pair_threads(CH, EPI, BATCH), 1)
                         }
                         // all 2 NP piece planes in one box (K-major: [plane][128 points][16 KB k]) or one box
                         // per atom (MN-major: [atom][plane][16 k][64 points])
-                        if (KMAJOR) {
+                        if (km) {
                             tma_load_3d_pair(mx, fb, st, kb * kBK, k_row, 0);
                         } else {
                             tma_load_4d_pair(mx, fb, st, ac_l[0], kb * kBK, ac_r[0], 0);
@@ -1599,20 +1642,30 @@ __global__ void __launch_bounds__(pair_threads(CH, EPI, BATCH), 1)
             // their start-address field (bits 0..13, wide enough for every shared-memory address of
             // the CTA).  This thread shares its SM sub-partition with four busy epilogue warps, so
             // few instructions per MMA keep the tensor pipe fed.
-            const uint32_t idesc = FX ? idesc_f16_f32(2 * kTileM, 2 * a.it, !KMAJOR, false)
-                                      : idesc_bf16_f32(2 * kTileM, 2 * a.it, !KMAJOR, false);
+            auto idesc_for = [&](bool km) {
+                return FX ? idesc_f16_f32(2 * kTileM, 2 * a.it, !km, false) : idesc_bf16_f32(2 * kTileM, 2 * a.it, !km, false);
+            };
+            const uint32_t idesc = idesc_for(KMAJOR || CHAIN), idesc_mn = idesc_for(false);
             const uint32_t st0 = smem_u32(smem), est0 = st0 + uint32_t(a.e_offset);
-            uint64_t adesc[2][NP], bdesc[2][NP];  // [real plane, imaginary plane][piece]
+            // [real plane, imaginary plane][piece]; CHAIN: adesc for K-major data, adesc_mn for MN-major
+            uint64_t adesc[2][NP], adesc_mn[2][NP], bdesc[2][NP];
+            auto data_descs = [&](bool km, uint64_t(&ad)[2][NP]) {
+#pragma unroll
+                for (int p = 0; p < NP; ++p) {
+                    // K-major: plane tiles of KB x 4 KB (rows of 32 KB bytes, 8-row swizzle atoms of 256 KB
+                    // bytes); MN-major: plane tiles of KB x 2 KB (16 KB k-rows of 128 bytes) per atom, atoms
+                    // 2 NP KB x 2 KB apart
+                    const uint32_t pb = km ? uint32_t(KB * kDataTileBytes) : uint32_t(KB * 2048);
+                    const uint32_t xre = st0 + uint32_t(p) * pb, xim = st0 + uint32_t(NP + p) * pb;
+                    constexpr uint32_t kmswz = KB == 2 ? kSwz64 : kSwz32;
+                    ad[0][p] = km ? smem_desc(xre, 16, 256 * KB, kmswz) : smem_desc(xre, 2 * NP * 2048 * KB, 1024, kSwz128);
+                    ad[1][p] = km ? smem_desc(xim, 16, 256 * KB, kmswz) : smem_desc(xim, 2 * NP * 2048 * KB, 1024, kSwz128);
+                }
+            };
+            data_descs(KMAJOR || CHAIN, adesc);
+            if (CHAIN) data_descs(false, adesc_mn);
 #pragma unroll
             for (int p = 0; p < NP; ++p) {
-                // K-major: plane tiles of KB x 4 KB (rows of 32 KB bytes, 8-row swizzle atoms of 256 KB
-                // bytes); MN-major: plane tiles of KB x 2 KB (16 KB k-rows of 128 bytes) per atom, atoms
-                // 2 NP KB x 2 KB apart
-                const uint32_t pb = KMAJOR ? uint32_t(KB * kDataTileBytes) : uint32_t(KB * 2048);
-                const uint32_t xre = st0 + uint32_t(p) * pb, xim = st0 + uint32_t(NP + p) * pb;
-                constexpr uint32_t kmswz = KB == 2 ? kSwz64 : kSwz32;
-                adesc[0][p] = KMAJOR ? smem_desc(xre, 16, 256 * KB, kmswz) : smem_desc(xre, 2 * NP * 2048 * KB, 1024, kSwz128);
-                adesc[1][p] = KMAJOR ? smem_desc(xim, 16, 256 * KB, kmswz) : smem_desc(xim, 2 * NP * 2048 * KB, 1024, kSwz128);
                 const uint32_t eb = est0 + uint32_t(p * e_bytes);
                 bdesc[0][p] = smem_desc(eb + uint32_t(half * 32), 16, 256, kSwz32);  // [C; S]
                 bdesc[1][p] = smem_desc(eb, 16, 256, kSwz32);                        // [-S; C]
@@ -1620,10 +1673,19 @@ __global__ void __launch_bounds__(pair_threads(CH, EPI, BATCH), 1)
             const uint64_t stage_step = uint64_t(uint32_t(a.stage_bytes) >> 4);
             int s = 0;
             uint32_t ph = 0, lt = 0;  // ring position, advanced with the producer's
+            int rec_at = 0;           // BATCH: the record of the previous item
             for (int64_t P = cid; P < items && !*abort_flag; P += nclusters, ++lt) {
-                const TcPairProblem *pr = BATCH ? &pair_problem(many, nprob, P) : nullptr;
+                const TcPairProblem *pr = BATCH ? &pair_problem_next(many, nprob, P, rec_at) : nullptr;
                 const TcArgs &A = BATCH ? pr->a : a;
                 const int h = int((BATCH ? P - pr->pairs_begin : P) % A.ni);
+                const bool km = CHAIN ? pr->km != 0 : KMAJOR;
+                const uint32_t id = CHAIN && !km ? idesc_mn : idesc;
+                // the item's data descriptors (CHAIN: chosen once per item, outside the MMA loop)
+                uint64_t ad[2][NP];
+#pragma unroll
+                for (int c = 0; c < 2; ++c)
+#pragma unroll
+                    for (int p = 0; p < NP; ++p) ad[c][p] = CHAIN && !km ? adesc_mn[c][p] : adesc[c][p];
                 const int b = int(lt % uint32_t(nsets));
                 const uint32_t use = lt / uint32_t(nsets);
                 if (use > 0 && !mbar_wait<true>(&tmem_empty[b], (use - 1) & 1u, a.err, MM_ERR_TIMEOUT, a.wait_limit)) {
@@ -1644,14 +1706,14 @@ __global__ void __launch_bounds__(pair_threads(CH, EPI, BATCH), 1)
                     for (int j = 0; j < nk; ++j) {
                         // k-block kb + j: its 32 bytes of every data row (K-major) or its 16 k-rows of
                         // 128 bytes (MN-major), its matrix blocks
-                        const uint64_t ao = so + uint64_t(j * (KMAJOR ? 2 : 128)), bo = so + uint64_t(j * (NP * e_bytes >> 4));
+                        const uint64_t ao = so + uint64_t(j * (km ? 2 : 128)), bo = so + uint64_t(j * (NP * e_bytes >> 4));
                         const uint32_t first = kb + j == kb_lo ? 0u : 1u;  // each accumulator starts at its first product
 #pragma unroll
                         for (int t = 0; t < num_terms(NP); ++t) {
                             const int pa = term_a(t), pb = term_b(t);
                             const uint32_t dcol = (NP > 1 && (pa != 0 || pb != 0)) ? d1 : d0;
-                            umma_f16_pair(dcol, adesc[0][pb] + ao, bdesc[0][pa] + bo, idesc, t <= 1 ? first : 1u);
-                            umma_f16_pair(dcol, adesc[1][pb] + ao, bdesc[1][pa] + bo, idesc, 1u);
+                            umma_f16_pair(dcol, ad[0][pb] + ao, bdesc[0][pa] + bo, id, t <= 1 ? first : 1u);
+                            umma_f16_pair(dcol, ad[1][pb] + ao, bdesc[1][pa] + bo, id, 1u);
                         }
                     }
                     umma_commit_pair_mc(&empty[s], 0x3);
@@ -1674,7 +1736,7 @@ __global__ void __launch_bounds__(pair_threads(CH, EPI, BATCH), 1)
         // ---------------- epilogue warps (both CTAs) ----------------
         const int ew = warp - 2;
         const int quarter = warp % 4;
-        constexpr int kGroups = pair_epi_warps(CH, EPI, BATCH) / 4;  // warps per lane quarter
+        constexpr int kGroups = pair_epi_warps(CH, EPI, BCFG) / 4;  // warps per lane quarter
         constexpr int kPerWarp = 4 * CH / kGroups;       // chunks of 16 output rows per warp
         const int grp = ew / 4;  // the warp's chunks: grp, grp + kGroups, ..
         const int nchunks = a.it / 16;
@@ -1697,15 +1759,49 @@ __global__ void __launch_bounds__(pair_threads(CH, EPI, BATCH), 1)
             es_out = grid_exponent(__uint_as_float(*A.sc.max_prev));
             inv_out = ldexpf(1.0f, -es_out);
             lim = ldexpf(16384.0f, es_out);
-            if (first_item && ew == 0 && lane == 0) *A.sc.s_out = ldexpf(1.0f, es_out);
+            if (first_item && ew == 0 && lane == 0) {
+                *A.sc.s_out = ldexpf(1.0f, es_out);
+                // a chain clears the word the same direction's product of the next sweep accumulates
+                // into (in a single launch, the launch's prologue does)
+                if (CHAIN && A.sc.zero_next) *A.sc.zero_next = 0u;
+            }
+        };
+        // CHAIN: every product below `signalled` has been signalled complete by this warp.  The
+        // warp signals a product once its own stores of that product have completed and its
+        // maximum has been merged, and before it waits for anything of a later product.
+        int signalled = 0;
+        auto signal_upto = [&](int upto) {
+            if (!CHAIN || signalled >= upto) return;
+            if (FX && cur) {
+                const unsigned m = __reduce_max_sync(0xffffffffu, __float_as_uint(local_max));
+                if (lane == 0 && m) atomicMax(cur->sc.max_cur, m);
+                local_max = 0.0f;
+            }
+            if (lane == 0) {
+                bulk_wait0();
+                fence_proxy_async_global();
+                // the CTA's last warp to finish a product (its tally word counts this CTA's warps)
+                // signals it for the whole CTA
+                unsigned *tally = a.tally + int64_t(blockIdx.x) * nprob;
+                for (int q = signalled; q < upto; ++q)
+                    if (atom_add_acqrel_cta_global(tally + q, 1u) + 1u == unsigned(kGroups * 4))
+                        red_release_gpu_add(a.done + q, 1u);
+            }
+            __syncwarp();
+            signalled = upto;
         };
         if (!BATCH) scales_for(a, blockIdx.x == 0);
         uint32_t lt = 0;
+        int rec_at = 0;  // BATCH: the record of the previous item
         for (int64_t P = cid; P < items; P += nclusters, ++lt) {
-            const TcPairProblem *pr = BATCH ? &pair_problem(many, nprob, P) : nullptr;
+            const TcPairProblem *pr = BATCH ? &pair_problem_next(many, nprob, P, rec_at) : nullptr;
             const TcArgs &A = BATCH ? pr->a : a;
             const int64_t Pl = BATCH ? P - pr->pairs_begin : P;
-            if (BATCH) scales_for(A, Pl == 0 && rank == 0);
+            if (CHAIN) {
+                signal_upto(pr->prod);
+                if (lane == 0 && cur != &A) tma_prefetch_desc(&pr->mapY);  // fetched while the item's MMAs run
+            }
+            if (BATCH && !CHAIN) scales_for(A, Pl == 0 && rank == 0);
             const int64_t tile = (Pl / A.ni) * 2 + rank;
             const int h = int(Pl % A.ni);
             const int b = int(lt % uint32_t(nsets));
@@ -1714,6 +1810,16 @@ __global__ void __launch_bounds__(pair_threads(CH, EPI, BATCH), 1)
                 0xffffffffu, !*abort_flag && mbar_wait(&accf[b], (lt / uint32_t(nsets)) & 1u, a.err, MM_ERR_TIMEOUT, a.wait_limit));
             if (!acc_ready) *abort_flag = 1;
             tc_fence_after();
+            if (CHAIN && acc_ready && cur != &A) {
+                // a new product: its data was loaded after the previous product completed, so the
+                // counter has reached its target; one lane acquires it (the previous products' scale
+                // words are read next), and the warp follows
+                bool ok = true;
+                if (lane == 0 && pr->prod > 0)
+                    ok = counter_wait(a.done + (pr->prod - 1), a.done_target, a.err, MM_ERR_TIMEOUT, a.wait_limit);
+                if (!__shfl_sync(0xffffffffu, ok ? 1 : 0, 0)) *abort_flag = 1;
+                scales_for(A, Pl == 0 && rank == 0);
+            }
             // drain in the matrix-fragment order: the warp's chunks of 16 output rows
             // (grp, grp + kGroups ..), each as two 16-lane halves, leading + corrections; tensor
             // memory is released before the values are scaled, split and stored
@@ -1750,18 +1856,28 @@ __global__ void __launch_bounds__(pair_threads(CH, EPI, BATCH), 1)
             if (lane == 0) mbarrier_arrive(&tmem_empty[b]);
             if (!acc_ready) break;
             const float2 phl = EPI == 2 ? point_phase<KMAJOR>(A, tile, quarter, lane) : make_float2(1.0f, 0.0f);
+            if (CHAIN && pr->km) {
 #pragma unroll
-            for (int q = 0; q < kPerWarp; ++q)
-                epi_frag_store<NP, KMAJOR, EPI, FX>(A, BATCH ? &pr->mapY : &mapY, staging + ew * kStagingPerWarp,
-                                                    vr[q], vi[q], tile, h, quarter, lane, grp + kGroups * q, nchunks,
-                                                    s_in, inv_out, lim, local_max, range_ok, phl);
+                for (int q = 0; q < kPerWarp; ++q)
+                    epi_frag_store<NP, true, EPI, FX>(A, &pr->mapY, staging + ew * kStagingPerWarp, vr[q], vi[q],
+                                                      tile, h, quarter, lane, grp + kGroups * q, nchunks, s_in,
+                                                      inv_out, lim, local_max, range_ok, phl);
+            } else {
+#pragma unroll
+                for (int q = 0; q < kPerWarp; ++q)
+                    epi_frag_store<NP, KMAJOR && !CHAIN, EPI, FX>(
+                        A, BATCH ? &pr->mapY : &mapY, staging + ew * kStagingPerWarp, vr[q], vi[q], tile, h,
+                        quarter, lane, grp + kGroups * q, nchunks, s_in, inv_out, lim, local_max, range_ok, phl);
+            }
         }
         if (lane == 0) bulk_wait0();  // this warp's stores are complete
         if (FX) {
             const unsigned m = __reduce_max_sync(0xffffffffu, __float_as_uint(local_max));
             if (lane == 0 && m && cur) atomicMax(cur->sc.max_cur, m);
+            local_max = 0.0f;
             if (!range_ok && a.err) atomicCAS(a.err, 0, MM_ERR_RANGE);
         }
+        signal_upto(nprob);  // CHAIN: the products left (also after an abort: no CTA waits for nothing)
     }
     tc_fence_before();
     __syncthreads();
@@ -2276,7 +2392,7 @@ static cudaError_t dispatch_np(bool km, int epi, const CUtensorMap &mx, const CU
 static const TcMatrix::TcPairTiles *pair_tiles(const TcMatrix &M, TcVariant v)
 {
     if (v == kTcOneSM) return nullptr;
-    const TcMatrix::TcPairTiles &P = M.pair[v == kTcPair128 ? 1 : 0];
+    const TcMatrix::TcPairTiles &P = M.pair[v == kTcPair128 ? 1 : 0];  // kTcChain: row tiles of 64
     return P.pieces ? &P : nullptr;
 }
 
@@ -2591,12 +2707,14 @@ size_t tc_pair_record_align() { return alignof(TcPairProblem); }
 
 cudaError_t tc_pair_record_build(const TcState &si, const TcState &so, int mu, const TcMatrix &M, mm_prec prec,
                                  const void *in_pieces, void *out_pieces, const TcScales &sc, void *rec, bool *kmajor,
-                                 int64_t *items)
+                                 int64_t *items, int chain_pos)
 {
     TcLaunch L;
-    cudaError_t e = tc_setup(si, so, mu, M, prec, in_pieces, out_pieces, TcEpilogue{}, sc, nullptr, kTcPair64, &L, true);
+    cudaError_t e = tc_setup(si, so, mu, M, prec, in_pieces, out_pieces, TcEpilogue{}, sc, nullptr, kTcPair64, &L,
+                             chain_pos < 0);
     if (e != cudaSuccess) return e;
     if (!L.pair || L.a.it > 64) return cudaErrorNotSupported;  // the batched pair kernel stores with TMA (CH = 1)
+    if (chain_pos >= 0 && !L.fx) return cudaErrorNotSupported;  // chains: the fixed-point pieces only
     TcPairProblem r;
     std::memset(&r, 0, sizeof r);
     r.mapX = L.mx;
@@ -2604,6 +2722,8 @@ cudaError_t tc_pair_record_build(const TcState &si, const TcState &so, int mu, c
     r.mapY = L.my;
     r.a = L.a;
     r.pairs_begin = 0;
+    r.km = L.km ? 1 : 0;
+    r.prod = chain_pos < 0 ? 0 : chain_pos;
     std::memcpy(rec, &r, sizeof r);
     *kmajor = L.km;
     *items = L.a.pairs;
@@ -2625,6 +2745,59 @@ bool tc_pair_batch_compatible(const void *host_recs, int nprob)
 
 // The records must agree on what the kernel's launch arguments fix: the row
 // tile size (stage layout) and the input layout.
+// One persistent launch over a chain of products (records built with chain positions 0, 1, ..,
+// in that order, all with row tiles of the same size): product k's loads wait until product k - 1
+// has been stored.  `done` holds nprod counters and `tally` num_sms() x nprod words, both zeroed
+// by the caller before the launch.
+int tc_chain_ctas() { return num_sms(); }
+
+cudaError_t tc_pair_chain_launch(const void *host_recs, const void *dev_recs, int nprod, unsigned *done,
+                                 unsigned *tally, int *d_err, cudaStream_t s)
+{
+    const auto *h = reinterpret_cast<const TcPairProblem *>(host_recs);
+    if (nprod < 1 || !done || !tally) return cudaErrorInvalidValue;
+    TcArgs a = h[0].a;
+    int64_t total = 0;
+    for (int q = 0; q < nprod; ++q) {
+        if (h[q].a.it != a.it || h[q].a.stage_bytes != a.stage_bytes || h[q].pairs_begin != total || h[q].prod != q)
+            return cudaErrorInvalidValue;
+        total += h[q].a.pairs;
+    }
+    a.err = d_err;
+    wait_hooks(&a.wait_limit, &a.withhold);
+    a.done = done;
+    auto kern = tc_pair_kernel<3, false, 0, true, 1, true, true>;
+    const int smem = pair_stages(1, 0, false) * a.stage_bytes + pair_staging_bytes(1, 0, false) + 1024 + 256;
+    cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
+    if (e != cudaSuccess) return e;
+    cudaLaunchConfig_t cfg = {};
+    cfg.gridDim = dim3(unsigned(2 * (total < num_sms() / 2 ? total : num_sms() / 2)));
+    cfg.blockDim = dim3(pair_threads(1, 0, false));
+    cfg.dynamicSmemBytes = size_t(smem);
+    cfg.stream = s;
+    cudaLaunchAttribute attr[2];
+    attr[0].id = cudaLaunchAttributeClusterDimension;
+    attr[0].val.clusterDim.x = 2;
+    attr[0].val.clusterDim.y = 1;
+    attr[0].val.clusterDim.z = 1;
+    attr[1].id = cudaLaunchAttributeProgrammaticStreamSerialization;
+    attr[1].val.programmaticStreamSerializationAllowed = 1;
+    cfg.attrs = attr;
+    cfg.numAttrs = 2;
+    // every cluster must be resident at once: a product's items wait for the whole previous product
+    int active = 0;
+    e = cudaOccupancyMaxActiveClusters(&active, kern, &cfg);
+    if (e != cudaSuccess || active < 1) return e != cudaSuccess ? e : cudaErrorInvalidConfiguration;
+    if (2 * active < int(cfg.gridDim.x)) cfg.gridDim = dim3(unsigned(2 * active));
+    a.done_target = cfg.gridDim.x;  // one signal per CTA and product
+    a.tally = tally;
+    e = cudaLaunchKernelEx(&cfg, kern, h[0].mapX, h[0].mapE, h[0].mapY, a,
+                           reinterpret_cast<const TcPairProblem *>(dev_recs), nprod, total);
+    count_launch();
+    if (e != cudaSuccess) return e;
+    return cudaGetLastError();
+}
+
 cudaError_t tc_pair_batch_launch(const void *host_recs, const void *dev_recs, int nprob, bool kmajor, mm_prec prec,
                                  int *d_err, cudaStream_t s)
 {

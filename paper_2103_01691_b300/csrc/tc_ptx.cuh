@@ -80,6 +80,48 @@ __device__ __forceinline__ bool mbar_wait(uint64_t *bar, uint32_t parity, int *e
     }
 }
 
+// ---- counters between the CTAs of a grid (chained launches) ----------------------
+__device__ __forceinline__ unsigned ld_acquire_gpu(const unsigned *p)
+{
+    unsigned v;
+    asm volatile("ld.acquire.gpu.global.u32 %0, [%1];" : "=r"(v) : "l"(p) : "memory");
+    return v;
+}
+__device__ __forceinline__ void red_release_gpu_add(unsigned *p, unsigned v)
+{
+    asm volatile("red.release.gpu.global.add.u32 [%0], %1;" ::"l"(p), "r"(v) : "memory");
+}
+// Global-memory atomic add, acquire and release at CTA scope (a word only one CTA's threads use);
+// returns the old value.
+__device__ __forceinline__ unsigned atom_add_acqrel_cta_global(unsigned *p, unsigned v)
+{
+    unsigned old;
+    asm volatile("atom.acq_rel.cta.global.add.u32 %0, [%1], %2;" : "=r"(old) : "l"(p), "r"(v) : "memory");
+    return old;
+}
+// Orders this thread's global-memory accesses through the generic proxy with those through the
+// async proxy (TMA), both ways: a TMA store's data is published by a later generic release, and
+// a generic acquire precedes a later TMA load.
+__device__ __forceinline__ void fence_proxy_async_global()
+{
+    asm volatile("fence.proxy.async.global;" ::: "memory");
+}
+// Bounded wait until *p >= target (acquire); on giving up records `code` in *err, returns false.
+__device__ __forceinline__ bool counter_wait(const unsigned *p, unsigned target, int *err, int code,
+                                             long long limit_cycles)
+{
+    if (ld_acquire_gpu(p) >= target) return true;
+    const long long t0 = clock64();
+    while (true) {
+        __nanosleep(64);
+        if (ld_acquire_gpu(p) >= target) return true;
+        if (clock64() - t0 > limit_cycles) {
+            if (err) atomicCAS(err, 0, code);
+            return false;
+        }
+    }
+}
+
 // ---- TMA (tiled tensor loads into shared memory) ------------------------------
 __device__ __forceinline__ void tma_prefetch_desc(const CUtensorMap *map)
 {

@@ -301,7 +301,9 @@ def mumode_product_noalloc(u, mu: int, L, out=None, stream=None):
     return out
 
 
-VARIANTS = ("pair64", "pair128", "one_sm")  # tensor-core kernels, mm_plan_set_config codes 0, 1, 2
+# tensor-core kernels, mm_plan_set_config codes 0..3; "chain" runs all products of a Tucker step
+# call in one persistent launch of the pair64 kernel (F16X6), elsewhere it launches like pair64
+VARIANTS = ("pair64", "pair128", "one_sm", "chain")
 
 
 class _Tunable:
