@@ -97,10 +97,18 @@ typedef enum {
  *                    n_mu (and m) is at most 512, else MM_PREC_FP32_SIMT;
  *                    MM_R32 -> MM_PREC_FP32_SIMT; MM_R64, MM_C128 ->
  *                    MM_PREC_FP64_DMMA.
- * Not provided: split TF32 modes.  The tcgen05 FP32 accumulator truncates,
- * so floating TF32 pieces carry the same bias as MM_PREC_BF16X6, and a
- * fixed-point TF32 split equals MM_PREC_F16X6 with twice the bytes at half
- * the tensor rate. */
+ * MM_PREC_TF32X3     "3xTF32": tcgen05 tensor cores (kind::tf32), state
+ *                    MM_C64.  Matrix and state are split into two TF32
+ *                    pieces each (x0 = TF32 of x, x1 = TF32 of x - x0, both
+ *                    rounded to nearest even; about 22 bits together), and
+ *                    the three products e0 x0, e0 x1, e1 x0 are summed in
+ *                    FP32 in tensor memory, the leading one in an
+ *                    accumulator of its own.  The tensor cores truncate
+ *                    when they add to an FP32 accumulator, so the floating
+ *                    pieces carry a bias, as in MM_PREC_BF16X6; the
+ *                    precision sweep reports its error.  Tucker plans and
+ *                    mumode_product only (the one-SM kernel); other calls
+ *                    return MM_ERR_UNSUPPORTED. */
 typedef enum {
     MM_PREC_FP64_SIMT = 0,
     MM_PREC_FP32_SIMT = 1,
@@ -109,7 +117,8 @@ typedef enum {
     MM_PREC_BF16 = 4,
     MM_PREC_F16X6 = 5,
     MM_PREC_FP64_DMMA = 6,
-    MM_PREC_AUTO = 7
+    MM_PREC_AUTO = 7,
+    MM_PREC_TF32X3 = 8
 } mm_prec;
 
 /* ---------------------------------------------------------------------

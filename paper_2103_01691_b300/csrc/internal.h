@@ -72,6 +72,7 @@ struct TcMatrix {
     } pair[2];
     int npieces = 0;
     bool fixed = false;             // MM_PREC_F16X6 pieces
+    bool tf32 = false;              // MM_PREC_TF32X3: 4-byte pieces ([..][8 elements] rows), k-blocks of 8
     float *rho = nullptr;           // fixed: power-of-two scale of each row (ni * it floats)
     double row_norm = 0.0;          // max_i sum_j |E_ij|, bounds the growth of one product
     int kb_lo[4] = {}, kb_hi[4] = {};  // per row tile (at most 4 of 128): k-blocks with a nonzero piece
@@ -98,8 +99,12 @@ TcVariant tc_default_variant();
 int tc_pieces(mm_prec p);
 bool tc_prec(mm_prec p);
 bool tc_fixed(mm_prec p);
-// Build the pieces of an m x n complex matrix (interleaved FP64, row-major).
-mm_status tc_matrix_create(const double *E, int64_t m, int64_t n, int npieces, bool fixed, TcMatrix *out);
+bool tc_tf32(mm_prec p);       // MM_PREC_TF32X3: 4-byte pieces, k-blocks of 8, the one-SM kernel only
+int tc_piece_bytes(mm_prec p);  // bytes of one piece element (2, or 4 for TF32)
+// Build the pieces of an m x n complex matrix (interleaved FP64, row-major); tf32: two TF32
+// pieces (npieces 2, not fixed), one-SM layout only.
+mm_status tc_matrix_create(const double *E, int64_t m, int64_t n, int npieces, bool fixed, TcMatrix *out,
+                           bool tf32 = false);
 void tc_matrix_destroy(TcMatrix *M);
 // Rewrite the pieces (all layouts) and row scales of M from a device
 // matrix E (n_out x n_in complex FP64, row-major), in stream order.  The
@@ -162,13 +167,16 @@ void pipe_axial(int n, double zmax, double alpha, const double *s, double *A);
 // Host half of tc_matrix_create: geometry (pieces/rho left null) and the
 // host images of the pieces and row scales.
 mm_status tc_matrix_host(const double *E, int64_t m, int64_t n, int npieces, bool fixed, TcMatrix *geom,
-                         std::vector<uint16_t> &pieces, std::vector<float> &rho);
+                         std::vector<uint16_t> &pieces, std::vector<float> &rho, bool tf32 = false);
 // Split an interleaved complex64 tensor into padded piece planes.  For the
 // fixed-point mode the scale comes from the tensor's maximum: `work` (one
 // unsigned, device) receives it, `scale_out` the chosen scale, and
 // bound_words[q] = max * bounds[q] (float bits) for the first sweep.
 cudaError_t tc_split(const TcState &st, int npieces, bool fixed, const void *u_c64, void *pieces, unsigned *work,
                      float *scale_out, unsigned *bound_words, const double *bounds, int nbounds, cudaStream_t s);
+// The TF32 forms: two 4-byte pieces per plane element (x0 = TF32 of x, x1 = TF32 of x - x0).
+cudaError_t tc_split_tf32(const TcState &st, const void *u_c64, void *pieces, cudaStream_t s);
+cudaError_t tc_merge_tf32(const TcState &st, const void *pieces, void *u_c64, cudaStream_t s);
 // Sum the piece planes back into an interleaved complex64 tensor
 // (fixed-point mode: times *scale).
 cudaError_t tc_merge(const TcState &st, int npieces, bool fixed, const void *pieces, const float *scale, void *u_c64,

@@ -44,6 +44,7 @@ struct mm_plan {
     int order[mm::kMaxDims] = {};
     bool tc = false;
     bool fixed = false;  // MM_PREC_F16X6
+    bool tf32 = false;   // MM_PREC_TF32X3 (4-byte pieces, one-SM kernel, Tucker plans only)
     int npieces = 0;
     mm::TcVariant variant = mm::kTcPair64;  // tensor-core kernel (mm_plan_autotune, mm_plan_set_config)
     // kTcChain: the records of a chained call (one launch for all products of nsteps steps) and its
@@ -186,6 +187,7 @@ mm_status check_combo(mm_dtype dt, mm_prec pr, bool matrix_complex)
     case MM_PREC_BF16X3:
     case MM_PREC_BF16:
     case MM_PREC_F16X6:
+    case MM_PREC_TF32X3:
         if (dt == MM_C64) return MM_OK;
         break;
     default: return fail(MM_ERR_INVALID_ARG, "unknown precision %d", int(pr));
@@ -415,8 +417,9 @@ mm_status tc_begin_bounds(mm_plan *p, const double *bounds, const void *u, cudaS
         if (e0 != cudaSuccess) return cuda_fail(e0, "scale word reset");
     }
     // sweep 0 reads its maximum words from set 2: the split writes the bounds there
-    cudaError_t e = mm::tc_split(p->st, p->npieces, p->fixed, u, p->work[0], p->d_work, p->d_scale,
-                                 p->d_max ? p->d_max + 2 * p->d : nullptr, bounds, p->d, s);
+    cudaError_t e = p->tf32 ? mm::tc_split_tf32(p->st, u, p->work[0], s)
+                            : mm::tc_split(p->st, p->npieces, p->fixed, u, p->work[0], p->d_work, p->d_scale,
+                                           p->d_max ? p->d_max + 2 * p->d : nullptr, bounds, p->d, s);
     if (e != cudaSuccess) return cuda_fail(e, "split");
     return MM_OK;
 }
@@ -425,7 +428,8 @@ mm_status tc_end(mm_plan *p, int cur, void *u, cudaStream_t s)
 {
     // the state's scale after p->sweep sweeps (see tc_sweep)
     float *scale = p->d_scale ? p->d_scale + (p->sweep & 1) * p->d : nullptr;
-    cudaError_t e = mm::tc_merge(p->st, p->npieces, p->fixed, p->work[cur], scale, u, s);
+    cudaError_t e = p->tf32 ? mm::tc_merge_tf32(p->st, p->work[cur], u, s)
+                            : mm::tc_merge(p->st, p->npieces, p->fixed, p->work[cur], scale, u, s);
     if (e != cudaSuccess) return cuda_fail(e, "merge");
     return MM_OK;
 }
@@ -462,7 +466,7 @@ mm_status alloc_workspace(mm_plan *p)
     cudaError_t e;
     if (p->tc) {
         p->st = make_state(p->d, p->n);
-        p->work_bytes = size_t(p->st.plane) * 2 * p->npieces * 2;
+        p->work_bytes = size_t(p->st.plane) * 2 * p->npieces * size_t(mm::tc_piece_bytes(p->prec));
         for (int b = 0; b < 2; ++b) {
             e = cudaMalloc(&p->work[b], p->work_bytes);
             if (e != cudaSuccess) return fail(MM_ERR_OOM, "workspace cudaMalloc(%zu) failed", p->work_bytes);
@@ -488,7 +492,7 @@ mm_status upload_matrix(mm_plan *p, const double *E, int64_t m, int64_t n, bool 
 {
     if (p->tc) {
         std::vector<double> c = as_complex(E, m * n, Ec);
-        return mm::tc_matrix_create(c.data(), m, n, p->npieces, p->fixed, tcm);
+        return mm::tc_matrix_create(c.data(), m, n, p->npieces, p->fixed, tcm, p->tf32);
     }
     return upload_simt(E, m, n, Ec, p->dtype, simt);
 }
@@ -532,8 +536,9 @@ mm_status plan_common(mm_ctx *ctx, int d, const int64_t *n, mm_dtype dtype, mm_p
     p->prec = prec;
     p->tc = tc;
     p->fixed = mm::tc_fixed(prec);
+    p->tf32 = mm::tc_tf32(prec);
     p->npieces = mm::tc_pieces(prec);
-    p->variant = mm::tc_default_variant();
+    p->variant = p->tf32 ? mm::kTcOneSM : mm::tc_default_variant();
     *made = p;
     return MM_OK;
 }
@@ -704,7 +709,8 @@ mm_status autotune_with(mm_plan *p, const void *u_dev, int64_t nsteps, void *str
     if (cudaMalloc(&scratch, bytes) != cudaSuccess) return fail(MM_ERR_OOM, "autotune scratch of %zu bytes", bytes);
     // candidates: kernel variants (tensor-core plans) x mode orders (Tucker plans, all orders for d <= 4)
     std::vector<int> variants;
-    if (p->tc) variants = {mm::kTcPair64, mm::kTcPair128, mm::kTcOneSM};
+    if (p->tc && p->tf32) variants = {mm::kTcOneSM};  // TF32 pieces run on the one-SM kernel only
+    else if (p->tc) variants = {mm::kTcPair64, mm::kTcPair128, mm::kTcOneSM};
     else variants = {int(p->variant)};
     if (p->tc && p->fixed && orders_too && !p->hermite) variants.push_back(mm::kTcChain);  // Tucker steps only
     std::vector<std::vector<int>> orders;
@@ -1014,13 +1020,15 @@ mm_status mumode_product(mm_ctx *ctx, int d, const int64_t *n, int mu, const dou
         return fail(MM_ERR_UNSUPPORTED, "tensor-core precisions need an sm_103 device");
     if (nmu > 512 || m > 512) return fail(MM_ERR_SHAPE, "tensor-core path supports n_mu, m <= 512");
     const int NP = mm::tc_pieces(prec);
-    const bool fixed = mm::tc_fixed(prec);
+    const bool fixed = mm::tc_fixed(prec), tf32 = mm::tc_tf32(prec);
     std::vector<double> Lc = as_complex(L, m * nmu, L_is_complex != 0);
     mm::TcMatrix M;
-    if ((st = mm::tc_matrix_create(Lc.data(), m, nmu, NP, fixed, &M))) return st;
+    if ((st = mm::tc_matrix_create(Lc.data(), m, nmu, NP, fixed, &M, tf32))) return st;
     mm::TcState si = make_state(d, n), so = make_state(d, nout);
     void *bi = nullptr, *bo = nullptr, *words = nullptr;
-    const size_t bytes_i = size_t(si.plane) * 2 * NP * 2, bytes_o = size_t(so.plane) * 2 * NP * 2;
+    const size_t eb_p = size_t(mm::tc_piece_bytes(prec));
+    size_t bytes_i = size_t(si.plane) * 2 * NP * eb_p, bytes_o = size_t(so.plane) * 2 * NP * eb_p;
+    if (tf32 && mu > 1) bytes_i = bytes_o = std::max(bytes_i, bytes_o);  // both hold either state (the swaps)
     cudaError_t e = cudaMalloc(&bi, bytes_i);
     if (e == cudaSuccess) e = cudaMalloc(&bo, bytes_o);
     if (e == cudaSuccess) e = cudaMalloc(&words, 64);
@@ -1042,10 +1050,12 @@ mm_status mumode_product(mm_ctx *ctx, int d, const int64_t *n, int mu, const dou
     }
     const double bound = M.row_norm;
     e = cudaMemsetAsync(words, 0, 64, s);
-    if (e == cudaSuccess) e = mm::tc_split(si, NP, fixed, u_dev, bi, uw + 4, scales, uw + 2, &bound, 1, s);
+    if (e == cudaSuccess)
+        e = tf32 ? mm::tc_split_tf32(si, u_dev, bi, s)
+                 : mm::tc_split(si, NP, fixed, u_dev, bi, uw + 4, scales, uw + 2, &bound, 1, s);
     if (e == cudaSuccess)
         e = mm::tc_mode_product(si, so, mu, M, prec, bi, bo, mm::TcEpilogue{}, sc, ctx->d_err, s, mm::tc_default_variant());
-    if (e == cudaSuccess) e = mm::tc_merge(so, NP, fixed, bo, scales + 1, s_dev, s);
+    if (e == cudaSuccess) e = tf32 ? mm::tc_merge_tf32(so, bo, s_dev, s) : mm::tc_merge(so, NP, fixed, bo, scales + 1, s_dev, s);
     cudaError_t e2 = cudaStreamSynchronize(s);
     cudaFree(bi);
     cudaFree(bo);
@@ -1191,6 +1201,10 @@ mm_status hermite_plan_create(mm_ctx *ctx, int d, const int64_t *n, mm_dtype dty
     if (!is_complex(dtype)) {
         delete p;
         return fail(MM_ERR_DTYPE, "Hermite plans need complex data");
+    }
+    if (p->tf32) {
+        delete p;
+        return fail(MM_ERR_UNSUPPORTED, "MM_PREC_TF32X3 serves Tucker plans and mumode_product only");
     }
     if ((st = hermite_setup(p))) {
         mm_plan_destroy(p);
@@ -1618,6 +1632,7 @@ extern "C" mm_status mumode_batch_create(mm_ctx *ctx, mm_plan *const *plans, int
     for (int k = 0; k < nprob; ++k) {
         mm_plan *p = plans[k];
         if (!p || p->hermite || !p->tc) return fail(MM_ERR_INVALID_ARG, "plan %d is not a tensor-core Tucker plan", k);
+        if (p->tf32) return fail(MM_ERR_UNSUPPORTED, "plan %d: batches do not serve MM_PREC_TF32X3", k);
         if (p->ctx != ctx) return fail(MM_ERR_INVALID_ARG, "plan %d belongs to another context", k);
         if (p->prec != p0->prec || p->d != p0->d) return fail(MM_ERR_INVALID_ARG, "plan %d differs in precision or d", k);
         for (int v = 0; v < p->d; ++v)
@@ -1875,6 +1890,7 @@ extern "C" mm_status mm_expm_device(mm_ctx *ctx, int n, const double *A_dev, con
 static mm_status set_matrix_device(mm_plan *p, int mu, const double2 *E, double row_norm_bound, cudaStream_t s)
 {
     const int v = mu - 1;
+    if (p->tf32) return fail(MM_ERR_UNSUPPORTED, "device matrix updates do not serve MM_PREC_TF32X3 plans");
     if (p->tc) {
         if (!p->full_bands[v]) {
             drop_graphs(p);  // captured launches carry the old bands
@@ -1931,6 +1947,10 @@ extern "C" mm_status hkmp_plan_create(mm_ctx *ctx, int d, const int64_t *n, cons
     if (!(p->tc || (dtype == MM_C128 && (p->prec == MM_PREC_FP64_SIMT || p->prec == MM_PREC_FP64_DMMA)))) {
         delete p;
         return fail(MM_ERR_DTYPE, "HKMP plans need a tensor-core precision (MM_C64) or an FP64 one (MM_C128)");
+    }
+    if (p->tf32) {
+        delete p;
+        return fail(MM_ERR_UNSUPPORTED, "MM_PREC_TF32X3 serves Tucker plans and mumode_product only");
     }
     if ((st = hermite_setup(p))) {
         mm_plan_destroy(p);

@@ -77,11 +77,14 @@ int tc_pieces(mm_prec p)
     case MM_PREC_BF16X3: return 2;
     case MM_PREC_BF16: return 1;
     case MM_PREC_F16X6: return 3;
+    case MM_PREC_TF32X3: return 2;
     default: return 0;
     }
 }
 bool tc_prec(mm_prec p) { return tc_pieces(p) > 0; }
 bool tc_fixed(mm_prec p) { return p == MM_PREC_F16X6; }
+bool tc_tf32(mm_prec p) { return p == MM_PREC_TF32X3; }
+int tc_piece_bytes(mm_prec p) { return tc_tf32(p) ? 4 : 2; }
 
 static inline int64_t round16(int64_t v) { return (v + 15) / 16 * 16; }
 
@@ -135,6 +138,19 @@ __host__ __device__ static uint16_t f16_bits(double exact)
     return uint16_t(sign | uint16_t((e + 15) << 10) | mant);
 }
 
+// Round a double to the nearest TF32 value (10 explicit mantissa bits, ties to even; below the
+// FP32 normal range: 0), returned as the FP32 bits.
+static uint32_t tf32_bits_of(double v)
+{
+    if (v == 0.0 || !std::isfinite(v)) return 0u;
+    const int e = std::ilogb(v);
+    if (e < -126) return 0u;
+    const float f = float(std::ldexp(std::rint(std::ldexp(v, 10 - e)), e - 10));  // 11 bits: exact in FP32
+    uint32_t u;
+    std::memcpy(&u, &f, 4);
+    return u;
+}
+
 // Fixed-point row scale: the power of two 2^ceil(log2(sum_abs / 4096)) (1 for
 // an empty row), by frexp so that host and device agree exactly.
 __host__ __device__ static double row_scale(double sum_abs)
@@ -174,7 +190,7 @@ __host__ __device__ static void entry_pieces(double c, double s, double r, int n
 }
 
 mm_status tc_matrix_host(const double *E, int64_t m, int64_t n, int npieces, bool fixed, TcMatrix *geom,
-                         std::vector<uint16_t> &h, std::vector<float> &rho)
+                         std::vector<uint16_t> &h, std::vector<float> &rho, bool tf32)
 {
     if (m < 1 || n < 1 || m > 512 || n > 512) return fail(MM_ERR_SHAPE, "tensor-core matrices need sizes in 1..512");
     TcMatrix M;
@@ -186,6 +202,60 @@ mm_status tc_matrix_host(const double *E, int64_t m, int64_t n, int npieces, boo
     M.it = int(round16((m_pad + M.ni - 1) / M.ni));
     M.npieces = npieces;
     M.fixed = fixed;
+    M.tf32 = tf32;
+    if (tf32) {
+        // two TF32 pieces, one-SM layout [piece][row tile][k-block of 8][C, S][it rows][8 x 4 bytes]
+        // (as 16-bit halves, low half first); the same bytes per row as the 16-bit pieces
+        if (npieces != 2 || fixed) return fail(MM_ERR_INVALID_ARG, "TF32 matrices take two floating pieces");
+        const int64_t kbs = M.k_pad / 8;
+        h.assign(size_t(int64_t(npieces) * M.ni * kbs * kBlocks * M.it * 16), 0);
+        rho.assign(size_t(M.ni) * M.it, 1.0f);
+        for (int64_t i = 0; i < m; ++i) {
+            double sum_mod = 0.0;
+            const int64_t tile = i / M.it, il = i % M.it;
+            for (int64_t j = 0; j < n; ++j) {
+                const double c = E[2 * (i * n + j)], sv = E[2 * (i * n + j) + 1];
+                sum_mod += std::hypot(c, sv);
+                const double val[2] = {c, sv};
+                for (int w = 0; w < kBlocks; ++w) {
+                    const uint32_t b0 = tf32_bits_of(val[w]);
+                    float f0;
+                    std::memcpy(&f0, &b0, 4);
+                    const uint32_t b1 = tf32_bits_of(val[w] - double(f0));
+                    const uint32_t bits[2] = {b0, b1};
+                    const int64_t kb = j / 8, jj = j % 8;
+                    for (int p = 0; p < npieces; ++p) {
+                        const int64_t row = (((int64_t(p) * M.ni + tile) * kbs + kb) * kBlocks + w) * M.it + il;
+                        h[size_t(row * 16 + 2 * jj)] = uint16_t(bits[p] & 0xffffu);
+                        h[size_t(row * 16 + 2 * jj + 1)] = uint16_t(bits[p] >> 16);
+                    }
+                }
+            }
+            M.row_norm = std::max(M.row_norm, sum_mod);
+        }
+        for (int tile = 0; tile < M.ni; ++tile) {
+            int lo = int(kbs), hi = 0;
+            for (int p = 0; p < npieces; ++p)
+                for (int64_t kb = 0; kb < kbs; ++kb) {
+                    const int64_t row0 = (((int64_t(p) * M.ni + tile) * kbs + kb) * kBlocks) * M.it;
+                    const uint16_t *blk = h.data() + size_t(row0 * 16);
+                    bool any = false;
+                    for (int64_t q = 0; q < int64_t(kBlocks) * M.it * 16 && !any; ++q) any = blk[q] != 0;
+                    if (any) {
+                        lo = std::min(lo, int(kb));
+                        hi = std::max(hi, int(kb) + 1);
+                    }
+                }
+            if (lo >= hi) {
+                lo = 0;
+                hi = 1;
+            }
+            M.kb_lo[tile] = lo;
+            M.kb_hi[tile] = hi;
+        }
+        *geom = M;
+        return MM_OK;
+    }
     const int64_t rows = int64_t(npieces) * M.ni * kBlocks * M.it;
     h.assign(size_t(rows * M.k_pad), 0);
     rho.assign(size_t(M.ni) * M.it, 1.0f);
@@ -328,12 +398,12 @@ static void tc_pair_layout(const TcMatrix &M, int64_t tmax, TcMatrix::TcPairTile
     }
 }
 
-mm_status tc_matrix_create(const double *E, int64_t m, int64_t n, int npieces, bool fixed, TcMatrix *out)
+mm_status tc_matrix_create(const double *E, int64_t m, int64_t n, int npieces, bool fixed, TcMatrix *out, bool tf32)
 {
     TcMatrix M;
     std::vector<uint16_t> h;
     std::vector<float> rho;
-    mm_status st = tc_matrix_host(E, m, n, npieces, fixed, &M, h, rho);
+    mm_status st = tc_matrix_host(E, m, n, npieces, fixed, &M, h, rho, tf32);
     if (st) return st;
     auto release = [&]() { tc_matrix_destroy(&M); };
     auto upload = [&](void **dst, const void *src, size_t bytes) -> mm_status {
@@ -350,7 +420,7 @@ mm_status tc_matrix_create(const double *E, int64_t m, int64_t n, int npieces, b
     };
     if ((st = upload(&M.pieces, h.data(), h.size() * 2))) return st;
     const int64_t tmax[2] = {64, 128};
-    for (int k = 0; k < 2; ++k) {
+    for (int k = 0; k < 2 && !tf32; ++k) {  // TF32 runs on the one-SM kernel only: no pair tilings
         std::vector<uint16_t> h2;
         tc_pair_layout(M, tmax[k], M.pair[k], h, h2);
         if ((st = upload(&M.pair[k].pieces, h2.data(), h2.size() * 2))) return st;
@@ -684,6 +754,71 @@ __global__ void merge_kernel(Dims dm, int64_t plane, int npieces, const uint16_t
     }
 }
 
+// FP32 -> the nearest TF32 value (10 explicit mantissa bits, ties to even), as FP32 bits.
+__device__ __forceinline__ uint32_t tf32_rne_bits(float x)
+{
+    const uint32_t u = __float_as_uint(x);
+    return (u + 0x0fffu + ((u >> 13) & 1u)) & 0xffffe000u;
+}
+
+// The two TF32 pieces of x: x0 = TF32(x), x1 = TF32(x - x0) (the difference is exact in FP32).
+__device__ __forceinline__ void split_tf32(float x, uint32_t &b0, uint32_t &b1)
+{
+    b0 = tf32_rne_bits(x);
+    b1 = tf32_rne_bits(x - __uint_as_float(b0));
+}
+
+// split_kernel for TF32 pieces: planes [re x0, re x1, im x0, im x1] of 4-byte elements, 8 padded
+// points per thread (two 16-byte stores per plane).
+template <typename I>
+__global__ void split_tf32_kernel(Dims dm, int64_t plane, const float2 *__restrict__ u, uint32_t *__restrict__ pieces)
+{
+    const I np0 = I(dm.np[0]), n0 = I(dm.n[0]), groups = I(plane / 8);
+    for (I g = I(blockIdx.x) * blockDim.x + threadIdx.x; g < groups; g += I(gridDim.x) * blockDim.x) {
+        const I q0 = g * 8, c0 = q0 % np0;
+        bool inside;
+        const I lin = row_offset<I>(dm, q0 / np0, inside) + c0;
+        uint32_t b[4][8];
+#pragma unroll
+        for (int k = 0; k < 8; ++k) {
+            const float2 x = inside && c0 + I(k) < n0 ? u[lin + I(k)] : make_float2(0.f, 0.f);
+            split_tf32(x.x, b[0][k], b[1][k]);
+            split_tf32(x.y, b[2][k], b[3][k]);
+        }
+#pragma unroll
+        for (int c = 0; c < 4; ++c) {
+            uint4 *dst = reinterpret_cast<uint4 *>(pieces + int64_t(c) * plane + q0);
+            dst[0] = make_uint4(b[c][0], b[c][1], b[c][2], b[c][3]);
+            dst[1] = make_uint4(b[c][4], b[c][5], b[c][6], b[c][7]);
+        }
+    }
+}
+
+// The sum of the two TF32 pieces (exact in FP32: they span at most 22 bits) back into complex64.
+template <typename I>
+__global__ void merge_tf32_kernel(Dims dm, int64_t plane, const uint32_t *__restrict__ pieces, float2 *__restrict__ u)
+{
+    const I np0 = I(dm.np[0]), n0 = I(dm.n[0]), groups = I(plane / 8);
+    for (I g = I(blockIdx.x) * blockDim.x + threadIdx.x; g < groups; g += I(gridDim.x) * blockDim.x) {
+        const I q0 = g * 8, c0 = q0 % np0;
+        bool inside;
+        const I lin = row_offset<I>(dm, q0 / np0, inside) + c0;
+        if (!inside || c0 >= n0) continue;
+        float v[4][8];
+#pragma unroll
+        for (int c = 0; c < 4; ++c) {
+            const uint4 *src = reinterpret_cast<const uint4 *>(pieces + int64_t(c) * plane + q0);
+            const uint4 w0 = src[0], w1 = src[1];
+            const uint32_t w[8] = {w0.x, w0.y, w0.z, w0.w, w1.x, w1.y, w1.z, w1.w};
+#pragma unroll
+            for (int k = 0; k < 8; ++k) v[c][k] = __uint_as_float(w[k]);
+        }
+#pragma unroll
+        for (int k = 0; k < 8; ++k)
+            if (c0 + I(k) < n0) u[lin + I(k)] = make_float2(v[1][k] + v[0][k], v[3][k] + v[2][k]);
+    }
+}
+
 static Dims make_dims(const TcState &st)
 {
     Dims dm;
@@ -732,6 +867,68 @@ cudaError_t tc_split(const TcState &st, int npieces, bool fixed, const void *u_c
                 make_dims(st), st.plane, npieces, (const float2 *)u_c64, (uint16_t *)pieces, nullptr, nullptr, nullptr,
                 bd, 0);
     }
+    count_launch();
+    return cudaGetLastError();
+}
+
+cudaError_t tc_split_tf32(const TcState &st, const void *u_c64, void *pieces, cudaStream_t s)
+{
+    if ((reinterpret_cast<uintptr_t>(pieces) & 15) || st.plane % 8) return cudaErrorMisalignedAddress;
+    if (st.plane < (int64_t(1) << 31))
+        split_tf32_kernel<uint32_t><<<grid_for(st.plane / 8), 256, 0, s>>>(make_dims(st), st.plane,
+                                                                          (const float2 *)u_c64, (uint32_t *)pieces);
+    else
+        split_tf32_kernel<int64_t><<<grid_for(st.plane / 8), 256, 0, s>>>(make_dims(st), st.plane,
+                                                                         (const float2 *)u_c64, (uint32_t *)pieces);
+    count_launch();
+    return cudaGetLastError();
+}
+
+cudaError_t tc_merge_tf32(const TcState &st, const void *pieces, void *u_c64, cudaStream_t s)
+{
+    if ((reinterpret_cast<uintptr_t>(pieces) & 15) || st.plane % 8) return cudaErrorMisalignedAddress;
+    if (st.plane < (int64_t(1) << 31))
+        merge_tf32_kernel<uint32_t><<<grid_for(st.plane / 8), 256, 0, s>>>(make_dims(st), st.plane,
+                                                                          (const uint32_t *)pieces, (float2 *)u_c64);
+    else
+        merge_tf32_kernel<int64_t><<<grid_for(st.plane / 8), 256, 0, s>>>(make_dims(st), st.plane,
+                                                                         (const uint32_t *)pieces, (float2 *)u_c64);
+    count_launch();
+    return cudaGetLastError();
+}
+
+// out[p][r][b][a] = in[p][r][a][b] for 4-byte elements: each of the `planes` planes (plane elements
+// apart) holds R matrices of A x B (B fastest); 32 x 32 tiles through shared memory.
+__global__ void swap_last2_kernel(const uint32_t *__restrict__ in, uint32_t *__restrict__ out, int64_t R, int64_t A,
+                                  int64_t B, int planes, int64_t plane)
+{
+    __shared__ uint32_t t[32][33];
+    const int64_t nz = R * planes;
+    for (int64_t z = blockIdx.z; z < nz; z += gridDim.z) {
+        const int64_t p = z / R, r = z % R;
+        const uint32_t *src = in + p * plane + r * A * B;
+        uint32_t *dst = out + p * plane + r * A * B;
+        const int64_t a0 = int64_t(blockIdx.y) * 32, b0 = int64_t(blockIdx.x) * 32;
+        for (int k = threadIdx.y; k < 32; k += blockDim.y) {
+            const int64_t a = a0 + k, b = b0 + threadIdx.x;
+            if (a < A && b < B) t[k][threadIdx.x] = src[a * B + b];
+        }
+        __syncthreads();
+        for (int k = threadIdx.y; k < 32; k += blockDim.y) {
+            const int64_t b = b0 + k, a = a0 + threadIdx.x;
+            if (a < A && b < B) dst[b * A + a] = t[threadIdx.x][k];
+        }
+        __syncthreads();
+    }
+}
+
+static cudaError_t swap_last2(const void *in, void *out, int64_t R, int64_t A, int64_t B, int planes, int64_t plane,
+                              cudaStream_t s)
+{
+    const int64_t nz = R * planes;
+    dim3 grid(unsigned((B + 31) / 32), unsigned((A + 31) / 32), unsigned(nz < 65535 ? nz : 65535));
+    if ((B + 31) / 32 > 0x7fffffff || (A + 31) / 32 > 65535) return cudaErrorInvalidConfiguration;
+    swap_last2_kernel<<<grid, dim3(32, 8), 0, s>>>((const uint32_t *)in, (uint32_t *)out, R, A, B, planes, plane);
     count_launch();
     return cudaGetLastError();
 }
@@ -845,21 +1042,22 @@ constexpr int kChunksPerWarp = 2;  // 16-row chunks each epilogue warp drains (I
 // i0 = h it + 16 (grp + 4 q) .. i0 + 15 (16 real, then 16 imaginary
 // values).  Scales them (fixed point), applies the nonlinear phase (EPI 1),
 // tracks the maximum and the range, splits them into pieces and stores.
-template <int NP, bool KMAJOR, int EPI, bool FX, int CH>
+template <int NP, bool KMAJOR, int EPI, bool FX, int CH, bool TF = false>
 __device__ __forceinline__ void epi_store(const TcArgs &a, float (&v)[CH][32], int64_t tile, int h, int row, int grp,
                                           int nchunks, float s_in, float inv_out, float lim, float &local_max,
                                           bool &range_ok)
 {
-    // this thread's point
+    // this thread's point (MN-major: atoms of 64 points, or 32 with TF32 pieces)
+    constexpr int AW = TF ? 32 : 64;
     bool valid;
     int64_t r, l = 0;
     if (KMAJOR) {
         r = tile * kTileM + row;
         valid = r < a.right;
     } else {
-        const int64_t atom = 2 * tile + row / 64;
+        const int64_t atom = int64_t(kTileM / AW) * tile + row / AW;
         r = atom / a.aps;
-        l = (atom % a.aps) * 64 + row % 64;
+        l = (atom % a.aps) * AW + row % AW;
         valid = r < a.right && l < a.left;
     }
 #pragma unroll
@@ -919,7 +1117,38 @@ __device__ __forceinline__ void epi_store(const TcArgs &a, float (&v)[CH][32], i
                 }
             }
         };
-        if (KMAJOR) {
+        if (TF) {
+            // two TF32 pieces, 4 bytes each: K-major, 16 consecutive outputs of one row as two 32-byte
+            // stores per (plane, piece); MN-major, one 4-byte store per value and piece
+            uint32_t *out32 = reinterpret_cast<uint32_t *>(a.out);
+            if (KMAJOR) {
+                const int64_t base = r * a.mp + i0;
+#pragma unroll
+                for (int c = 0; c < 2; ++c) {
+                    uint32_t w[2][2][8];  // [piece][half][value]
+#pragma unroll
+                    for (int k = 0; k < 16; ++k) split_tf32(v[q][16 * c + k], w[0][k / 8][k % 8], w[1][k / 8][k % 8]);
+#pragma unroll
+                    for (int p = 0; p < 2; ++p) {
+                        st_global_v8(out32 + int64_t(c * 2 + p) * a.plane_out + base, w[p][0]);
+                        st_global_v8(out32 + int64_t(c * 2 + p) * a.plane_out + base + 8, w[p][1]);
+                    }
+                }
+            } else {
+#pragma unroll
+                for (int k = 0; k < 16; ++k) {
+                    uint32_t br[2], bi[2];
+                    split_tf32(v[q][k], br[0], br[1]);
+                    split_tf32(v[q][16 + k], bi[0], bi[1]);
+                    const int64_t off = (r * a.mp + i0 + k) * a.left + l;
+#pragma unroll
+                    for (int p = 0; p < 2; ++p) {
+                        out32[int64_t(p) * a.plane_out + off] = br[p];
+                        out32[int64_t(2 + p) * a.plane_out + off] = bi[p];
+                    }
+                }
+            }
+        } else if (KMAJOR) {
             // 16 consecutive outputs of one row: one 32-byte store per (plane, piece)
             const int64_t base = r * a.mp + i0;
 #pragma unroll
@@ -962,7 +1191,7 @@ __device__ __forceinline__ void epi_store(const TcArgs &a, float (&v)[CH][32], i
 // memory.  The TMA warp runs ahead across item boundaries; the epilogue warps copy the
 // two accumulators into registers, release tensor memory to the MMA warp
 // at once, and then scale, split and store while the next item's MMAs run.
-template <int NP, bool KMAJOR, int EPI, bool FX>
+template <int NP, bool KMAJOR, int EPI, bool FX, bool TF = false>
 __global__ void __launch_bounds__(kThreads, 1)
     tc_mode_kernel(const __grid_constant__ CUtensorMap mapX, const __grid_constant__ CUtensorMap mapE, TcArgs a)
 {
@@ -977,6 +1206,10 @@ __global__ void __launch_bounds__(kThreads, 1)
     uint64_t *mma_fin = reinterpret_cast<uint64_t *>(tmem_slot + 2);  // abort: this CTA's MMAs have completed
 
     const int warp = threadIdx.x / 32, lane = threadIdx.x % 32;
+    // TF: 4-byte pieces, K = 8 per MMA and per k-block (32-byte rows, as the 16-bit pieces' K = 16);
+    // an MN-major data tile of 128 points is four 32-point atoms instead of two of 64
+    constexpr int kKB = TF ? 8 : kBK;
+    constexpr int kAtoms = TF ? 4 : 2, kAtomPoints = 128 / kAtoms, kAtomBytes = kDataTileBytes / kAtoms;
     const int acc_cols = 2 * a.it;
     const int need = NP > 1 ? 2 * acc_cols : acc_cols;
     const uint32_t ncols = need <= 32 ? 32 : (need <= 64 ? 64 : (need <= 128 ? 128 : (need <= 256 ? 256 : 512)));
@@ -1019,15 +1252,16 @@ __global__ void __launch_bounds__(kThreads, 1)
             for (int64_t P = cid; P < a.pairs && !*abort_flag; P += nclusters) {
                 const int64_t tile = (P / a.ni) * 2 + rank;
                 const int h = int(P % a.ni);
-                // TMA coordinates of this item's two 64-point atoms (MN-major), fixed over k
-                int ac_l[2] = {0, 0}, ac_r[2] = {0, 0};
+                // TMA coordinates of this item's atoms (MN-major: 128-byte rows, 64 points of 16-bit pieces
+                // or 32 of TF32), fixed over k
+                int ac_l[kAtoms] = {}, ac_r[kAtoms] = {};
                 if (!KMAJOR) {
-                    for (int q = 0; q < 2; ++q) {
-                        const int64_t atom = 2 * tile + q;
+                    for (int q = 0; q < kAtoms; ++q) {
+                        const int64_t atom = int64_t(kAtoms) * tile + q;
                         int64_t r = atom / a.aps;
                         if (r > a.right) r = a.right;  // past the end: zero fill
                         ac_r[q] = int(r);
-                        ac_l[q] = int((atom % a.aps) * 64);
+                        ac_l[q] = int((atom % a.aps) * kAtomPoints);
                     }
                 }
                 // matrix tiles are stored contiguously per (piece, row tile, k-block): 3 it rows of 16
@@ -1050,10 +1284,11 @@ __global__ void __launch_bounds__(kThreads, 1)
                         for (int p = 0; p < NP; ++p) {
                             uint8_t *dst = st + (c * NP + p) * kDataTileBytes;
                             if (KMAJOR) {
-                                tma_load_3d(&mapX, &full[s], dst, kb * kBK, k_row, c * NP + p);
+                                tma_load_3d(&mapX, &full[s], dst, kb * kKB, k_row, c * NP + p);
                             } else {
-                                tma_load_4d(&mapX, &full[s], dst, ac_l[0], kb * kBK, ac_r[0], c * NP + p);
-                                tma_load_4d(&mapX, &full[s], dst + 2048, ac_l[1], kb * kBK, ac_r[1], c * NP + p);
+                                for (int q = 0; q < kAtoms; ++q)
+                                    tma_load_4d(&mapX, &full[s], dst + q * kAtomBytes, ac_l[q], kb * kKB, ac_r[q],
+                                                c * NP + p);
                             }
                         }
                     // every matrix block, in two boxes of half the rows each
@@ -1070,10 +1305,16 @@ __global__ void __launch_bounds__(kThreads, 1)
     } else if (warp == 1) {
         if (lane == 0) {
             // ---------------- MMA issuer ----------------
-            const uint32_t idesc_full = FX ? idesc_f16_f32(kTileM, 2 * a.it, !KMAJOR, false)
-                                           : idesc_bf16_f32(kTileM, 2 * a.it, !KMAJOR, false);
-            const uint32_t idesc_half = FX ? idesc_f16_f32(kTileM, a.it, !KMAJOR, false)
-                                           : idesc_bf16_f32(kTileM, a.it, !KMAJOR, false);
+            const uint32_t idesc_full = TF   ? idesc_tf32_f32(kTileM, 2 * a.it, !KMAJOR, false)
+                                        : FX ? idesc_f16_f32(kTileM, 2 * a.it, !KMAJOR, false)
+                                             : idesc_bf16_f32(kTileM, 2 * a.it, !KMAJOR, false);
+            const uint32_t idesc_half = TF   ? idesc_tf32_f32(kTileM, a.it, !KMAJOR, false)
+                                        : FX ? idesc_f16_f32(kTileM, a.it, !KMAJOR, false)
+                                             : idesc_bf16_f32(kTileM, a.it, !KMAJOR, false);
+            auto mma = [&](uint32_t d, uint64_t ad, uint64_t bd, uint32_t id, uint32_t acc) {
+                if (TF) umma_tf32(d, ad, bd, id, acc);
+                else umma_f16(d, ad, bd, id, acc);
+            };
             const uint32_t idesc_half_neg = idesc_half | (1u << 13);  // negate A
             uint32_t gk = 0, lt = 0;
             for (int64_t P = cid; P < a.pairs && !*abort_flag; P += nclusters, ++lt) {
@@ -1105,12 +1346,14 @@ __global__ void __launch_bounds__(kThreads, 1)
                         const uint32_t eS = est + (pa * kBlocks + 1) * a.it * 32;
                         const uint32_t xre = st + (0 * NP + pb) * kDataTileBytes;
                         const uint32_t xim = st + (1 * NP + pb) * kDataTileBytes;
-                        const uint64_t are = KMAJOR ? smem_desc(xre, 16, 256, kSwz32) : smem_desc(xre, 2048, 1024, kSwz128);
-                        const uint64_t aim = KMAJOR ? smem_desc(xim, 16, 256, kSwz32) : smem_desc(xim, 2048, 1024, kSwz128);
-                        umma_f16(dcol, are, smem_desc(eC, 16, 256, kSwz32), idesc_full, started[acc] ? 1u : 0u);
+                        // MN-major: the atoms of a plane tile lie kAtomBytes apart (leading byte offset),
+                        // the 8-row groups along k 1024 bytes apart
+                        const uint64_t are = KMAJOR ? smem_desc(xre, 16, 256, kSwz32) : smem_desc(xre, kAtomBytes, 1024, kSwz128);
+                        const uint64_t aim = KMAJOR ? smem_desc(xim, 16, 256, kSwz32) : smem_desc(xim, kAtomBytes, 1024, kSwz128);
+                        mma(dcol, are, smem_desc(eC, 16, 256, kSwz32), idesc_full, started[acc] ? 1u : 0u);
                         started[acc] = true;
-                        umma_f16(dcol, aim, smem_desc(eS, 16, 256, kSwz32), idesc_half_neg, 1u);
-                        umma_f16(dcol + uint32_t(a.it), aim, smem_desc(eC, 16, 256, kSwz32), idesc_half, 1u);
+                        mma(dcol, aim, smem_desc(eS, 16, 256, kSwz32), idesc_half_neg, 1u);
+                        mma(dcol + uint32_t(a.it), aim, smem_desc(eC, 16, 256, kSwz32), idesc_half, 1u);
                     }
                     umma_commit(&empty[s]);
                 }
@@ -1171,8 +1414,8 @@ __global__ void __launch_bounds__(kThreads, 1)
             __syncwarp();
             if (lane == 0) mbarrier_arrive(tmem_empty);
             if (!acc_ready) break;
-            epi_store<NP, KMAJOR, EPI, FX, kChunksPerWarp>(a, v, tile, h, row, grp, nchunks, s_in, inv_out, lim,
-                                                          local_max, range_ok);
+            epi_store<NP, KMAJOR, EPI, FX, kChunksPerWarp, TF>(a, v, tile, h, row, grp, nchunks, s_in, inv_out,
+                                                              lim, local_max, range_ok);
         }
         if (FX) {
             const unsigned m = __reduce_max_sync(0xffffffffu, __float_as_uint(local_max));
@@ -2315,15 +2558,16 @@ static EncodeTiledFn encode_fn()
 }
 
 static bool encode(CUtensorMap *map, void *base, int rank, const cuuint64_t *dims, const cuuint64_t *strides_bytes,
-                   const cuuint32_t *box, CUtensorMapSwizzle swz)
+                   const cuuint32_t *box, CUtensorMapSwizzle swz, bool four_bytes = false)
 {
     EncodeTiledFn fn = encode_fn();
     if (!fn) return false;
     cuuint32_t estr[5] = {1, 1, 1, 1, 1};
-    // 16-bit elements (BF16 or FP16 pieces: TMA copies them bit for bit; zero fill is +0 in both)
-    return fn(map, CU_TENSOR_MAP_DATA_TYPE_BFLOAT16, cuuint32_t(rank), base, dims, strides_bytes, box, estr,
-              CU_TENSOR_MAP_INTERLEAVE_NONE, swz, CU_TENSOR_MAP_L2_PROMOTION_L2_256B,
-              CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE) == CUDA_SUCCESS;
+    // 16-bit elements (BF16 or FP16 pieces: TMA copies them bit for bit; zero fill is +0 in both),
+    // or 32-bit ones (TF32 pieces in FP32 containers)
+    return fn(map, four_bytes ? CU_TENSOR_MAP_DATA_TYPE_FLOAT32 : CU_TENSOR_MAP_DATA_TYPE_BFLOAT16, cuuint32_t(rank),
+              base, dims, strides_bytes, box, estr, CU_TENSOR_MAP_INTERLEAVE_NONE, swz,
+              CU_TENSOR_MAP_L2_PROMOTION_L2_256B, CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE) == CUDA_SUCCESS;
 }
 
 template <int NP, bool KM, int EPI, bool FX, bool PAIR>
@@ -2365,6 +2609,37 @@ static cudaError_t launch_tc(const CUtensorMap &mx, const CUtensorMap &me, const
             cfg.gridDim = dim3(unsigned(2 * active));
         e = cudaLaunchKernelEx(&cfg, kern, mx, me, a);
     }
+    count_launch();
+    if (e != cudaSuccess) return e;
+    return cudaGetLastError();
+}
+
+// The one-SM kernel on TF32 pieces (two pieces, plain epilogue).
+template <bool KM>
+static cudaError_t launch_tc_tf32(const CUtensorMap &mx, const CUtensorMap &me, const TcArgs &a, int grid, int smem,
+                                  cudaStream_t s)
+{
+    cudaLaunchConfig_t cfg = {};
+    cfg.gridDim = dim3(unsigned(grid));
+    cfg.blockDim = dim3(kThreads);
+    cfg.dynamicSmemBytes = size_t(smem);
+    cfg.stream = s;
+    cudaLaunchAttribute attr[2];
+    attr[0].id = cudaLaunchAttributeClusterDimension;
+    attr[0].val.clusterDim.x = 2;
+    attr[0].val.clusterDim.y = 1;
+    attr[0].val.clusterDim.z = 1;
+    attr[1].id = cudaLaunchAttributeProgrammaticStreamSerialization;
+    attr[1].val.programmaticStreamSerializationAllowed = 1;
+    cfg.attrs = attr;
+    cfg.numAttrs = 2;
+    auto kern = tc_mode_kernel<2, KM, 0, false, true>;
+    cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
+    if (e != cudaSuccess) return e;
+    int active = 0;
+    if (cudaOccupancyMaxActiveClusters(&active, kern, &cfg) == cudaSuccess && active > 0 && 2 * active < grid)
+        cfg.gridDim = dim3(unsigned(2 * active));
+    e = cudaLaunchKernelEx(&cfg, kern, mx, me, a);
     count_launch();
     if (e != cudaSuccess) return e;
     return cudaGetLastError();
@@ -2412,8 +2687,10 @@ static cudaError_t tc_setup(const TcState &si, const TcState &so, int mu, const 
 {
     const int NP = tc_pieces(prec);
     const bool fx = tc_fixed(prec);
-    if (NP == 0 || NP != M.npieces || fx != M.fixed) return cudaErrorInvalidValue;
+    const bool tf = tc_tf32(prec);
+    if (NP == 0 || NP != M.npieces || fx != M.fixed || tf != M.tf32) return cudaErrorInvalidValue;
     if (fx && (!sc.s_in || !sc.s_out || !sc.max_prev || !sc.max_cur || !M.rho)) return cudaErrorInvalidValue;
+    if (tf && (epi.kind != 0 || batch)) return cudaErrorNotSupported;  // TF32: plain products, one-SM kernel
     TcArgs &a = L->a;
     a = TcArgs{};
     a.left = 1;
@@ -2448,6 +2725,40 @@ static cudaError_t tc_setup(const TcState &si, const TcState &so, int mu, const 
     a.rho = M.rho;
     a.sc = sc;
     const bool km = a.left == 1;
+    if (tf) {
+        // TF32 pieces: 4-byte elements, k-blocks of 8 (32-byte rows, the same stage bytes as the 16-bit
+        // pieces), MN-major tiles of four 32-point atoms; the one-SM kernel only
+        a.kblocks = int(a.kp / 8);
+        a.aps = (a.left + 31) / 32;
+        CUtensorMap &mx = L->mx, &me = L->me;
+        void *xin = const_cast<void *>(in_pieces);
+        if (km) {
+            cuuint64_t dims[3] = {cuuint64_t(a.kp), cuuint64_t(a.right), cuuint64_t(2 * NP)};
+            cuuint64_t str[2] = {cuuint64_t(a.kp * 4), cuuint64_t(si.plane * 4)};
+            cuuint32_t box[3] = {8, kTileM, 1};
+            if (!encode(&mx, xin, 3, dims, str, box, CU_TENSOR_MAP_SWIZZLE_32B, true)) return cudaErrorInvalidValue;
+        } else {
+            cuuint64_t dims[4] = {cuuint64_t(a.left), cuuint64_t(a.kp), cuuint64_t(a.right), cuuint64_t(2 * NP)};
+            cuuint64_t str[3] = {cuuint64_t(a.left * 4), cuuint64_t(a.left * a.kp * 4), cuuint64_t(si.plane * 4)};
+            cuuint32_t box[4] = {32, 8, 1, 1};
+            if (!encode(&mx, xin, 4, dims, str, box, CU_TENSOR_MAP_SWIZZLE_128B, true)) return cudaErrorInvalidValue;
+        }
+        const int64_t rows = int64_t(NP) * M.ni * a.kblocks * kBlocks * M.it;
+        cuuint64_t dims[2] = {8, cuuint64_t(rows)};
+        cuuint64_t str[1] = {32};
+        cuuint32_t box[2] = {8, cuuint32_t(M.it / 2)};
+        if (!encode(&me, M.pieces, 2, dims, str, box, CU_TENSOR_MAP_SWIZZLE_32B, true)) return cudaErrorInvalidValue;
+        a.tiles = km ? (a.right + kTileM - 1) / kTileM : (a.right * a.aps + 3) / 4;
+        a.pairs = (a.tiles + 1) / 2 * a.ni;
+        std::memset(&L->my, 0, sizeof L->my);
+        L->km = km;
+        L->pair = false;
+        L->fx = false;
+        L->np = NP;
+        L->grid = int(2 * (a.pairs < num_sms() / 2 ? a.pairs : num_sms() / 2));
+        L->smem = kStages * a.stage_bytes + 1024 + 256;
+        return cudaSuccess;
+    }
 
     CUtensorMap &mx = L->mx, &me = L->me;
     void *xin = const_cast<void *>(in_pieces);
@@ -2545,11 +2856,41 @@ cudaError_t tc_mode_product(const TcState &si, const TcState &so, int mu, const 
                             const void *in_pieces, void *out_pieces, const TcEpilogue &epi, const TcScales &sc,
                             int *d_err, cudaStream_t s, TcVariant variant)
 {
+    if (tc_tf32(prec) && mu > 1) {
+        // The tcgen05 TF32 MMA takes the data K-major only (measured: an MN-major TF32 operand gives
+        // zeros), so directions after the first run as a first direction on swapped data: the
+        // pieces [right][n_mu][left] are swapped to [right][left][n_mu] into the output buffer, the
+        // product runs from there into the input buffer (whose contents are no longer needed), and
+        // the result is swapped back into the output buffer.  Both buffers hold the larger state.
+        int64_t left = 1, right = 1;
+        for (int v = 0; v < mu - 1; ++v) left *= si.np[v];
+        for (int v = mu; v < si.d; ++v) right *= si.np[v];
+        TcState ti, to;
+        ti.d = to.d = 3;
+        ti.n[0] = si.n[mu - 1];
+        ti.np[0] = si.np[mu - 1];
+        to.n[0] = so.n[mu - 1];
+        to.np[0] = so.np[mu - 1];
+        ti.n[1] = ti.np[1] = to.n[1] = to.np[1] = left;
+        ti.n[2] = ti.np[2] = to.n[2] = to.np[2] = right;
+        ti.plane = si.plane;
+        to.plane = so.plane;
+        const int planes = 2 * tc_pieces(prec);
+        cudaError_t e = swap_last2(in_pieces, out_pieces, right, si.np[mu - 1], left, planes, si.plane, s);
+        if (e == cudaSuccess)
+            e = tc_mode_product(ti, to, 1, M, prec, out_pieces, const_cast<void *>(in_pieces), epi, sc, d_err, s,
+                                variant);
+        if (e == cudaSuccess) e = swap_last2(in_pieces, out_pieces, right, left, so.np[mu - 1], planes, so.plane, s);
+        return e;
+    }
     TcLaunch L;
     cudaError_t e = tc_setup(si, so, mu, M, prec, in_pieces, out_pieces, epi, sc, d_err, variant, &L);
     if (e != cudaSuccess) return e;
     const TcArgs &a = L.a;
     const int kind = epi.kind;
+    if (tc_tf32(prec))
+        return L.km ? launch_tc_tf32<true>(L.mx, L.me, a, L.grid, L.smem, s)
+                    : launch_tc_tf32<false>(L.mx, L.me, a, L.grid, L.smem, s);
     if (L.pair) {
         if (L.fx) return dispatch_np<3, true, true>(L.km, kind, L.mx, L.me, L.my, a, L.grid, L.smem, s);
         switch (L.np) {
@@ -2856,8 +3197,9 @@ double tc_issued_flops(const TcState &si, int mu, const TcMatrix &M, mm_prec pre
     int64_t left = 1, right = 1;
     for (int v = 0; v < mu - 1; ++v) left *= si.np[v];
     for (int v = mu; v < si.d; ++v) right *= si.np[v];
-    const int64_t aps = (left + 63) / 64;
-    const int64_t tiles = left == 1 ? (right + kTileM - 1) / kTileM : (right * aps + 1) / 2;
+    const bool tf = tc_tf32(prec);
+    const int64_t aps = tf ? (left + 31) / 32 : (left + 63) / 64;
+    const int64_t tiles = left == 1 ? (right + kTileM - 1) / kTileM : (tf ? (right * aps + 3) / 4 : (right * aps + 1) / 2);
     const int64_t tiles_run = (tiles + 1) / 2 * 2;  // CTA pairs
     // the kernel that runs and its row tiling
     const TcMatrix::TcPairTiles *PT = pair_tiles(M, variant);
@@ -2865,7 +3207,7 @@ double tc_issued_flops(const TcState &si, int mu, const TcMatrix &M, mm_prec pre
     const int *lo = PT ? PT->kb_lo : M.kb_lo, *hi = PT ? PT->kb_hi : M.kb_hi;
     // one k-block of one point tile: per piece product 2 M N K over N = 4 it columns (one-SM kernel: the
     // real plane with N = 2 it and the imaginary plane as two of N = it; pair kernel: two of N = 2 it)
-    const double per_kb = double(num_terms(NP)) * 2.0 * kTileM * (4.0 * it) * kBK;
+    const double per_kb = double(num_terms(NP)) * 2.0 * kTileM * (4.0 * it) * (tf ? 8 : kBK);
     double total = 0.0;
     for (int h = 0; h < ni; ++h) total += double(tiles_run) * double(hi[h] - lo[h]) * per_kb;
     return total;

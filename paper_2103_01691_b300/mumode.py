@@ -19,7 +19,7 @@ _HERE = os.path.dirname(os.path.abspath(__file__))
 LIB_PATH = os.path.join(_HERE, "libmumode.so")
 
 MM_R64, MM_C64, MM_C128, MM_R32 = 0, 1, 2, 3
-PREC = {"fp64": 0, "fp32": 1, "bf16x6": 2, "bf16x3": 3, "bf16": 4, "f16x6": 5, "fp64dmma": 6, "auto": 7}
+PREC = {"fp64": 0, "fp32": 1, "bf16x6": 2, "bf16x3": 3, "bf16": 4, "f16x6": 5, "fp64dmma": 6, "auto": 7, "tf32x3": 8}
 STATUS = {0: "MM_OK", 1: "MM_ERR_INVALID_ARG", 2: "MM_ERR_SHAPE", 3: "MM_ERR_DTYPE", 4: "MM_ERR_ALIGN",
           5: "MM_ERR_OOM", 6: "MM_ERR_CUDA", 7: "MM_ERR_TIMEOUT", 8: "MM_ERR_UNSUPPORTED", 9: "MM_ERR_RANGE"}
 

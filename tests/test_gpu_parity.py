@@ -8,6 +8,9 @@ Tolerances (relative L2 over all compared points):
   BF16x6 (floating pieces)       3e-7 per mode product; its truncation bias
                                  grows linearly, so it fails the 50-step bound
   BF16x3                         2e-4 per run
+  3xTF32 (two TF32 pieces,       4e-6 per run of two steps (measured up to 1.6e-6 at 511),
+  three products)                2e-6 per mode product; its truncation bias grows like
+                                 BF16x6's (3.9e-5 after 50 steps at n = 256)
   BF16 (1 piece)                 3e-2 per run (reported only)
 """
 import numpy as np
@@ -17,7 +20,7 @@ from paper_2103_01691_b300 import inputs
 
 pytestmark = pytest.mark.gpu
 
-TOL_STEP = {"fp64": 1e-12, "fp32": 2e-5, "f16x6": 1e-6, "bf16x6": 1e-6, "bf16x3": 2e-4, "bf16": 3e-2}
+TOL_STEP = {"fp64": 1e-12, "fp32": 2e-5, "f16x6": 1e-6, "bf16x6": 1e-6, "bf16x3": 2e-4, "bf16": 3e-2, "tf32x3": 4e-6}
 TOL_MODE = {"f16x6": 1.5e-7, "bf16x6": 3e-7}
 
 
@@ -103,7 +106,7 @@ TC_DIMS = [(16, 16, 16), (32, 48, 16), (17, 33, 20), (64, 64, 64), (100, 37, 48)
 
 
 @pytest.mark.parametrize("dims", TC_DIMS)
-@pytest.mark.parametrize("prec", ["f16x6", "bf16x6", "bf16x3", "bf16"])
+@pytest.mark.parametrize("prec", ["f16x6", "bf16x6", "bf16x3", "bf16", "tf32x3"])
 def test_tc_tucker_steps(env, orc, dims, prec):
     mm, ctx, torch = env
     tau, steps = 1e-4, 2
@@ -116,11 +119,11 @@ def test_tc_tucker_steps(env, orc, dims, prec):
     err = rel(u.cpu().numpy(), ref)
     print(f"{prec} dims={dims} steps={steps} rel_err={err:.3e}")
     tol = {"f16x6": TOL_MODE["f16x6"] * steps * len(dims), "bf16x6": TOL_MODE["bf16x6"] * steps * len(dims),
-           "bf16x3": TOL_STEP["bf16x3"], "bf16": TOL_STEP["bf16"]}[prec]
+           "bf16x3": TOL_STEP["bf16x3"], "bf16": TOL_STEP["bf16"], "tf32x3": TOL_STEP["tf32x3"]}[prec]
     assert err <= tol
 
 
-@pytest.mark.parametrize("prec", ["f16x6", "bf16x6", "fp64", "fp64dmma", "fp32"])
+@pytest.mark.parametrize("prec", ["f16x6", "bf16x6", "fp64", "fp64dmma", "fp32", "tf32x3"])
 @pytest.mark.parametrize("dims", [(40, 24, 18), (17, 64, 9)])
 def test_mumode_product_rectangular(env, orc, prec, dims):
     """Definition 2.1 with a rectangular complex (and a real) L."""
@@ -128,7 +131,7 @@ def test_mumode_product_rectangular(env, orc, prec, dims):
     rng = np.random.default_rng(12)
     u0 = inputs.complex_normal(dims[::-1], seed=3)
     dt = torch.complex128 if prec in ("fp64", "fp64dmma") else torch.complex64
-    tol = {"fp64": 1e-13, "fp64dmma": 1e-13, "fp32": 1e-5, "bf16x6": 3e-7, "f16x6": 1.5e-7}[prec]
+    tol = {"fp64": 1e-13, "fp64dmma": 1e-13, "fp32": 1e-5, "bf16x6": 3e-7, "f16x6": 1.5e-7, "tf32x3": 8e-7}[prec]
     for mu in range(1, 4):
         for m in (dims[mu - 1] + 8, max(1, dims[mu - 1] - 5)):
             for cplx in (True, False):
@@ -139,6 +142,8 @@ def test_mumode_product_rectangular(env, orc, prec, dims):
                 s = mm.mumode_product(ctx, to_gpu(torch, uin, dt), mu, L, prec=prec)
                 ref = orc.mode_product(uin.astype(complex), mu, L.astype(complex))
                 err = rel(s.cpu().numpy(), ref)
+                if prec == "tf32x3":
+                    print(f"tf32x3 product dims={dims} mu={mu} m={m} complex={cplx}: rel_err={err:.3e}")
                 assert err <= tol, (mu, m, cplx, err)
 
 
