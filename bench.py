@@ -734,8 +734,13 @@ def other_workload(args):
         # the first call builds the adjoint's matrices and checkpoint buffers (kept with the plan)
         ms_adj_first = _time(lambda: plan.gpe_adjoint(psi0, gT, beta, tau, 100, ckpt_every=50), stream)
         ms_adj = _time(lambda: plan.gpe_adjoint(psi0, gT, beta, tau, 100, ckpt_every=50), stream)
+        # one segment (checkpoint interval >= steps): no state is computed twice
+        plan.gpe_adjoint(psi0, gT, beta, tau, 100, ckpt_every=100)
+        ms_adj1 = _time(lambda: plan.gpe_adjoint(psi0, gT, beta, tau, 100, ckpt_every=100), stream)
         line.update(value=K / (ms / 1e3), steps=K, precision="f16x6",
                     adjoint_ms_per_step=ms_adj / 100, adjoint_first_call_ms=ms_adj_first,
+                    adjoint_ms_per_step_one_segment=ms_adj1 / 100,
+                    forward_ms_per_step=ms / K,
                     config="GPE Strang, Hermite n=192^3 complex64, beta=100, tau=1e-3; adjoint 100 steps, ckpt 50")
     elif world > 1:  # batched64 over several GPUs: the problems dealt by flop count, no exchange
         dims_all = inputs.batched_dims(64, seed=3)

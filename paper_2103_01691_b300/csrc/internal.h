@@ -95,6 +95,8 @@ enum TcVariant { kTcPair64 = 0, kTcPair128 = 1, kTcOneSM = 2, kTcChain = 3, kTcV
 // The variant a plan starts with: kTcPair64, or what the environment forces
 // (MM_TC_1SM set to other than 0: kTcOneSM; MM_PAIR_TILE=128: kTcPair128).
 TcVariant tc_default_variant();
+// Whether a product with M runs on the CTA-pair kernel in this variant (else the one-SM kernel).
+bool tc_pair_ready(const TcMatrix &M, TcVariant variant);
 
 int tc_pieces(mm_prec p);
 bool tc_prec(mm_prec p);
@@ -203,8 +205,14 @@ struct TcProblem {  // the CUtensorMap members carry the 64-byte alignment TMA n
 };
 
 struct TcEpilogue {
-    int kind = 0;      // 0: store pieces, 1: nonlinear phase then store pieces, 2: point phase then store
-    double tb = 0.0;   // tau * beta for kind 1
+    // 0: store pieces, 1: nonlinear phase then store pieces, 2: point phase then store; 3: as 1,
+    // and the value before the phase goes to mid_out; 4: the adjoint of that phase at the state in
+    // mid_in (3 and 4: CTA-pair kernel, F16X6; mid buffers complex64 in the padded layout of one
+    // piece plane of the output)
+    int kind = 0;
+    double tb = 0.0;   // tau * beta for kinds 1, 3, 4
+    float2 *mid_out = nullptr;
+    const float2 *mid_in = nullptr;
     // kind 2 (CTA-pair kernel with row tiles of at most 64): every output at point (l, r) (the
     // non-contracted index groups left and right of the direction) is multiplied by
     // pl0[l % ldiv] pl1[l / ldiv] pr0[r % rdiv] pr1[r / rdiv] (device tables, null: factor 1)

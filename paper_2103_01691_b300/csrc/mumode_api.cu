@@ -1503,7 +1503,17 @@ extern "C" mm_status split_step_gpe_adjoint(mm_plan *p, const void *psi0, const 
         C.tau = tau;
     }
     MatSet &Fh = C.Fh, &Ff = C.Ff, &Ah = C.Ah, &Af = C.Af;
-    if (!C.reserve(bytes * size_t(nseg), bytes * size_t(seglen), bytes))
+    // Fused form (F16X6 on the CTA-pair kernel): the recomputed states before the nonlinear stages
+    // come from the epilogue of each forward sweep (kind 3, which applies the phase as well), the
+    // nonlinear adjoint runs in the epilogue of each adjoint sweep (kind 4), and the state stays in
+    // pieces through a segment: one split and one merge per segment instead of per step.  The
+    // stored states are complex64 in the padded layout of a piece plane.
+    bool fused = p->tc && p->fixed && p->variant != mm::kTcOneSM;
+    for (int v = 0; v < p->d && fused; ++v)
+        fused = mm::tc_pair_ready(Fh.tc[v], p->variant) && mm::tc_pair_ready(Ff.tc[v], p->variant) &&
+                mm::tc_pair_ready(Ah.tc[v], p->variant) && mm::tc_pair_ready(Af.tc[v], p->variant);
+    const size_t mid_state = fused ? size_t(p->st.plane) * sizeof(float2) : bytes;
+    if (!C.reserve(bytes * size_t(nseg), mid_state * size_t(seglen), bytes))
         return fail(MM_ERR_OOM, "checkpoint storage (%lld states)", (long long)(nseg + seglen + 1));
     void *ckpt = C.ckpt, *mid = C.mid, *tmp = C.tmp;
     auto ck = [&](int64_t k) { return static_cast<char *>(ckpt) + bytes * size_t(k); };
@@ -1521,6 +1531,50 @@ extern "C" mm_status split_step_gpe_adjoint(mm_plan *p, const void *psi0, const 
         if (e != cudaSuccess) return cuda_fail(e, "checkpoint copy");
         if (k == nseg - 1) break;
         if ((st = split_step_gpe(p, tmp, beta, tau, ckpt_every, stream))) return st;
+    }
+    if (fused) {
+        // reverse sweep, segment by segment.  Adjoint sweeps, in order: L_h^H then the nonlinear
+        // adjoint of the last step, L_tau^H then that of each earlier step, a last L_h^H.
+        e = cudaMemcpyAsync(g0, gT, bytes, cudaMemcpyDeviceToDevice, s);
+        if (e != cudaSuccess) return cuda_fail(e, "copy");
+        mm::TcMatrix *Mfh[mm::kMaxDims], *Mff[mm::kMaxDims], *Mah[mm::kMaxDims], *Maf[mm::kMaxDims];
+        for (int v = 0; v < p->d; ++v) {
+            Mfh[v] = &Fh.tc[v];
+            Mff[v] = &Ff.tc[v];
+            Mah[v] = &Ah.tc[v];
+            Maf[v] = &Af.tc[v];
+        }
+        auto mid_at = [&](int64_t j) { return reinterpret_cast<float2 *>(static_cast<char *>(mid) + mid_state * size_t(j)); };
+        for (int64_t k = nseg - 1; k >= 0 && !st; --k) {
+            const int64_t first = k * ckpt_every, last = std::min(nsteps, first + ckpt_every);
+            // the states before the nonlinear stages of steps first .. last - 1, from the checkpoint
+            int cur = 0;
+            st = tc_begin(p, Mfh, ck(k), s);
+            for (int64_t q = first; q < last && !st; ++q) {
+                mm::TcEpilogue ep;
+                ep.kind = 3;
+                ep.tb = tb;
+                ep.mid_out = mid_at(q - first);
+                st = tc_sweep(p, q == first ? Mfh : Mff, cur, ep, s);
+            }
+            if (st) break;
+            // the adjoint through the segment, its state in pieces from split to merge
+            cur = 0;
+            st = tc_begin(p, last == nsteps ? Mah : Maf, g0, s);
+            for (int64_t q = last - 1; q >= first && !st; --q) {
+                mm::TcEpilogue ep;
+                ep.kind = 4;
+                ep.tb = tb;
+                ep.mid_in = mid_at(q - first);
+                st = tc_sweep(p, q == nsteps - 1 ? Mah : Maf, cur, ep, s);
+            }
+            if (!st && k == 0) st = tc_sweep(p, Mah, cur, mm::TcEpilogue{}, s);
+            if (!st) st = tc_end(p, cur, g0, s);
+        }
+        cudaError_t e2 = cudaStreamSynchronize(s);
+        if (st) return st;
+        if (e2 != cudaSuccess) return cuda_fail(e2, "adjoint (sync)");
+        return MM_OK;
     }
     // reverse sweep, segment by segment: recompute the states before each
     // nonlinear stage, then g <- L_h^H (N^adj (L_h^H g)) per step, with the

@@ -986,6 +986,10 @@ struct TcArgs {
     // test hook: the stage (counted over the launch, per CTA) whose loads the producers skip,
     // so that the MMA's wait for it runs out; -1: none
     int64_t withhold;
+    // nonlinear epilogues of the GPE adjoint (TcEpilogue kinds 3, 4): the state before the
+    // nonlinear stage, complex64 in the padded layout of one piece plane
+    float2 *mid_out;
+    const float2 *mid_in;
     // chained launches (one launch over a sequence of products): completion counters, one per
     // product, and the count that marks a product complete (one signal per CTA)
     unsigned *done;
@@ -1545,7 +1549,31 @@ __device__ __forceinline__ void epi_frag_store(const TcArgs &a, const CUtensorMa
                 xr *= g[k >> 2][k & 1];  // power of two: exact
                 xi *= g[k >> 2][k & 1];
             }
-            if (EPI == 1) {
+            if (EPI == 3 || EPI == 4) {
+                // this value's place in the padded plane (the pieces' offset): the state before the
+                // nonlinear stage is stored there (3) or read from there (4)
+                const int s8 = (k >> 1) & 1;
+                const int64_t i = i0 + 8 * (k >> 2) + 2 * tc + (k & 1);
+                const int64_t off = KMAJOR ? (rr + 16 * hh + 8 * s8 + t4) * a.mp + i
+                                           : (rr * a.mp + i) * a.left + l0 + 16 * hh + 8 * s8 + t4;
+                if (EPI == 3) {
+                    if (valid[hh][s8]) a.mid_out[off] = make_float2(xr, xi);
+                } else {
+                    // adjoint of psi -> psi exp(-i tb |psi|^2) at psi (conjugate-Wirtinger gradient
+                    // convention): g = exp(i th) g' + 2 tb Im(conj(g') psi') psi, psi' = exp(-i th) psi
+                    const float2 ps = valid[hh][s8] ? a.mid_in[off] : make_float2(0.0f, 0.0f);
+                    const float th = a.tb * (ps.x * ps.x + ps.y * ps.y);
+                    float sn, cs;
+                    sincosf(th, &sn, &cs);
+                    const float pr = ps.x * cs + ps.y * sn, pi = ps.y * cs - ps.x * sn;  // psi'
+                    const float im = xr * pi - xi * pr;                                  // Im(conj(g') psi')
+                    const float f = 2.0f * a.tb * im;
+                    const float yr = xr * cs - xi * sn + f * ps.x, yi = xr * sn + xi * cs + f * ps.y;
+                    xr = yr;
+                    xi = yi;
+                }
+            }
+            if (EPI == 1 || EPI == 3) {
                 const float th = a.tb * (xr * xr + xi * xi);
                 float sn, cs;
                 sincosf(th, &sn, &cs);
@@ -1647,7 +1675,7 @@ __device__ __forceinline__ void epi_frag_store(const TcArgs &a, const CUtensorMa
 // whose small problems give short items with much epilogue work per MMA.
 __host__ __device__ constexpr int pair_epi_warps(int CH, int EPI, bool BATCH)
 {
-    return CH == 1 && EPI != 1 && !BATCH ? 8 : 16;
+    return CH == 1 && (EPI == 0 || EPI == 2) && !BATCH ? 8 : 16;
 }
 __host__ __device__ constexpr int pair_threads(int CH, int EPI, bool BATCH)
 {
@@ -2649,10 +2677,17 @@ template <int NP, bool FX, bool PAIR>
 static cudaError_t dispatch_np(bool km, int epi, const CUtensorMap &mx, const CUtensorMap &me, const CUtensorMap &my,
                                const TcArgs &a, int grid, int smem, cudaStream_t s)
 {
-    if (epi == 2) {  // the point-phase epilogue: CTA-pair kernel only
+    if (epi >= 2) {  // the point-phase and GPE-adjoint epilogues: CTA-pair kernel, F16X6 only
         if constexpr (PAIR && NP == 3 && FX) {
-            return km ? launch_tc<NP, true, 2, FX, PAIR>(mx, me, my, a, grid, smem, s)
-                      : launch_tc<NP, false, 2, FX, PAIR>(mx, me, my, a, grid, smem, s);
+            if (epi == 2)
+                return km ? launch_tc<NP, true, 2, FX, PAIR>(mx, me, my, a, grid, smem, s)
+                          : launch_tc<NP, false, 2, FX, PAIR>(mx, me, my, a, grid, smem, s);
+            if (epi == 3)
+                return km ? launch_tc<NP, true, 3, FX, PAIR>(mx, me, my, a, grid, smem, s)
+                          : launch_tc<NP, false, 3, FX, PAIR>(mx, me, my, a, grid, smem, s);
+            if (epi == 4)
+                return km ? launch_tc<NP, true, 4, FX, PAIR>(mx, me, my, a, grid, smem, s)
+                          : launch_tc<NP, false, 4, FX, PAIR>(mx, me, my, a, grid, smem, s);
         }
         return cudaErrorNotSupported;
     }
@@ -2670,6 +2705,8 @@ static const TcMatrix::TcPairTiles *pair_tiles(const TcMatrix &M, TcVariant v)
     const TcMatrix::TcPairTiles &P = M.pair[v == kTcPair128 ? 1 : 0];  // kTcChain: row tiles of 64
     return P.pieces ? &P : nullptr;
 }
+
+bool tc_pair_ready(const TcMatrix &M, TcVariant variant) { return pair_tiles(M, variant) != nullptr; }
 
 // Everything a launch of one product needs: tensor maps, kernel arguments,
 // which kernel (K-major or not, pair or one-SM), grid and shared memory.
@@ -2719,6 +2756,9 @@ static cudaError_t tc_setup(const TcState &si, const TcState &so, int mu, const 
     a.pr1 = epi.pr1;
     a.ldiv = epi.ldiv > 0 ? epi.ldiv : 1;
     a.rdiv = epi.rdiv > 0 ? epi.rdiv : 1;
+    a.mid_out = epi.mid_out;
+    a.mid_in = epi.mid_in;
+    if ((epi.kind == 3 && !epi.mid_out) || (epi.kind == 4 && !epi.mid_in)) return cudaErrorInvalidValue;
     a.out = (uint16_t *)out_pieces;
     a.err = d_err;
     wait_hooks(&a.wait_limit, &a.withhold);

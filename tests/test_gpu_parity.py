@@ -760,7 +760,7 @@ def test_gpe_adjoint_matches_oracle(env, orc, prec, ckpt):
     g0 = plan.gpe_adjoint(to_gpu(torch, p0, dt), to_gpu(torch, gT, dt), beta, tau, steps, ckpt_every=ckpt)
     err = rel(g0.cpu().numpy(), ref)
     print(f"adjoint {prec} ckpt={ckpt} rel_err={err:.3e}")
-    assert err <= (1e-10 if prec == "fp64" else 2e-5)
+    assert err <= (1e-10 if prec == "fp64" else 5e-7)
 
 
 @pytest.mark.parametrize("prec", ["f16x6", "fp64"])
@@ -786,7 +786,7 @@ def test_gpe_adjoint_repeated_calls(env, orc, prec):
         ref = orc.gpe_adjoint(p0.astype(complex), gT, xo, Wo, beta, tau, steps)
         return g0.cpu().numpy(), ref
 
-    tol = 1e-10 if prec == "fp64" else 2e-5
+    tol = 1e-10 if prec == "fp64" else 5e-7  # F16X6 measured 2.3e-7 and 2.5e-7
     ga, ref_a = case(1e-3)
     gb, _ = case(1e-3)
     assert np.array_equal(ga.view(np.float64 if prec == "fp64" else np.float32),
