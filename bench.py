@@ -730,6 +730,19 @@ def other_workload(args):
                                           inputs.gpe_psi0(x, W, seed=4), K))
             line["fp64dmma_steps_per_s"] = K / (ms64 / 1e3)
             del p64, t64, traj
+        # a mass monitor every 10 steps: the weighted norm from the last product's epilogue, against
+        # the same steps followed by a separate norm pass (both read the sum back to the host)
+        def monitored(fused):
+            for _ in range(K // 10):
+                if fused:
+                    plan.gpe_step_norm2(psi, beta, tau, 10)
+                else:
+                    plan.gpe_step(psi, beta, tau, 10)
+                    plan.norm2(psi)
+        monitored(True)
+        monitored(False)
+        ms_mon_fused = _time(lambda: monitored(True), stream)
+        ms_mon_sep = _time(lambda: monitored(False), stream)
         gT = torch.randn_like(psi0)
         # the first call builds the adjoint's matrices and checkpoint buffers (kept with the plan)
         ms_adj_first = _time(lambda: plan.gpe_adjoint(psi0, gT, beta, tau, 100, ckpt_every=50), stream)
@@ -741,6 +754,8 @@ def other_workload(args):
                     adjoint_ms_per_step=ms_adj / 100, adjoint_first_call_ms=ms_adj_first,
                     adjoint_ms_per_step_one_segment=ms_adj1 / 100,
                     forward_ms_per_step=ms / K,
+                    norm_every_10_ms_per_step_epilogue=ms_mon_fused / K,
+                    norm_every_10_ms_per_step_separate=ms_mon_sep / K,
                     config="GPE Strang, Hermite n=192^3 complex64, beta=100, tau=1e-3; adjoint 100 steps, ckpt 50")
     elif world > 1:  # batched64 over several GPUs: the problems dealt by flop count, no exchange
         dims_all = inputs.batched_dims(64, seed=3)

@@ -483,6 +483,19 @@ mm_status hkmp_evolve(mm_plan *plan, void *psi_dev, int64_t nsteps, const double
 mm_status split_step_gpe(mm_plan *plan, void *psi_dev, double beta, double tau, int64_t nsteps,
                          void *stream);
 
+/* split_step_gpe, then the weighted norm sum_x |psi(x)|^2 W1(x1) W2(x2) W3(x3)
+ * of the result (the Gauss-Hermite quadrature of ||psi||^2, the conserved
+ * mass of section 4.5) in FP64 to *norm2_host (host memory); the stream is
+ * synchronised.  On F16X6 plans with the CTA-pair kernel the sum is taken in
+ * the epilogue of the last mode product, from the FP32 values before they
+ * are split (one FP64 atomic per epilogue warp), so no pass re-reads psi;
+ * otherwise the steps are followed by mm_norm2(weighted).  nsteps = 0 gives
+ * the norm of psi_dev.  3D Hermite plans only.  Errors: those of
+ * split_step_gpe and mm_norm2, MM_ERR_INVALID_ARG (not a 3D Hermite plan,
+ * norm2_host NULL), MM_ERR_OOM (the plan's 8-byte accumulator). */
+mm_status split_step_gpe_norm2(mm_plan *plan, void *psi_dev, double beta, double tau, int64_t nsteps,
+                               double *norm2_host, void *stream);
+
 /* Gradient of a real loss J(psi_T), psi_T = nsteps Strang steps of psi0
  * (split_step_gpe with the same beta, tau), with respect to psi0 (reverse
  * mode; not in the paper).  Gradients are g = dJ/dRe psi + i dJ/dIm psi, so

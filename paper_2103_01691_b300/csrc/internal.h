@@ -208,7 +208,7 @@ struct TcEpilogue {
     // 0: store pieces, 1: nonlinear phase then store pieces, 2: point phase then store; 3: as 1,
     // and the value before the phase goes to mid_out; 4: the adjoint of that phase at the state in
     // mid_in (3 and 4: CTA-pair kernel, F16X6; mid buffers complex64 in the padded layout of one
-    // piece plane of the output)
+    // piece plane of the output); 5: store, and the weighted norm of the output (below)
     int kind = 0;
     double tb = 0.0;   // tau * beta for kinds 1, 3, 4
     float2 *mid_out = nullptr;
@@ -218,6 +218,12 @@ struct TcEpilogue {
     // pl0[l % ldiv] pl1[l / ldiv] pr0[r % rdiv] pr1[r / rdiv] (device tables, null: factor 1)
     const double2 *pl0 = nullptr, *pl1 = nullptr, *pr0 = nullptr, *pr1 = nullptr;
     int64_t ldiv = 1, rdiv = 1;
+    // kind 5 (CTA-pair kernel with row tiles of at most 64, F16X6): plain store, and the launch
+    // adds sum |y|^2 wl0[l % ldiv] wl1[l / ldiv] wr0[r % rdiv] wr1[r / rdiv] wo[i] over its outputs
+    // y (point (l, r), output index i) to *norm2 in FP64 (real device tables, null: factor 1; wo
+    // zero from the direction's length to its padded length)
+    const double *wl0 = nullptr, *wl1 = nullptr, *wr0 = nullptr, *wr1 = nullptr, *wo = nullptr;
+    double *norm2 = nullptr;
 };
 // One mu-mode product on the split state: in (sizes st_in) -> out (sizes
 // st_out, equal except direction mu which becomes M.n_out).

@@ -72,6 +72,8 @@ struct mm_plan {
     std::vector<double> x[mm::kMaxDims], W[mm::kMaxDims];
     std::vector<double> fwd[mm::kMaxDims], bwd[mm::kMaxDims];
     double *Wdev[mm::kMaxDims] = {};
+    double *Wpad[mm::kMaxDims] = {};  // the weights at padded length (zeros past n): the norm epilogue's
+    double *d_norm = nullptr;         // the norm epilogue's FP64 sum
     void *Fdev[mm::kMaxDims] = {}, *Bdev[mm::kMaxDims] = {};      // SIMT forward/backward
     mm::TcMatrix Ftc[mm::kMaxDims] = {}, Btc[mm::kMaxDims] = {};  // TC forward/backward
     // cached harmonic propagators Psi D(s) Phi_W for up to two step sizes
@@ -1162,6 +1164,7 @@ void mm_plan_destroy(mm_plan *p)
         if (p->Edev[v]) cudaFree(p->Edev[v]);
         mm::tc_matrix_destroy(&p->Etc[v]);
         if (p->Wdev[v]) cudaFree(p->Wdev[v]);
+        if (p->Wpad[v]) cudaFree(p->Wpad[v]);
         if (p->Fdev[v]) cudaFree(p->Fdev[v]);
         if (p->Bdev[v]) cudaFree(p->Bdev[v]);
         mm::tc_matrix_destroy(&p->Ftc[v]);
@@ -1175,6 +1178,7 @@ void mm_plan_destroy(mm_plan *p)
     if (p->d_scale) cudaFree(p->d_scale);
     if (p->d_max) cudaFree(p->d_max);
     if (p->d_work) cudaFree(p->d_work);
+    if (p->d_norm) cudaFree(p->d_norm);
     if (p->chain_dev) cudaFree(p->chain_dev);
     if (p->chain_done) cudaFree(p->chain_done);
     for (int v = 0; v < mm::kMaxDims; ++v) {
@@ -1229,6 +1233,11 @@ static mm_status hermite_setup(mm_plan *p)
         mm::hermite_matrices(m, p->x[v].data(), p->W[v].data(), p->fwd[v].data(), p->bwd[v].data());
         if (cudaMalloc(&p->Wdev[v], sizeof(double) * m) != cudaSuccess ||
             cudaMemcpy(p->Wdev[v], p->W[v].data(), sizeof(double) * m, cudaMemcpyHostToDevice) != cudaSuccess)
+            return fail(MM_ERR_OOM, "weights upload");
+        std::vector<double> wp(size_t((m + 15) / 16 * 16), 0.0);
+        std::copy(p->W[v].begin(), p->W[v].end(), wp.begin());
+        if (cudaMalloc(&p->Wpad[v], sizeof(double) * wp.size()) != cudaSuccess ||
+            cudaMemcpy(p->Wpad[v], wp.data(), sizeof(double) * wp.size(), cudaMemcpyHostToDevice) != cudaSuccess)
             return fail(MM_ERR_OOM, "weights upload");
         if ((st = upload_matrix(p, p->fwd[v].data(), m, m, false, &p->Fdev[v], &p->Ftc[v])) ||
             (st = upload_matrix(p, p->bwd[v].data(), m, m, false, &p->Bdev[v], &p->Btc[v])))
@@ -1302,13 +1311,16 @@ mm_status hermite_ho_step(mm_plan *p, void *psi, double tau, int64_t nsteps, voi
     });
 }
 
-mm_status split_step_gpe(mm_plan *p, void *psi, double beta, double tau, int64_t nsteps, void *stream)
+}  // extern "C"
+
+namespace {
+
+// Strang steps of the GPE; with d_norm (tensor cores, F16X6 on the CTA-pair kernel, pair tilings of
+// the half-step propagators), the last product's epilogue also sets *d_norm to the weighted norm
+// sum |psi|^2 W of the result (kind 5).
+mm_status gpe_steps(mm_plan *p, void *psi, double beta, double tau, int64_t nsteps, double *d_norm, cudaStream_t s)
 {
-    if (!p || !p->hermite) return fail(MM_ERR_INVALID_ARG, "not a Hermite plan");
-    mm_status st = check_ptr(psi, "psi_dev");
-    if (st) return st;
-    if (nsteps < 0 || !std::isfinite(tau) || !std::isfinite(beta)) return fail(MM_ERR_INVALID_ARG, "bad arguments");
-    if (nsteps == 0) return MM_OK;
+    mm_status st;
     int half, full;
     if ((st = ensure_prop(p, 0.5 * tau, -1, &half))) return st;
     if (nsteps > 1) {
@@ -1316,7 +1328,6 @@ mm_status split_step_gpe(mm_plan *p, void *psi, double beta, double tau, int64_t
     } else {
         full = half;
     }
-    cudaStream_t s = (cudaStream_t)stream;
     const double tb = tau * beta;
     if (!p->tc) {
         const bool fp64 = p->dtype == MM_C128;
@@ -1327,7 +1338,7 @@ mm_status split_step_gpe(mm_plan *p, void *psi, double beta, double tau, int64_t
         }
         return simt_sweep(p, p->Pdev[half], psi, s);
     }
-    return run_graphed(p, 2, psi, nsteps, s, tau, beta, [&]() -> mm_status {
+    return run_graphed(p, d_norm ? 5 : 2, psi, nsteps, s, tau, beta, [&]() -> mm_status {
         mm_status r;
         int cur = 0;
         mm::TcMatrix *Mh[mm::kMaxDims], *Mf[mm::kMaxDims];
@@ -1341,9 +1352,78 @@ mm_status split_step_gpe(mm_plan *p, void *psi, double beta, double tau, int64_t
         nl.tb = tb;
         for (int64_t k = 0; k < nsteps; ++k)
             if ((r = tc_sweep(p, k == 0 ? Mh : Mf, cur, nl, s))) return r;
-        if ((r = tc_sweep(p, Mh, cur, mm::TcEpilogue{}, s))) return r;
+        mm::TcEpilogue last;
+        if (d_norm) {
+            // the weights of the last direction's points: the directions before it (left index) and
+            // after it (right index), in the point phase's decomposition
+            const int v = p->order[p->d - 1] - 1, d = p->d;
+            const int64_t np0 = p->st.np[0], np1 = d > 1 ? p->st.np[1] : 1;
+            last.kind = 5;
+            last.wo = p->Wpad[v];
+            last.norm2 = d_norm;
+            if (v == 0) {
+                last.wr0 = d > 1 ? p->Wpad[1] : nullptr;
+                last.wr1 = d > 2 ? p->Wpad[2] : nullptr;
+                last.rdiv = np1;
+            } else if (v == 1) {
+                last.wl0 = p->Wpad[0];
+                last.ldiv = np0;
+                last.wr0 = d > 2 ? p->Wpad[2] : nullptr;
+            } else {
+                last.wl0 = p->Wpad[0];
+                last.wl1 = p->Wpad[1];
+                last.ldiv = np0;
+            }
+            cudaError_t e = cudaMemsetAsync(d_norm, 0, sizeof(double), s);
+            if (e != cudaSuccess) return cuda_fail(e, "norm accumulator");
+        }
+        if ((r = tc_sweep(p, Mh, cur, last, s))) return r;
         return tc_end(p, cur, psi, s);
     });
+}
+
+}  // namespace
+
+extern "C" {
+
+mm_status split_step_gpe_norm2(mm_plan *p, void *psi, double beta, double tau, int64_t nsteps, double *norm2_host,
+                               void *stream)
+{
+    if (!p || !p->hermite) return fail(MM_ERR_INVALID_ARG, "not a Hermite plan");
+    if (p->d != 3) return fail(MM_ERR_INVALID_ARG, "weighted norm needs a 3D Hermite plan");
+    if (!norm2_host) return fail(MM_ERR_INVALID_ARG, "norm2_host is NULL");
+    mm_status st = check_ptr(psi, "psi_dev");
+    if (st) return st;
+    if (nsteps < 0 || !std::isfinite(tau) || !std::isfinite(beta)) return fail(MM_ERR_INVALID_ARG, "bad arguments");
+    cudaStream_t s = (cudaStream_t)stream;
+    bool fused = nsteps > 0 && p->tc && p->fixed && p->variant != mm::kTcOneSM;
+    if (fused) {
+        // the half-step propagator (the last sweep's) must have its pair tiling
+        int half;
+        if ((st = ensure_prop(p, 0.5 * tau, -1, &half))) return st;
+        for (int v = 0; v < p->d && fused; ++v) fused = mm::tc_pair_ready(p->Ptc[half][v], p->variant);
+    }
+    if (!fused) {
+        if ((st = split_step_gpe(p, psi, beta, tau, nsteps, stream))) return st;
+        return mm_norm2(p, psi, 1, norm2_host, stream);
+    }
+    if (!p->d_norm && cudaMalloc(&p->d_norm, sizeof(double)) != cudaSuccess)
+        return fail(MM_ERR_OOM, "norm accumulator");
+    if ((st = gpe_steps(p, psi, beta, tau, nsteps, p->d_norm, s))) return st;
+    cudaError_t e = cudaMemcpyAsync(norm2_host, p->d_norm, sizeof(double), cudaMemcpyDeviceToHost, s);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(s);
+    if (e != cudaSuccess) return cuda_fail(e, "norm");
+    return MM_OK;
+}
+
+mm_status split_step_gpe(mm_plan *p, void *psi, double beta, double tau, int64_t nsteps, void *stream)
+{
+    if (!p || !p->hermite) return fail(MM_ERR_INVALID_ARG, "not a Hermite plan");
+    mm_status st = check_ptr(psi, "psi_dev");
+    if (st) return st;
+    if (nsteps < 0 || !std::isfinite(tau) || !std::isfinite(beta)) return fail(MM_ERR_INVALID_ARG, "bad arguments");
+    if (nsteps == 0) return MM_OK;
+    return gpe_steps(p, psi, beta, tau, nsteps, nullptr, (cudaStream_t)stream);
 }
 
 mm_status mm_norm2(mm_plan *p, const void *u_dev, int weighted, double *out_host, void *stream)

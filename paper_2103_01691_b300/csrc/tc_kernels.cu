@@ -979,6 +979,11 @@ struct TcArgs {
     float tb;               // tau * beta for the nonlinear epilogue
     const double2 *pl0, *pl1, *pr0, *pr1;  // point-phase epilogue (TcEpilogue kind 2)
     int64_t ldiv, rdiv;
+    // weighted-norm epilogue (TcEpilogue kind 5): real weights of the points, in the point
+    // phase's decomposition of (l, r), and of the outputs (zero past each direction's length),
+    // and the FP64 sum of |y|^2 w that the launch adds to
+    const double *wl0, *wl1, *wr0, *wr1, *wo;
+    double *norm2;
     uint16_t *out;
     int *err;
     // bounded waits give up after this many SM clocks (MM_ERR_TIMEOUT)
@@ -1472,6 +1477,32 @@ __device__ __forceinline__ float2 point_phase(const TcArgs &a, int64_t tile, int
     return make_float2(float(fr), float(fi));
 }
 
+// Weight (EPI 5) of point `lane` of the warp's 32 points in work item `tile`: the product of
+// its directions' quadrature weights in FP64; 0 outside the tensor.
+template <bool KMAJOR>
+__device__ __forceinline__ double point_weight(const TcArgs &a, int64_t tile, int quarter, int lane)
+{
+    int64_t l, r;
+    bool valid;
+    if (KMAJOR) {
+        l = 0;
+        r = tile * kTileM + quarter * 32 + lane;
+        valid = r < a.right;
+    } else {
+        const int64_t atom = 2 * tile + quarter / 2;
+        r = atom / a.aps;
+        l = (atom % a.aps) * 64 + (quarter & 1) * 32 + lane;
+        valid = r < a.right && l < a.left;
+    }
+    if (!valid) return 0.0;
+    double w = 1.0;
+    if (a.wl0) w *= a.wl0[l % a.ldiv];
+    if (a.wl1) w *= a.wl1[l / a.ldiv];
+    if (a.wr0) w *= a.wr0[r % a.rdiv];
+    if (a.wr1) w *= a.wr1[r / a.rdiv];
+    return w;
+}
+
 // Per-warp staging of the pair kernel's output boxes: one plane's three pieces, 1 KB each.
 constexpr int kStageBoxBytes = 1024;
 constexpr int kStagingPerWarp = 3 * kStageBoxBytes;
@@ -1492,7 +1523,7 @@ __device__ __forceinline__ void epi_frag_store(const TcArgs &a, const CUtensorMa
                                                float (&vr)[2][8], float (&vi)[2][8], int64_t tile, int h,
                                                int quarter, int lane, int grp, int nchunks, float s_in,
                                                float inv_out, float lim, float &local_max, bool &range_ok,
-                                               float2 phl)
+                                               float2 phl, double wpl, double &nacc)
 {
     if (grp >= nchunks) return;
     const int i0 = h * a.it + grp * 16;
@@ -1529,6 +1560,16 @@ __device__ __forceinline__ void epi_frag_store(const TcArgs &a, const CUtensorMa
                 ph[hh][s].x = __shfl_sync(0xffffffffu, phl.x, 16 * hh + 8 * s + t4);
                 ph[hh][s].y = __shfl_sync(0xffffffffu, phl.y, 16 * hh + 8 * s + t4);
             }
+    }
+    // output weights (EPI 5) of this thread's four outputs and the per-point sums of |y|^2 w over them
+    float wout[2][2] = {{0.0f, 0.0f}, {0.0f, 0.0f}}, psum[2][2] = {{0.0f, 0.0f}, {0.0f, 0.0f}};
+    if (EPI == 5) {
+#pragma unroll
+        for (int cb = 0; cb < 2; ++cb) {
+            const double2 w2 = __ldg(reinterpret_cast<const double2 *>(a.wo + i0 + 8 * cb + 2 * tc));
+            wout[cb][0] = float(w2.x);
+            wout[cb][1] = float(w2.y);
+        }
     }
     // row scales of this thread's four outputs (pairs at 2 tc and 8 + 2 tc)
     float g[2][2] = {{1.0f, 1.0f}, {1.0f, 1.0f}};
@@ -1587,6 +1628,7 @@ __device__ __forceinline__ void epi_frag_store(const TcArgs &a, const CUtensorMa
                 xr = yr;
                 xi = yi;
             }
+            if (EPI == 5) psum[hh][(k >> 1) & 1] += (xr * xr + xi * xi) * wout[k >> 2][k & 1];
             if (FX) {
                 const float ar = fabsf(xr), ai = fabsf(xi);
                 if (valid[hh][(k >> 1) & 1]) {
@@ -1599,6 +1641,14 @@ __device__ __forceinline__ void epi_frag_store(const TcArgs &a, const CUtensorMa
             vr[hh][k] = xr;
             vi[hh][k] = xi;
         }
+    if (EPI == 5) {
+        // the four points' weights (lane 16 hh + 8 s + t4 holds that point's; 0 outside the tensor)
+#pragma unroll
+        for (int hh = 0; hh < 2; ++hh)
+#pragma unroll
+            for (int s = 0; s < 2; ++s)
+                nacc += __shfl_sync(0xffffffffu, wpl, 16 * hh + 8 * s + t4) * double(psum[hh][s]);
+    }
     auto pieces_of = [&](float x, uint16_t *b) {
         if (FX) {
             split_fx_scaled(x, b[0], b[1], b[2]);
@@ -1675,7 +1725,7 @@ __device__ __forceinline__ void epi_frag_store(const TcArgs &a, const CUtensorMa
 // whose small problems give short items with much epilogue work per MMA.
 __host__ __device__ constexpr int pair_epi_warps(int CH, int EPI, bool BATCH)
 {
-    return CH == 1 && (EPI == 0 || EPI == 2) && !BATCH ? 8 : 16;
+    return CH == 1 && (EPI == 0 || EPI == 2 || EPI == 5) && !BATCH ? 8 : 16;
 }
 __host__ __device__ constexpr int pair_threads(int CH, int EPI, bool BATCH)
 {
@@ -2015,6 +2065,7 @@ __global__ void __launch_bounds__(pair_threads(CH, EPI, BATCH && !CHAIN), 1)
         int es_out = 0;
         float local_max = 0.0f;
         bool range_ok = true;
+        double nacc = 0.0;  // EPI 5: this thread's part of the weighted norm
         // the fixed-point scales of the problem being stored (BATCH: they change with the problem,
         // and the maximum gathered so far goes to the previous problem's word first)
         const TcArgs *cur = nullptr;
@@ -2127,21 +2178,28 @@ __global__ void __launch_bounds__(pair_threads(CH, EPI, BATCH && !CHAIN), 1)
             if (lane == 0) mbarrier_arrive(&tmem_empty[b]);
             if (!acc_ready) break;
             const float2 phl = EPI == 2 ? point_phase<KMAJOR>(A, tile, quarter, lane) : make_float2(1.0f, 0.0f);
+            const double wpl = EPI == 5 ? point_weight<KMAJOR>(A, tile, quarter, lane) : 0.0;
             if (CHAIN && pr->km) {
 #pragma unroll
                 for (int q = 0; q < kPerWarp; ++q)
                     epi_frag_store<NP, true, EPI, FX>(A, &pr->mapY, staging + ew * kStagingPerWarp, vr[q], vi[q],
                                                       tile, h, quarter, lane, grp + kGroups * q, nchunks, s_in,
-                                                      inv_out, lim, local_max, range_ok, phl);
+                                                      inv_out, lim, local_max, range_ok, phl, wpl, nacc);
             } else {
 #pragma unroll
                 for (int q = 0; q < kPerWarp; ++q)
                     epi_frag_store<NP, KMAJOR && !CHAIN, EPI, FX>(
                         A, BATCH ? &pr->mapY : &mapY, staging + ew * kStagingPerWarp, vr[q], vi[q], tile, h,
-                        quarter, lane, grp + kGroups * q, nchunks, s_in, inv_out, lim, local_max, range_ok, phl);
+                        quarter, lane, grp + kGroups * q, nchunks, s_in, inv_out, lim, local_max, range_ok, phl,
+                        wpl, nacc);
             }
         }
         if (lane == 0) bulk_wait0();  // this warp's stores are complete
+        if (EPI == 5) {
+#pragma unroll
+            for (int o = 16; o > 0; o >>= 1) nacc += __shfl_xor_sync(0xffffffffu, nacc, o);
+            if (lane == 0 && nacc != 0.0) atomicAdd(a.norm2, nacc);
+        }
         if (FX) {
             const unsigned m = __reduce_max_sync(0xffffffffu, __float_as_uint(local_max));
             if (lane == 0 && m && cur) atomicMax(cur->sc.max_cur, m);
@@ -2677,7 +2735,7 @@ template <int NP, bool FX, bool PAIR>
 static cudaError_t dispatch_np(bool km, int epi, const CUtensorMap &mx, const CUtensorMap &me, const CUtensorMap &my,
                                const TcArgs &a, int grid, int smem, cudaStream_t s)
 {
-    if (epi >= 2) {  // the point-phase and GPE-adjoint epilogues: CTA-pair kernel, F16X6 only
+    if (epi >= 2) {  // point phase, GPE adjoint, weighted norm: CTA-pair kernel, F16X6 only
         if constexpr (PAIR && NP == 3 && FX) {
             if (epi == 2)
                 return km ? launch_tc<NP, true, 2, FX, PAIR>(mx, me, my, a, grid, smem, s)
@@ -2688,6 +2746,9 @@ static cudaError_t dispatch_np(bool km, int epi, const CUtensorMap &mx, const CU
             if (epi == 4)
                 return km ? launch_tc<NP, true, 4, FX, PAIR>(mx, me, my, a, grid, smem, s)
                           : launch_tc<NP, false, 4, FX, PAIR>(mx, me, my, a, grid, smem, s);
+            if (epi == 5)
+                return km ? launch_tc<NP, true, 5, FX, PAIR>(mx, me, my, a, grid, smem, s)
+                          : launch_tc<NP, false, 5, FX, PAIR>(mx, me, my, a, grid, smem, s);
         }
         return cudaErrorNotSupported;
     }
@@ -2758,7 +2819,14 @@ static cudaError_t tc_setup(const TcState &si, const TcState &so, int mu, const 
     a.rdiv = epi.rdiv > 0 ? epi.rdiv : 1;
     a.mid_out = epi.mid_out;
     a.mid_in = epi.mid_in;
+    a.wl0 = epi.wl0;
+    a.wl1 = epi.wl1;
+    a.wr0 = epi.wr0;
+    a.wr1 = epi.wr1;
+    a.wo = epi.wo;
+    a.norm2 = epi.norm2;
     if ((epi.kind == 3 && !epi.mid_out) || (epi.kind == 4 && !epi.mid_in)) return cudaErrorInvalidValue;
+    if (epi.kind == 5 && (!epi.wo || !epi.norm2)) return cudaErrorInvalidValue;
     a.out = (uint16_t *)out_pieces;
     a.err = d_err;
     wait_hooks(&a.wait_limit, &a.withhold);

@@ -63,6 +63,18 @@ def gpe_psi0(x: np.ndarray, W: np.ndarray, seed: int = 4, noise: float = 0.05) -
     return _normalise(gaussian_at_nodes(x) * np.exp(1j * noise * xi), W)
 
 
+def gpe_psi0_dims(xs, Ws, seed: int = 4, noise: float = 0.05) -> np.ndarray:
+    """gpe_psi0 on a grid with its own nodes xs[v] and weights Ws[v] per
+    direction v = 0, 1, 2 (shape (n3, n2, n1)); equal to gpe_psi0 when all
+    three are the same."""
+    g = [np.exp(-0.5 * np.asarray(x) * np.asarray(x)) for x in xs]
+    gauss = (np.pi ** -0.75) * g[2][:, None, None] * g[1][None, :, None] * g[0][None, None, :]
+    rng = np.random.default_rng(seed)
+    psi = gauss * np.exp(1j * noise * rng.standard_normal(gauss.shape))
+    w3 = Ws[2][:, None, None] * Ws[1][None, :, None] * Ws[0][None, None, :]
+    return psi / np.sqrt(np.sum(np.abs(psi) ** 2 * w3))
+
+
 def gpe_target(x: np.ndarray, W: np.ndarray) -> np.ndarray:
     """Noise-free normalised Gaussian, the target state of the adjoint loss."""
     return _normalise(gaussian_at_nodes(x).astype(np.complex128), W)

@@ -76,6 +76,7 @@ SIGNATURES = {
     "hermite_backward": (_i, [_vp, _vp, _vp, _vp]),
     "hermite_ho_step": (_i, [_vp, _vp, _d, _i64, _vp]),
     "split_step_gpe": (_i, [_vp, _vp, _d, _d, _i64, _vp]),
+    "split_step_gpe_norm2": (_i, [_vp, _vp, _d, _d, _i64, ctypes.POINTER(ctypes.c_double), _vp]),
     "split_step_gpe_adjoint": (_i, [_vp, _vp, _vp, _vp, _d, _d, _i64, _i64, _vp]),
     "mm_norm2": (_i, [_vp, _vp, _i, _dp, _vp]),
 }
@@ -600,6 +601,15 @@ class HermitePlan(_Tunable):
         _check(lib().split_step_gpe(self.handle, ctypes.c_void_p(psi.data_ptr()), float(beta), float(tau),
                                     int(nsteps), _stream(stream)))
         return psi
+
+    def gpe_step_norm2(self, psi, beta: float, tau: float, nsteps: int = 1, stream=None) -> float:
+        """gpe_step, returning the weighted norm sum |psi|^2 W of the result (taken in the last
+        product's epilogue where the plan allows)."""
+        _need_cuda(psi)
+        out = ctypes.c_double()
+        _check(lib().split_step_gpe_norm2(self.handle, ctypes.c_void_p(psi.data_ptr()), float(beta), float(tau),
+                                          int(nsteps), ctypes.byref(out), _stream(stream)))
+        return out.value
 
     def gpe_autotune(self, psi, beta: float, tau: float, nsteps: int = 3, stream=None):
         """split_step_gpe_autotune: the kernel variant timed on GPE steps (on a copy of psi)."""

@@ -7,8 +7,10 @@ element by element over every point.
   exp(-i lambda t) of a Hermite eigenfunction (section 3), and the seeded
   datum against the oracle's literal steps;
 * Gross-Pitaevskii, n = 192, beta = 100, tau = 1e-3: two steps against the
-  oracle's Strang steps, 500 F16x6 steps against 500 FP64 GPU steps (the
-  FP64 path itself checked against the oracle at this size), norm drift;
+  oracle's Strang steps (and the weighted norm taken in the last product's
+  epilogue against the oracle's), 500 F16x6 steps against 500 FP64 GPU
+  steps (the FP64 path itself checked against the oracle at this size),
+  norm drift;
 * the 64 uneven batched problems, 3 steps, every problem against the
   oracle's application of E(3 tau).
 
@@ -141,11 +143,13 @@ def test_gpe_n192_against_oracle_and_fp64(env, orc):
 
     p16 = mm.HermitePlan(ctx, [m] * 3, prec="f16x6")
     f16 = to_gpu(torch, psi0.astype(np.complex64), torch.complex64)
-    p16.gpe_step(f16, beta, tau, 2)
+    nrm16 = p16.gpe_step_norm2(f16, beta, tau, 2)  # the weighted norm from the last product's epilogue
     err16 = rel(f16.cpu().numpy(), ref2, w3)
-    print(f"GPE n=192 2 steps vs oracle: fp64 {err64:.3e}, f16x6 {err16:.3e}")
+    enrm = abs(nrm16 / np.sum(np.abs(ref2) ** 2 * w3) - 1)
+    print(f"GPE n=192 2 steps vs oracle: fp64 {err64:.3e}, f16x6 {err16:.3e}; epilogue norm {enrm:.3e}")
     assert err64 <= 1e-12  # measured 4.7e-15
     assert err16 <= 2e-7  # measured 9.2e-8
+    assert enrm <= 2e-7
 
     p64.gpe_step(f64, beta, tau, 498)
     p16.gpe_step(f16, beta, tau, 498)

@@ -734,6 +734,58 @@ def test_graph_replay_matches_plain_launches(env):
     assert n1 - n0 == 2 * (2 + 3 * 3 + 1)  # max + split, 3 sweeps x 3 products, merge; counted per replay
 
 
+@pytest.mark.parametrize("dims", [(16, 16, 16), (20, 24, 40)])
+def test_gpe_norm_in_epilogue(env, orc, dims):
+    """split_step_gpe_norm2: the weighted norm sum |psi|^2 W1 W2 W3 taken in
+    the last product's epilogue (F16X6, CTA pair) against the same quadrature
+    of the oracle's Strang steps, against mm_norm2 of the returned state, and
+    the state itself bit for bit against split_step_gpe.  Sizes padded in
+    every direction (20, 24, 40 -> 32, 32, 48) check the weights' index
+    decomposition; the one-SM variant takes the unfused form (one more
+    launch: the norm pass)."""
+    mm, ctx, torch = env
+    beta, tau, steps = 100.0, 1e-3, 5
+    plan = mm.HermitePlan(ctx, list(dims), prec="f16x6")
+    grids = [orc.gauss_hermite(m) for m in dims]
+    w3 = np.einsum("k,j,i->kji", grids[2][2], grids[1][2], grids[0][2])
+    psi0 = inputs.gpe_psi0_dims([g[0] for g in grids], [g[2] for g in grids], seed=4).astype(np.complex64)
+    cubic = len(set(dims)) == 1
+    if cubic:  # the oracle's Strang steps (cubic grids)
+        ref = orc.gpe_steps(psi0.astype(complex), grids[0][0], grids[0][2], beta, tau, steps)
+        nref = float(np.sum(np.abs(ref) ** 2 * w3))
+    a = to_gpu(torch, psi0, torch.complex64)
+    b = to_gpu(torch, psi0, torch.complex64)
+    plan.gpe_step(a, beta, tau, steps)
+    torch.cuda.synchronize()
+    l0 = mm.launch_count()
+    plan.gpe_step(to_gpu(torch, psi0, torch.complex64), beta, tau, steps)
+    torch.cuda.synchronize()
+    l1 = mm.launch_count()
+    nf = plan.gpe_step_norm2(b, beta, tau, steps)
+    l2 = mm.launch_count()
+    assert l2 - l1 == l1 - l0, "the fused norm adds no launch"
+    assert torch.equal(a, b)
+    n_pass = plan.norm2(b)
+    n_np = float(np.sum(np.abs(b.cpu().numpy().astype(np.complex128)) ** 2 * w3))  # the quadrature, written out
+    if not cubic:
+        nref = n_np
+    e_orc, e_pass, e_np = abs(nf / nref - 1), abs(nf / n_pass - 1), abs(nf / n_np - 1)
+    print(f"GPE norm in epilogue {dims}: vs oracle {e_orc:.3e}, vs mm_norm2 {e_pass:.3e}, vs numpy {e_np:.3e}")
+    assert e_orc <= 1e-6
+    assert e_pass <= 2e-7 and e_np <= 2e-7
+    # unfused form: the same result through split_step_gpe + mm_norm2
+    plan.set_config("one_sm")
+    c = to_gpu(torch, psi0, torch.complex64)
+    l3 = mm.launch_count()
+    nu = plan.gpe_step_norm2(c, beta, tau, steps)
+    l4 = mm.launch_count()
+    assert l4 - l3 >= 1
+    if cubic:
+        assert abs(nu / nref - 1) <= 1e-6
+    assert abs(nu / plan.norm2(c) - 1) <= 1e-14  # the norm pass's FP64 atomics: order of additions
+    assert plan.gpe_step_norm2(c, beta, tau, 0) == nu  # nsteps = 0: the norm of psi
+
+
 def test_device_status_clean(env):
     mm, ctx, torch = env
     ctx.status()
