@@ -881,7 +881,10 @@ mm_status mm_device_status(mm_ctx *ctx, void *stream)
     if (e != cudaSuccess) return cuda_fail(e, "error word read");
     if (word != 0) {
         cudaMemset(ctx->d_err, 0, sizeof(int));
-        return fail(mm_status(word), "a device-side bounded wait gave up (status %d)", word);
+        if (word == MM_ERR_TIMEOUT) return fail(MM_ERR_TIMEOUT, "a device-side bounded wait gave up");
+        if (word == MM_ERR_RANGE)
+            return fail(MM_ERR_RANGE, "the fixed-point state left its range (grew more than 16x within a sweep)");
+        return fail(mm_status(word), "device error word %d", word);
     }
     return MM_OK;
 }
