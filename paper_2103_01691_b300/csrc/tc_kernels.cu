@@ -1727,9 +1727,13 @@ __host__ __device__ constexpr int pair_epi_warps(int CH, int EPI, bool BATCH)
 {
     return CH == 1 && (EPI == 0 || EPI == 2 || EPI == 5) && !BATCH ? 8 : 16;
 }
+// With row tiles of 64 outside batches the MMAs of a CTA pair come from two threads in two
+// warps (the leading accumulator's from warp 1, the correction accumulator's from the warp after
+// the epilogue warps), so that neither issue stream waits for the other.
+__host__ __device__ constexpr bool pair_two_issuers(int CH, bool BATCH) { return CH == 1 && !BATCH; }
 __host__ __device__ constexpr int pair_threads(int CH, int EPI, bool BATCH)
 {
-    return 32 * (2 + pair_epi_warps(CH, EPI, BATCH));
+    return 32 * (2 + pair_epi_warps(CH, EPI, BATCH) + (pair_two_issuers(CH, BATCH) ? 1 : 0));
 }
 // k-blocks of 16 per pipeline stage: 2 with 8 epilogue warps (K-major data boxes then have
 // 64-byte rows, 64-byte swizzled: half as many row requests per byte as 32-byte rows; MN-major
@@ -1784,6 +1788,10 @@ __global__ void __launch_bounds__(pair_threads(CH, EPI, BATCH && !CHAIN), 1)
     // Chained launches keep the single launch's warps and stages.
     static_assert(!CHAIN || (BATCH && EPI == 0), "a chain is a batched launch of plain products");
     constexpr bool BCFG = BATCH && !CHAIN;  // the batched launches' warp and stage configuration
+    // the second MMA issuer (correction accumulator) and whether it issues (NP > 1); with one
+    // piece it has nothing to issue and stays idle
+    constexpr int kIssuer2 = pair_two_issuers(CH, BCFG) ? 2 + pair_epi_warps(CH, EPI, BCFG) : -1;
+    constexpr bool kTwo = kIssuer2 >= 0 && NP > 1;
     const int64_t items = BATCH ? total : a.pairs;
     constexpr int kSt = pair_stages(CH, EPI, BCFG);
     constexpr int KB = pair_kb_per_stage(CH, EPI, BCFG);  // k-blocks per stage
@@ -1796,7 +1804,7 @@ __global__ void __launch_bounds__(pair_threads(CH, EPI, BATCH && !CHAIN), 1)
     uint64_t *tmem_empty = accf + 2;       // [2]: accumulator set b has been drained
     uint32_t *tmem_slot = reinterpret_cast<uint32_t *>(tmem_empty + 2);
     volatile int *abort_flag = reinterpret_cast<volatile int *>(tmem_slot + 1);
-    uint64_t *mma_fin = reinterpret_cast<uint64_t *>(tmem_slot + 2);  // abort: the leader's MMAs have completed
+    uint64_t *mma_fin = reinterpret_cast<uint64_t *>(tmem_slot + 2);  // [2] abort: an issuer's MMAs have completed
 
     const int warp = threadIdx.x / 32, lane = threadIdx.x % 32;
     const int rank = int(blockIdx.x & 1);
@@ -1809,14 +1817,15 @@ __global__ void __launch_bounds__(pair_threads(CH, EPI, BATCH && !CHAIN), 1)
     if (threadIdx.x == 0) {
         for (int s = 0; s < kSt; ++s) {
             mbar_init(&full[s], 1);   // the leader's producer (expecting both CTAs' bytes)
-            mbar_init(&empty[s], 1);  // the leader's commit
+            mbar_init(&empty[s], kTwo ? 2 : 1);  // the leader's commits (one per issuer)
         }
         for (int b = 0; b < 2; ++b) {
-            mbar_init(&accf[b], 1);
+            mbar_init(&accf[b], kTwo ? 2 : 1);
             // this CTA's epilogue warps, and in the leader the peer's relay
             mbar_init(&tmem_empty[b], pair_epi_warps(CH, EPI, BCFG) + (rank == 0 ? 1 : 0));
         }
         mbar_init(mma_fin, 1);
+        mbar_init(mma_fin + 1, 1);
         *abort_flag = 0;
         mbar_fence_init();
         if (!BATCH) {
@@ -1941,8 +1950,8 @@ __global__ void __launch_bounds__(pair_threads(CH, EPI, BATCH && !CHAIN), 1)
             }
         }
         __syncwarp();  // the role's other lanes wait for it: the warp meets the block barrier converged
-    } else if (warp == 1) {
-        if (lane == 0 && rank == 1) {
+    } else if (warp == 1 || warp == kIssuer2) {
+        if (lane == 0 && rank == 1 && warp == 1) {
             // ---------------- relay (peer only) ----------------
             // One cluster-scope arrival on the leader's barrier once all of this
             // CTA's epilogue warps have drained an accumulator set (their own
@@ -1957,12 +1966,17 @@ __global__ void __launch_bounds__(pair_threads(CH, EPI, BATCH && !CHAIN), 1)
                 mbar_arrive_cluster(tmem_empty_lead + uint32_t(b) * 8u);
             }
         }
-        if (lane == 0 && rank == 0) {
-            // ---------------- MMA issuer (leader only) ----------------
+        if (lane == 0 && rank == 0 && (warp == 1 || kTwo)) {
+            // ---------------- MMA issuers (leader only) ----------------
             // The operand descriptors of stage 0 are built once; stage s adds s stage_bytes / 16 to
             // their start-address field (bits 0..13, wide enough for every shared-memory address of
-            // the CTA).  This thread shares its SM sub-partition with four busy epilogue warps, so
-            // few instructions per MMA keep the tensor pipe fed.
+            // the CTA).  Each issuing thread shares its SM sub-partition with busy epilogue warps,
+            // whose shared-memory instructions delay its MMAs, so few instructions per MMA keep the
+            // tensor pipe fed.  With two issuers (kTwo), warp 1 issues the leading product's MMAs
+            // and warp kIssuer2 the corrections': each accumulator still receives its MMAs from one
+            // thread in the same order, both commit every stage and every item (the barriers
+            // count two), and the two streams interleave in the tensor pipe.
+            const int lead_part = !kTwo ? -1 : (warp == 1 ? 1 : 0);  // -1: all terms
             auto idesc_for = [&](bool km) {
                 return FX ? idesc_f16_f32(2 * kTileM, 2 * a.it, !km, false) : idesc_bf16_f32(2 * kTileM, 2 * a.it, !km, false);
             };
@@ -2031,6 +2045,7 @@ __global__ void __launch_bounds__(pair_threads(CH, EPI, BATCH && !CHAIN), 1)
                         const uint32_t first = kb + j == kb_lo ? 0u : 1u;  // each accumulator starts at its first product
 #pragma unroll
                         for (int t = 0; t < num_terms(NP); ++t) {
+                            if (lead_part >= 0 && (t == 0) != (lead_part == 1)) continue;
                             const int pa = term_a(t), pb = term_b(t);
                             const uint32_t dcol = (NP > 1 && (pa != 0 || pb != 0)) ? d1 : d0;
                             umma_f16_pair(dcol, ad[0][pb] + ao, bdesc[0][pa] + bo, id, t <= 1 ? first : 1u);
@@ -2048,8 +2063,9 @@ __global__ void __launch_bounds__(pair_threads(CH, EPI, BATCH && !CHAIN), 1)
             if (*abort_flag) {
                 // every MMA this thread issued (into both CTAs' tensor memory) completes before
                 // either CTA frees it
-                umma_commit_pair_mc(mma_fin, 0x1);
-                mbar_wait(mma_fin, 0u, nullptr, 0, a.wait_limit);
+                uint64_t *fin = mma_fin + (warp == 1 ? 0 : 1);
+                umma_commit_pair_mc(fin, 0x1);
+                mbar_wait(fin, 0u, nullptr, 0, a.wait_limit);
             }
         }
         __syncwarp();
