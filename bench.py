@@ -39,7 +39,7 @@ WORKLOAD = "free Schroedinger n=256^3 complex64, Dirichlet FD, E=expm(i*1e-4*A),
 # summarised in this profile, which records them together with the hash of the
 # kernel sources they were measured on (a line "bench-traffic: ...").
 TRAFFIC_PROFILE = os.path.join(ROOT, "profiles", "tc_pair_kernel_f16x6_n256.md")
-KERNEL_SOURCES = ("tc_kernels.cu", "tc_ptx.cuh", "internal.h", "mumode_api.cu")
+KERNEL_SOURCES = ("tc_kernels.cu", "tc_ptx.cuh", "internal.h")  # the kernel and its launch set-up
 
 
 def kernel_source_sha() -> str:
