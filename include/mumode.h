@@ -332,8 +332,11 @@ mm_status mm_plan_autotune(mm_plan *plan, const void *u_dev, int64_t nsteps, voi
 /* The plan's kernel variant and mode order (order_out: d ints, or NULL). */
 mm_status mm_plan_get_config(const mm_plan *plan, int *variant, int *order_out);
 /* Set them (order NULL keeps it; a Hermite plan's order cannot change).
- * Drops the plan's captured graphs.  Errors: MM_ERR_INVALID_ARG,
- * MM_ERR_UNSUPPORTED. */
+ * Variants 0..2 as for mm_plan_autotune; 3 = every product of a
+ * mumode_step call in one persistent launch of the CTA-pair kernel (F16X6
+ * Tucker plans with row tiles of at most 64; other plans and calls launch
+ * per product).  The autotuner does not try 3.  Drops the plan's captured
+ * graphs.  Errors: MM_ERR_INVALID_ARG, MM_ERR_UNSUPPORTED. */
 mm_status mm_plan_set_config(mm_plan *plan, int variant, const int *order);
 
 /* CUDA graphs (on by default; not from the paper).  With graphs on, the

@@ -714,7 +714,8 @@ mm_status autotune_with(mm_plan *p, const void *u_dev, int64_t nsteps, void *str
     if (p->tc && p->tf32) variants = {mm::kTcOneSM};  // TF32 pieces run on the one-SM kernel only
     else if (p->tc) variants = {mm::kTcPair64, mm::kTcPair128, mm::kTcOneSM};
     else variants = {int(p->variant)};
-    if (p->tc && p->fixed && orders_too && !p->hermite) variants.push_back(mm::kTcChain);  // Tucker steps only
+    // kTcChain is opt-in (mm_plan_set_config): slower than one launch per product at every size
+    // measured, and a profiler's fixed cost per launch would make it look faster
     std::vector<std::vector<int>> orders;
     std::vector<int> ord(p->order, p->order + p->d);
     if (orders_too && !p->hermite && p->d <= 4) {
