@@ -441,6 +441,10 @@ def main():
                          "tensor_alg_frac": achieved / tc_peak,
                          "tensor_peak_source": f"bf16 burst (f16 same rate), {peak_src}",
                          "issued_tflops": issued, "issued_frac": issued / tc_peak,
+                         # the launches run back to back for the whole timed region under the power
+                         # cap, the condition of the sustained GEMM measurement
+                         "issued_frac_sustained": issued / tc_peak_sust,
+                         "tensor_peak_sustained_tflops": tc_peak_sust,
                          "issued_flop_per_step": issued_per_step,
                          # DRAM bytes the launch actually moves (ncu, split state) over its time
                          "hbm_frac_traffic": (traffic / kern_avg_s / 1e9 / hbm_peak if traffic else None),
