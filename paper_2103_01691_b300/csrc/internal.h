@@ -244,11 +244,17 @@ size_t tc_pair_record_align();
 cudaError_t tc_pair_record_build(const TcState &si, const TcState &so, int mu, const TcMatrix &M, mm_prec prec,
                                  const void *in_pieces, void *out_pieces, const TcScales &sc, void *rec, bool *kmajor,
                                  int64_t *items, int chain_pos = -1);
+// The dependencies of a chain's records (positions 0 .. nprod - 1 of sweeps over d directions):
+// slab-group completion targets, row-tile-major items in the last direction, the product each
+// must wait for before its first load, and s_in_max[k], the maximum word whose grid exponent is
+// product k's input scale (null: its s_in word).
+cudaError_t tc_pair_chain_plan(void *host_recs, int nprod, int d, const unsigned *const *s_in_max);
+constexpr int kChainCounters = 33;  // words per product: its total, then its 32 slab groups
 // One persistent launch over a chain of products (records built with chain positions 0, 1, ..,
-// nprod - 1, their first items set in order); `done`: nprod counters and `tally`: tc_chain_ctas()
-// x nprod words, all zero at the launch.
+// nprod - 1, their first items set in order, then tc_pair_chain_plan); `done`: nprod counters and
+// `gcnt`: nprod x 32 slab-group counters, all zero at the launch.
 cudaError_t tc_pair_chain_launch(const void *host_recs, const void *dev_recs, int nprod, unsigned *done,
-                                 unsigned *tally, int *d_err, cudaStream_t s);
+                                 unsigned *gcnt, int *d_err, cudaStream_t s);
 int tc_chain_ctas();  // the most CTAs a chained launch uses (the SM count)
 void tc_pair_record_set_begin(void *rec, int64_t begin);
 bool tc_pair_batch_compatible(const void *host_recs, int nprob);  // same row tile size in all records

@@ -54,7 +54,9 @@ struct mm_plan {
     int chain_nprod = 0;
     std::vector<uint8_t> chain_host;
     void *chain_dev = nullptr;
-    unsigned *chain_done = nullptr;  // nprod completion counters, then tc_chain_ctas() x nprod tally words
+    // nprod completion counters, nprod x 32 slab-group counters, then nprod maximum words (one per
+    // product: a chain's products never share a maximum word)
+    unsigned *chain_done = nullptr;
     // fixed-point state scale words (device): scale[d], max[2][d], one work word
     float *d_scale = nullptr;
     unsigned *d_max = nullptr;
@@ -65,7 +67,7 @@ struct mm_plan {
     mm::TcMatrix Etc[mm::kMaxDims] = {};  // tensor cores
     // workspace
     mm::TcState st;
-    void *work[2] = {nullptr, nullptr};  // TC: piece buffers; SIMT: work[0] state-sized
+    void *work[3] = {nullptr, nullptr, nullptr};  // TC: piece buffers (the third for chains); SIMT: work[0] state-sized
     size_t work_bytes = 0;
     void *staging = nullptr;  // device copy for host stepping
     // Hermite data
@@ -334,35 +336,57 @@ bool chain_prepare(mm_plan *p, int64_t nsteps)
     const size_t rb = mm::tc_pair_record_bytes(), al = mm::tc_pair_record_align();
     std::vector<uint8_t> host(rb * size_t(nprod) + al, 0);
     uint8_t *base = reinterpret_cast<uint8_t *>((reinterpret_cast<uintptr_t>(host.data()) + al - 1) / al * al);
+    // Products overlap in a chain, so the state rotates through three buffers (product k reads
+    // buffer k mod 3 and writes k + 1 mod 3, which product k - 2 read) and each product has a
+    // maximum word of its own: product k's output scale comes from product k - d's maximum (sweep
+    // 0: the bounds the split writes), its input scale from product k - 1's.
+    if (!p->work[2]) {
+        if (cudaMalloc(&p->work[2], p->work_bytes) != cudaSuccess) {
+            p->work[2] = nullptr;
+            return false;
+        }
+        if (cudaMemset(p->work[2], 0, p->work_bytes) != cudaSuccess) return false;
+    }
+    const size_t counters = size_t(nprod) * (mm::kChainCounters + 1);
+    unsigned *done = nullptr;
+    if (cudaMalloc(&done, sizeof(unsigned) * counters) != cudaSuccess) return false;
+    unsigned *maxw = done + size_t(nprod) * mm::kChainCounters;
+    std::vector<const unsigned *> s_in_max(size_t(nprod), nullptr);
+    std::vector<const unsigned *> max_prev(size_t(nprod), nullptr);
     int64_t begin = 0;
     for (int64_t k = 0; k < nsteps; ++k)
         for (int q = 0; q < d; ++q) {
-            const int pos = int(k * d + q), cur = pos % 2, mu = p->order[q];
-            const int t = int(k % 3), par = int(k & 1);  // as tc_sweep with p->sweep = k
+            const int pos = int(k * d + q), mu = p->order[q];
+            const int par = int(k & 1);  // the state scale words as tc_sweep with p->sweep = k
             mm::TcScales sc;
             sc.s_in = p->d_scale + par * d + q;
             sc.s_out = (q + 1 < d) ? p->d_scale + par * d + q + 1 : p->d_scale + (1 - par) * d;
-            sc.max_prev = p->d_max + ((t + 2) % 3) * d + q;
-            sc.max_cur = p->d_max + t * d + q;
-            sc.zero_next = p->d_max + ((t + 1) % 3) * d + q;
+            sc.max_prev = pos >= d ? maxw + (pos - d) : p->d_max + 2 * d + q;
+            sc.max_cur = maxw + pos;
+            sc.zero_next = nullptr;
+            max_prev[size_t(pos)] = sc.max_prev;
+            s_in_max[size_t(pos)] = pos > 0 ? max_prev[size_t(pos - 1)] : nullptr;
             bool km = false;
             int64_t items = 0;
             void *rec = base + rb * size_t(pos);
-            if (mm::tc_pair_record_build(p->st, p->st, mu, p->Etc[mu - 1], p->prec, p->work[cur], p->work[1 - cur], sc,
-                                         rec, &km, &items, pos) != cudaSuccess)
+            if (mm::tc_pair_record_build(p->st, p->st, mu, p->Etc[mu - 1], p->prec, p->work[pos % 3],
+                                         p->work[(pos + 1) % 3], sc, rec, &km, &items, pos) != cudaSuccess) {
+                cudaFree(done);
                 return false;
+            }
             mm::tc_pair_record_set_begin(rec, begin);
             begin += items;
         }
-    if (!mm::tc_pair_batch_compatible(base, nprod)) return false;
+    if (!mm::tc_pair_batch_compatible(base, nprod) ||
+        mm::tc_pair_chain_plan(base, nprod, d, s_in_max.data()) != cudaSuccess) {
+        cudaFree(done);
+        return false;
+    }
     void *dev = nullptr;
-    unsigned *done = nullptr;
-    if (cudaMalloc(&dev, rb * size_t(nprod)) != cudaSuccess) return false;
-    const size_t counters = size_t(nprod) * (1 + size_t(mm::tc_chain_ctas()));
-    if (cudaMalloc(&done, sizeof(unsigned) * counters) != cudaSuccess ||
+    if (cudaMalloc(&dev, rb * size_t(nprod)) != cudaSuccess ||
         cudaMemcpy(dev, base, rb * size_t(nprod), cudaMemcpyHostToDevice) != cudaSuccess) {
-        cudaFree(dev);
-        if (done) cudaFree(done);
+        if (dev) cudaFree(dev);
+        cudaFree(done);
         return false;
     }
     drop_graphs(p);
@@ -380,7 +404,7 @@ bool chain_prepare(mm_plan *p, int64_t nsteps)
 // The products of a chained call (chain_prepare for nsteps has succeeded), between tc_begin and tc_end.
 mm_status chain_run(mm_plan *p, int &cur, cudaStream_t s)
 {
-    const size_t counters = size_t(p->chain_nprod) * (1 + size_t(mm::tc_chain_ctas()));
+    const size_t counters = size_t(p->chain_nprod) * (mm::kChainCounters + 1);
     cudaError_t e = cudaMemsetAsync(p->chain_done, 0, sizeof(unsigned) * counters, s);
     if (e != cudaSuccess) return cuda_fail(e, "chain counters");
     cudaEvent_t ev0 = timing_event(p->ctx, true);
@@ -390,7 +414,7 @@ mm_status chain_run(mm_plan *p, int &cur, cudaStream_t s)
     if (ev0) cudaEventRecord(timing_event(p->ctx, false, p->chain_nprod), s);
     if (e != cudaSuccess) return cuda_fail(e, "chained tensor-core launch");
     p->sweep += p->chain_steps;
-    cur = (p->chain_nprod % 2 == 0) ? cur : 1 - cur;
+    cur = int(p->chain_nprod % 3);  // product k wrote buffer k + 1 mod 3, starting from buffer 0
     return MM_OK;
 }
 
@@ -1178,6 +1202,7 @@ void mm_plan_destroy(mm_plan *p)
     free_prop(p, 1);
     if (p->work[0]) cudaFree(p->work[0]);
     if (p->work[1]) cudaFree(p->work[1]);
+    if (p->work[2]) cudaFree(p->work[2]);
     if (p->staging) cudaFree(p->staging);
     if (p->d_scale) cudaFree(p->d_scale);
     if (p->d_max) cudaFree(p->d_max);

@@ -997,9 +997,8 @@ struct TcArgs {
     const float2 *mid_in;
     // chained launches (one launch over a sequence of products): completion counters, one per
     // product, and the count that marks a product complete (one signal per CTA)
-    unsigned *done;
-    unsigned done_target;
-    unsigned *tally;        // [CTA][product]: the CTA's epilogue warps that have stored the product
+    unsigned *done;         // [product]: (CTA, item) signals received
+    unsigned *gcnt;         // [product][kChainGroups]: signals received per slab group of the output
     // fixed-point mode
     const float *rho;
     TcScales sc;
@@ -1013,13 +1012,83 @@ __host__ __device__ constexpr int term_b(int t) { return t == 1 ? 1 : (t == 3 ? 
 // One problem of a batched CTA-pair launch: its tensor maps (read by TMA from
 // global memory; CUtensorMap carries the alignment TMA needs), its kernel
 // arguments and its first work item.
+// Chained launches track their dependencies per slab group: groups of kChainSlabs consecutive
+// values of the slowest index, at most kChainGroups of them (directions up to 512).
+constexpr int kChainSlabs = 16, kChainGroups = 32;
+
 struct TcPairProblem {
     CUtensorMap mapX, mapE, mapY;
     TcArgs a;
     int64_t pairs_begin;
     int km;    // chained launches: direction 1 (K-major data) or not
     int prod;  // chained launches: position of the product in the chain
+    // chained launches: what completes this product's output, slab group by slab group (one
+    // signal per CTA and item for each group its points or rows touch) and as a whole (one signal
+    // per CTA and item)
+    unsigned g_expect[kChainGroups];
+    unsigned tot_target;
+    int64_t slab_div;    // direction < d: "right" units per slab (the slowest index)
+    int last_dir;        // direction d: the output rows are the slabs
+    int hmajor;          // items in row-tile-major order (direction d, so that slabs complete in order)
+    int wait_prod;       // product complete before any load of this one (-1: none)
+    const unsigned *s_in_max;  // the word whose grid exponent is the input scale (null: read a.sc.s_in)
 };
+
+// Pair tile and row tile of item Pl of a problem: point-tile-major (row tile fastest), or, for
+// the chained launches' last direction, row-tile-major.
+__host__ __device__ __forceinline__ void chain_item(const TcArgs &A, bool hmajor, int64_t Pl, int64_t &pair, int &h)
+{
+    if (hmajor) {
+        const int64_t np = A.pairs / A.ni;
+        h = int(Pl / np);
+        pair = Pl % np;
+    } else {
+        pair = Pl / A.ni;
+        h = int(Pl % A.ni);
+    }
+}
+
+// Slab groups [g_lo, g_hi] of the data one CTA of an item reads (reads = true) or writes; empty
+// (g_lo > g_hi) when the CTA's tile holds no points.  Direction < d: the slabs of the CTA's points;
+// direction d: its k-blocks (read) or its output rows (written).
+__host__ __device__ __forceinline__ void chain_groups(const TcPairProblem &R, int64_t pair, int h, int rank,
+                                                      bool reads, int &g_lo, int &g_hi)
+{
+    const TcArgs &A = R.a;
+    int64_t s_lo, s_hi;
+    if (R.last_dir) {
+        if (reads) {
+            s_lo = int64_t(A.kb_lo[h]) * 16;
+            s_hi = int64_t(A.kb_hi[h]) * 16 - 1;
+        } else {
+            s_lo = int64_t(h) * A.it;
+            s_hi = s_lo + A.it - 1;
+            if (s_hi > A.mp - 1) s_hi = A.mp - 1;
+        }
+    } else {
+        const int64_t tile = pair * 2 + rank;
+        int64_t u_lo, u_hi;  // "right" units of the tile's points
+        if (R.km) {
+            u_lo = tile * 128;
+            u_hi = u_lo + 127;
+            if (u_hi > A.right - 1) u_hi = A.right - 1;
+        } else {
+            const int64_t a0 = 2 * tile, a1 = a0 + 1;
+            u_lo = a0 / A.aps;
+            u_hi = a1 / A.aps;
+            if (u_hi > A.right - 1) u_hi = A.right - 1;
+        }
+        if (u_lo > u_hi) {
+            g_lo = 1;
+            g_hi = 0;
+            return;
+        }
+        s_lo = u_lo / R.slab_div;
+        s_hi = u_hi / R.slab_div;
+    }
+    g_lo = int(s_lo / kChainSlabs);
+    g_hi = int(s_hi / kChainSlabs);
+}
 
 // The problem of work item P (records sorted by pairs_begin, the first at 0).
 __device__ __forceinline__ const TcPairProblem &pair_problem(const TcPairProblem *many, int nprob, int64_t P)
@@ -1519,15 +1588,15 @@ constexpr int kStagingPerWarp = 3 * kStageBoxBytes;
 // Parts of a box outside the padded tensor are clipped by the TMA unit; boxes wholly outside
 // are not issued.
 template <int NP, bool KMAJOR, int EPI, bool FX>
-__device__ __forceinline__ void epi_frag_store(const TcArgs &a, const CUtensorMap *mapY, uint8_t *stg,
+__device__ __forceinline__ int epi_frag_store(const TcArgs &a, const CUtensorMap *mapY, uint8_t *stg,
                                                float (&vr)[2][8], float (&vi)[2][8], int64_t tile, int h,
                                                int quarter, int lane, int grp, int nchunks, float s_in,
                                                float inv_out, float lim, float &local_max, bool &range_ok,
                                                float2 phl, double wpl, double &nacc)
 {
-    if (grp >= nchunks) return;
+    if (grp >= nchunks) return 0;
     const int i0 = h * a.it + grp * 16;
-    if (i0 >= a.mp) return;
+    if (i0 >= a.mp) return 0;
     const int t4 = lane / 4, tc = lane % 4;
     // the warp's box origin and the validity of this thread's four points (hh, s)
     bool box_ok, valid[2][2];
@@ -1716,6 +1785,7 @@ __device__ __forceinline__ void epi_frag_store(const TcArgs &a, const CUtensorMa
             bulk_commit();
         }
     }
+    return box_ok ? 2 : 0;  // bulk groups committed (by lane 0)
 }
 
 // Epilogue warps of the pair kernel: 8 (two per tensor-memory lane quarter, two chunks of 16
@@ -1775,7 +1845,7 @@ __host__ __device__ constexpr int pair_staging_bytes(int CH, int EPI, bool BATCH
 // the peer's warps arrive on their own barrier, which one thread of the
 // peer relays to the leader's.
 template <int NP, bool KMAJOR, int EPI, bool FX, int CH, bool BATCH, bool CHAIN = false>
-__global__ void __launch_bounds__(pair_threads(CH, EPI, BATCH && !CHAIN), 1)
+__global__ void __launch_bounds__(pair_threads(CH, EPI, BATCH && !CHAIN) + (CHAIN ? 32 : 0), 1)
     tc_pair_kernel(const __grid_constant__ CUtensorMap mapX, const __grid_constant__ CUtensorMap mapE,
                    const __grid_constant__ CUtensorMap mapY, TcArgs a, const TcPairProblem *__restrict__ many,
                    int nprob, int64_t total)
@@ -1792,6 +1862,8 @@ __global__ void __launch_bounds__(pair_threads(CH, EPI, BATCH && !CHAIN), 1)
     // piece it has nothing to issue and stays idle
     constexpr int kIssuer2 = pair_two_issuers(CH, BCFG) ? 2 + pair_epi_warps(CH, EPI, BCFG) : -1;
     constexpr bool kTwo = kIssuer2 >= 0 && NP > 1;
+    // CHAIN: the warp that publishes the items this CTA has stored
+    constexpr int kSignal = CHAIN ? pair_threads(CH, EPI, BCFG) / 32 : -1;
     const int64_t items = BATCH ? total : a.pairs;
     constexpr int kSt = pair_stages(CH, EPI, BCFG);
     constexpr int KB = pair_kb_per_stage(CH, EPI, BCFG);  // k-blocks per stage
@@ -1805,6 +1877,7 @@ __global__ void __launch_bounds__(pair_threads(CH, EPI, BATCH && !CHAIN), 1)
     uint32_t *tmem_slot = reinterpret_cast<uint32_t *>(tmem_empty + 2);
     volatile int *abort_flag = reinterpret_cast<volatile int *>(tmem_slot + 1);
     uint64_t *mma_fin = reinterpret_cast<uint64_t *>(tmem_slot + 2);  // [2] abort: an issuer's MMAs have completed
+    uint64_t *item_done = mma_fin + 2;  // [8] CHAIN: this CTA's epilogue warps have stored item l (l mod 8)
 
     const int warp = threadIdx.x / 32, lane = threadIdx.x % 32;
     const int rank = int(blockIdx.x & 1);
@@ -1826,6 +1899,8 @@ __global__ void __launch_bounds__(pair_threads(CH, EPI, BATCH && !CHAIN), 1)
         }
         mbar_init(mma_fin, 1);
         mbar_init(mma_fin + 1, 1);
+        if (CHAIN)
+            for (int q = 0; q < 8; ++q) mbar_init(&item_done[q], pair_epi_warps(CH, EPI, BCFG));
         *abort_flag = 0;
         mbar_fence_init();
         if (!BATCH) {
@@ -1868,7 +1943,8 @@ __global__ void __launch_bounds__(pair_threads(CH, EPI, BATCH && !CHAIN), 1)
             int s = 0;
             uint32_t ph = 0;  // ring position
             int64_t g = 0;    // stages reached over the launch
-            int ready = 0;    // CHAIN: products up to this one may be loaded
+            int ready = 0;         // CHAIN: the product whose loads have begun on this CTA
+            uint32_t gready = 0;   // CHAIN: slab groups of the previous product known complete
             int rec_at = 0;   // BATCH: the record of the previous item
             const int e_rows = 3 * half / 4;  // 128-byte rows of one block triple
             for (int64_t P = cid; P < items && !*abort_flag; P += nclusters) {
@@ -1876,26 +1952,50 @@ __global__ void __launch_bounds__(pair_threads(CH, EPI, BATCH && !CHAIN), 1)
                 const TcArgs &A = BATCH ? pr->a : a;
                 const CUtensorMap *mx = BATCH ? &pr->mapX : &mapX, *me = BATCH ? &pr->mapE : &mapE;
                 const int64_t Pl = BATCH ? P - pr->pairs_begin : P;
-                const int64_t tile = (Pl / A.ni) * 2 + rank;
-                const int h = int(Pl % A.ni);
+                int64_t pairi;
+                int h;
+                chain_item(A, CHAIN && pr->hmajor, Pl, pairi, h);
+                const int64_t tile = pairi * 2 + rank;
                 const bool km = CHAIN ? pr->km != 0 : KMAJOR;
-                if (CHAIN && pr->prod > ready) {
-                    // the product's tensor maps are fetched while the wait below runs, and the next
-                    // product's as well
-                    tma_prefetch_desc(mx);
-                    tma_prefetch_desc(me);
-                    if (pr->prod + 1 < nprob) {
-                        tma_prefetch_desc(&pr[1].mapX);
-                        tma_prefetch_desc(&pr[1].mapE);
+                if (CHAIN) {
+                    bool ok = true, waited = false;
+                    if (pr->prod != ready || P == cid) {
+                        // a new product: its tensor maps are fetched while the waits below run, and
+                        // the next product's as well; the product two back (whose input buffer this
+                        // one overwrites, and whose maximum sets this one's scale) must be complete
+                        tma_prefetch_desc(mx);
+                        tma_prefetch_desc(me);
+                        if (pr->prod + 1 < nprob) {
+                            tma_prefetch_desc(&pr[1].mapX);
+                            tma_prefetch_desc(&pr[1].mapE);
+                        }
+                        if (pr->wait_prod >= 0) {
+                            ok = counter_wait(a.done + pr->wait_prod, many[pr->wait_prod].tot_target, a.err,
+                                              MM_ERR_TIMEOUT, a.wait_limit);
+                            waited = true;
+                        }
+                        ready = pr->prod;
+                        gready = 0;
                     }
-                    // the previous product's output is this one's input: wait until every CTA has
-                    // signalled it stored (bounded), then load through TMA
-                    if (!counter_wait(a.done + (pr->prod - 1), a.done_target, a.err, MM_ERR_TIMEOUT, a.wait_limit)) {
+                    if (ok && pr->prod > 0) {
+                        // the previous product's output is this one's input: every slab group this
+                        // CTA reads must be complete (bounded waits), then the loads go through TMA
+                        int g_lo, g_hi;
+                        chain_groups(*pr, pairi, h, rank, true, g_lo, g_hi);
+                        const TcPairProblem &Q = pr[-1];
+                        const unsigned *cnt = a.gcnt + int64_t(pr->prod - 1) * kChainGroups;
+                        for (int gq = g_lo; gq <= g_hi && ok; ++gq) {
+                            if (gready & (1u << gq)) continue;
+                            ok = counter_wait(cnt + gq, Q.g_expect[gq], a.err, MM_ERR_TIMEOUT, a.wait_limit);
+                            gready |= 1u << gq;
+                            waited = true;
+                        }
+                    }
+                    if (!ok) {
                         *abort_flag = 1;
                         break;
                     }
-                    fence_proxy_async_global();
-                    ready = pr->prod;
+                    if (waited) fence_proxy_async_global();  // the acquired data, read by TMA
                 }
                 // MN-major: the two 64-point atoms of the tile (slab row, first point), past the end zero fill
                 int ac_l[2] = {0, 0}, ac_r[2] = {0, 0};
@@ -1950,6 +2050,34 @@ __global__ void __launch_bounds__(pair_threads(CH, EPI, BATCH && !CHAIN), 1)
             }
         }
         __syncwarp();  // the role's other lanes wait for it: the warp meets the block barrier converged
+    } else if (CHAIN && warp == kSignal) {
+        if (lane == 0) {
+            // ---------------- signaller (CHAIN) ----------------
+            // Items in the cluster's order: once the CTA's epilogue warps have all reported item l
+            // stored, one release fence at GPU scope, then one count for every slab group this
+            // CTA's part of the item wrote and one for the product's total (relaxed adds after the
+            // fence).  The fence waits here, off the epilogue warps' path.
+            uint32_t lt = 0;
+            int rec_at = 0;
+            for (int64_t P = cid; P < items; P += nclusters, ++lt) {
+                const TcPairProblem *pr = &pair_problem_next(many, nprob, P, rec_at);
+                int64_t pairi;
+                int h;
+                chain_item(pr->a, pr->hmajor != 0, P - pr->pairs_begin, pairi, h);
+                if (*abort_flag ||
+                    !mbar_wait(&item_done[lt % 8u], (lt / 8u) & 1u, a.err, MM_ERR_TIMEOUT, a.wait_limit)) {
+                    *abort_flag = 1;
+                    break;
+                }
+                fence_acq_rel_gpu();
+                int g_lo, g_hi;
+                chain_groups(*pr, pairi, h, rank, false, g_lo, g_hi);
+                unsigned *cnt = a.gcnt + int64_t(pr->prod) * kChainGroups;
+                for (int gq = g_lo; gq <= g_hi; ++gq) red_relaxed_gpu_add(cnt + gq, 1u);
+                red_relaxed_gpu_add(a.done + pr->prod, 1u);
+            }
+        }
+        __syncwarp();
     } else if (warp == 1 || warp == kIssuer2) {
         if (lane == 0 && rank == 1 && warp == 1) {
             // ---------------- relay (peer only) ----------------
@@ -2012,7 +2140,9 @@ __global__ void __launch_bounds__(pair_threads(CH, EPI, BATCH && !CHAIN), 1)
             for (int64_t P = cid; P < items && !*abort_flag; P += nclusters, ++lt) {
                 const TcPairProblem *pr = BATCH ? &pair_problem_next(many, nprob, P, rec_at) : nullptr;
                 const TcArgs &A = BATCH ? pr->a : a;
-                const int h = int((BATCH ? P - pr->pairs_begin : P) % A.ni);
+                int64_t pairi;
+                int h;
+                chain_item(A, CHAIN && pr->hmajor, BATCH ? P - pr->pairs_begin : P, pairi, h);
                 const bool km = CHAIN ? pr->km != 0 : KMAJOR;
                 const uint32_t id = CHAIN && !km ? idesc_mn : idesc;
                 // the item's data descriptors (CHAIN: chosen once per item, outside the MMA loop)
@@ -2085,63 +2215,56 @@ __global__ void __launch_bounds__(pair_threads(CH, EPI, BATCH && !CHAIN), 1)
         // the fixed-point scales of the problem being stored (BATCH: they change with the problem,
         // and the maximum gathered so far goes to the previous problem's word first)
         const TcArgs *cur = nullptr;
-        auto scales_for = [&](const TcArgs &A, bool first_item) {
+        auto flush_max = [&]() {
+            if (!FX || !cur) return;
+            const unsigned m = __reduce_max_sync(0xffffffffu, __float_as_uint(local_max));
+            if (lane == 0 && m) atomicMax(cur->sc.max_cur, m);
+            local_max = 0.0f;
+        };
+        // s_in_max (chains): the input scale is the grid exponent of that maximum word (the one the
+        // previous product took its output scale from), not a word the previous product writes
+        auto scales_for = [&](const TcArgs &A, bool first_item, const unsigned *s_in_max) {
             if (!FX || cur == &A) return;
-            if (cur) {
-                const unsigned m = __reduce_max_sync(0xffffffffu, __float_as_uint(local_max));
-                if (lane == 0 && m) atomicMax(cur->sc.max_cur, m);
-                local_max = 0.0f;
-            }
+            flush_max();
             cur = &A;
-            s_in = *A.sc.s_in;
+            s_in = s_in_max ? ldexpf(1.0f, grid_exponent(__uint_as_float(*s_in_max))) : *A.sc.s_in;
             es_out = grid_exponent(__uint_as_float(*A.sc.max_prev));
             inv_out = ldexpf(1.0f, -es_out);
             lim = ldexpf(16384.0f, es_out);
-            if (first_item && ew == 0 && lane == 0) {
-                *A.sc.s_out = ldexpf(1.0f, es_out);
-                // a chain clears the word the same direction's product of the next sweep accumulates
-                // into (in a single launch, the launch's prologue does)
-                if (CHAIN && A.sc.zero_next) *A.sc.zero_next = 0u;
-            }
+            if (first_item && ew == 0 && lane == 0) *A.sc.s_out = ldexpf(1.0f, es_out);
         };
-        // CHAIN: every product below `signalled` has been signalled complete by this warp.  The
-        // warp signals a product once its own stores of that product have completed and its
-        // maximum has been merged, and before it waits for anything of a later product.
-        int signalled = 0;
-        auto signal_upto = [&](int upto) {
-            if (!CHAIN || signalled >= upto) return;
-            if (FX && cur) {
-                const unsigned m = __reduce_max_sync(0xffffffffu, __float_as_uint(local_max));
-                if (lane == 0 && m) atomicMax(cur->sc.max_cur, m);
-                local_max = 0.0f;
-            }
+        // CHAIN: a warp reports an item stored (its stores complete, then an arrival on the item's
+        // barrier) after it has committed the stores of its next item, whose loads do not wait for
+        // this one (both belong to the same product), except the last item of a product on this
+        // cluster, which it reports at once, after merging its maximum.  The signalling warp
+        // publishes the counters.
+        auto signal_item = [&](const TcPairProblem *R, int64_t pairi, int hh, uint32_t l) {
+            (void)R;
+            (void)pairi;
+            (void)hh;
             if (lane == 0) {
-                bulk_wait0();
                 fence_proxy_async_global();
-                // the CTA's last warp to finish a product (its tally word counts this CTA's warps)
-                // signals it for the whole CTA
-                unsigned *tally = a.tally + int64_t(blockIdx.x) * nprob;
-                for (int q = signalled; q < upto; ++q)
-                    if (atom_add_acqrel_cta_global(tally + q, 1u) + 1u == unsigned(kGroups * 4))
-                        red_release_gpu_add(a.done + q, 1u);
+                mbarrier_arrive(&item_done[l % 8u]);
             }
             __syncwarp();
-            signalled = upto;
         };
-        if (!BATCH) scales_for(a, blockIdx.x == 0);
+        const TcPairProblem *pend_pr = nullptr;  // CHAIN: the item stored but not yet signalled
+        int64_t pend_pair = 0;
+        int pend_h = 0;
+        uint32_t pend_lt = 0;
+        if (!BATCH) scales_for(a, blockIdx.x == 0, nullptr);
         uint32_t lt = 0;
         int rec_at = 0;  // BATCH: the record of the previous item
         for (int64_t P = cid; P < items; P += nclusters, ++lt) {
             const TcPairProblem *pr = BATCH ? &pair_problem_next(many, nprob, P, rec_at) : nullptr;
             const TcArgs &A = BATCH ? pr->a : a;
             const int64_t Pl = BATCH ? P - pr->pairs_begin : P;
-            if (CHAIN) {
-                signal_upto(pr->prod);
-                if (lane == 0 && cur != &A) tma_prefetch_desc(&pr->mapY);  // fetched while the item's MMAs run
-            }
-            if (BATCH && !CHAIN) scales_for(A, Pl == 0 && rank == 0);
-            const int64_t tile = (Pl / A.ni) * 2 + rank;
-            const int h = int(Pl % A.ni);
+            if (CHAIN && lane == 0 && cur != &A) tma_prefetch_desc(&pr->mapY);  // fetched while the item's MMAs run
+            if (BATCH && !CHAIN) scales_for(A, Pl == 0 && rank == 0, nullptr);
+            int64_t pairi;
+            int h;
+            chain_item(A, CHAIN && pr->hmajor, Pl, pairi, h);
+            const int64_t tile = pairi * 2 + rank;
             const int b = int(lt % uint32_t(nsets));
             // the same decision in every lane: the warp stays converged for its collective instructions
             const bool acc_ready = __all_sync(
@@ -2149,14 +2272,15 @@ __global__ void __launch_bounds__(pair_threads(CH, EPI, BATCH && !CHAIN), 1)
             if (!acc_ready) *abort_flag = 1;
             tc_fence_after();
             if (CHAIN && acc_ready && cur != &A) {
-                // a new product: its data was loaded after the previous product completed, so the
-                // counter has reached its target; one lane acquires it (the previous products' scale
-                // words are read next), and the warp follows
+                // a new product: its loads began after the product two back had completed (the
+                // maximum words its scales come from are that product's or older); one lane
+                // acquires that counter, and the warp follows
                 bool ok = true;
-                if (lane == 0 && pr->prod > 0)
-                    ok = counter_wait(a.done + (pr->prod - 1), a.done_target, a.err, MM_ERR_TIMEOUT, a.wait_limit);
+                if (lane == 0 && pr->wait_prod >= 0)
+                    ok = counter_wait(a.done + pr->wait_prod, many[pr->wait_prod].tot_target, a.err, MM_ERR_TIMEOUT,
+                                      a.wait_limit);
                 if (!__shfl_sync(0xffffffffu, ok ? 1 : 0, 0)) *abort_flag = 1;
-                scales_for(A, Pl == 0 && rank == 0);
+                scales_for(A, Pl == 0 && rank == 0, pr->s_in_max);
             }
             // drain in the matrix-fragment order: the warp's chunks of 16 output rows
             // (grp, grp + kGroups ..), each as two 16-lane halves, leading + corrections; tensor
@@ -2195,19 +2319,40 @@ __global__ void __launch_bounds__(pair_threads(CH, EPI, BATCH && !CHAIN), 1)
             if (!acc_ready) break;
             const float2 phl = EPI == 2 ? point_phase<KMAJOR>(A, tile, quarter, lane) : make_float2(1.0f, 0.0f);
             const double wpl = EPI == 5 ? point_weight<KMAJOR>(A, tile, quarter, lane) : 0.0;
+            int commits = 0;
             if (CHAIN && pr->km) {
 #pragma unroll
                 for (int q = 0; q < kPerWarp; ++q)
-                    epi_frag_store<NP, true, EPI, FX>(A, &pr->mapY, staging + ew * kStagingPerWarp, vr[q], vi[q],
-                                                      tile, h, quarter, lane, grp + kGroups * q, nchunks, s_in,
-                                                      inv_out, lim, local_max, range_ok, phl, wpl, nacc);
+                    commits += epi_frag_store<NP, true, EPI, FX>(A, &pr->mapY, staging + ew * kStagingPerWarp, vr[q],
+                                                                 vi[q], tile, h, quarter, lane, grp + kGroups * q,
+                                                                 nchunks, s_in, inv_out, lim, local_max, range_ok,
+                                                                 phl, wpl, nacc);
             } else {
 #pragma unroll
                 for (int q = 0; q < kPerWarp; ++q)
-                    epi_frag_store<NP, KMAJOR && !CHAIN, EPI, FX>(
+                    commits += epi_frag_store<NP, KMAJOR && !CHAIN, EPI, FX>(
                         A, BATCH ? &pr->mapY : &mapY, staging + ew * kStagingPerWarp, vr[q], vi[q], tile, h,
                         quarter, lane, grp + kGroups * q, nchunks, s_in, inv_out, lim, local_max, range_ok, phl,
                         wpl, nacc);
+            }
+            if (CHAIN) {
+                if (pend_pr) {
+                    // the previous item's stores (all but this item's groups) have completed
+                    if (lane == 0) bulk_wait_but(commits);
+                    signal_item(pend_pr, pend_pair, pend_h, pend_lt);
+                    pend_pr = nullptr;
+                }
+                if (P + nclusters >= items || P + nclusters >= pr->pairs_begin + A.pairs) {
+                    // this cluster's last item of the product
+                    flush_max();
+                    if (lane == 0) bulk_wait0();
+                    signal_item(pr, pairi, h, lt);
+                } else {
+                    pend_pr = pr;
+                    pend_pair = pairi;
+                    pend_h = h;
+                    pend_lt = lt;
+                }
             }
         }
         if (lane == 0) bulk_wait0();  // this warp's stores are complete
@@ -2222,7 +2367,7 @@ __global__ void __launch_bounds__(pair_threads(CH, EPI, BATCH && !CHAIN), 1)
             local_max = 0.0f;
             if (!range_ok && a.err) atomicCAS(a.err, 0, MM_ERR_RANGE);
         }
-        signal_upto(nprob);  // CHAIN: the products left (also after an abort: no CTA waits for nothing)
+        if (CHAIN && pend_pr) signal_item(pend_pr, pend_pair, pend_h, pend_lt);  // only after an abort
     }
     tc_fence_before();
     __syncthreads();
@@ -3189,9 +3334,49 @@ cudaError_t tc_pair_record_build(const TcState &si, const TcState &so, int mu, c
     r.pairs_begin = 0;
     r.km = L.km ? 1 : 0;
     r.prod = chain_pos < 0 ? 0 : chain_pos;
+    r.last_dir = mu == si.d ? 1 : 0;
+    r.slab_div = mu < si.d ? L.a.right / si.np[si.d - 1] : 1;
+    r.wait_prod = -1;
     std::memcpy(rec, &r, sizeof r);
     *kmajor = L.km;
     *items = L.a.pairs;
+    return cudaSuccess;
+}
+
+// The dependencies of a chain's products (records built with positions 0 .. nprod - 1 of a
+// d-direction sweep sequence): items of the last direction in row-tile-major order, what
+// completes each product and each of its slab groups, and the product that must be complete
+// before a product's first load (two back, or one for d = 1: the buffer a product overwrites was
+// read two products back, and its scale comes from the maximum of the product d back);
+// s_in_max[k]: the maximum word whose grid exponent is product k's input scale (null: its s_in).
+cudaError_t tc_pair_chain_plan(void *host_recs, int nprod, int d, const unsigned *const *s_in_max)
+{
+    auto *h = reinterpret_cast<TcPairProblem *>(host_recs);
+    for (int q = 0; q < nprod; ++q) {
+        TcPairProblem &R = h[q];
+        const int64_t np = R.a.pairs / R.a.ni;
+        if (R.a.ni < 1 || np * R.a.ni != R.a.pairs || R.a.mp > int64_t(kChainSlabs) * kChainGroups)
+            return cudaErrorInvalidValue;
+        R.hmajor = R.last_dir;
+        std::memset(R.g_expect, 0, sizeof R.g_expect);
+        for (int64_t Pl = 0; Pl < R.a.pairs; ++Pl) {
+            int64_t pair;
+            int hh;
+            chain_item(R.a, R.hmajor != 0, Pl, pair, hh);
+            for (int rank = 0; rank < 2; ++rank) {
+                int g_lo, g_hi;
+                chain_groups(R, pair, hh, rank, false, g_lo, g_hi);
+                for (int g = g_lo; g <= g_hi; ++g) {
+                    if (g < 0 || g >= kChainGroups) return cudaErrorInvalidValue;
+                    ++R.g_expect[g];
+                }
+            }
+        }
+        R.tot_target = unsigned(2 * R.a.pairs);
+        const int back = d >= 2 ? 2 : 1;
+        R.wait_prod = q >= back ? q - back : -1;
+        R.s_in_max = s_in_max[q];
+    }
     return cudaSuccess;
 }
 
@@ -3211,16 +3396,16 @@ bool tc_pair_batch_compatible(const void *host_recs, int nprob)
 // The records must agree on what the kernel's launch arguments fix: the row
 // tile size (stage layout) and the input layout.
 // One persistent launch over a chain of products (records built with chain positions 0, 1, ..,
-// in that order, all with row tiles of the same size): product k's loads wait until product k - 1
-// has been stored.  `done` holds nprod counters and `tally` num_sms() x nprod words, both zeroed
-// by the caller before the launch.
+// in that order, all with row tiles of the same size, then tc_pair_chain_plan): an item's loads
+// wait until the slab groups it reads have been stored by the previous product.  `done` holds
+// nprod counters and `gcnt` nprod x kChainGroups, all zeroed by the caller before the launch.
 int tc_chain_ctas() { return num_sms(); }
 
 cudaError_t tc_pair_chain_launch(const void *host_recs, const void *dev_recs, int nprod, unsigned *done,
-                                 unsigned *tally, int *d_err, cudaStream_t s)
+                                 unsigned *gcnt, int *d_err, cudaStream_t s)
 {
     const auto *h = reinterpret_cast<const TcPairProblem *>(host_recs);
-    if (nprod < 1 || !done || !tally) return cudaErrorInvalidValue;
+    if (nprod < 1 || !done || !gcnt) return cudaErrorInvalidValue;
     TcArgs a = h[0].a;
     int64_t total = 0;
     for (int q = 0; q < nprod; ++q) {
@@ -3237,7 +3422,7 @@ cudaError_t tc_pair_chain_launch(const void *host_recs, const void *dev_recs, in
     if (e != cudaSuccess) return e;
     cudaLaunchConfig_t cfg = {};
     cfg.gridDim = dim3(unsigned(2 * (total < num_sms() / 2 ? total : num_sms() / 2)));
-    cfg.blockDim = dim3(pair_threads(1, 0, false));
+    cfg.blockDim = dim3(pair_threads(1, 0, false) + 32);  // + the signalling warp
     cfg.dynamicSmemBytes = size_t(smem);
     cfg.stream = s;
     cudaLaunchAttribute attr[2];
@@ -3254,8 +3439,7 @@ cudaError_t tc_pair_chain_launch(const void *host_recs, const void *dev_recs, in
     e = cudaOccupancyMaxActiveClusters(&active, kern, &cfg);
     if (e != cudaSuccess || active < 1) return e != cudaSuccess ? e : cudaErrorInvalidConfiguration;
     if (2 * active < int(cfg.gridDim.x)) cfg.gridDim = dim3(unsigned(2 * active));
-    a.done_target = cfg.gridDim.x;  // one signal per CTA and product
-    a.tally = tally;
+    a.gcnt = gcnt;
     e = cudaLaunchKernelEx(&cfg, kern, h[0].mapX, h[0].mapE, h[0].mapY, a,
                            reinterpret_cast<const TcPairProblem *>(dev_recs), nprod, total);
     count_launch();

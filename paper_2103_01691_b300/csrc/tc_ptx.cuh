@@ -99,6 +99,12 @@ __device__ __forceinline__ unsigned atom_add_acqrel_cta_global(unsigned *p, unsi
     asm volatile("atom.acq_rel.cta.global.add.u32 %0, [%1], %2;" : "=r"(old) : "l"(p), "r"(v) : "memory");
     return old;
 }
+// A release fence at GPU scope followed by relaxed adds: one fence publishes several counters
+__device__ __forceinline__ void fence_acq_rel_gpu() { asm volatile("fence.acq_rel.gpu;" ::: "memory"); }
+__device__ __forceinline__ void red_relaxed_gpu_add(unsigned *p, unsigned v)
+{
+    asm volatile("red.relaxed.gpu.global.add.u32 [%0], %1;" ::"l"(p), "r"(v) : "memory");
+}
 // Orders this thread's global-memory accesses through the generic proxy with those through the
 // async proxy (TMA), both ways: a TMA store's data is published by a later generic release, and
 // a generic acquire precedes a later TMA load.
@@ -349,6 +355,17 @@ __device__ __forceinline__ void bulk_commit() { asm volatile("cp.async.bulk.comm
 __device__ __forceinline__ void bulk_wait_read0() { asm volatile("cp.async.bulk.wait_group.read 0;" ::: "memory"); }
 // Wait until every committed bulk group of this thread has completed.
 __device__ __forceinline__ void bulk_wait0() { asm volatile("cp.async.bulk.wait_group 0;" ::: "memory"); }
+// Completion of every bulk group of this thread but the n (0..4) most recent
+__device__ __forceinline__ void bulk_wait_but(int n)
+{
+    switch (n) {
+    case 0: asm volatile("cp.async.bulk.wait_group 0;" ::: "memory"); break;
+    case 1: asm volatile("cp.async.bulk.wait_group 1;" ::: "memory"); break;
+    case 2: asm volatile("cp.async.bulk.wait_group 2;" ::: "memory"); break;
+    case 3: asm volatile("cp.async.bulk.wait_group 3;" ::: "memory"); break;
+    default: asm volatile("cp.async.bulk.wait_group 4;" ::: "memory"); break;
+    }
+}
 
 // ---- programmatic dependent launch ---------------------------------------------------
 // Lets the next kernel of the stream (launched with programmatic stream serialization) be

@@ -261,13 +261,16 @@ def test_pair_kernel_matches_one_sm_kernel(env, monkeypatch, dims, prec, tile):
 
 
 @pytest.mark.parametrize("dims,steps", [((64, 64, 64), 3), ((128, 128, 128), 2), ((256, 64, 48), 2),
-                                         ((100, 37, 48), 2), ((40, 24), 4), ((256, 256, 256), 1)])
+                                         ((100, 37, 48), 2), ((40, 24), 4), ((256, 256, 256), 1),
+                                         ((64, 64, 64), 9), ((192, 192, 192), 3), ((32, 24, 40, 16), 3),
+                                         ((48, 40, 512), 2), ((300,), 5)])
 def test_chained_launch_matches_single_launches(env, orc, dims, steps):
-    """The chained variant (every product of a step call in one persistent launch, each product's
-    loads waiting for the previous product's stores through counters) runs the same items with
-    the same kernel code as one launch per product: the results agree bit for bit, from plain
-    launches and from a replayed graph.  Shapes whose directions have row tiles of different
-    sizes fall back to one launch per product."""
+    """The chained variant (every product of a step call in one persistent launch, each item's
+    loads waiting for the slab groups it reads through counters, so that products overlap) runs
+    the same items with the same kernel code as one launch per product: the results agree bit
+    for bit, from plain launches and from a replayed graph, over d = 1 .. 4 and padded directions.
+    Shapes whose directions have row tiles of different sizes fall back to one launch per
+    product."""
     mm, ctx, torch = env
     tau = 1e-4
     Es = [fd_schrodinger_E(mm, n, tau) for n in dims]
