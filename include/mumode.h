@@ -325,9 +325,16 @@ void mm_plan_destroy(mm_plan *plan);
  * scratch copy of u_dev (which is left unchanged), in two passes whose
  * faster time counts (the first pass also brings an idle GPU to its
  * clocks), and keeps the fastest in the plan.  Hermite plans time harmonic-oscillator steps and keep their
- * mode order.  Allocates a state-sized scratch for the call.  Errors:
- * MM_ERR_INVALID_ARG, MM_ERR_OOM, and those of the timed steps (the plan's
- * configuration is then unchanged). */
+ * mode order.  Allocates a state-sized scratch for the call.
+ * Cache (not from the paper): when the environment variable
+ * MM_AUTOTUNE_CACHE names a file, a plan whose key is in it takes the
+ * stored variant and order without timing anything (u_dev is not read),
+ * and a new result is appended as one JSON line {"key": ..., "variant":
+ * v, "order": [...]}.  The key holds the step kind (steps or GPE steps),
+ * the GPU's name, the plan kind, sizes, dtype, precision and, for
+ * tensor-core Tucker plans, a hash of the matrices' k-block bands.
+ * Errors: MM_ERR_INVALID_ARG, MM_ERR_OOM, and those of the timed steps (the
+ * plan's configuration is then unchanged). */
 mm_status mm_plan_autotune(mm_plan *plan, const void *u_dev, int64_t nsteps, void *stream);
 /* The plan's kernel variant and mode order (order_out: d ints, or NULL). */
 mm_status mm_plan_get_config(const mm_plan *plan, int *variant, int *order_out);

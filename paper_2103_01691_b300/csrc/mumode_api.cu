@@ -10,10 +10,27 @@
 #include <cstdio>
 #include <cstring>
 #include <map>
+#include <string>
 #include <tuple>
 #include <vector>
 
+#include <nvtx3/nvToolsExt.h>
+
 #include "internal.h"
+
+// An NVTX range over the scope: each public call and each mode-product launch is a named range
+// that profilers show on the timeline and can filter on (ncu --nvtx --nvtx-include ...); without
+// a tool attached the calls cost next to nothing.
+struct NvtxRange {
+    explicit NvtxRange(const char *name) { nvtxRangePushA(name); }
+    ~NvtxRange() { nvtxRangePop(); }
+    NvtxRange(const NvtxRange &) = delete;
+    NvtxRange &operator=(const NvtxRange &) = delete;
+};
+static const char *const kModeRangeNames[] = {"mode product 1", "mode product 2", "mode product 3",
+                                              "mode product 4", "mode product 5", "mode product 6",
+                                              "mode product 7", "mode product 8"};
+
 
 using cd = std::complex<double>;
 
@@ -307,6 +324,7 @@ mm_status tc_sweep(mm_plan *p, mm::TcMatrix *const *M, int &cur, const mm::TcEpi
             sc.max_cur = p->d_max + t * d + q;
             sc.zero_next = p->d_max + ((t + 1) % 3) * d + q;
         }
+        NvtxRange range(kModeRangeNames[(mu - 1) & 7]);
         cudaEvent_t ev0 = timing_event(p->ctx, true);
         if (ev0) cudaEventRecord(ev0, s);
         cudaError_t e = mm::tc_mode_product(p->st, p->st, mu, *M[mu - 1], p->prec, p->work[cur], p->work[1 - cur],
@@ -719,16 +737,118 @@ mm_status mm_plan_set_config(mm_plan *p, int variant, const int *order)
     return MM_OK;
 }
 
-// The tuner's loop; step(scratch, k) runs k steps of the kind being tuned on the scratch copy.
 extern "C++" {
+
+// The autotuner's cache key: what the timed work depends on.  The step kind, the GPU, the plan
+// kind, sizes, element type and precision, and for tensor-core Tucker plans the k-block bands of
+// each direction's matrix in both pair tilings (a banded propagator and a dense matrix of the
+// same size favour different variants).
+std::string autotune_key(const mm_plan *p, const char *kind)
+{
+    cudaDeviceProp prop;
+    if (cudaGetDeviceProperties(&prop, p->ctx->device) != cudaSuccess) prop.name[0] = 0;
+    std::string k = std::string(kind) + "|" + prop.name + "|" + (p->hermite ? "hermite" : "tucker") + "|d";
+    char buf[64];
+    for (int v = 0; v < p->d; ++v) {
+        std::snprintf(buf, sizeof buf, "%s%lld", v ? "x" : "=", (long long)p->n[v]);
+        k += buf;
+    }
+    std::snprintf(buf, sizeof buf, "|dtype=%d|prec=%d", int(p->dtype), int(p->prec));
+    k += buf;
+    if (p->tc && !p->hermite) {
+        uint64_t h = 1469598103934665603ull;  // FNV-1a over the band limits
+        auto mix = [&](int x) {
+            for (int b = 0; b < 4; ++b) {
+                h ^= uint64_t((x >> (8 * b)) & 0xff);
+                h *= 1099511628211ull;
+            }
+        };
+        for (int v = 0; v < p->d; ++v)
+            for (int t = 0; t < 2; ++t) {
+                const auto &P = p->Etc[v].pair[t];
+                mix(P.ni);
+                for (int r = 0; r < P.ni && r < 8; ++r) {
+                    mix(P.kb_lo[r]);
+                    mix(P.kb_hi[r]);
+                }
+            }
+        std::snprintf(buf, sizeof buf, "|bands=%016llx", (unsigned long long)h);
+        k += buf;
+    }
+    for (char &c : k)
+        if (c == '"' || c == '\\' || c == '\n') c = '_';
+    return k;
+}
+
+// A cached configuration for the key: sets the plan's variant and mode order and returns true.
+bool autotune_cache_lookup(const char *path, const std::string &key, mm_plan *p)
+{
+    FILE *f = std::fopen(path, "r");
+    if (!f) return false;
+    const std::string pat = "\"key\": \"" + key + "\"";
+    char line[2048];
+    bool found = false;
+    int variant = -1, order[mm::kMaxDims] = {};
+    while (std::fgets(line, sizeof line, f)) {
+        const char *at = std::strstr(line, pat.c_str());
+        if (!at) continue;
+        const char *v = std::strstr(at, "\"variant\": ");
+        const char *o = std::strstr(at, "\"order\": [");
+        if (!v || !o || std::sscanf(v + 11, "%d", &variant) != 1) continue;
+        o += 10;
+        bool ok = true;
+        for (int q = 0; q < p->d && ok; ++q) {
+            char *end = nullptr;
+            const long x = std::strtol(o, &end, 10);
+            ok = end != o && x >= 1 && x <= p->d;
+            order[q] = int(x);
+            o = end;
+            while (*o == ',' || *o == ' ') ++o;
+        }
+        if (ok && variant >= 0 && variant < mm::kTcVariants) found = true;  // the last matching line wins
+    }
+    std::fclose(f);
+    if (!found) return false;
+    bool perm = true;
+    for (int q = 0; q < p->d; ++q)
+        for (int r = q + 1; r < p->d; ++r) perm = perm && order[q] != order[r];
+    if (!perm) return false;
+    drop_graphs(p);
+    p->variant = mm::TcVariant(variant);
+    if (!p->hermite)
+        for (int q = 0; q < p->d; ++q) p->order[q] = order[q];
+    return true;
+}
+
+// Appends the plan's configuration under the key (one line, written in one call).
+void autotune_cache_store(const char *path, const std::string &key, const mm_plan *p)
+{
+    std::string line = "{\"key\": \"" + key + "\", \"variant\": " + std::to_string(int(p->variant)) + ", \"order\": [";
+    for (int q = 0; q < p->d; ++q) line += (q ? ", " : "") + std::to_string(p->order[q]);
+    line += "]}\n";
+    FILE *f = std::fopen(path, "a");
+    if (!f) return;
+    std::fwrite(line.data(), 1, line.size(), f);
+    std::fclose(f);
+}
+
+// The tuner's loop; step(scratch, k) runs k steps of the kind being tuned on the scratch copy.
 template <typename Step>
 mm_status autotune_with(mm_plan *p, const void *u_dev, int64_t nsteps, void *stream, bool orders_too,
-                               Step step)
+                               const char *kind, Step step)
 {
     if (!p) return fail(MM_ERR_INVALID_ARG, "plan is NULL");
     mm_status st = check_ptr(u_dev, "u_dev");
     if (st) return st;
     if (nsteps < 1 || nsteps > 1000) return fail(MM_ERR_INVALID_ARG, "nsteps = %lld outside 1..1000", (long long)nsteps);
+    // MM_AUTOTUNE_CACHE: a file of earlier results (one JSON object per line); a plan whose key is
+    // there takes that configuration without timing anything, and a new result is appended
+    const char *cache = std::getenv("MM_AUTOTUNE_CACHE");
+    std::string key;
+    if (cache && cache[0]) {
+        key = autotune_key(p, kind);
+        if (autotune_cache_lookup(cache, key, p)) return MM_OK;
+    }
     cudaStream_t s = (cudaStream_t)stream;
     const size_t bytes = size_t(p->count) * elem_bytes(p->dtype);
     void *scratch = nullptr;
@@ -797,6 +917,7 @@ mm_status autotune_with(mm_plan *p, const void *u_dev, int64_t nsteps, void *str
     const std::vector<int> &keep = st ? ord : best_o;
     for (int q = 0; q < p->d; ++q) p->order[q] = keep[size_t(q)];
     p->use_graphs = graphs;
+    if (!st && !key.empty()) autotune_cache_store(cache, key, p);
     return st;
 }
 
@@ -804,8 +925,9 @@ mm_status autotune_with(mm_plan *p, const void *u_dev, int64_t nsteps, void *str
 
 mm_status mm_plan_autotune(mm_plan *p, const void *u_dev, int64_t nsteps, void *stream)
 {
+    NvtxRange range("mm_plan_autotune");
     if (!p) return fail(MM_ERR_INVALID_ARG, "plan is NULL");
-    return autotune_with(p, u_dev, nsteps, stream, true, [&](void *u, int64_t k) {
+    return autotune_with(p, u_dev, nsteps, stream, true, "steps", [&](void *u, int64_t k) {
         return p->hermite ? hermite_ho_step(p, u, 0.01, k, stream) : mumode_step(p, u, k, stream);
     });
 }
@@ -815,7 +937,7 @@ mm_status split_step_gpe_autotune(mm_plan *p, const void *psi_dev, double beta, 
 {
     if (!p || !p->hermite) return fail(MM_ERR_INVALID_ARG, "not a Hermite plan");
     if (!std::isfinite(beta) || !std::isfinite(tau)) return fail(MM_ERR_INVALID_ARG, "beta or tau is not finite");
-    return autotune_with(p, psi_dev, nsteps, stream, false,
+    return autotune_with(p, psi_dev, nsteps, stream, false, "gpe",
                          [&](void *u, int64_t k) { return split_step_gpe(p, u, beta, tau, k, stream); });
 }
 
@@ -1010,6 +1132,7 @@ mm_status hkp_plan_create(mm_ctx *ctx, int d, const int64_t *n, const double *co
 mm_status mumode_product(mm_ctx *ctx, int d, const int64_t *n, int mu, const double *L, int64_t m, int L_is_complex,
                          mm_dtype dtype, mm_prec prec, const void *u_dev, void *s_dev, void *stream)
 {
+    NvtxRange range("mumode_product");
     if (!ctx) return fail(MM_ERR_INVALID_ARG, "ctx is NULL");
     mm_status st = check_dims(d, n);
     if (st) return st;
@@ -1127,6 +1250,7 @@ mm_status mumode_plan_create(mm_ctx *ctx, int d, const int64_t *n, const double 
 
 mm_status mumode_step(mm_plan *p, void *u_dev, int64_t nsteps, void *stream)
 {
+    NvtxRange range("mumode_step");
     if (!p) return fail(MM_ERR_INVALID_ARG, "plan is NULL");
     mm_status st = check_ptr(u_dev, "u_dev");
     if (st) return st;
@@ -1162,6 +1286,7 @@ mm_status mumode_step(mm_plan *p, void *u_dev, int64_t nsteps, void *stream)
 
 mm_status mumode_step_host(mm_plan *p, void *u_host, int64_t nsteps, void *stream)
 {
+    NvtxRange range("mumode_step_host");
     if (!p) return fail(MM_ERR_INVALID_ARG, "plan is NULL");
     if (!u_host) return fail(MM_ERR_INVALID_ARG, "u_host is NULL");
     const size_t bytes = size_t(p->count) * elem_bytes(p->dtype);
@@ -1305,16 +1430,19 @@ static mm_status hermite_apply(mm_plan *p, bool forward, const void *in, void *o
 
 mm_status hermite_forward(mm_plan *p, const void *values_dev, void *coeffs_dev, void *stream)
 {
+    NvtxRange range("hermite_forward");
     return hermite_apply(p, true, values_dev, coeffs_dev, stream);
 }
 
 mm_status hermite_backward(mm_plan *p, const void *coeffs_dev, void *values_dev, void *stream)
 {
+    NvtxRange range("hermite_backward");
     return hermite_apply(p, false, coeffs_dev, values_dev, stream);
 }
 
 mm_status hermite_ho_step(mm_plan *p, void *psi, double tau, int64_t nsteps, void *stream)
 {
+    NvtxRange range("hermite_ho_step");
     if (!p || !p->hermite) return fail(MM_ERR_INVALID_ARG, "not a Hermite plan");
     mm_status st = check_ptr(psi, "psi_dev");
     if (st) return st;
@@ -1418,6 +1546,7 @@ extern "C" {
 mm_status split_step_gpe_norm2(mm_plan *p, void *psi, double beta, double tau, int64_t nsteps, double *norm2_host,
                                void *stream)
 {
+    NvtxRange range("split_step_gpe_norm2");
     if (!p || !p->hermite) return fail(MM_ERR_INVALID_ARG, "not a Hermite plan");
     if (p->d != 3) return fail(MM_ERR_INVALID_ARG, "weighted norm needs a 3D Hermite plan");
     if (!norm2_host) return fail(MM_ERR_INVALID_ARG, "norm2_host is NULL");
@@ -1447,6 +1576,7 @@ mm_status split_step_gpe_norm2(mm_plan *p, void *psi, double beta, double tau, i
 
 mm_status split_step_gpe(mm_plan *p, void *psi, double beta, double tau, int64_t nsteps, void *stream)
 {
+    NvtxRange range("split_step_gpe");
     if (!p || !p->hermite) return fail(MM_ERR_INVALID_ARG, "not a Hermite plan");
     mm_status st = check_ptr(psi, "psi_dev");
     if (st) return st;
@@ -1582,6 +1712,7 @@ void adj_release(mm_plan *p)
 extern "C" mm_status split_step_gpe_adjoint(mm_plan *p, const void *psi0, const void *gT, void *g0, double beta,
                                             double tau, int64_t nsteps, int64_t ckpt_every, void *stream)
 {
+    NvtxRange range("split_step_gpe_adjoint");
     if (!p || !p->hermite) return fail(MM_ERR_INVALID_ARG, "not a Hermite plan");
     mm_status st;
     if ((st = check_ptr(psi0, "psi0_dev")) || (st = check_ptr(gT, "gT_dev")) || (st = check_ptr(g0, "g0_dev")))
@@ -1864,6 +1995,7 @@ extern "C" mm_status mumode_batch_create(mm_ctx *ctx, mm_plan *const *plans, int
 
 extern "C" mm_status mumode_batch_step(mm_batch *b, void *const *u_dev, int64_t nsteps, void *stream)
 {
+    NvtxRange range("mumode_batch_step");
     if (!b || !u_dev) return fail(MM_ERR_INVALID_ARG, "NULL argument");
     if (nsteps < 0) return fail(MM_ERR_INVALID_ARG, "nsteps < 0");
     mm_status st;
@@ -2222,6 +2354,7 @@ extern "C" mm_status hkmp_plan_create(mm_ctx *ctx, int d, const int64_t *n, cons
 
 extern "C" mm_status hkmp_evolve(mm_plan *p, void *psi, int64_t nsteps, const double *f_mid, void *stream)
 {
+    NvtxRange range("hkmp_evolve");
     if (!p || !p->hkmp) return fail(MM_ERR_INVALID_ARG, "not an HKMP plan");
     mm_status st = check_ptr(psi, "psi_dev");
     if (st) return st;

@@ -1132,6 +1132,45 @@ def test_gpe_autotune(env, orc):
     assert orc.rel_l2(psi.cpu().numpy(), ref, orc.weight3(Wo)) <= 1e-5
 
 
+def test_autotune_cache(env, orc, tmp_path, monkeypatch):
+    """With MM_AUTOTUNE_CACHE set, the first tuning of a plan appends one JSON
+    line; a second plan with the same key takes that configuration without
+    tuning (no new line; a line edited by hand is taken as written), and a
+    plan whose matrices have other k-block bands gets a key of its own."""
+    import json
+
+    mm, ctx, torch = env
+    path = tmp_path / "tune.jsonl"
+    monkeypatch.setenv("MM_AUTOTUNE_CACHE", str(path))
+    dims, tau = (256, 48, 40), 1e-4  # direction 1: a banded propagator (6 to 8 of 16 k-blocks per row tile)
+    Es = [fd_schrodinger_E(mm, n, tau) for n in dims]
+    u0 = inputs.complex_normal(dims[::-1], seed=2).astype(np.complex64)
+    u = to_gpu(torch, u0, torch.complex64)
+    cfg = mm.TuckerPlan(ctx, dims, Es, prec="f16x6").autotune(u, nsteps=1)
+    lines = path.read_text().splitlines()
+    assert len(lines) == 1
+    rec = json.loads(lines[0])
+    assert rec["variant"] == mm.VARIANTS.index(cfg[0]) and tuple(rec["order"]) == cfg[1]
+    assert "|tucker|d=256x48x40|" in rec["key"]
+    assert mm.TuckerPlan(ctx, dims, Es, prec="f16x6").autotune(u, nsteps=1) == cfg
+    assert len(path.read_text().splitlines()) == 1
+    # a stored configuration is applied as written
+    rec["variant"], rec["order"] = mm.VARIANTS.index("one_sm"), [2, 3, 1]
+    path.write_text(json.dumps(rec) + "\n")
+    plan = mm.TuckerPlan(ctx, dims, Es, prec="f16x6")
+    assert plan.autotune(u, nsteps=1) == ("one_sm", (2, 3, 1))
+    plan.step(u, 2)
+    ref = orc.tucker(u0.astype(complex), [orc.expm_dirichlet_fd(n, 1j * tau) for n in dims], order=(2, 3, 1),
+                     nsteps=2)
+    assert rel(u.cpu().numpy(), ref) <= TOL_MODE["f16x6"] * 6
+    # dense matrices of the same sizes: other bands, another key, tuned and appended
+    rng = np.random.default_rng(7)
+    dense = [np.linalg.qr(rng.standard_normal((n, n)) + 1j * rng.standard_normal((n, n)))[0] for n in dims]
+    mm.TuckerPlan(ctx, dims, dense, prec="f16x6").autotune(u, nsteps=1)
+    keys = [json.loads(ln)["key"] for ln in path.read_text().splitlines()]
+    assert len(keys) == 2 and keys[0] != keys[1]
+
+
 def test_autotune_hermite_and_fp64(env):
     """Hermite plans tune the kernel variant only; FP64 plans the mode order."""
     mm, ctx, torch = env
