@@ -35,6 +35,9 @@ cudaError_t dmma_mode_product(bool complex_data, int64_t left, int64_t n, int64_
                               const void *X, void *Y, cudaStream_t s);
 // psi *= exp(-i tb |psi|^2) for count complex elements.
 cudaError_t simt_nonlinear_phase(bool fp64, int64_t count, double tb, void *psi, cudaStream_t s);
+// Even/odd folding (inverse: unfolding) of a complex64 tensor with sizes n[0..d-1] (n[0] fastest)
+// in the directions of mask (bit v: direction v + 1; at most five of them); in and out are distinct.
+cudaError_t fold_state(int d, const int64_t *n, unsigned mask, bool inverse, const void *in, void *out, cudaStream_t s);
 // g <- adjoint of the nonlinear phase at psi (psi: state before the phase).
 cudaError_t simt_nonlinear_adjoint(bool fp64, int64_t count, double tb, const void *psi, void *g, cudaStream_t s);
 // out (device double) += sum |u|^2 w, w = w1[i1] w2[i2] w3[i3] if w1 != NULL.

@@ -82,6 +82,12 @@ struct mm_plan {
     // Tucker matrices (one per direction) in the form of the precision
     void *Edev[mm::kMaxDims] = {};        // SIMT: element type of the state
     mm::TcMatrix Etc[mm::kMaxDims] = {};  // tensor cores
+    // Even/odd folding (Tucker plans on the tensor cores): the directions whose matrix is
+    // centrosymmetric hold it folded, block-diagonal (Dtc); a step call folds the state once,
+    // runs its steps on the folded state and unfolds it once (fold_buf: a complex64 state)
+    unsigned fold_mask = 0;
+    mm::TcMatrix Dtc[mm::kMaxDims] = {};
+    void *fold_buf = nullptr;
     // workspace
     mm::TcState st;
     void *work[3] = {nullptr, nullptr, nullptr};  // TC: piece buffers (the third for chains); SIMT: work[0] state-sized
@@ -299,6 +305,14 @@ cudaEvent_t timing_event(mm_ctx *c, bool start, int products = 1)
     return c->events[c->events_used++].second;
 }
 
+// The tensor-core matrix the steps of a Tucker plan use in direction v (0-based): the folded
+// block-diagonal form where the plan folds that direction.
+mm::TcMatrix *step_matrix(mm_plan *p, int v) { return ((p->fold_mask >> v) & 1u) ? &p->Dtc[v] : &p->Etc[v]; }
+const mm::TcMatrix *step_matrix(const mm_plan *p, int v)
+{
+    return ((p->fold_mask >> v) & 1u) ? &p->Dtc[v] : &p->Etc[v];
+}
+
 // One Tucker sweep on the TC piece state: modes in plan order with
 // matrices M[mu-1]; cur is the index of the buffer holding the state.
 mm_status tc_sweep(mm_plan *p, mm::TcMatrix *const *M, int &cur, const mm::TcEpilogue &last_epi, cudaStream_t s)
@@ -387,7 +401,7 @@ bool chain_prepare(mm_plan *p, int64_t nsteps)
             bool km = false;
             int64_t items = 0;
             void *rec = base + rb * size_t(pos);
-            if (mm::tc_pair_record_build(p->st, p->st, mu, p->Etc[mu - 1], p->prec, p->work[pos % 3],
+            if (mm::tc_pair_record_build(p->st, p->st, mu, *step_matrix(p, mu - 1), p->prec, p->work[pos % 3],
                                          p->work[(pos + 1) % 3], sc, rec, &km, &items, pos) != cudaSuccess) {
                 cudaFree(done);
                 return false;
@@ -701,7 +715,7 @@ mm_status mm_plan_issued_flops(const mm_plan *p, double *flops_per_step)
     double f = 0.0;
     for (int q = 0; q < p->d; ++q) {
         const int mu = p->order[q];
-        f += mm::tc_issued_flops(p->st, mu, p->Etc[mu - 1], p->prec, p->variant);
+        f += mm::tc_issued_flops(p->st, mu, *step_matrix(p, mu - 1), p->prec, p->variant);
     }
     *flops_per_step = f;
     return MM_OK;
@@ -765,14 +779,14 @@ std::string autotune_key(const mm_plan *p, const char *kind)
         };
         for (int v = 0; v < p->d; ++v)
             for (int t = 0; t < 2; ++t) {
-                const auto &P = p->Etc[v].pair[t];
+                const auto &P = step_matrix(p, v)->pair[t];
                 mix(P.ni);
                 for (int r = 0; r < P.ni && r < 8; ++r) {
                     mix(P.kb_lo[r]);
                     mix(P.kb_hi[r]);
                 }
             }
-        std::snprintf(buf, sizeof buf, "|bands=%016llx", (unsigned long long)h);
+        std::snprintf(buf, sizeof buf, "|fold=%x|bands=%016llx", p->fold_mask, (unsigned long long)h);
         k += buf;
     }
     for (char &c : k)
@@ -1219,6 +1233,68 @@ mm_status mumode_product(mm_ctx *ctx, int d, const int64_t *n, int mu, const dou
     return MM_OK;
 }
 
+// The folded form of a centrosymmetric n x n matrix E (interleaved complex, row-major): with F
+// the even/odd fold (fold_state) D = F E F^-1 is block-diagonal, an even block of ceil(n/2) rows
+// and an odd block of floor(n/2).  Returns false (D untouched) when E is not centrosymmetric to
+// 1e-13 of its largest entry; the off-diagonal blocks of D, rounding-sized then, are set to zero.
+bool fold_matrix(const double *E, int64_t n, std::vector<double> &D)
+{
+    using cd = std::complex<double>;
+    const cd *e = reinterpret_cast<const cd *>(E);
+    double amax = 0.0, asym = 0.0;
+    for (int64_t i = 0; i < n; ++i)
+        for (int64_t j = 0; j < n; ++j) {
+            amax = std::max(amax, std::abs(e[i * n + j]));
+            asym = std::max(asym, std::abs(e[i * n + j] - e[(n - 1 - i) * n + (n - 1 - j)]));
+        }
+    if (n < 2 || !(asym <= 1e-13 * amax)) return false;
+    const int64_t c = (n + 1) / 2, h = n / 2;
+    std::vector<cd> G(size_t(n * n)), R(size_t(n * n));
+    for (int64_t j = 0; j < n; ++j) {  // G = F E (rows)
+        for (int64_t k = 0; k < h; ++k) {
+            G[size_t(k * n + j)] = e[k * n + j] + e[(n - 1 - k) * n + j];
+            G[size_t((c + k) * n + j)] = e[k * n + j] - e[(n - 1 - k) * n + j];
+        }
+        if (n % 2) G[size_t(h * n + j)] = e[h * n + j];
+    }
+    for (int64_t i = 0; i < n; ++i) {  // R = G F^-1 (columns)
+        for (int64_t k = 0; k < h; ++k) {
+            R[size_t(i * n + k)] = 0.5 * (G[size_t(i * n + k)] + G[size_t(i * n + n - 1 - k)]);
+            R[size_t(i * n + c + k)] = 0.5 * (G[size_t(i * n + k)] - G[size_t(i * n + n - 1 - k)]);
+        }
+        if (n % 2) R[size_t(i * n + h)] = G[size_t(i * n + h)];
+    }
+    for (int64_t i = 0; i < n; ++i)
+        for (int64_t j = 0; j < n; ++j)
+            if ((i < c) != (j < c)) R[size_t(i * n + j)] = 0.0;
+    D.assign(reinterpret_cast<const double *>(R.data()), reinterpret_cast<const double *>(R.data()) + 2 * n * n);
+    return true;
+}
+
+// Fold the directions of a tensor-core Tucker plan whose matrices are centrosymmetric (at most
+// five; MM_NO_FOLD set to other than 0 turns it off), and allocate the folded state's buffer.
+mm_status fold_matrices(mm_plan *p, const double *const *E_host, bool Ec)
+{
+    p->fold_mask = 0;
+    const char *off = std::getenv("MM_NO_FOLD");
+    if (!p->tc || p->hermite || p->dtype != MM_C64 || (off && off[0] && !(off[0] == '0' && off[1] == 0))) return MM_OK;
+    int folded = 0;
+    for (int v = 0; v < p->d && folded < 5; ++v) {
+        const int64_t n = p->n[v];
+        std::vector<double> c = as_complex(E_host[v], n * n, Ec), D;
+        if (!fold_matrix(c.data(), n, D)) continue;
+        mm_status st = mm::tc_matrix_create(D.data(), n, n, p->npieces, p->fixed, &p->Dtc[v], p->tf32);
+        if (st) return st;
+        p->fold_mask |= 1u << v;
+        ++folded;
+    }
+    if (p->fold_mask && cudaMalloc(&p->fold_buf, size_t(p->count) * 8) != cudaSuccess) {
+        p->fold_buf = nullptr;
+        return fail(MM_ERR_OOM, "folded state buffer of %lld bytes", (long long)(p->count * 8));
+    }
+    return MM_OK;
+}
+
 mm_status mumode_plan_create(mm_ctx *ctx, int d, const int64_t *n, const double *const *E_host, int E_is_complex,
                              mm_dtype dtype, mm_prec prec, const int *mode_order, mm_plan **out)
 {
@@ -1240,7 +1316,7 @@ mm_status mumode_plan_create(mm_ctx *ctx, int d, const int64_t *n, const double 
             return st;
         }
     }
-    if ((st = alloc_workspace(p))) {
+    if ((st = alloc_workspace(p)) || (st = fold_matrices(p, E_host, E_is_complex != 0))) {
         mm_plan_destroy(p);
         return st;
     }
@@ -1272,15 +1348,25 @@ mm_status mumode_step(mm_plan *p, void *u_dev, int64_t nsteps, void *stream)
         mm_status r;
         int cur = 0;
         mm::TcMatrix *M[mm::kMaxDims];
-        for (int v = 0; v < p->d; ++v) M[v] = &p->Etc[v];
-        if ((r = tc_begin(p, M, u_dev, s))) return r;
+        for (int v = 0; v < p->d; ++v) M[v] = step_matrix(p, v);
+        // folded directions: the steps run on the folded state, folded and unfolded once per call
+        const void *src = u_dev;
+        if (p->fold_mask) {
+            cudaError_t e = mm::fold_state(p->d, p->n, p->fold_mask, false, u_dev, p->fold_buf, s);
+            if (e != cudaSuccess) return cuda_fail(e, "fold");
+            src = p->fold_buf;
+        }
+        if ((r = tc_begin(p, M, src, s))) return r;
         if (chained) {
             if ((r = chain_run(p, cur, s))) return r;
         } else {
             for (int64_t k = 0; k < nsteps; ++k)
                 if ((r = tc_sweep(p, M, cur, mm::TcEpilogue{}, s))) return r;
         }
-        return tc_end(p, cur, u_dev, s);
+        if (!p->fold_mask) return tc_end(p, cur, u_dev, s);
+        if ((r = tc_end(p, cur, p->fold_buf, s))) return r;
+        cudaError_t e = mm::fold_state(p->d, p->n, p->fold_mask, true, p->fold_buf, u_dev, s);
+        return e == cudaSuccess ? MM_OK : cuda_fail(e, "unfold");
     });
 }
 
@@ -1316,6 +1402,7 @@ void mm_plan_destroy(mm_plan *p)
     for (int v = 0; v < mm::kMaxDims; ++v) {
         if (p->Edev[v]) cudaFree(p->Edev[v]);
         mm::tc_matrix_destroy(&p->Etc[v]);
+        mm::tc_matrix_destroy(&p->Dtc[v]);
         if (p->Wdev[v]) cudaFree(p->Wdev[v]);
         if (p->Wpad[v]) cudaFree(p->Wpad[v]);
         if (p->Fdev[v]) cudaFree(p->Fdev[v]);
@@ -1329,6 +1416,7 @@ void mm_plan_destroy(mm_plan *p)
     if (p->work[1]) cudaFree(p->work[1]);
     if (p->work[2]) cudaFree(p->work[2]);
     if (p->staging) cudaFree(p->staging);
+    if (p->fold_buf) cudaFree(p->fold_buf);
     if (p->d_scale) cudaFree(p->d_scale);
     if (p->d_max) cudaFree(p->d_max);
     if (p->d_work) cudaFree(p->d_work);
@@ -1898,7 +1986,7 @@ static bool build_pair_records(mm_batch *b, mm_plan *const *plans, int nprob)
                 bool km = false;
                 int64_t items = 0;
                 void *rec = buf + rb * size_t(k);
-                if (mm::tc_pair_record_build(p->st, p->st, mu, p->Etc[mu - 1], p->prec, p->work[cur], p->work[1 - cur],
+                if (mm::tc_pair_record_build(p->st, p->st, mu, *step_matrix(p, mu - 1), p->prec, p->work[cur], p->work[1 - cur],
                                              sc, rec, &km, &items) != cudaSuccess ||
                     km != b->kmajor[q])
                     return false;
@@ -1962,7 +2050,7 @@ extern "C" mm_status mumode_batch_create(mm_ctx *ctx, mm_plan *const *plans, int
                     zero = p->d_max + ((t + 1) % 3) * d + q;  // sweep k+1's word (see tc_sweep)
                 }
                 bool km = false;
-                cudaError_t e = mm::tc_problem_build(p->st, p->st, mu, p->Etc[mu - 1], p->prec, p->work[cur],
+                cudaError_t e = mm::tc_problem_build(p->st, p->st, mu, *step_matrix(p, mu - 1), p->prec, p->work[cur],
                                                      p->work[1 - cur], sc, &vec[size_t(k)], &km);
                 if (e != cudaSuccess) {
                     mm_batch_destroy(b);
@@ -2012,8 +2100,14 @@ extern "C" mm_status mumode_batch_step(mm_batch *b, void *const *u_dev, int64_t 
             if (e != cudaSuccess) return cuda_fail(e, "max words");
         }
         mm::TcMatrix *M[mm::kMaxDims];
-        for (int v = 0; v < d; ++v) M[v] = &p->Etc[v];
-        if ((st = tc_begin(p, M, u_dev[k], s))) return st;
+        for (int v = 0; v < d; ++v) M[v] = step_matrix(p, v);
+        const void *src = u_dev[k];
+        if (p->fold_mask) {  // folded directions, as in mumode_step
+            cudaError_t e = mm::fold_state(p->d, p->n, p->fold_mask, false, u_dev[k], p->fold_buf, s);
+            if (e != cudaSuccess) return cuda_fail(e, "fold");
+            src = p->fold_buf;
+        }
+        if ((st = tc_begin(p, M, src, s))) return st;
     }
     for (int64_t t = 0; t < nsteps; ++t)
         for (int q = 0; q < d; ++q) {
@@ -2031,8 +2125,15 @@ extern "C" mm_status mumode_batch_step(mm_batch *b, void *const *u_dev, int64_t 
         }
     const int cur = int((nsteps * d) % 2);
     for (size_t k = 0; k < b->plans.size(); ++k) {
-        b->plans[k]->sweep = nsteps;  // the batched launches ran nsteps sweeps of every plan
-        if ((st = tc_end(b->plans[k], cur, u_dev[k], s))) return st;
+        mm_plan *p = b->plans[k];
+        p->sweep = nsteps;  // the batched launches ran nsteps sweeps of every plan
+        if (!p->fold_mask) {
+            if ((st = tc_end(p, cur, u_dev[k], s))) return st;
+            continue;
+        }
+        if ((st = tc_end(p, cur, p->fold_buf, s))) return st;
+        cudaError_t e = mm::fold_state(p->d, p->n, p->fold_mask, true, p->fold_buf, u_dev[k], s);
+        if (e != cudaSuccess) return cuda_fail(e, "unfold");
     }
     return MM_OK;
 }
@@ -2184,6 +2285,11 @@ extern "C" mm_status mm_expm_device(mm_ctx *ctx, int n, const double *A_dev, con
 // Replace direction mu's matrix by a device matrix, in stream order.
 static mm_status set_matrix_device(mm_plan *p, int mu, const double2 *E, double row_norm_bound, cudaStream_t s)
 {
+    // the direction's new matrix is not folded: later steps use it as it is (the fold is per call)
+    if ((p->fold_mask >> (mu - 1)) & 1u) {
+        drop_graphs(p);
+        p->fold_mask &= ~(1u << (mu - 1));
+    }
     const int v = mu - 1;
     if (p->tf32) return fail(MM_ERR_UNSUPPORTED, "device matrix updates do not serve MM_PREC_TF32X3 plans");
     if (p->tc) {

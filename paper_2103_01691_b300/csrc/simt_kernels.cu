@@ -417,6 +417,90 @@ cudaError_t simt_nonlinear_adjoint(bool fp64, int64_t count, double tb, const vo
     return cudaGetLastError();
 }
 
+// Even/odd folding of a complex64 tensor in the directions of `mask` (bit v: direction v + 1).
+// In a folded direction of length n (c = ceil(n/2), h = floor(n/2)), index k < h of the folded
+// tensor holds x_k + x_(n-1-k), index c + k holds x_k - x_(n-1-k), and for odd n index h holds
+// x_h.  A centrosymmetric matrix E (E_ij = E_(n-1-i, n-1-j)) acts on the folded vector as a
+// block-diagonal matrix, so the mu-mode products of a Tucker step run on half-size blocks.
+// Each thread takes one orbit of the mirror maps: up to 2^d points read, butterflies in
+// registers, 2^d points written.  inverse: the unfold, with the factors 1/2.
+constexpr int kMaxFold = 5;  // folded directions at most (orbits of up to 32 points)
+struct FoldDims {
+    int d;
+    int64_t n[kMaxDims], c[kMaxDims], h[kMaxDims], stride[kMaxDims], rep[kMaxDims];
+    unsigned mask;
+};
+
+template <bool INV>
+__global__ void fold_kernel(FoldDims f, int64_t reps, const float2 *__restrict__ in, float2 *__restrict__ out)
+{
+    for (int64_t t = blockIdx.x * int64_t(blockDim.x) + threadIdx.x; t < reps; t += int64_t(gridDim.x) * blockDim.x) {
+        int64_t r[kMaxDims];
+        int64_t q = t;
+        int pv[kMaxDims], m = 0;  // the directions in which this orbit has a mirror pair
+        for (int v = 0; v < f.d; ++v) {
+            r[v] = q % f.rep[v];
+            q /= f.rep[v];
+            if (((f.mask >> v) & 1u) && r[v] < f.h[v]) pv[m++] = v;
+        }
+        const int cnt = 1 << m;
+        float2 buf[1 << kMaxFold];
+        // the original index of orbit pattern s (bit b: mirror in direction pv[b]) and the folded
+        // index of pattern s (bit b: odd part in direction pv[b])
+        auto orig = [&](int sp) {
+            int64_t off = 0;
+            for (int v = 0; v < f.d; ++v) off += r[v] * f.stride[v];
+            for (int b = 0; b < m; ++b)
+                if ((sp >> b) & 1) off += (f.n[pv[b]] - 1 - 2 * r[pv[b]]) * f.stride[pv[b]];
+            return off;
+        };
+        auto folded = [&](int sp) {
+            int64_t off = 0;
+            for (int v = 0; v < f.d; ++v) off += r[v] * f.stride[v];
+            for (int b = 0; b < m; ++b)
+                if ((sp >> b) & 1) off += f.c[pv[b]] * f.stride[pv[b]];
+            return off;
+        };
+        for (int sp = 0; sp < cnt; ++sp) buf[sp] = INV ? in[folded(sp)] : in[orig(sp)];
+        for (int b = 0; b < m; ++b)
+            for (int sp = 0; sp < cnt; ++sp)
+                if (!((sp >> b) & 1)) {
+                    const float2 a = buf[sp], z = buf[sp | (1 << b)];
+                    if (INV) {
+                        buf[sp] = make_float2(0.5f * (a.x + z.x), 0.5f * (a.y + z.y));
+                        buf[sp | (1 << b)] = make_float2(0.5f * (a.x - z.x), 0.5f * (a.y - z.y));
+                    } else {
+                        buf[sp] = make_float2(a.x + z.x, a.y + z.y);
+                        buf[sp | (1 << b)] = make_float2(a.x - z.x, a.y - z.y);
+                    }
+                }
+        for (int sp = 0; sp < cnt; ++sp) out[INV ? orig(sp) : folded(sp)] = buf[sp];
+    }
+}
+
+cudaError_t fold_state(int d, const int64_t *n, unsigned mask, bool inverse, const void *in, void *out, cudaStream_t s)
+{
+    if (d < 1 || d > kMaxDims || in == out || __builtin_popcount(mask) > kMaxFold) return cudaErrorInvalidValue;
+    FoldDims f;
+    f.d = d;
+    f.mask = mask;
+    int64_t stride = 1, reps = 1;
+    for (int v = 0; v < d; ++v) {
+        f.n[v] = n[v];
+        f.c[v] = (n[v] + 1) / 2;
+        f.h[v] = n[v] / 2;
+        f.stride[v] = stride;
+        f.rep[v] = ((mask >> v) & 1u) ? f.c[v] : n[v];
+        stride *= n[v];
+        reps *= f.rep[v];
+    }
+    const int64_t blocks = (reps + 255) / 256 < 148 * 16 ? (reps + 255) / 256 : 148 * 16;
+    if (inverse) fold_kernel<true><<<unsigned(blocks), 256, 0, s>>>(f, reps, (const float2 *)in, (float2 *)out);
+    else fold_kernel<false><<<unsigned(blocks), 256, 0, s>>>(f, reps, (const float2 *)in, (float2 *)out);
+    count_launch();
+    return cudaGetLastError();
+}
+
 cudaError_t norm2_accumulate(mm_dtype dt, int64_t n1, int64_t n2, int64_t n3, const void *u,
                              const double *w1, const double *w2, const double *w3, double *out,
                              cudaStream_t s)

@@ -499,11 +499,13 @@ def test_expm_device(env, orc, n):
 
 @pytest.mark.parametrize("prec,variant", [("f16x6", "pair64"), ("f16x6", "pair128"), ("f16x6", "one_sm"),
                                           ("bf16x3", "pair64"), ("fp64", None)])
-def test_set_matrix_device_matches_host_matrix(env, prec, variant):
+def test_set_matrix_device_matches_host_matrix(env, monkeypatch, prec, variant):
     """A matrix split on the device (mm_plan_set_matrix_device) gives the same
     bits as the host-built one: a plan created with other matrices and then
-    given E on the device steps exactly like a plan created with E."""
+    given E on the device steps exactly like a plan created with E (both
+    unfolded: a matrix set on the device is used as it is)."""
     mm, ctx, torch = env
+    monkeypatch.setenv("MM_NO_FOLD", "1")
     dims, tau = (72, 40, 33), 1e-4
     Es = [fd_schrodinger_E(mm, n, tau) for n in dims]
     other = [fd_schrodinger_E(mm, n, 3 * tau) for n in dims]
@@ -734,7 +736,9 @@ def test_graph_replay_matches_plain_launches(env):
         n1 = mm.launch_count()
     torch.cuda.synchronize()
     assert torch.equal(u, ref)
-    assert n1 - n0 == 2 * (2 + 3 * 3 + 1)  # max + split, 3 sweeps x 3 products, merge; counted per replay
+    # fold, max + split, 3 sweeps x 3 products, merge, unfold (the FD matrices are centrosymmetric,
+    # so the plan folds); counted per replay
+    assert n1 - n0 == 2 * (1 + 2 + 3 * 3 + 1 + 1)
 
 
 @pytest.mark.parametrize("dims", [(16, 16, 16), (20, 24, 40)])
@@ -1130,6 +1134,41 @@ def test_gpe_autotune(env, orc):
     plan.gpe_step(psi, beta, tau, steps)
     ref = orc.gpe_steps(psi0.astype(complex), xo, Wo, beta, tau, steps)
     assert orc.rel_l2(psi.cpu().numpy(), ref, orc.weight3(Wo)) <= 1e-5
+
+
+@pytest.mark.parametrize("dims,mixed", [((64, 48, 40), False), ((33, 40, 17), False), ((33, 40, 17), True),
+                                         ((300,), False), ((24, 20, 18, 16), False), ((256, 32, 31), True)])
+def test_fold_matches_unfolded(env, orc, monkeypatch, dims, mixed):
+    """Even/odd folding of a Tucker plan (centrosymmetric matrices run as block-diagonal products on
+    the folded state, folded and unfolded once per call) gives the unfolded plan's result to the
+    precision's tolerance, and the oracle's: even and odd sizes, d = 1 to 4, and plans where one
+    direction's matrix is not centrosymmetric (that direction stays unfolded)."""
+    mm, ctx, torch = env
+    tau, steps = 1e-4, 3
+    Es = [fd_schrodinger_E(mm, n, tau) for n in dims]
+    if mixed:  # the last direction: a random unitary matrix, not centrosymmetric
+        rng = np.random.default_rng(11)
+        n = dims[-1]
+        Es[-1] = np.linalg.qr(rng.standard_normal((n, n)) + 1j * rng.standard_normal((n, n)))[0]
+    u0 = inputs.complex_normal(dims[::-1], seed=6).astype(np.complex64)
+    out = {}
+    for fold in (True, False):
+        if fold:
+            monkeypatch.delenv("MM_NO_FOLD", raising=False)
+        else:
+            monkeypatch.setenv("MM_NO_FOLD", "1")
+        plan = mm.TuckerPlan(ctx, dims, Es, prec="f16x6")
+        u = to_gpu(torch, u0, torch.complex64)
+        plan.step(u, steps)
+        torch.cuda.synchronize()
+        ctx.status()
+        out[fold] = u.cpu().numpy()
+    monkeypatch.delenv("MM_NO_FOLD", raising=False)
+    d = rel(out[True], out[False])
+    ora = orc.tucker(u0.astype(complex), [np.asarray(E, dtype=complex) for E in Es], nsteps=steps)
+    print(f"fold vs unfolded dims={dims} mixed={mixed}: {d:.3e}; vs oracle {rel(out[True], ora):.3e}")
+    assert d <= TOL_MODE["f16x6"] * steps * len(dims)
+    assert rel(out[True], ora) <= TOL_MODE["f16x6"] * steps * len(dims)
 
 
 def test_autotune_cache(env, orc, tmp_path, monkeypatch):
