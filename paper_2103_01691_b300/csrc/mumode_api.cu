@@ -105,6 +105,10 @@ struct mm_plan {
     double prop_s[2] = {NAN, NAN};
     void *Pdev[2][mm::kMaxDims] = {};
     mm::TcMatrix Ptc[2][mm::kMaxDims] = {};
+    // the same propagators folded (even/odd, block-diagonal) where they are centrosymmetric, for
+    // the harmonic-oscillator steps (the GPE's pointwise nonlinearity needs the unfolded state)
+    mm::TcMatrix PFtc[2][mm::kMaxDims] = {};
+    unsigned pfold_mask[2] = {0u, 0u};
     // HKMP (hkmp_plan_create): per direction the Hamiltonian H0 and the
     // Galerkin matrix G of the time-dependent part (device, FP64), their
     // 1-norms, and the step's exponential exp(-i tau (H0 + f G))
@@ -627,13 +631,61 @@ std::vector<double> harmonic_propagator(const mm_plan *p, int v, double s)
     return P;
 }
 
+// The folded form of a centrosymmetric n x n matrix E (interleaved complex, row-major): with F
+// the even/odd fold (fold_state) D = F E F^-1 is block-diagonal, an even block of ceil(n/2) rows
+// and an odd block of floor(n/2).  Returns false (D untouched) when E is not centrosymmetric to
+// 1e-13 of its largest entry; the off-diagonal blocks of D, rounding-sized then, are set to zero.
+bool fold_matrix(const double *E, int64_t n, std::vector<double> &D)
+{
+    using cd = std::complex<double>;
+    const cd *e = reinterpret_cast<const cd *>(E);
+    double amax = 0.0, asym = 0.0;
+    for (int64_t i = 0; i < n; ++i)
+        for (int64_t j = 0; j < n; ++j) {
+            amax = std::max(amax, std::abs(e[i * n + j]));
+            asym = std::max(asym, std::abs(e[i * n + j] - e[(n - 1 - i) * n + (n - 1 - j)]));
+        }
+    if (n < 2 || !(asym <= 1e-13 * amax)) return false;
+    const int64_t c = (n + 1) / 2, h = n / 2;
+    std::vector<cd> G(size_t(n * n)), R(size_t(n * n));
+    for (int64_t j = 0; j < n; ++j) {  // G = F E (rows)
+        for (int64_t k = 0; k < h; ++k) {
+            G[size_t(k * n + j)] = e[k * n + j] + e[(n - 1 - k) * n + j];
+            G[size_t((c + k) * n + j)] = e[k * n + j] - e[(n - 1 - k) * n + j];
+        }
+        if (n % 2) G[size_t(h * n + j)] = e[h * n + j];
+    }
+    for (int64_t i = 0; i < n; ++i) {  // R = G F^-1 (columns)
+        for (int64_t k = 0; k < h; ++k) {
+            R[size_t(i * n + k)] = 0.5 * (G[size_t(i * n + k)] + G[size_t(i * n + n - 1 - k)]);
+            R[size_t(i * n + c + k)] = 0.5 * (G[size_t(i * n + k)] - G[size_t(i * n + n - 1 - k)]);
+        }
+        if (n % 2) R[size_t(i * n + h)] = G[size_t(i * n + h)];
+    }
+    for (int64_t i = 0; i < n; ++i)
+        for (int64_t j = 0; j < n; ++j)
+            if ((i < c) != (j < c)) R[size_t(i * n + j)] = 0.0;
+    D.assign(reinterpret_cast<const double *>(R.data()), reinterpret_cast<const double *>(R.data()) + 2 * n * n);
+    return true;
+}
+
+// Even/odd folding applies to tensor-core plans on complex64 data unless MM_NO_FOLD is set to
+// other than 0.
+bool fold_enabled(const mm_plan *p)
+{
+    const char *off = std::getenv("MM_NO_FOLD");
+    return p->tc && p->dtype == MM_C64 && !(off && off[0] && !(off[0] == '0' && off[1] == 0));
+}
+
 void free_prop(mm_plan *p, int slot)
 {
     for (int v = 0; v < p->d; ++v) {
         if (p->Pdev[slot][v]) cudaFree(p->Pdev[slot][v]);
         p->Pdev[slot][v] = nullptr;
         mm::tc_matrix_destroy(&p->Ptc[slot][v]);
+        mm::tc_matrix_destroy(&p->PFtc[slot][v]);
     }
+    p->pfold_mask[slot] = 0u;
     p->prop_s[slot] = NAN;
 }
 
@@ -654,6 +706,16 @@ mm_status ensure_prop(mm_plan *p, double s, int avoid, int *slot)
         std::vector<double> P = harmonic_propagator(p, v, s);
         mm_status st = upload_matrix(p, P.data(), p->n[v], p->n[v], true, &p->Pdev[k][v], &p->Ptc[k][v]);
         if (st) return st;
+        std::vector<double> D;
+        if (fold_enabled(p) && __builtin_popcount(p->pfold_mask[k]) < 5 && fold_matrix(P.data(), p->n[v], D)) {
+            if ((st = mm::tc_matrix_create(D.data(), p->n[v], p->n[v], p->npieces, p->fixed, &p->PFtc[k][v], p->tf32)))
+                return st;
+            p->pfold_mask[k] |= 1u << v;
+        }
+    }
+    if (p->pfold_mask[k] && !p->fold_buf && cudaMalloc(&p->fold_buf, size_t(p->count) * 8) != cudaSuccess) {
+        p->fold_buf = nullptr;
+        return fail(MM_ERR_OOM, "folded state buffer of %lld bytes", (long long)(p->count * 8));
     }
     p->prop_s[k] = s;
     *slot = k;
@@ -1233,51 +1295,12 @@ mm_status mumode_product(mm_ctx *ctx, int d, const int64_t *n, int mu, const dou
     return MM_OK;
 }
 
-// The folded form of a centrosymmetric n x n matrix E (interleaved complex, row-major): with F
-// the even/odd fold (fold_state) D = F E F^-1 is block-diagonal, an even block of ceil(n/2) rows
-// and an odd block of floor(n/2).  Returns false (D untouched) when E is not centrosymmetric to
-// 1e-13 of its largest entry; the off-diagonal blocks of D, rounding-sized then, are set to zero.
-bool fold_matrix(const double *E, int64_t n, std::vector<double> &D)
-{
-    using cd = std::complex<double>;
-    const cd *e = reinterpret_cast<const cd *>(E);
-    double amax = 0.0, asym = 0.0;
-    for (int64_t i = 0; i < n; ++i)
-        for (int64_t j = 0; j < n; ++j) {
-            amax = std::max(amax, std::abs(e[i * n + j]));
-            asym = std::max(asym, std::abs(e[i * n + j] - e[(n - 1 - i) * n + (n - 1 - j)]));
-        }
-    if (n < 2 || !(asym <= 1e-13 * amax)) return false;
-    const int64_t c = (n + 1) / 2, h = n / 2;
-    std::vector<cd> G(size_t(n * n)), R(size_t(n * n));
-    for (int64_t j = 0; j < n; ++j) {  // G = F E (rows)
-        for (int64_t k = 0; k < h; ++k) {
-            G[size_t(k * n + j)] = e[k * n + j] + e[(n - 1 - k) * n + j];
-            G[size_t((c + k) * n + j)] = e[k * n + j] - e[(n - 1 - k) * n + j];
-        }
-        if (n % 2) G[size_t(h * n + j)] = e[h * n + j];
-    }
-    for (int64_t i = 0; i < n; ++i) {  // R = G F^-1 (columns)
-        for (int64_t k = 0; k < h; ++k) {
-            R[size_t(i * n + k)] = 0.5 * (G[size_t(i * n + k)] + G[size_t(i * n + n - 1 - k)]);
-            R[size_t(i * n + c + k)] = 0.5 * (G[size_t(i * n + k)] - G[size_t(i * n + n - 1 - k)]);
-        }
-        if (n % 2) R[size_t(i * n + h)] = G[size_t(i * n + h)];
-    }
-    for (int64_t i = 0; i < n; ++i)
-        for (int64_t j = 0; j < n; ++j)
-            if ((i < c) != (j < c)) R[size_t(i * n + j)] = 0.0;
-    D.assign(reinterpret_cast<const double *>(R.data()), reinterpret_cast<const double *>(R.data()) + 2 * n * n);
-    return true;
-}
-
 // Fold the directions of a tensor-core Tucker plan whose matrices are centrosymmetric (at most
 // five; MM_NO_FOLD set to other than 0 turns it off), and allocate the folded state's buffer.
 mm_status fold_matrices(mm_plan *p, const double *const *E_host, bool Ec)
 {
     p->fold_mask = 0;
-    const char *off = std::getenv("MM_NO_FOLD");
-    if (!p->tc || p->hermite || p->dtype != MM_C64 || (off && off[0] && !(off[0] == '0' && off[1] == 0))) return MM_OK;
+    if (!fold_enabled(p) || p->hermite) return MM_OK;
     int folded = 0;
     for (int v = 0; v < p->d && folded < 5; ++v) {
         const int64_t n = p->n[v];
@@ -1547,12 +1570,23 @@ mm_status hermite_ho_step(mm_plan *p, void *psi, double tau, int64_t nsteps, voi
     return run_graphed(p, 1, psi, nsteps, s, tau, 0.0, [&]() -> mm_status {
         mm_status r;
         int cur = 0;
+        const unsigned fm = p->pfold_mask[slot];
         mm::TcMatrix *M[mm::kMaxDims];
-        for (int v = 0; v < p->d; ++v) M[v] = &p->Ptc[slot][v];
-        if ((r = tc_begin(p, M, psi, s))) return r;
+        for (int v = 0; v < p->d; ++v) M[v] = ((fm >> v) & 1u) ? &p->PFtc[slot][v] : &p->Ptc[slot][v];
+        // folded directions: the steps run on the folded state, folded and unfolded once per call
+        const void *src = psi;
+        if (fm) {
+            cudaError_t e = mm::fold_state(p->d, p->n, fm, false, psi, p->fold_buf, s);
+            if (e != cudaSuccess) return cuda_fail(e, "fold");
+            src = p->fold_buf;
+        }
+        if ((r = tc_begin(p, M, src, s))) return r;
         for (int64_t k = 0; k < nsteps; ++k)
             if ((r = tc_sweep(p, M, cur, mm::TcEpilogue{}, s))) return r;
-        return tc_end(p, cur, psi, s);
+        if (!fm) return tc_end(p, cur, psi, s);
+        if ((r = tc_end(p, cur, p->fold_buf, s))) return r;
+        cudaError_t e = mm::fold_state(p->d, p->n, fm, true, p->fold_buf, psi, s);
+        return e == cudaSuccess ? MM_OK : cuda_fail(e, "unfold");
     });
 }
 

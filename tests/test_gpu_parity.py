@@ -1171,6 +1171,36 @@ def test_fold_matches_unfolded(env, orc, monkeypatch, dims, mixed):
     assert rel(out[True], ora) <= TOL_MODE["f16x6"] * steps * len(dims)
 
 
+@pytest.mark.parametrize("m", [24, 25])
+def test_ho_fold_matches_unfolded(env, monkeypatch, m):
+    """Harmonic-oscillator steps of a Hermite plan run folded (the values-space propagators at
+    the symmetric Gauss-Hermite nodes are centrosymmetric): the result equals the unfolded
+    plan's to the precision's tolerance, for an even and an odd number of nodes; a GPE step on
+    the same plan (whose nonlinearity needs the values) is unchanged by folding."""
+    mm, ctx, torch = env
+    tau, steps = 0.05, 4
+    psi0 = inputs.complex_normal((m, m, m), seed=9).astype(np.complex64)
+    out, gpe = {}, {}
+    for fold in (True, False):
+        if fold:
+            monkeypatch.delenv("MM_NO_FOLD", raising=False)
+        else:
+            monkeypatch.setenv("MM_NO_FOLD", "1")
+        hp = mm.HermitePlan(ctx, [m] * 3, prec="f16x6")
+        u = to_gpu(torch, psi0, torch.complex64)
+        hp.ho_step(u, tau, steps)
+        g = to_gpu(torch, psi0, torch.complex64)
+        hp.gpe_step(g, 10.0, 1e-3, 2)
+        torch.cuda.synchronize()
+        ctx.status()
+        out[fold], gpe[fold] = u.cpu().numpy(), g.cpu().numpy()
+    monkeypatch.delenv("MM_NO_FOLD", raising=False)
+    d = rel(out[True], out[False])
+    print(f"HO fold vs unfolded m={m}: {d:.3e}")
+    assert d <= TOL_MODE["f16x6"] * steps * 3
+    assert np.array_equal(gpe[True].view(np.uint32), gpe[False].view(np.uint32))
+
+
 def test_autotune_cache(env, orc, tmp_path, monkeypatch):
     """With MM_AUTOTUNE_CACHE set, the first tuning of a plan appends one JSON
     line; a second plan with the same key takes that configuration without
