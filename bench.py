@@ -359,6 +359,17 @@ def main():
     issued_per_step = plan.issued_flops()
     issued = issued_per_step / 3 / kern_avg_s / 1e12
 
+    # the same steps with even/odd folding off, as context (the default folds: E is centrosymmetric)
+    fold_mask = plan.fold()
+    unfolded = None
+    if fold_mask:
+        plan.set_fold(False)
+        plan.step(u, args.steps)
+        torch.cuda.synchronize()
+        ms_unf = _time(lambda: plan.step(u, args.steps), stream)
+        plan.set_fold(True)
+        unfolded = {"steps_per_s": world * args.steps / (ms_unf / 1e3), "ms_per_step": ms_unf / args.steps}
+
     # end to end through the public host API: one 50-step trajectory per call
     u_host = torch.from_numpy(u0.copy()).pin_memory()
     plan.step_host(u_host, STEPS_PER_TRAJECTORY)  # warm
@@ -425,6 +436,8 @@ def main():
             "data": "synthetic",
             "config": {"workload": WORKLOAD, "n": N, "tau": TAU, "precision": args.prec,
                        "kernel_variant": tuned_variant, "mode_order": list(tuned_order),
+                       "fold": (f"even/odd, directions mask {fold_mask} (centrosymmetric E: block-diagonal "
+                                "half-size products on the folded state)") if fold_mask else "none",
                        "parallelism": f"replicas x{world}" if world > 1 else "single GPU",
                        "l2": "working set 537 MB > 126 MB L2, no flush"},
             "tflops_algorithmic": FLOP_PER_STEP * value / world / 1e12,
@@ -461,6 +474,8 @@ def main():
             "exp_setup_ms": exp_ms, "exp_host_pade_ms": exp_host_ms, "exp_device_vs_host_max_abs": exp_diff,
         }
         line.update(extra)
+        if unfolded:
+            line["unfolded"] = {"steps_per_s": unfolded["steps_per_s"], "ms_per_step": unfolded["ms_per_step"]}
         print(json.dumps(line), flush=True)
     if dist:
         dist.destroy_process_group()

@@ -355,6 +355,25 @@ mm_status mm_plan_set_config(mm_plan *plan, int variant, const int *order);
  * kernel timing is on.  Turning graphs off frees the cached graphs. */
 mm_status mm_plan_set_graphs(mm_plan *plan, int enable);
 
+/* Even/odd folding (not from the paper; on by default).  A direction
+ * whose matrix is centrosymmetric (E_ij = E_(n-1-i, n-1-j): the
+ * Dirichlet finite-difference propagators, Hermite propagators of even
+ * potentials at the symmetric Gauss-Hermite nodes) acts on the folded
+ * vector (x_k + x_(n-1-k) for k < n/2, then x_k - x_(n-1-k); the middle
+ * entry of an odd n as it is) as a block-diagonal matrix of two half-size
+ * blocks, which the tensor-core kernels run as half-size products.  With
+ * folding on, the steps of a tensor-core Tucker plan (mumode_step, its
+ * batches) and the harmonic-oscillator steps of a Hermite plan fold the
+ * state once per call, run on the folded state and unfold it at the end;
+ * the results agree with the unfolded form to the precision's rounding.
+ * Plans on complex64 data only; MM_NO_FOLD set (to other than 0) when a
+ * plan is made turns it off for that plan.  mm_plan_get_fold reports the
+ * folded directions (bit v: direction v + 1; 0: none) and
+ * mm_plan_set_fold turns folding off (0) or back on; it drops the plan's
+ * captured graphs.  Errors: MM_ERR_INVALID_ARG. */
+mm_status mm_plan_get_fold(const mm_plan *plan, int *mask_out);
+mm_status mm_plan_set_fold(mm_plan *plan, int enable);
+
 /* Tensor-core flops (2 M N K summed over the issued MMAs) of one step of a
  * tensor-core Tucker plan: all piece products, the zero padding, and none
  * of the matrix blocks skipped because every piece of them is zero.  For

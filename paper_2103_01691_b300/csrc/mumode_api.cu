@@ -85,7 +85,9 @@ struct mm_plan {
     // Even/odd folding (Tucker plans on the tensor cores): the directions whose matrix is
     // centrosymmetric hold it folded, block-diagonal (Dtc); a step call folds the state once,
     // runs its steps on the folded state and unfolds it once (fold_buf: a complex64 state)
-    unsigned fold_mask = 0;
+    unsigned fold_mask = 0;   // the directions the steps run folded (0 when folding is off)
+    unsigned fold_avail = 0;  // the directions that can fold (Tucker plans: Dtc built)
+    bool fold_on = true;      // mm_plan_set_fold
     mm::TcMatrix Dtc[mm::kMaxDims] = {};
     void *fold_buf = nullptr;
     // workspace
@@ -1025,6 +1027,25 @@ mm_status mm_plan_set_graphs(mm_plan *p, int enable)
     return MM_OK;
 }
 
+mm_status mm_plan_get_fold(const mm_plan *p, int *mask_out)
+{
+    if (!p || !mask_out) return fail(MM_ERR_INVALID_ARG, "NULL argument");
+    unsigned m = p->fold_mask;
+    if (p->hermite) m = p->fold_on ? (p->pfold_mask[0] | p->pfold_mask[1]) : 0u;
+    *mask_out = int(m);
+    return MM_OK;
+}
+
+mm_status mm_plan_set_fold(mm_plan *p, int enable)
+{
+    if (!p) return fail(MM_ERR_INVALID_ARG, "plan is NULL");
+    drop_graphs(p);
+    p->fold_on = enable != 0;
+    p->fold_mask = p->fold_on ? p->fold_avail : 0u;
+    p->chain_steps = -1;  // the chained records hold the matrices of the previous setting
+    return MM_OK;
+}
+
 const char *mm_last_error(void) { return mm::g_err; }
 
 int64_t mm_launch_count(void) { return mm::g_launches.load(); }
@@ -1311,6 +1332,7 @@ mm_status fold_matrices(mm_plan *p, const double *const *E_host, bool Ec)
         p->fold_mask |= 1u << v;
         ++folded;
     }
+    p->fold_avail = p->fold_mask;
     if (p->fold_mask && cudaMalloc(&p->fold_buf, size_t(p->count) * 8) != cudaSuccess) {
         p->fold_buf = nullptr;
         return fail(MM_ERR_OOM, "folded state buffer of %lld bytes", (long long)(p->count * 8));
@@ -1570,7 +1592,7 @@ mm_status hermite_ho_step(mm_plan *p, void *psi, double tau, int64_t nsteps, voi
     return run_graphed(p, 1, psi, nsteps, s, tau, 0.0, [&]() -> mm_status {
         mm_status r;
         int cur = 0;
-        const unsigned fm = p->pfold_mask[slot];
+        const unsigned fm = p->fold_on ? p->pfold_mask[slot] : 0u;
         mm::TcMatrix *M[mm::kMaxDims];
         for (int v = 0; v < p->d; ++v) M[v] = ((fm >> v) & 1u) ? &p->PFtc[slot][v] : &p->Ptc[slot][v];
         // folded directions: the steps run on the folded state, folded and unfolded once per call
@@ -1970,6 +1992,7 @@ extern "C" mm_status split_step_gpe_adjoint(mm_plan *p, const void *psi0, const 
 struct mm_batch {
     mm_ctx *ctx = nullptr;
     std::vector<mm_plan *> plans;
+    std::vector<unsigned> fold;  // each plan's folded directions when the batch was made (its records)
     int d = 0;
     mm_prec prec = MM_PREC_F16X6;
     bool fixed = false;
@@ -2059,6 +2082,7 @@ extern "C" mm_status mumode_batch_create(mm_ctx *ctx, mm_plan *const *plans, int
     auto *b = new mm_batch;
     b->ctx = ctx;
     b->plans.assign(plans, plans + nprob);
+    for (int k = 0; k < nprob; ++k) b->fold.push_back(plans[k]->fold_mask);
     b->d = p0->d;
     b->prec = p0->prec;
     b->fixed = p0->fixed;
@@ -2133,11 +2157,12 @@ extern "C" mm_status mumode_batch_step(mm_batch *b, void *const *u_dev, int64_t 
             cudaError_t e = cudaMemsetAsync(p->d_max, 0, sizeof(unsigned) * d, s);  // max words of sweep 0
             if (e != cudaSuccess) return cuda_fail(e, "max words");
         }
+        const unsigned fm = b->fold[k];
         mm::TcMatrix *M[mm::kMaxDims];
-        for (int v = 0; v < d; ++v) M[v] = step_matrix(p, v);
+        for (int v = 0; v < d; ++v) M[v] = ((fm >> v) & 1u) ? &p->Dtc[v] : &p->Etc[v];
         const void *src = u_dev[k];
-        if (p->fold_mask) {  // folded directions, as in mumode_step
-            cudaError_t e = mm::fold_state(p->d, p->n, p->fold_mask, false, u_dev[k], p->fold_buf, s);
+        if (fm) {  // folded directions, as in mumode_step
+            cudaError_t e = mm::fold_state(p->d, p->n, fm, false, u_dev[k], p->fold_buf, s);
             if (e != cudaSuccess) return cuda_fail(e, "fold");
             src = p->fold_buf;
         }
@@ -2160,13 +2185,14 @@ extern "C" mm_status mumode_batch_step(mm_batch *b, void *const *u_dev, int64_t 
     const int cur = int((nsteps * d) % 2);
     for (size_t k = 0; k < b->plans.size(); ++k) {
         mm_plan *p = b->plans[k];
+        const unsigned fm = b->fold[k];
         p->sweep = nsteps;  // the batched launches ran nsteps sweeps of every plan
-        if (!p->fold_mask) {
+        if (!fm) {
             if ((st = tc_end(p, cur, u_dev[k], s))) return st;
             continue;
         }
         if ((st = tc_end(p, cur, p->fold_buf, s))) return st;
-        cudaError_t e = mm::fold_state(p->d, p->n, p->fold_mask, true, p->fold_buf, u_dev[k], s);
+        cudaError_t e = mm::fold_state(p->d, p->n, fm, true, p->fold_buf, u_dev[k], s);
         if (e != cudaSuccess) return cuda_fail(e, "unfold");
     }
     return MM_OK;
@@ -2320,9 +2346,11 @@ extern "C" mm_status mm_expm_device(mm_ctx *ctx, int n, const double *A_dev, con
 static mm_status set_matrix_device(mm_plan *p, int mu, const double2 *E, double row_norm_bound, cudaStream_t s)
 {
     // the direction's new matrix is not folded: later steps use it as it is (the fold is per call)
-    if ((p->fold_mask >> (mu - 1)) & 1u) {
+    if ((p->fold_avail >> (mu - 1)) & 1u) {
         drop_graphs(p);
         p->fold_mask &= ~(1u << (mu - 1));
+        p->fold_avail &= ~(1u << (mu - 1));
+        p->chain_steps = -1;  // chained records point at the folded matrix
     }
     const int v = mu - 1;
     if (p->tf32) return fail(MM_ERR_UNSUPPORTED, "device matrix updates do not serve MM_PREC_TF32X3 plans");

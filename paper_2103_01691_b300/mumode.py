@@ -47,6 +47,8 @@ SIGNATURES = {
     "mumode_step_host": (_i, [_vp, _vp, _i64, _vp]),
     "mm_plan_destroy": (None, [_vp]),
     "mm_plan_set_graphs": (_i, [_vp, _i]),
+    "mm_plan_get_fold": (_i, [_vp, ctypes.POINTER(_i)]),
+    "mm_plan_set_fold": (_i, [_vp, _i]),
     "mm_plan_issued_flops": (_i, [_vp, _dp]),
     "mumode_batch_create": (_i, [_vp, ctypes.POINTER(_vp), _i, ctypes.POINTER(_vp)]),
     "mumode_batch_step": (_i, [_vp, ctypes.POINTER(_vp), _i64, _vp]),
@@ -325,6 +327,15 @@ class _Tunable:
 
     def set_graphs(self, enable: bool):
         _check(lib().mm_plan_set_graphs(self.handle, int(enable)))
+
+    def fold(self) -> int:
+        """mm_plan_get_fold: the directions the steps run folded (bit v: direction v + 1)."""
+        m = _i()
+        _check(lib().mm_plan_get_fold(self.handle, ctypes.byref(m)))
+        return m.value
+
+    def set_fold(self, enable: bool):
+        _check(lib().mm_plan_set_fold(self.handle, int(enable)))
 
     def set_config(self, variant: str, order=None):
         optr = (_i * len(order))(*order) if order is not None else None

@@ -1164,6 +1164,18 @@ def test_fold_matches_unfolded(env, orc, monkeypatch, dims, mixed):
         ctx.status()
         out[fold] = u.cpu().numpy()
     monkeypatch.delenv("MM_NO_FOLD", raising=False)
+    # the folded directions, and folding turned off on the plan: the unfolded plan's bits
+    plan = mm.TuckerPlan(ctx, dims, Es, prec="f16x6")
+    want = sum(1 << v for v, n in enumerate(dims) if n > 1 and not (mixed and v == len(dims) - 1))
+    assert plan.fold() == want
+    plan.set_fold(False)
+    assert plan.fold() == 0
+    u = to_gpu(torch, u0, torch.complex64)
+    plan.step(u, steps)
+    torch.cuda.synchronize()
+    assert np.array_equal(u.cpu().numpy().view(np.uint32), out[False].view(np.uint32))
+    plan.set_fold(True)
+    assert plan.fold() == want
     d = rel(out[True], out[False])
     ora = orc.tucker(u0.astype(complex), [np.asarray(E, dtype=complex) for E in Es], nsteps=steps)
     print(f"fold vs unfolded dims={dims} mixed={mixed}: {d:.3e}; vs oracle {rel(out[True], ora):.3e}")
