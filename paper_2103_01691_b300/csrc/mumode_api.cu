@@ -68,6 +68,7 @@ struct mm_plan {
     // completion counters, kept for the last nsteps used
     int64_t chain_steps = -1;
     int chain_order[mm::kMaxDims] = {};
+    unsigned chain_fold = 0;  // the folded directions the records were built for
     int chain_nprod = 0;
     std::vector<uint8_t> chain_host;
     void *chain_dev = nullptr;
@@ -88,6 +89,7 @@ struct mm_plan {
     unsigned fold_mask = 0;   // the directions the steps run folded (0 when folding is off)
     unsigned fold_avail = 0;  // the directions that can fold (Tucker plans: Dtc built)
     bool fold_on = true;      // mm_plan_set_fold
+    bool fold_force = false;  // MM_FOLD_ALWAYS at plan creation: fold every call, however short (tests)
     mm::TcMatrix Dtc[mm::kMaxDims] = {};
     void *fold_buf = nullptr;
     // workspace
@@ -319,6 +321,24 @@ const mm::TcMatrix *step_matrix(const mm_plan *p, int v)
     return ((p->fold_mask >> v) & 1u) ? &p->Dtc[v] : &p->Etc[v];
 }
 
+// Whether a call of nsteps steps should run folded: the tensor-core work the folded matrices save
+// (issued flops, at 1.5 PFLOP/s) must exceed the fold and unfold passes (two reads and two writes
+// of the complex64 state, at 6.5 TB/s).  Banded matrices save a few blocks per row tile and fold
+// from about four steps per call; dense ones save half of every product and fold from one.
+bool fold_pays(const mm_plan *p, unsigned mask, mm::TcMatrix *const *unfolded, mm::TcMatrix *const *folded,
+               int64_t nsteps)
+{
+    if (!mask) return false;
+    if (p->fold_force) return true;
+    double saved = 0.0;
+    for (int v = 0; v < p->d; ++v)
+        if ((mask >> v) & 1u)
+            saved += mm::tc_issued_flops(p->st, v + 1, *unfolded[v], p->prec, p->variant) -
+                     mm::tc_issued_flops(p->st, v + 1, *folded[v], p->prec, p->variant);
+    const double cost_s = 4.0 * double(p->count) * 8.0 / 6.5e12;
+    return double(nsteps) * saved / 1.5e15 > cost_s;
+}
+
 // One Tucker sweep on the TC piece state: modes in plan order with
 // matrices M[mu-1]; cur is the index of the buffer holding the state.
 mm_status tc_sweep(mm_plan *p, mm::TcMatrix *const *M, int &cur, const mm::TcEpilogue &last_epi, cudaStream_t s)
@@ -365,10 +385,11 @@ mm_status tc_sweep(mm_plan *p, mm::TcMatrix *const *M, int &cur, const mm::TcEpi
 // row tiles of different sizes, too many products); the caller launches them one by one.
 void drop_graphs(mm_plan *p);
 
-bool chain_prepare(mm_plan *p, int64_t nsteps)
+bool chain_prepare(mm_plan *p, int64_t nsteps, unsigned fold)
 {
     const int d = p->d;
-    if (p->chain_steps == nsteps && std::equal(p->order, p->order + d, p->chain_order)) return true;
+    if (p->chain_steps == nsteps && p->chain_fold == fold && std::equal(p->order, p->order + d, p->chain_order))
+        return true;
     if (!p->tc || !p->fixed || p->hermite || nsteps < 1 || nsteps * d > (int64_t(1) << 20)) return false;
     const int nprod = int(nsteps * d);
     const size_t rb = mm::tc_pair_record_bytes(), al = mm::tc_pair_record_align();
@@ -407,7 +428,8 @@ bool chain_prepare(mm_plan *p, int64_t nsteps)
             bool km = false;
             int64_t items = 0;
             void *rec = base + rb * size_t(pos);
-            if (mm::tc_pair_record_build(p->st, p->st, mu, *step_matrix(p, mu - 1), p->prec, p->work[pos % 3],
+            const mm::TcMatrix &Mq = ((fold >> (mu - 1)) & 1u) ? p->Dtc[mu - 1] : p->Etc[mu - 1];
+            if (mm::tc_pair_record_build(p->st, p->st, mu, Mq, p->prec, p->work[pos % 3],
                                          p->work[(pos + 1) % 3], sc, rec, &km, &items, pos) != cudaSuccess) {
                 cudaFree(done);
                 return false;
@@ -435,6 +457,7 @@ bool chain_prepare(mm_plan *p, int64_t nsteps)
     p->chain_done = done;
     p->chain_nprod = nprod;
     p->chain_steps = nsteps;
+    p->chain_fold = fold;
     std::copy(p->order, p->order + d, p->chain_order);
     return true;
 }
@@ -603,6 +626,10 @@ mm_status plan_common(mm_ctx *ctx, int d, const int64_t *n, mm_dtype dtype, mm_p
     p->tf32 = mm::tc_tf32(prec);
     p->npieces = mm::tc_pieces(prec);
     p->variant = p->tf32 ? mm::kTcOneSM : mm::tc_default_variant();
+    {
+        const char *fa = std::getenv("MM_FOLD_ALWAYS");
+        p->fold_force = fa && fa[0] && !(fa[0] == '0' && fa[1] == 0);
+    }
     *made = p;
     return MM_OK;
 }
@@ -1387,17 +1414,23 @@ mm_status mumode_step(mm_plan *p, void *u_dev, int64_t nsteps, void *stream)
             return MM_OK;
         });
     }
+    // folded directions (when the call is long enough to pay for it): the steps run on the folded
+    // state, folded and unfolded once per call
+    mm::TcMatrix *M[mm::kMaxDims], *U[mm::kMaxDims], *D[mm::kMaxDims];
+    for (int v = 0; v < p->d; ++v) {
+        U[v] = &p->Etc[v];
+        D[v] = &p->Dtc[v];
+    }
+    const unsigned fm = fold_pays(p, p->fold_mask, U, D, nsteps) ? p->fold_mask : 0u;
+    for (int v = 0; v < p->d; ++v) M[v] = ((fm >> v) & 1u) ? D[v] : U[v];
     // kTcChain: every product of the call in one persistent launch (records prepared outside any capture)
-    const bool chained = p->variant == mm::kTcChain && chain_prepare(p, nsteps);
+    const bool chained = p->variant == mm::kTcChain && chain_prepare(p, nsteps, fm);
     return run_graphed(p, 0, u_dev, nsteps, s, 0.0, 0.0, [&]() -> mm_status {
         mm_status r;
         int cur = 0;
-        mm::TcMatrix *M[mm::kMaxDims];
-        for (int v = 0; v < p->d; ++v) M[v] = step_matrix(p, v);
-        // folded directions: the steps run on the folded state, folded and unfolded once per call
         const void *src = u_dev;
-        if (p->fold_mask) {
-            cudaError_t e = mm::fold_state(p->d, p->n, p->fold_mask, false, u_dev, p->fold_buf, s);
+        if (fm) {
+            cudaError_t e = mm::fold_state(p->d, p->n, fm, false, u_dev, p->fold_buf, s);
             if (e != cudaSuccess) return cuda_fail(e, "fold");
             src = p->fold_buf;
         }
@@ -1408,9 +1441,9 @@ mm_status mumode_step(mm_plan *p, void *u_dev, int64_t nsteps, void *stream)
             for (int64_t k = 0; k < nsteps; ++k)
                 if ((r = tc_sweep(p, M, cur, mm::TcEpilogue{}, s))) return r;
         }
-        if (!p->fold_mask) return tc_end(p, cur, u_dev, s);
+        if (!fm) return tc_end(p, cur, u_dev, s);
         if ((r = tc_end(p, cur, p->fold_buf, s))) return r;
-        cudaError_t e = mm::fold_state(p->d, p->n, p->fold_mask, true, p->fold_buf, u_dev, s);
+        cudaError_t e = mm::fold_state(p->d, p->n, fm, true, p->fold_buf, u_dev, s);
         return e == cudaSuccess ? MM_OK : cuda_fail(e, "unfold");
     });
 }
@@ -1592,9 +1625,13 @@ mm_status hermite_ho_step(mm_plan *p, void *psi, double tau, int64_t nsteps, voi
     return run_graphed(p, 1, psi, nsteps, s, tau, 0.0, [&]() -> mm_status {
         mm_status r;
         int cur = 0;
-        const unsigned fm = p->fold_on ? p->pfold_mask[slot] : 0u;
-        mm::TcMatrix *M[mm::kMaxDims];
-        for (int v = 0; v < p->d; ++v) M[v] = ((fm >> v) & 1u) ? &p->PFtc[slot][v] : &p->Ptc[slot][v];
+        mm::TcMatrix *M[mm::kMaxDims], *U[mm::kMaxDims], *D[mm::kMaxDims];
+        for (int v = 0; v < p->d; ++v) {
+            U[v] = &p->Ptc[slot][v];
+            D[v] = &p->PFtc[slot][v];
+        }
+        const unsigned fm = p->fold_on && fold_pays(p, p->pfold_mask[slot], U, D, nsteps) ? p->pfold_mask[slot] : 0u;
+        for (int v = 0; v < p->d; ++v) M[v] = ((fm >> v) & 1u) ? D[v] : U[v];
         // folded directions: the steps run on the folded state, folded and unfolded once per call
         const void *src = psi;
         if (fm) {

@@ -478,6 +478,56 @@ __global__ void fold_kernel(FoldDims f, int64_t reps, const float2 *__restrict__
     }
 }
 
+// The same when every folded direction has even length (every orbit has 2^F points, F the number of
+// folded directions): the orbit lives in registers, indices in 32 bits.
+template <int F, bool INV>
+__global__ void fold_kernel_even(FoldDims f, uint32_t reps, int p0, int p1, int p2, const float2 *__restrict__ in,
+                                 float2 *__restrict__ out)
+{
+    const int pv[3] = {p0, p1, p2};
+    for (uint32_t t = blockIdx.x * blockDim.x + threadIdx.x; t < reps; t += gridDim.x * blockDim.x) {
+        uint32_t q = t, base = 0, mir[3], odd[3];
+        for (int v = 0; v < f.d; ++v) {
+            const uint32_t rep = uint32_t(f.rep[v]), r = q % rep;
+            q /= rep;
+            base += r * uint32_t(f.stride[v]);
+#pragma unroll
+            for (int b = 0; b < F; ++b)
+                if (pv[b] == v) {
+                    mir[b] = (uint32_t(f.n[v]) - 1u - 2u * r) * uint32_t(f.stride[v]);
+                    odd[b] = uint32_t(f.c[v]) * uint32_t(f.stride[v]);
+                }
+        }
+        float2 buf[1 << F];
+#pragma unroll
+        for (int sp = 0; sp < (1 << F); ++sp) {
+            uint32_t off = base;
+#pragma unroll
+            for (int b = 0; b < F; ++b)
+                if ((sp >> b) & 1) off += INV ? odd[b] : mir[b];
+            buf[sp] = in[off];
+        }
+#pragma unroll
+        for (int b = 0; b < F; ++b)
+#pragma unroll
+            for (int sp = 0; sp < (1 << F); ++sp)
+                if (!((sp >> b) & 1)) {
+                    const float2 a = buf[sp], z = buf[sp | (1 << b)];
+                    const float h = INV ? 0.5f : 1.0f;
+                    buf[sp] = make_float2(h * (a.x + z.x), h * (a.y + z.y));
+                    buf[sp | (1 << b)] = make_float2(h * (a.x - z.x), h * (a.y - z.y));
+                }
+#pragma unroll
+        for (int sp = 0; sp < (1 << F); ++sp) {
+            uint32_t off = base;
+#pragma unroll
+            for (int b = 0; b < F; ++b)
+                if ((sp >> b) & 1) off += INV ? mir[b] : odd[b];
+            out[off] = buf[sp];
+        }
+    }
+}
+
 cudaError_t fold_state(int d, const int64_t *n, unsigned mask, bool inverse, const void *in, void *out, cudaStream_t s)
 {
     if (d < 1 || d > kMaxDims || in == out || __builtin_popcount(mask) > kMaxFold) return cudaErrorInvalidValue;
@@ -495,8 +545,31 @@ cudaError_t fold_state(int d, const int64_t *n, unsigned mask, bool inverse, con
         reps *= f.rep[v];
     }
     const int64_t blocks = (reps + 255) / 256 < 148 * 16 ? (reps + 255) / 256 : 148 * 16;
-    if (inverse) fold_kernel<true><<<unsigned(blocks), 256, 0, s>>>(f, reps, (const float2 *)in, (float2 *)out);
-    else fold_kernel<false><<<unsigned(blocks), 256, 0, s>>>(f, reps, (const float2 *)in, (float2 *)out);
+    // the fast form: at most three folded directions, all of even length, 32-bit offsets
+    int pv[3] = {0, 0, 0}, F = 0;
+    bool even = stride < (int64_t(1) << 31);
+    for (int v = 0; v < d; ++v)
+        if ((mask >> v) & 1u) {
+            if (F < 3) pv[F] = v;
+            ++F;
+            even = even && n[v] % 2 == 0;
+        }
+    if (even && F >= 1 && F <= 3) {
+        const float2 *i2 = (const float2 *)in;
+        float2 *o2 = (float2 *)out;
+        const uint32_t r32 = uint32_t(reps);
+#define MM_FOLD(FF)                                                                                      \
+    (inverse ? (fold_kernel_even<FF, true><<<unsigned(blocks), 256, 0, s>>>(f, r32, pv[0], pv[1], pv[2], i2, o2), 0) \
+             : (fold_kernel_even<FF, false><<<unsigned(blocks), 256, 0, s>>>(f, r32, pv[0], pv[1], pv[2], i2, o2), 0))
+        if (F == 1) MM_FOLD(1);
+        else if (F == 2) MM_FOLD(2);
+        else MM_FOLD(3);
+#undef MM_FOLD
+    } else if (inverse) {
+        fold_kernel<true><<<unsigned(blocks), 256, 0, s>>>(f, reps, (const float2 *)in, (float2 *)out);
+    } else {
+        fold_kernel<false><<<unsigned(blocks), 256, 0, s>>>(f, reps, (const float2 *)in, (float2 *)out);
+    }
     count_launch();
     return cudaGetLastError();
 }

@@ -714,10 +714,12 @@ def test_fixed_point_wide_dynamic_range(env, orc):
     assert rel(u.cpu().numpy(), ref) <= TOL_MODE["f16x6"] * 9
 
 
-def test_graph_replay_matches_plain_launches(env):
+def test_graph_replay_matches_plain_launches(env, monkeypatch):
     """Steps replayed from a captured CUDA graph give the same bits as the
-    same steps launched one by one."""
+    same steps launched one by one (plans without folding, so that the
+    launch count is the products')."""
     mm, ctx, torch = env
+    monkeypatch.setenv("MM_NO_FOLD", "1")
     dims, tau = (48, 40, 32), 1e-4
     Es = [fd_schrodinger_E(mm, n, tau) for n in dims]
     u0 = inputs.complex_normal(dims[::-1], seed=2).astype(np.complex64)
@@ -736,9 +738,7 @@ def test_graph_replay_matches_plain_launches(env):
         n1 = mm.launch_count()
     torch.cuda.synchronize()
     assert torch.equal(u, ref)
-    # fold, max + split, 3 sweeps x 3 products, merge, unfold (the FD matrices are centrosymmetric,
-    # so the plan folds); counted per replay
-    assert n1 - n0 == 2 * (1 + 2 + 3 * 3 + 1 + 1)
+    assert n1 - n0 == 2 * (2 + 3 * 3 + 1)  # max + split, 3 sweeps x 3 products, merge; counted per replay
 
 
 @pytest.mark.parametrize("dims", [(16, 16, 16), (20, 24, 40)])
@@ -880,11 +880,13 @@ def test_gpe_autograd_gradient(env, orc):
 
 # ------------------------------------------------------- batched uneven problems
 
-def test_batched_uneven_problems(env, orc):
+def test_batched_uneven_problems(env, orc, monkeypatch):
     """Independent problems of uneven sizes (48..160 per direction) stepped
     in one launch per direction: identical to stepping each plan alone, and
-    within tolerance of the oracle."""
+    within tolerance of the oracle.  (A batch folds wherever its plans can;
+    the plans alone fold every call here too.)"""
     mm, ctx, torch = env
+    monkeypatch.setenv("MM_FOLD_ALWAYS", "1")
     dims = inputs.batched_dims(count=64, seed=3)[:6]
     us0 = inputs.batched_u0(inputs.batched_dims(count=64, seed=3), seed=3)[:6]
     tau, steps = 1e-4, 3
@@ -1144,6 +1146,7 @@ def test_fold_matches_unfolded(env, orc, monkeypatch, dims, mixed):
     precision's tolerance, and the oracle's: even and odd sizes, d = 1 to 4, and plans where one
     direction's matrix is not centrosymmetric (that direction stays unfolded)."""
     mm, ctx, torch = env
+    monkeypatch.setenv("MM_FOLD_ALWAYS", "1")  # fold every call, also where it would not pay
     tau, steps = 1e-4, 3
     Es = [fd_schrodinger_E(mm, n, tau) for n in dims]
     if mixed:  # the last direction: a random unitary matrix, not centrosymmetric
@@ -1190,6 +1193,7 @@ def test_ho_fold_matches_unfolded(env, monkeypatch, m):
     plan's to the precision's tolerance, for an even and an odd number of nodes; a GPE step on
     the same plan (whose nonlinearity needs the values) is unchanged by folding."""
     mm, ctx, torch = env
+    monkeypatch.setenv("MM_FOLD_ALWAYS", "1")
     tau, steps = 0.05, 4
     psi0 = inputs.complex_normal((m, m, m), seed=9).astype(np.complex64)
     out, gpe = {}, {}
