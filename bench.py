@@ -754,6 +754,14 @@ def other_workload(args):
                                   else plan.gpe_autotune(psi, beta, tau, nsteps=5)[0])
         plan.gpe_step(psi, beta, tau, K)
         ms = _time(lambda: plan.gpe_step(psi, beta, tau, K), stream)
+        line["fold"] = plan.fold()
+        if line["fold"]:
+            # the same steps with folding off (the phase in the last product's epilogue), for comparison
+            plan.set_fold(False)
+            plan.gpe_step(psi, beta, tau, K)
+            ms_unf = _time(lambda: plan.gpe_step(psi, beta, tau, K), stream)
+            plan.set_fold(True)
+            line["unfolded"] = {"steps_per_s": K / (ms_unf / 1e3), "ms_per_step": ms_unf / K}
         if not args.no_fp64:
             # the whole 500-step trajectory in F16X6 and in FP64 (warp-level FP64 MMA), for the accuracy fields
             traj = psi0.clone()

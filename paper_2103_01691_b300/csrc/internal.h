@@ -181,6 +181,11 @@ cudaError_t tc_split(const TcState &st, int npieces, bool fixed, const void *u_c
                      float *scale_out, unsigned *bound_words, const double *bounds, int nbounds, cudaStream_t s);
 // The TF32 forms: two 4-byte pieces per plane element (x0 = TF32 of x, x1 = TF32 of x - x0).
 cudaError_t tc_split_tf32(const TcState &st, const void *u_c64, void *pieces, cudaStream_t s);
+// The GPE nonlinear phase psi exp(-i tb |psi|^2) on an F16X6 piece state folded in the directions of
+// mask (at most five): unfold, phase, fold per orbit; input and output scale 2^grid_exponent(*max_in),
+// written to *s_out; values past the split's range set MM_ERR_RANGE in *err; in and out distinct.
+cudaError_t tc_phase_fold(const TcState &st, unsigned mask, const void *in_pieces, void *out_pieces,
+                          const unsigned *max_in, float *s_out, double tb, int *err, cudaStream_t s);
 cudaError_t tc_merge_tf32(const TcState &st, const void *pieces, void *u_c64, cudaStream_t s);
 // Sum the piece planes back into an interleaved complex64 tensor
 // (fixed-point mode: times *scale).

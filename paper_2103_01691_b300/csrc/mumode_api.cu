@@ -325,18 +325,23 @@ const mm::TcMatrix *step_matrix(const mm_plan *p, int v)
 // (issued flops, at 1.5 PFLOP/s) must exceed the fold and unfold passes (two reads and two writes
 // of the complex64 state, at 6.5 TB/s).  Banded matrices save a few blocks per row tile and fold
 // from about four steps per call; dense ones save half of every product and fold from one.
-bool fold_pays(const mm_plan *p, unsigned mask, mm::TcMatrix *const *unfolded, mm::TcMatrix *const *folded,
-               int64_t nsteps)
+double fold_saved_s(const mm_plan *p, unsigned mask, mm::TcMatrix *const *unfolded, mm::TcMatrix *const *folded)
 {
-    if (!mask) return false;
-    if (p->fold_force) return true;
     double saved = 0.0;
     for (int v = 0; v < p->d; ++v)
         if ((mask >> v) & 1u)
             saved += mm::tc_issued_flops(p->st, v + 1, *unfolded[v], p->prec, p->variant) -
                      mm::tc_issued_flops(p->st, v + 1, *folded[v], p->prec, p->variant);
+    return saved / 1.5e15;
+}
+
+bool fold_pays(const mm_plan *p, unsigned mask, mm::TcMatrix *const *unfolded, mm::TcMatrix *const *folded,
+               int64_t nsteps)
+{
+    if (!mask) return false;
+    if (p->fold_force) return true;
     const double cost_s = 4.0 * double(p->count) * 8.0 / 6.5e12;
-    return double(nsteps) * saved / 1.5e15 > cost_s;
+    return double(nsteps) * fold_saved_s(p, mask, unfolded, folded) > cost_s;
 }
 
 // One Tucker sweep on the TC piece state: modes in plan order with
@@ -1675,6 +1680,53 @@ mm_status gpe_steps(mm_plan *p, void *psi, double beta, double tau, int64_t nste
             if (e != cudaSuccess) return cuda_fail(e, "nonlinear phase");
         }
         return simt_sweep(p, p->Pdev[half], psi, s);
+    }
+    // Folded (F16X6, no norm, the half and full propagators folded alike, and long enough to pay for
+    // it): the linear sweeps run on the folded state with plain epilogues, and the nonlinear phase
+    // is a pass on the folded pieces between sweeps (unfold, phase, fold per orbit)
+    const unsigned fm = p->pfold_mask[half];
+    bool folded = p->fixed && !d_norm && p->fold_on && fm && p->pfold_mask[full] == fm;
+    if (folded) {
+        mm::TcMatrix *U[mm::kMaxDims], *D[mm::kMaxDims];
+        for (int v = 0; v < p->d; ++v) {
+            U[v] = &p->Ptc[full][v];
+            D[v] = &p->PFtc[full][v];
+        }
+        // the tensor work of nsteps + 1 sweeps saved against the fold and unfold (32 bytes a point)
+        // and the nsteps phase passes (the pieces read and written: 24 bytes a point each)
+        const double cost_s = double(32 + 24 * nsteps) * double(p->count) / 6.5e12;
+        folded = p->fold_force || double(nsteps + 1) * fold_saved_s(p, fm, U, D) > cost_s;
+    }
+    if (folded) {
+        return run_graphed(p, 6, psi, nsteps, s, tau, beta, [&]() -> mm_status {
+            mm_status r;
+            int cur = 0;
+            mm::TcMatrix *Mh[mm::kMaxDims], *Mf[mm::kMaxDims];
+            for (int v = 0; v < p->d; ++v) {
+                Mh[v] = ((fm >> v) & 1u) ? &p->PFtc[half][v] : &p->Ptc[half][v];
+                Mf[v] = ((fm >> v) & 1u) ? &p->PFtc[full][v] : &p->Ptc[full][v];
+            }
+            cudaError_t e = mm::fold_state(p->d, p->n, fm, false, psi, p->fold_buf, s);
+            if (e != cudaSuccess) return cuda_fail(e, "fold");
+            if ((r = tc_begin(p, Mh, p->fold_buf, s))) return r;
+            for (int64_t k = 0; k < nsteps; ++k) {
+                const int64_t sw = p->sweep;  // the sweep about to run (tc_sweep's word rotation)
+                if ((r = tc_sweep(p, k == 0 ? Mh : Mf, cur, mm::TcEpilogue{}, s))) return r;
+                // its last product took its output scale from the maximum word W[sw - 1 mod 3][d - 1],
+                // and the next sweep's first product reads its input scale from S[sw + 1 mod 2][0]
+                const int d = p->d, t = int(sw % 3);
+                const unsigned *max_in = p->d_max + ((t + 2) % 3) * d + (d - 1);
+                float *s_next = p->d_scale + int((sw + 1) & 1) * d;
+                e = mm::tc_phase_fold(p->st, fm, p->work[cur], p->work[1 - cur], max_in, s_next, tb, p->ctx->d_err,
+                                      s);
+                if (e != cudaSuccess) return cuda_fail(e, "nonlinear phase on the folded state");
+                cur = 1 - cur;
+            }
+            if ((r = tc_sweep(p, Mh, cur, mm::TcEpilogue{}, s))) return r;
+            if ((r = tc_end(p, cur, p->fold_buf, s))) return r;
+            e = mm::fold_state(p->d, p->n, fm, true, p->fold_buf, psi, s);
+            return e == cudaSuccess ? MM_OK : cuda_fail(e, "unfold");
+        });
     }
     return run_graphed(p, d_norm ? 5 : 2, psi, nsteps, s, tau, beta, [&]() -> mm_status {
         mm_status r;

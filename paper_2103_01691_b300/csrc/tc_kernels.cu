@@ -871,6 +871,264 @@ cudaError_t tc_split(const TcState &st, int npieces, bool fixed, const void *u_c
     return cudaGetLastError();
 }
 
+// The GPE nonlinear phase on a folded F16X6 piece state (even/odd folding in the directions of
+// `mask`): each thread takes one orbit of the mirror maps, merges its points' pieces (input scale
+// 2^grid_exponent(*max_in), the scale the product before wrote them with), unfolds them into point
+// values, applies psi -> psi exp(-i tb |psi|^2) at each point, folds them back and splits them on
+// the input's grid, and writes them to `out`.  The phase keeps every point's modulus, so a folded
+// value grows by at most 2^f (f folded directions) and in practice hardly at all; the split takes
+// values up to 16 times past the grid's bound of 1024 (the products' headroom for their predicted
+// scales) and reports larger ones as MM_ERR_RANGE in *err.  Block 0 writes the scale to *s_out,
+// which the next product reads as its input scale.
+struct PhaseFoldDims {
+    int d;
+    int64_t n[kMaxDims], c[kMaxDims], h[kMaxDims], pstride[kMaxDims], rep[kMaxDims];
+    unsigned mask;
+};
+
+__global__ void phase_fold_kernel(PhaseFoldDims g, int64_t reps, int64_t plane, const uint16_t *__restrict__ in,
+                                  uint16_t *__restrict__ out, const unsigned *max_in, float *s_out, float tb,
+                                  int *err)
+{
+    const int es = grid_exponent(__uint_as_float(*max_in));
+    const float s_in = ldexpf(1.0f, es), inv_out = ldexpf(1.0f, -es);
+    if (blockIdx.x == 0 && threadIdx.x == 0) *s_out = s_in;
+    bool range_ok = true;
+    for (int64_t t = blockIdx.x * int64_t(blockDim.x) + threadIdx.x; t < reps; t += int64_t(gridDim.x) * blockDim.x) {
+        int64_t r[kMaxDims], q = t, base = 0;
+        int pv[5], m = 0;
+        for (int v = 0; v < g.d; ++v) {
+            r[v] = q % g.rep[v];
+            q /= g.rep[v];
+            base += r[v] * g.pstride[v];
+            if (((g.mask >> v) & 1u) && r[v] < g.h[v] && m < 5) pv[m++] = v;
+        }
+        const int cnt = 1 << m;
+        float2 z[32];
+        int64_t off[32];
+        for (int sp = 0; sp < cnt; ++sp) {
+            int64_t o = base;
+            for (int b = 0; b < m; ++b)
+                if ((sp >> b) & 1) o += g.c[pv[b]] * g.pstride[pv[b]];
+            off[sp] = o;
+            float v2[2];
+            for (int c = 0; c < 2; ++c) {
+                const float x0 = __half2float(__ushort_as_half(in[(3 * c + 0) * plane + o]));
+                const float x1 = __half2float(__ushort_as_half(in[(3 * c + 1) * plane + o]));
+                const float x2 = __half2float(__ushort_as_half(in[(3 * c + 2) * plane + o]));
+                v2[c] = s_in * (x0 + (x1 + x2));
+            }
+            z[sp] = make_float2(v2[0], v2[1]);
+        }
+        // unfold, phase at each point, fold
+        for (int b = 0; b < m; ++b)
+            for (int sp = 0; sp < cnt; ++sp)
+                if (!((sp >> b) & 1)) {
+                    const float2 a = z[sp], e = z[sp | (1 << b)];
+                    z[sp] = make_float2(0.5f * (a.x + e.x), 0.5f * (a.y + e.y));
+                    z[sp | (1 << b)] = make_float2(0.5f * (a.x - e.x), 0.5f * (a.y - e.y));
+                }
+        for (int sp = 0; sp < cnt; ++sp) {
+            const float xr = z[sp].x, xi = z[sp].y;
+            float sn, cs;
+            sincosf(tb * (xr * xr + xi * xi), &sn, &cs);
+            z[sp] = make_float2(xr * cs + xi * sn, xi * cs - xr * sn);
+        }
+        for (int b = 0; b < m; ++b)
+            for (int sp = 0; sp < cnt; ++sp)
+                if (!((sp >> b) & 1)) {
+                    const float2 a = z[sp], e = z[sp | (1 << b)];
+                    z[sp] = make_float2(a.x + e.x, a.y + e.y);
+                    z[sp | (1 << b)] = make_float2(a.x - e.x, a.y - e.y);
+                }
+        for (int sp = 0; sp < cnt; ++sp) {
+            uint16_t br[3], bi[3];
+            const float xr = z[sp].x * inv_out, xi = z[sp].y * inv_out;
+            range_ok &= fabsf(xr) < 16384.0f && fabsf(xi) < 16384.0f;
+            split_fx_scaled(xr, br[0], br[1], br[2]);
+            split_fx_scaled(xi, bi[0], bi[1], bi[2]);
+            for (int p = 0; p < 3; ++p) {
+                out[p * plane + off[sp]] = br[p];
+                out[(3 + p) * plane + off[sp]] = bi[p];
+            }
+        }
+    }
+    if (!range_ok && err) atomicCAS(err, 0, MM_ERR_RANGE);
+}
+
+// The same when every folded direction has even length (every orbit has 2^F points, F at most 3)
+// and the pieces fit 32-bit offsets: the orbit lives in registers.  Each thread takes the orbits of
+// V consecutive points of direction 1 (V pieces per load and store: a warp's access to a plane
+// covers 128 contiguous bytes for V = 2).
+template <int V>
+struct PiecesV;
+template <>
+struct PiecesV<1> {
+    using T = uint16_t;
+};
+template <>
+struct PiecesV<2> {
+    using T = uint32_t;
+};
+
+template <int F, int V>
+__global__ void phase_fold_kernel_even(PhaseFoldDims g, uint32_t reps, uint32_t plane, int p0, int p1, int p2,
+                                       const uint16_t *__restrict__ in, uint16_t *__restrict__ out,
+                                       const unsigned *max_in, float *s_out, float tb, int *err)
+{
+    using T = typename PiecesV<V>::T;
+    const int pv[3] = {p0, p1, p2};
+    const int es = grid_exponent(__uint_as_float(*max_in));
+    const float s_in = ldexpf(1.0f, es), inv_out = ldexpf(1.0f, -es);
+    if (blockIdx.x == 0 && threadIdx.x == 0) *s_out = s_in;
+    bool range_ok = true;
+    for (uint32_t t = blockIdx.x * blockDim.x + threadIdx.x; t < reps; t += gridDim.x * blockDim.x) {
+        uint32_t q = t, base = 0, odd[3];
+        for (int v = 0; v < g.d; ++v) {
+            const uint32_t rep = uint32_t(v == 0 ? g.rep[0] / V : g.rep[v]), r = q % rep;
+            q /= rep;
+            base += (v == 0 ? r * V : r) * uint32_t(g.pstride[v]);
+#pragma unroll
+            for (int b = 0; b < F; ++b)
+                if (pv[b] == v) odd[b] = uint32_t(g.c[v]) * uint32_t(g.pstride[v]);
+        }
+        uint32_t off[1 << F];
+        float2 z[1 << F][V];
+#pragma unroll
+        for (int sp = 0; sp < (1 << F); ++sp) {
+            uint32_t o = base;
+#pragma unroll
+            for (int b = 0; b < F; ++b)
+                if ((sp >> b) & 1) o += odd[b];
+            off[sp] = o;
+#pragma unroll
+            for (int c = 0; c < 2; ++c) {
+                T w[3];
+#pragma unroll
+                for (int p = 0; p < 3; ++p) w[p] = *reinterpret_cast<const T *>(in + (3 * c + p) * plane + o);
+                const uint16_t *h0 = reinterpret_cast<const uint16_t *>(&w[0]);
+                const uint16_t *h1 = reinterpret_cast<const uint16_t *>(&w[1]);
+                const uint16_t *h2 = reinterpret_cast<const uint16_t *>(&w[2]);
+#pragma unroll
+                for (int j = 0; j < V; ++j) {
+                    const float x = s_in * (__half2float(__ushort_as_half(h0[j])) +
+                                            (__half2float(__ushort_as_half(h1[j])) +
+                                             __half2float(__ushort_as_half(h2[j]))));
+                    if (c == 0)
+                        z[sp][j].x = x;
+                    else
+                        z[sp][j].y = x;
+                }
+            }
+        }
+#pragma unroll
+        for (int j = 0; j < V; ++j) {
+#pragma unroll
+            for (int b = 0; b < F; ++b)
+#pragma unroll
+                for (int sp = 0; sp < (1 << F); ++sp)
+                    if (!((sp >> b) & 1)) {
+                        const float2 a = z[sp][j], e = z[sp | (1 << b)][j];
+                        z[sp][j] = make_float2(0.5f * (a.x + e.x), 0.5f * (a.y + e.y));
+                        z[sp | (1 << b)][j] = make_float2(0.5f * (a.x - e.x), 0.5f * (a.y - e.y));
+                    }
+#pragma unroll
+            for (int sp = 0; sp < (1 << F); ++sp) {
+                const float xr = z[sp][j].x, xi = z[sp][j].y;
+                float sn, cs;
+                sincosf(tb * (xr * xr + xi * xi), &sn, &cs);
+                z[sp][j] = make_float2(xr * cs + xi * sn, xi * cs - xr * sn);
+            }
+#pragma unroll
+            for (int b = 0; b < F; ++b)
+#pragma unroll
+                for (int sp = 0; sp < (1 << F); ++sp)
+                    if (!((sp >> b) & 1)) {
+                        const float2 a = z[sp][j], e = z[sp | (1 << b)][j];
+                        z[sp][j] = make_float2(a.x + e.x, a.y + e.y);
+                        z[sp | (1 << b)][j] = make_float2(a.x - e.x, a.y - e.y);
+                    }
+        }
+#pragma unroll
+        for (int sp = 0; sp < (1 << F); ++sp) {
+            T w[6];
+            uint16_t *hw = reinterpret_cast<uint16_t *>(w);
+#pragma unroll
+            for (int j = 0; j < V; ++j) {
+                const float xr = z[sp][j].x * inv_out, xi = z[sp][j].y * inv_out;
+                range_ok &= fabsf(xr) < 16384.0f && fabsf(xi) < 16384.0f;
+                split_fx_scaled(xr, hw[0 * V + j], hw[1 * V + j], hw[2 * V + j]);
+                split_fx_scaled(xi, hw[3 * V + j], hw[4 * V + j], hw[5 * V + j]);
+            }
+#pragma unroll
+            for (int p = 0; p < 6; ++p) *reinterpret_cast<T *>(out + p * plane + off[sp]) = w[p];
+        }
+    }
+    if (!range_ok && err) atomicCAS(err, 0, MM_ERR_RANGE);
+}
+
+cudaError_t tc_phase_fold(const TcState &st, unsigned mask, const void *in_pieces, void *out_pieces,
+                          const unsigned *max_in, float *s_out, double tb, int *err, cudaStream_t s)
+{
+    if (st.d < 1 || st.d > kMaxDims || !mask || __builtin_popcount(mask) > 5 || in_pieces == out_pieces)
+        return cudaErrorInvalidValue;
+    PhaseFoldDims g;
+    g.d = st.d;
+    g.mask = mask;
+    int64_t stride = 1, reps = 1;
+    for (int v = 0; v < st.d; ++v) {
+        const bool fv = (mask >> v) & 1u;
+        g.n[v] = st.n[v];
+        g.c[v] = (st.n[v] + 1) / 2;
+        g.h[v] = st.n[v] / 2;
+        g.pstride[v] = stride;
+        g.rep[v] = fv ? g.c[v] : st.n[v];
+        stride *= st.np[v];
+        reps *= g.rep[v];
+    }
+    const int64_t blocks = (reps + 255) / 256 < 148 * 16 ? (reps + 255) / 256 : 148 * 16;
+    int pv[3] = {0, 0, 0}, F = 0;
+    bool even = 6 * st.plane < (int64_t(1) << 31);
+    for (int v = 0; v < st.d; ++v)
+        if ((mask >> v) & 1u) {
+            if (F < 3) pv[F] = v;
+            ++F;
+            even = even && st.n[v] % 2 == 0;
+        }
+    if (even && F >= 1 && F <= 3) {
+        const uint16_t *i16 = (const uint16_t *)in_pieces;
+        uint16_t *o16 = (uint16_t *)out_pieces;
+        const uint32_t pl = uint32_t(st.plane);
+        const float tf = float(tb);
+        // two points a thread when every offset of a pair is even: direction 1's range (and its
+        // fold offset c), the padded row and the plane even, and the buffers on 4-byte boundaries
+        const bool v2 = g.rep[0] % 2 == 0 && (!(mask & 1u) || g.c[0] % 2 == 0) && st.np[0] % 2 == 0 &&
+                        st.plane % 2 == 0 && !(reinterpret_cast<uintptr_t>(in_pieces) & 3) &&
+                        !(reinterpret_cast<uintptr_t>(out_pieces) & 3);
+        const uint32_t r32 = uint32_t(v2 ? reps / 2 : reps);
+        const int64_t nb = (int64_t(r32) + 255) / 256 < 148 * 16 ? (int64_t(r32) + 255) / 256 : 148 * 16;
+#define MM_PHASE_FOLD(FF, VV)                                                                                  \
+    phase_fold_kernel_even<FF, VV><<<unsigned(nb), 256, 0, s>>>(g, r32, pl, pv[0], pv[1], pv[2], i16, o16, max_in, \
+                                                               s_out, tf, err)
+        if (v2) {
+            if (F == 1) MM_PHASE_FOLD(1, 2);
+            else if (F == 2) MM_PHASE_FOLD(2, 2);
+            else MM_PHASE_FOLD(3, 2);
+        } else {
+            if (F == 1) MM_PHASE_FOLD(1, 1);
+            else if (F == 2) MM_PHASE_FOLD(2, 1);
+            else MM_PHASE_FOLD(3, 1);
+        }
+#undef MM_PHASE_FOLD
+        count_launch();
+        return cudaGetLastError();
+    }
+    phase_fold_kernel<<<unsigned(blocks), 256, 0, s>>>(g, reps, st.plane, (const uint16_t *)in_pieces,
+                                                      (uint16_t *)out_pieces, max_in, s_out, float(tb), err);
+    count_launch();
+    return cudaGetLastError();
+}
+
 cudaError_t tc_split_tf32(const TcState &st, const void *u_c64, void *pieces, cudaStream_t s)
 {
     if ((reinterpret_cast<uintptr_t>(pieces) & 15) || st.plane % 8) return cudaErrorMisalignedAddress;

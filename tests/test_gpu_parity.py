@@ -1187,16 +1187,21 @@ def test_fold_matches_unfolded(env, orc, monkeypatch, dims, mixed):
 
 
 @pytest.mark.parametrize("m", [24, 25])
-def test_ho_fold_matches_unfolded(env, monkeypatch, m):
+def test_ho_fold_matches_unfolded(env, orc, monkeypatch, m):
     """Harmonic-oscillator steps of a Hermite plan run folded (the values-space propagators at
     the symmetric Gauss-Hermite nodes are centrosymmetric): the result equals the unfolded
-    plan's to the precision's tolerance, for an even and an odd number of nodes; a GPE step on
-    the same plan (whose nonlinearity needs the values) is unchanged by folding."""
+    plan's to the precision's tolerance, for an even and an odd number of nodes.  GPE steps on
+    the same plan run folded too, with the nonlinear phase as a pass on the folded pieces between
+    the sweeps: they match the unfolded plan and the oracle, and the steps that also return the
+    norm (whose epilogue needs the values) are unchanged by folding."""
     mm, ctx, torch = env
     monkeypatch.setenv("MM_FOLD_ALWAYS", "1")
     tau, steps = 0.05, 4
+    beta, gtau, gsteps = 100.0, 1e-3, 6
     psi0 = inputs.complex_normal((m, m, m), seed=9).astype(np.complex64)
-    out, gpe = {}, {}
+    xo, _, Wo = orc.gauss_hermite(m)
+    g0 = inputs.gpe_psi0(xo, Wo, seed=4).astype(np.complex64)
+    out, gpe, gnorm = {}, {}, {}
     for fold in (True, False):
         if fold:
             monkeypatch.delenv("MM_NO_FOLD", raising=False)
@@ -1205,16 +1210,24 @@ def test_ho_fold_matches_unfolded(env, monkeypatch, m):
         hp = mm.HermitePlan(ctx, [m] * 3, prec="f16x6")
         u = to_gpu(torch, psi0, torch.complex64)
         hp.ho_step(u, tau, steps)
-        g = to_gpu(torch, psi0, torch.complex64)
-        hp.gpe_step(g, 10.0, 1e-3, 2)
+        g = to_gpu(torch, g0, torch.complex64)
+        hp.gpe_step(g, beta, gtau, gsteps)
+        gn = to_gpu(torch, g0, torch.complex64)
+        hp.gpe_step_norm2(gn, beta, gtau, gsteps)
         torch.cuda.synchronize()
         ctx.status()
-        out[fold], gpe[fold] = u.cpu().numpy(), g.cpu().numpy()
+        out[fold], gpe[fold], gnorm[fold] = u.cpu().numpy(), g.cpu().numpy(), gn.cpu().numpy()
     monkeypatch.delenv("MM_NO_FOLD", raising=False)
     d = rel(out[True], out[False])
     print(f"HO fold vs unfolded m={m}: {d:.3e}")
     assert d <= TOL_MODE["f16x6"] * steps * 3
-    assert np.array_equal(gpe[True].view(np.uint32), gpe[False].view(np.uint32))
+    ref = orc.gpe_steps(g0.astype(complex), xo, Wo, beta, gtau, gsteps)
+    w3 = orc.weight3(Wo)
+    e_fold, e_unf = orc.rel_l2(gpe[True], ref, w3), orc.rel_l2(gpe[False], ref, w3)
+    print(f"GPE fold m={m}: {e_fold:.3e} against the oracle (unfolded {e_unf:.3e})")
+    assert e_fold <= 1e-6 and rel(gpe[True], gpe[False]) <= 2e-6
+    assert not np.array_equal(gpe[True].view(np.uint32), gpe[False].view(np.uint32)), "the GPE steps ran folded"
+    assert np.array_equal(gnorm[True].view(np.uint32), gnorm[False].view(np.uint32))
 
 
 def test_autotune_cache(env, orc, tmp_path, monkeypatch):
