@@ -517,8 +517,10 @@ mm_status split_step_gpe(mm_plan *plan, void *psi_dev, double beta, double tau, 
  * mass of section 4.5) in FP64 to *norm2_host (host memory); the stream is
  * synchronised.  On F16X6 plans with the CTA-pair kernel the sum is taken in
  * the epilogue of the last mode product, from the FP32 values before they
- * are split (one FP64 atomic per epilogue warp), so no pass re-reads psi;
- * otherwise the steps are followed by mm_norm2(weighted).  nsteps = 0 gives
+ * are split (one FP64 atomic per epilogue warp), or, when the steps run on
+ * the even/odd-folded state, by the pass that unfolds the result (from the
+ * complex64 values it writes), so no pass re-reads psi; otherwise the steps
+ * are followed by mm_norm2(weighted).  nsteps = 0 gives
  * the norm of psi_dev.  3D Hermite plans only.  Errors: those of
  * split_step_gpe and mm_norm2, MM_ERR_INVALID_ARG (not a 3D Hermite plan,
  * norm2_host NULL), MM_ERR_OOM (the plan's 8-byte accumulator). */

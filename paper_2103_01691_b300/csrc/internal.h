@@ -37,7 +37,10 @@ cudaError_t dmma_mode_product(bool complex_data, int64_t left, int64_t n, int64_
 cudaError_t simt_nonlinear_phase(bool fp64, int64_t count, double tb, void *psi, cudaStream_t s);
 // Even/odd folding (inverse: unfolding) of a complex64 tensor with sizes n[0..d-1] (n[0] fastest)
 // in the directions of mask (bit v: direction v + 1; at most five of them); in and out are distinct.
-cudaError_t fold_state(int d, const int64_t *n, unsigned mask, bool inverse, const void *in, void *out, cudaStream_t s);
+// With norm2 (inverse only) the unfold also adds sum |out|^2 w[0][i_1] ... w[d-1][i_d] over its
+// outputs to *norm2 in FP64 (w null, or a null table: factor 1).
+cudaError_t fold_state(int d, const int64_t *n, unsigned mask, bool inverse, const void *in, void *out, cudaStream_t s,
+                       const double *const *w = nullptr, double *norm2 = nullptr);
 // g <- adjoint of the nonlinear phase at psi (psi: state before the phase).
 cudaError_t simt_nonlinear_adjoint(bool fp64, int64_t count, double tb, const void *psi, void *g, cudaStream_t s);
 // out (device double) += sum |u|^2 w, w = w1[i1] w2[i2] w3[i3] if w1 != NULL.

@@ -1659,8 +1659,8 @@ mm_status hermite_ho_step(mm_plan *p, void *psi, double tau, int64_t nsteps, voi
 namespace {
 
 // Strang steps of the GPE; with d_norm (tensor cores, F16X6 on the CTA-pair kernel, pair tilings of
-// the half-step propagators), the last product's epilogue also sets *d_norm to the weighted norm
-// sum |psi|^2 W of the result (kind 5).
+// the half-step propagators), *d_norm is also set to the weighted norm sum |psi|^2 W of the result:
+// by the last product's epilogue (kind 5), or by the final unfold when the steps run folded.
 mm_status gpe_steps(mm_plan *p, void *psi, double beta, double tau, int64_t nsteps, double *d_norm, cudaStream_t s)
 {
     mm_status st;
@@ -1681,11 +1681,12 @@ mm_status gpe_steps(mm_plan *p, void *psi, double beta, double tau, int64_t nste
         }
         return simt_sweep(p, p->Pdev[half], psi, s);
     }
-    // Folded (F16X6, no norm, the half and full propagators folded alike, and long enough to pay for
-    // it): the linear sweeps run on the folded state with plain epilogues, and the nonlinear phase
-    // is a pass on the folded pieces between sweeps (unfold, phase, fold per orbit)
+    // Folded (F16X6, the half and full propagators folded alike, and long enough to pay for it): the
+    // linear sweeps run on the folded state with plain epilogues, the nonlinear phase is a pass on
+    // the folded pieces between sweeps (unfold, phase, fold per orbit), and the weighted norm, when
+    // asked for, is summed by the final unfold
     const unsigned fm = p->pfold_mask[half];
-    bool folded = p->fixed && !d_norm && p->fold_on && fm && p->pfold_mask[full] == fm;
+    bool folded = p->fixed && p->fold_on && fm && p->pfold_mask[full] == fm;
     if (folded) {
         mm::TcMatrix *U[mm::kMaxDims], *D[mm::kMaxDims];
         for (int v = 0; v < p->d; ++v) {
@@ -1698,7 +1699,7 @@ mm_status gpe_steps(mm_plan *p, void *psi, double beta, double tau, int64_t nste
         folded = p->fold_force || double(nsteps + 1) * fold_saved_s(p, fm, U, D) > cost_s;
     }
     if (folded) {
-        return run_graphed(p, 6, psi, nsteps, s, tau, beta, [&]() -> mm_status {
+        return run_graphed(p, d_norm ? 7 : 6, psi, nsteps, s, tau, beta, [&]() -> mm_status {
             mm_status r;
             int cur = 0;
             mm::TcMatrix *Mh[mm::kMaxDims], *Mf[mm::kMaxDims];
@@ -1724,7 +1725,13 @@ mm_status gpe_steps(mm_plan *p, void *psi, double beta, double tau, int64_t nste
             }
             if ((r = tc_sweep(p, Mh, cur, mm::TcEpilogue{}, s))) return r;
             if ((r = tc_end(p, cur, p->fold_buf, s))) return r;
-            e = mm::fold_state(p->d, p->n, fm, true, p->fold_buf, psi, s);
+            const double *W[mm::kMaxDims] = {};
+            if (d_norm) {
+                for (int v = 0; v < p->d; ++v) W[v] = p->Wpad[v];
+                if ((e = cudaMemsetAsync(d_norm, 0, sizeof(double), s)) != cudaSuccess)
+                    return cuda_fail(e, "norm accumulator");
+            }
+            e = mm::fold_state(p->d, p->n, fm, true, p->fold_buf, psi, s, d_norm ? W : nullptr, d_norm);
             return e == cudaSuccess ? MM_OK : cuda_fail(e, "unfold");
         });
     }

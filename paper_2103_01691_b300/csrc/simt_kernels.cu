@@ -429,11 +429,47 @@ struct FoldDims {
     int d;
     int64_t n[kMaxDims], c[kMaxDims], h[kMaxDims], stride[kMaxDims], rep[kMaxDims];
     unsigned mask;
+    // the unfold can also add sum |out|^2 w[0][i_1] w[1][i_2] ... over its outputs to *norm2 (FP64;
+    // null table: factor 1; norm2 null: no sum)
+    const double *w[kMaxDims];
+    double *norm2;
 };
+
+// The block's sum of s added to *out (every thread of the block calls it).
+__device__ void block_sum_add(double s, double *out)
+{
+    __shared__ double red[32];
+    for (int o = 16; o > 0; o >>= 1) s += __shfl_down_sync(0xffffffffu, s, o);
+    if ((threadIdx.x & 31) == 0) red[threadIdx.x >> 5] = s;
+    __syncthreads();
+    if (threadIdx.x < 32) {
+        s = (threadIdx.x < blockDim.x / 32) ? red[threadIdx.x] : 0.0;
+        for (int o = 16; o > 0; o >>= 1) s += __shfl_down_sync(0xffffffffu, s, o);
+        if (threadIdx.x == 0) atomicAdd(out, s);
+    }
+}
+
+// The weight of the orbit point whose index in direction v is r[v], or n[v] - 1 - r[v] where bit b
+// of sp is set and v = pv[b].
+template <typename R>
+__device__ __forceinline__ double orbit_weight(const FoldDims &f, const R *r, const int *pv, int m, int sp)
+{
+    double w = 1.0;
+#pragma unroll
+    for (int v = 0; v < kMaxDims; ++v) {
+        if (v >= f.d || !f.w[v]) continue;
+        int64_t i = int64_t(r[v]);
+        for (int b = 0; b < m; ++b)
+            if (pv[b] == v && ((sp >> b) & 1)) i = f.n[v] - 1 - i;
+        w *= f.w[v][i];
+    }
+    return w;
+}
 
 template <bool INV>
 __global__ void fold_kernel(FoldDims f, int64_t reps, const float2 *__restrict__ in, float2 *__restrict__ out)
 {
+    double acc = 0.0;
     for (int64_t t = blockIdx.x * int64_t(blockDim.x) + threadIdx.x; t < reps; t += int64_t(gridDim.x) * blockDim.x) {
         int64_t r[kMaxDims];
         int64_t q = t;
@@ -475,7 +511,11 @@ __global__ void fold_kernel(FoldDims f, int64_t reps, const float2 *__restrict__
                     }
                 }
         for (int sp = 0; sp < cnt; ++sp) out[INV ? orig(sp) : folded(sp)] = buf[sp];
+        if (INV && f.norm2)
+            for (int sp = 0; sp < cnt; ++sp)
+                acc += (double(buf[sp].x) * buf[sp].x + double(buf[sp].y) * buf[sp].y) * orbit_weight(f, r, pv, m, sp);
     }
+    if (INV && f.norm2) block_sum_add(acc, f.norm2);
 }
 
 // The same when every folded direction has even length (every orbit has 2^F points, F the number of
@@ -485,10 +525,14 @@ __global__ void fold_kernel_even(FoldDims f, uint32_t reps, int p0, int p1, int 
                                  float2 *__restrict__ out)
 {
     const int pv[3] = {p0, p1, p2};
+    double acc = 0.0;
     for (uint32_t t = blockIdx.x * blockDim.x + threadIdx.x; t < reps; t += gridDim.x * blockDim.x) {
-        uint32_t q = t, base = 0, mir[3], odd[3];
-        for (int v = 0; v < f.d; ++v) {
+        uint32_t q = t, base = 0, mir[3], odd[3], rv[kMaxDims];
+#pragma unroll
+        for (int v = 0; v < kMaxDims; ++v) {
+            if (v >= f.d) break;
             const uint32_t rep = uint32_t(f.rep[v]), r = q % rep;
+            rv[v] = r;
             q /= rep;
             base += r * uint32_t(f.stride[v]);
 #pragma unroll
@@ -525,15 +569,24 @@ __global__ void fold_kernel_even(FoldDims f, uint32_t reps, int p0, int p1, int 
                 if ((sp >> b) & 1) off += INV ? mir[b] : odd[b];
             out[off] = buf[sp];
         }
+        if (INV && f.norm2)
+#pragma unroll
+            for (int sp = 0; sp < (1 << F); ++sp)
+                acc += (double(buf[sp].x) * buf[sp].x + double(buf[sp].y) * buf[sp].y) * orbit_weight(f, rv, pv, F, sp);
     }
+    if (INV && f.norm2) block_sum_add(acc, f.norm2);
 }
 
-cudaError_t fold_state(int d, const int64_t *n, unsigned mask, bool inverse, const void *in, void *out, cudaStream_t s)
+cudaError_t fold_state(int d, const int64_t *n, unsigned mask, bool inverse, const void *in, void *out, cudaStream_t s,
+                       const double *const *w, double *norm2)
 {
-    if (d < 1 || d > kMaxDims || in == out || __builtin_popcount(mask) > kMaxFold) return cudaErrorInvalidValue;
+    if (d < 1 || d > kMaxDims || in == out || __builtin_popcount(mask) > kMaxFold || (norm2 && !inverse))
+        return cudaErrorInvalidValue;
     FoldDims f;
     f.d = d;
     f.mask = mask;
+    f.norm2 = norm2;
+    for (int v = 0; v < kMaxDims; ++v) f.w[v] = (w && v < d) ? w[v] : nullptr;
     int64_t stride = 1, reps = 1;
     for (int v = 0; v < d; ++v) {
         f.n[v] = n[v];

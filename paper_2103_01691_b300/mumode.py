@@ -615,7 +615,7 @@ class HermitePlan(_Tunable):
 
     def gpe_step_norm2(self, psi, beta: float, tau: float, nsteps: int = 1, stream=None) -> float:
         """gpe_step, returning the weighted norm sum |psi|^2 W of the result (taken in the last
-        product's epilogue where the plan allows)."""
+        product's epilogue, or in the unfold of folded steps, where the plan allows)."""
         _need_cuda(psi)
         out = ctypes.c_double()
         _check(lib().split_step_gpe_norm2(self.handle, ctypes.c_void_p(psi.data_ptr()), float(beta), float(tau),

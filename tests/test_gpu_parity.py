@@ -1192,8 +1192,8 @@ def test_ho_fold_matches_unfolded(env, orc, monkeypatch, m):
     the symmetric Gauss-Hermite nodes are centrosymmetric): the result equals the unfolded
     plan's to the precision's tolerance, for an even and an odd number of nodes.  GPE steps on
     the same plan run folded too, with the nonlinear phase as a pass on the folded pieces between
-    the sweeps: they match the unfolded plan and the oracle, and the steps that also return the
-    norm (whose epilogue needs the values) are unchanged by folding."""
+    the sweeps: they match the unfolded plan and the oracle; the steps that also return the
+    weighted norm sum it in the final unfold, and it equals the norm of the state they return."""
     mm, ctx, torch = env
     monkeypatch.setenv("MM_FOLD_ALWAYS", "1")
     tau, steps = 0.05, 4
@@ -1201,7 +1201,7 @@ def test_ho_fold_matches_unfolded(env, orc, monkeypatch, m):
     psi0 = inputs.complex_normal((m, m, m), seed=9).astype(np.complex64)
     xo, _, Wo = orc.gauss_hermite(m)
     g0 = inputs.gpe_psi0(xo, Wo, seed=4).astype(np.complex64)
-    out, gpe, gnorm = {}, {}, {}
+    out, gpe, gnorm, nret, nsep = {}, {}, {}, {}, {}
     for fold in (True, False):
         if fold:
             monkeypatch.delenv("MM_NO_FOLD", raising=False)
@@ -1213,7 +1213,8 @@ def test_ho_fold_matches_unfolded(env, orc, monkeypatch, m):
         g = to_gpu(torch, g0, torch.complex64)
         hp.gpe_step(g, beta, gtau, gsteps)
         gn = to_gpu(torch, g0, torch.complex64)
-        hp.gpe_step_norm2(gn, beta, gtau, gsteps)
+        nret[fold] = hp.gpe_step_norm2(gn, beta, gtau, gsteps)
+        nsep[fold] = hp.norm2(gn)
         torch.cuda.synchronize()
         ctx.status()
         out[fold], gpe[fold], gnorm[fold] = u.cpu().numpy(), g.cpu().numpy(), gn.cpu().numpy()
@@ -1227,7 +1228,12 @@ def test_ho_fold_matches_unfolded(env, orc, monkeypatch, m):
     print(f"GPE fold m={m}: {e_fold:.3e} against the oracle (unfolded {e_unf:.3e})")
     assert e_fold <= 1e-6 and rel(gpe[True], gpe[False]) <= 2e-6
     assert not np.array_equal(gpe[True].view(np.uint32), gpe[False].view(np.uint32)), "the GPE steps ran folded"
-    assert np.array_equal(gnorm[True].view(np.uint32), gnorm[False].view(np.uint32))
+    assert np.array_equal(gnorm[True].view(np.uint32), gpe[True].view(np.uint32))
+    assert np.array_equal(gnorm[False].view(np.uint32), gpe[False].view(np.uint32))
+    # the unfold sums the complex64 values it writes; the unfolded epilogue sums the FP32 values
+    # before their split, which the merge rounds (the tolerance of test_gpe_norm_in_epilogue)
+    assert abs(nret[True] / nsep[True] - 1) <= 1e-12, (nret[True], nsep[True])
+    assert abs(nret[False] / nsep[False] - 1) <= 2e-7, (nret[False], nsep[False])
 
 
 def test_autotune_cache(env, orc, tmp_path, monkeypatch):
