@@ -518,16 +518,18 @@ __global__ void fold_kernel(FoldDims f, int64_t reps, const float2 *__restrict__
     if (INV && f.norm2) block_sum_add(acc, f.norm2);
 }
 
-// The same when every folded direction has even length (every orbit has 2^F points, F the number of
-// folded directions): the orbit lives in registers, indices in 32 bits.
+// The same for at most three folded directions and 32-bit offsets: the orbit lives in registers.
+// Orbit pattern sp (bit b: direction pv[b]) exists where every set bit's direction has a mirror
+// pair at this orbit (pm); at the middle index of an odd length the direction has none and its
+// butterfly is the identity.
 template <int F, bool INV>
-__global__ void fold_kernel_even(FoldDims f, uint32_t reps, int p0, int p1, int p2, const float2 *__restrict__ in,
-                                 float2 *__restrict__ out)
+__global__ void fold_kernel_reg(FoldDims f, uint32_t reps, int p0, int p1, int p2, const float2 *__restrict__ in,
+                                float2 *__restrict__ out)
 {
     const int pv[3] = {p0, p1, p2};
     double acc = 0.0;
     for (uint32_t t = blockIdx.x * blockDim.x + threadIdx.x; t < reps; t += gridDim.x * blockDim.x) {
-        uint32_t q = t, base = 0, mir[3], odd[3], rv[kMaxDims];
+        uint32_t q = t, base = 0, mir[3], odd[3], rv[kMaxDims], pm = 0;
 #pragma unroll
         for (int v = 0; v < kMaxDims; ++v) {
             if (v >= f.d) break;
@@ -540,11 +542,14 @@ __global__ void fold_kernel_even(FoldDims f, uint32_t reps, int p0, int p1, int 
                 if (pv[b] == v) {
                     mir[b] = (uint32_t(f.n[v]) - 1u - 2u * r) * uint32_t(f.stride[v]);
                     odd[b] = uint32_t(f.c[v]) * uint32_t(f.stride[v]);
+                    if (r < uint32_t(f.h[v])) pm |= 1u << b;
                 }
         }
         float2 buf[1 << F];
 #pragma unroll
         for (int sp = 0; sp < (1 << F); ++sp) {
+            buf[sp] = make_float2(0.0f, 0.0f);
+            if (uint32_t(sp) & ~pm) continue;
             uint32_t off = base;
 #pragma unroll
             for (int b = 0; b < F; ++b)
@@ -552,7 +557,8 @@ __global__ void fold_kernel_even(FoldDims f, uint32_t reps, int p0, int p1, int 
             buf[sp] = in[off];
         }
 #pragma unroll
-        for (int b = 0; b < F; ++b)
+        for (int b = 0; b < F; ++b) {
+            if (!((pm >> b) & 1u)) continue;
 #pragma unroll
             for (int sp = 0; sp < (1 << F); ++sp)
                 if (!((sp >> b) & 1)) {
@@ -561,18 +567,18 @@ __global__ void fold_kernel_even(FoldDims f, uint32_t reps, int p0, int p1, int 
                     buf[sp] = make_float2(h * (a.x + z.x), h * (a.y + z.y));
                     buf[sp | (1 << b)] = make_float2(h * (a.x - z.x), h * (a.y - z.y));
                 }
+        }
 #pragma unroll
         for (int sp = 0; sp < (1 << F); ++sp) {
+            if (uint32_t(sp) & ~pm) continue;
             uint32_t off = base;
 #pragma unroll
             for (int b = 0; b < F; ++b)
                 if ((sp >> b) & 1) off += INV ? mir[b] : odd[b];
             out[off] = buf[sp];
-        }
-        if (INV && f.norm2)
-#pragma unroll
-            for (int sp = 0; sp < (1 << F); ++sp)
+            if (INV && f.norm2)
                 acc += (double(buf[sp].x) * buf[sp].x + double(buf[sp].y) * buf[sp].y) * orbit_weight(f, rv, pv, F, sp);
+        }
     }
     if (INV && f.norm2) block_sum_add(acc, f.norm2);
 }
@@ -598,22 +604,21 @@ cudaError_t fold_state(int d, const int64_t *n, unsigned mask, bool inverse, con
         reps *= f.rep[v];
     }
     const int64_t blocks = (reps + 255) / 256 < 148 * 16 ? (reps + 255) / 256 : 148 * 16;
-    // the fast form: at most three folded directions, all of even length, 32-bit offsets
+    // the fast form: at most three folded directions, 32-bit offsets
     int pv[3] = {0, 0, 0}, F = 0;
-    bool even = stride < (int64_t(1) << 31);
+    const bool off32 = stride < (int64_t(1) << 31);
     for (int v = 0; v < d; ++v)
         if ((mask >> v) & 1u) {
             if (F < 3) pv[F] = v;
             ++F;
-            even = even && n[v] % 2 == 0;
         }
-    if (even && F >= 1 && F <= 3) {
+    if (off32 && F >= 1 && F <= 3) {
         const float2 *i2 = (const float2 *)in;
         float2 *o2 = (float2 *)out;
         const uint32_t r32 = uint32_t(reps);
 #define MM_FOLD(FF)                                                                                      \
-    (inverse ? (fold_kernel_even<FF, true><<<unsigned(blocks), 256, 0, s>>>(f, r32, pv[0], pv[1], pv[2], i2, o2), 0) \
-             : (fold_kernel_even<FF, false><<<unsigned(blocks), 256, 0, s>>>(f, r32, pv[0], pv[1], pv[2], i2, o2), 0))
+    (inverse ? (fold_kernel_reg<FF, true><<<unsigned(blocks), 256, 0, s>>>(f, r32, pv[0], pv[1], pv[2], i2, o2), 0) \
+             : (fold_kernel_reg<FF, false><<<unsigned(blocks), 256, 0, s>>>(f, r32, pv[0], pv[1], pv[2], i2, o2), 0))
         if (F == 1) MM_FOLD(1);
         else if (F == 2) MM_FOLD(2);
         else MM_FOLD(3);

@@ -956,10 +956,12 @@ __global__ void phase_fold_kernel(PhaseFoldDims g, int64_t reps, int64_t plane, 
     if (!range_ok && err) atomicCAS(err, 0, MM_ERR_RANGE);
 }
 
-// The same when every folded direction has even length (every orbit has 2^F points, F at most 3)
-// and the pieces fit 32-bit offsets: the orbit lives in registers.  Each thread takes the orbits of
-// V consecutive points of direction 1 (V pieces per load and store: a warp's access to a plane
-// covers 128 contiguous bytes for V = 2).
+// The same for at most three folded directions and pieces that fit 32-bit offsets: the orbit
+// lives in registers.  Orbit pattern sp (bit b: direction pv[b]) exists where every set bit's
+// direction has a mirror pair at this orbit (pm); at the middle index of an odd length the
+// direction has none and its butterflies are skipped.  Each thread takes the orbits of V
+// consecutive points of direction 1 (V pieces per load and store: a warp's access to a plane
+// covers 128 contiguous bytes for V = 2), which share pm.
 template <int V>
 struct PiecesV;
 template <>
@@ -972,7 +974,7 @@ struct PiecesV<2> {
 };
 
 template <int F, int V>
-__global__ void phase_fold_kernel_even(PhaseFoldDims g, uint32_t reps, uint32_t plane, int p0, int p1, int p2,
+__global__ void phase_fold_kernel_reg(PhaseFoldDims g, uint32_t reps, uint32_t plane, int p0, int p1, int p2,
                                        const uint16_t *__restrict__ in, uint16_t *__restrict__ out,
                                        const unsigned *max_in, float *s_out, float tb, int *err)
 {
@@ -983,19 +985,26 @@ __global__ void phase_fold_kernel_even(PhaseFoldDims g, uint32_t reps, uint32_t 
     if (blockIdx.x == 0 && threadIdx.x == 0) *s_out = s_in;
     bool range_ok = true;
     for (uint32_t t = blockIdx.x * blockDim.x + threadIdx.x; t < reps; t += gridDim.x * blockDim.x) {
-        uint32_t q = t, base = 0, odd[3];
+        uint32_t q = t, base = 0, odd[3], pm = 0;
         for (int v = 0; v < g.d; ++v) {
             const uint32_t rep = uint32_t(v == 0 ? g.rep[0] / V : g.rep[v]), r = q % rep;
             q /= rep;
             base += (v == 0 ? r * V : r) * uint32_t(g.pstride[v]);
 #pragma unroll
             for (int b = 0; b < F; ++b)
-                if (pv[b] == v) odd[b] = uint32_t(g.c[v]) * uint32_t(g.pstride[v]);
+                if (pv[b] == v) {
+                    odd[b] = uint32_t(g.c[v]) * uint32_t(g.pstride[v]);
+                    if ((v == 0 ? r * V : r) < uint32_t(g.h[v])) pm |= 1u << b;
+                }
         }
         uint32_t off[1 << F];
         float2 z[1 << F][V];
 #pragma unroll
         for (int sp = 0; sp < (1 << F); ++sp) {
+#pragma unroll
+            for (int j = 0; j < V; ++j) z[sp][j] = make_float2(0.0f, 0.0f);
+            off[sp] = 0;
+            if (uint32_t(sp) & ~pm) continue;
             uint32_t o = base;
 #pragma unroll
             for (int b = 0; b < F; ++b)
@@ -1024,7 +1033,8 @@ __global__ void phase_fold_kernel_even(PhaseFoldDims g, uint32_t reps, uint32_t 
 #pragma unroll
         for (int j = 0; j < V; ++j) {
 #pragma unroll
-            for (int b = 0; b < F; ++b)
+            for (int b = 0; b < F; ++b) {
+                if (!((pm >> b) & 1u)) continue;
 #pragma unroll
                 for (int sp = 0; sp < (1 << F); ++sp)
                     if (!((sp >> b) & 1)) {
@@ -1032,6 +1042,7 @@ __global__ void phase_fold_kernel_even(PhaseFoldDims g, uint32_t reps, uint32_t 
                         z[sp][j] = make_float2(0.5f * (a.x + e.x), 0.5f * (a.y + e.y));
                         z[sp | (1 << b)][j] = make_float2(0.5f * (a.x - e.x), 0.5f * (a.y - e.y));
                     }
+            }
 #pragma unroll
             for (int sp = 0; sp < (1 << F); ++sp) {
                 const float xr = z[sp][j].x, xi = z[sp][j].y;
@@ -1040,7 +1051,8 @@ __global__ void phase_fold_kernel_even(PhaseFoldDims g, uint32_t reps, uint32_t 
                 z[sp][j] = make_float2(xr * cs + xi * sn, xi * cs - xr * sn);
             }
 #pragma unroll
-            for (int b = 0; b < F; ++b)
+            for (int b = 0; b < F; ++b) {
+                if (!((pm >> b) & 1u)) continue;
 #pragma unroll
                 for (int sp = 0; sp < (1 << F); ++sp)
                     if (!((sp >> b) & 1)) {
@@ -1048,9 +1060,11 @@ __global__ void phase_fold_kernel_even(PhaseFoldDims g, uint32_t reps, uint32_t 
                         z[sp][j] = make_float2(a.x + e.x, a.y + e.y);
                         z[sp | (1 << b)][j] = make_float2(a.x - e.x, a.y - e.y);
                     }
+            }
         }
 #pragma unroll
         for (int sp = 0; sp < (1 << F); ++sp) {
+            if (uint32_t(sp) & ~pm) continue;
             T w[6];
             uint16_t *hw = reinterpret_cast<uint16_t *>(w);
 #pragma unroll
@@ -1088,27 +1102,27 @@ cudaError_t tc_phase_fold(const TcState &st, unsigned mask, const void *in_piece
     }
     const int64_t blocks = (reps + 255) / 256 < 148 * 16 ? (reps + 255) / 256 : 148 * 16;
     int pv[3] = {0, 0, 0}, F = 0;
-    bool even = 6 * st.plane < (int64_t(1) << 31);
+    const bool off32 = 6 * st.plane < (int64_t(1) << 31);
     for (int v = 0; v < st.d; ++v)
         if ((mask >> v) & 1u) {
             if (F < 3) pv[F] = v;
             ++F;
-            even = even && st.n[v] % 2 == 0;
         }
-    if (even && F >= 1 && F <= 3) {
+    if (off32 && F >= 1 && F <= 3) {
         const uint16_t *i16 = (const uint16_t *)in_pieces;
         uint16_t *o16 = (uint16_t *)out_pieces;
         const uint32_t pl = uint32_t(st.plane);
         const float tf = float(tb);
-        // two points a thread when every offset of a pair is even: direction 1's range (and its
-        // fold offset c), the padded row and the plane even, and the buffers on 4-byte boundaries
-        const bool v2 = g.rep[0] % 2 == 0 && (!(mask & 1u) || g.c[0] % 2 == 0) && st.np[0] % 2 == 0 &&
+        // two points a thread when every offset of a pair is even (direction 1's range and the
+        // padded row even, the plane even, the buffers on 4-byte boundaries) and both points of a
+        // pair have the same mirror pairs (direction 1 not folded, or of even length)
+        const bool v2 = g.rep[0] % 2 == 0 && (!(mask & 1u) || st.n[0] % 2 == 0) && st.np[0] % 2 == 0 &&
                         st.plane % 2 == 0 && !(reinterpret_cast<uintptr_t>(in_pieces) & 3) &&
                         !(reinterpret_cast<uintptr_t>(out_pieces) & 3);
         const uint32_t r32 = uint32_t(v2 ? reps / 2 : reps);
         const int64_t nb = (int64_t(r32) + 255) / 256 < 148 * 16 ? (int64_t(r32) + 255) / 256 : 148 * 16;
 #define MM_PHASE_FOLD(FF, VV)                                                                                  \
-    phase_fold_kernel_even<FF, VV><<<unsigned(nb), 256, 0, s>>>(g, r32, pl, pv[0], pv[1], pv[2], i16, o16, max_in, \
+    phase_fold_kernel_reg<FF, VV><<<unsigned(nb), 256, 0, s>>>(g, r32, pl, pv[0], pv[1], pv[2], i16, o16, max_in, \
                                                                s_out, tf, err)
         if (v2) {
             if (F == 1) MM_PHASE_FOLD(1, 2);
