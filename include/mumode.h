@@ -363,9 +363,13 @@ mm_status mm_plan_set_graphs(mm_plan *plan, int enable);
  * entry of an odd n as it is) as a block-diagonal matrix of two half-size
  * blocks, which the tensor-core kernels run as half-size products.  With
  * folding on, the steps of a tensor-core Tucker plan (mumode_step, its
- * batches) and the harmonic-oscillator steps of a Hermite plan fold the
- * state once per call, run on the folded state and unfold it at the end;
- * the results agree with the unfolded form to the precision's rounding.
+ * batches) and the harmonic-oscillator and GPE steps of an F16X6 Hermite
+ * plan fold the state once per call, run on the folded state and unfold it
+ * at the end (GPE: the nonlinear phase is a pass on the folded state between
+ * the linear flows, unfolding, multiplying and refolding each orbit of
+ * mirror points); a call folds when it is long enough for the saved tensor
+ * work to pay for these passes.  The results agree with the unfolded form to
+ * the precision's rounding.
  * Plans on complex64 data only; MM_NO_FOLD set (to other than 0) when a
  * plan is made turns it off for that plan.  mm_plan_get_fold reports the
  * folded directions (bit v: direction v + 1; 0: none) and
