@@ -1236,6 +1236,72 @@ def test_ho_fold_matches_unfolded(env, orc, monkeypatch, m):
     assert abs(nret[False] / nsep[False] - 1) <= 2e-7, (nret[False], nsep[False])
 
 
+def _hermite_flow(orc, x, W, s):
+    """Values-space harmonic-oscillator flow over time s in one direction, from the oracle's nodes,
+    weights and Hermite functions: backward transform, exp(-i s (k + 1/2)), forward transform."""
+    H = orc.hermite_functions(x.size, x)
+    return H.T @ np.diag(np.exp(-1j * s * (np.arange(x.size) + 0.5))) @ H @ np.diag(W)
+
+
+def _strang_fp64(orc, psi, xs, Ws, beta, tau, nsteps):
+    """FP64 Strang steps of the GPE on a grid of its own size per direction (the oracle's scheme,
+    section 4.5, written with per-direction flows; shape (n3, n2, n1))."""
+    def flow(u, s):
+        P = [_hermite_flow(orc, x, W, s) for x, W in zip(xs, Ws)]
+        u = np.einsum("ij,abj->abi", P[0], u)
+        u = np.einsum("ij,ajb->aib", P[1], u)
+        return np.einsum("ij,jab->iab", P[2], u)
+
+    u = psi.astype(complex)
+    for _ in range(nsteps):
+        u = flow(u, 0.5 * tau)
+        u = u * np.exp(-1j * tau * beta * np.abs(u) ** 2)
+        u = flow(u, 0.5 * tau)
+    return u
+
+
+@pytest.mark.parametrize("dims", [(24, 25, 21), (25, 22, 24)])
+def test_gpe_fold_mixed_sizes(env, orc, monkeypatch, dims):
+    """Folded GPE steps on grids of different, even and odd, sizes per direction: the phase pass
+    takes two points a thread when direction 1 has even length (24, 25, 21) and one otherwise
+    (25, 22, 24); the result matches an FP64 Strang reference built from the oracle's Hermite
+    functions (equal to the oracle's own GPE steps on a cube grid, checked first) and the
+    unfolded plan."""
+    mm, ctx, torch = env
+    monkeypatch.setenv("MM_FOLD_ALWAYS", "1")
+    beta, tau, nsteps = 100.0, 1e-3, 5
+    x9, _, W9 = orc.gauss_hermite(9)
+    p9 = inputs.gpe_psi0(x9, W9, seed=4)
+    r9 = orc.gpe_steps(p9, x9, W9, beta, tau, nsteps)
+    assert np.max(np.abs(_strang_fp64(orc, p9, [x9] * 3, [W9] * 3, beta, tau, nsteps) - r9)) <= 1e-12
+    xs, Ws = [], []
+    for n in dims:
+        x, _, W = orc.gauss_hermite(n)
+        xs.append(x)
+        Ws.append(W)
+    psi0 = inputs.gpe_psi0_dims(xs, Ws, seed=4).astype(np.complex64)
+    out = {}
+    for fold in (True, False):
+        if fold:
+            monkeypatch.delenv("MM_NO_FOLD", raising=False)
+        else:
+            monkeypatch.setenv("MM_NO_FOLD", "1")
+        hp = mm.HermitePlan(ctx, list(dims), prec="f16x6")
+        g = to_gpu(torch, psi0, torch.complex64)
+        hp.gpe_step(g, beta, tau, nsteps)
+        torch.cuda.synchronize()
+        ctx.status()
+        assert hp.fold() == (7 if fold else 0)  # the propagators (and their folded forms) exist now
+        out[fold] = g.cpu().numpy()
+    monkeypatch.delenv("MM_NO_FOLD", raising=False)
+    ref = _strang_fp64(orc, psi0, xs, Ws, beta, tau, nsteps)
+    w3 = Ws[2][:, None, None] * Ws[1][None, :, None] * Ws[0][None, None, :]
+    e_fold, e_unf = orc.rel_l2(out[True], ref, w3), orc.rel_l2(out[False], ref, w3)
+    print(f"GPE fold dims={dims}: {e_fold:.3e} against FP64 (unfolded {e_unf:.3e})")
+    assert e_fold <= 1e-6 and e_unf <= 1e-6
+    assert rel(out[True], out[False]) <= 2e-6
+
+
 def test_autotune_cache(env, orc, tmp_path, monkeypatch):
     """With MM_AUTOTUNE_CACHE set, the first tuning of a plan appends one JSON
     line; a second plan with the same key takes that configuration without
