@@ -1694,8 +1694,9 @@ mm_status gpe_steps(mm_plan *p, void *psi, double beta, double tau, int64_t nste
             D[v] = &p->PFtc[full][v];
         }
         // the tensor work of nsteps + 1 sweeps saved against the fold and unfold (32 bytes a point)
-        // and the nsteps phase passes (the pieces read and written: 24 bytes a point each)
-        const double cost_s = double(32 + 24 * nsteps) * double(p->count) / 6.5e12;
+        // and the nsteps phase passes: each reads and writes 24 bytes a point but takes about as
+        // long as 40 would at the HBM rate (it is bound by its instructions and load latency)
+        const double cost_s = double(32 + 40 * nsteps) * double(p->count) / 6.5e12;
         folded = p->fold_force || double(nsteps + 1) * fold_saved_s(p, fm, U, D) > cost_s;
     }
     if (folded) {

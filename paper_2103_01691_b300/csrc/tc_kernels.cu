@@ -973,8 +973,22 @@ struct PiecesV<2> {
     using T = uint32_t;
 };
 
+// sin and cos of the nonlinear phase: by their Taylor series about 0 for |a| <= 1/4 (the first
+// omitted terms, a^11 / 11! and a^10 / 10!, are below 3e-13), else sincosf.  The phase tau beta
+// |psi|^2 of a step is usually far below 1/4.
+__device__ __forceinline__ void sincos_phase(float a, float &sn, float &cs)
+{
+    if (fabsf(a) <= 0.25f) {
+        const float a2 = a * a;
+        sn = a * (1.0f + a2 * (-1.0f / 6.0f + a2 * (1.0f / 120.0f + a2 * (-1.0f / 5040.0f + a2 * (1.0f / 362880.0f)))));
+        cs = 1.0f + a2 * (-0.5f + a2 * (1.0f / 24.0f + a2 * (-1.0f / 720.0f + a2 * (1.0f / 40320.0f))));
+    } else {
+        sincosf(a, &sn, &cs);
+    }
+}
+
 template <int F, int V>
-__global__ void phase_fold_kernel_reg(PhaseFoldDims g, uint32_t reps, uint32_t plane, int p0, int p1, int p2,
+__global__ void __launch_bounds__(256, 4) phase_fold_kernel_reg(PhaseFoldDims g, uint32_t reps, uint32_t plane, int p0, int p1, int p2,
                                        const uint16_t *__restrict__ in, uint16_t *__restrict__ out,
                                        const unsigned *max_in, float *s_out, float tb, int *err)
 {
@@ -1015,18 +1029,33 @@ __global__ void phase_fold_kernel_reg(PhaseFoldDims g, uint32_t reps, uint32_t p
                 T w[3];
 #pragma unroll
                 for (int p = 0; p < 3; ++p) w[p] = *reinterpret_cast<const T *>(in + (3 * c + p) * plane + o);
-                const uint16_t *h0 = reinterpret_cast<const uint16_t *>(&w[0]);
-                const uint16_t *h1 = reinterpret_cast<const uint16_t *>(&w[1]);
-                const uint16_t *h2 = reinterpret_cast<const uint16_t *>(&w[2]);
+                float x[V];
+                if constexpr (V >= 2) {  // paired conversions, the same values
+                    const __half2 *q0 = reinterpret_cast<const __half2 *>(&w[0]);
+                    const __half2 *q1 = reinterpret_cast<const __half2 *>(&w[1]);
+                    const __half2 *q2 = reinterpret_cast<const __half2 *>(&w[2]);
+#pragma unroll
+                    for (int jp = 0; jp < V / 2; ++jp) {
+                        const float2 f0 = __half22float2(q0[jp]), f1 = __half22float2(q1[jp]),
+                                     f2 = __half22float2(q2[jp]);
+                        x[2 * jp] = s_in * (f0.x + (f1.x + f2.x));
+                        x[2 * jp + 1] = s_in * (f0.y + (f1.y + f2.y));
+                    }
+                } else {
+                    const uint16_t *h0 = reinterpret_cast<const uint16_t *>(&w[0]);
+                    const uint16_t *h1 = reinterpret_cast<const uint16_t *>(&w[1]);
+                    const uint16_t *h2 = reinterpret_cast<const uint16_t *>(&w[2]);
+#pragma unroll
+                    for (int j = 0; j < V; ++j)
+                        x[j] = s_in * (__half2float(__ushort_as_half(h0[j])) +
+                                       (__half2float(__ushort_as_half(h1[j])) + __half2float(__ushort_as_half(h2[j]))));
+                }
 #pragma unroll
                 for (int j = 0; j < V; ++j) {
-                    const float x = s_in * (__half2float(__ushort_as_half(h0[j])) +
-                                            (__half2float(__ushort_as_half(h1[j])) +
-                                             __half2float(__ushort_as_half(h2[j]))));
                     if (c == 0)
-                        z[sp][j].x = x;
+                        z[sp][j].x = x[j];
                     else
-                        z[sp][j].y = x;
+                        z[sp][j].y = x[j];
                 }
             }
         }
@@ -1047,7 +1076,7 @@ __global__ void phase_fold_kernel_reg(PhaseFoldDims g, uint32_t reps, uint32_t p
             for (int sp = 0; sp < (1 << F); ++sp) {
                 const float xr = z[sp][j].x, xi = z[sp][j].y;
                 float sn, cs;
-                sincosf(tb * (xr * xr + xi * xi), &sn, &cs);
+                sincos_phase(tb * (xr * xr + xi * xi), sn, cs);
                 z[sp][j] = make_float2(xr * cs + xi * sn, xi * cs - xr * sn);
             }
 #pragma unroll
@@ -1066,13 +1095,27 @@ __global__ void phase_fold_kernel_reg(PhaseFoldDims g, uint32_t reps, uint32_t p
         for (int sp = 0; sp < (1 << F); ++sp) {
             if (uint32_t(sp) & ~pm) continue;
             T w[6];
-            uint16_t *hw = reinterpret_cast<uint16_t *>(w);
+            if constexpr (V >= 2) {  // paired conversions, the same pieces
+                uint32_t *u[6];
 #pragma unroll
-            for (int j = 0; j < V; ++j) {
-                const float xr = z[sp][j].x * inv_out, xi = z[sp][j].y * inv_out;
-                range_ok &= fabsf(xr) < 16384.0f && fabsf(xi) < 16384.0f;
-                split_fx_scaled(xr, hw[0 * V + j], hw[1 * V + j], hw[2 * V + j]);
-                split_fx_scaled(xi, hw[3 * V + j], hw[4 * V + j], hw[5 * V + j]);
+                for (int p = 0; p < 6; ++p) u[p] = reinterpret_cast<uint32_t *>(&w[p]);
+#pragma unroll
+                for (int jp = 0; jp < V / 2; ++jp) {
+                    const float r0 = z[sp][2 * jp].x * inv_out, r1 = z[sp][2 * jp + 1].x * inv_out;
+                    const float i0 = z[sp][2 * jp].y * inv_out, i1 = z[sp][2 * jp + 1].y * inv_out;
+                    range_ok &= fmaxf(fmaxf(fabsf(r0), fabsf(r1)), fmaxf(fabsf(i0), fabsf(i1))) < 16384.0f;
+                    split_fx_pair(r0, r1, u[0][jp], u[1][jp], u[2][jp]);
+                    split_fx_pair(i0, i1, u[3][jp], u[4][jp], u[5][jp]);
+                }
+            } else {
+                uint16_t *hw = reinterpret_cast<uint16_t *>(w);
+#pragma unroll
+                for (int j = 0; j < V; ++j) {
+                    const float xr = z[sp][j].x * inv_out, xi = z[sp][j].y * inv_out;
+                    range_ok &= fabsf(xr) < 16384.0f && fabsf(xi) < 16384.0f;
+                    split_fx_scaled(xr, hw[0 * V + j], hw[1 * V + j], hw[2 * V + j]);
+                    split_fx_scaled(xi, hw[3 * V + j], hw[4 * V + j], hw[5 * V + j]);
+                }
             }
 #pragma unroll
             for (int p = 0; p < 6; ++p) *reinterpret_cast<T *>(out + p * plane + off[sp]) = w[p];
