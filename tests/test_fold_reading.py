@@ -1,7 +1,10 @@
 """Pins for the even/odd folding the tensor-core path runs on (a change of basis, not from the
 paper): the propagators it folds are centrosymmetric, their folded form is block-diagonal, and
 steps taken in the folded basis (the GPE's nonlinear phase applied between unfold and refold)
-give the oracle's results.  Everything here is FP64 numpy around the oracle; CPU only."""
+give the oracle's results (FP64 numpy around the oracle); and the phase pass's short series for
+sine and cosine holds FP32 accuracy.  CPU only."""
+import math
+
 import numpy as np
 import pytest
 
@@ -49,7 +52,7 @@ def test_dirichlet_propagator_is_centrosymmetric_and_folds_block_diagonal(orc, n
     D = F @ E @ np.linalg.inv(F)
     c = (n + 1) // 2
     assert np.max(np.abs(D[:c, c:])) <= 1e-14 and np.max(np.abs(D[c:, :c])) <= 1e-14
-    # a matrix that is not centrosymmetric (the periodic Laplacian's shifted copy) does not fold
+    # a matrix that is not centrosymmetric (one off-diagonal entry doubled) does not fold
     A = orc.fd_dirichlet(n)
     A[0, 1] *= 2.0
     Dn = F @ A @ np.linalg.inv(F)
@@ -118,3 +121,23 @@ def test_folded_gpe_steps_equal_oracle(orc, m):
     wrong = apply_all(v, [hermite_propagator(orc, m, 0.5 * tau)] * 3)
     one = orc.gpe_steps(psi0, x, W, beta, tau, 1)
     assert np.max(np.abs(wrong - one)) > 1e-6 * np.max(np.abs(one))
+
+
+def test_phase_series_error_bound():
+    """The folded GPE's phase pass takes sin a and cos a for |a| <= 1/4 from their Taylor series
+    (through a^9 and a^8, Horner form, FP32).  Evaluated the same way in FP32 here, both stay
+    within 2 units in the last place of FP32 of the FP64 library values over the whole range:
+    the truncation (below 3e-13) is far under FP32 rounding."""
+    a = np.linspace(-0.25, 0.25, 200001, dtype=np.float32)
+    a2 = a * a
+    f = np.float32
+    sn = a * (f(1) + a2 * (f(-1 / 6) + a2 * (f(1 / 120) + a2 * (f(-1 / 5040) + a2 * f(1 / 362880)))))
+    cs = f(1) + a2 * (f(-0.5) + a2 * (f(1 / 24) + a2 * (f(-1 / 720) + a2 * f(1 / 40320))))
+    ad = a.astype(np.float64)
+    ulp_s = np.spacing(np.abs(np.sin(ad)).astype(np.float32)).astype(np.float64)
+    ulp_c = np.spacing(np.cos(ad).astype(np.float32)).astype(np.float64)
+    nz = ad != 0
+    assert np.all(np.abs(sn[nz] - np.sin(ad[nz])) <= 2 * ulp_s[nz])
+    assert np.all(np.abs(cs - np.cos(ad)) <= 2 * ulp_c)
+    # the first omitted terms, at the end of the range
+    assert 0.25 ** 11 / math.factorial(11) < 3e-13 and 0.25 ** 10 / math.factorial(10) < 3e-13
