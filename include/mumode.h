@@ -508,6 +508,20 @@ mm_status hkmp_plan_create(mm_ctx *ctx, int d, const int64_t *n, const double *c
                            const double *const *U_nodes, double tau, mm_dtype dtype, mm_prec prec, mm_plan **out);
 mm_status hkmp_evolve(mm_plan *plan, void *psi_dev, int64_t nsteps, const double *f_mid, void *stream);
 
+/* Declares a range [f_lo, f_hi] that f_mid takes (not from the paper; for
+ * f = sin^2 t, [0, 1]).  The plan computes the exponentials at the K
+ * Chebyshev nodes of that range once (K = 4..12 by the bound above, on
+ * stream, which is synchronised) and keeps them; from then on every chunk
+ * of hkmp_evolve whose f values all lie in the range combines its steps'
+ * exponentials from those nodes instead of computing nodes of its own
+ * (chunks with a value outside it do as before).  The interpolation error
+ * stays below 1e-14, under the pieces' resolution.  f_lo >= f_hi drops a
+ * declared range.  Errors: MM_ERR_INVALID_ARG (not an HKMP plan, a bound
+ * not finite, a range needing more than 12 nodes), MM_ERR_UNSUPPORTED (an
+ * FP64 plan: its steps take exact exponentials), MM_ERR_OOM (12 matrices
+ * per time-dependent direction), MM_ERR_CUDA. */
+mm_status hkmp_set_f_range(mm_plan *plan, double f_lo, double f_hi, void *stream);
+
 /* nsteps Strang steps of i psi_t = -1/2 Lap psi + |x|^2/2 psi + beta |psi|^2 psi
  * (section 4.5): half linear step, exact nonlinear phase
  * psi <- psi exp(-i tau beta |psi|^2), half linear step.  Adjacent linear

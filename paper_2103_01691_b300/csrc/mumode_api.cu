@@ -126,6 +126,11 @@ struct mm_plan {
     // device interpolation weights of a chunk (cap x kInterpNodes)
     double2 *hk_nodesE[mm::kMaxDims] = {};
     double *hk_w = nullptr;
+    // hkmp_set_f_range: the exponentials at hk_rK Chebyshev nodes of a declared f range
+    // [hk_rlo, hk_rhi], kept with the plan (hk_rK = 0: none)
+    double2 *hk_rangeE[mm::kMaxDims] = {};
+    double hk_rlo = 0.0, hk_rhi = 0.0;
+    int hk_rK = 0;
     void *coef = nullptr;  // coefficient tensor of hkmp_evolve
     mm::ExpmBatch expmb;
     // HKMP with one time-dependent direction and harmonic others: a step is that direction's
@@ -1511,6 +1516,7 @@ void mm_plan_destroy(mm_plan *p)
         if (p->Gdev[v]) cudaFree(p->Gdev[v]);
         if (p->Ebatch[v]) cudaFree(p->Ebatch[v]);
         if (p->hk_nodesE[v]) cudaFree(p->hk_nodesE[v]);
+        if (p->hk_rangeE[v]) cudaFree(p->hk_rangeE[v]);
     }
     if (p->coef) cudaFree(p->coef);
     if (p->hk_w) cudaFree(p->hk_w);
@@ -2617,6 +2623,99 @@ extern "C" mm_status hkmp_plan_create(mm_ctx *ctx, int d, const int64_t *n, cons
     return MM_OK;
 }
 
+namespace {
+
+// The fewest Chebyshev nodes (4..kInterpNodes) whose interpolation error bound for
+// exp(-i tau (H0 + f G)) over f in [flo, fhi], 2 (tau ||G|| (fhi - flo) / 4)^K / K!, is below
+// 1e-14 in every time-dependent direction; kInterpNodes + 1 when none is.
+int hk_nodes_for(const mm_plan *p, double flo, double fhi)
+{
+    int K = 0;
+    for (int v = 0; v < p->d; ++v) {
+        if (!p->H0dev[v]) continue;
+        const double x = std::fabs(p->tau) * p->gnorm[v] * (fhi - flo) / 4.0;
+        int k = 4;
+        double bound = 2.0 * std::pow(x, 4) / 24.0;
+        while (bound > 1e-14 && k < mm::kInterpNodes) {
+            ++k;
+            bound *= x / k;
+        }
+        if (bound > 1e-14) k = mm::kInterpNodes + 1;
+        K = std::max(K, k);
+    }
+    return K;
+}
+
+// The K Chebyshev points of the first kind of [flo, fhi] and their barycentric weights.
+void hk_cheb_nodes(double flo, double fhi, int K, double *nodes, double *bw)
+{
+    const double mid = 0.5 * (flo + fhi), half = 0.5 * (fhi - flo), pi = 3.14159265358979323846;
+    for (int j = 0; j < K; ++j) {
+        const double th = (2 * j + 1) * pi / (2 * K);
+        nodes[j] = mid + half * std::cos(th);
+        bw[j] = (j % 2 ? -1.0 : 1.0) * std::sin(th);
+    }
+}
+
+// W[q K + j]: the Lagrange basis of the nodes at f[q] (barycentric form), q < cnt.
+void hk_lagrange(const double *nodes, const double *bw, int K, const double *f, int cnt, double *W)
+{
+    for (int q = 0; q < cnt; ++q) {
+        const double x = f[q];
+        double *w = W + size_t(q) * K, sum = 0.0;
+        int hit = -1;
+        for (int j = 0; j < K && hit < 0; ++j)
+            if (x == nodes[j]) hit = j;
+        for (int j = 0; j < K; ++j) {
+            w[j] = hit >= 0 ? (j == hit ? 1.0 : 0.0) : bw[j] / (x - nodes[j]);
+            sum += w[j];
+        }
+        for (int j = 0; j < K; ++j) w[j] /= sum;
+    }
+}
+
+}  // namespace
+
+extern "C" mm_status hkmp_set_f_range(mm_plan *p, double f_lo, double f_hi, void *stream)
+{
+    NvtxRange range("hkmp_set_f_range");
+    if (!p || !p->hkmp) return fail(MM_ERR_INVALID_ARG, "not an HKMP plan");
+    if (!std::isfinite(f_lo) || !std::isfinite(f_hi)) return fail(MM_ERR_INVALID_ARG, "f range not finite");
+    if (f_lo >= f_hi) {  // drop the range
+        p->hk_rK = 0;
+        return MM_OK;
+    }
+    if (!p->tc || !p->hk_w) return fail(MM_ERR_UNSUPPORTED, "a declared f range needs a tensor-core HKMP plan");
+    const int K = hk_nodes_for(p, f_lo, f_hi);
+    if (K > mm::kInterpNodes)
+        return fail(MM_ERR_INVALID_ARG, "f range [%g, %g] needs more than %d interpolation nodes", f_lo, f_hi,
+                    mm::kInterpNodes);
+    cudaStream_t s = (cudaStream_t)stream;
+    p->hk_rK = 0;  // invalid until the new nodes are in place
+    double nodes[mm::kInterpNodes], bw[mm::kInterpNodes];
+    hk_cheb_nodes(f_lo, f_hi, K, nodes, bw);
+    const double fmax = std::max(std::fabs(f_lo), std::fabs(f_hi));
+    for (int v = 0; v < p->d; ++v) {
+        if (!p->H0dev[v]) continue;
+        if (!p->hk_rangeE[v] && cudaMalloc(&p->hk_rangeE[v], sizeof(double2) * size_t(mm::kInterpNodes) *
+                                                                  size_t(p->n[v] * p->n[v])) != cudaSuccess) {
+            p->hk_rangeE[v] = nullptr;
+            return fail(MM_ERR_OOM, "node exponentials of the f range");
+        }
+        const double bound = p->h0norm[v] + fmax * p->gnorm[v];
+        cudaError_t e = mm::expm_imag_batched(&p->expmb, int(p->n[v]), p->H0dev[v], p->Gdev[v], nodes, K, -p->tau,
+                                              bound, p->hk_rangeE[v], s, p->hshift[v], 2.0);
+        if (e != cudaSuccess) return cuda_fail(e, "node exponentials of the f range");
+    }
+    // the nodes are read by asynchronous copies
+    cudaError_t e = cudaStreamSynchronize(s);
+    if (e != cudaSuccess) return cuda_fail(e, "node exponentials of the f range");
+    p->hk_rlo = f_lo;
+    p->hk_rhi = f_hi;
+    p->hk_rK = K;
+    return MM_OK;
+}
+
 extern "C" mm_status hkmp_evolve(mm_plan *p, void *psi, int64_t nsteps, const double *f_mid, void *stream)
 {
     NvtxRange range("hkmp_evolve");
@@ -2650,43 +2749,28 @@ extern "C" mm_status hkmp_evolve(mm_plan *p, void *psi, int64_t nsteps, const do
             flo = std::min(flo, f_mid[k0 + q]);
             fhi = std::max(fhi, f_mid[k0 + q]);
         }
-        // the fewest nodes whose error bound is below 1e-14, over the time-dependent directions
-        int K = 0;
-        for (int v = 0; v < p->d; ++v) {
-            if (!p->H0dev[v]) continue;
-            const double x = std::fabs(p->tau) * p->gnorm[v] * (fhi - flo) / 4.0;
-            int k = 4;
-            double bound = 2.0 * std::pow(x, 4) / 24.0;
-            while (bound > 1e-14 && k < Kmax) {
-                ++k;
-                bound *= x / k;
-            }
-            if (bound > 1e-14) k = Kmax + 1;  // too wide a range: no interpolation
-            K = std::max(K, k);
+        // a declared f range that holds the chunk: its node exponentials, combined only
+        if (interp && p->hk_rK > 0 && flo >= p->hk_rlo && fhi <= p->hk_rhi) {
+            const int K = p->hk_rK;
+            double *nodes = ihost.data() + size_t(k0 / cap) * size_t(Kmax + size_t(cap) * Kmax);
+            double *W = nodes + Kmax, bw[mm::kInterpNodes];
+            hk_cheb_nodes(p->hk_rlo, p->hk_rhi, K, nodes, bw);
+            hk_lagrange(nodes, bw, K, f_mid + k0, cnt, W);
+            cudaError_t e = cudaMemcpyAsync(p->hk_w, W, sizeof(double) * size_t(cnt) * K, cudaMemcpyHostToDevice, s);
+            for (int v = 0; v < p->d && e == cudaSuccess; ++v)
+                if (p->H0dev[v])
+                    e = mm::combine_interp_nodes(int(p->n[v]), cnt, K, p->hk_w, p->hk_rangeE[v], p->Ebatch[v], s);
+            return e == cudaSuccess ? MM_OK : cuda_fail(e, "exponentials from the f range's nodes");
         }
+        // the fewest nodes whose error bound is below 1e-14, over the time-dependent directions
+        const int K = hk_nodes_for(p, flo, fhi);
         const bool use_interp = interp && K <= Kmax && cnt > K && fhi > flo;
         double *nodes = nullptr;
         if (use_interp) {
             nodes = ihost.data() + size_t(k0 / cap) * size_t(Kmax + size_t(cap) * Kmax);
             double *W = nodes + Kmax, bw[mm::kInterpNodes];
-            const double mid = 0.5 * (flo + fhi), half = 0.5 * (fhi - flo), pi = 3.14159265358979323846;
-            for (int j = 0; j < K; ++j) {  // Chebyshev points of the first kind, barycentric weights
-                const double th = (2 * j + 1) * pi / (2 * K);
-                nodes[j] = mid + half * std::cos(th);
-                bw[j] = (j % 2 ? -1.0 : 1.0) * std::sin(th);
-            }
-            for (int q = 0; q < cnt; ++q) {  // Lagrange basis at f_k (barycentric form)
-                const double x = f_mid[k0 + q];
-                double *w = W + size_t(q) * K, sum = 0.0;
-                int hit = -1;
-                for (int j = 0; j < K && hit < 0; ++j)
-                    if (x == nodes[j]) hit = j;
-                for (int j = 0; j < K; ++j) {
-                    w[j] = hit >= 0 ? (j == hit ? 1.0 : 0.0) : bw[j] / (x - nodes[j]);
-                    sum += w[j];
-                }
-                for (int j = 0; j < K; ++j) w[j] /= sum;
-            }
+            hk_cheb_nodes(flo, fhi, K, nodes, bw);  // Chebyshev points of the first kind
+            hk_lagrange(nodes, bw, K, f_mid + k0, cnt, W);
             cudaError_t e = cudaMemcpyAsync(p->hk_w, W, sizeof(double) * size_t(cnt) * K, cudaMemcpyHostToDevice, s);
             if (e != cudaSuccess) return cuda_fail(e, "interpolation weights");
         }

@@ -67,6 +67,7 @@ SIGNATURES = {
     "hkmp_plan_create": (_i, [_vp, _i, _i64p, ctypes.POINTER(_dp), ctypes.POINTER(_dp), ctypes.c_double, _i, _i,
                               ctypes.POINTER(_vp)]),
     "hkmp_evolve": (_i, [_vp, _vp, _i64, _dp, _vp]),
+    "hkmp_set_f_range": (_i, [_vp, ctypes.c_double, ctypes.c_double, _vp]),
     "mm_pipe_operators": (_i, [_i, _i, ctypes.c_double, ctypes.c_double, ctypes.c_double, ctypes.c_double, _dp, _dp,
                                _dp]),
     "pipe_plan_create": (_i, [_vp, _i, _i, ctypes.c_double, ctypes.c_double, ctypes.c_double, ctypes.c_double, _dp,
@@ -539,6 +540,11 @@ class HKMPPlan:
         _check(lib().hkmp_plan_create(ctx.handle, d, self.dims.ctypes.data_as(_i64p), vp, up, float(tau), code,
                                       PREC[prec], ctypes.byref(h)))
         self.handle = h
+
+    def set_f_range(self, f_lo: float, f_hi: float, stream=None):
+        """hkmp_set_f_range: the exponentials at the Chebyshev nodes of [f_lo, f_hi], computed
+        once and used by every later chunk of steps whose f values lie in the range."""
+        _check(lib().hkmp_set_f_range(self.handle, float(f_lo), float(f_hi), _stream(stream)))
 
     def evolve(self, psi, f_mid, stream=None):
         """len(f_mid) Magnus steps on the values psi (in place); f_mid[k] = f(t_k + tau/2)."""

@@ -577,6 +577,50 @@ def test_hkmp_vs_oracle(env, orc, prec, tdir, variant):
 # ---------------------------------------------------------- pipe flow (section 4.2)
 
 
+def test_hkmp_declared_f_range(env, orc):
+    """hkmp_set_f_range(0, 1) for f = sin^2 t: the node exponentials are computed once and every
+    chunk combines from them.  Against the oracle's literal Magnus steps and the plan without a
+    range (the two exponentials differ below the pieces' resolution); a range that does not hold
+    the values, and a dropped range, give the plan's own per-chunk nodes bit for bit; a range too
+    wide for 12 nodes and an FP64 plan are refused."""
+    mm, ctx, torch = env
+    n = (40, 24, 36)
+    xs, Ws = _hkmp_case(orc, n)
+    Vs, Us = inputs.hkmp_potentials(*xs)
+    tau, steps = 0.025, 40
+    f_mid = inputs.hkmp_f_mid(tau, steps)
+    psi0 = inputs.hkp_psi0(*xs).astype(np.complex64)
+    ref = orc.hkmp_steps(psi0.astype(complex), xs, Ws, Vs, Us, tau, f_mid)
+    xl = [mm.gauss_hermite(v)[0] for v in n]
+    _, Ul = inputs.hkmp_potentials(*xl)
+
+    def run(rng):
+        plan = mm.HKMPPlan(ctx, n, [None, None, None], list(Ul), tau, prec="f16x6")
+        if rng is not None:
+            plan.set_f_range(*rng)
+        psi = to_gpu(torch, psi0, torch.complex64)
+        plan.evolve(psi, f_mid)
+        torch.cuda.synchronize()
+        ctx.status()
+        return psi.cpu().numpy()
+
+    base, ranged = run(None), run((0.0, 1.0))
+    w3 = Ws[2][:, None, None] * Ws[1][None, :, None] * Ws[0][None, None, :]
+    e_base, e_rng = orc.rel_l2(base, ref, w3), orc.rel_l2(ranged, ref, w3)
+    print(f"HKMP declared f range: {e_rng:.3e} against the oracle (per-chunk nodes {e_base:.3e}), "
+          f"{rel(ranged, base):.2e} between them")
+    assert e_rng <= 5e-6 and rel(ranged, base) <= 1e-6
+    assert f_mid.min() < 0.5  # the next range misses some values: every chunk takes its own nodes
+    assert np.array_equal(run((0.5, 1.0)).view(np.uint32), base.view(np.uint32))
+    assert np.array_equal(run((1.0, 0.0)).view(np.uint32), base.view(np.uint32))  # dropped
+    plan = mm.HKMPPlan(ctx, n, [None, None, None], list(Ul), tau, prec="f16x6")
+    with pytest.raises(mm.MumodeError, match="MM_ERR_INVALID_ARG"):
+        plan.set_f_range(0.0, 1e7)
+    p64 = mm.HKMPPlan(ctx, n, [None, None, None], list(Ul), tau, prec="fp64dmma")
+    with pytest.raises(mm.MumodeError, match="MM_ERR_UNSUPPORTED"):
+        p64.set_f_range(0.0, 1.0)
+
+
 @pytest.mark.parametrize("tdir,variant", [(3, None), (1, "one_sm")])
 def test_hkmp_interpolated_exponentials(env, orc, tdir, variant):
     """Tensor-core HKMP with more than 12 steps in a chunk takes the chunk's
