@@ -117,7 +117,9 @@ void tc_matrix_destroy(TcMatrix *M);
 // Rewrite the pieces (all layouts) and row scales of M from a device
 // matrix E (n_out x n_in complex FP64, row-major), in stream order.  The
 // k-block bands are not touched: call tc_matrix_full_bands once first.
-cudaError_t tc_matrix_update(TcMatrix &M, const double2 *E, cudaStream_t s);
+// With only_for set, only the layout that variant's products read is written (the others are
+// then stale until the next full update); the row scales always are.
+cudaError_t tc_matrix_update(TcMatrix &M, const double2 *E, cudaStream_t s, const TcVariant *only_for = nullptr);
 void tc_matrix_full_bands(TcMatrix &M);
 // Device FP64 matrix exponential E = exp(z (A + f B)) (expm_device.cu).
 struct ExpmWorkspace {

@@ -2803,7 +2803,8 @@ extern "C" mm_status hkmp_evolve(mm_plan *p, void *psi, int64_t nsteps, const do
                 Ed[v] = E;
                 continue;
             }
-            cudaError_t e = mm::tc_matrix_update(p->Etc[v], E, s);
+            // each step's matrix is split again before its product: only the variant's layout
+            cudaError_t e = mm::tc_matrix_update(p->Etc[v], E, s, &p->variant);
             if (e != cudaSuccess) return cuda_fail(e, "matrix update");
         }
         return MM_OK;

@@ -479,11 +479,12 @@ __global__ void matrix_update_kernel(const double2 *__restrict__ E, int64_t m, i
         const double2 e = E[i * n + j];
         entry_pieces(e.x, e.y, r, npieces, fixed, bits);
         const int64_t kb = j / 16, jj = j % 16;
-        for (int p = 0; p < npieces; ++p)
-            for (int w = 0; w < kBlocks; ++w) {
-                const int64_t row = (((int64_t(p) * ni + tile) * kbs + kb) * kBlocks + w) * it + il;
-                pieces[row * 16 + jj] = bits[p][w];
-            }
+        if (pieces)
+            for (int p = 0; p < npieces; ++p)
+                for (int w = 0; w < kBlocks; ++w) {
+                    const int64_t row = (((int64_t(p) * ni + tile) * kbs + kb) * kBlocks + w) * it + il;
+                    pieces[row * 16 + jj] = bits[p][w];
+                }
         for (int k = 0; k < 2; ++k) {
             uint16_t *pp = k == 0 ? pp0 : pp1;
             const int itk = k == 0 ? it0 : it1;
@@ -503,15 +504,23 @@ __global__ void matrix_update_kernel(const double2 *__restrict__ E, int64_t m, i
     }
 }
 
-cudaError_t tc_matrix_update(TcMatrix &M, const double2 *E, cudaStream_t s)
+static const TcMatrix::TcPairTiles *pair_tiles(const TcMatrix &M, TcVariant v);
+
+cudaError_t tc_matrix_update(TcMatrix &M, const double2 *E, cudaStream_t s, const TcVariant *only_for)
 {
     if (!M.pieces || !E || (M.fixed && !M.rho)) return cudaErrorInvalidValue;
     const size_t smem = sizeof(double) * size_t(pow2_at_least(M.n_in));
     if (smem > 48 * 1024) return cudaErrorInvalidValue;  // n_in <= 4096
+    void *one = M.pieces, *pp0 = M.pair[0].pieces, *pp1 = M.pair[1].pieces;
+    if (only_for) {  // the layout the variant's products read: its pair tiling, else the one-SM layout
+        const TcMatrix::TcPairTiles *PT = pair_tiles(M, *only_for);
+        one = PT ? nullptr : M.pieces;
+        pp0 = PT == &M.pair[0] ? M.pair[0].pieces : nullptr;
+        pp1 = PT == &M.pair[1] ? M.pair[1].pieces : nullptr;
+    }
     matrix_update_kernel<<<unsigned(M.n_out), 128, smem, s>>>(
-        E, M.n_out, M.n_in, M.npieces, M.fixed, M.ni, M.it, M.k_pad / 16, static_cast<uint16_t *>(M.pieces), M.rho,
-        static_cast<uint16_t *>(M.pair[0].pieces), M.pair[0].it, static_cast<uint16_t *>(M.pair[1].pieces),
-        M.pair[1].it);
+        E, M.n_out, M.n_in, M.npieces, M.fixed, M.ni, M.it, M.k_pad / 16, static_cast<uint16_t *>(one), M.rho,
+        static_cast<uint16_t *>(pp0), M.pair[0].it, static_cast<uint16_t *>(pp1), M.pair[1].it);
     count_launch();
     return cudaGetLastError();
 }
