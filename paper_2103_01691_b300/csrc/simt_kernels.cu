@@ -522,7 +522,7 @@ __global__ void fold_kernel(FoldDims f, int64_t reps, const float2 *__restrict__
 // Orbit pattern sp (bit b: direction pv[b]) exists where every set bit's direction has a mirror
 // pair at this orbit (pm); at the middle index of an odd length the direction has none and its
 // butterfly is the identity.
-template <int F, bool INV>
+template <int F, bool INV, bool NORM>
 __global__ void fold_kernel_reg(FoldDims f, uint32_t reps, int p0, int p1, int p2, const float2 *__restrict__ in,
                                 float2 *__restrict__ out)
 {
@@ -543,6 +543,34 @@ __global__ void fold_kernel_reg(FoldDims f, uint32_t reps, int p0, int p1, int p
                     mir[b] = (uint32_t(f.n[v]) - 1u - 2u * r) * uint32_t(f.stride[v]);
                     odd[b] = uint32_t(f.c[v]) * uint32_t(f.stride[v]);
                     if (r < uint32_t(f.h[v])) pm |= 1u << b;
+                }
+        }
+        // the unfold's weighted norm: the weight of every orbit point (FP64), built as products
+        // over the folded directions' weights at r and at the mirror and the other directions'
+        double wsp[1 << F];
+        if (NORM) {
+            double wa[3] = {1.0, 1.0, 1.0}, wm[3] = {1.0, 1.0, 1.0}, wrest = 1.0;
+#pragma unroll
+            for (int v = 0; v < kMaxDims; ++v) {
+                if (v >= f.d) break;
+                if (!f.w[v]) continue;
+                bool folded_v = false;
+#pragma unroll
+                for (int b = 0; b < F; ++b)
+                    if (pv[b] == v) {
+                        folded_v = true;
+                        wa[b] = f.w[v][rv[v]];
+                        wm[b] = f.w[v][uint32_t(f.n[v]) - 1u - rv[v]];
+                    }
+                if (!folded_v) wrest *= f.w[v][rv[v]];
+            }
+            wsp[0] = wrest;
+#pragma unroll
+            for (int b = 0; b < F; ++b)
+#pragma unroll
+                for (int sp = (1 << b) - 1; sp >= 0; --sp) {
+                    wsp[sp | (1 << b)] = wsp[sp] * wm[b];
+                    wsp[sp] *= wa[b];
                 }
         }
         float2 buf[1 << F];
@@ -576,11 +604,11 @@ __global__ void fold_kernel_reg(FoldDims f, uint32_t reps, int p0, int p1, int p
             for (int b = 0; b < F; ++b)
                 if ((sp >> b) & 1) off += INV ? mir[b] : odd[b];
             out[off] = buf[sp];
-            if (INV && f.norm2)
-                acc += (double(buf[sp].x) * buf[sp].x + double(buf[sp].y) * buf[sp].y) * orbit_weight(f, rv, pv, F, sp);
+            if (NORM)  // |out|^2 in FP32 (its rounding is unbiased), times the FP64 weight
+                acc += wsp[sp] * double(buf[sp].x * buf[sp].x + buf[sp].y * buf[sp].y);
         }
     }
-    if (INV && f.norm2) block_sum_add(acc, f.norm2);
+    if (NORM) block_sum_add(acc, f.norm2);
 }
 
 cudaError_t fold_state(int d, const int64_t *n, unsigned mask, bool inverse, const void *in, void *out, cudaStream_t s,
@@ -616,9 +644,10 @@ cudaError_t fold_state(int d, const int64_t *n, unsigned mask, bool inverse, con
         const float2 *i2 = (const float2 *)in;
         float2 *o2 = (float2 *)out;
         const uint32_t r32 = uint32_t(reps);
-#define MM_FOLD(FF)                                                                                      \
-    (inverse ? (fold_kernel_reg<FF, true><<<unsigned(blocks), 256, 0, s>>>(f, r32, pv[0], pv[1], pv[2], i2, o2), 0) \
-             : (fold_kernel_reg<FF, false><<<unsigned(blocks), 256, 0, s>>>(f, r32, pv[0], pv[1], pv[2], i2, o2), 0))
+#define MM_FOLD(FF)                                                                                            \
+    (norm2 ? (fold_kernel_reg<FF, true, true><<<unsigned(blocks), 256, 0, s>>>(f, r32, pv[0], pv[1], pv[2], i2, o2), 0) \
+     : inverse ? (fold_kernel_reg<FF, true, false><<<unsigned(blocks), 256, 0, s>>>(f, r32, pv[0], pv[1], pv[2], i2, o2), 0) \
+               : (fold_kernel_reg<FF, false, false><<<unsigned(blocks), 256, 0, s>>>(f, r32, pv[0], pv[1], pv[2], i2, o2), 0))
         if (F == 1) MM_FOLD(1);
         else if (F == 2) MM_FOLD(2);
         else MM_FOLD(3);

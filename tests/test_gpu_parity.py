@@ -1274,9 +1274,10 @@ def test_ho_fold_matches_unfolded(env, orc, monkeypatch, m):
     assert not np.array_equal(gpe[True].view(np.uint32), gpe[False].view(np.uint32)), "the GPE steps ran folded"
     assert np.array_equal(gnorm[True].view(np.uint32), gpe[True].view(np.uint32))
     assert np.array_equal(gnorm[False].view(np.uint32), gpe[False].view(np.uint32))
-    # the unfold sums the complex64 values it writes; the unfolded epilogue sums the FP32 values
-    # before their split, which the merge rounds (the tolerance of test_gpe_norm_in_epilogue)
-    assert abs(nret[True] / nsep[True] - 1) <= 1e-12, (nret[True], nsep[True])
+    # the unfold sums the complex64 values it writes (|psi|^2 in FP32, times the FP64 weight, the
+    # sum in FP64: 2e-9 here); the unfolded epilogue sums the FP32 values before their split, which
+    # the merge rounds (the tolerance of test_gpe_norm_in_epilogue)
+    assert abs(nret[True] / nsep[True] - 1) <= 1e-8, (nret[True], nsep[True])
     assert abs(nret[False] / nsep[False] - 1) <= 2e-7, (nret[False], nsep[False])
 
 
