@@ -319,19 +319,45 @@ __device__ double abs2<double2>(const double2 &v) { return v.x * v.x + v.y * v.y
 template <>
 __device__ double abs2<float2>(const float2 &v) { return double(v.x) * v.x + double(v.y) * v.y; }
 
+// |v|^2 with the weight: FP32 data squared in FP32 (its rounding is unbiased), so that a point
+// costs one FP64 operation, the fused multiply-add with its weight; FP64 data in FP64.
+template <typename T>
+__device__ __forceinline__ double abs2_weighted(const T &v, double w)
+{
+    return abs2(v) * w;
+}
+template <>
+__device__ __forceinline__ double abs2_weighted<float2>(const float2 &v, double w)
+{
+    return double(v.x * v.x + v.y * v.y) * w;
+}
+template <>
+__device__ __forceinline__ double abs2_weighted<float>(const float &v, double w)
+{
+    return double(v * v) * w;
+}
+
 template <typename T>
 __global__ void norm2_kernel(int64_t n1, int64_t n2, int64_t n3, const T *u, const double *w1,
                              const double *w2, const double *w3, double *out)
 {
     const int64_t N = n1 * n2 * n3;
     double s = 0.0;
-    for (int64_t q = blockIdx.x * int64_t(blockDim.x) + threadIdx.x; q < N; q += int64_t(gridDim.x) * blockDim.x) {
-        double w = 1.0;
-        if (w1) {
-            const int64_t i1 = q % n1, i2 = (q / n1) % n2, i3 = q / (n1 * n2);
-            w = w1[i1] * w2[i2] * w3[i3];
+    if (!w1) {
+        for (int64_t q = blockIdx.x * int64_t(blockDim.x) + threadIdx.x; q < N; q += int64_t(gridDim.x) * blockDim.x)
+            s += abs2(u[q]);
+    } else {
+        // one warp per row (i2, i3) at a time: the row's weight w2 w3 once, then the row's points
+        // (no index division per point)
+        const int64_t warps = int64_t(gridDim.x) * (blockDim.x / 32), rows = n2 * n3;
+        const int lane = threadIdx.x & 31;
+        for (int64_t r = blockIdx.x * int64_t(blockDim.x / 32) + threadIdx.x / 32; r < rows; r += warps) {
+            const int64_t i2 = r % n2, i3 = r / n2;
+            const T *row = u + r * n1;
+            double sr = 0.0;
+            for (int64_t i1 = lane; i1 < n1; i1 += 32) sr += abs2_weighted(row[i1], w1[i1]);
+            s += sr * (w2[i2] * w3[i3]);
         }
-        s += abs2(u[q]) * w;
     }
     __shared__ double red[32];
     for (int o = 16; o > 0; o >>= 1) s += __shfl_down_sync(0xffffffffu, s, o);
