@@ -1230,6 +1230,30 @@ def test_fold_matches_unfolded(env, orc, monkeypatch, dims, mixed):
     assert rel(out[True], ora) <= TOL_MODE["f16x6"] * steps * len(dims)
 
 
+@pytest.mark.parametrize("dims", [(64, 48, 40), (33, 40, 17)])
+@pytest.mark.parametrize("prec", ["bf16x6", "bf16x3", "bf16", "tf32x3"])
+def test_fold_other_precisions(env, orc, monkeypatch, dims, prec):
+    """Folded steps in the other tensor-core precisions (floating BF16 pieces, TF32 pieces) match
+    the oracle to the precision's tolerance, as the unfolded ones do."""
+    mm, ctx, torch = env
+    monkeypatch.setenv("MM_FOLD_ALWAYS", "1")
+    tau, steps = 1e-4, 2
+    Es = [fd_schrodinger_E(mm, n, tau) for n in dims]
+    u0 = inputs.complex_normal(dims[::-1], seed=2).astype(np.complex64)
+    plan = mm.TuckerPlan(ctx, dims, Es, prec=prec)
+    assert plan.fold() == 7
+    u = to_gpu(torch, u0, torch.complex64)
+    plan.step(u, steps)
+    torch.cuda.synchronize()
+    ctx.status()
+    ref = orc.tucker(u0.astype(complex), [orc.expm_dirichlet_fd(n, 1j * tau) for n in dims], nsteps=steps)
+    err = rel(u.cpu().numpy(), ref)
+    print(f"folded {prec} dims={dims}: {err:.3e}")
+    tol = {"bf16x6": TOL_MODE["bf16x6"] * steps * len(dims), "bf16x3": TOL_STEP["bf16x3"], "bf16": TOL_STEP["bf16"],
+           "tf32x3": TOL_STEP["tf32x3"]}[prec]
+    assert err <= tol
+
+
 @pytest.mark.parametrize("m", [24, 25])
 def test_ho_fold_matches_unfolded(env, orc, monkeypatch, m):
     """Harmonic-oscillator steps of a Hermite plan run folded (the values-space propagators at
